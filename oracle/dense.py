@@ -1,0 +1,107 @@
+"""Brute force: the global collocation system that Algorithms 1-2 eliminate, assembled
+densely and solved with numpy.linalg.solve (tiny meshes only).
+
+Unknowns z = [u_g (all Gaussian nodes) ; u_ci of leaf 0 ; u_ci of leaf 1 ; ...].
+Equations, in this order:
+  1. every leaf interior Chebyshev node i:  A_ci,ci u_ci + A_ci,ce L_ce,ge u_ge = g_ci
+     (Eqs. local_sol and alpine2p5),
+  2. every interior Gaussian node j shared by the W/S leaf a and the E/N leaf b:
+     (D_ge,c u_c)_a(j) - (D_ge,c u_c)_b(j) = rho_j   (flux continuity, Sec. 4 / Eq. pair),
+  3. every boundary Gaussian node: u_j = f_j   (Eq. basic, Algorithm 2 root step),
+with u_c = [L_ce,ge u_ge on I_ce ; u_ci on I_ci] on each leaf.
+
+This module is oracle code (test infrastructure); see ``oracle/__init__.py``.
+"""
+import numpy as np
+
+from . import spectral as sp
+from .leaf import leaf_A
+
+
+def assemble(tree, coeffs, p):
+    """Return (K, meta): the dense system matrix and the index bookkeeping."""
+    q = tree.q
+    ce, ci, _ = sp.leaf_index_sets(p)
+    m = len(ci)
+    L = sp.L_ce_ge(p, q)
+    ng = tree.n_gauss
+    nl = tree.n_leaves
+    n = ng + nl * m
+    K = np.zeros((n, n))
+    row = 0
+    # map from leaf-local u_c (p^2) to global unknowns: u_c = E_l z
+    E = []
+    for lf in range(nl):
+        b = tree.boxes[tree.leaves[lf]]
+        El = np.zeros((p * p, n))
+        El[np.ix_(ce, b.ge)] = L
+        El[ci, ng + lf * m + np.arange(m)] = 1.0
+        E.append(El)
+    Arows = []
+    for lf in range(nl):
+        x0, y0, x1, y1 = tree.leaf_rect(lf)
+        A = leaf_A([coeffs[k][lf] for k in range(6)], p, x1 - x0, y1 - y0)
+        K[row:row + m] = A[ci] @ E[lf]
+        Arows.append(A[ci])
+        row += m
+    flux = []
+    for lf in range(nl):
+        x0, y0, x1, y1 = tree.leaf_rect(lf)
+        flux.append(sp.D_ge_c(p, q, x1 - x0, y1 - y0) @ E[lf])
+    for la, pa, lb, pb in tree.interior_pairs:
+        K[row] = flux[la][pa] - flux[lb][pb]
+        row += 1
+    for j in tree.boundary:
+        K[row, j] = 1.0
+        row += 1
+    assert row == n
+    return K, {"E": E, "m": m, "ci": ci, "ng": ng}
+
+
+def rhs(tree, p, f, g, rho=None):
+    """Right-hand side of the assembled system, same equation order."""
+    _, ci, _ = sp.leaf_index_sets(p)
+    g = np.asarray(g, dtype=np.float64)
+    f = np.asarray(f, dtype=np.float64)
+    if g.ndim == 2:
+        g = g[..., None]
+    if f.ndim == 1:
+        f = f[:, None]
+    nrhs = g.shape[-1]
+    parts = [g[lf][ci] for lf in range(tree.n_leaves)]
+    if rho is None:
+        parts.append(np.zeros((len(tree.interior_pairs), nrhs)))
+    else:
+        rho = np.asarray(rho, dtype=np.float64).reshape(tree.n_gauss, -1)
+        parts.append(rho[tree.interior])
+    parts.append(f)
+    return np.vstack(parts)
+
+
+def solve(tree, coeffs, p, f, g, rho=None):
+    """Dense solve; returns (u_c (n_leaf, p^2, nrhs), u_g (n_gauss, nrhs))."""
+    K, meta = assemble(tree, coeffs, p)
+    z = np.linalg.solve(K, rhs(tree, p, f, g, rho))
+    u_c = np.array([El @ z for El in meta["E"]])
+    return u_c, z[:meta["ng"]]
+
+
+def solve_transpose(tree, coeffs, p, ubar):
+    """The adjoint by brute force: lambda = K^-T (dJ/dz), with dJ/dz = sum_l E_l^T ubar_l.
+    Returns (fbar, gbar, rhobar) laid out like oracle.hps.adjoint."""
+    K, meta = assemble(tree, coeffs, p)
+    ubar = np.asarray(ubar, dtype=np.float64)
+    if ubar.ndim == 2:
+        ubar = ubar[..., None]
+    dz = sum(meta["E"][lf].T @ ubar[lf] for lf in range(tree.n_leaves))
+    lam = np.linalg.solve(K.T, dz)
+    m, ci = meta["m"], meta["ci"]
+    nl = tree.n_leaves
+    gbar = np.zeros((nl, p * p, ubar.shape[-1]))
+    for lf in range(nl):
+        gbar[lf][ci] = lam[lf * m:(lf + 1) * m]
+    nint = len(tree.interior_pairs)
+    rhobar = np.zeros((tree.n_gauss, ubar.shape[-1]))
+    rhobar[tree.interior] = lam[nl * m:nl * m + nint]
+    fbar = lam[nl * m + nint:]
+    return fbar, gbar, rhobar

@@ -1,0 +1,45 @@
+"""Test helpers: node coordinates and manufactured data built from the oracle's tables
+(never from the GPU library), so that every input the parity tests feed to both sides
+comes from the oracle or from ``synthetic``."""
+import numpy as np
+
+from oracle import spectral as sp
+
+
+def leaf_points(tree, p):
+    """(X, Y), each (n_leaf, p^2): leaf Chebyshev node coordinates, node iy * p + ix."""
+    X, Y = [], []
+    for lf in range(tree.n_leaves):
+        x0, y0, x1, y1 = tree.leaf_rect(lf)
+        x, y = sp.leaf_cheb_points(x0, y0, x1 - x0, y1 - y0, p)
+        X.append(x)
+        Y.append(y)
+    return np.array(X), np.array(Y)
+
+
+def boundary_points(tree):
+    gp = tree.gauss_points()
+    return gp[tree.boundary, 0], gp[tree.boundary, 1]
+
+
+def poly_data(X, Y, coeffs, a, b):
+    """u = x^a y^b and g = A u evaluated in closed form (Eq. defA)."""
+    def mono(i, j, dx, dy):
+        cx = 1.0
+        for k in range(dx):
+            cx *= (i - k)
+        cy = 1.0
+        for k in range(dy):
+            cy *= (j - k)
+        if cx == 0.0 or cy == 0.0:
+            return np.zeros_like(X)
+        return cx * cy * X ** (i - dx) * Y ** (j - dy)
+    u = mono(a, b, 0, 0)
+    c11, c12, c22, c1, c2, c0 = coeffs
+    g = (-c11 * mono(a, b, 2, 0) - 2 * c12 * mono(a, b, 1, 1) - c22 * mono(a, b, 0, 2)
+         + c1 * mono(a, b, 1, 0) + c2 * mono(a, b, 0, 1) + c0 * u)
+    return u, g
+
+
+def rel_linf(a, b):
+    return float(np.max(np.abs(np.asarray(a) - np.asarray(b))) / max(np.max(np.abs(b)), 1e-300))
