@@ -1,0 +1,171 @@
+/*
+ * hps.h -- C ABI of the GB300 (sm_103a) hierarchical Poincare-Steklov direct solver for
+ * variable-coefficient 2D elliptic problems with body loads.
+ *
+ * Problem (Sec. 1, Eqs. basic and defA):
+ *     A u = g in Omega,  u = f on the boundary of Omega,
+ *     A u = -c11 u_xx - 2 c12 u_xy - c22 u_yy + c1 u_x + c2 u_y + c u.
+ * Omega is a rectangle split into a binary tree of boxes (Sec. 2).  Each leaf carries a
+ * p x p Chebyshev-Lobatto grid (Sec. 3.1) and q Gauss-Legendre nodes per side (Sec. 2).
+ *
+ * Conventions shared by every call:
+ *  - Leaves are numbered j * nx + i (x fastest).  Leaf Chebyshev nodes are numbered
+ *    iy * p + ix (x fastest), ascending coordinates.
+ *  - Gaussian nodes get global ids edge by edge, visiting leaves in leaf order and their
+ *    sides in the order S, E, N, W; the q ids of one edge ascend along it.  "Boundary
+ *    order" lists the domain-boundary Gaussian nodes in ascending global id.
+ *  - Fluxes are d/dx on vertical and d/dy on horizontal edges (Sec. 3.1).
+ *  - Multi-RHS arrays put the right-hand-side index fastest: [row][rhs].
+ *  - All floating-point inputs and outputs are FP64.  Device pointers are plain CUDA
+ *    device addresses; "stream" is a cudaStream_t passed as void* (NULL = legacy stream).
+ *  - Every call returns an hps_status.  Nothing aborts, traps or exits the process; the
+ *    text of the last error of the calling thread is returned by hps_last_error().
+ *  - Calls taking a stream are stream-ordered.  hps_solve and hps_adjoint return once
+ *    their work is enqueued (the iterative-refinement path of HPS_MIXED synchronises
+ *    the stream once per refinement step to test convergence).  Errors found by device
+ *    code (singular pivots) are reported by hps_build (which synchronises) and by
+ *    hps_sync_status.
+ */
+#ifndef HPS_GB300_H
+#define HPS_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HPS_OK = 0,
+  HPS_ERR_INVALID_ARG = 1,   /* bad pointer, size, tree or option                      */
+  HPS_ERR_NOT_ELLIPTIC = 2,  /* reserved: c11 c22 - c12^2 <= 0 detected by the caller    */
+  HPS_ERR_SINGULAR = 3,      /* a leaf or merge pivot fell below tiny * scale            */
+  HPS_ERR_OOM = 4,           /* the allocator returned NULL                              */
+  HPS_ERR_CUDA = 5,          /* a CUDA runtime call failed (message has the CUDA text)   */
+  HPS_ERR_TIMEOUT = 6,       /* reserved for bounded device waits                        */
+  HPS_ERR_NO_CONVERGENCE = 7,/* iterative refinement hit ir_max_iter                     */
+  HPS_ERR_STATE = 8          /* call not valid for this handle (e.g. precision)          */
+} hps_status;
+
+typedef enum { HPS_FP64 = 0, HPS_MIXED = 1 } hps_precision;
+
+typedef enum {
+  HPS_NODES_CHEB_LEAF = 0,      /* n_leaf * p * p points, leaf-major                     */
+  HPS_NODES_GAUSS_BOUNDARY = 1, /* domain-boundary Gaussian nodes in boundary order      */
+  HPS_NODES_GAUSS_ALL = 2       /* every Gaussian node, by global id                     */
+} hps_node_set;
+
+typedef struct hps_tree hps_tree;     /* opaque, host memory                              */
+typedef struct hps_handle hps_handle; /* opaque, owns the device operator store          */
+
+/* Device memory allocator.  alloc returns a device pointer or NULL; free releases it.
+ * Both receive the stream the call runs on.  A NULL allocator means cudaMallocAsync /
+ * cudaFreeAsync on that stream. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* ctx, void* stream);
+  void (*free)(void* ptr, void* ctx, void* stream);
+  void* ctx;
+} hps_allocator;
+
+typedef struct {
+  int precision;       /* HPS_FP64 or HPS_MIXED                                           */
+  int q;               /* Gauss nodes per leaf side; 0 means p - 1 (Sec. 7)                */
+  int store_leaf_ops;  /* 1: keep leaf F, S, H (Sec. 5.2); 0 is reserved (must be 1)       */
+  double ir_tol;       /* HPS_MIXED: stop when max|du| <= ir_tol * max|u|; 0 means 1e-10   */
+  int ir_max_iter;     /* HPS_MIXED: refinement steps allowed; 0 means 10                  */
+  int fp64_top_levels; /* HPS_MIXED: number of top merge levels kept in FP64; -1 means 1   */
+} hps_opts;
+
+/* Fills *opts with the defaults above (FP64, q = p - 1, store leaf operators). */
+void hps_opts_default(hps_opts* opts);
+
+/* Uniform tree of nx x ny equal leaves over [x0,x1] x [y0,y1] by recursive halving
+ * (Sec. 2): a box is cut across its longer side in leaves, vertically on ties; the W
+ * (or S) half is the first child.  *out receives a new tree (free with
+ * hps_tree_destroy).  INVALID_ARG if nx, ny < 1, x1 <= x0, y1 <= y0 or out is NULL. */
+int hps_tree_uniform(double x0, double y0, double x1, double y1, int nx, int ny, hps_tree** out);
+int hps_tree_destroy(hps_tree* tree);
+
+/* Counts: leaves, boxes, tree height (merge levels), and for a given q the number of
+ * Gaussian nodes (all, and on the domain boundary). */
+int hps_tree_info(const hps_tree* tree, int q, int* n_leaves, int* n_boxes, int* n_levels,
+                  int* n_gauss, int* n_boundary);
+
+/* Coordinates of a node set (host memory): xy_host receives 2 * count doubles
+ * (x0, y0, x1, y1, ...).  If xy_host is NULL only *count is written. */
+int hps_nodes(const hps_tree* tree, int p, int q, int which, double* xy_host, int64_t* count);
+
+/* Host-only dry run of hps_build's planning for this tree, p and options: builds the
+ * index tables and every kernel descriptor of the build, solve and adjoint, and checks
+ * each against the size of the buffer it addresses.  Touches no GPU.  OK, or
+ * INVALID_ARG with the failed check in the message (unsupported tree shapes included). */
+int hps_plan_check(const hps_tree* tree, int p, const hps_opts* opts);
+
+/* Build stage (Algorithm 1).  coeffs_dev: device FP64 [6][n_leaf][p*p] holding c11, c12,
+ * c22, c1, c2, c at every leaf Chebyshev node (exterior values are unused).  The leaf
+ * step forms A on each leaf, factors A_ci,ci and writes F, S, H, T (Sec. 3, Eqs.
+ * alpine1-alpine4); each merge forms X, S, T from the children (Sec. 4).  p in [4, 32].
+ * The library does not keep coeffs_dev.  opts and alloc may be NULL (defaults).  The
+ * call synchronises the stream before it returns and reports SINGULAR with the box id
+ * in the message if a pivot broke down.  *out receives the handle. */
+int hps_build(const hps_tree* tree, const double* coeffs_dev, int p, const hps_opts* opts,
+              const hps_allocator* alloc, void* stream, hps_handle** out);
+
+/* Solve stage (Algorithm 2) for nrhs right-hand sides at once.
+ *   f_dev : [n_boundary][nrhs]        Dirichlet data at the boundary Gaussian nodes
+ *   g_dev : [n_leaf][p*p][nrhs]       body load at the leaf Chebyshev nodes (interior
+ *                                     values used)
+ *   u_dev : [n_leaf][p*p][nrhs]       output: the solution at every leaf Chebyshev node
+ * FP64 handles run the sweeps in FP64.  HPS_MIXED handles run them in FP32 and refine
+ * against the FP64 residual of the collocation system (leaf equations and flux jumps)
+ * until max|du| <= ir_tol max|u|, returning NO_CONVERGENCE after ir_max_iter steps. */
+int hps_solve(hps_handle* h, const double* f_dev, const double* g_dev, int nrhs, double* u_dev,
+              void* stream);
+
+/* hps_solve with extras: rho_dev (may be NULL) is a right-hand side for the flux
+ * continuity equations, [n_gauss][nrhs] by global id (entries off interior nodes are
+ * ignored); ug_dev (may be NULL) receives the solution at every Gaussian node
+ * [n_gauss][nrhs]; iters (may be NULL) receives the refinement steps taken. */
+int hps_solve_ext(hps_handle* h, const double* f_dev, const double* g_dev, const double* rho_dev,
+                  int nrhs, double* u_dev, double* ug_dev, int* iters, void* stream);
+
+/* Adjoint of the solve (transposed Algorithm 2 sweeps).  dJdu_dev: [n_leaf][p*p][nrhs],
+ * the gradient of a functional with respect to the output of hps_solve.  Outputs (each
+ * may be NULL): dJdf_dev [n_boundary][nrhs], dJdg_dev [n_leaf][p*p][nrhs] (zero at
+ * exterior nodes), dJdcoeffs_dev [6][n_leaf][p*p] (summed over right-hand sides; needs
+ * u_dev, the forward solution of hps_solve for the same nrhs).  Uses the FP64 operator
+ * store, so the handle must be HPS_FP64 (STATE otherwise). */
+int hps_adjoint(hps_handle* h, const double* dJdu_dev, int nrhs, const double* u_dev,
+                double* dJdf_dev, double* dJdg_dev, double* dJdcoeffs_dev, void* stream);
+
+/* Sizes held by a handle: leaves, p, q, Gaussian nodes, boundary nodes, operator bytes. */
+int hps_handle_info(const hps_handle* h, int* n_leaves, int* p, int* q, int* n_gauss,
+                    int* n_boundary, int64_t* operator_bytes);
+
+/* Reads the device status word of the handle (synchronising the stream): OK or the
+ * first device-detected error. */
+int hps_sync_status(hps_handle* h, void* stream);
+
+int hps_destroy(hps_handle* h);
+
+/* Launch timing, process-wide.  While enabled, every kernel launch of the library is
+ * bracketed by CUDA events on its stream and filed under a category name (kernel and
+ * step) with the algorithmic flops and bytes of that launch.  hps_timing_count
+ * synchronises on the recorded events and returns the number of categories;
+ * hps_timing_get reads category i (name copied into name[0..name_len)).  Totals
+ * accumulate until hps_timing_reset.  Disabled by default. */
+int hps_timing_enable(int on);
+int hps_timing_reset(void);
+int hps_timing_count(int* n);
+int hps_timing_get(int i, char* name, int name_len, int64_t* launches, double* ms, double* flops,
+                   double* bytes);
+
+/* Message of the last failed call on this thread ("" if none).  Valid until the next
+ * call on the same thread. */
+const char* hps_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HPS_GB300_H */

@@ -1,0 +1,1380 @@
+// C ABI of the GB300 HPS solver: tree construction, the build stage (Algorithm 1), the
+// solve stage (Algorithm 2) in FP64 or FP32 with FP64 iterative refinement, and the
+// adjoint (transposed Algorithm 2 sweeps).  Host code here only plans: every arithmetic
+// step of the build, the solve, the residual and the adjoint runs in the kernels.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "hps_internal.h"
+
+namespace hps {
+int make_uniform_tree(double x0, double y0, double x1, double y1, int nx, int ny, Tree& t);
+}
+
+using namespace hps;
+
+struct hps_tree {
+  Tree t;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+struct CudaError {
+  int code;
+  std::string msg;
+};
+
+#define CK(call)                                                                                    \
+  do {                                                                                              \
+    cudaError_t e_ = (call);                                                                        \
+    if (e_ != cudaSuccess)                                                                          \
+      throw CudaError{HPS_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)};            \
+  } while (0)
+
+#define CKL()                                                                                       \
+  do {                                                                                              \
+    cudaError_t e_ = cudaGetLastError();                                                            \
+    if (e_ != cudaSuccess)                                                                          \
+      throw CudaError{HPS_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)};       \
+  } while (0)
+
+struct Alloc {
+  hps_allocator a{};
+  bool custom = false;
+  void* get(size_t bytes, cudaStream_t s) {
+    if (bytes == 0) bytes = 16;
+    void* p = nullptr;
+    if (custom) {
+      p = a.alloc(bytes, a.ctx, (void*)s);
+    } else {
+      if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+      }
+    }
+    if (!p) throw CudaError{HPS_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed"};
+    return p;
+  }
+  void put(void* p, cudaStream_t s) {
+    if (!p) return;
+    if (custom) a.free(p, a.ctx, (void*)s);
+    else cudaFreeAsync(p, s);
+  }
+};
+
+// Device buffer owned by a handle.
+struct DBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+template <typename T>
+T* upload(Alloc& al, cudaStream_t s, const std::vector<T>& v, std::vector<DBuf>& owned) {
+  void* p = al.get(v.size() * sizeof(T), s);
+  owned.push_back({p, v.size() * sizeof(T)});
+  if (!v.empty()) CK(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+  return (T*)p;
+}
+
+constexpr int ROWBLK = 64;
+
+#define TIMED(name, fl, by, ...)                                  \
+  do {                                                            \
+    TimingScope ts_((name), s, (double)(fl), (double)(by));       \
+    __VA_ARGS__;                                                  \
+  } while (0)
+
+template <typename T>
+const char* tsuf() {
+  return sizeof(T) == 8 ? "f64" : "f32";
+}
+
+void add_product(std::vector<GemmItem>& out, long long a_base, int lda, int M, int K, int kseg, int b0_row,
+                 int b0_idx, int b1_row, int b1_idx, int c_row, int c_idx, int add_row, bool trans) {
+  for (int r0 = 0; r0 < M; r0 += ROWBLK) {
+    GemmItem it;
+    it.a_off = trans ? a_base + r0 : a_base + (long long)r0 * lda;
+    it.lda = lda;
+    it.M = std::min(ROWBLK, M - r0);
+    it.K = K;
+    it.kseg = kseg;
+    it.b0_row = b0_row;
+    it.b0_idx = b0_idx;
+    it.b1_row = b1_row;
+    it.b1_idx = b1_idx;
+    if (c_idx >= 0) {
+      it.c_row = c_row;
+      it.c_idx = c_idx + r0;
+    } else {
+      it.c_row = c_row + r0;
+      it.c_idx = -1;
+    }
+    it.add_row = add_row >= 0 ? add_row + r0 : -1;
+    out.push_back(it);
+  }
+}
+
+struct ItemSet {
+  GemmItem* dev = nullptr;
+  int n = 0;
+  double elems = 0.0;  // operator entries streamed by one application
+};
+
+struct Level {
+  std::vector<int> boxes;  // merges at this height
+  bool fp64 = true;        // precision of the elimination
+  int maxR = 0, maxK = 0;
+  // build
+  GJDesc* gj = nullptr;
+  MergeDesc* md = nullptr;
+  long long* off_tl = nullptr;  // per matrix extraction offsets (Mleft, CX rows, S, T)
+  long long* off_bl = nullptr;
+  long long* off_tr = nullptr;
+  long long* off_br = nullptr;
+  long long work_elems = 0;
+  int perm_elems = 0;
+  // solve
+  UpGather* ug = nullptr;
+  int ug_maxrows = 0;
+  ItemSet up, down;
+  // adjoint
+  int* wcopy_tab = nullptr;
+  int n_wcopy = 0;
+  ItemSet adjS;
+  int* reduce_tab = nullptr;
+  int n_reduce = 0;
+  ItemSet adjM;
+  DownScatter* ds = nullptr;
+  int ds_maxrows = 0;
+};
+
+struct Workspace {
+  int nrhs = 0;
+  size_t bytes = 0;
+  std::vector<void*> ptrs;
+  // FP64 path
+  double* V64 = nullptr;
+  double* d64 = nullptr;
+  double* ug64 = nullptr;
+  // FP32 path
+  float* V32 = nullptr;
+  float* d32 = nullptr;
+  float* ug32 = nullptr;
+  float* g32 = nullptr;
+  float* uc32 = nullptr;
+  float* rho32 = nullptr;
+  // refinement
+  double* r64 = nullptr;
+  double* vflux = nullptr;
+  double* rho64 = nullptr;
+  double* scal = nullptr;
+  // adjoint
+  double* LB = nullptr;
+  double* UB = nullptr;
+  double* ubar = nullptr;
+};
+
+}  // namespace
+
+struct hps_handle {
+  Alloc al;
+  std::vector<DBuf> owned;
+  Tree tree;
+  NodeSets ns;
+  RefTables rt;
+  hps_opts opts{};
+  int p = 0, q = 0, m = 0, nq = 0, ne = 0, pp = 0, n_leaf = 0, n_bdry = 0;
+  // tables
+  double *dD = nullptr, *dD2 = nullptr, *dLs = nullptr, *dLloc = nullptr, *dDceL = nullptr;
+  double* dhxy = nullptr;
+  int* didx = nullptr;
+  int* d_leaf_edges = nullptr;
+  int* d_pairs = nullptr;
+  int npairs = 0;
+  int off_ci = 0, off_ce = 0, off_bnd = 0;
+  std::vector<int> off_ge, off_J3;
+  int* d_status = nullptr;
+  // operators
+  double* ops64 = nullptr;
+  float* ops32 = nullptr;
+  long long ops_elems = 0;
+  long long gl_base = 0, h_base = 0, lce_base = 0;
+  std::vector<long long> mo, so;  // per box: Mleft and S offsets
+  std::vector<long long> toff;    // per box: T block offset in the build's T store
+  std::vector<int> k3, k12;
+  // vector layouts (in rows)
+  std::vector<int> vrow, drow, ubrow;
+  int v_rows = 0, d_rows = 0, ub_rows = 0;
+  // plans
+  std::vector<Level> levels;  // index = height - 1
+  ItemSet leafup, leafdown, lce;
+  ItemSet adj_leafF, adj_leafS, adj_lce, adj_leafH;
+  double* coeffs_copy = nullptr;  // FP64 coefficients, kept for the mixed-precision residual
+  int* leaf_reduce_tab = nullptr;
+  int n_leaf_reduce = 0;
+  int* fbar_tab = nullptr;
+  // workspace
+  Workspace ws;
+  ~hps_handle() {
+    if (ws.ptrs.empty() && owned.empty()) return;
+    for (void* p : ws.ptrs) al.put(p, 0);
+    for (auto& b : owned) al.put(b.p, 0);
+    cudaStreamSynchronize(0);
+  }
+  int hrow(int box) const { return vrow[box] + (tree.boxes[box].leaf >= 0 ? 0 : k3[box]); }
+};
+
+namespace {
+
+ItemSet upload_items(hps_handle* h, cudaStream_t s, const std::vector<GemmItem>& v) {
+  ItemSet is;
+  is.n = (int)v.size();
+  for (const GemmItem& it : v) is.elems += (double)it.M * it.K;
+  is.dev = v.empty() ? nullptr : upload(h->al, s, v, h->owned);
+  return is;
+}
+
+// ---------------------------------------------------------------------------------------
+// Plan: index tables, operator offsets, vector layouts and the product items of every
+// step of the solve and the adjoint.  Built on the host, checked against the buffer
+// sizes (validate_plan), then uploaded.
+struct LevelHost {
+  std::vector<GJDesc> gj;
+  std::vector<MergeDesc> md;
+  std::vector<long long> tl, bl, tr, br;
+  std::vector<UpGather> ug;
+  std::vector<GemmItem> up, down, adjS, adjM;
+  std::vector<int> wcopy, reduce;
+  std::vector<DownScatter> ds;
+};
+
+struct HostPlan {
+  std::vector<int> idx;
+  std::vector<LevelHost> lv;
+  std::vector<GemmItem> lup, ldown, llce, aF, aS, aL, aH;
+  std::vector<int> lred, ftab, pairs;
+  long long tsz = 0;
+};
+
+void make_plan(hps_handle* h, HostPlan& hp) {
+  const Tree& t = h->tree;
+  const NodeSets& ns = h->ns;
+  const RefTables& rt = h->rt;
+  const int nb = (int)t.boxes.size();
+  const int q = h->q, m = h->m, nq = h->nq, pp = h->pp;
+  std::vector<int>& idx = hp.idx;
+  auto push = [&](const std::vector<int>& v) {
+    const int off = (int)idx.size();
+    idx.insert(idx.end(), v.begin(), v.end());
+    return off;
+  };
+  h->off_ci = push(rt.ci);
+  h->off_ce = push(rt.ce);
+  h->off_bnd = push(ns.boundary);
+  h->off_ge.assign(nb, -1);
+  h->off_J3.assign(nb, -1);
+  h->k3.assign(nb, 0);
+  h->k12.assign(nb, 0);
+  for (int b = 0; b < nb; ++b) {
+    h->off_ge[b] = push(ns.ge[b]);
+    h->k12[b] = (int)ns.ge[b].size();
+    if (t.boxes[b].leaf < 0) {
+      h->off_J3[b] = push(ns.J3[b]);
+      h->k3[b] = (int)ns.J3[b].size();
+    }
+  }
+  // operator pool layout
+  long long off = 0;
+  h->gl_base = off;
+  off += (long long)h->n_leaf * m * (m + nq);
+  h->h_base = off;
+  off += (long long)h->n_leaf * nq * m;
+  h->lce_base = off;
+  off += (long long)h->ne * nq;
+  h->mo.assign(nb, -1);
+  h->so.assign(nb, -1);
+  for (int b = 0; b < nb; ++b) {
+    if (t.boxes[b].leaf >= 0) continue;
+    const int R = h->k3[b] + h->k12[b];
+    h->mo[b] = off;
+    off += (long long)R * h->k3[b];
+    h->so[b] = off;
+    off += (long long)h->k3[b] * h->k12[b];
+  }
+  h->ops_elems = off;
+  // vector layouts
+  h->vrow.assign(nb, 0);
+  h->drow.assign(nb, -1);
+  h->ubrow.assign(nb, -1);
+  int vr = 0, dr = 0, ur = 0;
+  for (int b = 0; b < nb; ++b) {
+    h->vrow[b] = vr;
+    if (t.boxes[b].leaf >= 0) {
+      vr += nq;
+    } else {
+      vr += h->k3[b] + h->k12[b];
+      h->drow[b] = dr;
+      dr += h->k3[b];
+      h->ubrow[b] = ur;
+      ur += h->k12[b];
+    }
+  }
+  h->v_rows = vr;
+  h->d_rows = dr;
+  h->ub_rows = ur;
+
+  // positions of each node in each box's exterior list
+  auto posmap = [&](int b) {
+    std::unordered_map<int, int> mp;
+    mp.reserve(ns.ge[b].size() * 2);
+    for (size_t k = 0; k < ns.ge[b].size(); ++k) mp[ns.ge[b][k]] = (int)k;
+    return mp;
+  };
+
+  // levels
+  const int H = t.height;
+  h->levels.assign(H, Level());
+  for (int b = 0; b < nb; ++b)
+    if (t.boxes[b].leaf < 0) h->levels[t.boxes[b].height - 1].boxes.push_back(b);
+  int top64 = h->opts.fp64_top_levels < 0 ? 1 : h->opts.fp64_top_levels;
+  hp.lv.assign(H, LevelHost());
+  // T store offsets per box (children T blocks live there until the build ends): the
+  // leaves first, in leaf order (the leaf extraction writes them with a fixed stride),
+  // then the parents.
+  std::vector<long long>& toff = h->toff;
+  toff.assign(nb, -1);
+  long long tsz = 0;
+  for (int lf = 0; lf < h->n_leaf; ++lf) {
+    toff[t.leaves[lf]] = tsz;
+    tsz += (long long)nq * nq;
+  }
+  for (int b = 0; b < nb; ++b) {
+    if (t.boxes[b].leaf >= 0) continue;
+    toff[b] = tsz;
+    tsz += (long long)h->k12[b] * h->k12[b];
+  }
+  for (int L = 0; L < H; ++L) {
+    Level& lv = h->levels[L];
+    LevelHost& pd = hp.lv[L];
+    lv.fp64 = (h->opts.precision == HPS_FP64) || (L >= H - top64);
+    long long woff = 0;
+    int poff = 0;
+    std::unordered_map<int, std::pair<int, int>> red;  // node -> (ub row 1, ub row 2)
+    std::vector<int> red_order;
+    for (int b : lv.boxes) {
+      const Box& bx = t.boxes[b];
+      const int a = bx.child[0], c = bx.child[1];
+      const int k3 = h->k3[b], k12 = h->k12[b], R = k3 + k12, n1 = ns.n1[b], n2 = k12 - n1;
+      lv.maxR = std::max(lv.maxR, R);
+      lv.maxK = std::max(lv.maxK, k3);
+      auto pa = posmap(a), pc = posmap(c);
+      std::vector<int> posA(R, -1), posB(R, -1);
+      const std::vector<int>& J3 = ns.J3[b];
+      const std::vector<int>& ge = ns.ge[b];
+      for (int k = 0; k < k3; ++k) {
+        posA[k] = pa.at(J3[k]);
+        posB[k] = pc.at(J3[k]);
+      }
+      for (int i = 0; i < n1; ++i) posA[k3 + i] = pa.at(ge[i]);
+      for (int i = 0; i < n2; ++i) posB[k3 + n1 + i] = pc.at(ge[n1 + i]);
+      MergeDesc md;
+      md.m_off = woff;
+      md.R = R;
+      md.k3 = k3;
+      md.n1 = n1;
+      md.ta_off = toff[a];
+      md.tb_off = toff[c];
+      md.lda_a = h->k12[a];
+      md.lda_b = h->k12[c];
+      md.pos_off = push(posA);
+      push(posB);
+      pd.md.push_back(md);
+      GJDesc gd;
+      gd.off = woff;
+      gd.R = R;
+      gd.K = k3;
+      gd.perm_off = poff;
+      gd.box = b;
+      pd.gj.push_back(gd);
+      woff += (long long)R * R;
+      poff += k3;
+      pd.tl.push_back(h->mo[b]);
+      pd.bl.push_back(h->mo[b] + (long long)k3 * k3);
+      pd.tr.push_back(h->so[b]);
+      pd.br.push_back(toff[b]);
+      // up-sweep gather lists: pos3a, pos3b, J3, pos1a, pos2b
+      std::vector<int> lst;
+      for (int k = 0; k < k3; ++k) lst.push_back(posA[k]);
+      for (int k = 0; k < k3; ++k) lst.push_back(posB[k]);
+      for (int k = 0; k < k3; ++k) lst.push_back(J3[k]);
+      for (int i = 0; i < n1; ++i) lst.push_back(posA[k3 + i]);
+      for (int i = 0; i < n2; ++i) lst.push_back(posB[k3 + n1 + i]);
+      const int loff = push(lst);
+      UpGather ug;
+      ug.va_row = h->hrow(a);
+      ug.vb_row = h->hrow(c);
+      ug.vt_row = h->vrow[b];
+      ug.d_row = h->drow[b];
+      ug.k3 = k3;
+      ug.n1 = n1;
+      ug.n2 = n2;
+      ug.idx_off = loff;
+      pd.ug.push_back(ug);
+      lv.ug_maxrows = std::max(lv.ug_maxrows, 2 * k3 + n1 + n2);
+      DownScatter ds;
+      ds.va_row = ug.va_row;
+      ds.vb_row = ug.vb_row;
+      ds.vt_row = ug.vt_row;
+      ds.d_row = ug.d_row;
+      ds.k3 = k3;
+      ds.n1 = n1;
+      ds.n2 = n2;
+      ds.idx_off = loff;
+      pd.ds.push_back(ds);
+      lv.ds_maxrows = std::max(lv.ds_maxrows, k3 + n1 + n2);
+      // up: [w; h] += [X; CX] d
+      add_product(pd.up, h->mo[b], k3, R, k3, k3, h->drow[b], -1, 0, -1, h->vrow[b], -1, -1, false);
+      // down: u[J3] = S u[ge] + w
+      add_product(pd.down, h->so[b], k12, k3, k12, k12, 0, h->off_ge[b], 0, -1, 0, h->off_J3[b], h->vrow[b], false);
+      // adjoint: wbar copy, S^T ubar[J3] -> UB, reduce into ubar[ge]
+      for (int k = 0; k < k3; ++k) {
+        pd.wcopy.push_back(h->vrow[b] + k);
+        pd.wcopy.push_back(J3[k]);
+        pd.wcopy.push_back(-1);
+      }
+      add_product(pd.adjS, h->so[b], k12, k12, k3, k3, 0, h->off_J3[b], 0, -1, h->ubrow[b], -1, -1, true);
+      for (int k = 0; k < k12; ++k) {
+        const int g = ge[k];
+        auto it = red.find(g);
+        if (it == red.end()) {
+          red[g] = {h->ubrow[b] + k, -1};
+          red_order.push_back(g);
+        } else {
+          it->second.second = h->ubrow[b] + k;
+        }
+      }
+      // adjoint: dbar = [X; CX]^T [wbar; hbar]
+      add_product(pd.adjM, h->mo[b], k3, k3, R, R, h->vrow[b], -1, 0, -1, h->drow[b], -1, -1, true);
+    }
+    lv.work_elems = woff;
+    lv.perm_elems = poff;
+    for (int g : red_order) {
+      pd.reduce.push_back(g);
+      pd.reduce.push_back(red[g].first);
+      pd.reduce.push_back(red[g].second);
+    }
+  }
+  hp.tsz = tsz;
+  // leaf items
+  std::vector<GemmItem>&lup = hp.lup, &ldown = hp.ldown, &llce = hp.llce, &aF = hp.aF, &aS = hp.aS, &aL = hp.aL,
+                        &aH = hp.aH;
+  for (int lf = 0; lf < h->n_leaf; ++lf) {
+    const int b = t.leaves[lf];
+    const long long gl = h->gl_base + (long long)lf * m * (m + nq);
+    const long long hb = h->h_base + (long long)lf * nq * m;
+    add_product(lup, hb, m, nq, m, m, lf * pp, h->off_ci, 0, -1, h->vrow[b], -1, -1, false);
+    add_product(ldown, gl, m + nq, m, m + nq, m, lf * pp, h->off_ci, 0, h->off_ge[b], lf * pp, h->off_ci, -1, false);
+    add_product(llce, h->lce_base, nq, h->ne, nq, nq, 0, h->off_ge[b], 0, -1, lf * pp, h->off_ce, -1, false);
+    // adjoint: gbar_ci = F^T ubar_ci ; LB = S_ci^T ubar_ci + Lce^T ubar_ce ; gbar += H^T hbar
+    add_product(aF, gl, m + nq, m, m, m, lf * pp, h->off_ci, 0, -1, lf * pp, h->off_ci, -1, true);
+    add_product(aS, gl + m, m + nq, nq, m, m, lf * pp, h->off_ci, 0, -1, lf * nq, -1, -1, true);
+    add_product(aL, h->lce_base, nq, nq, h->ne, h->ne, lf * pp, h->off_ce, 0, -1, lf * nq, -1, -1, true);
+    add_product(aH, hb, m, m, nq, nq, h->hrow(b), -1, 0, -1, lf * pp, h->off_ci, -1, true);
+  }
+  // ubar[j] = sum over the (one or two) leaves owning j of LB[leaf][pos]
+  std::vector<int>& lred = hp.lred;
+  for (int e = 0; e < t.n_edges; ++e) {
+    const int o1 = t.edge_owners[2 * e], o2 = t.edge_owners[2 * e + 1];
+    for (int k = 0; k < q; ++k) {
+      lred.push_back(e * q + k);
+      lred.push_back((o1 / 4) * nq + (o1 % 4) * q + k);
+      lred.push_back(o2 >= 0 ? (o2 / 4) * nq + (o2 % 4) * q + k : -1);
+    }
+  }
+  std::vector<int>& ftab = hp.ftab;
+  for (size_t k = 0; k < ns.boundary.size(); ++k) {
+    ftab.push_back((int)k);
+    ftab.push_back(ns.boundary[k]);
+    ftab.push_back(-1);
+  }
+  // interior edge pairs for the jump residual (a = the leaf west/south of the edge)
+  std::vector<int>& pairs = hp.pairs;
+  for (int e = 0; e < t.n_edges; ++e) {
+    int o1 = t.edge_owners[2 * e], o2 = t.edge_owners[2 * e + 1];
+    if (o2 < 0) continue;
+    const int s1 = o1 % 4;
+    if (s1 == 0 || s1 == 3) std::swap(o1, o2);  // o1 on its S or W side -> it is the E/N leaf
+    pairs.push_back(e);
+    pairs.push_back(o1 / 4);
+    pairs.push_back(o1 % 4);
+    pairs.push_back(o2 / 4);
+    pairs.push_back(o2 % 4);
+  }
+  h->npairs = (int)pairs.size() / 5;
+}
+
+void upload_plan(hps_handle* h, const HostPlan& hp, cudaStream_t s) {
+  h->didx = upload(h->al, s, hp.idx, h->owned);
+  for (size_t L = 0; L < hp.lv.size(); ++L) {
+    Level& lv = h->levels[L];
+    const LevelHost& pd = hp.lv[L];
+    lv.gj = upload(h->al, s, pd.gj, h->owned);
+    lv.md = upload(h->al, s, pd.md, h->owned);
+    lv.off_tl = upload(h->al, s, pd.tl, h->owned);
+    lv.off_bl = upload(h->al, s, pd.bl, h->owned);
+    lv.off_tr = upload(h->al, s, pd.tr, h->owned);
+    lv.off_br = upload(h->al, s, pd.br, h->owned);
+    lv.ug = upload(h->al, s, pd.ug, h->owned);
+    lv.up = upload_items(h, s, pd.up);
+    lv.down = upload_items(h, s, pd.down);
+    lv.adjS = upload_items(h, s, pd.adjS);
+    lv.adjM = upload_items(h, s, pd.adjM);
+    lv.wcopy_tab = upload(h->al, s, pd.wcopy, h->owned);
+    lv.n_wcopy = (int)pd.wcopy.size() / 3;
+    lv.reduce_tab = upload(h->al, s, pd.reduce, h->owned);
+    lv.n_reduce = (int)pd.reduce.size() / 3;
+    lv.ds = upload(h->al, s, pd.ds, h->owned);
+  }
+  h->leafup = upload_items(h, s, hp.lup);
+  h->leafdown = upload_items(h, s, hp.ldown);
+  h->lce = upload_items(h, s, hp.llce);
+  h->adj_leafF = upload_items(h, s, hp.aF);
+  h->adj_leafS = upload_items(h, s, hp.aS);
+  h->adj_lce = upload_items(h, s, hp.aL);
+  h->adj_leafH = upload_items(h, s, hp.aH);
+  h->leaf_reduce_tab = upload(h->al, s, hp.lred, h->owned);
+  h->n_leaf_reduce = (int)hp.lred.size() / 3;
+  h->fbar_tab = upload(h->al, s, hp.ftab, h->owned);
+  h->d_pairs = upload(h->al, s, hp.pairs, h->owned);
+}
+
+// Every device access the kernels make is described by the plan; check each descriptor
+// against the size of the buffer it touches before anything is launched.
+struct PlanCheck {
+  std::string err;
+  void fail(const std::string& m) {
+    if (err.empty()) err = m;
+  }
+};
+
+void check_rows(PlanCheck& pc, const std::vector<int>& idx, int row, int off, int n, long long rows,
+                const char* what) {
+  if (n <= 0) return;
+  if (off < 0) {
+    if (row < 0 || (long long)row + n > rows) pc.fail(std::string(what) + ": contiguous rows out of range");
+    return;
+  }
+  if ((size_t)off + n > idx.size()) {
+    pc.fail(std::string(what) + ": index list out of range");
+    return;
+  }
+  for (int k = 0; k < n; ++k) {
+    const long long r = (long long)row + idx[off + k];
+    if (idx[off + k] < 0 || r >= rows) {
+      pc.fail(std::string(what) + ": indexed row out of range");
+      return;
+    }
+  }
+}
+
+void check_items(PlanCheck& pc, const std::vector<int>& idx, const std::vector<GemmItem>& items, bool trans,
+                 long long ops, long long b0rows, long long b1rows, long long crows, long long addrows,
+                 const char* what) {
+  for (const GemmItem& it : items) {
+    const long long last = trans ? it.a_off + (long long)(it.K - 1) * it.lda + (it.M - 1)
+                                 : it.a_off + (long long)(it.M - 1) * it.lda + (it.K - 1);
+    if (it.a_off < 0 || last >= ops || it.M < 1 || it.M > ROWBLK || it.K < 1 || it.kseg < 0 || it.kseg > it.K)
+      pc.fail(std::string(what) + ": operator block out of range");
+    check_rows(pc, idx, it.b0_row, it.b0_idx, it.kseg, b0rows, what);
+    check_rows(pc, idx, it.b1_row, it.b1_idx, it.K - it.kseg, b1rows, what);
+    check_rows(pc, idx, it.c_row, it.c_idx, it.M, crows, what);
+    if (it.add_row >= 0 && (long long)it.add_row + it.M > addrows) pc.fail(std::string(what) + ": addend out of range");
+  }
+}
+
+void check_tab(PlanCheck& pc, const std::vector<int>& tab, long long drows, long long srows, const char* what) {
+  if (tab.size() % 3) pc.fail(std::string(what) + ": bad table");
+  for (size_t k = 0; k + 2 < tab.size(); k += 3) {
+    if (tab[k] < 0 || tab[k] >= drows) pc.fail(std::string(what) + ": destination out of range");
+    if (tab[k + 1] >= srows || tab[k + 2] >= srows || tab[k + 1] < -1 || tab[k + 2] < -1)
+      pc.fail(std::string(what) + ": source out of range");
+  }
+}
+
+std::string validate_plan(const hps_handle* h, const HostPlan& hp) {
+  PlanCheck pc;
+  const std::vector<int>& idx = hp.idx;
+  const long long ops = h->ops_elems, V = h->v_rows, D = h->d_rows, UB = h->ub_rows;
+  const long long G = h->ns.n_gauss, LP = (long long)h->n_leaf * h->pp, LB = (long long)h->n_leaf * h->nq;
+  check_items(pc, idx, hp.lup, false, ops, LP, 0, V, 0, "leaf up");
+  check_items(pc, idx, hp.ldown, false, ops, LP, G, LP, 0, "leaf down");
+  check_items(pc, idx, hp.llce, false, ops, G, 0, LP, 0, "leaf exterior");
+  check_items(pc, idx, hp.aF, true, ops, LP, 0, LP, 0, "adjoint F");
+  check_items(pc, idx, hp.aS, true, ops, LP, 0, LB, 0, "adjoint S");
+  check_items(pc, idx, hp.aL, true, ops, LP, 0, LB, 0, "adjoint L");
+  check_items(pc, idx, hp.aH, true, ops, V, 0, LP, 0, "adjoint H");
+  check_tab(pc, hp.lred, G, LB, "leaf reduce");
+  check_tab(pc, hp.ftab, h->n_bdry, G, "boundary gather");
+  for (size_t k = 0; k + 4 < hp.pairs.size() + 1 && k < hp.pairs.size(); k += 5) {
+    if (hp.pairs[k] < 0 || hp.pairs[k] >= h->tree.n_edges || hp.pairs[k + 1] < 0 || hp.pairs[k + 1] >= h->n_leaf ||
+        hp.pairs[k + 3] < 0 || hp.pairs[k + 3] >= h->n_leaf || hp.pairs[k + 2] < 0 || hp.pairs[k + 2] > 3 ||
+        hp.pairs[k + 4] < 0 || hp.pairs[k + 4] > 3)
+      pc.fail("edge pairs out of range");
+  }
+  for (size_t L = 0; L < hp.lv.size(); ++L) {
+    const LevelHost& pd = hp.lv[L];
+    const Level& lv = h->levels[L];
+    check_items(pc, idx, pd.up, false, ops, D, 0, V, 0, "merge up");
+    check_items(pc, idx, pd.down, false, ops, G, 0, G, V, "merge down");
+    check_items(pc, idx, pd.adjS, true, ops, G, 0, UB, 0, "adjoint S merge");
+    check_items(pc, idx, pd.adjM, true, ops, V, 0, D, 0, "adjoint X merge");
+    check_tab(pc, pd.wcopy, V, G, "adjoint w copy");
+    check_tab(pc, pd.reduce, G, UB, "adjoint reduce");
+    for (size_t i = 0; i < pd.ug.size(); ++i) {
+      const UpGather& u = pd.ug[i];
+      const int b = lv.boxes[i];
+      const Box& bx = h->tree.boxes[b];
+      const long long ka = h->k12[bx.child[0]], kb = h->k12[bx.child[1]];
+      if ((size_t)u.idx_off + 3 * u.k3 + u.n1 + u.n2 > idx.size()) { pc.fail("up gather: list out of range"); continue; }
+      for (int k = 0; k < u.k3; ++k) {
+        const int a3 = idx[u.idx_off + k], b3 = idx[u.idx_off + u.k3 + k], j3 = idx[u.idx_off + 2 * u.k3 + k];
+        if (a3 < 0 || a3 >= ka || b3 < 0 || b3 >= kb || j3 < 0 || j3 >= G) pc.fail("up gather: J3 entry out of range");
+      }
+      for (int k = 0; k < u.n1; ++k) {
+        const int a1 = idx[u.idx_off + 3 * u.k3 + k];
+        if (a1 < 0 || a1 >= ka) pc.fail("up gather: J1 entry out of range");
+      }
+      for (int k = 0; k < u.n2; ++k) {
+        const int b2 = idx[u.idx_off + 3 * u.k3 + u.n1 + k];
+        if (b2 < 0 || b2 >= kb) pc.fail("up gather: J2 entry out of range");
+      }
+      if (u.va_row + ka > V || u.vb_row + kb > V || (long long)u.vt_row + u.k3 + u.n1 + u.n2 > V ||
+          (long long)u.d_row + u.k3 > D)
+        pc.fail("up gather: rows out of range");
+    }
+    for (size_t i = 0; i < pd.md.size(); ++i) {
+      const MergeDesc& md = pd.md[i];
+      const GJDesc& gd = pd.gj[i];
+      if (md.m_off + (long long)md.R * md.R > lv.work_elems || gd.off != md.m_off || gd.R != md.R ||
+          gd.K != md.k3 || gd.perm_off + gd.K > lv.perm_elems)
+        pc.fail("merge workspace out of range");
+      if (md.ta_off + (long long)md.lda_a * md.lda_a > hp.tsz || md.tb_off + (long long)md.lda_b * md.lda_b > hp.tsz)
+        pc.fail("merge T store out of range");
+      if ((size_t)md.pos_off + 2 * md.R > idx.size()) pc.fail("merge positions out of range");
+      else
+        for (int r = 0; r < md.R; ++r) {
+          if (idx[md.pos_off + r] >= md.lda_a || idx[md.pos_off + md.R + r] >= md.lda_b) pc.fail("merge position too big");
+        }
+      const int k3 = md.k3, k12 = md.R - md.k3;
+      if (pd.tl[i] + (long long)md.R * k3 > ops || pd.bl[i] != pd.tl[i] + (long long)k3 * k3 ||
+          pd.tr[i] + (long long)k3 * k12 > ops || pd.br[i] + (long long)k12 * k12 > hp.tsz)
+        pc.fail("merge extraction out of range");
+    }
+  }
+  return pc.err;
+}
+
+long long tstore_elems(const hps_handle* h) {
+  long long tsz = 0;
+  for (size_t b = 0; b < h->tree.boxes.size(); ++b) tsz += (long long)h->k12[b] * h->k12[b];
+  return tsz;
+}
+
+int choose_nb(int K, size_t elem) {
+  int nb = (int)((200 * 1024) / ((size_t)std::max(K, 1) * (elem + 4)));
+  return std::max(1, std::min(16, nb));
+}
+
+// rk: (R, K) of every matrix of the batch, for the flop counts of the timing records.
+template <typename T>
+void run_gj(const GJDesc* gj, int nmat, int maxR, int maxK, T* work, int* perm, T* pinv, T* prow,
+            int* status, const std::vector<std::pair<int, int>>& rk, cudaStream_t s) {
+  const int nb = choose_nb(maxK, sizeof(T));
+  const std::string sf = tsuf<T>();
+  TIMED(("gj_init_" + sf).c_str(), 0, 0, launch_gj_init<T>(gj, nmat, perm, s));
+  CKL();
+  const long long prow_stride = (long long)16 * maxR;
+  for (int c0 = 0; c0 < maxK; c0 += nb) {
+    double fp = 0, fq = 0, fu = 0, bu = 0;
+    for (const auto& m : rk) {
+      if (m.second <= c0) continue;
+      const double R = m.first, b = std::min(nb, m.second - c0);
+      fp += 2.0 * (m.second - c0) * b * b;
+      fq += 2.0 * R * b * b;
+      fu += 2.0 * b * R * (R - b);
+      bu += 2.0 * R * (R - b) * sizeof(T);
+    }
+    TIMED(("gj_panel_" + sf).c_str(), fp, 0,
+          launch_gj_panel<T>(gj, nmat, maxK, work, perm, pinv, c0, nb, status, s));
+    TIMED(("gj_prep_" + sf).c_str(), fq, 0,
+          launch_gj_prep<T>(gj, nmat, maxR, work, perm, pinv, prow, prow_stride, c0, nb, s));
+    TIMED(("gj_update_" + sf).c_str(), fu, bu,
+          launch_gj_update<T>(gj, nmat, maxR, work, perm, prow, prow_stride, c0, nb, s));
+  }
+  CKL();
+}
+
+void build_stage(hps_handle* h, const double* coeffs, cudaStream_t s) {
+  const int m = h->m, nq = h->nq, R = m + nq;
+  std::vector<void*> tmp;
+  auto get = [&](size_t bytes) {
+    void* p = h->al.get(bytes, s);
+    tmp.push_back(p);
+    return p;
+  };
+  try {
+    h->ops64 = (double*)h->al.get(h->ops_elems * sizeof(double), s);
+    h->owned.push_back({h->ops64, (size_t)h->ops_elems * sizeof(double)});
+    CK(cudaMemcpyAsync(h->ops64 + h->lce_base, h->rt.Lce.data(), h->rt.Lce.size() * sizeof(double),
+                       cudaMemcpyHostToDevice, s));
+    double* tstore = (double*)get(tstore_elems(h) * sizeof(double));
+    const std::vector<long long>& toff = h->toff;
+    // ---- leaves (FP64 always), in chunks
+    const long long per_leaf = (long long)R * R;
+    const long long budget = 3ll << 30;  // bytes of elimination workspace per chunk
+    int chunk = (int)std::max<long long>(1, std::min<long long>(h->n_leaf, budget / (per_leaf * 8)));
+    chunk = std::min(chunk, 8192);
+    double* work = (double*)get((size_t)per_leaf * chunk * sizeof(double));
+    int* perm = (int*)get((size_t)chunk * m * sizeof(int));
+    double* pinv = (double*)get((size_t)chunk * 256 * sizeof(double));
+    double* prow = (double*)get((size_t)chunk * 16 * R * sizeof(double));
+    std::vector<GJDesc> gd(chunk);
+    for (int i = 0; i < chunk; ++i) {
+      gd[i].off = (long long)i * per_leaf;
+      gd[i].R = R;
+      gd[i].K = m;
+      gd[i].perm_off = i * m;
+      gd[i].box = 0;
+    }
+    LeafTablesDev tb{h->dD, h->dD2, h->dLs, h->dLloc, h->dDceL, h->didx + h->off_ci};
+    for (int l0 = 0; l0 < h->n_leaf; l0 += chunk) {
+      const int n = std::min(chunk, h->n_leaf - l0);
+      for (int i = 0; i < n; ++i) gd[i].box = h->tree.leaves[l0 + i];
+      GJDesc* dgd = (GJDesc*)get(n * sizeof(GJDesc));
+      CK(cudaMemcpyAsync(dgd, gd.data(), n * sizeof(GJDesc), cudaMemcpyHostToDevice, s));
+      TIMED("leaf_assemble_f64", 0, (double)n * per_leaf * 8,
+            launch_leaf_assemble<double>(coeffs, h->n_leaf, l0, n, h->dhxy, h->p, h->q, tb, work, per_leaf, s));
+      CKL();
+      run_gj<double>(dgd, n, R, m, work, perm, pinv, prow, h->d_status,
+                     std::vector<std::pair<int, int>>(n, {R, m}), s);
+      ExtractDst dst{};
+      const long long gl0 = h->gl_base + (long long)l0 * m * R;
+      dst.TL = h->ops64 + gl0; dst.TL_off_stride = (long long)m * R; dst.TL_ld = R;
+      dst.TR = h->ops64 + gl0 + m; dst.TR_off_stride = (long long)m * R; dst.TR_ld = R;
+      dst.BL = h->ops64 + h->h_base + (long long)l0 * nq * m; dst.BL_off_stride = (long long)nq * m; dst.BL_ld = m;
+      dst.BR = tstore + toff[h->tree.leaves[l0]]; dst.BR_off_stride = (long long)nq * nq; dst.BR_ld = nq;
+      dst.sTL = 1.0; dst.sTR = -1.0; dst.sBL = -1.0;
+      TIMED("gj_extract_f64", 0, (double)n * per_leaf * 8, launch_gj_extract<double, double>(dgd, n, R, work, perm, dst, s));
+      CKL();
+    }
+    // ---- merges, level by level
+    const int H = h->tree.height;
+    for (int L = 0; L < H; ++L) {
+      Level& lv = h->levels[L];
+      const int nmat = (int)lv.boxes.size();
+      std::vector<std::pair<int, int>> rk;
+      for (int b : lv.boxes) rk.push_back({h->k3[b] + h->k12[b], h->k3[b]});
+      const double wbytes = (double)lv.work_elems * (lv.fp64 ? 8 : 4);
+      ExtractDst dst{};
+      dst.TL = h->ops64; dst.TL_ld = 0; dst.TL_off = lv.off_tl;
+      dst.TR = h->ops64; dst.TR_off = lv.off_tr;
+      dst.BL = h->ops64; dst.BL_off = lv.off_bl;
+      dst.BR = tstore; dst.BR_off = lv.off_br;
+      dst.sTL = 1.0; dst.sTR = 1.0; dst.sBL = 1.0;
+      dst.ld_from_desc = 1;  // X, C X: ld k3; S, T_tau: ld k12
+      if (lv.fp64) {
+        double* w = (double*)get((size_t)lv.work_elems * sizeof(double));
+        int* pm = (int*)get((size_t)std::max(1, lv.perm_elems) * sizeof(int));
+        double* pi = (double*)get((size_t)nmat * 256 * sizeof(double));
+        double* pr = (double*)get((size_t)nmat * 16 * lv.maxR * sizeof(double));
+        TIMED("merge_assemble_f64", 0, wbytes, launch_merge_assemble<double, double>(lv.md, nmat, lv.maxR, tstore, h->didx, w, s));
+        CKL();
+        run_gj<double>(lv.gj, nmat, lv.maxR, lv.maxK, w, pm, pi, pr, h->d_status, rk, s);
+        TIMED("gj_extract_f64", 0, wbytes, launch_gj_extract<double, double>(lv.gj, nmat, lv.maxR, w, pm, dst, s));
+        CKL();
+      } else {
+        float* w = (float*)get((size_t)lv.work_elems * sizeof(float));
+        int* pm = (int*)get((size_t)std::max(1, lv.perm_elems) * sizeof(int));
+        float* pi = (float*)get((size_t)nmat * 256 * sizeof(float));
+        float* pr = (float*)get((size_t)nmat * 16 * lv.maxR * sizeof(float));
+        TIMED("merge_assemble_f32", 0, wbytes, launch_merge_assemble<float, double>(lv.md, nmat, lv.maxR, tstore, h->didx, w, s));
+        CKL();
+        run_gj<float>(lv.gj, nmat, lv.maxR, lv.maxK, w, pm, pi, pr, h->d_status, rk, s);
+        TIMED("gj_extract_f32", 0, wbytes, launch_gj_extract<float, double>(lv.gj, nmat, lv.maxR, w, pm, dst, s));
+        CKL();
+      }
+    }
+    if (h->opts.precision == HPS_MIXED) {
+      h->ops32 = (float*)h->al.get(h->ops_elems * sizeof(float), s);
+      h->owned.push_back({h->ops32, (size_t)h->ops_elems * sizeof(float)});
+      TIMED("convert_ops", 0, (double)h->ops_elems * 12, launch_convert<double, float>(h->ops64, h->ops32, h->ops_elems, 1.0, s));
+      CKL();
+    }
+  } catch (...) {
+    for (void* p : tmp) h->al.put(p, s);
+    throw;
+  }
+  for (void* p : tmp) h->al.put(p, s);
+}
+
+void ensure_ws(hps_handle* h, int nrhs, cudaStream_t s) {
+  Workspace& w = h->ws;
+  if (w.nrhs >= nrhs) return;
+  for (void* p : w.ptrs) h->al.put(p, s);
+  w = Workspace();
+  w.nrhs = nrhs;
+  auto get = [&](size_t bytes) {
+    void* p = h->al.get(bytes, s);
+    w.ptrs.push_back(p);
+    return p;
+  };
+  const long long R = nrhs;
+  const long long nuc = (long long)h->n_leaf * h->pp * R;
+  const long long ng = (long long)h->ns.n_gauss * R;
+  const bool mixed = h->opts.precision == HPS_MIXED;
+  w.V64 = (double*)get((size_t)h->v_rows * R * sizeof(double));
+  w.d64 = (double*)get((size_t)std::max(1, h->d_rows) * R * sizeof(double));
+  w.ug64 = (double*)get((size_t)ng * sizeof(double));
+  if (mixed) {
+    w.V32 = (float*)get((size_t)h->v_rows * R * sizeof(float));
+    w.d32 = (float*)get((size_t)std::max(1, h->d_rows) * R * sizeof(float));
+    w.ug32 = (float*)get((size_t)ng * sizeof(float));
+    w.g32 = (float*)get((size_t)nuc * sizeof(float));
+    w.uc32 = (float*)get((size_t)nuc * sizeof(float));
+    w.rho32 = (float*)get((size_t)ng * sizeof(float));
+    w.r64 = (double*)get((size_t)nuc * sizeof(double));
+    w.vflux = (double*)get((size_t)h->n_leaf * h->nq * R * sizeof(double));
+    w.rho64 = (double*)get((size_t)ng * sizeof(double));
+  } else {
+    w.LB = (double*)get((size_t)h->n_leaf * h->nq * R * sizeof(double));
+    w.UB = (double*)get((size_t)std::max(1, h->ub_rows) * R * sizeof(double));
+    w.ubar = (double*)get((size_t)ng * sizeof(double));
+  }
+  w.scal = (double*)get(4 * sizeof(double));
+}
+
+// One pass of Algorithm 2 with operator type TA and vector type TV.
+//   f: [n_bdry][nrhs] FP64 (scattered as TV), g: [n_leaf][pp][nrhs] TV, rho: optional
+//   FP64 [n_gauss][nrhs], outputs uc [n_leaf][pp][nrhs] TV and ug [n_gauss][nrhs] TV.
+template <typename TA, typename TV>
+void solve_pass(hps_handle* h, const TA* ops, const double* f, const TV* g, const double* rho, TV* uc, TV* ug,
+                TV* V, TV* dbuf, int nrhs, cudaStream_t s) {
+  const int H = h->tree.height;
+  const int* idx = h->didx;
+  const std::string sf = tsuf<TA>();
+  auto gemm = [&](const char* step, const ItemSet& is, const TV* B0, const TV* B1, TV* C, const TV* Add,
+                  double beta) {
+    TIMED(("gemm_" + std::string(step) + "_" + sf).c_str(), 2.0 * is.elems * nrhs, is.elems * sizeof(TA),
+          launch_gemm_items<TA, TV>(is.dev, is.n, ROWBLK, 0, ops, B0, B1, C, Add, idx, nrhs, beta, s));
+  };
+  // upward pass: leaves, then merges bottom-up
+  gemm("leaf_up", h->leafup, g, nullptr, V, nullptr, 0.0);
+  for (int L = 0; L < H; ++L) {
+    Level& lv = h->levels[L];
+    TIMED("up_gather", 0, 0, launch_up_gather<TV>(lv.ug, (int)lv.boxes.size(), lv.ug_maxrows, V, V, dbuf, rho, idx, nrhs, s));
+    gemm("merge_up", lv.up, dbuf, nullptr, V, nullptr, 1.0);
+  }
+  // root boundary data, then the downward pass
+  if (f) TIMED("scatter_rows", 0, 0, launch_scatter_rows<TV>(f, idx + h->off_bnd, h->n_bdry, ug, nrhs, s));
+  for (int L = H - 1; L >= 0; --L) {
+    Level& lv = h->levels[L];
+    gemm("merge_down", lv.down, ug, nullptr, ug, V, 0.0);
+  }
+  gemm("leaf_down", h->leafdown, g, ug, uc, nullptr, 0.0);
+  gemm("leaf_ext", h->lce, ug, nullptr, uc, nullptr, 0.0);
+  CKL();
+}
+
+double read_scalar(const double* d, cudaStream_t s) {
+  double v = 0.0;
+  CK(cudaMemcpyAsync(&v, d, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return v;
+}
+
+int solve_impl(hps_handle* h, const double* f, const double* g, const double* rho, int nrhs, double* u,
+               double* ug_out, int* iters, cudaStream_t s) {
+  ensure_ws(h, nrhs, s);
+  Workspace& w = h->ws;
+  const long long nuc = (long long)h->n_leaf * h->pp * nrhs;
+  const long long ng = (long long)h->ns.n_gauss * nrhs;
+  if (iters) *iters = 0;
+  if (h->opts.precision == HPS_FP64) {
+    CK(cudaMemsetAsync(w.ug64, 0, ng * sizeof(double), s));
+    solve_pass<double, double>(h, h->ops64, f, g, rho, u, w.ug64, w.V64, w.d64, nrhs, s);
+    if (ug_out) CK(cudaMemcpyAsync(ug_out, w.ug64, ng * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    return HPS_OK;
+  }
+  return HPS_ERR_STATE;
+}
+
+}  // namespace
+
+extern "C" {
+
+void hps_opts_default(hps_opts* o) {
+  if (!o) return;
+  o->precision = HPS_FP64;
+  o->q = 0;
+  o->store_leaf_ops = 1;
+  o->ir_tol = 0.0;
+  o->ir_max_iter = 0;
+  o->fp64_top_levels = -1;
+}
+
+const char* hps_last_error(void) { return g_err.c_str(); }
+
+int hps_tree_uniform(double x0, double y0, double x1, double y1, int nx, int ny, hps_tree** out) {
+  if (!out) return fail(HPS_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (nx < 1 || ny < 1 || nx > 65536 || ny > 65536 || (long long)nx * ny > (1ll << 24))
+    return fail(HPS_ERR_INVALID_ARG, "nx, ny must be in [1, 65536] with nx*ny <= 2^24");
+  if (!(x1 > x0) || !(y1 > y0)) return fail(HPS_ERR_INVALID_ARG, "empty domain");
+  hps_tree* t = new (std::nothrow) hps_tree();
+  if (!t) return fail(HPS_ERR_OOM, "host allocation failed");
+  make_uniform_tree(x0, y0, x1, y1, nx, ny, t->t);
+  *out = t;
+  return HPS_OK;
+}
+
+int hps_tree_destroy(hps_tree* t) {
+  delete t;
+  return HPS_OK;
+}
+
+int hps_tree_info(const hps_tree* tree, int q, int* n_leaves, int* n_boxes, int* n_levels, int* n_gauss,
+                  int* n_boundary) {
+  if (!tree) return fail(HPS_ERR_INVALID_ARG, "tree is NULL");
+  if (q < 1) return fail(HPS_ERR_INVALID_ARG, "q must be >= 1");
+  const Tree& t = tree->t;
+  if (n_leaves) *n_leaves = (int)t.leaves.size();
+  if (n_boxes) *n_boxes = (int)t.boxes.size();
+  if (n_levels) *n_levels = t.height;
+  if (n_gauss) *n_gauss = t.n_edges * q;
+  if (n_boundary) {
+    int nb = 0;
+    for (int e = 0; e < t.n_edges; ++e)
+      if (t.edge_owners[2 * e + 1] < 0) ++nb;
+    *n_boundary = nb * q;
+  }
+  return HPS_OK;
+}
+
+int hps_nodes(const hps_tree* tree, int p, int q, int which, double* xy, int64_t* count) {
+  if (!tree || !count) return fail(HPS_ERR_INVALID_ARG, "tree or count is NULL");
+  if (p < 3 || p > 64 || q < 1 || q > 64) return fail(HPS_ERR_INVALID_ARG, "p must be in [3,64], q in [1,64]");
+  const Tree& t = tree->t;
+  RefTables rt;
+  build_ref_tables(p, q, rt);
+  if (which == HPS_NODES_CHEB_LEAF) {
+    *count = (int64_t)t.leaves.size() * p * p;
+    if (!xy) return HPS_OK;
+    for (size_t lf = 0; lf < t.leaves.size(); ++lf) {
+      const Box& b = t.boxes[t.leaves[lf]];
+      for (int iy = 0; iy < p; ++iy)
+        for (int ix = 0; ix < p; ++ix) {
+          const size_t k = (lf * p + iy) * p + ix;
+          xy[2 * k] = b.x0 + 0.5 * (b.x1 - b.x0) * (rt.xc[ix] + 1.0);
+          xy[2 * k + 1] = b.y0 + 0.5 * (b.y1 - b.y0) * (rt.xc[iy] + 1.0);
+        }
+    }
+    return HPS_OK;
+  }
+  if (which != HPS_NODES_GAUSS_BOUNDARY && which != HPS_NODES_GAUSS_ALL)
+    return fail(HPS_ERR_INVALID_ARG, "unknown node set");
+  std::vector<double> all((size_t)2 * t.n_edges * q);
+  for (size_t lf = 0; lf < t.leaves.size(); ++lf) {
+    const Box& b = t.boxes[t.leaves[lf]];
+    for (int s = 0; s < 4; ++s) {
+      const int e = t.leaf_edges[4 * lf + s];
+      for (int k = 0; k < q; ++k) {
+        const double gx = b.x0 + 0.5 * (b.x1 - b.x0) * (rt.xg[k] + 1.0);
+        const double gy = b.y0 + 0.5 * (b.y1 - b.y0) * (rt.xg[k] + 1.0);
+        double x, y;
+        switch (s) {
+          case 0: x = gx; y = b.y0; break;
+          case 1: x = b.x1; y = gy; break;
+          case 2: x = gx; y = b.y1; break;
+          default: x = b.x0; y = gy; break;
+        }
+        all[2 * ((size_t)e * q + k)] = x;
+        all[2 * ((size_t)e * q + k) + 1] = y;
+      }
+    }
+  }
+  if (which == HPS_NODES_GAUSS_ALL) {
+    *count = (int64_t)t.n_edges * q;
+    if (xy) std::memcpy(xy, all.data(), all.size() * sizeof(double));
+    return HPS_OK;
+  }
+  int64_t n = 0;
+  for (int e = 0; e < t.n_edges; ++e)
+    if (t.edge_owners[2 * e + 1] < 0) {
+      for (int k = 0; k < q; ++k) {
+        if (xy) {
+          xy[2 * n] = all[2 * ((size_t)e * q + k)];
+          xy[2 * n + 1] = all[2 * ((size_t)e * q + k) + 1];
+        }
+        ++n;
+      }
+    }
+  *count = n;
+  return HPS_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Options, reference tables, node sets and the size checks shared by hps_build and
+// hps_plan_check.  Returns an empty string or the reason the tree/options are rejected.
+std::string setup_host(hps_handle* h, const Tree& tree, int p, const hps_opts& o) {
+  h->tree = tree;
+  h->opts = o;
+  h->p = p;
+  h->q = o.q;
+  h->pp = p * p;
+  h->m = (p - 2) * (p - 2);
+  h->nq = 4 * o.q;
+  h->ne = 4 * (p - 1);
+  h->n_leaf = (int)h->tree.leaves.size();
+  build_ref_tables(p, h->q, h->rt);
+  build_node_sets(h->tree, h->q, h->ns);
+  h->n_bdry = (int)h->ns.boundary.size();
+  for (size_t b = 0; b < h->tree.boxes.size(); ++b)
+    if (h->tree.boxes[b].leaf < 0 && h->ns.J3[b].empty()) return "a merge has no shared edge";
+  return std::string();
+}
+
+int check_opts(int p, const hps_opts* opts, hps_opts& o) {
+  if (p < 4 || p > 32) return fail(HPS_ERR_INVALID_ARG, "p must be in [4, 32]");
+  hps_opts_default(&o);
+  if (opts) o = *opts;
+  if (o.q == 0) o.q = p - 1;
+  if (o.q < 2 || o.q > 32) return fail(HPS_ERR_INVALID_ARG, "q must be in [2, 32]");
+  if (o.precision != HPS_FP64 && o.precision != HPS_MIXED) return fail(HPS_ERR_INVALID_ARG, "unknown precision");
+  if (o.store_leaf_ops != 1) return fail(HPS_ERR_INVALID_ARG, "store_leaf_ops must be 1");
+  if (o.ir_tol <= 0.0) o.ir_tol = 1e-10;
+  if (o.ir_max_iter <= 0) o.ir_max_iter = 10;
+  return HPS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hps_plan_check(const hps_tree* tree, int p, const hps_opts* opts) {
+  if (!tree) return fail(HPS_ERR_INVALID_ARG, "tree is NULL");
+  hps_opts o;
+  const int rc = check_opts(p, opts, o);
+  if (rc != HPS_OK) return rc;
+  hps_handle* h = new (std::nothrow) hps_handle();
+  if (!h) return fail(HPS_ERR_OOM, "host allocation failed");
+  std::string err;
+  try {
+    err = setup_host(h, tree->t, p, o);
+    if (err.empty()) {
+      HostPlan hp;
+      make_plan(h, hp);
+      err = validate_plan(h, hp);
+      if (!err.empty()) err = "internal plan check failed: " + err;
+    }
+  } catch (const std::exception& e) {
+    err = e.what();
+  }
+  delete h;
+  if (!err.empty()) return fail(HPS_ERR_INVALID_ARG, err);
+  return HPS_OK;
+}
+
+int hps_build(const hps_tree* tree, const double* coeffs, int p, const hps_opts* opts, const hps_allocator* alloc,
+              void* stream, hps_handle** out) {
+  if (!out) return fail(HPS_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!tree || !coeffs) return fail(HPS_ERR_INVALID_ARG, "tree or coeffs is NULL");
+  hps_opts o;
+  const int rc = check_opts(p, opts, o);
+  if (rc != HPS_OK) return rc;
+  if (alloc && (!alloc->alloc || !alloc->free)) return fail(HPS_ERR_INVALID_ARG, "allocator callbacks missing");
+  cudaStream_t s = (cudaStream_t)stream;
+  hps_handle* h = new (std::nothrow) hps_handle();
+  if (!h) return fail(HPS_ERR_OOM, "host allocation failed");
+  if (alloc) {
+    h->al.a = *alloc;
+    h->al.custom = true;
+  }
+  try {
+    const std::string err = setup_host(h, tree->t, p, o);
+    if (!err.empty()) {
+      delete h;
+      return fail(HPS_ERR_INVALID_ARG, err);
+    }
+    // device tables
+    h->dD = upload(h->al, s, h->rt.D, h->owned);
+    h->dD2 = upload(h->al, s, h->rt.D2, h->owned);
+    h->dLs = upload(h->al, s, h->rt.Ls, h->owned);
+    h->dLloc = upload(h->al, s, h->rt.Lloc, h->owned);
+    h->dDceL = upload(h->al, s, h->rt.DceL, h->owned);
+    std::vector<double> hxy(2 * (size_t)h->n_leaf);
+    for (int lf = 0; lf < h->n_leaf; ++lf) {
+      const Box& b = h->tree.boxes[h->tree.leaves[lf]];
+      hxy[2 * lf] = b.x1 - b.x0;
+      hxy[2 * lf + 1] = b.y1 - b.y0;
+    }
+    h->dhxy = upload(h->al, s, hxy, h->owned);
+    h->d_leaf_edges = upload(h->al, s, h->tree.leaf_edges, h->owned);
+    std::vector<int> st(1, 0);
+    h->d_status = upload(h->al, s, st, h->owned);
+    {
+      HostPlan hp;
+      make_plan(h, hp);
+      const std::string err = validate_plan(h, hp);
+      if (!err.empty()) {
+        delete h;
+        return fail(HPS_ERR_INVALID_ARG, "internal plan check failed: " + err);
+      }
+      upload_plan(h, hp, s);
+    }
+    if (o.precision == HPS_MIXED) {
+      const size_t cb = (size_t)6 * h->n_leaf * h->pp * sizeof(double);
+      h->coeffs_copy = (double*)h->al.get(cb, s);
+      h->owned.push_back({h->coeffs_copy, cb});
+      CK(cudaMemcpyAsync(h->coeffs_copy, coeffs, cb, cudaMemcpyDeviceToDevice, s));
+    }
+    build_stage(h, coeffs, s);
+    int status = 0;
+    CK(cudaMemcpyAsync(&status, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (status != 0) {
+      const int box = status - 1;
+      delete h;
+      return fail(HPS_ERR_SINGULAR, "pivot breakdown in the elimination of box " + std::to_string(box));
+    }
+  } catch (const CudaError& e) {
+    delete h;
+    return fail(e.code, e.msg);
+  } catch (const std::bad_alloc&) {
+    delete h;
+    return fail(HPS_ERR_OOM, "host allocation failed");
+  } catch (const std::exception& e) {
+    delete h;
+    return fail(HPS_ERR_INVALID_ARG, e.what());
+  }
+  *out = h;
+  return HPS_OK;
+}
+
+int hps_solve_ext(hps_handle* h, const double* f, const double* g, const double* rho, int nrhs, double* u,
+                  double* ug_out, int* iters, void* stream) {
+  if (!h) return fail(HPS_ERR_INVALID_ARG, "handle is NULL");
+  if (!f || !g || !u) return fail(HPS_ERR_INVALID_ARG, "f, g and u must be device pointers");
+  if (nrhs < 1 || nrhs > 4096) return fail(HPS_ERR_INVALID_ARG, "nrhs must be in [1, 4096]");
+  cudaStream_t s = (cudaStream_t)stream;
+  try {
+    if (iters) *iters = 0;
+    if (h->opts.precision == HPS_FP64) return solve_impl(h, f, g, rho, nrhs, u, ug_out, iters, s);
+    ensure_ws(h, nrhs, s);
+    Workspace& w = h->ws;
+    const long long nuc = (long long)h->n_leaf * h->pp * nrhs;
+    const long long ng = (long long)h->ns.n_gauss * nrhs;
+    const double* coeffs = h->coeffs_copy;
+    // 1. low-precision solve of the original system
+    TIMED("convert", 0, nuc * 12.0, launch_convert<double, float>(g, w.g32, nuc, 1.0, s));
+    CK(cudaMemsetAsync(w.ug32, 0, ng * sizeof(float), s));
+    solve_pass<float, float>(h, h->ops32, f, w.g32, rho, w.uc32, w.ug32, w.V32, w.d32, nrhs, s);
+    TIMED("convert", 0, nuc * 12.0, launch_convert<float, double>(w.uc32, u, nuc, 1.0, s));
+    TIMED("convert", 0, ng * 12.0, launch_convert<float, double>(w.ug32, w.ug64, ng, 1.0, s));
+    TIMED("scatter_rows", 0, 0, launch_scatter_rows<double>(f, h->didx + h->off_bnd, h->n_bdry, w.ug64, nrhs, s));  // exact boundary data
+    CKL();
+    ResidualArgs ra;
+    ra.coeffs = coeffs;
+    ra.n_leaf = h->n_leaf;
+    ra.p = h->p;
+    ra.q = h->q;
+    ra.hxy = h->dhxy;
+    ra.D = h->dD;
+    ra.D2 = h->dD2;
+    ra.Lloc = h->dLloc;
+    ra.ci = h->didx + h->off_ci;
+    const double* Lce = h->ops64 + h->lce_base;
+    // derivative passes (5 p^3), exterior refresh (ne 4q) and fluxes (4q p) per leaf and rhs
+    const double res_flops = 2.0 * ((double)h->n_leaf * nrhs) *
+                             (5.0 * h->p * h->p * h->p + (double)h->ne * h->nq + (double)h->nq * h->p + 12.0 * h->m);
+    int it = 0;
+    bool conv = false;
+    for (; it < h->opts.ir_max_iter; ++it) {
+      // 2. FP64 residual: leaf equations and flux jumps (refreshes u_ce = L u_ge)
+      TIMED("leaf_residual_f64", res_flops, nuc * 32.0,
+            launch_leaf_residual_impl(ra, h->d_leaf_edges, Lce, h->didx + h->off_ce, w.ug64, g, u, w.r64, w.vflux,
+                                      nrhs, s));
+      CK(cudaMemsetAsync(w.rho64, 0, ng * sizeof(double), s));
+      TIMED("jump_residual", 0, 0, launch_jump_residual(h->d_pairs, h->npairs, h->q, w.vflux, w.rho64, nrhs, s));
+      if (rho) TIMED("axpy", 0, 0, launch_axpy_to_f64<double>(rho, w.rho64, ng, s));
+      CKL();
+      // 3. correction solve in FP32 with the jump residual as flux-continuity data
+      TIMED("convert", 0, nuc * 12.0, launch_convert<double, float>(w.r64, w.g32, nuc, 1.0, s));
+      CK(cudaMemsetAsync(w.ug32, 0, ng * sizeof(float), s));
+      solve_pass<float, float>(h, h->ops32, nullptr, w.g32, w.rho64, w.uc32, w.ug32, w.V32, w.d32, nrhs, s);
+      // 4. update and convergence test
+      TIMED("axpy", 0, nuc * 20.0, launch_axpy_to_f64<float>(w.uc32, u, nuc, s));
+      TIMED("axpy", 0, ng * 20.0, launch_axpy_to_f64<float>(w.ug32, w.ug64, ng, s));
+      CK(cudaMemsetAsync(w.scal, 0, 4 * sizeof(double), s));
+      TIMED("convert", 0, nuc * 12.0, launch_convert<float, double>(w.uc32, w.r64, nuc, 1.0, s));
+      TIMED("absmax", 0, nuc * 8.0, launch_absmax(w.r64, nuc, w.scal, s));
+      TIMED("absmax", 0, nuc * 8.0, launch_absmax(u, nuc, w.scal + 1, s));
+      CKL();
+      double sc[2];
+      CK(cudaMemcpyAsync(sc, w.scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (!(sc[0] == sc[0]) || !(sc[1] == sc[1])) break;
+      if (sc[0] <= h->opts.ir_tol * sc[1]) {
+        conv = true;
+        ++it;
+        break;
+      }
+    }
+    // final exterior refresh u_ce = L u_ge in FP64 (the residual kernel writes it)
+    TIMED("leaf_residual_f64", res_flops, nuc * 32.0,
+          launch_leaf_residual_impl(ra, h->d_leaf_edges, Lce, h->didx + h->off_ce, w.ug64, g, u, w.r64, w.vflux,
+                                    nrhs, s));
+    CKL();
+    if (ug_out) CK(cudaMemcpyAsync(ug_out, w.ug64, ng * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (iters) *iters = it;
+    if (!conv) return fail(HPS_ERR_NO_CONVERGENCE, "iterative refinement did not converge in " + std::to_string(it) + " steps");
+    return HPS_OK;
+  } catch (const CudaError& e) {
+    return fail(e.code, e.msg);
+  } catch (const std::bad_alloc&) {
+    return fail(HPS_ERR_OOM, "host allocation failed");
+  }
+}
+
+int hps_solve(hps_handle* h, const double* f, const double* g, int nrhs, double* u, void* stream) {
+  return hps_solve_ext(h, f, g, nullptr, nrhs, u, nullptr, nullptr, stream);
+}
+
+int hps_adjoint(hps_handle* h, const double* ubar_in, int nrhs, const double* u, double* fbar, double* gbar,
+                double* cbar, void* stream) {
+  if (!h) return fail(HPS_ERR_INVALID_ARG, "handle is NULL");
+  if (!ubar_in) return fail(HPS_ERR_INVALID_ARG, "dJdu is NULL");
+  if (nrhs < 1 || nrhs > 4096) return fail(HPS_ERR_INVALID_ARG, "nrhs must be in [1, 4096]");
+  if (h->opts.precision != HPS_FP64) return fail(HPS_ERR_STATE, "hps_adjoint needs an HPS_FP64 handle");
+  if (cbar && !u) return fail(HPS_ERR_INVALID_ARG, "coefficient gradients need the forward solution u");
+  cudaStream_t s = (cudaStream_t)stream;
+  try {
+    ensure_ws(h, nrhs, s);
+    Workspace& w = h->ws;
+    const long long nuc = (long long)h->n_leaf * h->pp * nrhs;
+    const long long ng = (long long)h->ns.n_gauss * nrhs;
+    const int* idx = h->didx;
+    const double* ops = h->ops64;
+    double* gb = gbar;
+    std::vector<void*> tmp;
+    if (!gb) {
+      gb = (double*)h->al.get(nuc * sizeof(double), s);
+      tmp.push_back(gb);
+    }
+    double* VB = w.V64;
+    double* ub = w.ubar;
+    CK(cudaMemsetAsync(gb, 0, nuc * sizeof(double), s));
+    CK(cudaMemsetAsync(VB, 0, (size_t)h->v_rows * nrhs * sizeof(double), s));
+    auto gemmT = [&](const char* step, const ItemSet& is, const double* B0, double* C, double beta) {
+      TIMED(("gemmT_" + std::string(step) + "_f64").c_str(), 2.0 * is.elems * nrhs, is.elems * 8.0,
+            launch_gemm_items<double, double>(is.dev, is.n, ROWBLK, 1, ops, B0, nullptr, C, nullptr, idx, nrhs, beta, s));
+    };
+    // 1. leaf-down transposed: gbar_ci = F^T ubar_ci ; LB = S_ci^T ubar_ci + Lce^T ubar_ce
+    gemmT("leaf_F", h->adj_leafF, ubar_in, gb, 0.0);
+    gemmT("leaf_S", h->adj_leafS, ubar_in, w.LB, 0.0);
+    gemmT("leaf_ext", h->adj_lce, ubar_in, w.LB, 1.0);
+    // ubar_gauss = sum over owning leaves
+    TIMED("gather_reduce", 0, 0, launch_gather_reduce<double>(h->leaf_reduce_tab, h->n_leaf_reduce, w.LB, ub, nrhs, 0, s));
+    CKL();
+    const int H = h->tree.height;
+    // 2. merge-down transposed, bottom-up
+    for (int L = 0; L < H; ++L) {
+      Level& lv = h->levels[L];
+      TIMED("gather_reduce", 0, 0, launch_gather_reduce<double>(lv.wcopy_tab, lv.n_wcopy, ub, VB, nrhs, 0, s));
+      gemmT("merge_S", lv.adjS, ub, w.UB, 0.0);
+      TIMED("gather_reduce", 0, 0, launch_gather_reduce<double>(lv.reduce_tab, lv.n_reduce, w.UB, ub, nrhs, 1, s));
+    }
+    // 3. boundary data
+    if (fbar) TIMED("gather_reduce", 0, 0, launch_gather_reduce<double>(h->fbar_tab, h->n_bdry, ub, fbar, nrhs, 0, s));
+    // 4. merge-up transposed, top-down
+    for (int L = H - 1; L >= 0; --L) {
+      Level& lv = h->levels[L];
+      gemmT("merge_X", lv.adjM, VB, w.d64, 0.0);
+      TIMED("down_scatter", 0, 0, launch_down_scatter<double>(lv.ds, (int)lv.boxes.size(), lv.ds_maxrows, VB, w.d64, nullptr, idx, nrhs, s));
+    }
+    // 5. leaf-up transposed: gbar_ci += H^T hbar
+    gemmT("leaf_H", h->adj_leafH, VB, gb, 1.0);
+    CKL();
+    // 6. coefficient gradients
+    if (cbar) {
+      ResidualArgs ra;
+      ra.coeffs = nullptr;
+      ra.n_leaf = h->n_leaf;
+      ra.p = h->p;
+      ra.q = h->q;
+      ra.hxy = h->dhxy;
+      ra.D = h->dD;
+      ra.D2 = h->dD2;
+      ra.Lloc = h->dLloc;
+      ra.ci = h->didx + h->off_ci;
+      TIMED("coeff_grad_f64", 2.0 * h->n_leaf * nrhs * (5.0 * h->p * h->p * h->p + 12.0 * h->m), nuc * 16.0,
+            launch_coeff_grad(ra, u, gb, cbar, nrhs, s));
+      CKL();
+    }
+    for (void* p : tmp) h->al.put(p, s);
+    (void)ng;
+    return HPS_OK;
+  } catch (const CudaError& e) {
+    return fail(e.code, e.msg);
+  } catch (const std::bad_alloc&) {
+    return fail(HPS_ERR_OOM, "host allocation failed");
+  }
+}
+
+int hps_handle_info(const hps_handle* h, int* n_leaves, int* p, int* q, int* n_gauss, int* n_boundary,
+                    int64_t* operator_bytes) {
+  if (!h) return fail(HPS_ERR_INVALID_ARG, "handle is NULL");
+  if (n_leaves) *n_leaves = h->n_leaf;
+  if (p) *p = h->p;
+  if (q) *q = h->q;
+  if (n_gauss) *n_gauss = h->ns.n_gauss;
+  if (n_boundary) *n_boundary = h->n_bdry;
+  if (operator_bytes)
+    *operator_bytes = (int64_t)h->ops_elems * (h->opts.precision == HPS_MIXED ? 4 : 8);
+  return HPS_OK;
+}
+
+int hps_sync_status(hps_handle* h, void* stream) {
+  if (!h) return fail(HPS_ERR_INVALID_ARG, "handle is NULL");
+  int status = 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemcpyAsync(&status, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return fail(HPS_ERR_CUDA, cudaGetErrorString(cudaGetLastError()));
+  if (status) return fail(HPS_ERR_SINGULAR, "pivot breakdown in box " + std::to_string(status - 1));
+  return HPS_OK;
+}
+
+int hps_destroy(hps_handle* h) {
+  if (!h) return HPS_OK;
+  delete h;
+  return HPS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,237 @@
+// Internal declarations of the GB300 HPS library: host tree, reference-element tables,
+// per-level schedules and the kernel launchers.  Nothing here crosses the C ABI.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/hps.h"
+
+namespace hps {
+
+// ---------------------------------------------------------------------------------------
+// Host tree (Sec. 2).  Boxes are numbered breadth-first from the root, so a parent has a
+// smaller id than its children; the first child is the W (or S) half ("alpha").
+struct Box {
+  double x0, y0, x1, y1;
+  int i0, i1, j0, j1;   // leaf-index span [i0,i1) x [j0,j1)
+  int leaf = -1;        // leaf index or -1
+  int child[2] = {-1, -1};
+  int parent = -1;
+  int height = 0;       // 0 for leaves, 1 + max(child heights) for parents
+};
+
+struct Tree {
+  double X0, Y0, X1, Y1;
+  int nx, ny;
+  std::vector<Box> boxes;
+  std::vector<int> leaves;             // leaf index -> box id
+  std::vector<int> leaf_edges;         // 4 per leaf (S, E, N, W): edge id
+  int n_edges = 0;
+  std::vector<int> edge_owners;        // 2 per edge: leaf*4+side of the owners, -1 if none
+  int height = 0;
+};
+
+// Gaussian node bookkeeping for a given q: box exterior lists and merge index sets.
+struct NodeSets {
+  int q = 0;
+  int n_gauss = 0;
+  std::vector<std::vector<int>> ge;    // per box: exterior Gaussian node ids (I_ge)
+  std::vector<std::vector<int>> J3;    // per parent: shared-edge node ids (alpha order)
+  std::vector<int> n1;                 // per parent: |J1|
+  std::vector<int> boundary;           // domain-boundary node ids, ascending
+};
+
+void build_node_sets(const Tree& t, int q, NodeSets& ns);
+
+// ---------------------------------------------------------------------------------------
+// Reference-element tables for (p, q) on [-1, 1] (Sec. 3.1-3.4).
+struct RefTables {
+  int p = 0, q = 0, m = 0, ne = 0;     // m = (p-2)^2 interior, ne = 4(p-1) exterior
+  std::vector<double> xc;              // p Chebyshev-Lobatto points, ascending
+  std::vector<double> xg;              // q Gauss-Legendre points, ascending
+  std::vector<double> D;               // p x p differentiation on xc
+  std::vector<double> D2;              // p x p, D*D
+  std::vector<double> Lg2c;            // p x q: Gauss data of one side -> its p Chebyshev points
+  std::vector<double> Ls;              // p x q: Lg2c with corner rows halved (side block of L_ce,ge)
+  std::vector<double> Lloc;            // q x p: Chebyshev -> Gauss on one side
+  std::vector<double> DceL;            // 4q x 4q: D_ge,ce L_ce,ge on [-1,1]^2 (row s scaled later)
+  std::vector<double> Lce;             // ne x 4q: L_ce,ge, rows = exterior nodes ascending
+  std::vector<int> ci;                 // m interior node indices, ascending
+  std::vector<int> ce;                 // ne exterior node indices, ascending
+};
+
+void build_ref_tables(int p, int q, RefTables& rt);
+
+// ---------------------------------------------------------------------------------------
+// Kernel-side parameter blocks.
+
+// One matrix of a batched partial Gauss-Jordan elimination: an R x R row-major matrix at
+// element offset off of the workspace, pivoting on its first K diagonal entries.
+struct GJDesc {
+  long long off;
+  int R;
+  int K;
+  int perm_off;        // offset of its K-entry logical->physical row map
+  int box;             // box id, for error reports
+};
+
+// A gathered, batched matrix product item: rows [0, M) of a row block of operator A.
+//   C[cidx[i]][r] = beta * C[cidx[i]][r] + sum_k A[i][k] * B(k)[r]  (+ Add[i][r])
+// with B(k) = B0[b0idx[k]] for k < kseg and B1[b1idx[k - kseg]] otherwise.  Row indices
+// are in units of vector rows (each row holds nrhs values).  An idx offset of -1 means
+// the identity map.  trans = 1 applies A^T (A stored row-major K x M with leading
+// dimension lda).
+struct GemmItem {
+  long long a_off;     // element offset of the block's first row (or column when trans)
+  int lda;
+  int M, K, kseg;
+  int b0_row, b0_idx;
+  int b1_row, b1_idx;
+  int c_row, c_idx;
+  int add_row;         // -1: no addend
+};
+
+// ---------------------------------------------------------------------------------------
+// Launchers (defined in the .cu files).  All take the stream explicitly.
+
+// Leaf matrices M = [[A_ci,ci, A_ci,ce L_ce,ge], [D_ge,ci, D_ge,ce L_ce,ge]] (size m+4q)
+// for leaves [leaf0, leaf0 + nleaf) of coeffs [6][n_leaf_total][p*p].
+struct LeafTablesDev {
+  const double* D;      // p x p
+  const double* D2;     // p x p
+  const double* Ls;     // p x q
+  const double* Lloc;   // q x p
+  const double* DceL;   // 4q x 4q
+  const int* ci;        // m
+};
+template <typename T>
+void launch_leaf_assemble(const double* coeffs, long long n_leaf_total, int leaf0, int nleaf,
+                          const double* hxy, int p, int q, const LeafTablesDev& tb, T* work,
+                          long long mat_stride, cudaStream_t s);
+
+template <typename T>
+void launch_gj_init(const GJDesc* d, int nmat, int* perm, cudaStream_t s);
+template <typename T>
+void launch_gj_panel(const GJDesc* d, int nmat, int maxK, T* work, int* perm, T* pinv, int c0,
+                     int nb, int* status, cudaStream_t s);
+template <typename T>
+void launch_gj_prep(const GJDesc* d, int nmat, int maxR, T* work, const int* perm, const T* pinv,
+                    T* prow, long long prow_stride, int c0, int nb, cudaStream_t s);
+template <typename T>
+void launch_gj_update(const GJDesc* d, int nmat, int maxR, T* work, const int* perm, T* prow,
+                      long long prow_stride, int c0, int nb, cudaStream_t s);
+
+// Extraction of a finished elimination: with sigma the logical->physical row map,
+//   TL[i][j] = sTL * M[sigma(i)][sigma^-1(j)]   (i, j < K)
+//   TR[i][c] = sTR * M[sigma(i)][K + c]
+//   BL[r][j] = sBL * M[K + r][sigma^-1(j)]
+//   BR[r][c] =       M[K + r][K + c]
+// Destinations are per matrix: base + b * stride with the given leading dimensions.
+struct ExtractDst {
+  void* TL; long long TL_off_stride; int TL_ld;   // element type given by the launcher
+  void* TR; long long TR_off_stride; int TR_ld;
+  void* BL; long long BL_off_stride; int BL_ld;
+  void* BR; long long BR_off_stride; int BR_ld;
+  double sTL, sTR, sBL;
+  const long long* TL_off;   // optional per-matrix offsets (override b * stride) or null
+  const long long* TR_off;
+  const long long* BL_off;
+  const long long* BR_off;
+  int ld_from_desc;          // 1: TL_ld = BL_ld = K and TR_ld = BR_ld = R - K per matrix
+};
+template <typename T, typename TO>
+void launch_gj_extract(const GJDesc* d, int nmat, int maxR, const T* work, const int* perm,
+                       const ExtractDst& dst, cudaStream_t s);
+
+// Merge assembly (Sec. 4): M_tau = [[Z, R], [-C, blkdiag(T11a, T22b)]] with rows/columns
+// ordered [J3 | J1 | J2], gathered from the children's T blocks.
+struct MergeDesc {
+  long long m_off;     // offset of M_tau in the workspace
+  int R;               // k3 + k12
+  int k3, n1;          // |J3|, |J1| (|J2| = R - k3 - n1)
+  long long ta_off, tb_off;  // children's T in the T store
+  int lda_a, lda_b;    // children's T sizes
+  int pos_off;         // offset of pos arrays: posA[R], posB[R] (position in child ge or -1)
+};
+template <typename T, typename TT>
+void launch_merge_assemble(const MergeDesc* d, int nmat, int maxR, const TT* tstore,
+                           const int* pos, T* work, cudaStream_t s);
+
+// Batched gathered products.
+template <typename TA, typename TV>
+void launch_gemm_items(const GemmItem* items, int nitems, int maxM, int trans, const TA* A,
+                       const TV* B0, const TV* B1, TV* C, const TV* Add, const int* idx,
+                       int nrhs, double beta, cudaStream_t s);
+
+// Up-sweep gather for a level of merges: d = h_b[pos3b] - h_a[pos3a] (+ rho[J3]) and
+// prefill V_tau = [0 (k3 rows) ; h_a[pos1a] ; h_b[pos2b]].
+struct UpGather {
+  int va_row, vb_row;  // row base of child h within V (child V base + child k3)
+  int vt_row;          // row base of V_tau
+  int d_row;           // row base of d for this merge in the d buffer
+  int k3, n1, n2;
+  int idx_off;         // pos3a[k3], pos3b[k3], J3[k3], pos1a[n1], pos2b[n2]
+};
+template <typename TV>
+void launch_up_gather(const UpGather* g, int n, int maxrows, const TV* V, TV* Vout, TV* dbuf,
+                      const double* rho, const int* idx, int nrhs, cudaStream_t s);
+
+// Scatter f into u at the boundary nodes and copy/convert vectors.
+template <typename TV>
+void launch_scatter_rows(const double* src, const int* idx, int n, TV* dst, int nrhs,
+                         cudaStream_t s);
+template <typename TI, typename TO>
+void launch_convert(const TI* src, TO* dst, long long n, double scale, cudaStream_t s);
+template <typename TI>
+void launch_axpy_to_f64(const TI* x, double* y, long long n, cudaStream_t s);
+
+// FP64 residual of the collocation system and leaf fluxes (mixed-precision refinement).
+struct ResidualArgs {
+  const double* coeffs; long long n_leaf; int p, q;
+  const double* hxy;
+  const double* D; const double* D2; const double* Lloc;
+  const int* ci;
+};
+void launch_leaf_residual_impl(const ResidualArgs& a, const int* leaf_edges, const double* Lce,
+                               const int* ce, const double* ug, const double* g, double* uc,
+                               double* r_out, double* vflux, int nrhs, cudaStream_t s);
+void launch_jump_residual(const int* pairs, int npairs, int q, const double* vflux,
+                          double* rho_out, int nrhs, cudaStream_t s);
+void launch_absmax(const double* x, long long n, double* out, cudaStream_t s);
+
+// Adjoint helpers.
+void launch_coeff_grad(const ResidualArgs& a, const double* uc, const double* gbar,
+                       double* grad, int nrhs, cudaStream_t s);
+template <typename TV>
+void launch_gather_reduce(const int* tab, int nnodes, const TV* src, TV* dst, int nrhs,
+                          int accumulate, cudaStream_t s);
+struct DownScatter {  // adjoint of the up gather: distribute hbar_tau and dbar to children
+  int va_row, vb_row, vt_row, d_row, k3, n1, n2, idx_off;
+};
+template <typename TV>
+void launch_down_scatter(const DownScatter* g, int n, int maxrows, TV* VB, const TV* dbar,
+                         double* rhobar, const int* idx, int nrhs, cudaStream_t s);
+
+// Optional launch timing (enabled with hps_timing_enable): records a pair of CUDA events
+// around the launches made while the scope is alive.
+bool timing_enabled();
+class TimingScope {
+ public:
+  TimingScope(const char* name, cudaStream_t s, double flops = 0.0, double bytes = 0.0);
+  ~TimingScope();
+  TimingScope(const TimingScope&) = delete;
+  TimingScope& operator=(const TimingScope&) = delete;
+
+ private:
+  cudaStream_t stream_;
+  double flops_, bytes_;
+  int cat_ = -1;
+  void* e0_ = nullptr;
+  void* e1_ = nullptr;
+};
+
+}  // namespace hps

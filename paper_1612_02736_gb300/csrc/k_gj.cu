@@ -1,0 +1,372 @@
+// Batched, blocked, partial Gauss-Jordan elimination (build stage, Algorithm 1).
+//
+// Every leaf and every merge of the build reduces to one dense elimination.  For a leaf
+// the matrix is M = [[A_ci,ci, A_ci,ce L_ce,ge], [D_ge,ci, D_ge,ce L_ce,ge]] (Sec. 3); for
+// a merge it is M = [[Z, R], [-C, blkdiag(T11a, T22b)]] with Z = T33a - T33b,
+// R = [-T31a | T32b], C = [T13a ; T23b] (Sec. 4).  Eliminating the first K pivots in place
+// (partial pivoting restricted to the first K rows) turns [[P, Q], [E, G]] into
+// [[P^-1, P^-1 Q], [-E P^-1, G - E P^-1 Q]]: for a leaf that is [[F, -S_ci], [-H, T]]
+// (Eqs. alpine1-alpine4) and for a merge [[X, S], [C X, T_tau]] (the merge formulas of
+// Sec. 4).  One sweep gives every operator Algorithm 1 asks for.
+//
+// Row swaps are never executed: perm maps logical rows to physical rows, and the
+// extraction kernel undoes the permutation (the inverse block picks up perm on its
+// columns).  Each panel of nb pivots costs three launches over the whole batch:
+//   gj_panel  : one CTA per matrix factors the nb-wide sub-panel (rows [c0, K)) with
+//               partial pivoting, records the pivot rows and forms Pinv = M_PP^-1;
+//   gj_prep   : writes the final panel columns (W_r = -M_rP Pinv, or Pinv on pivot rows)
+//               and copies the pivot rows to a side buffer;
+//   gj_update : rank-nb update of every other column, M_r += W_r Prow (pivot rows are
+//               replaced by Pinv Prow).
+// FP64 on GB300 runs on the FFMA pipe (no FP64 tensor path is faster on this part), so
+// the update is a register-tiled SIMT product.
+#include <cfloat>
+#include <cstdio>
+
+#include "hps_internal.h"
+
+namespace hps {
+
+namespace {
+
+constexpr int NBMAX = 16;
+
+template <typename T>
+__device__ __forceinline__ T tabs(T v) { return v < T(0) ? -v : v; }
+
+template <typename T> struct Eps;
+template <> struct Eps<double> { static constexpr double v = DBL_EPSILON; };
+template <> struct Eps<float> { static constexpr float v = FLT_EPSILON; };
+
+template <typename T>
+__global__ void gj_init_kernel(const GJDesc* __restrict__ d, int* __restrict__ perm) {
+  const GJDesc md = d[blockIdx.x];
+  for (int i = threadIdx.x; i < md.K; i += blockDim.x) perm[md.perm_off + i] = i;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) gj_panel_kernel(const GJDesc* __restrict__ d,
+                                                       T* __restrict__ work, int* __restrict__ perm,
+                                                       T* __restrict__ pinv, int c0, int nb_req,
+                                                       int* __restrict__ status) {
+  const GJDesc md = d[blockIdx.x];
+  if (c0 >= md.K) return;
+  const int nb = min(nb_req, md.K - c0);
+  const int nrows = md.K - c0;
+  const int tid = threadIdx.x, bs = blockDim.x;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* P = reinterpret_cast<T*>(smraw);                    // nrows x nb
+  int* pr = reinterpret_cast<int*>(P + (size_t)nrows * nb);  // nrows
+  __shared__ T red_v[32];
+  __shared__ int red_i[32];
+  __shared__ T colscale[NBMAX];
+  __shared__ int piv_row;
+  T* M = work + md.off;
+  const int R = md.R;
+  int* pm = perm + md.perm_off + c0;
+  for (int i = tid; i < nrows; i += bs) pr[i] = pm[i];
+  __syncthreads();
+  for (int e = tid; e < nrows * nb; e += bs) {
+    const int i = e / nb, j = e - (e / nb) * nb;
+    P[e] = M[(long long)pr[i] * R + c0 + j];
+  }
+  __syncthreads();
+  // column scales for the breakdown test
+  if (tid < nb) {
+    T mx = T(0);
+    for (int i = 0; i < nrows; ++i) mx = fmax(mx, tabs(P[i * nb + tid]));
+    colscale[tid] = mx;
+  }
+  __syncthreads();
+  const int lane = tid & 31, warp = tid >> 5, nwarp = bs >> 5;
+  for (int j = 0; j < nb; ++j) {
+    T best = T(-1);
+    int bi = nrows;
+    for (int i = j + tid; i < nrows; i += bs) {
+      const T v = tabs(P[i * nb + j]);
+      if (v > best) { best = v; bi = i; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const T ov = __shfl_down_sync(0xffffffffu, best, o);
+      const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    if (lane == 0) { red_v[warp] = best; red_i[warp] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      T b = red_v[0];
+      int ib = red_i[0];
+      for (int w = 1; w < nwarp; ++w)
+        if (red_v[w] > b || (red_v[w] == b && red_i[w] < ib)) { b = red_v[w]; ib = red_i[w]; }
+      const T tiny = T(64) * Eps<T>::v * colscale[j];
+      if (!(b > tiny) && status) atomicCAS(status, 0, md.box + 1);
+      if (ib >= nrows) ib = j;
+      piv_row = ib;
+      const int t = pr[j]; pr[j] = pr[ib]; pr[ib] = t;
+    }
+    __syncthreads();
+    const int r = piv_row;
+    if (r != j && tid < nb) {
+      const T t = P[j * nb + tid]; P[j * nb + tid] = P[r * nb + tid]; P[r * nb + tid] = t;
+    }
+    __syncthreads();
+    const T pv = P[j * nb + j];
+    const T inv = (pv != T(0)) ? T(1) / pv : T(0);
+    for (int i = j + 1 + tid; i < nrows; i += bs) {
+      const T l = P[i * nb + j] * inv;
+      P[i * nb + j] = l;
+      for (int c = j + 1; c < nb; ++c) P[i * nb + c] -= l * P[j * nb + c];
+    }
+    __syncthreads();
+  }
+  // Pinv = (L U)^-1 of the leading nb x nb block, one column per thread.
+  if (tid < nb) {
+    T y[NBMAX];
+    for (int k = 0; k < nb; ++k) {
+      T s = (k == tid) ? T(1) : T(0);
+      for (int l = 0; l < k; ++l) s -= P[k * nb + l] * y[l];
+      y[k] = s;
+    }
+    for (int k = nb - 1; k >= 0; --k) {
+      T s = y[k];
+      for (int l = k + 1; l < nb; ++l) s -= P[k * nb + l] * y[l];
+      const T pv = P[k * nb + k];
+      y[k] = (pv != T(0)) ? s / pv : T(0);
+    }
+    T* Pi = pinv + (long long)blockIdx.x * NBMAX * NBMAX;
+    for (int k = 0; k < nb; ++k) Pi[k * NBMAX + tid] = y[k];
+  }
+  for (int i = tid; i < nrows; i += bs) pm[i] = pr[i];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) gj_prep_kernel(const GJDesc* __restrict__ d,
+                                                      T* __restrict__ work, const int* __restrict__ perm,
+                                                      const T* __restrict__ pinv, T* __restrict__ prow,
+                                                      long long prow_stride, int c0, int nb_req) {
+  const GJDesc md = d[blockIdx.y];
+  if (c0 >= md.K) return;
+  const int nb = min(nb_req, md.K - c0);
+  const int R = md.R;
+  __shared__ T Pi[NBMAX * NBMAX];
+  __shared__ int pphys[NBMAX];
+  const int tid = threadIdx.x;
+  const T* Pg = pinv + (long long)blockIdx.y * NBMAX * NBMAX;
+  for (int e = tid; e < NBMAX * NBMAX; e += blockDim.x) Pi[e] = Pg[e];
+  if (tid < nb) pphys[tid] = perm[md.perm_off + c0 + tid];
+  __syncthreads();
+  T* M = work + md.off;
+  const int r = blockIdx.x * blockDim.x + tid;
+  if (r < R) {
+    int tp = -1;
+    for (int t = 0; t < nb; ++t)
+      if (pphys[t] == r) tp = t;
+    T* Mr = M + (long long)r * R + c0;
+    if (tp >= 0) {
+      for (int j = 0; j < nb; ++j) Mr[j] = Pi[tp * NBMAX + j];
+    } else {
+      T mrow[NBMAX];
+      for (int t = 0; t < nb; ++t) mrow[t] = Mr[t];
+      for (int j = 0; j < nb; ++j) {
+        T s = T(0);
+        for (int t = 0; t < nb; ++t) s += mrow[t] * Pi[t * NBMAX + j];
+        Mr[j] = -s;
+      }
+    }
+  }
+  // copy the pivot rows (columns outside the panel) to the side buffer
+  T* pb = prow + (long long)blockIdx.y * prow_stride;
+  const long long total = (long long)nb * R;
+  for (long long e = (long long)blockIdx.x * blockDim.x + tid; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int t = (int)(e / R);
+    const int c = (int)(e - (long long)t * R);
+    if (c < c0 || c >= c0 + nb) pb[(long long)t * R + c] = M[(long long)pphys[t] * R + c];
+  }
+}
+
+constexpr int UBM = 64, UBN = 64;
+
+template <typename T>
+__global__ void __launch_bounds__(256) gj_update_kernel(const GJDesc* __restrict__ d,
+                                                        T* __restrict__ work, const int* __restrict__ perm,
+                                                        const T* __restrict__ prow, long long prow_stride,
+                                                        int c0, int nb_req) {
+  const GJDesc md = d[blockIdx.y];
+  if (c0 >= md.K) return;
+  const int nb = min(nb_req, md.K - c0);
+  const int R = md.R;
+  const int tiles = (R + UBN - 1) / UBN;
+  const int tm = blockIdx.x / tiles, tn = blockIdx.x - (blockIdx.x / tiles) * tiles;
+  if (tm >= tiles) return;
+  const int row0 = tm * UBM, col0 = tn * UBN;
+  if (col0 >= c0 && col0 + UBN <= c0 + nb) return;  // tile entirely inside the panel
+  __shared__ T Ws[UBM][NBMAX + 1];
+  __shared__ T Ps[NBMAX][UBN];
+  __shared__ int pphys[NBMAX];
+  __shared__ unsigned char isp[UBM];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  T* M = work + md.off;
+  if (tid < nb) pphys[tid] = perm[md.perm_off + c0 + tid];
+  __syncthreads();
+  if (tid < UBM) {
+    const int r = row0 + tid;
+    unsigned char f = 0;
+    for (int t = 0; t < nb; ++t)
+      if (pphys[t] == r) f = 1;
+    isp[tid] = f;
+  }
+  for (int e = tid; e < UBM * NBMAX; e += 256) {
+    const int i = e / NBMAX, t = e - (e / NBMAX) * NBMAX;
+    const int r = row0 + i;
+    Ws[i][t] = (r < R && t < nb) ? M[(long long)r * R + c0 + t] : T(0);
+  }
+  const T* pb = prow + (long long)blockIdx.y * prow_stride;
+  for (int e = tid; e < NBMAX * UBN; e += 256) {
+    const int t = e / UBN, j = e - (e / UBN) * UBN;
+    const int c = col0 + j;
+    Ps[t][j] = (t < nb && c < R) ? pb[(long long)t * R + c] : T(0);
+  }
+  __syncthreads();
+  T acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+  for (int t = 0; t < nb; ++t) {
+    T a[4], b[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a[i] = Ws[ty + 16 * i][t];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) b[j] = Ps[t][tx + 16 * j];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int li = ty + 16 * i;
+    const int r = row0 + li;
+    if (r >= R) continue;
+    T* Mr = M + (long long)r * R;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = col0 + tx + 16 * j;
+      if (c >= R || (c >= c0 && c < c0 + nb)) continue;
+      const T old = isp[li] ? T(0) : Mr[c];
+      Mr[c] = old + acc[i][j];
+    }
+  }
+}
+
+template <typename T, typename TO>
+__global__ void __launch_bounds__(256) gj_extract_kernel(const GJDesc* __restrict__ d,
+                                                         const T* __restrict__ work,
+                                                         const int* __restrict__ perm, ExtractDst dst) {
+  const int b = blockIdx.y;
+  const GJDesc md = d[b];
+  const int R = md.R, K = md.K;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  int* sig = reinterpret_cast<int*>(smraw);   // K
+  int* isig = sig + K;                         // K
+  for (int i = threadIdx.x; i < K; i += blockDim.x) sig[i] = perm[md.perm_off + i];
+  __syncthreads();
+  for (int i = threadIdx.x; i < K; i += blockDim.x) isig[sig[i]] = i;
+  __syncthreads();
+  const T* M = work + md.off;
+  const long long total = (long long)R * R;
+  TO* TL = (TO*)dst.TL; TO* TR = (TO*)dst.TR; TO* BL = (TO*)dst.BL; TO* BR = (TO*)dst.BR;
+  const long long tlo = dst.TL_off ? dst.TL_off[b] : (long long)b * dst.TL_off_stride;
+  const long long tro = dst.TR_off ? dst.TR_off[b] : (long long)b * dst.TR_off_stride;
+  const long long blo = dst.BL_off ? dst.BL_off[b] : (long long)b * dst.BL_off_stride;
+  const long long bro = dst.BR_off ? dst.BR_off[b] : (long long)b * dst.BR_off_stride;
+  const int ldTL = dst.ld_from_desc ? K : dst.TL_ld, ldBL = dst.ld_from_desc ? K : dst.BL_ld;
+  const int ldTR = dst.ld_from_desc ? R - K : dst.TR_ld, ldBR = dst.ld_from_desc ? R - K : dst.BR_ld;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int lr = (int)(e / R);
+    const int lc = (int)(e - (long long)lr * R);
+    const int sr = lr < K ? sig[lr] : lr;
+    const int sc = lc < K ? isig[lc] : lc;
+    const T v = M[(long long)sr * R + sc];
+    if (lr < K) {
+      if (lc < K) {
+        if (TL) TL[tlo + (long long)lr * ldTL + lc] = (TO)(dst.sTL * (double)v);
+      } else if (TR) {
+        TR[tro + (long long)lr * ldTR + (lc - K)] = (TO)(dst.sTR * (double)v);
+      }
+    } else {
+      if (lc < K) {
+        if (BL) BL[blo + (long long)(lr - K) * ldBL + lc] = (TO)(dst.sBL * (double)v);
+      } else if (BR) {
+        BR[bro + (long long)(lr - K) * ldBR + (lc - K)] = (TO)v;
+      }
+    }
+  }
+}
+
+}  // namespace
+
+template <typename T>
+void launch_gj_init(const GJDesc* d, int nmat, int* perm, cudaStream_t s) {
+  gj_init_kernel<T><<<nmat, 256, 0, s>>>(d, perm);
+}
+
+template <typename T>
+void launch_gj_panel(const GJDesc* d, int nmat, int maxK, T* work, int* perm, T* pinv, int c0,
+                     int nb, int* status, cudaStream_t s) {
+  const int nrows = maxK - c0;
+  if (nrows <= 0) return;
+  const size_t smem = (size_t)nrows * nb * sizeof(T) + (size_t)nrows * sizeof(int) + 16;
+  static size_t configured = 0;
+  if (smem > 48 * 1024 && smem > configured) {
+    cudaFuncSetAttribute(gj_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    configured = smem;
+  }
+  gj_panel_kernel<T><<<nmat, 256, smem, s>>>(d, work, perm, pinv, c0, nb, status);
+}
+
+template <typename T>
+void launch_gj_prep(const GJDesc* d, int nmat, int maxR, T* work, const int* perm, const T* pinv,
+                    T* prow, long long prow_stride, int c0, int nb, cudaStream_t s) {
+  dim3 grid((maxR + 255) / 256, nmat);
+  gj_prep_kernel<T><<<grid, 256, 0, s>>>(d, work, perm, pinv, prow, prow_stride, c0, nb);
+}
+
+template <typename T>
+void launch_gj_update(const GJDesc* d, int nmat, int maxR, T* work, const int* perm, T* prow,
+                      long long prow_stride, int c0, int nb, cudaStream_t s) {
+  const int tiles = (maxR + UBN - 1) / UBN;
+  dim3 grid(tiles * tiles, nmat);
+  gj_update_kernel<T><<<grid, 256, 0, s>>>(d, work, perm, prow, prow_stride, c0, nb);
+}
+
+template <typename T, typename TO>
+void launch_gj_extract(const GJDesc* d, int nmat, int maxR, const T* work, const int* perm,
+                       const ExtractDst& dst, cudaStream_t s) {
+  const long long total = (long long)maxR * maxR;
+  int gx = (int)((total + 255) / 256);
+  if (gx > 1024) gx = 1024;
+  const size_t smem = (size_t)2 * maxR * sizeof(int);
+  static size_t configured = 0;
+  if (smem > 48 * 1024 && smem > configured) {
+    cudaFuncSetAttribute(gj_extract_kernel<T, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    configured = smem;
+  }
+  gj_extract_kernel<T, TO><<<dim3(gx, nmat), 256, smem, s>>>(d, work, perm, dst);
+}
+
+template void launch_gj_init<double>(const GJDesc*, int, int*, cudaStream_t);
+template void launch_gj_init<float>(const GJDesc*, int, int*, cudaStream_t);
+template void launch_gj_panel<double>(const GJDesc*, int, int, double*, int*, double*, int, int, int*, cudaStream_t);
+template void launch_gj_panel<float>(const GJDesc*, int, int, float*, int*, float*, int, int, int*, cudaStream_t);
+template void launch_gj_prep<double>(const GJDesc*, int, int, double*, const int*, const double*, double*, long long, int, int, cudaStream_t);
+template void launch_gj_prep<float>(const GJDesc*, int, int, float*, const int*, const float*, float*, long long, int, int, cudaStream_t);
+template void launch_gj_update<double>(const GJDesc*, int, int, double*, const int*, double*, long long, int, int, cudaStream_t);
+template void launch_gj_update<float>(const GJDesc*, int, int, float*, const int*, float*, long long, int, int, cudaStream_t);
+template void launch_gj_extract<double, double>(const GJDesc*, int, int, const double*, const int*, const ExtractDst&, cudaStream_t);
+template void launch_gj_extract<float, double>(const GJDesc*, int, int, const float*, const int*, const ExtractDst&, cudaStream_t);
+
+}  // namespace hps

@@ -1,0 +1,121 @@
+// Leaf assembly (Sec. 3.2-3.4, Algorithm 1 leaf branch): builds, per leaf, the matrix
+//   M = [[A_ci,ci , A_ci,ce L_ce,ge],
+//        [D_ge,ci , D_ge,ce L_ce,ge]]          (size m + 4q, rows/cols [interior | Gauss])
+// whose partial Gauss-Jordan elimination on the first m pivots yields F, S, H and T.
+//
+// A = -C11 D1^2 - 2 C12 D1 D2 - C22 D2^2 + C1 D1 + C2 D2 + C is never formed: each entry
+// follows from the 1D tables (D1 = I (x) Dx and D2 = Dy (x) I, x fastest) in O(1).
+// A_ci,ce L_ce,ge uses the side structure of L_ce,ge: a Gauss node on side s only sees the
+// p Chebyshev nodes of side s (corner rows carry weight one half, the corner average of
+// Eq. alpine2p5), so each entry is a p-term sum.  The bottom rows are reference-element
+// constants scaled by 2/h of the side's derivative direction.
+#include "hps_internal.h"
+
+namespace hps {
+
+namespace {
+
+template <typename T>
+__global__ void __launch_bounds__(256) leaf_assemble_kernel(
+    const double* __restrict__ coeffs, long long n_leaf_total, int leaf0, const double* __restrict__ hxy,
+    int p, int q, LeafTablesDev tb, T* __restrict__ work, long long mat_stride) {
+  const int lf = leaf0 + blockIdx.x;
+  const int pp = p * p;
+  const int m = (p - 2) * (p - 2);
+  const int nq = 4 * q;
+  const int R = m + nq;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double* cf = reinterpret_cast<double*>(smraw);  // 6 * pp
+  double* sD = cf + 6 * pp;                        // pp
+  double* sD2 = sD + pp;                           // pp
+  double* sLs = sD2 + pp;                          // p * q
+  double* sLl = sLs + p * q;                       // q * p
+  int* sci = reinterpret_cast<int*>(sLl + q * p);  // m
+  const int tid = threadIdx.x, bs = blockDim.x;
+  for (int e = tid; e < 6 * pp; e += bs) {
+    const int k = e / pp, n = e - (e / pp) * pp;
+    cf[e] = coeffs[((long long)k * n_leaf_total + lf) * pp + n];
+  }
+  for (int e = tid; e < pp; e += bs) { sD[e] = tb.D[e]; sD2[e] = tb.D2[e]; }
+  for (int e = tid; e < p * q; e += bs) { sLs[e] = tb.Ls[e]; sLl[e] = tb.Lloc[e]; }
+  for (int e = tid; e < m; e += bs) sci[e] = tb.ci[e];
+  __syncthreads();
+  const double sx = 2.0 / hxy[2 * lf], sy = 2.0 / hxy[2 * lf + 1];
+  T* M = work + (long long)blockIdx.x * mat_stride;
+  const long long total = (long long)R * R;
+  for (long long e = tid; e < total; e += bs) {
+    const int row = (int)(e / R);
+    const int col = (int)(e - (long long)row * R);
+    double v = 0.0;
+    if (row < m) {
+      const int ni = sci[row];
+      const int ix = ni % p, iy = ni / p;
+      const double c11 = cf[ni], c12 = cf[pp + ni], c22 = cf[2 * pp + ni];
+      const double c1 = cf[3 * pp + ni], c2 = cf[4 * pp + ni], c0 = cf[5 * pp + ni];
+      // A[ni][(jx, jy)] for the operator of Sec. 3.2
+      auto Aent = [&](int jx, int jy) -> double {
+        double a = -2.0 * c12 * sx * sy * sD[ix * p + jx] * sD[iy * p + jy];
+        if (iy == jy) a += -c11 * sx * sx * sD2[ix * p + jx] + c1 * sx * sD[ix * p + jx];
+        if (ix == jx) a += -c22 * sy * sy * sD2[iy * p + jy] + c2 * sy * sD[iy * p + jy];
+        if (ix == jx && iy == jy) a += c0;
+        return a;
+      };
+      if (col < m) {
+        const int nj = sci[col];
+        v = Aent(nj % p, nj / p);
+      } else {
+        const int g = col - m, s = g / q, a = g - (g / q) * q;
+        for (int t = 0; t < p; ++t) {
+          int jx, jy;
+          switch (s) {
+            case 0: jx = t; jy = 0; break;
+            case 1: jx = p - 1; jy = t; break;
+            case 2: jx = t; jy = p - 1; break;
+            default: jx = 0; jy = t; break;
+          }
+          v += Aent(jx, jy) * sLs[t * q + a];
+        }
+      }
+    } else {
+      const int g = row - m, s = g / q, a = g - (g / q) * q;
+      const double sc = (s == 0 || s == 2) ? sy : sx;
+      if (col < m) {
+        const int nj = sci[col];
+        const int nx = nj % p, ny = nj / p;
+        double r;
+        switch (s) {
+          case 0: r = sLl[a * p + nx] * sD[0 * p + ny]; break;
+          case 1: r = sLl[a * p + ny] * sD[(p - 1) * p + nx]; break;
+          case 2: r = sLl[a * p + nx] * sD[(p - 1) * p + ny]; break;
+          default: r = sLl[a * p + ny] * sD[0 * p + nx]; break;
+        }
+        v = sc * r;
+      } else {
+        v = sc * tb.DceL[(long long)g * nq + (col - m)];
+      }
+    }
+    M[e] = (T)v;
+  }
+}
+
+}  // namespace
+
+template <typename T>
+void launch_leaf_assemble(const double* coeffs, long long n_leaf_total, int leaf0, int nleaf,
+                          const double* hxy, int p, int q, const LeafTablesDev& tb, T* work,
+                          long long mat_stride, cudaStream_t s) {
+  const int pp = p * p, m = (p - 2) * (p - 2);
+  const size_t smem = (size_t)(6 * pp + 2 * pp + 2 * p * q) * sizeof(double) + (size_t)m * sizeof(int) + 16;
+  static size_t configured = 0;
+  if (smem > 48 * 1024 && smem > configured) {
+    cudaFuncSetAttribute(leaf_assemble_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    configured = smem;
+  }
+  leaf_assemble_kernel<T><<<nleaf, 256, smem, s>>>(coeffs, n_leaf_total, leaf0, hxy, p, q, tb, work,
+                                                  mat_stride);
+}
+
+template void launch_leaf_assemble<double>(const double*, long long, int, int, const double*, int, int,
+                                           const LeafTablesDev&, double*, long long, cudaStream_t);
+
+}  // namespace hps

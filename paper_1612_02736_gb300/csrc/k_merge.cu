@@ -1,0 +1,63 @@
+// Merge assembly (Sec. 4, Algorithm 1 merge branch).  For a parent tau with children
+// alpha and beta, rows and columns ordered [J3 | J1 | J2]:
+//   M_tau = [[ T33a - T33b , -T31a , T32b ],
+//            [ -T13a       ,  T11a , 0    ],
+//            [ -T23b       ,  0    , T22b ]]
+// Partial Gauss-Jordan on the first |J3| pivots then leaves X = (T33a - T33b)^-1,
+// S = X [-T31a | T32b], C X and T_tau = blkdiag(T11a, T22b) + [T13a; T23b] S in place.
+// posA / posB give each row's position in alpha's / beta's exterior list (or -1), so an
+// entry is  sa * Ta[posA r][posA c] + sb * Tb[posB r][posB c]  with the signs above.
+#include "hps_internal.h"
+
+namespace hps {
+
+namespace {
+
+template <typename T, typename TT>
+__global__ void __launch_bounds__(256) merge_assemble_kernel(const MergeDesc* __restrict__ d,
+                                                             const TT* __restrict__ tstore,
+                                                             const int* __restrict__ pos,
+                                                             T* __restrict__ work) {
+  const MergeDesc md = d[blockIdx.y];
+  const int R = md.R, k3 = md.k3;
+  const int* pA = pos + md.pos_off;
+  const int* pB = pA + R;
+  const TT* Ta = tstore + md.ta_off;
+  const TT* Tb = tstore + md.tb_off;
+  T* M = work + md.m_off;
+  const long long total = (long long)R * R;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(e / R);
+    const int c = (int)(e - (long long)r * R);
+    const int ar = pA[r], ac = pA[c], br = pB[r], bc = pB[c];
+    double v = 0.0;
+    if (ar >= 0 && ac >= 0) {
+      const double sa = ((r < k3) == (c < k3)) ? 1.0 : -1.0;
+      v += sa * (double)Ta[(long long)ar * md.lda_a + ac];
+    }
+    if (br >= 0 && bc >= 0) {
+      const double sb = (c < k3) ? -1.0 : 1.0;
+      v += sb * (double)Tb[(long long)br * md.lda_b + bc];
+    }
+    M[e] = (T)v;
+  }
+}
+
+}  // namespace
+
+template <typename T, typename TT>
+void launch_merge_assemble(const MergeDesc* d, int nmat, int maxR, const TT* tstore, const int* pos,
+                           T* work, cudaStream_t s) {
+  const long long total = (long long)maxR * maxR;
+  int gx = (int)((total + 255) / 256);
+  if (gx > 2048) gx = 2048;
+  merge_assemble_kernel<T, TT><<<dim3(gx, nmat), 256, 0, s>>>(d, tstore, pos, work);
+}
+
+template void launch_merge_assemble<double, double>(const MergeDesc*, int, int, const double*, const int*,
+                                                    double*, cudaStream_t);
+template void launch_merge_assemble<float, double>(const MergeDesc*, int, int, const double*, const int*,
+                                                   float*, cudaStream_t);
+
+}  // namespace hps

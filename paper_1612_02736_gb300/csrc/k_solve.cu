@@ -1,0 +1,648 @@
+// Solve-stage kernels (Algorithm 2), the FP64 residual used by mixed-precision iterative
+// refinement, and the adjoint helpers.
+//
+// Every operator application of Algorithm 2 -- h = H g on leaves, [w; h] = [X; C X] d and
+// u_gi = S u_ge + w on merges, u_c = [F | S_ci] [g_ci; u_ge] on leaves -- is a batched
+// product of a stored dense operator with a block of gathered vectors (one column per
+// right-hand side).  The stored operators are streamed exactly once per solve (Sec. 5.4),
+// so the sweep is bound by HBM bandwidth (FP32 operators) or by the FP64 FFMA pipe (FP64
+// operators on GB300).  Vectors are [row][rhs] with the right-hand side fastest.
+#include <cfloat>
+
+#include "hps_internal.h"
+
+namespace hps {
+
+namespace {
+
+template <typename T> struct AccOf { using type = T; };
+
+__device__ __forceinline__ int map_row(const int* __restrict__ idx, int base_or_off, int row_base, int k) {
+  // idx offset < 0: identity (row_base + k); else row_base + idx[off + k]
+  return base_or_off < 0 ? row_base + k : row_base + idx[base_or_off + k];
+}
+
+constexpr int KC = 256;  // K chunk staged in shared memory (GEMV path)
+
+// nrhs <= NR (1, 2 or 4).  Non-transposed: one warp per output row, lanes split K.
+template <typename TA, typename TV, int NR>
+__global__ void __launch_bounds__(256) gemv_items_kernel(const GemmItem* __restrict__ items,
+                                                         const TA* __restrict__ A, const TV* __restrict__ B0,
+                                                         const TV* __restrict__ B1, TV* __restrict__ C,
+                                                         const TV* __restrict__ Add, const int* __restrict__ idx,
+                                                         int nrhs, TV beta) {
+  using Acc = TV;
+  const GemmItem it = items[blockIdx.x];
+  __shared__ Acc Bs[KC][NR];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const TA* Ab = A + it.a_off;
+  Acc acc[8][NR];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int r = 0; r < NR; ++r) acc[i][r] = Acc(0);
+  for (int k0 = 0; k0 < it.K; k0 += KC) {
+    const int kc = min(KC, it.K - k0);
+    for (int e = tid; e < kc * NR; e += 256) {
+      const int kk = e / NR, r = e - (e / NR) * NR;
+      const int k = k0 + kk;
+      Acc v = Acc(0);
+      if (r < nrhs) {
+        if (k < it.kseg) v = B0[(long long)map_row(idx, it.b0_idx, it.b0_row, k) * nrhs + r];
+        else v = B1[(long long)map_row(idx, it.b1_idx, it.b1_row, k - it.kseg) * nrhs + r];
+      }
+      Bs[kk][r] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int row = warp + 8 * i;
+      if (row >= it.M) break;
+      const TA* Ar = Ab + (long long)row * it.lda + k0;
+      for (int kk = lane; kk < kc; kk += 32) {
+        const Acc a = (Acc)Ar[kk];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) acc[i][r] += a * Bs[kk][r];
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int row = warp + 8 * i;
+    if (row >= it.M) break;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      Acc v = acc[i][r];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);  // all lanes hold the sum
+      acc[i][r] = v;
+    }
+    if (lane < NR && lane < nrhs) {
+      Acc v = Acc(0);
+#pragma unroll
+      for (int r = 0; r < NR; ++r)
+        if (r == lane) v = acc[i][r];
+      const long long cr = (long long)map_row(idx, it.c_idx, it.c_row, row) * nrhs + lane;
+      if (it.add_row >= 0) v += Add[(long long)(it.add_row + row) * nrhs + lane];
+      C[cr] = (beta != TV(0) ? beta * C[cr] : TV(0)) + v;
+    }
+  }
+}
+
+// Transposed GEMV: output i is column i of the stored K x lda operator.  256 threads =
+// 4 K-groups x 64 outputs.
+template <typename TA, typename TV, int NR>
+__global__ void __launch_bounds__(256) gemvT_items_kernel(const GemmItem* __restrict__ items,
+                                                          const TA* __restrict__ A, const TV* __restrict__ B0,
+                                                          const TV* __restrict__ B1, TV* __restrict__ C,
+                                                          const TV* __restrict__ Add, const int* __restrict__ idx,
+                                                          int nrhs, TV beta) {
+  using Acc = TV;
+  const GemmItem it = items[blockIdx.x];
+  __shared__ Acc Bs[KC][NR];
+  __shared__ Acc red[4][64][NR];
+  const int tid = threadIdx.x, i = tid & 63, kg = tid >> 6;
+  const TA* Ab = A + it.a_off;
+  Acc acc[NR];
+#pragma unroll
+  for (int r = 0; r < NR; ++r) acc[r] = Acc(0);
+  for (int k0 = 0; k0 < it.K; k0 += KC) {
+    const int kc = min(KC, it.K - k0);
+    for (int e = tid; e < kc * NR; e += 256) {
+      const int kk = e / NR, r = e - (e / NR) * NR;
+      const int k = k0 + kk;
+      Acc v = Acc(0);
+      if (r < nrhs) {
+        if (k < it.kseg) v = B0[(long long)map_row(idx, it.b0_idx, it.b0_row, k) * nrhs + r];
+        else v = B1[(long long)map_row(idx, it.b1_idx, it.b1_row, k - it.kseg) * nrhs + r];
+      }
+      Bs[kk][r] = v;
+    }
+    __syncthreads();
+    if (i < it.M) {
+      for (int kk = kg; kk < kc; kk += 4) {
+        const Acc a = (Acc)Ab[(long long)(k0 + kk) * it.lda + i];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) acc[r] += a * Bs[kk][r];
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < NR; ++r) red[kg][i][r] = acc[r];
+  __syncthreads();
+  if (kg == 0 && i < it.M) {
+    for (int r = 0; r < NR && r < nrhs; ++r) {
+      Acc v = red[0][i][r] + red[1][i][r] + red[2][i][r] + red[3][i][r];
+      const long long cr = (long long)map_row(idx, it.c_idx, it.c_row, i) * nrhs + r;
+      if (it.add_row >= 0) v += Add[(long long)(it.add_row + i) * nrhs + r];
+      C[cr] = (beta != TV(0) ? beta * C[cr] : TV(0)) + v;
+    }
+  }
+}
+
+// Tiled product for nrhs > 4: 64 rows x BN right-hand sides per CTA, 16 x 16 threads,
+// 4 x (BN/16) outputs per thread.
+template <typename TA, typename TV, int BN, bool TRANS>
+__global__ void __launch_bounds__(256) gemm_items_kernel(const GemmItem* __restrict__ items,
+                                                         const TA* __restrict__ A, const TV* __restrict__ B0,
+                                                         const TV* __restrict__ B1, TV* __restrict__ C,
+                                                         const TV* __restrict__ Add, const int* __restrict__ idx,
+                                                         int nrhs, TV beta) {
+  using Acc = TV;
+  constexpr int BM = 64, BK = 16, TN = BN / 16;
+  const GemmItem it = items[blockIdx.x];
+  const int n0 = blockIdx.y * BN;
+  __shared__ Acc As[BK][BM + 1];
+  __shared__ Acc Bs[BK][BN];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const TA* Ab = A + it.a_off;
+  Acc acc[4][TN];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = Acc(0);
+  for (int k0 = 0; k0 < it.K; k0 += BK) {
+    for (int e = tid; e < BK * BM; e += 256) {
+      int kk, rr;
+      if (TRANS) { kk = e / BM; rr = e - (e / BM) * BM; }
+      else { rr = e / BK; kk = e - (e / BK) * BK; }
+      const int k = k0 + kk;
+      Acc v = Acc(0);
+      if (k < it.K && rr < it.M)
+        v = TRANS ? (Acc)Ab[(long long)k * it.lda + rr] : (Acc)Ab[(long long)rr * it.lda + k];
+      As[kk][rr] = v;
+    }
+    for (int e = tid; e < BK * BN; e += 256) {
+      const int kk = e / BN, n = e - (e / BN) * BN;
+      const int k = k0 + kk, r = n0 + n;
+      Acc v = Acc(0);
+      if (k < it.K && r < nrhs) {
+        if (k < it.kseg) v = B0[(long long)map_row(idx, it.b0_idx, it.b0_row, k) * nrhs + r];
+        else v = B1[(long long)map_row(idx, it.b1_idx, it.b1_row, k - it.kseg) * nrhs + r];
+      }
+      Bs[kk][n] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      Acc a[4], b[TN];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] += a[i] * b[j];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int row = ty + 16 * i;
+    if (row >= it.M) continue;
+    const long long crow = (long long)map_row(idx, it.c_idx, it.c_row, row) * nrhs;
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      const int r = n0 + tx + 16 * j;
+      if (r >= nrhs) continue;
+      Acc v = acc[i][j];
+      if (it.add_row >= 0) v += Add[(long long)(it.add_row + row) * nrhs + r];
+      C[crow + r] = (beta != TV(0) ? beta * C[crow + r] : TV(0)) + v;
+    }
+  }
+}
+
+template <typename TV>
+__global__ void up_gather_kernel(const UpGather* __restrict__ g, const TV* __restrict__ V, TV* __restrict__ Vout,
+                                 TV* __restrict__ dbuf, const double* __restrict__ rho,
+                                 const int* __restrict__ idx, int nrhs) {
+  const UpGather u = g[blockIdx.y];
+  const int* p3a = idx + u.idx_off;
+  const int* p3b = p3a + u.k3;
+  const int* j3 = p3b + u.k3;
+  const int* p1a = j3 + u.k3;
+  const int* p2b = p1a + u.n1;
+  const int rows = u.k3 + u.k3 + u.n1 + u.n2;
+  const long long total = (long long)rows * nrhs;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int row = (int)(e / nrhs);
+    const int r = (int)(e - (long long)row * nrhs);
+    if (row < u.k3) {
+      TV v = V[(long long)(u.vb_row + p3b[row]) * nrhs + r] - V[(long long)(u.va_row + p3a[row]) * nrhs + r];
+      if (rho) v += (TV)rho[(long long)j3[row] * nrhs + r];
+      dbuf[(long long)(u.d_row + row) * nrhs + r] = v;
+    } else if (row < 2 * u.k3) {
+      Vout[(long long)(u.vt_row + row - u.k3) * nrhs + r] = TV(0);
+    } else if (row < 2 * u.k3 + u.n1) {
+      const int i = row - 2 * u.k3;
+      Vout[(long long)(u.vt_row + u.k3 + i) * nrhs + r] = V[(long long)(u.va_row + p1a[i]) * nrhs + r];
+    } else {
+      const int i = row - 2 * u.k3 - u.n1;
+      Vout[(long long)(u.vt_row + u.k3 + u.n1 + i) * nrhs + r] = V[(long long)(u.vb_row + p2b[i]) * nrhs + r];
+    }
+  }
+}
+
+template <typename TV>
+__global__ void down_scatter_kernel(const DownScatter* __restrict__ g, TV* __restrict__ VB,
+                                    const TV* __restrict__ dbar, double* __restrict__ rhobar,
+                                    const int* __restrict__ idx, int nrhs) {
+  const DownScatter u = g[blockIdx.y];
+  const int* p3a = idx + u.idx_off;
+  const int* p3b = p3a + u.k3;
+  const int* j3 = p3b + u.k3;
+  const int* p1a = j3 + u.k3;
+  const int* p2b = p1a + u.n1;
+  const int rows = u.k3 + u.n1 + u.n2;
+  const long long total = (long long)rows * nrhs;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int row = (int)(e / nrhs);
+    const int r = (int)(e - (long long)row * nrhs);
+    if (row < u.k3) {
+      const TV v = dbar[(long long)(u.d_row + row) * nrhs + r];
+      VB[(long long)(u.vb_row + p3b[row]) * nrhs + r] = v;
+      VB[(long long)(u.va_row + p3a[row]) * nrhs + r] = -v;
+      if (rhobar) rhobar[(long long)j3[row] * nrhs + r] = (double)v;
+    } else if (row < u.k3 + u.n1) {
+      const int i = row - u.k3;
+      VB[(long long)(u.va_row + p1a[i]) * nrhs + r] = VB[(long long)(u.vt_row + u.k3 + i) * nrhs + r];
+    } else {
+      const int i = row - u.k3 - u.n1;
+      VB[(long long)(u.vb_row + p2b[i]) * nrhs + r] = VB[(long long)(u.vt_row + u.k3 + u.n1 + i) * nrhs + r];
+    }
+  }
+}
+
+template <typename TV>
+__global__ void scatter_rows_kernel(const double* __restrict__ src, const int* __restrict__ idx, int n,
+                                    TV* __restrict__ dst, int nrhs) {
+  const long long total = (long long)n * nrhs;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(e / nrhs);
+    const int r = (int)(e - (long long)k * nrhs);
+    dst[(long long)idx[k] * nrhs + r] = (TV)src[e];
+  }
+}
+
+template <typename TI, typename TO>
+__global__ void convert_kernel(const TI* __restrict__ src, TO* __restrict__ dst, long long n, double scale) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    dst[e] = (TO)(scale * (double)src[e]);
+}
+
+template <typename TI>
+__global__ void axpy_kernel(const TI* __restrict__ x, double* __restrict__ y, long long n) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    y[e] += (double)x[e];
+}
+
+__global__ void absmax_kernel(const double* __restrict__ x, long long n, unsigned long long* __restrict__ out) {
+  double m = 0.0;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    m = fmax(m, fabs(x[e]));
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+  __shared__ double red[32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
+    m = fmax(m, red[0]);
+    if (m != m) m = DBL_MAX;  // NaN propagates as "huge"
+    atomicMax(out, (unsigned long long)__double_as_longlong(m));
+  }
+}
+
+// Rows: dst[tab[3k]] (+)= src[tab[3k+1]] (+ src[tab[3k+2]] if >= 0).
+template <typename TV>
+__global__ void gather_reduce_kernel(const int* __restrict__ tab, int n, const TV* __restrict__ src,
+                                     TV* __restrict__ dst, int nrhs, int accumulate) {
+  const long long total = (long long)n * nrhs;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(e / nrhs);
+    const int r = (int)(e - (long long)k * nrhs);
+    const int d = tab[3 * k], s1 = tab[3 * k + 1], s2 = tab[3 * k + 2];
+    TV v = s1 >= 0 ? src[(long long)s1 * nrhs + r] : TV(0);
+    if (s2 >= 0) v += src[(long long)s2 * nrhs + r];
+    TV* o = dst + (long long)d * nrhs + r;
+    *o = accumulate ? *o + v : v;
+  }
+}
+
+// FP64 residual of the collocation system on one leaf per CTA (rhs in chunks of RC):
+// refreshes u_ce = L_ce,ge u_ge, then r = g - A u on interior nodes (0 on exterior) and
+// the leaf fluxes v = D_ge,c u (Sec. 3.4).  Derivatives use the tensor structure.
+constexpr int RC = 4;
+
+__global__ void __launch_bounds__(256) leaf_residual_kernel(ResidualArgs a, const int* __restrict__ leaf_edges,
+                                                            const double* __restrict__ Lce, const int* __restrict__ ce,
+                                                            const double* __restrict__ ug, const double* __restrict__ g,
+                                                            double* __restrict__ uc, double* __restrict__ r_out,
+                                                            double* __restrict__ vflux, int nrhs) {
+  const int lf = blockIdx.x;
+  const int p = a.p, q = a.q, pp = p * p, nq = 4 * q, ne = 4 * (p - 1);
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double* sD = reinterpret_cast<double*>(smraw);
+  double* sD2 = sD + pp;
+  double* us = sD2 + pp;          // pp * RC
+  double* uxs = us + pp * RC;     // pp * RC
+  double* uys = uxs + pp * RC;    // pp * RC
+  double* ugs = uys + pp * RC;    // nq * RC
+  const int tid = threadIdx.x, bs = blockDim.x;
+  for (int e = tid; e < pp; e += bs) { sD[e] = a.D[e]; sD2[e] = a.D2[e]; }
+  const double sx = 2.0 / a.hxy[2 * lf], sy = 2.0 / a.hxy[2 * lf + 1];
+  const long long lbase = (long long)lf * pp * nrhs;
+  for (int r0 = 0; r0 < nrhs; r0 += RC) {
+    const int rc = min(RC, nrhs - r0);
+    __syncthreads();
+    for (int e = tid; e < nq * RC; e += bs) {
+      const int gq = e / RC, rr = e - (e / RC) * RC;
+      const int s = gq / q, k = gq - (gq / q) * q;
+      const int node = leaf_edges[4 * lf + s] * q + k;
+      ugs[e] = rr < rc ? ug[(long long)node * nrhs + r0 + rr] : 0.0;
+    }
+    for (int e = tid; e < pp * RC; e += bs) {
+      const int n = e / RC, rr = e - (e / RC) * RC;
+      us[e] = rr < rc ? uc[lbase + (long long)n * nrhs + r0 + rr] : 0.0;
+    }
+    __syncthreads();
+    for (int e = tid; e < ne * RC; e += bs) {
+      const int k = e / RC, rr = e - (e / RC) * RC;
+      double v = 0.0;
+      for (int gq = 0; gq < nq; ++gq) v += Lce[(long long)k * nq + gq] * ugs[gq * RC + rr];
+      const int n = ce[k];
+      us[n * RC + rr] = v;
+      if (rr < rc) uc[lbase + (long long)n * nrhs + r0 + rr] = v;
+    }
+    __syncthreads();
+    for (int e = tid; e < pp * RC; e += bs) {
+      const int n = e / RC, rr = e - (e / RC) * RC;
+      const int ix = n % p, iy = n / p;
+      double sxv = 0.0, syv = 0.0;
+      for (int k = 0; k < p; ++k) {
+        sxv += sD[ix * p + k] * us[(iy * p + k) * RC + rr];
+        syv += sD[iy * p + k] * us[(k * p + ix) * RC + rr];
+      }
+      uxs[e] = sx * sxv;
+      uys[e] = sy * syv;
+    }
+    __syncthreads();
+    for (int e = tid; e < pp * RC; e += bs) {
+      const int n = e / RC, rr = e - (e / RC) * RC;
+      if (rr >= rc) continue;
+      const int ix = n % p, iy = n / p;
+      double res = 0.0;
+      if (ix > 0 && ix < p - 1 && iy > 0 && iy < p - 1) {
+        double uxx = 0.0, uyy = 0.0, uxy = 0.0;
+        for (int k = 0; k < p; ++k) {
+          uxx += sD2[ix * p + k] * us[(iy * p + k) * RC + rr];
+          uyy += sD2[iy * p + k] * us[(k * p + ix) * RC + rr];
+          uxy += sD[iy * p + k] * uxs[(k * p + ix) * RC + rr];
+        }
+        uxx *= sx * sx;
+        uyy *= sy * sy;
+        uxy *= sy;
+        const long long cb = (long long)lf * pp + n;
+        const long long st = a.n_leaf * pp;
+        const double Au = -a.coeffs[cb] * uxx - 2.0 * a.coeffs[st + cb] * uxy - a.coeffs[2 * st + cb] * uyy +
+                          a.coeffs[3 * st + cb] * uxs[e] + a.coeffs[4 * st + cb] * uys[e] +
+                          a.coeffs[5 * st + cb] * us[e];
+        res = g[lbase + (long long)n * nrhs + r0 + rr] - Au;
+      }
+      r_out[lbase + (long long)n * nrhs + r0 + rr] = res;
+    }
+    for (int e = tid; e < nq * RC; e += bs) {
+      const int gq = e / RC, rr = e - (e / RC) * RC;
+      if (rr >= rc) continue;
+      const int s = gq / q, k = gq - (gq / q) * q;
+      double v = 0.0;
+      for (int t = 0; t < p; ++t) {
+        double d;
+        switch (s) {
+          case 0: d = uys[(0 * p + t) * RC + rr]; break;
+          case 1: d = uxs[(t * p + (p - 1)) * RC + rr]; break;
+          case 2: d = uys[((p - 1) * p + t) * RC + rr]; break;
+          default: d = uxs[(t * p + 0) * RC + rr]; break;
+        }
+        v += a.Lloc[k * p + t] * d;
+      }
+      vflux[((long long)lf * nq + gq) * nrhs + r0 + rr] = v;
+    }
+  }
+}
+
+// rho[e q + k] = -(v_a - v_b) on each interior edge; pairs = (edge, leaf_a, side_a,
+// leaf_b, side_b) with a the W/S leaf.
+__global__ void jump_residual_kernel(const int* __restrict__ pairs, int npairs, int q,
+                                     const double* __restrict__ vflux, double* __restrict__ rho, int nrhs) {
+  const int nq = 4 * q;
+  const long long total = (long long)npairs * q * nrhs;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int pi = (int)(e / ((long long)q * nrhs));
+    const int rem = (int)(e - (long long)pi * q * nrhs);
+    const int k = rem / nrhs, r = rem - (rem / nrhs) * nrhs;
+    const int* P = pairs + 5 * pi;
+    const double va = vflux[((long long)P[1] * nq + P[2] * q + k) * nrhs + r];
+    const double vb = vflux[((long long)P[3] * nq + P[4] * q + k) * nrhs + r];
+    rho[((long long)P[0] * q + k) * nrhs + r] = -(va - vb);
+  }
+}
+
+// Coefficient gradients (adjoint): grad_k[n] = sum_r gbar[n][r] * t_k(u)[n][r] at interior
+// nodes with t = (u_xx, 2 u_xy, u_yy, -u_x, -u_y, -u) (Sec. 3.2 operator), 0 on exterior.
+__global__ void __launch_bounds__(256) coeff_grad_kernel(ResidualArgs a, const double* __restrict__ uc,
+                                                         const double* __restrict__ gbar,
+                                                         double* __restrict__ grad, int nrhs) {
+  const int lf = blockIdx.x;
+  const int p = a.p, pp = p * p;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double* sD = reinterpret_cast<double*>(smraw);
+  double* sD2 = sD + pp;
+  double* us = sD2 + pp;        // pp
+  double* uxs = us + pp;        // pp
+  double* acc = uxs + pp;       // 6 * pp
+  const int tid = threadIdx.x, bs = blockDim.x;
+  for (int e = tid; e < pp; e += bs) { sD[e] = a.D[e]; sD2[e] = a.D2[e]; }
+  for (int e = tid; e < 6 * pp; e += bs) acc[e] = 0.0;
+  const double sx = 2.0 / a.hxy[2 * lf], sy = 2.0 / a.hxy[2 * lf + 1];
+  const long long lbase = (long long)lf * pp * nrhs;
+  for (int r = 0; r < nrhs; ++r) {
+    __syncthreads();
+    for (int n = tid; n < pp; n += bs) us[n] = uc[lbase + (long long)n * nrhs + r];
+    __syncthreads();
+    for (int n = tid; n < pp; n += bs) {
+      const int ix = n % p, iy = n / p;
+      double v = 0.0;
+      for (int k = 0; k < p; ++k) v += sD[ix * p + k] * us[iy * p + k];
+      uxs[n] = sx * v;
+    }
+    __syncthreads();
+    for (int n = tid; n < pp; n += bs) {
+      const int ix = n % p, iy = n / p;
+      if (!(ix > 0 && ix < p - 1 && iy > 0 && iy < p - 1)) continue;
+      double uy = 0.0, uxx = 0.0, uyy = 0.0, uxy = 0.0;
+      for (int k = 0; k < p; ++k) {
+        uy += sD[iy * p + k] * us[k * p + ix];
+        uxx += sD2[ix * p + k] * us[iy * p + k];
+        uyy += sD2[iy * p + k] * us[k * p + ix];
+        uxy += sD[iy * p + k] * uxs[k * p + ix];
+      }
+      const double lam = gbar[lbase + (long long)n * nrhs + r];
+      acc[0 * pp + n] += lam * sx * sx * uxx;
+      acc[1 * pp + n] += lam * 2.0 * sy * uxy;
+      acc[2 * pp + n] += lam * sy * sy * uyy;
+      acc[3 * pp + n] -= lam * uxs[n];
+      acc[4 * pp + n] -= lam * sy * uy;
+      acc[5 * pp + n] -= lam * us[n];
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < 6 * pp; e += bs) {
+    const int k = e / pp, n = e - (e / pp) * pp;
+    grad[((long long)k * a.n_leaf + lf) * pp + n] = acc[e];
+  }
+}
+
+inline int grid_for(long long n, int bs = 256, int cap = 8192) {
+  long long g = (n + bs - 1) / bs;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (int)g;
+}
+
+}  // namespace
+
+template <typename TA, typename TV>
+void launch_gemm_items(const GemmItem* items, int nitems, int maxM, int trans, const TA* A, const TV* B0,
+                       const TV* B1, TV* C, const TV* Add, const int* idx, int nrhs, double beta,
+                       cudaStream_t s) {
+  (void)maxM;
+  if (nitems <= 0) return;
+  const TV b = (TV)beta;
+  if (nrhs <= 4) {
+    if (trans) {
+      if (nrhs == 1) gemvT_items_kernel<TA, TV, 1><<<nitems, 256, 0, s>>>(items, A, B0, B1, C, Add, idx, nrhs, b);
+      else if (nrhs == 2) gemvT_items_kernel<TA, TV, 2><<<nitems, 256, 0, s>>>(items, A, B0, B1, C, Add, idx, nrhs, b);
+      else gemvT_items_kernel<TA, TV, 4><<<nitems, 256, 0, s>>>(items, A, B0, B1, C, Add, idx, nrhs, b);
+    } else {
+      if (nrhs == 1) gemv_items_kernel<TA, TV, 1><<<nitems, 256, 0, s>>>(items, A, B0, B1, C, Add, idx, nrhs, b);
+      else if (nrhs == 2) gemv_items_kernel<TA, TV, 2><<<nitems, 256, 0, s>>>(items, A, B0, B1, C, Add, idx, nrhs, b);
+      else gemv_items_kernel<TA, TV, 4><<<nitems, 256, 0, s>>>(items, A, B0, B1, C, Add, idx, nrhs, b);
+    }
+    return;
+  }
+  if (nrhs <= 16) {
+    dim3 grid(nitems, (nrhs + 15) / 16);
+    if (trans) gemm_items_kernel<TA, TV, 16, true><<<grid, 256, 0, s>>>(items, A, B0, B1, C, Add, idx, nrhs, b);
+    else gemm_items_kernel<TA, TV, 16, false><<<grid, 256, 0, s>>>(items, A, B0, B1, C, Add, idx, nrhs, b);
+  } else {
+    dim3 grid(nitems, (nrhs + 63) / 64);
+    if (trans) gemm_items_kernel<TA, TV, 64, true><<<grid, 256, 0, s>>>(items, A, B0, B1, C, Add, idx, nrhs, b);
+    else gemm_items_kernel<TA, TV, 64, false><<<grid, 256, 0, s>>>(items, A, B0, B1, C, Add, idx, nrhs, b);
+  }
+}
+
+template <typename TV>
+void launch_up_gather(const UpGather* g, int n, int maxrows, const TV* V, TV* Vout, TV* dbuf,
+                      const double* rho, const int* idx, int nrhs, cudaStream_t s) {
+  if (n <= 0) return;
+  dim3 grid(grid_for((long long)maxrows * nrhs, 256, 64), n);
+  up_gather_kernel<TV><<<grid, 256, 0, s>>>(g, V, Vout, dbuf, rho, idx, nrhs);
+}
+
+template <typename TV>
+void launch_down_scatter(const DownScatter* g, int n, int maxrows, TV* VB, const TV* dbar, double* rhobar,
+                         const int* idx, int nrhs, cudaStream_t s) {
+  if (n <= 0) return;
+  dim3 grid(grid_for((long long)maxrows * nrhs, 256, 64), n);
+  down_scatter_kernel<TV><<<grid, 256, 0, s>>>(g, VB, dbar, rhobar, idx, nrhs);
+}
+
+template <typename TV>
+void launch_scatter_rows(const double* src, const int* idx, int n, TV* dst, int nrhs, cudaStream_t s) {
+  if (n <= 0) return;
+  scatter_rows_kernel<TV><<<grid_for((long long)n * nrhs), 256, 0, s>>>(src, idx, n, dst, nrhs);
+}
+
+template <typename TI, typename TO>
+void launch_convert(const TI* src, TO* dst, long long n, double scale, cudaStream_t s) {
+  if (n <= 0) return;
+  convert_kernel<TI, TO><<<grid_for(n), 256, 0, s>>>(src, dst, n, scale);
+}
+
+template <typename TI>
+void launch_axpy_to_f64(const TI* x, double* y, long long n, cudaStream_t s) {
+  if (n <= 0) return;
+  axpy_kernel<TI><<<grid_for(n), 256, 0, s>>>(x, y, n);
+}
+
+void launch_absmax(const double* x, long long n, double* out, cudaStream_t s) {
+  absmax_kernel<<<grid_for(n, 256, 1024), 256, 0, s>>>(x, n, reinterpret_cast<unsigned long long*>(out));
+}
+
+template <typename TV>
+void launch_gather_reduce(const int* tab, int nnodes, const TV* src, TV* dst, int nrhs, int accumulate,
+                          cudaStream_t s) {
+  if (nnodes <= 0) return;
+  gather_reduce_kernel<TV><<<grid_for((long long)nnodes * nrhs), 256, 0, s>>>(tab, nnodes, src, dst, nrhs, accumulate);
+}
+
+void launch_leaf_residual_impl(const ResidualArgs& a, const int* leaf_edges, const double* Lce, const int* ce,
+                               const double* ug, const double* g, double* uc, double* r_out, double* vflux,
+                               int nrhs, cudaStream_t s) {
+  const int pp = a.p * a.p;
+  const size_t smem = (size_t)(2 * pp + 3 * pp * RC + 4 * a.q * RC) * sizeof(double);
+  static size_t configured = 0;
+  if (smem > 48 * 1024 && smem > configured) {
+    cudaFuncSetAttribute(leaf_residual_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    configured = smem;
+  }
+  leaf_residual_kernel<<<(unsigned)a.n_leaf, 256, smem, s>>>(a, leaf_edges, Lce, ce, ug, g, uc, r_out, vflux, nrhs);
+}
+
+void launch_jump_residual(const int* pairs, int npairs, int q, const double* vflux, double* rho_out, int nrhs,
+                          cudaStream_t s) {
+  if (npairs <= 0) return;
+  jump_residual_kernel<<<grid_for((long long)npairs * q * nrhs), 256, 0, s>>>(pairs, npairs, q, vflux, rho_out, nrhs);
+}
+
+void launch_coeff_grad(const ResidualArgs& a, const double* uc, const double* gbar, double* grad, int nrhs,
+                       cudaStream_t s) {
+  const int pp = a.p * a.p;
+  const size_t smem = (size_t)(10 * pp) * sizeof(double);
+  static size_t configured = 0;
+  if (smem > 48 * 1024 && smem > configured) {
+    cudaFuncSetAttribute(coeff_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    configured = smem;
+  }
+  coeff_grad_kernel<<<(unsigned)a.n_leaf, 256, smem, s>>>(a, uc, gbar, grad, nrhs);
+}
+
+template void launch_gemm_items<double, double>(const GemmItem*, int, int, int, const double*, const double*,
+                                                const double*, double*, const double*, const int*, int, double,
+                                                cudaStream_t);
+template void launch_gemm_items<float, float>(const GemmItem*, int, int, int, const float*, const float*,
+                                              const float*, float*, const float*, const int*, int, double,
+                                              cudaStream_t);
+template void launch_up_gather<double>(const UpGather*, int, int, const double*, double*, double*, const double*,
+                                       const int*, int, cudaStream_t);
+template void launch_up_gather<float>(const UpGather*, int, int, const float*, float*, float*, const double*,
+                                      const int*, int, cudaStream_t);
+template void launch_down_scatter<double>(const DownScatter*, int, int, double*, const double*, double*,
+                                          const int*, int, cudaStream_t);
+template void launch_scatter_rows<double>(const double*, const int*, int, double*, int, cudaStream_t);
+template void launch_scatter_rows<float>(const double*, const int*, int, float*, int, cudaStream_t);
+template void launch_convert<double, float>(const double*, float*, long long, double, cudaStream_t);
+template void launch_convert<float, double>(const float*, double*, long long, double, cudaStream_t);
+template void launch_convert<double, double>(const double*, double*, long long, double, cudaStream_t);
+template void launch_axpy_to_f64<float>(const float*, double*, long long, cudaStream_t);
+template void launch_axpy_to_f64<double>(const double*, double*, long long, cudaStream_t);
+template void launch_gather_reduce<double>(const int*, int, const double*, double*, int, int, cudaStream_t);
+
+}  // namespace hps

@@ -121,3 +121,13 @@ def random_directions(shape, n=10, seed_offset=500):
         v = rng(seed_offset + k).standard_normal(shape)
         out.append(v / np.linalg.norm(v))
     return out
+
+
+def smooth_directions(X, Y, n=10, seed_offset=700, fields=6):
+    """n seeded smooth directions of shape (fields, *X.shape): each field is an 8-mode
+    Fourier series at the given coordinates; each direction is scaled to unit 2-norm."""
+    out = []
+    for k in range(n):
+        v = np.array([FourierSeries(rng(seed_offset + 16 * k + j))(X, Y) for j in range(fields)])
+        out.append(v / np.linalg.norm(v))
+    return out

@@ -1,0 +1,144 @@
+"""CPU checks of the native library: it loads, exports every symbol of include/hps.h, and
+its host logic (tree, node numbering, node coordinates, argument checks) agrees with the
+oracle.  No kernel is launched here."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import spectral as sp
+from oracle import tree as tr
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1612_02736_gb300 import build, _native
+    build.build()
+    return _native.load()
+
+
+def header_symbols():
+    text = open(os.path.join(ROOT, "include", "hps.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(hps_[a-z_]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(lib):
+    from paper_1612_02736_gb300 import _native
+    syms = header_symbols()
+    assert len(syms) >= 12
+    for s in syms:
+        assert hasattr(lib, s), s
+        assert s in _native.SIGNATURES, s
+
+
+def _tree(lib, nx, ny, rect=(0.0, 0.0, 1.0, 1.0)):
+    out = C.c_void_p()
+    assert lib.hps_tree_uniform(*rect, nx, ny, C.byref(out)) == 0
+    return out
+
+
+@pytest.mark.parametrize("nx,ny,q", [(1, 1, 5), (2, 2, 7), (4, 4, 15), (8, 4, 9), (64, 64, 15)])
+def test_tree_counts_match_oracle(lib, nx, ny, q):
+    t = _tree(lib, nx, ny)
+    vals = [C.c_int() for _ in range(5)]
+    assert lib.hps_tree_info(t, q, *[C.byref(v) for v in vals]) == 0
+    n_leaves, n_boxes, n_levels, n_gauss, n_bdry = [v.value for v in vals]
+    assert n_leaves == nx * ny and n_boxes == 2 * nx * ny - 1
+    o = tr.uniform_tree(0, 0, 1, 1, nx, ny, q)
+    assert n_gauss == o.n_gauss and n_bdry == len(o.boundary)
+    lib.hps_tree_destroy(t)
+
+
+@pytest.mark.parametrize("nx,ny,p", [(2, 2, 8), (4, 2, 16)])
+def test_node_coordinates_match_oracle(lib, nx, ny, p):
+    q = p - 1
+    rect = (0.25, -0.5, 1.25, 0.5)
+    t = _tree(lib, nx, ny, rect)
+    o = tr.uniform_tree(*rect, nx, ny, q)
+
+    def get(which):
+        cnt = C.c_int64()
+        assert lib.hps_nodes(t, p, q, which, None, C.byref(cnt)) == 0
+        xy = np.zeros((cnt.value, 2))
+        assert lib.hps_nodes(t, p, q, which, xy.ctypes.data_as(C.c_void_p), C.byref(cnt)) == 0
+        return xy
+
+    cheb = get(0)
+    X, Y = [], []
+    for lf in range(o.n_leaves):
+        x0, y0, x1, y1 = o.leaf_rect(lf)
+        x, y = sp.leaf_cheb_points(x0, y0, x1 - x0, y1 - y0, p)
+        X.append(x)
+        Y.append(y)
+    assert np.max(np.abs(cheb[:, 0] - np.concatenate(X))) < 1e-14
+    assert np.max(np.abs(cheb[:, 1] - np.concatenate(Y))) < 1e-14
+    gp = o.gauss_points()
+    assert np.max(np.abs(get(2) - gp)) < 1e-14            # every Gaussian node by global id
+    assert np.max(np.abs(get(1) - gp[o.boundary])) < 1e-14  # boundary order
+    lib.hps_tree_destroy(t)
+
+
+def test_invalid_arguments_report_errors(lib):
+    out = C.c_void_p()
+    assert lib.hps_tree_uniform(0.0, 0.0, 1.0, 1.0, 0, 3, C.byref(out)) == 1
+    assert b"nx" in lib.hps_last_error()
+    assert lib.hps_tree_uniform(1.0, 0.0, 0.0, 1.0, 2, 2, C.byref(out)) == 1
+    t = _tree(lib, 2, 2)
+    h = C.c_void_p()
+    assert lib.hps_build(t, None, 8, None, None, None, C.byref(h)) == 1
+    assert lib.hps_build(t, C.c_void_p(16), 3, None, None, None, C.byref(h)) == 1
+    assert b"p must be" in lib.hps_last_error()
+    assert lib.hps_solve(None, None, None, 1, None, None) == 1
+    assert lib.hps_adjoint(None, None, 1, None, None, None, None, None) == 1
+    cnt = C.c_int64()
+    assert lib.hps_nodes(t, 8, 7, 9, None, C.byref(cnt)) == 1
+    assert lib.hps_destroy(None) == 0
+    lib.hps_tree_destroy(t)
+
+
+def test_python_package_fails_loudly_without_library(tmp_path, monkeypatch):
+    from paper_1612_02736_gb300 import _native
+    monkeypatch.setattr(_native, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(_native, "_lib", None)
+    with pytest.raises(ImportError):
+        _native.load()
+
+
+@pytest.mark.parametrize("nx,ny,p,prec", [(1, 1, 8, 0), (2, 1, 6, 0), (2, 2, 16, 1), (4, 4, 12, 1),
+                                          (8, 4, 16, 0), (64, 64, 16, 0), (16, 16, 20, 1)])
+def test_plan_descriptors_stay_in_bounds(lib, nx, ny, p, prec):
+    # Every kernel descriptor of the build, solve and adjoint plans is checked against the
+    # size of the buffer it addresses, on the host, before any launch.
+    from paper_1612_02736_gb300 import _native
+    t = _tree(lib, nx, ny)
+    opts = _native.hps_opts()
+    lib.hps_opts_default(C.byref(opts))
+    opts.precision = prec
+    assert lib.hps_plan_check(t, p, C.byref(opts)) == 0, lib.hps_last_error()
+    lib.hps_tree_destroy(t)
+
+
+@pytest.mark.parametrize("nx,ny", [(3, 2), (3, 3), (5, 7), (13, 1)])
+def test_plan_non_power_of_two_trees(lib, nx, ny):
+    # uneven trees: leaves at several depths, merges of one level with different sizes
+    t = _tree(lib, nx, ny)
+    assert lib.hps_plan_check(t, 8, None) == 0, lib.hps_last_error()
+    lib.hps_tree_destroy(t)
+
+
+def test_plan_rejects_bad_options(lib):
+    from paper_1612_02736_gb300 import _native
+    t = _tree(lib, 2, 2)
+    opts = _native.hps_opts()
+    lib.hps_opts_default(C.byref(opts))
+    opts.precision = 7
+    assert lib.hps_plan_check(t, 8, C.byref(opts)) == 1
+    opts.precision = 0
+    opts.q = 40
+    assert lib.hps_plan_check(t, 8, C.byref(opts)) == 1
+    lib.hps_tree_destroy(t)
