@@ -130,6 +130,25 @@ int hps_solve(hps_handle* h, const double* f_dev, const double* g_dev, int nrhs,
 int hps_solve_ext(hps_handle* h, const double* f_dev, const double* g_dev, const double* rho_dev,
                   int nrhs, double* u_dev, double* ug_dev, int* iters, void* stream);
 
+/* Solve without allocating device memory.  The paper has no counterpart: this serves
+ * callers that cannot let a solve allocate -- a host framework that has already reserved
+ * nearly all device memory for its own pool, or a time-stepping loop that must not pay
+ * for (or risk failing) an allocation once it runs.  Same arguments and result as
+ * hps_solve for an HPS_FP64 handle (STATE for other precisions); the handle itself still
+ * comes from hps_build, which does allocate.  The per-call work buffers -- the box
+ * flux/particular-solution pool, the merge difference vectors and the Gaussian-node
+ * solution, (n_box_rows + n_merge_rows + n_gauss) * nrhs doubles -- live in one fixed
+ * array of HPS_NOALLOC_SCRATCH_BYTES in device memory that the library image carries and
+ * every GPU that loads it keeps until the process exits; a call that would need more is
+ * rejected with INVALID_ARG and a message giving the size.  All calls share that array:
+ * calls whose work overlaps on the GPU (several streams or host threads) race on it and
+ * must be serialised.  The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call before any
+ * stream capture. */
+#define HPS_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+int hps_solve_noalloc(hps_handle* h, const double* f_dev, const double* g_dev, int nrhs, double* u_dev,
+                      void* stream);
+
 /* Adjoint of the solve (transposed Algorithm 2 sweeps).  dJdu_dev: [n_leaf][p*p][nrhs],
  * the gradient of a functional with respect to the output of hps_solve.  Outputs (each
  * may be NULL): dJdf_dev [n_boundary][nrhs], dJdg_dev [n_leaf][p*p][nrhs] (zero at

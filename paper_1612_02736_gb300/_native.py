@@ -45,6 +45,7 @@ SIGNATURES = {
     "hps_plan_check": (C.c_int, [P, C.c_int, C.POINTER(hps_opts)]),
     "hps_build": (C.c_int, [P, P, C.c_int, C.POINTER(hps_opts), C.POINTER(hps_allocator), P, C.POINTER(P)]),
     "hps_solve": (C.c_int, [P, P, P, C.c_int, P, P]),
+    "hps_solve_noalloc": (C.c_int, [P, P, P, C.c_int, P, P]),
     "hps_solve_ext": (C.c_int, [P, P, P, P, C.c_int, P, P, C.POINTER(C.c_int), P]),
     "hps_adjoint": (C.c_int, [P, P, C.c_int, P, P, P, P, P]),
     "hps_handle_info": (C.c_int, [P] + [C.POINTER(C.c_int)] * 5 + [C.POINTER(C.c_int64)]),

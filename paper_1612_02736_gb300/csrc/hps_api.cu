@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <unordered_map>
@@ -1378,3 +1379,85 @@ int hps_destroy(hps_handle* h) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// Solve without device allocation.
+//
+// hps_solve keeps its per-call work buffers (the per-box flux/particular-solution pool,
+// the merge difference vectors and the Gaussian-node solution vector) in the handle and
+// allocates them on the first call for a given nrhs.  Some callers cannot let a solve
+// allocate: a host framework that has already reserved nearly all device memory for its
+// own pool, or a time-stepping loop that must not pay for (or risk failing) an allocation
+// once it is running.  hps_solve_noalloc runs the same FP64 sweep kernels with those work
+// buffers carved from one fixed array in device memory that is part of the library image
+// (every GPU that loads the library holds it until the process exits).
+//
+// The array is shared by every call: calls whose work overlaps on the GPU (two streams,
+// or two host threads) race on it and give wrong results; serialise them.  Each call
+// clears what has to start at zero.  Host code cannot use the array's name as a device
+// address, so the first call on each device looks the address up (cudaGetSymbolAddress,
+// with that device current) and caches it; make that first call before any stream capture.
+namespace {
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[HPS_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kMaxDevices] = {nullptr};
+
+// Device address of the scratch array for the current device (looked up once per device).
+int noalloc_scratch(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(HPS_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  if (dev < 0 || dev >= kMaxDevices) return fail(HPS_ERR_INVALID_ARG, "device index out of range");
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(HPS_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return HPS_OK;
+}
+
+size_t align256(size_t n) { return (n + 255) & ~(size_t)255; }
+
+}  // namespace
+
+extern "C" int hps_solve_noalloc(hps_handle* h, const double* f, const double* g, int nrhs, double* u,
+                                 void* stream) {
+  if (!h) return fail(HPS_ERR_INVALID_ARG, "handle is NULL");
+  if (!f || !g || !u) return fail(HPS_ERR_INVALID_ARG, "f, g and u must be device pointers");
+  if (nrhs < 1) return fail(HPS_ERR_INVALID_ARG, "nrhs must be >= 1");
+  if (h->opts.precision != HPS_FP64) return fail(HPS_ERR_STATE, "hps_solve_noalloc needs an HPS_FP64 handle");
+  const size_t R = (size_t)nrhs;
+  const size_t bV = align256((size_t)h->v_rows * R * sizeof(double));
+  const size_t bD = align256((size_t)std::max(1, h->d_rows) * R * sizeof(double));
+  const size_t bG = align256((size_t)h->ns.n_gauss * R * sizeof(double));
+  const size_t need = bV + bD + bG;
+  if (need > (size_t)HPS_NOALLOC_SCRATCH_BYTES)
+    return fail(HPS_ERR_INVALID_ARG, "hps_solve_noalloc needs " + std::to_string(need) +
+                                         " bytes of scratch for this tree and nrhs, more than the fixed " +
+                                         std::to_string((size_t)HPS_NOALLOC_SCRATCH_BYTES) +
+                                         " (use fewer right-hand sides per call, or hps_solve)");
+  void* base = nullptr;
+  int rc = noalloc_scratch(&base);
+  if (rc != HPS_OK) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned char* b = (unsigned char*)base;
+  double* V = (double*)b;
+  double* d = (double*)(b + bV);
+  double* ug = (double*)(b + bV + bD);
+  try {
+    // the Gaussian-node vector is assembled by scatters, so it must start at zero; the
+    // other buffers are fully written before they are read
+    CK(cudaMemsetAsync(ug, 0, (size_t)h->ns.n_gauss * R * sizeof(double), s));
+    solve_pass<double, double>(h, h->ops64, f, g, nullptr, u, ug, V, d, nrhs, s);
+  } catch (const CudaError& e) {
+    return fail(e.code, e.msg);
+  }
+  return HPS_OK;
+}
