@@ -31,7 +31,6 @@ sys.path.insert(0, ROOT)
 
 NX = 64
 P = 16
-WORKLOAD = "varcoef-64x64-p16"
 METRIC = "build s & solve DOF/s at 1e-8 rel err: mixed vs FP64 GPU; grad/forward ratio"
 UNIT = "DOF/s"
 # FP64 FFMA peak of GB300: 152 SMs x 2 FP64 FMA/clock/SM x 2 flop x 2070 MHz (the 1.25
@@ -48,7 +47,16 @@ def parse():
     ap.add_argument("--nrhs", type=int, default=64)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    return ap.parse_args()
+    ap.add_argument("--nx", type=int, default=64, help="leaves per side (64 is the benchmark workload; "
+                    "smaller values are for profiling captures)")
+    args = ap.parse_args()
+    global NX
+    NX = args.nx
+    return args
+
+
+def workload():
+    return "varcoef-%dx%d-p%d" % (NX, NX, P)
 
 
 def dist_setup(args):
@@ -316,7 +324,7 @@ def run_gpu(args, rank, world, local):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64 (mixed path: f32 sweeps + f64 residual)",
         "data": "synthetic (seeded 8-mode Fourier-series coefficients and loads)",
-        "config": {"workload": WORKLOAD, "leaves": n_leaf, "p": P, "q": P - 1, "nrhs": nrhs,
+        "config": {"workload": workload(), "leaves": n_leaf, "p": P, "q": P - 1, "nrhs": nrhs,
                    "dof_per_rhs": n_leaf * P * P, "paper_N_per_rhs": NX * NX * (P - 1) ** 2 + 2 * NX * (P - 1) + 1,
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (operator store of 2.7 GB streamed per solve)"},
@@ -399,7 +407,7 @@ def run_reference(args, rank, world):
     return {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "leaves": NX * NX, "p": P, "q": P - 1, "nrhs": nrhs},
+            "config": {"workload": workload(), "leaves": NX * NX, "p": P, "q": P - 1, "nrhs": nrhs},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
                              "sample": "16x16 leaves of the same workload (sub-square [0,1/4]^2, leaf size 1/64, "
                                        "p=16, nrhs=%d) per step: FP64 build + solve + adjoint" % nrhs},
