@@ -119,7 +119,9 @@ int hps_build(const hps_tree* tree, const double* coeffs_dev, int p, const hps_o
  *   u_dev : [n_leaf][p*p][nrhs]       output: the solution at every leaf Chebyshev node
  * FP64 handles run the sweeps in FP64.  HPS_MIXED handles run them in FP32 and refine
  * against the FP64 residual of the collocation system (leaf equations and flux jumps)
- * until max|du| <= ir_tol max|u|, returning NO_CONVERGENCE after ir_max_iter steps. */
+ * until max|du| <= ir_tol max|u|, or until the observed contraction of two successive
+ * corrections (ratio r < 1/2) predicts the remaining error r max|du| below that; they
+ * return NO_CONVERGENCE after ir_max_iter steps. */
 int hps_solve(hps_handle* h, const double* f_dev, const double* g_dev, int nrhs, double* u_dev,
               void* stream);
 
@@ -136,8 +138,9 @@ int hps_solve_ext(hps_handle* h, const double* f_dev, const double* g_dev, const
  * for (or risk failing) an allocation once it runs.  Same arguments and result as
  * hps_solve for an HPS_FP64 handle (STATE for other precisions); the handle itself still
  * comes from hps_build, which does allocate.  The per-call work buffers -- the box
- * flux/particular-solution pool, the merge difference vectors and the Gaussian-node
- * solution, (n_box_rows + n_merge_rows + n_gauss) * nrhs doubles -- live in one fixed
+ * flux/particular-solution pool, the merge difference vectors, the Gaussian-node
+ * solution and the split-K partial sums, (box rows + merge rows + n_gauss + partial rows)
+ * * nrhs doubles -- live in one fixed
  * array of HPS_NOALLOC_SCRATCH_BYTES in device memory that the library image carries and
  * every GPU that loads it keeps until the process exits; a call that would need more is
  * rejected with INVALID_ARG and a message giving the size.  All calls share that array:

@@ -134,6 +134,14 @@ struct ItemSet {
   double elems = 0.0;  // operator entries streamed by one application
 };
 
+// A product step of one level: items writing final outputs, and split-K items writing
+// partial sums that a reduction adds into the outputs.
+struct Prod {
+  ItemSet direct, split;
+  SplitRed* red = nullptr;
+  int nred = 0;
+};
+
 struct Level {
   std::vector<int> boxes;  // merges at this height
   bool fp64 = true;        // precision of the elimination
@@ -150,14 +158,14 @@ struct Level {
   // solve
   UpGather* ug = nullptr;
   int ug_maxrows = 0;
-  ItemSet up, down;
+  Prod up, down;
   // adjoint
   int* wcopy_tab = nullptr;
   int n_wcopy = 0;
-  ItemSet adjS;
+  Prod adjS;
   int* reduce_tab = nullptr;
   int n_reduce = 0;
-  ItemSet adjM;
+  Prod adjM;
   DownScatter* ds = nullptr;
   int ds_maxrows = 0;
 };
@@ -170,8 +178,10 @@ struct Workspace {
   double* V64 = nullptr;
   double* d64 = nullptr;
   double* ug64 = nullptr;
+  double* P64 = nullptr;  // split-K partial sums
   // FP32 path
   float* V32 = nullptr;
+  float* P32 = nullptr;
   float* d32 = nullptr;
   float* ug32 = nullptr;
   float* g32 = nullptr;
@@ -199,7 +209,7 @@ struct hps_handle {
   hps_opts opts{};
   int p = 0, q = 0, m = 0, nq = 0, ne = 0, pp = 0, n_leaf = 0, n_bdry = 0;
   // tables
-  double *dD = nullptr, *dD2 = nullptr, *dLs = nullptr, *dLloc = nullptr, *dDceL = nullptr;
+  double *dD = nullptr, *dD2 = nullptr, *dLs = nullptr, *dDLs = nullptr, *dLloc = nullptr, *dDceL = nullptr;
   double* dhxy = nullptr;
   int* didx = nullptr;
   int* d_leaf_edges = nullptr;
@@ -219,6 +229,7 @@ struct hps_handle {
   // vector layouts (in rows)
   std::vector<int> vrow, drow, ubrow;
   int v_rows = 0, d_rows = 0, ub_rows = 0;
+  int p_rows = 0;  // split-K partial rows (max over the product steps)
   // plans
   std::vector<Level> levels;  // index = height - 1
   ItemSet leafup, leafdown, lce;
@@ -252,12 +263,61 @@ ItemSet upload_items(hps_handle* h, cudaStream_t s, const std::vector<GemmItem>&
 // Plan: index tables, operator offsets, vector layouts and the product items of every
 // step of the solve and the adjoint.  Built on the host, checked against the buffer
 // sizes (validate_plan), then uploaded.
+struct ProdHost {
+  std::vector<GemmItem> direct, split;
+  std::vector<SplitRed> red;
+};
+
+// Split-K: when a level has too few row blocks to fill the GPU (the large merges near the
+// root), each row block's K range is cut into nsplit pieces computed by separate CTAs
+// into a partial buffer and summed in fixed order by a reduction (deterministic).
+int split_prod(ProdHost& ph, bool trans) {
+  const int target = 2 * 152;
+  const int n = (int)ph.direct.size();
+  if (n == 0 || n >= target) return 0;
+  std::vector<GemmItem> keep;
+  int prow = 0;
+  for (const GemmItem& it : ph.direct) {
+    int ns = std::min((target + n - 1) / n, it.K / 128);
+    if (it.kseg != it.K || ns < 2) {
+      keep.push_back(it);
+      continue;
+    }
+    const int kc = (it.K + ns - 1) / ns;
+    ns = (it.K + kc - 1) / kc;
+    SplitRed sr;
+    sr.M = it.M;
+    sr.nsplit = ns;
+    sr.p_row = prow;
+    sr.c_row = it.c_row;
+    sr.c_idx = it.c_idx;
+    sr.add_row = it.add_row;
+    for (int j = 0; j < ns; ++j) {
+      const int k0 = j * kc;
+      GemmItem s = it;
+      s.K = std::min(kc, it.K - k0);
+      s.kseg = s.K;
+      s.a_off = trans ? it.a_off + (long long)k0 * it.lda : it.a_off + k0;
+      if (it.b0_idx >= 0) s.b0_idx = it.b0_idx + k0;
+      else s.b0_row = it.b0_row + k0;
+      s.c_row = prow + j * it.M;
+      s.c_idx = -1;
+      s.add_row = -1;
+      ph.split.push_back(s);
+    }
+    prow += ns * it.M;
+    ph.red.push_back(sr);
+  }
+  ph.direct.swap(keep);
+  return prow;
+}
+
 struct LevelHost {
   std::vector<GJDesc> gj;
   std::vector<MergeDesc> md;
   std::vector<long long> tl, bl, tr, br;
   std::vector<UpGather> ug;
-  std::vector<GemmItem> up, down, adjS, adjM;
+  ProdHost up, down, adjS, adjM;
   std::vector<int> wcopy, reduce;
   std::vector<DownScatter> ds;
 };
@@ -447,16 +507,17 @@ void make_plan(hps_handle* h, HostPlan& hp) {
       pd.ds.push_back(ds);
       lv.ds_maxrows = std::max(lv.ds_maxrows, k3 + n1 + n2);
       // up: [w; h] += [X; CX] d
-      add_product(pd.up, h->mo[b], k3, R, k3, k3, h->drow[b], -1, 0, -1, h->vrow[b], -1, -1, false);
+      add_product(pd.up.direct, h->mo[b], k3, R, k3, k3, h->drow[b], -1, 0, -1, h->vrow[b], -1, -1, false);
       // down: u[J3] = S u[ge] + w
-      add_product(pd.down, h->so[b], k12, k3, k12, k12, 0, h->off_ge[b], 0, -1, 0, h->off_J3[b], h->vrow[b], false);
+      add_product(pd.down.direct, h->so[b], k12, k3, k12, k12, 0, h->off_ge[b], 0, -1, 0, h->off_J3[b], h->vrow[b],
+                  false);
       // adjoint: wbar copy, S^T ubar[J3] -> UB, reduce into ubar[ge]
       for (int k = 0; k < k3; ++k) {
         pd.wcopy.push_back(h->vrow[b] + k);
         pd.wcopy.push_back(J3[k]);
         pd.wcopy.push_back(-1);
       }
-      add_product(pd.adjS, h->so[b], k12, k12, k3, k3, 0, h->off_J3[b], 0, -1, h->ubrow[b], -1, -1, true);
+      add_product(pd.adjS.direct, h->so[b], k12, k12, k3, k3, 0, h->off_J3[b], 0, -1, h->ubrow[b], -1, -1, true);
       for (int k = 0; k < k12; ++k) {
         const int g = ge[k];
         auto it = red.find(g);
@@ -468,10 +529,14 @@ void make_plan(hps_handle* h, HostPlan& hp) {
         }
       }
       // adjoint: dbar = [X; CX]^T [wbar; hbar]
-      add_product(pd.adjM, h->mo[b], k3, k3, R, R, h->vrow[b], -1, 0, -1, h->drow[b], -1, -1, true);
+      add_product(pd.adjM.direct, h->mo[b], k3, k3, R, R, h->vrow[b], -1, 0, -1, h->drow[b], -1, -1, true);
     }
     lv.work_elems = woff;
     lv.perm_elems = poff;
+    h->p_rows = std::max(h->p_rows, split_prod(pd.up, false));
+    h->p_rows = std::max(h->p_rows, split_prod(pd.down, false));
+    h->p_rows = std::max(h->p_rows, split_prod(pd.adjS, true));
+    h->p_rows = std::max(h->p_rows, split_prod(pd.adjM, true));
     for (int g : red_order) {
       pd.reduce.push_back(g);
       pd.reduce.push_back(red[g].first);
@@ -527,6 +592,15 @@ void make_plan(hps_handle* h, HostPlan& hp) {
   h->npairs = (int)pairs.size() / 5;
 }
 
+Prod upload_prod(hps_handle* h, cudaStream_t s, const ProdHost& ph) {
+  Prod pr;
+  pr.direct = upload_items(h, s, ph.direct);
+  pr.split = upload_items(h, s, ph.split);
+  pr.nred = (int)ph.red.size();
+  pr.red = ph.red.empty() ? nullptr : upload(h->al, s, ph.red, h->owned);
+  return pr;
+}
+
 void upload_plan(hps_handle* h, const HostPlan& hp, cudaStream_t s) {
   h->didx = upload(h->al, s, hp.idx, h->owned);
   for (size_t L = 0; L < hp.lv.size(); ++L) {
@@ -539,10 +613,10 @@ void upload_plan(hps_handle* h, const HostPlan& hp, cudaStream_t s) {
     lv.off_tr = upload(h->al, s, pd.tr, h->owned);
     lv.off_br = upload(h->al, s, pd.br, h->owned);
     lv.ug = upload(h->al, s, pd.ug, h->owned);
-    lv.up = upload_items(h, s, pd.up);
-    lv.down = upload_items(h, s, pd.down);
-    lv.adjS = upload_items(h, s, pd.adjS);
-    lv.adjM = upload_items(h, s, pd.adjM);
+    lv.up = upload_prod(h, s, pd.up);
+    lv.down = upload_prod(h, s, pd.down);
+    lv.adjS = upload_prod(h, s, pd.adjS);
+    lv.adjM = upload_prod(h, s, pd.adjM);
     lv.wcopy_tab = upload(h->al, s, pd.wcopy, h->owned);
     lv.n_wcopy = (int)pd.wcopy.size() / 3;
     lv.reduce_tab = upload(h->al, s, pd.reduce, h->owned);
@@ -606,6 +680,18 @@ void check_items(PlanCheck& pc, const std::vector<int>& idx, const std::vector<G
   }
 }
 
+void check_prod(PlanCheck& pc, const std::vector<int>& idx, const ProdHost& ph, bool trans, long long ops,
+                long long b0rows, long long crows, long long addrows, long long prows, const char* what) {
+  check_items(pc, idx, ph.direct, trans, ops, b0rows, 0, crows, addrows, what);
+  check_items(pc, idx, ph.split, trans, ops, b0rows, 0, prows, 0, what);
+  for (const SplitRed& r : ph.red) {
+    if (r.M < 1 || r.nsplit < 1 || r.p_row < 0 || (long long)r.p_row + (long long)r.nsplit * r.M > prows)
+      pc.fail(std::string(what) + ": split partials out of range");
+    check_rows(pc, idx, r.c_row, r.c_idx, r.M, crows, what);
+    if (r.add_row >= 0 && (long long)r.add_row + r.M > addrows) pc.fail(std::string(what) + ": split addend out of range");
+  }
+}
+
 void check_tab(PlanCheck& pc, const std::vector<int>& tab, long long drows, long long srows, const char* what) {
   if (tab.size() % 3) pc.fail(std::string(what) + ": bad table");
   for (size_t k = 0; k + 2 < tab.size(); k += 3) {
@@ -638,10 +724,10 @@ std::string validate_plan(const hps_handle* h, const HostPlan& hp) {
   for (size_t L = 0; L < hp.lv.size(); ++L) {
     const LevelHost& pd = hp.lv[L];
     const Level& lv = h->levels[L];
-    check_items(pc, idx, pd.up, false, ops, D, 0, V, 0, "merge up");
-    check_items(pc, idx, pd.down, false, ops, G, 0, G, V, "merge down");
-    check_items(pc, idx, pd.adjS, true, ops, G, 0, UB, 0, "adjoint S merge");
-    check_items(pc, idx, pd.adjM, true, ops, V, 0, D, 0, "adjoint X merge");
+    check_prod(pc, idx, pd.up, false, ops, D, V, 0, h->p_rows, "merge up");
+    check_prod(pc, idx, pd.down, false, ops, G, G, V, h->p_rows, "merge down");
+    check_prod(pc, idx, pd.adjS, true, ops, G, UB, 0, h->p_rows, "adjoint S merge");
+    check_prod(pc, idx, pd.adjM, true, ops, V, D, 0, h->p_rows, "adjoint X merge");
     check_tab(pc, pd.wcopy, V, G, "adjoint w copy");
     check_tab(pc, pd.reduce, G, UB, "adjoint reduce");
     for (size_t i = 0; i < pd.ug.size(); ++i) {
@@ -694,16 +780,19 @@ long long tstore_elems(const hps_handle* h) {
   return tsz;
 }
 
-int choose_nb(int K, size_t elem) {
+// Panel width: 16 for batches of many matrices; 8 for a level of few large matrices, whose
+// panels run on one CTA each and whose per-panel work grows with nb; capped so the panel
+// fits in shared memory.
+int choose_nb(int K, size_t elem, int nmat) {
   int nb = (int)((200 * 1024) / ((size_t)std::max(K, 1) * (elem + 4)));
-  return std::max(1, std::min(16, nb));
+  return std::max(1, std::min(nmat < 64 ? 8 : 16, nb));
 }
 
 // rk: (R, K) of every matrix of the batch, for the flop counts of the timing records.
 template <typename T>
 void run_gj(const GJDesc* gj, int nmat, int maxR, int maxK, T* work, int* perm, T* pinv, T* prow,
             int* status, const std::vector<std::pair<int, int>>& rk, cudaStream_t s) {
-  const int nb = choose_nb(maxK, sizeof(T));
+  const int nb = choose_nb(maxK, sizeof(T), nmat);
   const std::string sf = tsuf<T>();
   TIMED(("gj_init_" + sf).c_str(), 0, 0, launch_gj_init<T>(gj, nmat, perm, s));
   CKL();
@@ -760,7 +849,7 @@ void build_stage(hps_handle* h, const double* coeffs, cudaStream_t s) {
       gd[i].perm_off = i * m;
       gd[i].box = 0;
     }
-    LeafTablesDev tb{h->dD, h->dD2, h->dLs, h->dLloc, h->dDceL, h->didx + h->off_ci};
+    LeafTablesDev tb{h->dD, h->dD2, h->dLs, h->dDLs, h->dLloc, h->dDceL, h->didx + h->off_ci};
     for (int l0 = 0; l0 < h->n_leaf; l0 += chunk) {
       const int n = std::min(chunk, h->n_leaf - l0);
       for (int i = 0; i < n; ++i) gd[i].box = h->tree.leaves[l0 + i];
@@ -847,10 +936,12 @@ void ensure_ws(hps_handle* h, int nrhs, cudaStream_t s) {
   const long long ng = (long long)h->ns.n_gauss * R;
   const bool mixed = h->opts.precision == HPS_MIXED;
   w.V64 = (double*)get((size_t)h->v_rows * R * sizeof(double));
+  w.P64 = (double*)get((size_t)std::max(1, h->p_rows) * R * sizeof(double));
   w.d64 = (double*)get((size_t)std::max(1, h->d_rows) * R * sizeof(double));
   w.ug64 = (double*)get((size_t)ng * sizeof(double));
   if (mixed) {
     w.V32 = (float*)get((size_t)h->v_rows * R * sizeof(float));
+    w.P32 = (float*)get((size_t)std::max(1, h->p_rows) * R * sizeof(float));
     w.d32 = (float*)get((size_t)std::max(1, h->d_rows) * R * sizeof(float));
     w.ug32 = (float*)get((size_t)ng * sizeof(float));
     w.g32 = (float*)get((size_t)nuc * sizeof(float));
@@ -872,7 +963,7 @@ void ensure_ws(hps_handle* h, int nrhs, cudaStream_t s) {
 //   FP64 [n_gauss][nrhs], outputs uc [n_leaf][pp][nrhs] TV and ug [n_gauss][nrhs] TV.
 template <typename TA, typename TV>
 void solve_pass(hps_handle* h, const TA* ops, const double* f, const TV* g, const double* rho, TV* uc, TV* ug,
-                TV* V, TV* dbuf, int nrhs, cudaStream_t s) {
+                TV* V, TV* dbuf, TV* P, int nrhs, cudaStream_t s) {
   const int H = h->tree.height;
   const int* idx = h->didx;
   const std::string sf = tsuf<TA>();
@@ -881,18 +972,25 @@ void solve_pass(hps_handle* h, const TA* ops, const double* f, const TV* g, cons
     TIMED(("gemm_" + std::string(step) + "_" + sf).c_str(), 2.0 * is.elems * nrhs, is.elems * sizeof(TA),
           launch_gemm_items<TA, TV>(is.dev, is.n, ROWBLK, 0, ops, B0, B1, C, Add, idx, nrhs, beta, s));
   };
+  auto gemmp = [&](const char* step, const Prod& pr, const TV* B0, TV* C, const TV* Add, double beta) {
+    gemm(step, pr.direct, B0, nullptr, C, Add, beta);
+    if (pr.nred > 0) {
+      gemm(step, pr.split, B0, nullptr, P, nullptr, 0.0);
+      TIMED("split_reduce", 0, 0, launch_split_reduce<TV>(pr.red, pr.nred, P, C, Add, idx, nrhs, beta, s));
+    }
+  };
   // upward pass: leaves, then merges bottom-up
   gemm("leaf_up", h->leafup, g, nullptr, V, nullptr, 0.0);
   for (int L = 0; L < H; ++L) {
     Level& lv = h->levels[L];
     TIMED("up_gather", 0, 0, launch_up_gather<TV>(lv.ug, (int)lv.boxes.size(), lv.ug_maxrows, V, V, dbuf, rho, idx, nrhs, s));
-    gemm("merge_up", lv.up, dbuf, nullptr, V, nullptr, 1.0);
+    gemmp("merge_up", lv.up, dbuf, V, nullptr, 1.0);
   }
   // root boundary data, then the downward pass
   if (f) TIMED("scatter_rows", 0, 0, launch_scatter_rows<TV>(f, idx + h->off_bnd, h->n_bdry, ug, nrhs, s));
   for (int L = H - 1; L >= 0; --L) {
     Level& lv = h->levels[L];
-    gemm("merge_down", lv.down, ug, nullptr, ug, V, 0.0);
+    gemmp("merge_down", lv.down, ug, ug, V, 0.0);
   }
   gemm("leaf_down", h->leafdown, g, ug, uc, nullptr, 0.0);
   gemm("leaf_ext", h->lce, ug, nullptr, uc, nullptr, 0.0);
@@ -915,7 +1013,7 @@ int solve_impl(hps_handle* h, const double* f, const double* g, const double* rh
   if (iters) *iters = 0;
   if (h->opts.precision == HPS_FP64) {
     CK(cudaMemsetAsync(w.ug64, 0, ng * sizeof(double), s));
-    solve_pass<double, double>(h, h->ops64, f, g, rho, u, w.ug64, w.V64, w.d64, nrhs, s);
+    solve_pass<double, double>(h, h->ops64, f, g, rho, u, w.ug64, w.V64, w.d64, w.P64, nrhs, s);
     if (ug_out) CK(cudaMemcpyAsync(ug_out, w.ug64, ng * sizeof(double), cudaMemcpyDeviceToDevice, s));
     return HPS_OK;
   }
@@ -1127,6 +1225,7 @@ int hps_build(const hps_tree* tree, const double* coeffs, int p, const hps_opts*
     h->dD = upload(h->al, s, h->rt.D, h->owned);
     h->dD2 = upload(h->al, s, h->rt.D2, h->owned);
     h->dLs = upload(h->al, s, h->rt.Ls, h->owned);
+    h->dDLs = upload(h->al, s, h->rt.DLs, h->owned);
     h->dLloc = upload(h->al, s, h->rt.Lloc, h->owned);
     h->dDceL = upload(h->al, s, h->rt.DceL, h->owned);
     std::vector<double> hxy(2 * (size_t)h->n_leaf);
@@ -1195,7 +1294,7 @@ int hps_solve_ext(hps_handle* h, const double* f, const double* g, const double*
     // 1. low-precision solve of the original system
     TIMED("convert", 0, nuc * 12.0, launch_convert<double, float>(g, w.g32, nuc, 1.0, s));
     CK(cudaMemsetAsync(w.ug32, 0, ng * sizeof(float), s));
-    solve_pass<float, float>(h, h->ops32, f, w.g32, rho, w.uc32, w.ug32, w.V32, w.d32, nrhs, s);
+    solve_pass<float, float>(h, h->ops32, f, w.g32, rho, w.uc32, w.ug32, w.V32, w.d32, w.P32, nrhs, s);
     TIMED("convert", 0, nuc * 12.0, launch_convert<float, double>(w.uc32, u, nuc, 1.0, s));
     TIMED("convert", 0, ng * 12.0, launch_convert<float, double>(w.ug32, w.ug64, ng, 1.0, s));
     TIMED("scatter_rows", 0, 0, launch_scatter_rows<double>(f, h->didx + h->off_bnd, h->n_bdry, w.ug64, nrhs, s));  // exact boundary data
@@ -1216,6 +1315,7 @@ int hps_solve_ext(hps_handle* h, const double* f, const double* g, const double*
                              (5.0 * h->p * h->p * h->p + (double)h->ne * h->nq + (double)h->nq * h->p + 12.0 * h->m);
     int it = 0;
     bool conv = false;
+    double prev = -1.0;
     for (; it < h->opts.ir_max_iter; ++it) {
       // 2. FP64 residual: leaf equations and flux jumps (refreshes u_ce = L u_ge)
       TIMED("leaf_residual_f64", res_flops, nuc * 32.0,
@@ -1228,7 +1328,7 @@ int hps_solve_ext(hps_handle* h, const double* f, const double* g, const double*
       // 3. correction solve in FP32 with the jump residual as flux-continuity data
       TIMED("convert", 0, nuc * 12.0, launch_convert<double, float>(w.r64, w.g32, nuc, 1.0, s));
       CK(cudaMemsetAsync(w.ug32, 0, ng * sizeof(float), s));
-      solve_pass<float, float>(h, h->ops32, nullptr, w.g32, w.rho64, w.uc32, w.ug32, w.V32, w.d32, nrhs, s);
+      solve_pass<float, float>(h, h->ops32, nullptr, w.g32, w.rho64, w.uc32, w.ug32, w.V32, w.d32, w.P32, nrhs, s);
       // 4. update and convergence test
       TIMED("axpy", 0, nuc * 20.0, launch_axpy_to_f64<float>(w.uc32, u, nuc, s));
       TIMED("axpy", 0, ng * 20.0, launch_axpy_to_f64<float>(w.ug32, w.ug64, ng, s));
@@ -1241,16 +1341,22 @@ int hps_solve_ext(hps_handle* h, const double* f, const double* g, const double*
       CK(cudaMemcpyAsync(sc, w.scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
       if (!(sc[0] == sc[0]) || !(sc[1] == sc[1])) break;
-      if (sc[0] <= h->opts.ir_tol * sc[1]) {
+      // Converged when this correction is below tolerance, or when the observed contraction
+      // rho = |du_k| / |du_(k-1)| (< 1/2) predicts the error left after it, rho |du_k|, is.
+      const double tolu = h->opts.ir_tol * sc[1];
+      const bool small = sc[0] <= tolu;
+      const bool predicted = prev > 0.0 && sc[0] < 0.5 * prev && (sc[0] / prev) * sc[0] <= tolu;
+      prev = sc[0];
+      if (small || predicted) {
         conv = true;
         ++it;
         break;
       }
     }
-    // final exterior refresh u_ce = L u_ge in FP64 (the residual kernel writes it)
-    TIMED("leaf_residual_f64", res_flops, nuc * 32.0,
-          launch_leaf_residual_impl(ra, h->d_leaf_edges, Lce, h->didx + h->off_ce, w.ug64, g, u, w.r64, w.vflux,
-                                    nrhs, s));
+    // final exterior refresh u_ce = L_ce,ge u_ge in FP64
+    TIMED("exterior_refresh", 2.0 * h->n_leaf * nrhs * h->ne * h->nq, 0,
+          launch_exterior_refresh(h->n_leaf, h->p, h->q, h->d_leaf_edges, Lce, h->didx + h->off_ce, w.ug64, u,
+                                  nrhs, s));
     CKL();
     if (ug_out) CK(cudaMemcpyAsync(ug_out, w.ug64, ng * sizeof(double), cudaMemcpyDeviceToDevice, s));
     if (iters) *iters = it;
@@ -1296,6 +1402,14 @@ int hps_adjoint(hps_handle* h, const double* ubar_in, int nrhs, const double* u,
       TIMED(("gemmT_" + std::string(step) + "_f64").c_str(), 2.0 * is.elems * nrhs, is.elems * 8.0,
             launch_gemm_items<double, double>(is.dev, is.n, ROWBLK, 1, ops, B0, nullptr, C, nullptr, idx, nrhs, beta, s));
     };
+    auto gemmTp = [&](const char* step, const Prod& pr, const double* B0, double* C, double beta) {
+      gemmT(step, pr.direct, B0, C, beta);
+      if (pr.nred > 0) {
+        gemmT(step, pr.split, B0, w.P64, 0.0);
+        TIMED("split_reduce", 0, 0,
+              launch_split_reduce<double>(pr.red, pr.nred, w.P64, C, nullptr, idx, nrhs, beta, s));
+      }
+    };
     // 1. leaf-down transposed: gbar_ci = F^T ubar_ci ; LB = S_ci^T ubar_ci + Lce^T ubar_ce
     gemmT("leaf_F", h->adj_leafF, ubar_in, gb, 0.0);
     gemmT("leaf_S", h->adj_leafS, ubar_in, w.LB, 0.0);
@@ -1308,7 +1422,7 @@ int hps_adjoint(hps_handle* h, const double* ubar_in, int nrhs, const double* u,
     for (int L = 0; L < H; ++L) {
       Level& lv = h->levels[L];
       TIMED("gather_reduce", 0, 0, launch_gather_reduce<double>(lv.wcopy_tab, lv.n_wcopy, ub, VB, nrhs, 0, s));
-      gemmT("merge_S", lv.adjS, ub, w.UB, 0.0);
+      gemmTp("merge_S", lv.adjS, ub, w.UB, 0.0);
       TIMED("gather_reduce", 0, 0, launch_gather_reduce<double>(lv.reduce_tab, lv.n_reduce, w.UB, ub, nrhs, 1, s));
     }
     // 3. boundary data
@@ -1316,7 +1430,7 @@ int hps_adjoint(hps_handle* h, const double* ubar_in, int nrhs, const double* u,
     // 4. merge-up transposed, top-down
     for (int L = H - 1; L >= 0; --L) {
       Level& lv = h->levels[L];
-      gemmT("merge_X", lv.adjM, VB, w.d64, 0.0);
+      gemmTp("merge_X", lv.adjM, VB, w.d64, 0.0);
       TIMED("down_scatter", 0, 0, launch_down_scatter<double>(lv.ds, (int)lv.boxes.size(), lv.ds_maxrows, VB, w.d64, nullptr, idx, nrhs, s));
     }
     // 5. leaf-up transposed: gbar_ci += H^T hbar
@@ -1437,7 +1551,8 @@ extern "C" int hps_solve_noalloc(hps_handle* h, const double* f, const double* g
   const size_t bV = align256((size_t)h->v_rows * R * sizeof(double));
   const size_t bD = align256((size_t)std::max(1, h->d_rows) * R * sizeof(double));
   const size_t bG = align256((size_t)h->ns.n_gauss * R * sizeof(double));
-  const size_t need = bV + bD + bG;
+  const size_t bP = align256((size_t)std::max(1, h->p_rows) * R * sizeof(double));
+  const size_t need = bV + bD + bG + bP;
   if (need > (size_t)HPS_NOALLOC_SCRATCH_BYTES)
     return fail(HPS_ERR_INVALID_ARG, "hps_solve_noalloc needs " + std::to_string(need) +
                                          " bytes of scratch for this tree and nrhs, more than the fixed " +
@@ -1451,11 +1566,12 @@ extern "C" int hps_solve_noalloc(hps_handle* h, const double* f, const double* g
   double* V = (double*)b;
   double* d = (double*)(b + bV);
   double* ug = (double*)(b + bV + bD);
+  double* Pp = (double*)(b + bV + bD + bG);
   try {
     // the Gaussian-node vector is assembled by scatters, so it must start at zero; the
     // other buffers are fully written before they are read
     CK(cudaMemsetAsync(ug, 0, (size_t)h->ns.n_gauss * R * sizeof(double), s));
-    solve_pass<double, double>(h, h->ops64, f, g, nullptr, u, ug, V, d, nrhs, s);
+    solve_pass<double, double>(h, h->ops64, f, g, nullptr, u, ug, V, d, Pp, nrhs, s);
   } catch (const CudaError& e) {
     return fail(e.code, e.msg);
   }

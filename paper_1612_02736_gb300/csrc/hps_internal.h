@@ -57,6 +57,7 @@ struct RefTables {
   std::vector<double> D2;              // p x p, D*D
   std::vector<double> Lg2c;            // p x q: Gauss data of one side -> its p Chebyshev points
   std::vector<double> Ls;              // p x q: Lg2c with corner rows halved (side block of L_ce,ge)
+  std::vector<double> DLs;             // p x q: D * Ls (differentiation along a side, then Ls)
   std::vector<double> Lloc;            // q x p: Chebyshev -> Gauss on one side
   std::vector<double> DceL;            // 4q x 4q: D_ge,ce L_ce,ge on [-1,1]^2 (row s scaled later)
   std::vector<double> Lce;             // ne x 4q: L_ce,ge, rows = exterior nodes ascending
@@ -104,6 +105,7 @@ struct LeafTablesDev {
   const double* D;      // p x p
   const double* D2;     // p x p
   const double* Ls;     // p x q
+  const double* DLs;    // p x q: D Ls
   const double* Lloc;   // q x p
   const double* DceL;   // 4q x 4q
   const int* ci;        // m
@@ -166,6 +168,20 @@ template <typename TA, typename TV>
 void launch_gemm_items(const GemmItem* items, int nitems, int maxM, int trans, const TA* A,
                        const TV* B0, const TV* B1, TV* C, const TV* Add, const int* idx,
                        int nrhs, double beta, cudaStream_t s);
+
+// Split-K partial products: rows [0, M) of one output block were computed in nsplit K
+// ranges into the partial buffer P (rows p_row + j * M + i); the reduction writes
+//   C[map(i)][r] = beta * C[map(i)][r] + sum_j P[p_row + j * M + i][r] (+ Add[add_row + i][r]).
+struct SplitRed {
+  int M, nsplit, p_row;
+  int c_row, c_idx, add_row;
+};
+template <typename TV>
+void launch_split_reduce(const SplitRed* d, int n, const TV* P, TV* C, const TV* Add, const int* idx,
+                         int nrhs, double beta, cudaStream_t s);
+// u_ce = L_ce,ge u_ge on every leaf (FP64), rows of uc at the exterior nodes.
+void launch_exterior_refresh(int n_leaf, int p, int q, const int* leaf_edges, const double* Lce,
+                             const int* ce, const double* ug, double* uc, int nrhs, cudaStream_t s);
 
 // Up-sweep gather for a level of merges: d = h_b[pos3b] - h_a[pos3a] (+ rho[J3]) and
 // prefill V_tau = [0 (k3 rows) ; h_a[pos1a] ; h_b[pos2b]].

@@ -7,8 +7,14 @@
 // follows from the 1D tables (D1 = I (x) Dx and D2 = Dy (x) I, x fastest) in O(1).
 // A_ci,ce L_ce,ge uses the side structure of L_ce,ge: a Gauss node on side s only sees the
 // p Chebyshev nodes of side s (corner rows carry weight one half, the corner average of
-// Eq. alpine2p5), so each entry is a p-term sum.  The bottom rows are reference-element
-// constants scaled by 2/h of the side's derivative direction.
+// Eq. alpine2p5), with the side block Ls.  For an interior row only two terms of A reach a
+// side: the cross term -2 c12 Dx Dy (through every node of the side) and the 1D operator
+// along the row's own line (through the one node on that line).  With the table
+// DLs = D Ls the p-term sum collapses to two products, e.g. on the south side
+//   sum_t A[i][(t,0)] Ls[t][a] = -2 c12 sx sy D[iy][0] DLs[ix][a]
+//                                + (-c22 sy^2 D2[iy][0] + c2 sy D[iy][0]) Ls[ix][a].
+// The bottom rows are reference-element constants scaled by 2/h of the side's
+// derivative direction.
 #include "hps_internal.h"
 
 namespace hps {
@@ -30,14 +36,15 @@ __global__ void __launch_bounds__(256) leaf_assemble_kernel(
   double* sD2 = sD + pp;                           // pp
   double* sLs = sD2 + pp;                          // p * q
   double* sLl = sLs + p * q;                       // q * p
-  int* sci = reinterpret_cast<int*>(sLl + q * p);  // m
+  double* sDL = sLl + q * p;                       // p * q
+  int* sci = reinterpret_cast<int*>(sDL + p * q);  // m
   const int tid = threadIdx.x, bs = blockDim.x;
   for (int e = tid; e < 6 * pp; e += bs) {
     const int k = e / pp, n = e - (e / pp) * pp;
     cf[e] = coeffs[((long long)k * n_leaf_total + lf) * pp + n];
   }
   for (int e = tid; e < pp; e += bs) { sD[e] = tb.D[e]; sD2[e] = tb.D2[e]; }
-  for (int e = tid; e < p * q; e += bs) { sLs[e] = tb.Ls[e]; sLl[e] = tb.Lloc[e]; }
+  for (int e = tid; e < p * q; e += bs) { sLs[e] = tb.Ls[e]; sLl[e] = tb.Lloc[e]; sDL[e] = tb.DLs[e]; }
   for (int e = tid; e < m; e += bs) sci[e] = tb.ci[e];
   __syncthreads();
   const double sx = 2.0 / hxy[2 * lf], sy = 2.0 / hxy[2 * lf + 1];
@@ -65,15 +72,16 @@ __global__ void __launch_bounds__(256) leaf_assemble_kernel(
         v = Aent(nj % p, nj / p);
       } else {
         const int g = col - m, s = g / q, a = g - (g / q) * q;
-        for (int t = 0; t < p; ++t) {
-          int jx, jy;
-          switch (s) {
-            case 0: jx = t; jy = 0; break;
-            case 1: jx = p - 1; jy = t; break;
-            case 2: jx = t; jy = p - 1; break;
-            default: jx = 0; jy = t; break;
-          }
-          v += Aent(jx, jy) * sLs[t * q + a];
+        if (s == 0 || s == 2) {  // horizontal side jy = 0 or p-1: node (ix, jy) on the row's column
+          const int jy = (s == 0) ? 0 : p - 1;
+          const double dy = sD[iy * p + jy];
+          v = -2.0 * c12 * sx * sy * dy * sDL[ix * q + a] +
+              (-c22 * sy * sy * sD2[iy * p + jy] + c2 * sy * dy) * sLs[ix * q + a];
+        } else {  // vertical side jx = p-1 or 0: node (jx, iy) on the row's line
+          const int jx = (s == 1) ? p - 1 : 0;
+          const double dx = sD[ix * p + jx];
+          v = -2.0 * c12 * sx * sy * dx * sDL[iy * q + a] +
+              (-c11 * sx * sx * sD2[ix * p + jx] + c1 * sx * dx) * sLs[iy * q + a];
         }
       }
     } else {
@@ -105,7 +113,7 @@ void launch_leaf_assemble(const double* coeffs, long long n_leaf_total, int leaf
                           const double* hxy, int p, int q, const LeafTablesDev& tb, T* work,
                           long long mat_stride, cudaStream_t s) {
   const int pp = p * p, m = (p - 2) * (p - 2);
-  const size_t smem = (size_t)(6 * pp + 2 * pp + 2 * p * q) * sizeof(double) + (size_t)m * sizeof(int) + 16;
+  const size_t smem = (size_t)(6 * pp + 2 * pp + 3 * p * q) * sizeof(double) + (size_t)m * sizeof(int) + 16;
   static size_t configured = 0;
   if (smem > 48 * 1024 && smem > configured) {
     cudaFuncSetAttribute(leaf_assemble_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -23,6 +23,7 @@ __device__ __forceinline__ int map_row(const int* __restrict__ idx, int base_or_
 }
 
 constexpr int KC = 256;  // K chunk staged in shared memory (GEMV path)
+constexpr int ROWS_HINT = 64;  // rows of one split-K output block
 
 // nrhs <= NR (1, 2 or 4).  Non-transposed: one warp per output row, lanes split K.
 template <typename TA, typename TV, int NR>
@@ -509,6 +510,42 @@ __global__ void __launch_bounds__(256) coeff_grad_kernel(ResidualArgs a, const d
   }
 }
 
+template <typename TV>
+__global__ void split_reduce_kernel(const SplitRed* __restrict__ d, const TV* __restrict__ P, TV* __restrict__ C,
+                                    const TV* __restrict__ Add, const int* __restrict__ idx, int nrhs, TV beta) {
+  const SplitRed sr = d[blockIdx.y];
+  const long long total = (long long)sr.M * nrhs;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / nrhs);
+    const int r = (int)(e - (long long)i * nrhs);
+    TV v = TV(0);
+    for (int j = 0; j < sr.nsplit; ++j) v += P[(long long)(sr.p_row + j * sr.M + i) * nrhs + r];
+    if (sr.add_row >= 0) v += Add[(long long)(sr.add_row + i) * nrhs + r];
+    const long long cr = (long long)map_row(idx, sr.c_idx, sr.c_row, i) * nrhs + r;
+    C[cr] = (beta != TV(0) ? beta * C[cr] : TV(0)) + v;
+  }
+}
+
+// u_ce = L_ce,ge u_ge (FP64): one leaf per CTA, one exterior node and rhs per thread.
+__global__ void exterior_refresh_kernel(int p, int q, const int* __restrict__ leaf_edges,
+                                        const double* __restrict__ Lce, const int* __restrict__ ce,
+                                        const double* __restrict__ ug, double* __restrict__ uc, int nrhs) {
+  const int lf = blockIdx.x;
+  const int ne = 4 * (p - 1), nq = 4 * q, pp = p * p;
+  const long long total = (long long)ne * nrhs;
+  for (long long e = threadIdx.x; e < total; e += blockDim.x) {
+    const int k = (int)(e / nrhs);
+    const int r = (int)(e - (long long)k * nrhs);
+    double v = 0.0;
+    for (int g = 0; g < nq; ++g) {
+      const int s = g / q, a = g - (g / q) * q;
+      v += Lce[(long long)k * nq + g] * ug[((long long)leaf_edges[4 * lf + s] * q + a) * nrhs + r];
+    }
+    uc[((long long)lf * pp + ce[k]) * nrhs + r] = v;
+  }
+}
+
 inline int grid_for(long long n, int bs = 256, int cap = 8192) {
   long long g = (n + bs - 1) / bs;
   if (g < 1) g = 1;
@@ -546,6 +583,20 @@ void launch_gemm_items(const GemmItem* items, int nitems, int maxM, int trans, c
     if (trans) gemm_items_kernel<TA, TV, 64, true><<<grid, 256, 0, s>>>(items, A, B0, B1, C, Add, idx, nrhs, b);
     else gemm_items_kernel<TA, TV, 64, false><<<grid, 256, 0, s>>>(items, A, B0, B1, C, Add, idx, nrhs, b);
   }
+}
+
+template <typename TV>
+void launch_split_reduce(const SplitRed* d, int n, const TV* P, TV* C, const TV* Add, const int* idx, int nrhs,
+                         double beta, cudaStream_t s) {
+  if (n <= 0) return;
+  dim3 grid(grid_for((long long)ROWS_HINT * nrhs, 256, 16), n);
+  split_reduce_kernel<TV><<<grid, 256, 0, s>>>(d, P, C, Add, idx, nrhs, (TV)beta);
+}
+
+void launch_exterior_refresh(int n_leaf, int p, int q, const int* leaf_edges, const double* Lce, const int* ce,
+                             const double* ug, double* uc, int nrhs, cudaStream_t s) {
+  if (n_leaf <= 0) return;
+  exterior_refresh_kernel<<<n_leaf, 256, 0, s>>>(p, q, leaf_edges, Lce, ce, ug, uc, nrhs);
 }
 
 template <typename TV>
@@ -630,6 +681,10 @@ template void launch_gemm_items<double, double>(const GemmItem*, int, int, int, 
 template void launch_gemm_items<float, float>(const GemmItem*, int, int, int, const float*, const float*,
                                               const float*, float*, const float*, const int*, int, double,
                                               cudaStream_t);
+template void launch_split_reduce<double>(const SplitRed*, int, const double*, double*, const double*, const int*,
+                                          int, double, cudaStream_t);
+template void launch_split_reduce<float>(const SplitRed*, int, const float*, float*, const float*, const int*, int,
+                                         double, cudaStream_t);
 template void launch_up_gather<double>(const UpGather*, int, int, const double*, double*, double*, const double*,
                                        const int*, int, cudaStream_t);
 template void launch_up_gather<float>(const UpGather*, int, int, const float*, float*, float*, const double*,

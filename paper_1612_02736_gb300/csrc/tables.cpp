@@ -133,6 +133,13 @@ void build_ref_tables(int p, int q, RefTables& rt) {
     rt.Ls[0 * q + k] *= 0.5;
     rt.Ls[(size_t)(p - 1) * q + k] *= 0.5;
   }
+  rt.DLs.assign((size_t)p * q, 0.0);
+  for (int i = 0; i < p; ++i)
+    for (int a = 0; a < q; ++a) {
+      long double acc = 0.0L;
+      for (int t = 0; t < p; ++t) acc += (long double)rt.D[(size_t)i * p + t] * rt.Ls[(size_t)t * q + a];
+      rt.DLs[(size_t)i * q + a] = (double)acc;
+    }
   rt.ci.clear();
   rt.ce.clear();
   for (int iy = 0; iy < p; ++iy)
