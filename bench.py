@@ -302,7 +302,7 @@ def run_gpu(args, rank, world, local):
     peaks, src = measured_peaks()
     dom = max(table, key=lambda r: r["ms"])
     per_launch_ms = dom["ms"] / max(dom["launches"], 1)
-    if dom["name"].endswith("_f64") and dom["flops"] > 0:
+    if ("_f64" in dom["name"]) and dom["flops"] > 0:
         achieved = dom["flops"] / (dom["ms"] / 1e3) / 1e12
         roof = {"kernel": dom["name"], "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,

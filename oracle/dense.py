@@ -5,8 +5,13 @@ Unknowns z = [u_g (all Gaussian nodes) ; u_ci of leaf 0 ; u_ci of leaf 1 ; ...].
 Equations, in this order:
   1. every leaf interior Chebyshev node i:  A_ci,ci u_ci + A_ci,ce L_ce,ge u_ge = g_ci
      (Eqs. local_sol and alpine2p5),
-  2. every interior Gaussian node j shared by the W/S leaf a and the E/N leaf b:
-     (D_ge,c u_c)_a(j) - (D_ge,c u_c)_b(j) = rho_j   (flux continuity, Sec. 4 / Eq. pair),
+  2. every Gaussian node j on an interface, one equation each:
+     - shared by the W/S leaf a and the E/N leaf b:
+       (D_ge,c u_c)_a(j) - (D_ge,c u_c)_b(j) = rho_j   (flux continuity, Sec. 4 / Eq. pair);
+     - a fine node on a coarsened side of a refined parent (Sec. 6.4):
+       u_j - (P_up u_coarse)_j = 0;
+     - a coarse node facing a refined parent: the coarse leaf's flux minus the P_down
+       projection of the fine leaves' fluxes (W/S side minus E/N side) = rho_j,
   3. every boundary Gaussian node: u_j = f_j   (Eq. basic, Algorithm 2 root step),
 with u_c = [L_ce,ge u_ge on I_ce ; u_ci on I_ci] on each leaf.
 
@@ -16,6 +21,9 @@ import numpy as np
 
 from . import spectral as sp
 from .leaf import leaf_A
+
+# A node on a leaf's E or N side lies on the W/S side of the interface it belongs to.
+SIDES_WS = {0: False, 1: True, 2: True, 3: False}
 
 
 def assemble(tree, coeffs, p):
@@ -51,10 +59,30 @@ def assemble(tree, coeffs, p):
     for la, pa, lb, pb in tree.interior_pairs:
         K[row] = flux[la][pa] - flux[lb][pb]
         row += 1
+    # coarse-fine interfaces of refined parents
+    own = tree.owners
+    for g in sorted(tree.slave):
+        bid, r = tree.slave[g]
+        b = tree.boxes[bid]
+        K[row, g] = 1.0
+        K[row, b.ge] -= b.Pup[r]
+        row += 1
+    for g in sorted(tree.coarse_of):
+        bid, r = tree.coarse_of[g]
+        b = tree.boxes[bid]
+        (lc, pc), = own[g]
+        proj = np.zeros(n)
+        for k, gf in enumerate(b.ge_old):
+            if b.Pdown[r, k] != 0.0 and gf in tree.slave:
+                (lf, pf), = own[gf]
+                proj += b.Pdown[r, k] * flux[lf][pf]
+        coarse_is_ws = SIDES_WS[pc // q]
+        K[row] = (flux[lc][pc] - proj) if coarse_is_ws else (proj - flux[lc][pc])
+        row += 1
     for j in tree.boundary:
         K[row, j] = 1.0
         row += 1
-    assert row == n
+    assert row == n, "every Gaussian node needs exactly one interface or boundary equation"
     return K, {"E": E, "m": m, "ci": ci, "ng": ng}
 
 
@@ -74,6 +102,11 @@ def rhs(tree, p, f, g, rho=None):
     else:
         rho = np.asarray(rho, dtype=np.float64).reshape(tree.n_gauss, -1)
         parts.append(rho[tree.interior])
+    parts.append(np.zeros((len(tree.slave), nrhs)))
+    if rho is None:
+        parts.append(np.zeros((len(tree.coarse_of), nrhs)))
+    else:
+        parts.append(rho[sorted(tree.coarse_of)])
     parts.append(f)
     return np.vstack(parts)
 
@@ -103,5 +136,8 @@ def solve_transpose(tree, coeffs, p, ubar):
     nint = len(tree.interior_pairs)
     rhobar = np.zeros((tree.n_gauss, ubar.shape[-1]))
     rhobar[tree.interior] = lam[nl * m:nl * m + nint]
-    fbar = lam[nl * m + nint:]
+    nsl, nco = len(tree.slave), len(tree.coarse_of)
+    off = nl * m + nint + nsl
+    rhobar[sorted(tree.coarse_of)] = lam[off:off + nco]
+    fbar = lam[off + nco:]
     return fbar, gbar, rhobar

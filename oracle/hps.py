@@ -24,7 +24,9 @@ def _pos(lst):
 
 
 def build(tree, coeffs, p):
-    """Algorithm 1: one upward sweep; leaf operators by Sec. 3, merges by Sec. 4."""
+    """Algorithm 1: one upward sweep; leaf operators by Sec. 3, merges by Sec. 4.  A
+    refined parent's DtN map is re-expressed on its coarsened sides, T_new = P_down T P_up
+    (Sec. 6.3); its S keeps acting on the fine nodes, which the solve fills by P_up."""
     q = tree.q
     ops = {}
     for bid in tree.order_up():
@@ -51,6 +53,8 @@ def build(tree, coeffs, p):
         Tblk[n1:, n1:] = T22
         C = np.vstack([T13, T23])
         T = Tblk + C @ S
+        if b.Pup is not None:
+            T = b.Pdown @ T @ b.Pup
         ops[bid] = {"X": X, "S": S, "T": T, "C": C, "I1": I1, "I2": I2, "I3a": I3a, "I3b": I3b}
     return ops
 
@@ -64,7 +68,9 @@ def solve(tree, ops, p, f, g, rho=None):
     """Algorithm 2 (upward pass for particular solutions, downward pass for potentials),
     with per-box flux vectors h.  A non-zero ``rho`` enters the merge of the box whose J3
     holds the node: Eq. swiss with the continuity condition v3(alpha) - v3(beta) = rho3
-    gives u3 = X (T32b u2 - T31a u1 + h3b - h3a + rho3)."""
+    gives u3 = X (T32b u2 - T31a u1 + h3b - h3a + rho3).  Refined parents (Sec. 6.4): the
+    upward flux is projected, h_new = P_down h_old, and on the way down the fine nodes of a
+    coarsened side get u_fine = P_up u_coarse before the parent's S is applied."""
     f = _as2d(f, 1)
     g = _as2d(g, 2)
     nrhs = g.shape[-1]
@@ -84,6 +90,8 @@ def solve(tree, ops, p, f, g, rho=None):
             d = d + rho[b.J3]
         w[bid] = o["X"] @ d
         h[bid] = np.vstack([h[a][o["I1"]], h[c][o["I2"]]]) + o["C"] @ w[bid]
+        if b.Pup is not None:
+            h[bid] = b.Pdown @ h[bid]
     u_g = np.zeros((tree.n_gauss, nrhs))
     u_g[tree.boundary] = f
     u_c = np.zeros((tree.n_leaves, p * p, nrhs))
@@ -91,7 +99,10 @@ def solve(tree, ops, p, f, g, rho=None):
         b = tree.boxes[bid]
         o = ops[bid]
         if b.children is not None:
-            u_g[b.J3] = o["S"] @ u_g[b.ge] + w[bid]
+            if b.Pup is not None:
+                fine = [k for k, g in enumerate(b.ge_old) if g not in set(b.ge)]
+                u_g[np.array(b.ge_old)[fine]] = (b.Pup @ u_g[b.ge])[fine]
+            u_g[b.J3] = o["S"] @ u_g[b.ge_old] + w[bid]
         else:
             u_c[b.leaf] = o["S"] @ u_g[b.ge] + o["F"] @ g[b.leaf][ci]
     return u_c, u_g
@@ -157,7 +168,10 @@ def adjoint(tree, ops, p, ubar):
             gbar[b.leaf][ci] += o["F"].T @ ubar[b.leaf]
         else:
             wbar[bid] = ubar_g[b.J3].copy()
-            ubar_g[b.ge] += o["S"].T @ ubar_g[b.J3]
+            ubar_g[b.ge_old] += o["S"].T @ ubar_g[b.J3]
+            if b.Pup is not None:
+                fine = [k for k, g in enumerate(b.ge_old) if g not in set(b.ge)]
+                ubar_g[b.ge] += b.Pup[fine].T @ ubar_g[np.array(b.ge_old)[fine]]
     fbar = ubar_g[tree.boundary].copy()
     hbar = {bid: None for bid in range(len(tree.boxes))}
     rhobar = np.zeros((tree.n_gauss, nrhs))
@@ -170,6 +184,8 @@ def adjoint(tree, ops, p, ubar):
             continue
         a, c = b.children
         n1 = len(o["I1"])
+        if b.Pup is not None:
+            hbar[bid] = b.Pdown.T @ hbar[bid]
         dbar = o["X"].T @ (wbar[bid] + o["C"].T @ hbar[bid])
         ha = np.zeros((len(tree.boxes[a].ge), nrhs))
         hc = np.zeros((len(tree.boxes[c].ge), nrhs))

@@ -791,9 +791,9 @@ int choose_nb(int K, size_t elem, int nmat) {
 // rk: (R, K) of every matrix of the batch, for the flop counts of the timing records.
 template <typename T>
 void run_gj(const GJDesc* gj, int nmat, int maxR, int maxK, T* work, int* perm, T* pinv, T* prow,
-            int* status, const std::vector<std::pair<int, int>>& rk, cudaStream_t s) {
+            int* status, const std::vector<std::pair<int, int>>& rk, const char* what, cudaStream_t s) {
   const int nb = choose_nb(maxK, sizeof(T), nmat);
-  const std::string sf = tsuf<T>();
+  const std::string sf = std::string(tsuf<T>()) + ":" + what;
   TIMED(("gj_init_" + sf).c_str(), 0, 0, launch_gj_init<T>(gj, nmat, perm, s));
   CKL();
   const long long prow_stride = (long long)16 * maxR;
@@ -859,7 +859,7 @@ void build_stage(hps_handle* h, const double* coeffs, cudaStream_t s) {
             launch_leaf_assemble<double>(coeffs, h->n_leaf, l0, n, h->dhxy, h->p, h->q, tb, work, per_leaf, s));
       CKL();
       run_gj<double>(dgd, n, R, m, work, perm, pinv, prow, h->d_status,
-                     std::vector<std::pair<int, int>>(n, {R, m}), s);
+                     std::vector<std::pair<int, int>>(n, {R, m}), "leaf", s);
       ExtractDst dst{};
       const long long gl0 = h->gl_base + (long long)l0 * m * R;
       dst.TL = h->ops64 + gl0; dst.TL_off_stride = (long long)m * R; dst.TL_ld = R;
@@ -892,7 +892,7 @@ void build_stage(hps_handle* h, const double* coeffs, cudaStream_t s) {
         double* pr = (double*)get((size_t)nmat * 16 * lv.maxR * sizeof(double));
         TIMED("merge_assemble_f64", 0, wbytes, launch_merge_assemble<double, double>(lv.md, nmat, lv.maxR, tstore, h->didx, w, s));
         CKL();
-        run_gj<double>(lv.gj, nmat, lv.maxR, lv.maxK, w, pm, pi, pr, h->d_status, rk, s);
+        run_gj<double>(lv.gj, nmat, lv.maxR, lv.maxK, w, pm, pi, pr, h->d_status, rk, "merge", s);
         TIMED("gj_extract_f64", 0, wbytes, launch_gj_extract<double, double>(lv.gj, nmat, lv.maxR, w, pm, dst, s));
         CKL();
       } else {
@@ -902,7 +902,7 @@ void build_stage(hps_handle* h, const double* coeffs, cudaStream_t s) {
         float* pr = (float*)get((size_t)nmat * 16 * lv.maxR * sizeof(float));
         TIMED("merge_assemble_f32", 0, wbytes, launch_merge_assemble<float, double>(lv.md, nmat, lv.maxR, tstore, h->didx, w, s));
         CKL();
-        run_gj<float>(lv.gj, nmat, lv.maxR, lv.maxK, w, pm, pi, pr, h->d_status, rk, s);
+        run_gj<float>(lv.gj, nmat, lv.maxR, lv.maxK, w, pm, pi, pr, h->d_status, rk, "merge", s);
         TIMED("gj_extract_f32", 0, wbytes, launch_gj_extract<float, double>(lv.gj, nmat, lv.maxR, w, pm, dst, s));
         CKL();
       }
