@@ -9,11 +9,13 @@
  * p x p Chebyshev-Lobatto grid (Sec. 3.1) and q Gauss-Legendre nodes per side (Sec. 2).
  *
  * Conventions shared by every call:
- *  - Leaves are numbered j * nx + i (x fastest).  Leaf Chebyshev nodes are numbered
- *    iy * p + ix (x fastest), ascending coordinates.
- *  - Gaussian nodes get global ids edge by edge, visiting leaves in leaf order and their
- *    sides in the order S, E, N, W; the q ids of one edge ascend along it.  "Boundary
- *    order" lists the domain-boundary Gaussian nodes in ascending global id.
+ *  - Leaves are numbered by their lower-left corner, y first, then x (j * nx + i on a
+ *    uniform grid).  Leaf Chebyshev nodes are numbered iy * p + ix (x fastest),
+ *    ascending coordinates.
+ *  - Gaussian nodes get global ids edge segment by segment, visiting leaves in leaf order
+ *    and their sides in the order S, E, N, W; the q ids of one segment ascend along it; a
+ *    segment two leaves share exactly has one set of ids.  "Boundary order" lists the
+ *    domain-boundary Gaussian nodes in ascending global id.
  *  - Fluxes are d/dx on vertical and d/dy on horizontal edges (Sec. 3.1).
  *  - Multi-RHS arrays put the right-hand-side index fastest: [row][rhs].
  *  - All floating-point inputs and outputs are FP64.  Device pointers are plain CUDA
@@ -86,6 +88,25 @@ void hps_opts_default(hps_opts* opts);
  * hps_tree_destroy).  INVALID_ARG if nx, ny < 1, x1 <= x0, y1 <= y0 or out is NULL. */
 int hps_tree_uniform(double x0, double y0, double x1, double y1, int nx, int ny, hps_tree** out);
 int hps_tree_destroy(hps_tree* tree);
+
+/* Union of squares (Sec. 1: domains that are unions of rectangles): the squares
+ * [x0 + i h, x0 + (i+1) h] x [y0 + j h, y0 + (j+1) h] with mask[j * nx + i] != 0 are the
+ * leaves.  The tree bisects the nx x ny grid as hps_tree_uniform does and skips empty
+ * halves, so e.g. the L-shaped domain is glued from its squares by the top merges.
+ * INVALID_ARG if the mask selects nothing. */
+int hps_tree_mask(double x0, double y0, double h, int nx, int ny, const uint8_t* mask, hps_tree** out);
+
+/* Local refinement (Sec. 6.1): returns a new tree in which, `levels` times over, every leaf
+ * whose distance d to one of the npts points (pts_xy = x0, y0, x1, y1, ...) satisfies
+ * d <= sqrt(2) l (leaf side 2 l) is split into 2 x 2 leaves (a vertical cut, then
+ * horizontal cuts).  After such a refined parent is merged, each of its sides that faces a
+ * leaf of its own size is re-expressed on that leaf's nodes with the interpolation
+ * operators of Sec. 6.3 (P_up: fine <- coarse, one polynomial through the coarse Gauss
+ * nodes; P_down: coarse <- fine, from the fine segment holding each coarse node, averaged
+ * when a node sits on the junction of two segments).  The input tree is unchanged.
+ * Refined trees support HPS_FP64 only; hps_build rejects meshes whose interfaces the rule
+ * leaves unmatched. */
+int hps_tree_refine(const hps_tree* tree, const double* pts_xy, int npts, int levels, hps_tree** out);
 
 /* Counts: leaves, boxes, tree height (merge levels), and for a given q the number of
  * Gaussian nodes (all, and on the domain boundary). */

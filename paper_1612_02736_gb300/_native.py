@@ -40,6 +40,8 @@ SIGNATURES = {
     "hps_opts_default": (None, [C.POINTER(hps_opts)]),
     "hps_tree_uniform": (C.c_int, [C.c_double, C.c_double, C.c_double, C.c_double, C.c_int, C.c_int, C.POINTER(P)]),
     "hps_tree_destroy": (C.c_int, [P]),
+    "hps_tree_mask": (C.c_int, [C.c_double, C.c_double, C.c_double, C.c_int, C.c_int, P, C.POINTER(P)]),
+    "hps_tree_refine": (C.c_int, [P, P, C.c_int, C.c_int, C.POINTER(P)]),
     "hps_tree_info": (C.c_int, [P, C.c_int] + [C.POINTER(C.c_int)] * 5),
     "hps_nodes": (C.c_int, [P, C.c_int, C.c_int, C.c_int, P, C.POINTER(C.c_int64)]),
     "hps_plan_check": (C.c_int, [P, C.c_int, C.POINTER(hps_opts)]),

@@ -14,10 +14,6 @@
 
 #include "hps_internal.h"
 
-namespace hps {
-int make_uniform_tree(double x0, double y0, double x1, double y1, int nx, int ny, Tree& t);
-}
-
 using namespace hps;
 
 struct hps_tree {
@@ -27,6 +23,15 @@ struct hps_tree {
 namespace {
 
 thread_local std::string g_err;
+
+// Domain-boundary Gaussian nodes (ascending id) of a tree for a given q.
+void boundary_nodes(const Tree& t, int q, std::vector<int>& out) {
+  RefTables rt;
+  build_ref_tables(std::max(q + 1, 4), q, rt);
+  NodeSets ns;
+  build_node_sets(t, q, ns, rt.xg);
+  out = ns.boundary;
+}
 
 int fail(int code, const std::string& msg) {
   g_err = msg;
@@ -166,6 +171,12 @@ struct Level {
   int* reduce_tab = nullptr;
   int n_reduce = 0;
   Prod adjM;
+  // coarsened refined parents of this level (Sec. 6.3-6.4)
+  ItemSet iup, idown, aiup, aidown;
+  BGemm* tp1 = nullptr;  // T_tmp P_up -> scratch
+  BGemm* tp2 = nullptr;  // P_down (T_tmp P_up) -> T store
+  int ntp = 0;
+  long long tp_scratch = 0;
   DownScatter* ds = nullptr;
   int ds_maxrows = 0;
 };
@@ -225,7 +236,11 @@ struct hps_handle {
   long long gl_base = 0, h_base = 0, lce_base = 0;
   std::vector<long long> mo, so;  // per box: Mleft and S offsets
   std::vector<long long> toff;    // per box: T block offset in the build's T store
-  std::vector<int> k3, k12;
+  std::vector<long long> ttmp;    // coarsened boxes: T before coarsening (T store)
+  std::vector<long long> puo, pdo, pco;  // coarsened boxes: P_up, P_down, P_up(fine, coarse)
+  std::vector<int> k3, k12, k12o; // |J3|, |I_ge| seen by the parent, |J1 + J2|
+  std::vector<int> off_geo, off_fine, off_coarse;
+  bool any_coarsened = false;
   // vector layouts (in rows)
   std::vector<int> vrow, drow, ubrow;
   int v_rows = 0, d_rows = 0, ub_rows = 0;
@@ -246,7 +261,12 @@ struct hps_handle {
     for (auto& b : owned) al.put(b.p, 0);
     cudaStreamSynchronize(0);
   }
-  int hrow(int box) const { return vrow[box] + (tree.boxes[box].leaf >= 0 ? 0 : k3[box]); }
+  // row base of the flux vector a box hands to its parent (after coarsening)
+  int hrow(int box) const {
+    if (tree.boxes[box].leaf >= 0) return vrow[box];
+    return vrow[box] + k3[box] + (ns.co[box].active ? k12o[box] : 0);
+  }
+  int hrow_old(int box) const { return vrow[box] + (tree.boxes[box].leaf >= 0 ? 0 : k3[box]); }
 };
 
 namespace {
@@ -318,6 +338,8 @@ struct LevelHost {
   std::vector<long long> tl, bl, tr, br;
   std::vector<UpGather> ug;
   ProdHost up, down, adjS, adjM;
+  std::vector<GemmItem> iup, idown, aiup, aidown;
+  std::vector<BGemm> tp1, tp2;
   std::vector<int> wcopy, reduce;
   std::vector<DownScatter> ds;
 };
@@ -347,14 +369,25 @@ void make_plan(hps_handle* h, HostPlan& hp) {
   h->off_bnd = push(ns.boundary);
   h->off_ge.assign(nb, -1);
   h->off_J3.assign(nb, -1);
+  h->off_geo.assign(nb, -1);
+  h->off_fine.assign(nb, -1);
+  h->off_coarse.assign(nb, -1);
   h->k3.assign(nb, 0);
   h->k12.assign(nb, 0);
+  h->k12o.assign(nb, 0);
   for (int b = 0; b < nb; ++b) {
     h->off_ge[b] = push(ns.ge[b]);
     h->k12[b] = (int)ns.ge[b].size();
+    h->k12o[b] = (int)ns.ge_old[b].size();
     if (t.boxes[b].leaf < 0) {
       h->off_J3[b] = push(ns.J3[b]);
+      h->off_geo[b] = push(ns.ge_old[b]);
       h->k3[b] = (int)ns.J3[b].size();
+    }
+    if (ns.co[b].active) {
+      h->off_fine[b] = push(ns.co[b].fine);
+      h->off_coarse[b] = push(ns.co[b].coarse);
+      h->any_coarsened = true;
     }
   }
   // operator pool layout
@@ -367,13 +400,24 @@ void make_plan(hps_handle* h, HostPlan& hp) {
   off += (long long)h->ne * nq;
   h->mo.assign(nb, -1);
   h->so.assign(nb, -1);
+  h->puo.assign(nb, -1);
+  h->pdo.assign(nb, -1);
+  h->pco.assign(nb, -1);
   for (int b = 0; b < nb; ++b) {
     if (t.boxes[b].leaf >= 0) continue;
-    const int R = h->k3[b] + h->k12[b];
+    const int R = h->k3[b] + h->k12o[b];
     h->mo[b] = off;
     off += (long long)R * h->k3[b];
     h->so[b] = off;
-    off += (long long)h->k3[b] * h->k12[b];
+    off += (long long)h->k3[b] * h->k12o[b];
+    if (ns.co[b].active) {
+      h->puo[b] = off;
+      off += (long long)h->k12o[b] * h->k12[b];
+      h->pdo[b] = off;
+      off += (long long)h->k12[b] * h->k12o[b];
+      h->pco[b] = off;
+      off += (long long)ns.co[b].fine.size() * ns.co[b].coarse.size();
+    }
   }
   h->ops_elems = off;
   // vector layouts
@@ -386,11 +430,11 @@ void make_plan(hps_handle* h, HostPlan& hp) {
     if (t.boxes[b].leaf >= 0) {
       vr += nq;
     } else {
-      vr += h->k3[b] + h->k12[b];
+      vr += h->k3[b] + h->k12o[b] + (ns.co[b].active ? h->k12[b] : 0);
       h->drow[b] = dr;
       dr += h->k3[b];
       h->ubrow[b] = ur;
-      ur += h->k12[b];
+      ur += h->k12o[b];
     }
   }
   h->v_rows = vr;
@@ -422,10 +466,15 @@ void make_plan(hps_handle* h, HostPlan& hp) {
     toff[t.leaves[lf]] = tsz;
     tsz += (long long)nq * nq;
   }
+  h->ttmp.assign(nb, -1);
   for (int b = 0; b < nb; ++b) {
     if (t.boxes[b].leaf >= 0) continue;
     toff[b] = tsz;
     tsz += (long long)h->k12[b] * h->k12[b];
+    if (ns.co[b].active) {
+      h->ttmp[b] = tsz;
+      tsz += (long long)h->k12o[b] * h->k12o[b];
+    }
   }
   for (int L = 0; L < H; ++L) {
     Level& lv = h->levels[L];
@@ -438,13 +487,13 @@ void make_plan(hps_handle* h, HostPlan& hp) {
     for (int b : lv.boxes) {
       const Box& bx = t.boxes[b];
       const int a = bx.child[0], c = bx.child[1];
-      const int k3 = h->k3[b], k12 = h->k12[b], R = k3 + k12, n1 = ns.n1[b], n2 = k12 - n1;
+      const int k3 = h->k3[b], k12 = h->k12o[b], R = k3 + k12, n1 = ns.n1[b], n2 = k12 - n1;
       lv.maxR = std::max(lv.maxR, R);
       lv.maxK = std::max(lv.maxK, k3);
       auto pa = posmap(a), pc = posmap(c);
       std::vector<int> posA(R, -1), posB(R, -1);
       const std::vector<int>& J3 = ns.J3[b];
-      const std::vector<int>& ge = ns.ge[b];
+      const std::vector<int>& ge = ns.ge_old[b];
       for (int k = 0; k < k3; ++k) {
         posA[k] = pa.at(J3[k]);
         posB[k] = pc.at(J3[k]);
@@ -475,7 +524,7 @@ void make_plan(hps_handle* h, HostPlan& hp) {
       pd.tl.push_back(h->mo[b]);
       pd.bl.push_back(h->mo[b] + (long long)k3 * k3);
       pd.tr.push_back(h->so[b]);
-      pd.br.push_back(toff[b]);
+      pd.br.push_back(ns.co[b].active ? h->ttmp[b] : toff[b]);
       // up-sweep gather lists: pos3a, pos3b, J3, pos1a, pos2b
       std::vector<int> lst;
       for (int k = 0; k < k3; ++k) lst.push_back(posA[k]);
@@ -509,7 +558,7 @@ void make_plan(hps_handle* h, HostPlan& hp) {
       // up: [w; h] += [X; CX] d
       add_product(pd.up.direct, h->mo[b], k3, R, k3, k3, h->drow[b], -1, 0, -1, h->vrow[b], -1, -1, false);
       // down: u[J3] = S u[ge] + w
-      add_product(pd.down.direct, h->so[b], k12, k3, k12, k12, 0, h->off_ge[b], 0, -1, 0, h->off_J3[b], h->vrow[b],
+      add_product(pd.down.direct, h->so[b], k12, k3, k12, k12, 0, h->off_geo[b], 0, -1, 0, h->off_J3[b], h->vrow[b],
                   false);
       // adjoint: wbar copy, S^T ubar[J3] -> UB, reduce into ubar[ge]
       for (int k = 0; k < k3; ++k) {
@@ -530,6 +579,23 @@ void make_plan(hps_handle* h, HostPlan& hp) {
       }
       // adjoint: dbar = [X; CX]^T [wbar; hbar]
       add_product(pd.adjM.direct, h->mo[b], k3, k3, R, R, h->vrow[b], -1, 0, -1, h->drow[b], -1, -1, true);
+      // coarsened refined parent (Sec. 6.3-6.4)
+      const Coarsen& co = ns.co[b];
+      if (co.active) {
+        const int kn = h->k12[b], nf = (int)co.fine.size(), nc = (int)co.coarse.size();
+        // up: h_new = P_down h_old ; down: u_fine = P_up(fine, coarse) u_coarse
+        add_product(pd.iup, h->pdo[b], k12, kn, k12, k12, h->hrow_old(b), -1, 0, -1, h->hrow(b), -1, -1, false);
+        add_product(pd.idown, h->pco[b], nc, nf, nc, nc, 0, h->off_coarse[b], 0, -1, 0, h->off_fine[b], -1, false);
+        // adjoint: hbar_old = P_down^T hbar_new ; ubar_coarse += P_up(fine, coarse)^T ubar_fine
+        add_product(pd.aiup, h->pdo[b], k12, k12, kn, kn, h->hrow(b), -1, 0, -1, h->hrow_old(b), -1, -1, true);
+        add_product(pd.aidown, h->pco[b], nc, nc, nf, nf, 0, h->off_fine[b], 0, -1, 0, h->off_coarse[b], -1, true);
+        // build: T_new = P_down (T_old P_up)
+        BGemm t1{h->ttmp[b], h->puo[b], lv.tp_scratch, k12, kn, k12, k12, kn, kn};
+        BGemm t2{h->pdo[b], lv.tp_scratch, toff[b], kn, kn, k12, k12, kn, kn};
+        pd.tp1.push_back(t1);
+        pd.tp2.push_back(t2);
+        lv.tp_scratch += (long long)k12 * kn;
+      }
     }
     lv.work_elems = woff;
     lv.perm_elems = poff;
@@ -622,6 +688,13 @@ void upload_plan(hps_handle* h, const HostPlan& hp, cudaStream_t s) {
     lv.reduce_tab = upload(h->al, s, pd.reduce, h->owned);
     lv.n_reduce = (int)pd.reduce.size() / 3;
     lv.ds = upload(h->al, s, pd.ds, h->owned);
+    lv.iup = upload_items(h, s, pd.iup);
+    lv.idown = upload_items(h, s, pd.idown);
+    lv.aiup = upload_items(h, s, pd.aiup);
+    lv.aidown = upload_items(h, s, pd.aidown);
+    lv.ntp = (int)pd.tp1.size();
+    lv.tp1 = pd.tp1.empty() ? nullptr : upload(h->al, s, pd.tp1, h->owned);
+    lv.tp2 = pd.tp2.empty() ? nullptr : upload(h->al, s, pd.tp2, h->owned);
   }
   h->leafup = upload_items(h, s, hp.lup);
   h->leafdown = upload_items(h, s, hp.ldown);
@@ -728,6 +801,18 @@ std::string validate_plan(const hps_handle* h, const HostPlan& hp) {
     check_prod(pc, idx, pd.down, false, ops, G, G, V, h->p_rows, "merge down");
     check_prod(pc, idx, pd.adjS, true, ops, G, UB, 0, h->p_rows, "adjoint S merge");
     check_prod(pc, idx, pd.adjM, true, ops, V, D, 0, h->p_rows, "adjoint X merge");
+    check_items(pc, idx, pd.iup, false, ops, V, 0, V, 0, "coarsen up");
+    check_items(pc, idx, pd.idown, false, ops, G, 0, G, 0, "refine down");
+    check_items(pc, idx, pd.aiup, true, ops, V, 0, V, 0, "adjoint coarsen up");
+    check_items(pc, idx, pd.aidown, true, ops, G, 0, G, 0, "adjoint refine down");
+    for (size_t i = 0; i < pd.tp1.size(); ++i) {
+      const BGemm &a = pd.tp1[i], &b2 = pd.tp2[i];
+      if (a.a_off + (long long)a.M * a.lda > hp.tsz || a.b_off + (long long)a.K * a.ldb > ops ||
+          a.c_off + (long long)a.M * a.ldc > lv.tp_scratch || b2.a_off + (long long)b2.M * b2.lda > ops ||
+          b2.b_off + (long long)b2.K * b2.ldb > lv.tp_scratch || b2.c_off + (long long)b2.M * b2.ldc > hp.tsz ||
+          a.N > a.ldb || a.K > a.lda || b2.K > b2.lda || b2.N > b2.ldc)
+        pc.fail("coarsened T product out of range");
+    }
     check_tab(pc, pd.wcopy, V, G, "adjoint w copy");
     check_tab(pc, pd.reduce, G, UB, "adjoint reduce");
     for (size_t i = 0; i < pd.ug.size(); ++i) {
@@ -735,6 +820,7 @@ std::string validate_plan(const hps_handle* h, const HostPlan& hp) {
       const int b = lv.boxes[i];
       const Box& bx = h->tree.boxes[b];
       const long long ka = h->k12[bx.child[0]], kb = h->k12[bx.child[1]];
+      if (u.n1 + u.n2 != h->k12o[b]) pc.fail("up gather: parent size mismatch");
       if ((size_t)u.idx_off + 3 * u.k3 + u.n1 + u.n2 > idx.size()) { pc.fail("up gather: list out of range"); continue; }
       for (int k = 0; k < u.k3; ++k) {
         const int a3 = idx[u.idx_off + k], b3 = idx[u.idx_off + u.k3 + k], j3 = idx[u.idx_off + 2 * u.k3 + k];
@@ -830,6 +916,15 @@ void build_stage(hps_handle* h, const double* coeffs, cudaStream_t s) {
     h->owned.push_back({h->ops64, (size_t)h->ops_elems * sizeof(double)});
     CK(cudaMemcpyAsync(h->ops64 + h->lce_base, h->rt.Lce.data(), h->rt.Lce.size() * sizeof(double),
                        cudaMemcpyHostToDevice, s));
+    for (size_t b = 0; b < h->tree.boxes.size(); ++b) {
+      const Coarsen& co = h->ns.co[b];
+      if (!co.active) continue;
+      CK(cudaMemcpyAsync(h->ops64 + h->puo[b], co.Pup.data(), co.Pup.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+      CK(cudaMemcpyAsync(h->ops64 + h->pdo[b], co.Pdown.data(), co.Pdown.size() * sizeof(double),
+                         cudaMemcpyHostToDevice, s));
+      CK(cudaMemcpyAsync(h->ops64 + h->pco[b], co.Pupc.data(), co.Pupc.size() * sizeof(double),
+                         cudaMemcpyHostToDevice, s));
+    }
     double* tstore = (double*)get(tstore_elems(h) * sizeof(double));
     const std::vector<long long>& toff = h->toff;
     // ---- leaves (FP64 always), in chunks
@@ -904,6 +999,18 @@ void build_stage(hps_handle* h, const double* coeffs, cudaStream_t s) {
         CKL();
         run_gj<float>(lv.gj, nmat, lv.maxR, lv.maxK, w, pm, pi, pr, h->d_status, rk, "merge", s);
         TIMED("gj_extract_f32", 0, wbytes, launch_gj_extract<float, double>(lv.gj, nmat, lv.maxR, w, pm, dst, s));
+        CKL();
+      }
+      if (lv.ntp > 0) {  // refined parents: T_new = P_down T P_up (Sec. 6.3)
+        double* tmp = (double*)get((size_t)lv.tp_scratch * sizeof(double));
+        int mM = 1, mN = 1;
+        for (int b : lv.boxes)
+          if (h->ns.co[b].active) {
+            mM = std::max(mM, std::max(h->k12o[b], h->k12[b]));
+            mN = std::max(mN, h->k12[b]);
+          }
+        TIMED("coarsen_T", 0, 0, launch_bgemm(lv.tp1, lv.ntp, mM, mN, tstore, h->ops64, tmp, s));
+        TIMED("coarsen_T", 0, 0, launch_bgemm(lv.tp2, lv.ntp, mM, mN, h->ops64, tmp, tstore, s));
         CKL();
       }
     }
@@ -985,11 +1092,13 @@ void solve_pass(hps_handle* h, const TA* ops, const double* f, const TV* g, cons
     Level& lv = h->levels[L];
     TIMED("up_gather", 0, 0, launch_up_gather<TV>(lv.ug, (int)lv.boxes.size(), lv.ug_maxrows, V, V, dbuf, rho, idx, nrhs, s));
     gemmp("merge_up", lv.up, dbuf, V, nullptr, 1.0);
+    if (lv.iup.n) gemm("coarsen_up", lv.iup, V, nullptr, V, nullptr, 0.0);
   }
   // root boundary data, then the downward pass
   if (f) TIMED("scatter_rows", 0, 0, launch_scatter_rows<TV>(f, idx + h->off_bnd, h->n_bdry, ug, nrhs, s));
   for (int L = H - 1; L >= 0; --L) {
     Level& lv = h->levels[L];
+    if (lv.idown.n) gemm("refine_down", lv.idown, ug, nullptr, ug, nullptr, 0.0);
     gemmp("merge_down", lv.down, ug, ug, V, 0.0);
   }
   gemm("leaf_down", h->leafdown, g, ug, uc, nullptr, 0.0);
@@ -1064,10 +1173,9 @@ int hps_tree_info(const hps_tree* tree, int q, int* n_leaves, int* n_boxes, int*
   if (n_levels) *n_levels = t.height;
   if (n_gauss) *n_gauss = t.n_edges * q;
   if (n_boundary) {
-    int nb = 0;
-    for (int e = 0; e < t.n_edges; ++e)
-      if (t.edge_owners[2 * e + 1] < 0) ++nb;
-    *n_boundary = nb * q;
+    std::vector<int> bnd;
+    boundary_nodes(t, q, bnd);
+    *n_boundary = (int)bnd.size();
   }
   return HPS_OK;
 }
@@ -1119,18 +1227,45 @@ int hps_nodes(const hps_tree* tree, int p, int q, int which, double* xy, int64_t
     if (xy) std::memcpy(xy, all.data(), all.size() * sizeof(double));
     return HPS_OK;
   }
-  int64_t n = 0;
-  for (int e = 0; e < t.n_edges; ++e)
-    if (t.edge_owners[2 * e + 1] < 0) {
-      for (int k = 0; k < q; ++k) {
-        if (xy) {
-          xy[2 * n] = all[2 * ((size_t)e * q + k)];
-          xy[2 * n + 1] = all[2 * ((size_t)e * q + k) + 1];
-        }
-        ++n;
-      }
+  std::vector<int> bnd;
+  boundary_nodes(t, q, bnd);
+  if (xy)
+    for (size_t n = 0; n < bnd.size(); ++n) {
+      xy[2 * n] = all[2 * (size_t)bnd[n]];
+      xy[2 * n + 1] = all[2 * (size_t)bnd[n] + 1];
     }
-  *count = n;
+  *count = (int64_t)bnd.size();
+  return HPS_OK;
+}
+
+int hps_tree_mask(double x0, double y0, double h, int nx, int ny, const uint8_t* mask, hps_tree** out) {
+  if (!out) return fail(HPS_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!mask) return fail(HPS_ERR_INVALID_ARG, "mask is NULL");
+  if (nx < 1 || ny < 1 || (long long)nx * ny > (1ll << 24)) return fail(HPS_ERR_INVALID_ARG, "bad grid size");
+  if (!(h > 0.0)) return fail(HPS_ERR_INVALID_ARG, "h must be positive");
+  hps_tree* t = new (std::nothrow) hps_tree();
+  if (!t) return fail(HPS_ERR_OOM, "host allocation failed");
+  if (make_mask_tree(x0, y0, h, nx, ny, mask, t->t) != 0) {
+    delete t;
+    return fail(HPS_ERR_INVALID_ARG, "mask selects no square");
+  }
+  *out = t;
+  return HPS_OK;
+}
+
+int hps_tree_refine(const hps_tree* tree, const double* pts_xy, int npts, int levels, hps_tree** out) {
+  if (!out) return fail(HPS_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!tree || (npts > 0 && !pts_xy) || npts < 0) return fail(HPS_ERR_INVALID_ARG, "tree or points missing");
+  if (levels < 0 || levels > 12) return fail(HPS_ERR_INVALID_ARG, "levels must be in [0, 12]");
+  long long span = 0;
+  for (const Box& b : tree->t.boxes) span = std::max<long long>(span, std::max(b.i1, b.j1));
+  if ((span << levels) > (1ll << 28)) return fail(HPS_ERR_INVALID_ARG, "refinement too deep for this tree");
+  hps_tree* t = new (std::nothrow) hps_tree();
+  if (!t) return fail(HPS_ERR_OOM, "host allocation failed");
+  refine_tree(tree->t, pts_xy, npts, levels, t->t);
+  *out = t;
   return HPS_OK;
 }
 
@@ -1151,8 +1286,25 @@ std::string setup_host(hps_handle* h, const Tree& tree, int p, const hps_opts& o
   h->ne = 4 * (p - 1);
   h->n_leaf = (int)h->tree.leaves.size();
   build_ref_tables(p, h->q, h->rt);
-  build_node_sets(h->tree, h->q, h->ns);
+  build_node_sets(h->tree, h->q, h->ns, h->rt.xg);
   h->n_bdry = (int)h->ns.boundary.size();
+  bool coarsened = false;
+  for (const Coarsen& c : h->ns.co) coarsened = coarsened || c.active;
+  if (coarsened && o.precision == HPS_MIXED)
+    return "HPS_MIXED needs a tree without coarse-fine interfaces (its residual checks only matching edges)";
+  // every Gaussian node must end up in some merge's J3, the domain boundary, or a
+  // coarsened side: a node owned by one leaf that is none of these is an interface the
+  // refinement rule left unmatched
+  {
+    std::vector<char> seen((size_t)h->ns.n_gauss, 0);
+    for (size_t b = 0; b < h->tree.boxes.size(); ++b) {
+      for (int g : h->ns.J3[b]) seen[g] = 1;
+      for (int g : h->ns.co[b].fine) seen[g] = 1;
+    }
+    for (int g : h->ns.boundary) seen[g] = 1;
+    for (int g = 0; g < h->ns.n_gauss; ++g)
+      if (!seen[g]) return "mesh has an unmatched interface (refined leaves next to leaves more than one size larger)";
+  }
   for (size_t b = 0; b < h->tree.boxes.size(); ++b)
     if (h->tree.boxes[b].leaf < 0 && h->ns.J3[b].empty()) return "a merge has no shared edge";
   return std::string();
@@ -1424,12 +1576,14 @@ int hps_adjoint(hps_handle* h, const double* ubar_in, int nrhs, const double* u,
       TIMED("gather_reduce", 0, 0, launch_gather_reduce<double>(lv.wcopy_tab, lv.n_wcopy, ub, VB, nrhs, 0, s));
       gemmTp("merge_S", lv.adjS, ub, w.UB, 0.0);
       TIMED("gather_reduce", 0, 0, launch_gather_reduce<double>(lv.reduce_tab, lv.n_reduce, w.UB, ub, nrhs, 1, s));
+      if (lv.aidown.n) gemmT("refine_down", lv.aidown, ub, ub, 1.0);
     }
     // 3. boundary data
     if (fbar) TIMED("gather_reduce", 0, 0, launch_gather_reduce<double>(h->fbar_tab, h->n_bdry, ub, fbar, nrhs, 0, s));
     // 4. merge-up transposed, top-down
     for (int L = H - 1; L >= 0; --L) {
       Level& lv = h->levels[L];
+      if (lv.aiup.n) gemmT("coarsen_up", lv.aiup, VB, VB, 0.0);
       gemmTp("merge_X", lv.adjM, VB, w.d64, 0.0);
       TIMED("down_scatter", 0, 0, launch_down_scatter<double>(lv.ds, (int)lv.boxes.size(), lv.ds_maxrows, VB, w.d64, nullptr, idx, nrhs, s));
     }

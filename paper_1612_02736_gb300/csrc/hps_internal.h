@@ -2,7 +2,9 @@
 // per-level schedules and the kernel launchers.  Nothing here crosses the C ABI.
 #pragma once
 
+#include <array>
 #include <cstdint>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -16,36 +18,54 @@ namespace hps {
 // Host tree (Sec. 2).  Boxes are numbered breadth-first from the root, so a parent has a
 // smaller id than its children; the first child is the W (or S) half ("alpha").
 struct Box {
-  double x0, y0, x1, y1;
-  int i0, i1, j0, j1;   // leaf-index span [i0,i1) x [j0,j1)
+  int i0 = 0, i1 = 0, j0 = 0, j1 = 0;  // span in finest-grid units
+  double x0 = 0, y0 = 0, x1 = 0, y1 = 0;
   int leaf = -1;        // leaf index or -1
   int child[2] = {-1, -1};
   int parent = -1;
   int height = 0;       // 0 for leaves, 1 + max(child heights) for parents
+  bool refined = false; // root of a 2 x 2 refinement of a former leaf (Sec. 6)
 };
 
 struct Tree {
-  double X0, Y0, X1, Y1;
-  int nx, ny;
+  double ox = 0, oy = 0, ux = 1, uy = 1;  // origin and finest-grid unit
   std::vector<Box> boxes;
-  std::vector<int> leaves;             // leaf index -> box id
-  std::vector<int> leaf_edges;         // 4 per leaf (S, E, N, W): edge id
+  std::vector<int> leaves;             // leaf index -> box id (ordered by lower-left corner)
+  std::vector<int> leaf_edges;         // 4 per leaf (S, E, N, W): edge segment id
   int n_edges = 0;
   std::vector<int> edge_owners;        // 2 per edge: leaf*4+side of the owners, -1 if none
+  std::vector<std::array<int, 4>> edge_keys;    // (orient 0=h/1=v, line, lo, hi)
+  std::map<std::array<int, 4>, int> edge_of;    // key -> edge id
   int height = 0;
+};
+
+int make_uniform_tree(double x0, double y0, double x1, double y1, int nx, int ny, Tree& t);
+int make_mask_tree(double x0, double y0, double h, int nx, int ny, const uint8_t* mask, Tree& t);
+int refine_tree(const Tree& in, const double* pts, int npts, int levels, Tree& out);
+
+// Coarsened sides of a refined parent (Sec. 6.3): dense interpolation operators.
+struct Coarsen {
+  bool active = false;
+  std::vector<double> Pup;    // |ge_old| x |ge|  (fine <- coarse; identity on kept nodes)
+  std::vector<double> Pdown;  // |ge| x |ge_old|  (coarse <- fine)
+  std::vector<double> Pupc;   // |fine| x |coarse|: P_up rows of the fine nodes, coarse columns
+  std::vector<int> fine;      // node ids replaced by the coarsening (in ge_old order)
+  std::vector<int> coarse;    // coarse node ids (in ge order)
 };
 
 // Gaussian node bookkeeping for a given q: box exterior lists and merge index sets.
 struct NodeSets {
   int q = 0;
   int n_gauss = 0;
-  std::vector<std::vector<int>> ge;    // per box: exterior Gaussian node ids (I_ge)
-  std::vector<std::vector<int>> J3;    // per parent: shared-edge node ids (alpha order)
-  std::vector<int> n1;                 // per parent: |J1|
-  std::vector<int> boundary;           // domain-boundary node ids, ascending
+  std::vector<std::vector<int>> ge;     // per box: exterior ids as seen by the parent (I_ge)
+  std::vector<std::vector<int>> ge_old; // per parent: J1 ++ J2 (before coarsening)
+  std::vector<std::vector<int>> J3;     // per parent: shared-edge node ids (alpha order)
+  std::vector<int> n1;                  // per parent: |J1|
+  std::vector<Coarsen> co;              // per box
+  std::vector<int> boundary;            // domain-boundary node ids, ascending
 };
 
-void build_node_sets(const Tree& t, int q, NodeSets& ns);
+void build_node_sets(const Tree& t, int q, NodeSets& ns, const std::vector<double>& xg);
 
 // ---------------------------------------------------------------------------------------
 // Reference-element tables for (p, q) on [-1, 1] (Sec. 3.1-3.4).
@@ -162,6 +182,15 @@ struct MergeDesc {
 template <typename T, typename TT>
 void launch_merge_assemble(const MergeDesc* d, int nmat, int maxR, const TT* tstore,
                            const int* pos, T* work, cudaStream_t s);
+
+// Small batched dense products C = A B (row-major, per-matrix offsets from three bases),
+// used for the coarsened DtN maps T_new = P_down T P_up of refined parents.
+struct BGemm {
+  long long a_off, b_off, c_off;
+  int M, N, K, lda, ldb, ldc;
+};
+void launch_bgemm(const BGemm* d, int n, int maxM, int maxN, const double* A, const double* B, double* C,
+                  cudaStream_t s);
 
 // Batched gathered products.
 template <typename TA, typename TV>

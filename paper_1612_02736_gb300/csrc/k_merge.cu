@@ -44,7 +44,35 @@ __global__ void __launch_bounds__(256) merge_assemble_kernel(const MergeDesc* __
   }
 }
 
+__global__ void __launch_bounds__(256) bgemm_kernel(const BGemm* __restrict__ d, const double* __restrict__ A,
+                                                    const double* __restrict__ B, double* __restrict__ C) {
+  const BGemm g = d[blockIdx.y];
+  const int tilesN = (g.N + 15) / 16;
+  const int ti = blockIdx.x / tilesN, tj = blockIdx.x - (blockIdx.x / tilesN) * tilesN;
+  const int i = ti * 16 + (threadIdx.x >> 4), j = tj * 16 + (threadIdx.x & 15);
+  if (ti * 16 >= g.M) return;
+  __shared__ double As[16][17], Bs[16][17];
+  double acc = 0.0;
+  for (int k0 = 0; k0 < g.K; k0 += 16) {
+    const int r = threadIdx.x >> 4, c = threadIdx.x & 15;
+    const int ai = ti * 16 + r, ak = k0 + c, bk = k0 + r, bj = tj * 16 + c;
+    As[r][c] = (ai < g.M && ak < g.K) ? A[g.a_off + (long long)ai * g.lda + ak] : 0.0;
+    Bs[r][c] = (bk < g.K && bj < g.N) ? B[g.b_off + (long long)bk * g.ldb + bj] : 0.0;
+    __syncthreads();
+    for (int k = 0; k < 16; ++k) acc += As[threadIdx.x >> 4][k] * Bs[k][threadIdx.x & 15];
+    __syncthreads();
+  }
+  if (i < g.M && j < g.N) C[g.c_off + (long long)i * g.ldc + j] = acc;
+}
+
 }  // namespace
+
+void launch_bgemm(const BGemm* d, int n, int maxM, int maxN, const double* A, const double* B, double* C,
+                  cudaStream_t s) {
+  if (n <= 0) return;
+  const int tiles = ((maxM + 15) / 16) * ((maxN + 15) / 16);
+  bgemm_kernel<<<dim3(tiles, n), 256, 0, s>>>(d, A, B, C);
+}
 
 template <typename T, typename TT>
 void launch_merge_assemble(const MergeDesc* d, int nmat, int maxR, const TT* tstore, const int* pos,

@@ -1,7 +1,9 @@
 // Host-side tables: reference-element operators (Sec. 3.1-3.4) and the box tree with its
 // Gaussian node bookkeeping (Sec. 2, Sec. 4, Sec. 5.1).  Plain C++17, no CUDA calls.
 #include <algorithm>
+#include <array>
 #include <cmath>
+#include <cstdint>
 #include <map>
 #include <set>
 #include <stdexcept>
@@ -190,8 +192,88 @@ void build_ref_tables(int p, int q, RefTables& rt) {
 }
 
 // ---------------------------------------------------------------------------------------
+// Trees (Sec. 2, Sec. 6).  Geometry is in integer units of the finest grid, so edges
+// compare exactly.  Trees are built as "proto" nodes, then numbered breadth-first.
 
-static void finish_tree(Tree& t) {
+namespace {
+
+struct PNode {
+  int i0, i1, j0, j1;
+  int c0 = -1, c1 = -1;
+  bool refined = false;
+};
+
+// Subtree of the cell region [i0,i1) x [j0,j1) restricted to present cells: the box is
+// cut across its longer side (vertically on ties), empty halves are dropped.
+int bisect(std::vector<PNode>& P, int i0, int i1, int j0, int j1, const std::vector<uint8_t>& present, int nx) {
+  bool any = false;
+  for (int j = j0; j < j1 && !any; ++j)
+    for (int i = i0; i < i1; ++i)
+      if (present[(size_t)j * nx + i]) {
+        any = true;
+        break;
+      }
+  if (!any) return -1;
+  const int wi = i1 - i0, wj = j1 - j0;
+  if (wi == 1 && wj == 1) {
+    P.push_back(PNode{i0, i1, j0, j1});
+    return (int)P.size() - 1;
+  }
+  int a, b;
+  if (wi >= wj) {
+    const int im = i0 + wi / 2;
+    a = bisect(P, i0, im, j0, j1, present, nx);
+    b = bisect(P, im, i1, j0, j1, present, nx);
+  } else {
+    const int jm = j0 + wj / 2;
+    a = bisect(P, i0, i1, j0, jm, present, nx);
+    b = bisect(P, i0, i1, jm, j1, present, nx);
+  }
+  if (a < 0) return b;
+  if (b < 0) return a;
+  PNode n{std::min(P[a].i0, P[b].i0), std::max(P[a].i1, P[b].i1), std::min(P[a].j0, P[b].j0),
+          std::max(P[a].j1, P[b].j1)};
+  n.c0 = a;
+  n.c1 = b;
+  P.push_back(n);
+  return (int)P.size() - 1;
+}
+
+void finalize(const std::vector<PNode>& P, int root, double ox, double oy, double ux, double uy, Tree& t) {
+  t = Tree();
+  t.ox = ox;
+  t.oy = oy;
+  t.ux = ux;
+  t.uy = uy;
+  std::vector<int> map(P.size(), -1);
+  std::vector<int> queue{root};
+  std::vector<int> order;
+  while (!queue.empty()) {
+    std::vector<int> nq;
+    for (int pi : queue) {
+      map[pi] = (int)order.size();
+      order.push_back(pi);
+      if (P[pi].c0 >= 0) {
+        nq.push_back(P[pi].c0);
+        nq.push_back(P[pi].c1);
+      }
+    }
+    queue.swap(nq);
+  }
+  t.boxes.resize(order.size());
+  for (size_t k = 0; k < order.size(); ++k) {
+    const PNode& n = P[order[k]];
+    Box& b = t.boxes[k];
+    b.i0 = n.i0; b.i1 = n.i1; b.j0 = n.j0; b.j1 = n.j1;
+    b.x0 = ox + n.i0 * ux; b.x1 = ox + n.i1 * ux; b.y0 = oy + n.j0 * uy; b.y1 = oy + n.j1 * uy;
+    b.refined = n.refined;
+    if (n.c0 >= 0) {
+      b.child[0] = map[n.c0];
+      b.child[1] = map[n.c1];
+      t.boxes[b.child[0]].parent = (int)k;
+      t.boxes[b.child[1]].parent = (int)k;
+    }
+  }
   // heights
   for (int b = (int)t.boxes.size() - 1; b >= 0; --b) {
     Box& bx = t.boxes[b];
@@ -199,21 +281,28 @@ static void finish_tree(Tree& t) {
       bx.height = 1 + std::max(t.boxes[bx.child[0]].height, t.boxes[bx.child[1]].height);
   }
   t.height = t.boxes.empty() ? 0 : t.boxes[0].height;
-  // edges: canonical numbering, leaves in order, sides S, E, N, W
+  // leaves ordered by lower-left corner (y, then x): row-major on uniform grids
+  for (size_t b = 0; b < t.boxes.size(); ++b)
+    if (t.boxes[b].child[0] < 0) t.leaves.push_back((int)b);
+  std::sort(t.leaves.begin(), t.leaves.end(), [&](int a, int b) {
+    const Box &A = t.boxes[a], &B = t.boxes[b];
+    return A.j0 != B.j0 ? A.j0 < B.j0 : A.i0 < B.i0;
+  });
+  for (size_t lf = 0; lf < t.leaves.size(); ++lf) t.boxes[t.leaves[lf]].leaf = (int)lf;
+  // edge segments: canonical numbering, leaves in order, sides S, E, N, W
   const int nl = (int)t.leaves.size();
   t.leaf_edges.assign((size_t)4 * nl, -1);
-  std::map<std::tuple<int, int, int>, int> key2edge;  // (orient, line, start)
-  t.edge_owners.clear();
   for (int lf = 0; lf < nl; ++lf) {
     const Box& b = t.boxes[t.leaves[lf]];
-    std::tuple<int, int, int> keys[4] = {
-        {0, b.j0, b.i0}, {1, b.i1, b.j0}, {0, b.j1, b.i0}, {1, b.i0, b.j0}};
+    const std::array<int, 4> keys[4] = {{0, b.j0, b.i0, b.i1}, {1, b.i1, b.j0, b.j1},
+                                        {0, b.j1, b.i0, b.i1}, {1, b.i0, b.j0, b.j1}};
     for (int s = 0; s < 4; ++s) {
-      auto it = key2edge.find(keys[s]);
+      auto it = t.edge_of.find(keys[s]);
       int e;
-      if (it == key2edge.end()) {
+      if (it == t.edge_of.end()) {
         e = t.n_edges++;
-        key2edge[keys[s]] = e;
+        t.edge_of[keys[s]] = e;
+        t.edge_keys.push_back(keys[s]);
         t.edge_owners.push_back(lf * 4 + s);
         t.edge_owners.push_back(-1);
       } else {
@@ -225,67 +314,111 @@ static void finish_tree(Tree& t) {
   }
 }
 
-int make_uniform_tree(double x0, double y0, double x1, double y1, int nx, int ny, Tree& t) {
-  t = Tree();
-  t.X0 = x0; t.Y0 = y0; t.X1 = x1; t.Y1 = y1;
-  t.nx = nx; t.ny = ny;
-  t.leaves.assign((size_t)nx * ny, -1);
-  auto xs = [&](int i) { return x0 + (x1 - x0) * (double)i / (double)nx; };
-  auto ys = [&](int j) { return y0 + (y1 - y0) * (double)j / (double)ny; };
-  struct Q { int parent, i0, i1, j0, j1; };
-  std::vector<Q> queue{{-1, 0, nx, 0, ny}};
-  while (!queue.empty()) {
-    std::vector<Q> nq;
-    for (const Q& e : queue) {
-      Box b;
-      b.i0 = e.i0; b.i1 = e.i1; b.j0 = e.j0; b.j1 = e.j1;
-      b.x0 = xs(e.i0); b.x1 = xs(e.i1); b.y0 = ys(e.j0); b.y1 = ys(e.j1);
-      b.parent = e.parent;
-      const int id = (int)t.boxes.size();
-      t.boxes.push_back(b);
-      if (e.parent >= 0) {
-        Box& pb = t.boxes[e.parent];
-        if (pb.child[0] < 0) pb.child[0] = id; else pb.child[1] = id;
-      }
-      const int wi = e.i1 - e.i0, wj = e.j1 - e.j0;
-      if (wi == 1 && wj == 1) {
-        t.boxes[id].leaf = e.j0 * nx + e.i0;
-        t.leaves[(size_t)e.j0 * nx + e.i0] = id;
-        continue;
-      }
-      if (wi >= wj) {  // vertical cut (ties vertical)
-        const int im = e.i0 + wi / 2;
-        nq.push_back({id, e.i0, im, e.j0, e.j1});
-        nq.push_back({id, im, e.i1, e.j0, e.j1});
-      } else {
-        const int jm = e.j0 + wj / 2;
-        nq.push_back({id, e.i0, e.i1, e.j0, jm});
-        nq.push_back({id, e.i0, e.i1, jm, e.j1});
-      }
-    }
-    queue.swap(nq);
+void to_protos(const Tree& t, int b, int scale, std::vector<PNode>& P, std::vector<int>& idx) {
+  const Box& bx = t.boxes[b];
+  PNode n{bx.i0 * scale, bx.i1 * scale, bx.j0 * scale, bx.j1 * scale};
+  n.refined = bx.refined;
+  P.push_back(n);
+  const int me = (int)P.size() - 1;
+  idx[b] = me;
+  if (bx.child[0] >= 0) {
+    to_protos(t, bx.child[0], scale, P, idx);
+    to_protos(t, bx.child[1], scale, P, idx);
+    P[me].c0 = idx[bx.child[0]];
+    P[me].c1 = idx[bx.child[1]];
   }
-  finish_tree(t);
+}
+
+}  // namespace
+
+int make_uniform_tree(double x0, double y0, double x1, double y1, int nx, int ny, Tree& t) {
+  std::vector<uint8_t> all((size_t)nx * ny, 1);
+  std::vector<PNode> P;
+  const int root = bisect(P, 0, nx, 0, ny, all, nx);
+  finalize(P, root, x0, y0, (x1 - x0) / nx, (y1 - y0) / ny, t);
   return 0;
 }
 
-void build_node_sets(const Tree& t, int q, NodeSets& ns) {
+int make_mask_tree(double x0, double y0, double h, int nx, int ny, const uint8_t* mask, Tree& t) {
+  std::vector<uint8_t> present(mask, mask + (size_t)nx * ny);
+  std::vector<PNode> P;
+  const int root = bisect(P, 0, nx, 0, ny, present, nx);
+  if (root < 0) return 1;
+  finalize(P, root, x0, y0, h, h, t);
+  return 0;
+}
+
+// Sec. 6.1: at each level every leaf whose distance d to one of the points satisfies
+// d <= sqrt(2) l (side 2 l) is split 2 x 2: a vertical cut into W/E halves, each cut
+// horizontally into S/N leaves; the former leaf is marked as a refined parent.
+int refine_tree(const Tree& in, const double* pts, int npts, int levels, Tree& out) {
+  const int scale = 1 << levels;
+  std::vector<PNode> P;
+  std::vector<int> idx(in.boxes.size(), -1);
+  to_protos(in, 0, scale, P, idx);
+  const double ux = in.ux / scale, uy = in.uy / scale;
+  for (int lev = 0; lev < levels; ++lev) {
+    const size_t n0 = P.size();
+    for (size_t k = 0; k < n0; ++k) {
+      if (P[k].c0 >= 0) continue;
+      const double bx0 = in.ox + P[k].i0 * ux, bx1 = in.ox + P[k].i1 * ux;
+      const double by0 = in.oy + P[k].j0 * uy, by1 = in.oy + P[k].j1 * uy;
+      const double l = 0.5 * std::max(bx1 - bx0, by1 - by0);
+      bool close = false;
+      for (int pi = 0; pi < npts && !close; ++pi) {
+        const double dx = std::max(std::max(bx0 - pts[2 * pi], 0.0), pts[2 * pi] - bx1);
+        const double dy = std::max(std::max(by0 - pts[2 * pi + 1], 0.0), pts[2 * pi + 1] - by1);
+        close = std::hypot(dx, dy) <= std::sqrt(2.0) * l;
+      }
+      if (!close) continue;
+      const int i0 = P[k].i0, i1 = P[k].i1, j0 = P[k].j0, j1 = P[k].j1;
+      const int im = (i0 + i1) / 2, jm = (j0 + j1) / 2;
+      const int base = (int)P.size();
+      P.push_back(PNode{i0, im, j0, jm});  // W-S
+      P.push_back(PNode{i0, im, jm, j1});  // W-N
+      P.push_back(PNode{im, i1, j0, jm});  // E-S
+      P.push_back(PNode{im, i1, jm, j1});  // E-N
+      PNode w{i0, im, j0, j1}, e{im, i1, j0, j1};
+      w.c0 = base; w.c1 = base + 1;
+      e.c0 = base + 2; e.c1 = base + 3;
+      P.push_back(w);
+      P.push_back(e);
+      P[k].c0 = base + 4;
+      P[k].c1 = base + 5;
+      P[k].refined = true;
+    }
+  }
+  finalize(P, 0, in.ox, in.oy, ux, uy, out);
+  return 0;
+}
+
+void build_node_sets(const Tree& t, int q, NodeSets& ns, const std::vector<double>& xg) {
   ns = NodeSets();
   ns.q = q;
   ns.n_gauss = t.n_edges * q;
   const int nb = (int)t.boxes.size();
   ns.ge.assign(nb, {});
+  ns.ge_old.assign(nb, {});
   ns.J3.assign(nb, {});
   ns.n1.assign(nb, 0);
+  ns.co.assign(nb, Coarsen());
+  // position of node (edge e, index k) along its segment, in physical units
+  auto pos_along = [&](int node) {
+    const std::array<int, 4>& key = t.edge_keys[node / q];
+    const double u = key[0] == 0 ? t.ux : t.uy;
+    const double o = key[0] == 0 ? t.ox : t.oy;
+    const double a = o + key[2] * u, b = o + key[3] * u;
+    return a + 0.5 * (b - a) * (xg[node % q] + 1.0);
+  };
   for (int b = nb - 1; b >= 0; --b) {
     const Box& bx = t.boxes[b];
     if (bx.leaf >= 0) {
       std::vector<int>& ge = ns.ge[b];
-      ge.reserve(4 * q);
       for (int s = 0; s < 4; ++s) {
         const int e = t.leaf_edges[(size_t)4 * bx.leaf + s];
         for (int k = 0; k < q; ++k) ge.push_back(e * q + k);
       }
+      ns.ge_old[b] = ge;
       continue;
     }
     const std::vector<int>& ga = ns.ge[bx.child[0]];
@@ -302,14 +435,93 @@ void build_node_sets(const Tree& t, int q, NodeSets& ns) {
       if (!s3.count(g)) J2.push_back(g);
     ns.J3[b] = J3;
     ns.n1[b] = (int)J1.size();
-    std::vector<int>& ge = ns.ge[b];
-    ge = J1;
-    ge.insert(ge.end(), J2.begin(), J2.end());
+    std::vector<int>& old = ns.ge_old[b];
+    old = J1;
+    old.insert(old.end(), J2.begin(), J2.end());
+    ns.ge[b] = old;
+    if (!bx.refined) continue;
+    // Sec. 6.3: coarsen every side that faces a leaf of this box's size
+    std::set<int> inold(old.begin(), old.end());
+    const std::array<int, 4> keys[4] = {{0, bx.j0, bx.i0, bx.i1}, {1, bx.i1, bx.j0, bx.j1},
+                                        {0, bx.j1, bx.i0, bx.i1}, {1, bx.i0, bx.j0, bx.j1}};
+    std::vector<int> cseg(4, -1);
+    for (int s = 0; s < 4; ++s) {
+      auto it = t.edge_of.find(keys[s]);
+      if (it == t.edge_of.end()) continue;
+      bool mine = false;
+      for (int k = 0; k < q; ++k) mine = mine || inold.count(it->second * q + k);
+      if (!mine) cseg[s] = it->second;
+    }
+    if (cseg[0] < 0 && cseg[1] < 0 && cseg[2] < 0 && cseg[3] < 0) continue;
+    auto side_of = [&](int node) {
+      const std::array<int, 4>& key = t.edge_keys[node / q];
+      if (key[0] == 0) return key[1] == bx.j0 ? 0 : 2;
+      return key[1] == bx.i1 ? 1 : 3;
+    };
+    Coarsen& C = ns.co[b];
+    std::vector<int> nw;
+    for (int g : old)
+      if (cseg[side_of(g)] < 0) nw.push_back(g);
+    for (int s = 0; s < 4; ++s)
+      if (cseg[s] >= 0)
+        for (int k = 0; k < q; ++k) nw.push_back(cseg[s] * q + k);
+    std::unordered_map<int, int> po, pn;
+    for (size_t k = 0; k < old.size(); ++k) po[old[k]] = (int)k;
+    for (size_t k = 0; k < nw.size(); ++k) pn[nw[k]] = (int)k;
+    const int ko = (int)old.size(), kn = (int)nw.size();
+    C.Pup.assign((size_t)ko * kn, 0.0);
+    C.Pdown.assign((size_t)kn * ko, 0.0);
+    for (int g : old)
+      if (cseg[side_of(g)] < 0) {
+        C.Pup[(size_t)po[g] * kn + pn[g]] = 1.0;
+        C.Pdown[(size_t)pn[g] * ko + po[g]] = 1.0;
+      }
+    for (int s = 0; s < 4; ++s) {
+      if (cseg[s] < 0) continue;
+      std::vector<double> cpts(q);
+      for (int k = 0; k < q; ++k) cpts[k] = pos_along(cseg[s] * q + k);
+      std::vector<int> fine;
+      for (int g : old)
+        if (side_of(g) == s) fine.push_back(g);
+      // P_up: every fine node from the one polynomial through the coarse nodes
+      std::vector<double> fpts;
+      for (int g : fine) fpts.push_back(pos_along(g));
+      const std::vector<double> Iu = interp(cpts, fpts);
+      for (size_t r = 0; r < fine.size(); ++r)
+        for (int k = 0; k < q; ++k) C.Pup[(size_t)po[fine[r]] * kn + pn[cseg[s] * q + k]] = Iu[r * q + k];
+      // P_down: every coarse node from the fine segment(s) containing it (mean on a shared end)
+      std::vector<int> fsegs;
+      for (int g : fine)
+        if (std::find(fsegs.begin(), fsegs.end(), g / q) == fsegs.end()) fsegs.push_back(g / q);
+      for (int k = 0; k < q; ++k) {
+        const double tc = cpts[k];
+        std::vector<int> hits;
+        for (int e : fsegs) {
+          const std::array<int, 4>& key = t.edge_keys[e];
+          const double u = key[0] == 0 ? t.ux : t.uy, o = key[0] == 0 ? t.ox : t.oy;
+          if (o + key[2] * u <= tc && tc <= o + key[3] * u) hits.push_back(e);
+        }
+        for (int e : hits) {
+          std::vector<double> fp(q);
+          for (int i = 0; i < q; ++i) fp[i] = pos_along(e * q + i);
+          const std::vector<double> row = interp(fp, std::vector<double>{tc});
+          for (int i = 0; i < q; ++i)
+            C.Pdown[(size_t)pn[cseg[s] * q + k] * ko + po[e * q + i]] += row[i] / (double)hits.size();
+        }
+      }
+      for (int g : fine) C.fine.push_back(g);
+      for (int k = 0; k < q; ++k) C.coarse.push_back(cseg[s] * q + k);
+    }
+    // rows of P_up for the fine nodes, columns for the coarse nodes
+    const int nf = (int)C.fine.size(), nc = (int)C.coarse.size();
+    C.Pupc.assign((size_t)nf * nc, 0.0);
+    for (int r = 0; r < nf; ++r)
+      for (int c = 0; c < nc; ++c) C.Pupc[(size_t)r * nc + c] = C.Pup[(size_t)po[C.fine[r]] * kn + pn[C.coarse[c]]];
+    ns.ge[b] = nw;
+    C.active = true;
   }
-  ns.boundary.clear();
-  for (int e = 0; e < t.n_edges; ++e)
-    if (t.edge_owners[(size_t)2 * e + 1] < 0)
-      for (int k = 0; k < q; ++k) ns.boundary.push_back(e * q + k);
+  ns.boundary = ns.ge[0];
+  std::sort(ns.boundary.begin(), ns.boundary.end());
 }
 
 }  // namespace hps

@@ -63,6 +63,31 @@ class Tree:
         N.check(lib.hps_tree_uniform(x0, y0, x1, y1, nx, ny, C.byref(out)))
         return cls(out, nx, ny, (x0, y0, x1, y1))
 
+    @classmethod
+    def mask(cls, x0, y0, h, mask):
+        """Union of squares of side h: mask[j][i] != 0 keeps the square (i, j)."""
+        lib = N.load()
+        m = np.ascontiguousarray(np.asarray(mask, dtype=np.uint8))
+        ny, nx = m.shape
+        out = C.c_void_p()
+        N.check(lib.hps_tree_mask(x0, y0, h, nx, ny, m.ctypes.data_as(C.c_void_p), C.byref(out)))
+        return cls(out, nx, ny, (x0, y0, x0 + nx * h, y0 + ny * h))
+
+    @classmethod
+    def l_shape(cls, n):
+        """[-1,1]^2 minus [0,1] x [-1,0] on a 2n x 2n grid of squares."""
+        m = np.ones((2 * n, 2 * n), dtype=np.uint8)
+        m[:n, n:] = 0
+        return cls.mask(-1.0, -1.0, 1.0 / n, m)
+
+    def refine(self, points, levels):
+        """A new tree refined `levels` times toward the points (Sec. 6.1)."""
+        lib = N.load()
+        pts = np.ascontiguousarray(np.asarray(points, dtype=np.float64).reshape(-1, 2))
+        out = C.c_void_p()
+        N.check(lib.hps_tree_refine(self._ptr, pts.ctypes.data_as(C.c_void_p), len(pts), levels, C.byref(out)))
+        return Tree(out, self.nx, self.ny, self.rect)
+
     def info(self, q):
         vals = [C.c_int() for _ in range(5)]
         N.check(N.load().hps_tree_info(self._ptr, q, *[C.byref(v) for v in vals]))

@@ -131,3 +131,24 @@ def smooth_directions(X, Y, n=10, seed_offset=700, fields=6):
         v = np.array([FourierSeries(rng(seed_offset + 16 * k + j))(X, Y) for j in range(fields)])
         out.append(v / np.linalg.norm(v))
     return out
+
+
+def lshape_load_centre(seed_offset=300):
+    """Seeded centre of the point load on the L-shaped domain [-1,1]^2 minus [0,1]x[-1,0]:
+    uniform in the L, at distance > 0.1 from its boundary."""
+    gen = rng(seed_offset)
+    while True:
+        x, y = gen.uniform(-1.0, 1.0, 2)
+        in_l = not (x > 0.0 and y < 0.0)
+        far = min(x + 1.0, 1.0 - x, y + 1.0, 1.0 - y) > 0.1
+        if x > 0.0:
+            far = far and y > 0.1
+        if y < 0.0:
+            far = far and x < -0.1
+        if in_l and far:
+            return float(x), float(y)
+
+
+def point_load(x, y, centre, width=1e-3):
+    """g = exp(-|x - centre|^2 / width^2) (a Gaussian point load of the given width)."""
+    return np.exp(-((x - centre[0]) ** 2 + (y - centre[1]) ** 2) / width ** 2)

@@ -142,3 +142,61 @@ def test_plan_rejects_bad_options(lib):
     opts.q = 40
     assert lib.hps_plan_check(t, 8, C.byref(opts)) == 1
     lib.hps_tree_destroy(t)
+
+
+def _nodes(lib, t, p, q, which):
+    cnt = C.c_int64()
+    assert lib.hps_nodes(t, p, q, which, None, C.byref(cnt)) == 0
+    xy = np.zeros((cnt.value, 2))
+    assert lib.hps_nodes(t, p, q, which, xy.ctypes.data_as(C.c_void_p), C.byref(cnt)) == 0
+    return xy
+
+
+def _refined_pair(lib, kind, p):
+    q = p - 1
+    if kind == "uniform-refined":
+        t = _tree(lib, 4, 4)
+        o = tr.refine_tree(tr.uniform_tree(0, 0, 1, 1, 4, 4, q), [(0.37, 0.58), (0.9, 0.1)], 2)
+        pts = np.array([[0.37, 0.58], [0.9, 0.1]])
+        levels = 2
+    else:
+        m = np.ones((4, 4), dtype=np.uint8)
+        m[:2, 2:] = 0
+        t = C.c_void_p()
+        assert lib.hps_tree_mask(-1.0, -1.0, 0.5, 4, 4, m.ctypes.data_as(C.c_void_p), C.byref(t)) == 0
+        o = tr.refine_tree(tr.l_shape_tree(2, q), [(0.0, 0.0)], 3)
+        pts = np.array([[0.0, 0.0]])
+        levels = 3
+    r = C.c_void_p()
+    assert lib.hps_tree_refine(t, pts.ctypes.data_as(C.c_void_p), len(pts), levels, C.byref(r)) == 0
+    lib.hps_tree_destroy(t)
+    return r, o
+
+
+@pytest.mark.parametrize("kind", ["uniform-refined", "l-shape-refined"])
+def test_refined_and_mask_trees_match_oracle(lib, kind):
+    p = 8
+    q = p - 1
+    r, o = _refined_pair(lib, kind, p)
+    vals = [C.c_int() for _ in range(5)]
+    assert lib.hps_tree_info(r, q, *[C.byref(v) for v in vals]) == 0
+    assert vals[0].value == o.n_leaves and vals[3].value == o.n_gauss and vals[4].value == len(o.boundary)
+    X, Y = [], []
+    for lf in range(o.n_leaves):
+        x0, y0, x1, y1 = o.leaf_rect(lf)
+        x, y = sp.leaf_cheb_points(x0, y0, x1 - x0, y1 - y0, p)
+        X.append(x)
+        Y.append(y)
+    cheb = _nodes(lib, r, p, q, 0)
+    assert np.max(np.abs(cheb[:, 0] - np.concatenate(X))) < 1e-13
+    assert np.max(np.abs(cheb[:, 1] - np.concatenate(Y))) < 1e-13
+    gp = o.gauss_points()
+    assert np.max(np.abs(_nodes(lib, r, p, q, 2) - gp)) < 1e-13
+    assert np.max(np.abs(_nodes(lib, r, p, q, 1) - gp[o.boundary])) < 1e-13
+    assert lib.hps_plan_check(r, p, None) == 0, lib.hps_last_error()
+    from paper_1612_02736_gb300 import _native
+    opts = _native.hps_opts()
+    lib.hps_opts_default(C.byref(opts))
+    opts.precision = 1
+    assert lib.hps_plan_check(r, p, C.byref(opts)) == 1   # mixed needs matching interfaces
+    lib.hps_tree_destroy(r)
