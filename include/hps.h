@@ -73,7 +73,10 @@ typedef struct {
 typedef struct {
   int precision;       /* HPS_FP64 or HPS_MIXED                                           */
   int q;               /* Gauss nodes per leaf side; 0 means p - 1 (Sec. 7)                */
-  int store_leaf_ops;  /* 1: keep leaf F, S, H (Sec. 5.2); 0 is reserved (must be 1)       */
+  int store_leaf_ops;  /* 1: keep leaf F, S, H (Sec. 5.2); 0: keep only the coefficients and
+                        * rebuild F, S, H chunk by chunk whenever a solve or adjoint needs
+                        * them (the storage-efficient variant of the Sec. 5.4 remark;
+                        * HPS_FP64 only)                                                    */
   double ir_tol;       /* HPS_MIXED: stop when max|du| <= ir_tol * max|u|; 0 means 1e-10   */
   int ir_max_iter;     /* HPS_MIXED: refinement steps allowed; 0 means 10                  */
   int fp64_top_levels; /* HPS_MIXED: number of top merge levels kept in FP64; -1 means 1   */

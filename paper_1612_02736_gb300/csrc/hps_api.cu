@@ -9,6 +9,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <unordered_map>
 #include <vector>
 
@@ -249,7 +250,17 @@ struct hps_handle {
   std::vector<Level> levels;  // index = height - 1
   ItemSet leafup, leafdown, lce;
   ItemSet adj_leafF, adj_leafS, adj_lce, adj_leafH;
-  double* coeffs_copy = nullptr;  // FP64 coefficients, kept for the mixed-precision residual
+  double* coeffs_copy = nullptr;  // FP64 coefficients (mixed-precision residual, leaf recomputation)
+  // leaf recomputation ("econ", store_leaf_ops = 0): leaf operators are rebuilt chunk by
+  // chunk whenever a sweep needs them (Sec. 5.4 remark)
+  bool econ = false;
+  int echunk = 0;                 // leaves per chunk
+  double* ework = nullptr;        // elimination workspace of one chunk
+  int* eperm = nullptr;
+  double* epinv = nullptr;
+  double* eprow = nullptr;
+  double* eops = nullptr;         // [F | S_ci] and H of one chunk
+  GJDesc* egd = nullptr;          // per-leaf descriptors with chunk-relative offsets
   int* leaf_reduce_tab = nullptr;
   int n_leaf_reduce = 0;
   int* fbar_tab = nullptr;
@@ -392,10 +403,20 @@ void make_plan(hps_handle* h, HostPlan& hp) {
   }
   // operator pool layout
   long long off = 0;
-  h->gl_base = off;
-  off += (long long)h->n_leaf * m * (m + nq);
-  h->h_base = off;
-  off += (long long)h->n_leaf * nq * m;
+  const long long gsz = (long long)m * (m + nq), hsz = (long long)nq * m;
+  h->econ = h->opts.store_leaf_ops == 0;
+  if (h->econ) {
+    // leaf operators live in a per-chunk buffer: about 512 MiB of operators and workspace
+    const long long per = (long long)(m + nq) * (m + nq) + gsz + hsz;
+    h->echunk = (int)std::max<long long>(1, std::min<long long>(h->n_leaf, (512ll << 20) / (per * 8)));
+    h->gl_base = 0;
+    h->h_base = (long long)h->echunk * gsz;
+  } else {
+    h->gl_base = off;
+    off += (long long)h->n_leaf * gsz;
+    h->h_base = off;
+    off += (long long)h->n_leaf * hsz;
+  }
   h->lce_base = off;
   off += (long long)h->ne * nq;
   h->mo.assign(nb, -1);
@@ -615,8 +636,9 @@ void make_plan(hps_handle* h, HostPlan& hp) {
                         &aH = hp.aH;
   for (int lf = 0; lf < h->n_leaf; ++lf) {
     const int b = t.leaves[lf];
-    const long long gl = h->gl_base + (long long)lf * m * (m + nq);
-    const long long hb = h->h_base + (long long)lf * nq * m;
+    const int slot = h->econ ? lf % h->echunk : lf;  // econ: offsets inside the chunk buffer
+    const long long gl = h->gl_base + (long long)slot * gsz;
+    const long long hb = h->h_base + (long long)slot * hsz;
     add_product(lup, hb, m, nq, m, m, lf * pp, h->off_ci, 0, -1, h->vrow[b], -1, -1, false);
     add_product(ldown, gl, m + nq, m, m + nq, m, lf * pp, h->off_ci, 0, h->off_ge[b], lf * pp, h->off_ci, -1, false);
     add_product(llce, h->lce_base, nq, h->ne, nq, nq, 0, h->off_ge[b], 0, -1, lf * pp, h->off_ce, -1, false);
@@ -779,13 +801,19 @@ std::string validate_plan(const hps_handle* h, const HostPlan& hp) {
   const std::vector<int>& idx = hp.idx;
   const long long ops = h->ops_elems, V = h->v_rows, D = h->d_rows, UB = h->ub_rows;
   const long long G = h->ns.n_gauss, LP = (long long)h->n_leaf * h->pp, LB = (long long)h->n_leaf * h->nq;
-  check_items(pc, idx, hp.lup, false, ops, LP, 0, V, 0, "leaf up");
-  check_items(pc, idx, hp.ldown, false, ops, LP, G, LP, 0, "leaf down");
+  const long long gsz = (long long)h->m * (h->m + h->nq), hsz = (long long)h->nq * h->m;
+  const long long lops = h->econ ? (long long)h->echunk * (gsz + hsz) : ops;  // econ: chunk buffer
+  check_items(pc, idx, hp.lup, false, lops, LP, 0, V, 0, "leaf up");
+  check_items(pc, idx, hp.ldown, false, lops, LP, G, LP, 0, "leaf down");
   check_items(pc, idx, hp.llce, false, ops, G, 0, LP, 0, "leaf exterior");
-  check_items(pc, idx, hp.aF, true, ops, LP, 0, LP, 0, "adjoint F");
-  check_items(pc, idx, hp.aS, true, ops, LP, 0, LB, 0, "adjoint S");
+  check_items(pc, idx, hp.aF, true, lops, LP, 0, LP, 0, "adjoint F");
+  check_items(pc, idx, hp.aS, true, lops, LP, 0, LB, 0, "adjoint S");
   check_items(pc, idx, hp.aL, true, ops, LP, 0, LB, 0, "adjoint L");
-  check_items(pc, idx, hp.aH, true, ops, V, 0, LP, 0, "adjoint H");
+  check_items(pc, idx, hp.aH, true, lops, V, 0, LP, 0, "adjoint H");
+  if (h->econ) {
+    for (auto* v : {&hp.lup, &hp.ldown, &hp.aF, &hp.aS, &hp.aH})
+      if (v->size() % (size_t)h->n_leaf) pc.fail("econ: leaf items are not uniform per leaf");
+  }
   check_tab(pc, hp.lred, G, LB, "leaf reduce");
   check_tab(pc, hp.ftab, h->n_bdry, G, "boundary gather");
   for (size_t k = 0; k + 4 < hp.pairs.size() + 1 && k < hp.pairs.size(); k += 5) {
@@ -960,10 +988,33 @@ void build_stage(hps_handle* h, const double* coeffs, cudaStream_t s) {
       dst.TL = h->ops64 + gl0; dst.TL_off_stride = (long long)m * R; dst.TL_ld = R;
       dst.TR = h->ops64 + gl0 + m; dst.TR_off_stride = (long long)m * R; dst.TR_ld = R;
       dst.BL = h->ops64 + h->h_base + (long long)l0 * nq * m; dst.BL_off_stride = (long long)nq * m; dst.BL_ld = m;
+      if (h->econ) dst.TL = dst.TR = dst.BL = nullptr;  // only T is kept; F, S, H are recomputed
       dst.BR = tstore + toff[h->tree.leaves[l0]]; dst.BR_off_stride = (long long)nq * nq; dst.BR_ld = nq;
       dst.sTL = 1.0; dst.sTR = -1.0; dst.sBL = -1.0;
       TIMED("gj_extract_f64", 0, (double)n * per_leaf * 8, launch_gj_extract<double, double>(dgd, n, R, work, perm, dst, s));
       CKL();
+    }
+    if (h->econ) {  // buffers for recomputing one chunk of leaves during the sweeps
+      const int E = h->echunk;
+      auto own = [&](size_t bytes) {
+        void* p = h->al.get(bytes, s);
+        h->owned.push_back({p, bytes});
+        return p;
+      };
+      h->ework = (double*)own((size_t)E * per_leaf * sizeof(double));
+      h->eperm = (int*)own((size_t)E * m * sizeof(int));
+      h->epinv = (double*)own((size_t)E * 256 * sizeof(double));
+      h->eprow = (double*)own((size_t)E * 16 * R * sizeof(double));
+      h->eops = (double*)own((size_t)E * ((size_t)m * R + (size_t)nq * m) * sizeof(double));
+      std::vector<GJDesc> eg(h->n_leaf);
+      for (int lf = 0; lf < h->n_leaf; ++lf) {
+        eg[lf].off = (long long)(lf % E) * per_leaf;
+        eg[lf].R = R;
+        eg[lf].K = m;
+        eg[lf].perm_off = (lf % E) * m;
+        eg[lf].box = h->tree.leaves[lf];
+      }
+      h->egd = upload(h->al, s, eg, h->owned);
     }
     // ---- merges, level by level
     const int H = h->tree.height;
@@ -971,7 +1022,7 @@ void build_stage(hps_handle* h, const double* coeffs, cudaStream_t s) {
       Level& lv = h->levels[L];
       const int nmat = (int)lv.boxes.size();
       std::vector<std::pair<int, int>> rk;
-      for (int b : lv.boxes) rk.push_back({h->k3[b] + h->k12[b], h->k3[b]});
+      for (int b : lv.boxes) rk.push_back({h->k3[b] + h->k12o[b], h->k3[b]});
       const double wbytes = (double)lv.work_elems * (lv.fp64 ? 8 : 4);
       ExtractDst dst{};
       dst.TL = h->ops64; dst.TL_ld = 0; dst.TL_off = lv.off_tl;
@@ -1065,6 +1116,38 @@ void ensure_ws(hps_handle* h, int nrhs, cudaStream_t s) {
   w.scal = (double*)get(4 * sizeof(double));
 }
 
+// Econ mode: rebuild the leaf operators [F | S_ci] and H of chunk c into the chunk buffer
+// (the same assembly, elimination and extraction as the build, T discarded).
+void recompute_leaf_chunk(hps_handle* h, int c, cudaStream_t s) {
+  const int E = h->echunk, l0 = c * E, n = std::min(E, h->n_leaf - l0);
+  const int m = h->m, nq = h->nq, R = m + nq;
+  const long long per_leaf = (long long)R * R;
+  LeafTablesDev tb{h->dD, h->dD2, h->dLs, h->dDLs, h->dLloc, h->dDceL, h->didx + h->off_ci};
+  TIMED("leaf_assemble_f64", 0, (double)n * per_leaf * 8,
+        launch_leaf_assemble<double>(h->coeffs_copy, h->n_leaf, l0, n, h->dhxy, h->p, h->q, tb, h->ework, per_leaf,
+                                     s));
+  run_gj<double>(h->egd + l0, n, R, m, h->ework, h->eperm, h->epinv, h->eprow, h->d_status,
+                 std::vector<std::pair<int, int>>(n, {R, m}), "leaf_econ", s);
+  ExtractDst dst{};
+  dst.TL = h->eops; dst.TL_off_stride = (long long)m * R; dst.TL_ld = R;
+  dst.TR = h->eops + m; dst.TR_off_stride = (long long)m * R; dst.TR_ld = R;
+  dst.BL = h->eops + (long long)E * m * R; dst.BL_off_stride = (long long)nq * m; dst.BL_ld = m;
+  dst.sTL = 1.0; dst.sTR = -1.0; dst.sBL = -1.0;
+  TIMED("gj_extract_f64", 0, (double)n * per_leaf * 8,
+        launch_gj_extract<double, double>(h->egd + l0, n, R, h->ework, h->eperm, dst, s));
+  CKL();
+}
+
+// Items [l0, l0 + n) leaves of a leaf item set (every leaf has the same number of items).
+ItemSet leaf_range(const hps_handle* h, const ItemSet& is, int l0, int n) {
+  ItemSet r;
+  const int per = is.n / h->n_leaf;
+  r.dev = is.dev + (long long)l0 * per;
+  r.n = n * per;
+  r.elems = is.elems * (double)n / h->n_leaf;
+  return r;
+}
+
 // One pass of Algorithm 2 with operator type TA and vector type TV.
 //   f: [n_bdry][nrhs] FP64 (scattered as TV), g: [n_leaf][pp][nrhs] TV, rho: optional
 //   FP64 [n_gauss][nrhs], outputs uc [n_leaf][pp][nrhs] TV and ug [n_gauss][nrhs] TV.
@@ -1086,8 +1169,24 @@ void solve_pass(hps_handle* h, const TA* ops, const double* f, const TV* g, cons
       TIMED("split_reduce", 0, 0, launch_split_reduce<TV>(pr.red, pr.nred, P, C, Add, idx, nrhs, beta, s));
     }
   };
+  // leaf steps read the stored operators, or (econ) operators rebuilt chunk by chunk
+  auto leaf_step = [&](const char* step, const ItemSet& is, const TV* B0, const TV* B1, TV* C) {
+    if (!h->econ) {
+      gemm(step, is, B0, B1, C, nullptr, 0.0);
+      return;
+    }
+    if constexpr (std::is_same<TA, double>::value) {
+      for (int c = 0; c * h->echunk < h->n_leaf; ++c) {
+        recompute_leaf_chunk(h, c, s);
+        const int l0 = c * h->echunk, n = std::min(h->echunk, h->n_leaf - l0);
+        const ItemSet r = leaf_range(h, is, l0, n);
+        TIMED(("gemm_" + std::string(step) + "_" + sf).c_str(), 2.0 * r.elems * nrhs, r.elems * sizeof(TA),
+              launch_gemm_items<TA, TV>(r.dev, r.n, ROWBLK, 0, h->eops, B0, B1, C, nullptr, idx, nrhs, 0.0, s));
+      }
+    }
+  };
   // upward pass: leaves, then merges bottom-up
-  gemm("leaf_up", h->leafup, g, nullptr, V, nullptr, 0.0);
+  leaf_step("leaf_up", h->leafup, g, nullptr, V);
   for (int L = 0; L < H; ++L) {
     Level& lv = h->levels[L];
     TIMED("up_gather", 0, 0, launch_up_gather<TV>(lv.ug, (int)lv.boxes.size(), lv.ug_maxrows, V, V, dbuf, rho, idx, nrhs, s));
@@ -1101,7 +1200,7 @@ void solve_pass(hps_handle* h, const TA* ops, const double* f, const TV* g, cons
     if (lv.idown.n) gemm("refine_down", lv.idown, ug, nullptr, ug, nullptr, 0.0);
     gemmp("merge_down", lv.down, ug, ug, V, 0.0);
   }
-  gemm("leaf_down", h->leafdown, g, ug, uc, nullptr, 0.0);
+  leaf_step("leaf_down", h->leafdown, g, ug, uc);
   gemm("leaf_ext", h->lce, ug, nullptr, uc, nullptr, 0.0);
   CKL();
 }
@@ -1317,7 +1416,9 @@ int check_opts(int p, const hps_opts* opts, hps_opts& o) {
   if (o.q == 0) o.q = p - 1;
   if (o.q < 2 || o.q > 32) return fail(HPS_ERR_INVALID_ARG, "q must be in [2, 32]");
   if (o.precision != HPS_FP64 && o.precision != HPS_MIXED) return fail(HPS_ERR_INVALID_ARG, "unknown precision");
-  if (o.store_leaf_ops != 1) return fail(HPS_ERR_INVALID_ARG, "store_leaf_ops must be 1");
+  if (o.store_leaf_ops != 0 && o.store_leaf_ops != 1) return fail(HPS_ERR_INVALID_ARG, "store_leaf_ops must be 0 or 1");
+  if (o.store_leaf_ops == 0 && o.precision != HPS_FP64)
+    return fail(HPS_ERR_INVALID_ARG, "leaf recomputation (store_leaf_ops = 0) needs precision HPS_FP64");
   if (o.ir_tol <= 0.0) o.ir_tol = 1e-10;
   if (o.ir_max_iter <= 0) o.ir_max_iter = 10;
   return HPS_OK;
@@ -1400,7 +1501,7 @@ int hps_build(const hps_tree* tree, const double* coeffs, int p, const hps_opts*
       }
       upload_plan(h, hp, s);
     }
-    if (o.precision == HPS_MIXED) {
+    if (o.precision == HPS_MIXED || o.store_leaf_ops == 0) {
       const size_t cb = (size_t)6 * h->n_leaf * h->pp * sizeof(double);
       h->coeffs_copy = (double*)h->al.get(cb, s);
       h->owned.push_back({h->coeffs_copy, cb});
@@ -1562,9 +1663,31 @@ int hps_adjoint(hps_handle* h, const double* ubar_in, int nrhs, const double* u,
               launch_split_reduce<double>(pr.red, pr.nred, w.P64, C, nullptr, idx, nrhs, beta, s));
       }
     };
+    // leaf steps: stored operators, or (econ) operators rebuilt chunk by chunk
+    auto leafT = [&](const char* step, const ItemSet& is, const double* B0, double* C, double beta,
+                     const ItemSet* is2, double* C2) {
+      if (!h->econ) {
+        gemmT(step, is, B0, C, beta);
+        if (is2) gemmT(step, *is2, B0, C2, beta);
+        return;
+      }
+      for (int c = 0; c * h->echunk < h->n_leaf; ++c) {
+        recompute_leaf_chunk(h, c, s);
+        const int l0 = c * h->echunk, n = std::min(h->echunk, h->n_leaf - l0);
+        const ItemSet r = leaf_range(h, is, l0, n);
+        TIMED(("gemmT_" + std::string(step) + "_f64").c_str(), 2.0 * r.elems * nrhs, r.elems * 8.0,
+              launch_gemm_items<double, double>(r.dev, r.n, ROWBLK, 1, h->eops, B0, nullptr, C, nullptr, idx, nrhs,
+                                                beta, s));
+        if (is2) {
+          const ItemSet r2 = leaf_range(h, *is2, l0, n);
+          TIMED(("gemmT_" + std::string(step) + "_f64").c_str(), 2.0 * r2.elems * nrhs, r2.elems * 8.0,
+                launch_gemm_items<double, double>(r2.dev, r2.n, ROWBLK, 1, h->eops, B0, nullptr, C2, nullptr, idx,
+                                                  nrhs, beta, s));
+        }
+      }
+    };
     // 1. leaf-down transposed: gbar_ci = F^T ubar_ci ; LB = S_ci^T ubar_ci + Lce^T ubar_ce
-    gemmT("leaf_F", h->adj_leafF, ubar_in, gb, 0.0);
-    gemmT("leaf_S", h->adj_leafS, ubar_in, w.LB, 0.0);
+    leafT("leaf_FS", h->adj_leafF, ubar_in, gb, 0.0, &h->adj_leafS, w.LB);
     gemmT("leaf_ext", h->adj_lce, ubar_in, w.LB, 1.0);
     // ubar_gauss = sum over owning leaves
     TIMED("gather_reduce", 0, 0, launch_gather_reduce<double>(h->leaf_reduce_tab, h->n_leaf_reduce, w.LB, ub, nrhs, 0, s));
@@ -1588,7 +1711,7 @@ int hps_adjoint(hps_handle* h, const double* ubar_in, int nrhs, const double* u,
       TIMED("down_scatter", 0, 0, launch_down_scatter<double>(lv.ds, (int)lv.boxes.size(), lv.ds_maxrows, VB, w.d64, nullptr, idx, nrhs, s));
     }
     // 5. leaf-up transposed: gbar_ci += H^T hbar
-    gemmT("leaf_H", h->adj_leafH, VB, gb, 1.0);
+    leafT("leaf_H", h->adj_leafH, VB, gb, 1.0, nullptr, nullptr);
     CKL();
     // 6. coefficient gradients
     if (cbar) {

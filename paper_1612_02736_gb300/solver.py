@@ -133,7 +133,7 @@ class Solver:
     """
 
     def __init__(self, tree, coeffs, p, precision="fp64", q=None, ir_tol=None, ir_max_iter=None,
-                 fp64_top_levels=None, allocator="torch"):
+                 fp64_top_levels=None, store_leaf_ops=True, allocator="torch"):
         lib = N.load()
         if not (coeffs.is_cuda and coeffs.dtype == torch.float64 and coeffs.is_contiguous()):
             raise ValueError("coeffs must be a contiguous CUDA float64 tensor")
@@ -148,6 +148,7 @@ class Solver:
             opts.ir_max_iter = ir_max_iter
         if fp64_top_levels is not None:
             opts.fp64_top_levels = fp64_top_levels
+        opts.store_leaf_ops = 1 if store_leaf_ops else 0
         self.tree, self.p, self.precision = tree, p, precision
         self._alloc = _allocator() if allocator == "torch" else None
         out = C.c_void_p()
@@ -224,8 +225,8 @@ class HPSFunction(torch.autograd.Function):
     stored FP64 factorization (hps_adjoint) gives dJ/df, dJ/dg and dJ/dcoeffs."""
 
     @staticmethod
-    def forward(ctx, coeffs, f, g, tree, p):
-        solver = Solver(tree, coeffs.detach().contiguous(), p, precision="fp64")
+    def forward(ctx, coeffs, f, g, tree, p, store_leaf_ops=True):
+        solver = Solver(tree, coeffs.detach().contiguous(), p, precision="fp64", store_leaf_ops=store_leaf_ops)
         u = solver.solve(f.detach(), g.detach())
         ctx.solver = solver
         ctx.save_for_backward(u)
@@ -239,4 +240,4 @@ class HPSFunction(torch.autograd.Function):
         ctx.solver.close()
         return (cb if ctx.needs_input_grad[0] else None,
                 fb.reshape(ctx.f_shape) if ctx.needs_input_grad[1] else None,
-                gb.reshape(ctx.g_shape) if ctx.needs_input_grad[2] else None, None, None)
+                gb.reshape(ctx.g_shape) if ctx.needs_input_grad[2] else None, None, None, None)

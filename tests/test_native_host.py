@@ -109,9 +109,10 @@ def test_python_package_fails_loudly_without_library(tmp_path, monkeypatch):
         _native.load()
 
 
-@pytest.mark.parametrize("nx,ny,p,prec", [(1, 1, 8, 0), (2, 1, 6, 0), (2, 2, 16, 1), (4, 4, 12, 1),
-                                          (8, 4, 16, 0), (64, 64, 16, 0), (16, 16, 20, 1)])
-def test_plan_descriptors_stay_in_bounds(lib, nx, ny, p, prec):
+@pytest.mark.parametrize("nx,ny,p,prec,store", [(1, 1, 8, 0, 1), (2, 1, 6, 0, 1), (2, 2, 16, 1, 1), (4, 4, 12, 1, 1),
+                                                (8, 4, 16, 0, 1), (64, 64, 16, 0, 1), (16, 16, 20, 1, 1),
+                                                (8, 8, 16, 0, 0), (64, 64, 16, 0, 0), (3, 5, 9, 0, 0)])
+def test_plan_descriptors_stay_in_bounds(lib, nx, ny, p, prec, store):
     # Every kernel descriptor of the build, solve and adjoint plans is checked against the
     # size of the buffer it addresses, on the host, before any launch.
     from paper_1612_02736_gb300 import _native
@@ -119,6 +120,7 @@ def test_plan_descriptors_stay_in_bounds(lib, nx, ny, p, prec):
     opts = _native.hps_opts()
     lib.hps_opts_default(C.byref(opts))
     opts.precision = prec
+    opts.store_leaf_ops = store
     assert lib.hps_plan_check(t, p, C.byref(opts)) == 0, lib.hps_last_error()
     lib.hps_tree_destroy(t)
 
