@@ -80,9 +80,13 @@ typedef struct {
   double ir_tol;       /* HPS_MIXED: stop when max|du| <= ir_tol * max|u|; 0 means 1e-10   */
   int ir_max_iter;     /* HPS_MIXED: refinement steps allowed; 0 means 10                  */
   int fp64_top_levels; /* HPS_MIXED: number of top merge levels kept in FP64; -1 means 1   */
+  int use_graphs;      /* HPS_FP64 solves without a flux-jump input: 1 (default) replays
+                        * one captured CUDA graph of the whole sweep per nrhs (the inputs
+                        * are copied into and the result out of staging buffers the
+                        * handle owns); 0 launches the kernels one by one              */
 } hps_opts;
 
-/* Fills *opts with the defaults above (FP64, q = p - 1, store leaf operators). */
+/* Fills *opts with the defaults above (FP64, q = p - 1, store leaf operators, graphs on). */
 void hps_opts_default(hps_opts* opts);
 
 /* Uniform tree of nx x ny equal leaves over [x0,x1] x [y0,y1] by recursive halving

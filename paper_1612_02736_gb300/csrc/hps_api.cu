@@ -266,7 +266,27 @@ struct hps_handle {
   int* fbar_tab = nullptr;
   // workspace
   Workspace ws;
+  // captured FP64 sweep (per nrhs) and its staging buffers
+  struct {
+    int nrhs = 0;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cs = nullptr;
+    double *f_in = nullptr, *g_in = nullptr, *u_out = nullptr;
+    bool broken = false;
+    int last_nrhs = 0;   // capture on the second call with the same nrhs
+    int kernels = 0;     // kernel nodes in the graph
+    double flops = 0.0, bytes = 0.0;
+  } graph;
+  void drop_graph() {
+    if (graph.exec) cudaGraphExecDestroy(graph.exec);
+    graph.exec = nullptr;
+    for (double* p : {graph.f_in, graph.g_in, graph.u_out}) al.put(p, 0);
+    graph.f_in = graph.g_in = graph.u_out = nullptr;
+    graph.nrhs = 0;
+  }
   ~hps_handle() {
+    drop_graph();
+    if (graph.cs) cudaStreamDestroy(graph.cs);
     if (ws.ptrs.empty() && owned.empty()) return;
     for (void* p : ws.ptrs) al.put(p, 0);
     for (auto& b : owned) al.put(b.p, 0);
@@ -1081,6 +1101,7 @@ void build_stage(hps_handle* h, const double* coeffs, cudaStream_t s) {
 void ensure_ws(hps_handle* h, int nrhs, cudaStream_t s) {
   Workspace& w = h->ws;
   if (w.nrhs >= nrhs) return;
+  h->drop_graph();  // a captured sweep points into the old buffers
   for (void* p : w.ptrs) h->al.put(p, s);
   w = Workspace();
   w.nrhs = nrhs;
@@ -1212,6 +1233,62 @@ double read_scalar(const double* d, cudaStream_t s) {
   return v;
 }
 
+// Capture the whole FP64 sweep for this nrhs into a CUDA graph that reads its inputs from
+// (and writes u to) staging buffers owned by the handle.  Capture runs on a private
+// stream; a capture failure disables graphs for this handle (direct launches remain).
+void capture_solve(hps_handle* h, int nrhs, cudaStream_t s) {
+  h->drop_graph();
+  Workspace& w = h->ws;
+  const long long nuc = (long long)h->n_leaf * h->pp * nrhs;
+  const long long ng = (long long)h->ns.n_gauss * nrhs;
+  h->graph.f_in = (double*)h->al.get((size_t)h->n_bdry * nrhs * sizeof(double), s);
+  h->graph.g_in = (double*)h->al.get((size_t)nuc * sizeof(double), s);
+  h->graph.u_out = (double*)h->al.get((size_t)nuc * sizeof(double), s);
+  CK(cudaStreamSynchronize(s));
+  if (!h->graph.cs) CK(cudaStreamCreateWithFlags(&h->graph.cs, cudaStreamNonBlocking));
+  cudaStream_t cs = h->graph.cs;
+  cudaGraph_t graph = nullptr;
+  timing_suspend(true);
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    try {
+      cudaMemsetAsync(w.ug64, 0, ng * sizeof(double), cs);
+      solve_pass<double, double>(h, h->ops64, h->graph.f_in, h->graph.g_in, nullptr, h->graph.u_out, w.ug64, w.V64,
+                                 w.d64, w.P64, nrhs, cs);
+    } catch (const CudaError&) {
+    }
+    e = cudaStreamEndCapture(cs, &graph);
+  }
+  timing_suspend(false);
+  if (e == cudaSuccess && graph) {
+    size_t nn = 0;
+    cudaGraphGetNodes(graph, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (nn) cudaGraphGetNodes(graph, nodes.data(), &nn);
+    int nk = 0;
+    for (cudaGraphNode_t nd : nodes) {
+      cudaGraphNodeType ty;
+      if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++nk;
+    }
+    h->graph.kernels = nk;
+    double el = h->leafup.elems + h->leafdown.elems + h->lce.elems;
+    for (const Level& lv : h->levels)
+      el += lv.up.direct.elems + lv.up.split.elems + lv.down.direct.elems + lv.down.split.elems + lv.iup.elems +
+            lv.idown.elems;
+    h->graph.flops = 2.0 * el * nrhs;
+    h->graph.bytes = 8.0 * el;
+    e = cudaGraphInstantiate(&h->graph.exec, graph, 0);
+  }
+  if (graph) cudaGraphDestroy(graph);
+  if (e != cudaSuccess || !h->graph.exec) {
+    cudaGetLastError();
+    h->graph.exec = nullptr;
+    h->graph.broken = true;
+    return;
+  }
+  h->graph.nrhs = nrhs;
+}
+
 int solve_impl(hps_handle* h, const double* f, const double* g, const double* rho, int nrhs, double* u,
                double* ug_out, int* iters, cudaStream_t s) {
   ensure_ws(h, nrhs, s);
@@ -1220,6 +1297,22 @@ int solve_impl(hps_handle* h, const double* f, const double* g, const double* rh
   const long long ng = (long long)h->ns.n_gauss * nrhs;
   if (iters) *iters = 0;
   if (h->opts.precision == HPS_FP64) {
+    const long long nf = (long long)h->n_bdry * nrhs;
+    if (h->opts.use_graphs && !rho && !h->graph.broken) {
+      if (h->graph.nrhs != nrhs && h->graph.last_nrhs == nrhs) capture_solve(h, nrhs, s);
+      h->graph.last_nrhs = nrhs;
+      if (h->graph.exec && h->graph.nrhs == nrhs) {
+        CK(cudaMemcpyAsync(h->graph.f_in, f, nf * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(h->graph.g_in, g, nuc * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        {
+          TimingScope ts_("graph_solve_f64", s, h->graph.flops, h->graph.bytes, std::max(1, h->graph.kernels));
+          CK(cudaGraphLaunch(h->graph.exec, s));
+        }
+        CK(cudaMemcpyAsync(u, h->graph.u_out, nuc * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        if (ug_out) CK(cudaMemcpyAsync(ug_out, w.ug64, ng * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        return HPS_OK;
+      }
+    }
     CK(cudaMemsetAsync(w.ug64, 0, ng * sizeof(double), s));
     solve_pass<double, double>(h, h->ops64, f, g, rho, u, w.ug64, w.V64, w.d64, w.P64, nrhs, s);
     if (ug_out) CK(cudaMemcpyAsync(ug_out, w.ug64, ng * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -1240,6 +1333,7 @@ void hps_opts_default(hps_opts* o) {
   o->ir_tol = 0.0;
   o->ir_max_iter = 0;
   o->fp64_top_levels = -1;
+  o->use_graphs = 1;
 }
 
 const char* hps_last_error(void) { return g_err.c_str(); }

@@ -264,9 +264,10 @@ void launch_down_scatter(const DownScatter* g, int n, int maxrows, TV* VB, const
 // Optional launch timing (enabled with hps_timing_enable): records a pair of CUDA events
 // around the launches made while the scope is alive.
 bool timing_enabled();
+void timing_suspend(bool on);  // no event records while a stream is being captured
 class TimingScope {
  public:
-  TimingScope(const char* name, cudaStream_t s, double flops = 0.0, double bytes = 0.0);
+  TimingScope(const char* name, cudaStream_t s, double flops = 0.0, double bytes = 0.0, int launches = 1);
   ~TimingScope();
   TimingScope(const TimingScope&) = delete;
   TimingScope& operator=(const TimingScope&) = delete;
@@ -274,6 +275,7 @@ class TimingScope {
  private:
   cudaStream_t stream_;
   double flops_, bytes_;
+  int launches_ = 1;
   int cat_ = -1;
   void* e0_ = nullptr;
   void* e1_ = nullptr;

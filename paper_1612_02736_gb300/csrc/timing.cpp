@@ -19,6 +19,7 @@ struct Rec {
   int cat;
   cudaEvent_t e0, e1;
   double flops, bytes;
+  int launches;
 };
 
 struct Cat {
@@ -58,7 +59,7 @@ int drain() {
       rc = 1;
     }
     Cat& c = g_cats[r.cat];
-    c.launches += 1;
+    c.launches += r.launches;
     c.ms += ms;
     c.flops += r.flops;
     c.bytes += r.bytes;
@@ -71,10 +72,13 @@ int drain() {
 
 }  // namespace
 
-bool timing_enabled() { return g_on.load(std::memory_order_relaxed); }
+thread_local int g_suspended = 0;
 
-TimingScope::TimingScope(const char* name, cudaStream_t s, double flops, double bytes)
-    : stream_(s), flops_(flops), bytes_(bytes) {
+bool timing_enabled() { return g_on.load(std::memory_order_relaxed) && !g_suspended; }
+void timing_suspend(bool on) { g_suspended += on ? 1 : -1; }
+
+TimingScope::TimingScope(const char* name, cudaStream_t s, double flops, double bytes, int launches)
+    : stream_(s), flops_(flops), bytes_(bytes), launches_(launches) {
   if (!timing_enabled()) return;
   std::lock_guard<std::mutex> lk(g_mu);
   auto it = g_ids.find(name);
@@ -99,7 +103,7 @@ TimingScope::~TimingScope() {
   if (cat_ < 0) return;
   cudaEventRecord((cudaEvent_t)e1_, stream_);
   std::lock_guard<std::mutex> lk(g_mu);
-  g_pending.push_back({cat_, (cudaEvent_t)e0_, (cudaEvent_t)e1_, flops_, bytes_});
+  g_pending.push_back({cat_, (cudaEvent_t)e0_, (cudaEvent_t)e1_, flops_, bytes_, launches_});
 }
 
 }  // namespace hps

@@ -133,7 +133,7 @@ class Solver:
     """
 
     def __init__(self, tree, coeffs, p, precision="fp64", q=None, ir_tol=None, ir_max_iter=None,
-                 fp64_top_levels=None, store_leaf_ops=True, allocator="torch"):
+                 fp64_top_levels=None, store_leaf_ops=True, use_graphs=True, allocator="torch"):
         lib = N.load()
         if not (coeffs.is_cuda and coeffs.dtype == torch.float64 and coeffs.is_contiguous()):
             raise ValueError("coeffs must be a contiguous CUDA float64 tensor")
@@ -149,6 +149,7 @@ class Solver:
         if fp64_top_levels is not None:
             opts.fp64_top_levels = fp64_top_levels
         opts.store_leaf_ops = 1 if store_leaf_ops else 0
+        opts.use_graphs = 1 if use_graphs else 0
         self.tree, self.p, self.precision = tree, p, precision
         self._alloc = _allocator() if allocator == "torch" else None
         out = C.c_void_p()
