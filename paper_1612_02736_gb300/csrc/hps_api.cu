@@ -3,9 +3,11 @@
 // adjoint (transposed Algorithm 2 sweeps).  Host code here only plans: every arithmetic
 // step of the build, the solve, the residual and the adjoint runs in the kernels.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <string>
@@ -17,8 +19,13 @@
 
 using namespace hps;
 
+struct PlanCache;
+
 struct hps_tree {
   Tree t;
+  // host plans already made for this tree (a tree never changes once made)
+  mutable std::mutex cache_mu;
+  mutable std::shared_ptr<PlanCache> cache;
 };
 
 namespace {
@@ -88,6 +95,18 @@ struct DBuf {
   size_t bytes = 0;
 };
 
+// FP64 table as unevaluated pairs hi + lo of floats (hi = x rounded to float, lo = the
+// remainder rounded to float) for the double-float residual kernels.
+std::vector<float> split_df(const std::vector<double>& v) {
+  std::vector<float> o(2 * v.size());
+  for (size_t i = 0; i < v.size(); ++i) {
+    const float hi = (float)v[i];
+    o[2 * i] = hi;
+    o[2 * i + 1] = (float)(v[i] - (double)hi);
+  }
+  return o;
+}
+
 template <typename T>
 T* upload(Alloc& al, cudaStream_t s, const std::vector<T>& v, std::vector<DBuf>& owned) {
   void* p = al.get(v.size() * sizeof(T), s);
@@ -151,7 +170,7 @@ struct Prod {
 struct Level {
   std::vector<int> boxes;  // merges at this height
   bool fp64 = true;        // precision of the elimination
-  int maxR = 0, maxK = 0;
+  int maxR = 0, maxK = 0, maxRows = 0;
   // build
   GJDesc* gj = nullptr;
   MergeDesc* md = nullptr;
@@ -222,6 +241,7 @@ struct hps_handle {
   int p = 0, q = 0, m = 0, nq = 0, ne = 0, pp = 0, n_leaf = 0, n_bdry = 0;
   // tables
   double *dD = nullptr, *dD2 = nullptr, *dLs = nullptr, *dDLs = nullptr, *dLloc = nullptr, *dDceL = nullptr;
+  float2 *dLloc_df = nullptr, *dLce_df = nullptr;
   double* dhxy = nullptr;
   int* didx = nullptr;
   int* d_leaf_edges = nullptr;
@@ -237,6 +257,7 @@ struct hps_handle {
   long long gl_base = 0, h_base = 0, lce_base = 0;
   std::vector<long long> mo, so;  // per box: Mleft and S offsets
   std::vector<long long> toff;    // per box: T block offset in the build's T store
+  long long tstore_elems = 0;     // size of the build's T store
   std::vector<long long> ttmp;    // coarsened boxes: T before coarsening (T store)
   std::vector<long long> puo, pdo, pco;  // coarsened boxes: P_up, P_down, P_up(fine, coarse)
   std::vector<int> k3, k12, k12o; // |J3|, |I_ge| seen by the parent, |J1 + J2|
@@ -446,7 +467,8 @@ void make_plan(hps_handle* h, HostPlan& hp) {
   h->pco.assign(nb, -1);
   for (int b = 0; b < nb; ++b) {
     if (t.boxes[b].leaf >= 0) continue;
-    const int R = h->k3[b] + h->k12o[b];
+    // [X; C X] (the root keeps X only: nothing above it applies C X)
+    const int R = t.boxes[b].parent < 0 ? h->k3[b] : h->k3[b] + h->k12o[b];
     h->mo[b] = off;
     off += (long long)R * h->k3[b];
     h->so[b] = off;
@@ -509,7 +531,7 @@ void make_plan(hps_handle* h, HostPlan& hp) {
   }
   h->ttmp.assign(nb, -1);
   for (int b = 0; b < nb; ++b) {
-    if (t.boxes[b].leaf >= 0) continue;
+    if (t.boxes[b].leaf >= 0 || t.boxes[b].parent < 0) continue;  // no DtN map is kept for the root
     toff[b] = tsz;
     tsz += (long long)h->k12[b] * h->k12[b];
     if (ns.co[b].active) {
@@ -529,8 +551,13 @@ void make_plan(hps_handle* h, HostPlan& hp) {
       const Box& bx = t.boxes[b];
       const int a = bx.child[0], c = bx.child[1];
       const int k3 = h->k3[b], k12 = h->k12o[b], R = k3 + k12, n1 = ns.n1[b], n2 = k12 - n1;
+      // The root's solve needs X and S only (u_ge = f there): its elimination forms and
+      // eliminates the top rows [Z | R] and never computes C X or T_tau.
+      const bool root = bx.parent < 0;
+      const int rows = root ? k3 : R;
       lv.maxR = std::max(lv.maxR, R);
       lv.maxK = std::max(lv.maxK, k3);
+      lv.maxRows = std::max(lv.maxRows, rows);
       auto pa = posmap(a), pc = posmap(c);
       std::vector<int> posA(R, -1), posB(R, -1);
       const std::vector<int>& J3 = ns.J3[b];
@@ -544,6 +571,7 @@ void make_plan(hps_handle* h, HostPlan& hp) {
       MergeDesc md;
       md.m_off = woff;
       md.R = R;
+      md.rows = rows;
       md.k3 = k3;
       md.n1 = n1;
       md.ta_off = toff[a];
@@ -557,10 +585,11 @@ void make_plan(hps_handle* h, HostPlan& hp) {
       gd.off = woff;
       gd.R = R;
       gd.K = k3;
+      gd.rows = rows;
       gd.perm_off = poff;
       gd.box = b;
       pd.gj.push_back(gd);
-      woff += (long long)R * R;
+      woff += (long long)rows * R;
       poff += k3;
       pd.tl.push_back(h->mo[b]);
       pd.bl.push_back(h->mo[b] + (long long)k3 * k3);
@@ -597,7 +626,7 @@ void make_plan(hps_handle* h, HostPlan& hp) {
       pd.ds.push_back(ds);
       lv.ds_maxrows = std::max(lv.ds_maxrows, k3 + n1 + n2);
       // up: [w; h] += [X; CX] d
-      add_product(pd.up.direct, h->mo[b], k3, R, k3, k3, h->drow[b], -1, 0, -1, h->vrow[b], -1, -1, false);
+      add_product(pd.up.direct, h->mo[b], k3, rows, k3, k3, h->drow[b], -1, 0, -1, h->vrow[b], -1, -1, false);
       // down: u[J3] = S u[ge] + w
       add_product(pd.down.direct, h->so[b], k12, k3, k12, k12, 0, h->off_geo[b], 0, -1, 0, h->off_J3[b], h->vrow[b],
                   false);
@@ -619,7 +648,7 @@ void make_plan(hps_handle* h, HostPlan& hp) {
         }
       }
       // adjoint: dbar = [X; CX]^T [wbar; hbar]
-      add_product(pd.adjM.direct, h->mo[b], k3, k3, R, R, h->vrow[b], -1, 0, -1, h->drow[b], -1, -1, true);
+      add_product(pd.adjM.direct, h->mo[b], k3, k3, rows, rows, h->vrow[b], -1, 0, -1, h->drow[b], -1, -1, true);
       // coarsened refined parent (Sec. 6.3-6.4)
       const Coarsen& co = ns.co[b];
       if (co.active) {
@@ -651,6 +680,7 @@ void make_plan(hps_handle* h, HostPlan& hp) {
     }
   }
   hp.tsz = tsz;
+  h->tstore_elems = tsz;
   // leaf items
   std::vector<GemmItem>&lup = hp.lup, &ldown = hp.ldown, &llce = hp.llce, &aF = hp.aF, &aS = hp.aS, &aL = hp.aL,
                         &aH = hp.aH;
@@ -707,6 +737,30 @@ Prod upload_prod(hps_handle* h, cudaStream_t s, const ProdHost& ph) {
   pr.nred = (int)ph.red.size();
   pr.red = ph.red.empty() ? nullptr : upload(h->al, s, ph.red, h->owned);
   return pr;
+}
+
+}  // namespace
+
+// Host plans of one tree, reused by later builds on it.  A plan (node sets, operator
+// offsets, vector layouts, product lists, elimination descriptors) depends on the mesh,
+// p, q and the precision layout, never on the coefficients, so a rebuild with new
+// coefficients (an optimisation loop, a time-dependent operator, a second precision of
+// the same problem) copies it instead of recomputing it.
+struct PlanCache {
+  struct Entry {
+    std::array<int, 5> key;
+    std::shared_ptr<const hps_handle> layout;  // the handle's host fields after planning
+    std::shared_ptr<const HostPlan> plan;
+  };
+  std::vector<Entry> entries;  // oldest first, at most kMax
+  static constexpr size_t kMax = 4;
+};
+
+namespace {
+
+std::array<int, 5> plan_key(int p, const hps_opts& o) {
+  const int top = o.precision == HPS_FP64 ? 0 : (o.fp64_top_levels < 0 ? 1 : o.fp64_top_levels);
+  return {p, o.q, o.precision, top, o.store_leaf_ops};
 }
 
 void upload_plan(hps_handle* h, const HostPlan& hp, cudaStream_t s) {
@@ -889,8 +943,9 @@ std::string validate_plan(const hps_handle* h, const HostPlan& hp) {
     for (size_t i = 0; i < pd.md.size(); ++i) {
       const MergeDesc& md = pd.md[i];
       const GJDesc& gd = pd.gj[i];
-      if (md.m_off + (long long)md.R * md.R > lv.work_elems || gd.off != md.m_off || gd.R != md.R ||
-          gd.K != md.k3 || gd.perm_off + gd.K > lv.perm_elems)
+      if (md.rows != md.R && md.rows != md.k3) pc.fail("merge row count");
+      if (md.m_off + (long long)md.rows * md.R > lv.work_elems || gd.off != md.m_off || gd.R != md.R ||
+          gd.K != md.k3 || gd.rows != md.rows || gd.perm_off + gd.K > lv.perm_elems || md.rows > lv.maxRows)
         pc.fail("merge workspace out of range");
       if (md.ta_off + (long long)md.lda_a * md.lda_a > hp.tsz || md.tb_off + (long long)md.lda_b * md.lda_b > hp.tsz)
         pc.fail("merge T store out of range");
@@ -900,19 +955,16 @@ std::string validate_plan(const hps_handle* h, const HostPlan& hp) {
           if (idx[md.pos_off + r] >= md.lda_a || idx[md.pos_off + md.R + r] >= md.lda_b) pc.fail("merge position too big");
         }
       const int k3 = md.k3, k12 = md.R - md.k3;
-      if (pd.tl[i] + (long long)md.R * k3 > ops || pd.bl[i] != pd.tl[i] + (long long)k3 * k3 ||
-          pd.tr[i] + (long long)k3 * k12 > ops || pd.br[i] + (long long)k12 * k12 > hp.tsz)
+      if (pd.tl[i] + (long long)md.rows * k3 > ops || pd.bl[i] != pd.tl[i] + (long long)k3 * k3 ||
+          pd.tr[i] + (long long)k3 * k12 > ops ||
+          (md.rows > k3 && (pd.br[i] < 0 || pd.br[i] + (long long)k12 * k12 > hp.tsz)))
         pc.fail("merge extraction out of range");
     }
   }
   return pc.err;
 }
 
-long long tstore_elems(const hps_handle* h) {
-  long long tsz = 0;
-  for (size_t b = 0; b < h->tree.boxes.size(); ++b) tsz += (long long)h->k12[b] * h->k12[b];
-  return tsz;
-}
+long long tstore_elems(const hps_handle* h) { return h->tstore_elems; }
 
 // Panel width: 16 for batches of many matrices; 8 for a level of few large matrices, whose
 // panels run on one CTA each and whose per-panel work grows with nb; capped so the panel
@@ -922,10 +974,13 @@ int choose_nb(int K, size_t elem, int nmat) {
   return std::max(1, std::min(nmat < 64 ? 8 : 16, nb));
 }
 
-// rk: (R, K) of every matrix of the batch, for the flop counts of the timing records.
+// rk: (R, K, rows) of every matrix of the batch, for the grid and the flop counts of the
+// timing records.
 template <typename T>
 void run_gj(const GJDesc* gj, int nmat, int maxR, int maxK, T* work, int* perm, T* pinv, T* prow,
-            int* status, const std::vector<std::pair<int, int>>& rk, const char* what, cudaStream_t s) {
+            int* status, const std::vector<std::array<int, 3>>& rk, const char* what, cudaStream_t s) {
+  int maxRows = 0;
+  for (const auto& m : rk) maxRows = std::max(maxRows, m[2]);
   const int nb = choose_nb(maxK, sizeof(T), nmat);
   const std::string sf = std::string(tsuf<T>()) + ":" + what;
   TIMED(("gj_init_" + sf).c_str(), 0, 0, launch_gj_init<T>(gj, nmat, perm, s));
@@ -934,19 +989,19 @@ void run_gj(const GJDesc* gj, int nmat, int maxR, int maxK, T* work, int* perm, 
   for (int c0 = 0; c0 < maxK; c0 += nb) {
     double fp = 0, fq = 0, fu = 0, bu = 0;
     for (const auto& m : rk) {
-      if (m.second <= c0) continue;
-      const double R = m.first, b = std::min(nb, m.second - c0);
-      fp += 2.0 * (m.second - c0) * b * b;
-      fq += 2.0 * R * b * b;
-      fu += 2.0 * b * R * (R - b);
-      bu += 2.0 * R * (R - b) * sizeof(T);
+      if (m[1] <= c0) continue;
+      const double R = m[0], rows = m[2], b = std::min(nb, m[1] - c0);
+      fp += 2.0 * (m[1] - c0) * b * b;
+      fq += 2.0 * rows * b * b;
+      fu += 2.0 * b * rows * (R - b);
+      bu += 2.0 * rows * (R - b) * sizeof(T);
     }
     TIMED(("gj_panel_" + sf).c_str(), fp, 0,
           launch_gj_panel<T>(gj, nmat, maxK, work, perm, pinv, c0, nb, status, s));
     TIMED(("gj_prep_" + sf).c_str(), fq, 0,
           launch_gj_prep<T>(gj, nmat, maxR, work, perm, pinv, prow, prow_stride, c0, nb, s));
     TIMED(("gj_update_" + sf).c_str(), fu, bu,
-          launch_gj_update<T>(gj, nmat, maxR, work, perm, prow, prow_stride, c0, nb, s));
+          launch_gj_update<T>(gj, nmat, maxR, maxRows, work, perm, prow, prow_stride, c0, nb, s));
   }
   CKL();
 }
@@ -989,6 +1044,7 @@ void build_stage(hps_handle* h, const double* coeffs, cudaStream_t s) {
       gd[i].off = (long long)i * per_leaf;
       gd[i].R = R;
       gd[i].K = m;
+      gd[i].rows = R;
       gd[i].perm_off = i * m;
       gd[i].box = 0;
     }
@@ -1002,7 +1058,7 @@ void build_stage(hps_handle* h, const double* coeffs, cudaStream_t s) {
             launch_leaf_assemble<double>(coeffs, h->n_leaf, l0, n, h->dhxy, h->p, h->q, tb, work, per_leaf, s));
       CKL();
       run_gj<double>(dgd, n, R, m, work, perm, pinv, prow, h->d_status,
-                     std::vector<std::pair<int, int>>(n, {R, m}), "leaf", s);
+                     std::vector<std::array<int, 3>>(n, {R, m, R}), "leaf", s);
       ExtractDst dst{};
       const long long gl0 = h->gl_base + (long long)l0 * m * R;
       dst.TL = h->ops64 + gl0; dst.TL_off_stride = (long long)m * R; dst.TL_ld = R;
@@ -1031,6 +1087,7 @@ void build_stage(hps_handle* h, const double* coeffs, cudaStream_t s) {
         eg[lf].off = (long long)(lf % E) * per_leaf;
         eg[lf].R = R;
         eg[lf].K = m;
+        eg[lf].rows = R;
         eg[lf].perm_off = (lf % E) * m;
         eg[lf].box = h->tree.leaves[lf];
       }
@@ -1041,8 +1098,11 @@ void build_stage(hps_handle* h, const double* coeffs, cudaStream_t s) {
     for (int L = 0; L < H; ++L) {
       Level& lv = h->levels[L];
       const int nmat = (int)lv.boxes.size();
-      std::vector<std::pair<int, int>> rk;
-      for (int b : lv.boxes) rk.push_back({h->k3[b] + h->k12o[b], h->k3[b]});
+      std::vector<std::array<int, 3>> rk;
+      for (int b : lv.boxes) {
+        const int R = h->k3[b] + h->k12o[b];
+        rk.push_back({R, h->k3[b], h->tree.boxes[b].parent < 0 ? h->k3[b] : R});
+      }
       const double wbytes = (double)lv.work_elems * (lv.fp64 ? 8 : 4);
       ExtractDst dst{};
       dst.TL = h->ops64; dst.TL_ld = 0; dst.TL_off = lv.off_tl;
@@ -1148,7 +1208,7 @@ void recompute_leaf_chunk(hps_handle* h, int c, cudaStream_t s) {
         launch_leaf_assemble<double>(h->coeffs_copy, h->n_leaf, l0, n, h->dhxy, h->p, h->q, tb, h->ework, per_leaf,
                                      s));
   run_gj<double>(h->egd + l0, n, R, m, h->ework, h->eperm, h->epinv, h->eprow, h->d_status,
-                 std::vector<std::pair<int, int>>(n, {R, m}), "leaf_econ", s);
+                 std::vector<std::array<int, 3>>(n, {R, m, R}), "leaf_econ", s);
   ExtractDst dst{};
   dst.TL = h->eops; dst.TL_off_stride = (long long)m * R; dst.TL_ld = R;
   dst.TR = h->eops + m; dst.TR_off_stride = (long long)m * R; dst.TR_ld = R;
@@ -1563,10 +1623,39 @@ int hps_build(const hps_tree* tree, const double* coeffs, int p, const hps_opts*
     h->al.custom = true;
   }
   try {
-    const std::string err = setup_host(h, tree->t, p, o);
-    if (!err.empty()) {
-      delete h;
-      return fail(HPS_ERR_INVALID_ARG, err);
+    // host plan: from the tree's cache, or made, checked and cached
+    std::shared_ptr<const HostPlan> plan;
+    {
+      std::lock_guard<std::mutex> lk(tree->cache_mu);
+      if (!tree->cache) tree->cache = std::make_shared<PlanCache>();
+      const std::array<int, 5> key = plan_key(p, o);
+      for (const PlanCache::Entry& e : tree->cache->entries)
+        if (e.key == key) {
+          const Alloc al = h->al;
+          *h = *e.layout;
+          h->al = al;
+          h->opts = o;
+          plan = e.plan;
+          break;
+        }
+      if (!plan) {
+        std::string err = setup_host(h, tree->t, p, o);
+        auto hp = std::make_shared<HostPlan>();
+        if (err.empty()) {
+          make_plan(h, *hp);
+          err = validate_plan(h, *hp);
+          if (!err.empty()) err = "internal plan check failed: " + err;
+        }
+        if (!err.empty()) {
+          delete h;
+          return fail(HPS_ERR_INVALID_ARG, err);
+        }
+        auto lay = std::make_shared<hps_handle>(*h);  // host fields only: nothing is on the device yet
+        lay->al = Alloc();
+        if (tree->cache->entries.size() >= PlanCache::kMax) tree->cache->entries.erase(tree->cache->entries.begin());
+        tree->cache->entries.push_back({key, lay, hp});
+        plan = hp;
+      }
     }
     // device tables
     h->dD = upload(h->al, s, h->rt.D, h->owned);
@@ -1574,6 +1663,8 @@ int hps_build(const hps_tree* tree, const double* coeffs, int p, const hps_opts*
     h->dLs = upload(h->al, s, h->rt.Ls, h->owned);
     h->dDLs = upload(h->al, s, h->rt.DLs, h->owned);
     h->dLloc = upload(h->al, s, h->rt.Lloc, h->owned);
+    h->dLloc_df = (float2*)upload(h->al, s, split_df(h->rt.Lloc), h->owned);
+    h->dLce_df = (float2*)upload(h->al, s, split_df(h->rt.Lce), h->owned);
     h->dDceL = upload(h->al, s, h->rt.DceL, h->owned);
     std::vector<double> hxy(2 * (size_t)h->n_leaf);
     for (int lf = 0; lf < h->n_leaf; ++lf) {
@@ -1585,16 +1676,7 @@ int hps_build(const hps_tree* tree, const double* coeffs, int p, const hps_opts*
     h->d_leaf_edges = upload(h->al, s, h->tree.leaf_edges, h->owned);
     std::vector<int> st(1, 0);
     h->d_status = upload(h->al, s, st, h->owned);
-    {
-      HostPlan hp;
-      make_plan(h, hp);
-      const std::string err = validate_plan(h, hp);
-      if (!err.empty()) {
-        delete h;
-        return fail(HPS_ERR_INVALID_ARG, "internal plan check failed: " + err);
-      }
-      upload_plan(h, hp, s);
-    }
+    upload_plan(h, *plan, s);
     if (o.precision == HPS_MIXED || o.store_leaf_ops == 0) {
       const size_t cb = (size_t)6 * h->n_leaf * h->pp * sizeof(double);
       h->coeffs_copy = (double*)h->al.get(cb, s);
@@ -1656,7 +1738,8 @@ int hps_solve_ext(hps_handle* h, const double* f, const double* g, const double*
     ra.D2 = h->dD2;
     ra.Lloc = h->dLloc;
     ra.ci = h->didx + h->off_ci;
-    const double* Lce = h->ops64 + h->lce_base;
+    ra.Lloc_df = h->dLloc_df;
+    ra.Lce_df = h->dLce_df;
     // derivative passes (5 p^3), exterior refresh (ne 4q) and fluxes (4q p) per leaf and rhs
     const double res_flops = 2.0 * ((double)h->n_leaf * nrhs) *
                              (5.0 * h->p * h->p * h->p + (double)h->ne * h->nq + (double)h->nq * h->p + 12.0 * h->m);
@@ -1665,8 +1748,8 @@ int hps_solve_ext(hps_handle* h, const double* f, const double* g, const double*
     double prev = -1.0;
     for (; it < h->opts.ir_max_iter; ++it) {
       // 2. FP64 residual: leaf equations and flux jumps (refreshes u_ce = L u_ge)
-      TIMED("leaf_residual_f64", res_flops, nuc * 32.0,
-            launch_leaf_residual_impl(ra, h->d_leaf_edges, Lce, h->didx + h->off_ce, w.ug64, g, u, w.r64, w.vflux,
+      TIMED("leaf_residual_df", res_flops, nuc * 32.0,
+            launch_leaf_residual_df(ra, h->d_leaf_edges, h->didx + h->off_ce, w.ug64, g, u, w.r64, w.vflux,
                                       nrhs, s));
       CK(cudaMemsetAsync(w.rho64, 0, ng * sizeof(double), s));
       TIMED("jump_residual", 0, 0, launch_jump_residual(h->d_pairs, h->npairs, h->q, w.vflux, w.rho64, nrhs, s));
@@ -1702,7 +1785,7 @@ int hps_solve_ext(hps_handle* h, const double* f, const double* g, const double*
     }
     // final exterior refresh u_ce = L_ce,ge u_ge in FP64
     TIMED("exterior_refresh", 2.0 * h->n_leaf * nrhs * h->ne * h->nq, 0,
-          launch_exterior_refresh(h->n_leaf, h->p, h->q, h->d_leaf_edges, Lce, h->didx + h->off_ce, w.ug64, u,
+          launch_exterior_refresh(h->n_leaf, h->p, h->q, h->d_leaf_edges, h->ops64 + h->lce_base, h->didx + h->off_ce, w.ug64, u,
                                   nrhs, s));
     CKL();
     if (ug_out) CK(cudaMemcpyAsync(ug_out, w.ug64, ng * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -1818,8 +1901,10 @@ int hps_adjoint(hps_handle* h, const double* ubar_in, int nrhs, const double* u,
       ra.D = h->dD;
       ra.D2 = h->dD2;
       ra.Lloc = h->dLloc;
+      ra.Lloc_df = h->dLloc_df;
+      ra.Lce_df = h->dLce_df;
       ra.ci = h->didx + h->off_ci;
-      TIMED("coeff_grad_f64", 2.0 * h->n_leaf * nrhs * (5.0 * h->p * h->p * h->p + 12.0 * h->m), nuc * 16.0,
+      TIMED("coeff_grad_df", 2.0 * h->n_leaf * nrhs * (5.0 * h->p * h->p * h->p + 12.0 * h->m), nuc * 16.0,
             launch_coeff_grad(ra, u, gb, cbar, nrhs, s));
       CKL();
     }

@@ -96,6 +96,8 @@ struct GJDesc {
   long long off;
   int R;
   int K;
+  int rows;            // rows formed and eliminated: R, or K at the root, where only the
+                       // top block rows [X | S] are wanted (row stride stays R)
   int perm_off;        // offset of its K-entry logical->physical row map
   int box;             // box id, for error reports
 };
@@ -144,7 +146,7 @@ template <typename T>
 void launch_gj_prep(const GJDesc* d, int nmat, int maxR, T* work, const int* perm, const T* pinv,
                     T* prow, long long prow_stride, int c0, int nb, cudaStream_t s);
 template <typename T>
-void launch_gj_update(const GJDesc* d, int nmat, int maxR, T* work, const int* perm, T* prow,
+void launch_gj_update(const GJDesc* d, int nmat, int maxR, int maxRows, T* work, const int* perm, T* prow,
                       long long prow_stride, int c0, int nb, cudaStream_t s);
 
 // Extraction of a finished elimination: with sigma the logical->physical row map,
@@ -174,6 +176,7 @@ void launch_gj_extract(const GJDesc* d, int nmat, int maxR, const T* work, const
 struct MergeDesc {
   long long m_off;     // offset of M_tau in the workspace
   int R;               // k3 + k12
+  int rows;            // rows to assemble (R, or k3 at the root)
   int k3, n1;          // |J3|, |J1| (|J2| = R - k3 - n1)
   long long ta_off, tb_off;  // children's T in the T store
   int lda_a, lda_b;    // children's T sizes
@@ -240,10 +243,12 @@ struct ResidualArgs {
   const double* hxy;
   const double* D; const double* D2; const double* Lloc;
   const int* ci;
+  // the same tables as unevaluated float pairs (hi, lo) for the double-float kernels
+  const float2* Lloc_df; const float2* Lce_df;
 };
-void launch_leaf_residual_impl(const ResidualArgs& a, const int* leaf_edges, const double* Lce,
-                               const int* ce, const double* ug, const double* g, double* uc,
-                               double* r_out, double* vflux, int nrhs, cudaStream_t s);
+// Residual r = g - A u, leaf fluxes and u_ce = L_ce,ge u_ge, in double-float arithmetic.
+void launch_leaf_residual_df(const ResidualArgs& a, const int* leaf_edges, const int* ce, const double* ug, const double* g, double* uc,
+                             double* r_out, double* vflux, int nrhs, cudaStream_t s);
 void launch_jump_residual(const int* pairs, int npairs, int q, const double* vflux,
                           double* rho_out, int nrhs, cudaStream_t s);
 void launch_absmax(const double* x, long long n, double* out, cudaStream_t s);

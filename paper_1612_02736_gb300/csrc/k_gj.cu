@@ -71,14 +71,15 @@ __global__ void __launch_bounds__(256) gj_panel_kernel(const GJDesc* __restrict_
     P[e] = M[(long long)pr[i] * R + c0 + j];
   }
   __syncthreads();
-  // column scales for the breakdown test
-  if (tid < nb) {
+  // column scales for the breakdown test: one warp per column, lanes stride the rows
+  const int lane = tid & 31, warp = tid >> 5, nwarp = bs >> 5;
+  for (int j = warp; j < nb; j += nwarp) {
     T mx = T(0);
-    for (int i = 0; i < nrows; ++i) mx = fmax(mx, tabs(P[i * nb + tid]));
-    colscale[tid] = mx;
+    for (int i = lane; i < nrows; i += 32) mx = fmax(mx, tabs(P[i * nb + j]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) colscale[j] = mx;
   }
   __syncthreads();
-  const int lane = tid & 31, warp = tid >> 5, nwarp = bs >> 5;
   for (int j = 0; j < nb; ++j) {
     T best = T(-1);
     int bi = nrows;
@@ -157,7 +158,7 @@ __global__ void __launch_bounds__(256) gj_prep_kernel(const GJDesc* __restrict__
   __syncthreads();
   T* M = work + md.off;
   const int r = blockIdx.x * blockDim.x + tid;
-  if (r < R) {
+  if (r < md.rows) {
     int tp = -1;
     for (int t = 0; t < nb; ++t)
       if (pphys[t] == r) tp = t;
@@ -195,10 +196,10 @@ __global__ void __launch_bounds__(256) gj_update_kernel(const GJDesc* __restrict
   const GJDesc md = d[blockIdx.y];
   if (c0 >= md.K) return;
   const int nb = min(nb_req, md.K - c0);
-  const int R = md.R;
-  const int tiles = (R + UBN - 1) / UBN;
+  const int R = md.R, rows = md.rows;
+  const int tiles = (R + UBN - 1) / UBN;  // column tiles
   const int tm = blockIdx.x / tiles, tn = blockIdx.x - (blockIdx.x / tiles) * tiles;
-  if (tm >= tiles) return;
+  if (tm * UBM >= rows) return;
   const int row0 = tm * UBM, col0 = tn * UBN;
   if (col0 >= c0 && col0 + UBN <= c0 + nb) return;  // tile entirely inside the panel
   __shared__ T Ws[UBM][NBMAX + 1];
@@ -220,7 +221,7 @@ __global__ void __launch_bounds__(256) gj_update_kernel(const GJDesc* __restrict
   for (int e = tid; e < UBM * NBMAX; e += 256) {
     const int i = e / NBMAX, t = e - (e / NBMAX) * NBMAX;
     const int r = row0 + i;
-    Ws[i][t] = (r < R && t < nb) ? M[(long long)r * R + c0 + t] : T(0);
+    Ws[i][t] = (r < rows && t < nb) ? M[(long long)r * R + c0 + t] : T(0);
   }
   const T* pb = prow + (long long)blockIdx.y * prow_stride;
   for (int e = tid; e < NBMAX * UBN; e += 256) {
@@ -249,7 +250,7 @@ __global__ void __launch_bounds__(256) gj_update_kernel(const GJDesc* __restrict
   for (int i = 0; i < 4; ++i) {
     const int li = ty + 16 * i;
     const int r = row0 + li;
-    if (r >= R) continue;
+    if (r >= rows) continue;
     T* Mr = M + (long long)r * R;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -276,7 +277,7 @@ __global__ void __launch_bounds__(256) gj_extract_kernel(const GJDesc* __restric
   for (int i = threadIdx.x; i < K; i += blockDim.x) isig[sig[i]] = i;
   __syncthreads();
   const T* M = work + md.off;
-  const long long total = (long long)R * R;
+  const long long total = (long long)md.rows * R;
   TO* TL = (TO*)dst.TL; TO* TR = (TO*)dst.TR; TO* BL = (TO*)dst.BL; TO* BR = (TO*)dst.BR;
   const long long tlo = dst.TL_off ? dst.TL_off[b] : (long long)b * dst.TL_off_stride;
   const long long tro = dst.TR_off ? dst.TR_off[b] : (long long)b * dst.TR_off_stride;
@@ -336,10 +337,11 @@ void launch_gj_prep(const GJDesc* d, int nmat, int maxR, T* work, const int* per
 }
 
 template <typename T>
-void launch_gj_update(const GJDesc* d, int nmat, int maxR, T* work, const int* perm, T* prow,
+void launch_gj_update(const GJDesc* d, int nmat, int maxR, int maxRows, T* work, const int* perm, T* prow,
                       long long prow_stride, int c0, int nb, cudaStream_t s) {
-  const int tiles = (maxR + UBN - 1) / UBN;
-  dim3 grid(tiles * tiles, nmat);
+  // every matrix needs ceil(rows / UBM) x ceil(R / UBN) tiles, which this grid covers
+  const int tiles = (maxR + UBN - 1) / UBN, rtiles = (maxRows + UBM - 1) / UBM;
+  dim3 grid(rtiles * tiles, nmat);
   gj_update_kernel<T><<<grid, 256, 0, s>>>(d, work, perm, prow, prow_stride, c0, nb);
 }
 
@@ -364,8 +366,8 @@ template void launch_gj_panel<double>(const GJDesc*, int, int, double*, int*, do
 template void launch_gj_panel<float>(const GJDesc*, int, int, float*, int*, float*, int, int, int*, cudaStream_t);
 template void launch_gj_prep<double>(const GJDesc*, int, int, double*, const int*, const double*, double*, long long, int, int, cudaStream_t);
 template void launch_gj_prep<float>(const GJDesc*, int, int, float*, const int*, const float*, float*, long long, int, int, cudaStream_t);
-template void launch_gj_update<double>(const GJDesc*, int, int, double*, const int*, double*, long long, int, int, cudaStream_t);
-template void launch_gj_update<float>(const GJDesc*, int, int, float*, const int*, float*, long long, int, int, cudaStream_t);
+template void launch_gj_update<double>(const GJDesc*, int, int, int, double*, const int*, double*, long long, int, int, cudaStream_t);
+template void launch_gj_update<float>(const GJDesc*, int, int, int, float*, const int*, float*, long long, int, int, cudaStream_t);
 template void launch_gj_extract<double, double>(const GJDesc*, int, int, const double*, const int*, const ExtractDst&, cudaStream_t);
 template void launch_gj_extract<float, double>(const GJDesc*, int, int, const float*, const int*, const ExtractDst&, cudaStream_t);
 

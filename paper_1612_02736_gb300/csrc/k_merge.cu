@@ -25,7 +25,7 @@ __global__ void __launch_bounds__(256) merge_assemble_kernel(const MergeDesc* __
   const TT* Ta = tstore + md.ta_off;
   const TT* Tb = tstore + md.tb_off;
   T* M = work + md.m_off;
-  const long long total = (long long)R * R;
+  const long long total = (long long)md.rows * R;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
     const int r = (int)(e / R);

@@ -1,5 +1,5 @@
-// Solve-stage kernels (Algorithm 2), the FP64 residual used by mixed-precision iterative
-// refinement, and the adjoint helpers.
+// Solve-stage kernels (Algorithm 2), the flux-jump residual used by mixed-precision
+// iterative refinement, and the adjoint helpers.
 //
 // Every operator application of Algorithm 2 -- h = H g on leaves, [w; h] = [X; C X] d and
 // u_gi = S u_ge + w on merges, u_c = [F | S_ci] [g_ci; u_ge] on leaves -- is a batched
@@ -335,108 +335,6 @@ __global__ void gather_reduce_kernel(const int* __restrict__ tab, int n, const T
   }
 }
 
-// FP64 residual of the collocation system on one leaf per CTA (rhs in chunks of RC):
-// refreshes u_ce = L_ce,ge u_ge, then r = g - A u on interior nodes (0 on exterior) and
-// the leaf fluxes v = D_ge,c u (Sec. 3.4).  Derivatives use the tensor structure.
-constexpr int RC = 4;
-
-__global__ void __launch_bounds__(256) leaf_residual_kernel(ResidualArgs a, const int* __restrict__ leaf_edges,
-                                                            const double* __restrict__ Lce, const int* __restrict__ ce,
-                                                            const double* __restrict__ ug, const double* __restrict__ g,
-                                                            double* __restrict__ uc, double* __restrict__ r_out,
-                                                            double* __restrict__ vflux, int nrhs) {
-  const int lf = blockIdx.x;
-  const int p = a.p, q = a.q, pp = p * p, nq = 4 * q, ne = 4 * (p - 1);
-  extern __shared__ __align__(16) unsigned char smraw[];
-  double* sD = reinterpret_cast<double*>(smraw);
-  double* sD2 = sD + pp;
-  double* us = sD2 + pp;          // pp * RC
-  double* uxs = us + pp * RC;     // pp * RC
-  double* uys = uxs + pp * RC;    // pp * RC
-  double* ugs = uys + pp * RC;    // nq * RC
-  const int tid = threadIdx.x, bs = blockDim.x;
-  for (int e = tid; e < pp; e += bs) { sD[e] = a.D[e]; sD2[e] = a.D2[e]; }
-  const double sx = 2.0 / a.hxy[2 * lf], sy = 2.0 / a.hxy[2 * lf + 1];
-  const long long lbase = (long long)lf * pp * nrhs;
-  for (int r0 = 0; r0 < nrhs; r0 += RC) {
-    const int rc = min(RC, nrhs - r0);
-    __syncthreads();
-    for (int e = tid; e < nq * RC; e += bs) {
-      const int gq = e / RC, rr = e - (e / RC) * RC;
-      const int s = gq / q, k = gq - (gq / q) * q;
-      const int node = leaf_edges[4 * lf + s] * q + k;
-      ugs[e] = rr < rc ? ug[(long long)node * nrhs + r0 + rr] : 0.0;
-    }
-    for (int e = tid; e < pp * RC; e += bs) {
-      const int n = e / RC, rr = e - (e / RC) * RC;
-      us[e] = rr < rc ? uc[lbase + (long long)n * nrhs + r0 + rr] : 0.0;
-    }
-    __syncthreads();
-    for (int e = tid; e < ne * RC; e += bs) {
-      const int k = e / RC, rr = e - (e / RC) * RC;
-      double v = 0.0;
-      for (int gq = 0; gq < nq; ++gq) v += Lce[(long long)k * nq + gq] * ugs[gq * RC + rr];
-      const int n = ce[k];
-      us[n * RC + rr] = v;
-      if (rr < rc) uc[lbase + (long long)n * nrhs + r0 + rr] = v;
-    }
-    __syncthreads();
-    for (int e = tid; e < pp * RC; e += bs) {
-      const int n = e / RC, rr = e - (e / RC) * RC;
-      const int ix = n % p, iy = n / p;
-      double sxv = 0.0, syv = 0.0;
-      for (int k = 0; k < p; ++k) {
-        sxv += sD[ix * p + k] * us[(iy * p + k) * RC + rr];
-        syv += sD[iy * p + k] * us[(k * p + ix) * RC + rr];
-      }
-      uxs[e] = sx * sxv;
-      uys[e] = sy * syv;
-    }
-    __syncthreads();
-    for (int e = tid; e < pp * RC; e += bs) {
-      const int n = e / RC, rr = e - (e / RC) * RC;
-      if (rr >= rc) continue;
-      const int ix = n % p, iy = n / p;
-      double res = 0.0;
-      if (ix > 0 && ix < p - 1 && iy > 0 && iy < p - 1) {
-        double uxx = 0.0, uyy = 0.0, uxy = 0.0;
-        for (int k = 0; k < p; ++k) {
-          uxx += sD2[ix * p + k] * us[(iy * p + k) * RC + rr];
-          uyy += sD2[iy * p + k] * us[(k * p + ix) * RC + rr];
-          uxy += sD[iy * p + k] * uxs[(k * p + ix) * RC + rr];
-        }
-        uxx *= sx * sx;
-        uyy *= sy * sy;
-        uxy *= sy;
-        const long long cb = (long long)lf * pp + n;
-        const long long st = a.n_leaf * pp;
-        const double Au = -a.coeffs[cb] * uxx - 2.0 * a.coeffs[st + cb] * uxy - a.coeffs[2 * st + cb] * uyy +
-                          a.coeffs[3 * st + cb] * uxs[e] + a.coeffs[4 * st + cb] * uys[e] +
-                          a.coeffs[5 * st + cb] * us[e];
-        res = g[lbase + (long long)n * nrhs + r0 + rr] - Au;
-      }
-      r_out[lbase + (long long)n * nrhs + r0 + rr] = res;
-    }
-    for (int e = tid; e < nq * RC; e += bs) {
-      const int gq = e / RC, rr = e - (e / RC) * RC;
-      if (rr >= rc) continue;
-      const int s = gq / q, k = gq - (gq / q) * q;
-      double v = 0.0;
-      for (int t = 0; t < p; ++t) {
-        double d;
-        switch (s) {
-          case 0: d = uys[(0 * p + t) * RC + rr]; break;
-          case 1: d = uxs[(t * p + (p - 1)) * RC + rr]; break;
-          case 2: d = uys[((p - 1) * p + t) * RC + rr]; break;
-          default: d = uxs[(t * p + 0) * RC + rr]; break;
-        }
-        v += a.Lloc[k * p + t] * d;
-      }
-      vflux[((long long)lf * nq + gq) * nrhs + r0 + rr] = v;
-    }
-  }
-}
-
 // rho[e q + k] = -(v_a - v_b) on each interior edge; pairs = (edge, leaf_a, side_a,
 // leaf_b, side_b) with a the W/S leaf.
 __global__ void jump_residual_kernel(const int* __restrict__ pairs, int npairs, int q,
@@ -452,61 +350,6 @@ __global__ void jump_residual_kernel(const int* __restrict__ pairs, int npairs, 
     const double va = vflux[((long long)P[1] * nq + P[2] * q + k) * nrhs + r];
     const double vb = vflux[((long long)P[3] * nq + P[4] * q + k) * nrhs + r];
     rho[((long long)P[0] * q + k) * nrhs + r] = -(va - vb);
-  }
-}
-
-// Coefficient gradients (adjoint): grad_k[n] = sum_r gbar[n][r] * t_k(u)[n][r] at interior
-// nodes with t = (u_xx, 2 u_xy, u_yy, -u_x, -u_y, -u) (Sec. 3.2 operator), 0 on exterior.
-__global__ void __launch_bounds__(256) coeff_grad_kernel(ResidualArgs a, const double* __restrict__ uc,
-                                                         const double* __restrict__ gbar,
-                                                         double* __restrict__ grad, int nrhs) {
-  const int lf = blockIdx.x;
-  const int p = a.p, pp = p * p;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  double* sD = reinterpret_cast<double*>(smraw);
-  double* sD2 = sD + pp;
-  double* us = sD2 + pp;        // pp
-  double* uxs = us + pp;        // pp
-  double* acc = uxs + pp;       // 6 * pp
-  const int tid = threadIdx.x, bs = blockDim.x;
-  for (int e = tid; e < pp; e += bs) { sD[e] = a.D[e]; sD2[e] = a.D2[e]; }
-  for (int e = tid; e < 6 * pp; e += bs) acc[e] = 0.0;
-  const double sx = 2.0 / a.hxy[2 * lf], sy = 2.0 / a.hxy[2 * lf + 1];
-  const long long lbase = (long long)lf * pp * nrhs;
-  for (int r = 0; r < nrhs; ++r) {
-    __syncthreads();
-    for (int n = tid; n < pp; n += bs) us[n] = uc[lbase + (long long)n * nrhs + r];
-    __syncthreads();
-    for (int n = tid; n < pp; n += bs) {
-      const int ix = n % p, iy = n / p;
-      double v = 0.0;
-      for (int k = 0; k < p; ++k) v += sD[ix * p + k] * us[iy * p + k];
-      uxs[n] = sx * v;
-    }
-    __syncthreads();
-    for (int n = tid; n < pp; n += bs) {
-      const int ix = n % p, iy = n / p;
-      if (!(ix > 0 && ix < p - 1 && iy > 0 && iy < p - 1)) continue;
-      double uy = 0.0, uxx = 0.0, uyy = 0.0, uxy = 0.0;
-      for (int k = 0; k < p; ++k) {
-        uy += sD[iy * p + k] * us[k * p + ix];
-        uxx += sD2[ix * p + k] * us[iy * p + k];
-        uyy += sD2[iy * p + k] * us[k * p + ix];
-        uxy += sD[iy * p + k] * uxs[k * p + ix];
-      }
-      const double lam = gbar[lbase + (long long)n * nrhs + r];
-      acc[0 * pp + n] += lam * sx * sx * uxx;
-      acc[1 * pp + n] += lam * 2.0 * sy * uxy;
-      acc[2 * pp + n] += lam * sy * sy * uyy;
-      acc[3 * pp + n] -= lam * uxs[n];
-      acc[4 * pp + n] -= lam * sy * uy;
-      acc[5 * pp + n] -= lam * us[n];
-    }
-  }
-  __syncthreads();
-  for (int e = tid; e < 6 * pp; e += bs) {
-    const int k = e / pp, n = e - (e / pp) * pp;
-    grad[((long long)k * a.n_leaf + lf) * pp + n] = acc[e];
   }
 }
 
@@ -644,35 +487,10 @@ void launch_gather_reduce(const int* tab, int nnodes, const TV* src, TV* dst, in
   gather_reduce_kernel<TV><<<grid_for((long long)nnodes * nrhs), 256, 0, s>>>(tab, nnodes, src, dst, nrhs, accumulate);
 }
 
-void launch_leaf_residual_impl(const ResidualArgs& a, const int* leaf_edges, const double* Lce, const int* ce,
-                               const double* ug, const double* g, double* uc, double* r_out, double* vflux,
-                               int nrhs, cudaStream_t s) {
-  const int pp = a.p * a.p;
-  const size_t smem = (size_t)(2 * pp + 3 * pp * RC + 4 * a.q * RC) * sizeof(double);
-  static size_t configured = 0;
-  if (smem > 48 * 1024 && smem > configured) {
-    cudaFuncSetAttribute(leaf_residual_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    configured = smem;
-  }
-  leaf_residual_kernel<<<(unsigned)a.n_leaf, 256, smem, s>>>(a, leaf_edges, Lce, ce, ug, g, uc, r_out, vflux, nrhs);
-}
-
 void launch_jump_residual(const int* pairs, int npairs, int q, const double* vflux, double* rho_out, int nrhs,
                           cudaStream_t s) {
   if (npairs <= 0) return;
   jump_residual_kernel<<<grid_for((long long)npairs * q * nrhs), 256, 0, s>>>(pairs, npairs, q, vflux, rho_out, nrhs);
-}
-
-void launch_coeff_grad(const ResidualArgs& a, const double* uc, const double* gbar, double* grad, int nrhs,
-                       cudaStream_t s) {
-  const int pp = a.p * a.p;
-  const size_t smem = (size_t)(10 * pp) * sizeof(double);
-  static size_t configured = 0;
-  if (smem > 48 * 1024 && smem > configured) {
-    cudaFuncSetAttribute(coeff_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    configured = smem;
-  }
-  coeff_grad_kernel<<<(unsigned)a.n_leaf, 256, smem, s>>>(a, uc, gbar, grad, nrhs);
 }
 
 template void launch_gemm_items<double, double>(const GemmItem*, int, int, int, const double*, const double*,

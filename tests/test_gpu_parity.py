@@ -159,3 +159,28 @@ def test_graph_replay_matches_direct_launches():
         ua, ub = a.solve(fk, gk), b.solve(fk, gk)
         assert ((ua - ub).abs().max() / ub.abs().max()).item() < 1e-13
     torch.cuda.synchronize()
+
+
+def test_reused_tree_plan_matches_fresh_tree():
+    # Builds on one tree reuse its host plan: new coefficients, both precisions and other
+    # p on the same tree must give bit-identical results to builds on freshly made trees.
+    from paper_1612_02736_gb300 import Solver
+    import torch
+    case = make_case(4, 8, 10, nrhs=2)
+    case2 = make_case(4, 8, 10, nrhs=2, rect=(0.0, 0.0, 1.0, 1.0), seed=1)
+    c2 = case2["coeffs"] * np.array([1.1, 0.5, 0.9, -1.0, 2.0, 1.5])[:, None, None]
+    t = gpu_tree(case)
+    f, g = to_dev(case["f"]), to_dev(case["g"])
+    for prec in ("fp64", "mixed", "fp64"):
+        for coeffs in (case["coeffs"], c2, case["coeffs"]):
+            u_re = Solver(t, to_dev(coeffs), 10, prec).solve(f, g)
+            u_new = Solver(gpu_tree(case), to_dev(coeffs), 10, prec).solve(f, g)
+            assert torch.equal(u_re, u_new)
+    # another p on the same tree, then back
+    case8 = make_case(4, 8, 8, nrhs=1)
+    u8 = Solver(t, to_dev(case8["coeffs"]), 8).solve(to_dev(case8["f"]), to_dev(case8["g"]))
+    (uc, _), _ = oracle_solve(case8)
+    assert rel_linf(u8.cpu().numpy(), uc) < 1e-10
+    u_again = Solver(t, to_dev(case["coeffs"]), 10).solve(f, g)
+    (uo, _), _ = oracle_solve(case)
+    assert rel_linf(u_again.cpu().numpy(), uo) < 1e-10
