@@ -298,6 +298,29 @@ def run_gpu(args, rank, world, local):
         e2e = {"value": world * dof / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
+    # ---- solve-only throughput at nrhs 1, 8, 64 on one built operator of each precision
+    # (repeat solves: the FP64 sweep replays its captured CUDA graph from the second call)
+    sweep = {}
+    s64 = Solver(tree, coeffs, P, "fp64")
+    smx = Solver(tree, coeffs, P, "mixed")
+    for nr in (1, 8, 64):
+        fk, gk = f[:, :nr].contiguous(), g[..., :nr].contiguous()
+        row = {}
+        for name, s in (("fp64", s64), ("mixed", smx)):
+            for _ in range(3):
+                s.solve(fk, gk)
+            torch.cuda.synchronize()
+            a = ev()
+            for _ in range(5):
+                s.solve(fk, gk)
+            b = ev()
+            torch.cuda.synchronize()
+            ms = allmax(a.elapsed_time(b), world) / 5
+            row[name] = {"ms": ms, "dof_per_s": world * n_leaf * P * P * nr / (ms / 1e3)}
+        sweep[str(nr)] = row
+    s64.close()
+    smx.close()
+
     # ---- roofline of the dominant kernel
     peaks, src = measured_peaks()
     dom = max(table, key=lambda r: r["ms"])
@@ -332,6 +355,7 @@ def run_gpu(args, rank, world, local):
                      "solve_mixed": sm},
         "build_s": {"fp64": b64, "mixed": bm},
         "solve_dof_per_s": {"fp64": dof / s64, "mixed": dof / sm},
+        "solve_only_by_nrhs": sweep,
         "grad_forward_ratio": {"adjoint_over_build_plus_solve": a64 / (b64 + s64), "adjoint_over_solve": a64 / s64},
         "mixed": {"rel_linf_vs_fp64": rel_err, "ir_steps": int(np.median(iters)) if iters else None},
         "gpu_launches": launches, "gpu_launches_per_step": launches / args.steps,
