@@ -84,9 +84,20 @@ typedef struct {
                         * one captured CUDA graph of the whole sweep per nrhs (the inputs
                         * are copied into and the result out of staging buffers the
                         * handle owns); 0 launches the kernels one by one              */
+  int autotune;        /* 1: the first time a launch shape is met, time each candidate tile
+                        * configuration once (the elimination panel width of a batch of
+                        * leaves or merges; the right-hand-side tile of a solve product) and
+                        * keep the fastest for the rest of the process; 0 (default): fixed
+                        * rules.  Candidates of one product give bit-identical results;
+                        * panel widths change the rounding of the build within the stated
+                        * tolerances.  Tuning runs synchronise the stream                 */
+  const char* autotune_cache; /* with autotune: a text file of earlier choices, read once
+                        * and appended to (one "key value" line per shape); NULL keeps the
+                        * choices in process memory only.  The library copies the path    */
 } hps_opts;
 
-/* Fills *opts with the defaults above (FP64, q = p - 1, store leaf operators, graphs on). */
+/* Fills *opts with the defaults above (FP64, q = p - 1, store leaf operators, graphs on,
+ * no autotuning). */
 void hps_opts_default(hps_opts* opts);
 
 /* Uniform tree of nx x ny equal leaves over [x0,x1] x [y0,y1] by recursive halving

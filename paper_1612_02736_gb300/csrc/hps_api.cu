@@ -46,11 +46,6 @@ int fail(int code, const std::string& msg) {
   return code;
 }
 
-struct CudaError {
-  int code;
-  std::string msg;
-};
-
 #define CK(call)                                                                                    \
   do {                                                                                              \
     cudaError_t e_ = (call);                                                                        \
@@ -258,6 +253,7 @@ struct hps_handle {
   std::vector<long long> mo, so;  // per box: Mleft and S offsets
   std::vector<long long> toff;    // per box: T block offset in the build's T store
   long long tstore_elems = 0;     // size of the build's T store
+  std::string tune_path;          // autotuner cache file ("" = process memory only)
   std::vector<long long> ttmp;    // coarsened boxes: T before coarsening (T store)
   std::vector<long long> puo, pdo, pco;  // coarsened boxes: P_up, P_down, P_up(fine, coarse)
   std::vector<int> k3, k12, k12o; // |J3|, |I_ge| seen by the parent, |J1 + J2|
@@ -969,19 +965,20 @@ long long tstore_elems(const hps_handle* h) { return h->tstore_elems; }
 // Panel width: 16 for batches of many matrices; 8 for a level of few large matrices, whose
 // panels run on one CTA each and whose per-panel work grows with nb; capped so the panel
 // fits in shared memory.
-int choose_nb(int K, size_t elem, int nmat) {
-  int nb = (int)((200 * 1024) / ((size_t)std::max(K, 1) * (elem + 4)));
-  return std::max(1, std::min(nmat < 64 ? 8 : 16, nb));
+int nb_cap(int K, size_t elem) {
+  return std::max(1, std::min(16, (int)((200 * 1024) / ((size_t)std::max(K, 1) * (elem + 4)))));
 }
+int choose_nb(int K, size_t elem, int nmat) { return std::min(nmat < 64 ? 8 : 16, nb_cap(K, elem)); }
 
 // rk: (R, K, rows) of every matrix of the batch, for the grid and the flop counts of the
 // timing records.
 template <typename T>
 void run_gj(const GJDesc* gj, int nmat, int maxR, int maxK, T* work, int* perm, T* pinv, T* prow,
-            int* status, const std::vector<std::array<int, 3>>& rk, const char* what, cudaStream_t s) {
+            int* status, const std::vector<std::array<int, 3>>& rk, const char* what, cudaStream_t s,
+            int nb_force = 0) {
   int maxRows = 0;
   for (const auto& m : rk) maxRows = std::max(maxRows, m[2]);
-  const int nb = choose_nb(maxK, sizeof(T), nmat);
+  const int nb = nb_force > 0 ? std::min(nb_force, nb_cap(maxK, sizeof(T))) : choose_nb(maxK, sizeof(T), nmat);
   const std::string sf = std::string(tsuf<T>()) + ":" + what;
   TIMED(("gj_init_" + sf).c_str(), 0, 0, launch_gj_init<T>(gj, nmat, perm, s));
   CKL();
@@ -1004,6 +1001,28 @@ void run_gj(const GJDesc* gj, int nmat, int maxR, int maxK, T* work, int* perm, 
           launch_gj_update<T>(gj, nmat, maxR, maxRows, work, perm, prow, prow_stride, c0, nb, s));
   }
   CKL();
+}
+
+// Panel width of one batched elimination: the fixed rule, or with autotuning the fastest
+// of 4, 8 and 16 (within the shared-memory cap) measured on the batch itself; elim(nb)
+// assembles the batch's matrices and eliminates them with panel width nb.
+int pick_nb(const hps_handle* h, const char* what, size_t elem, const std::vector<std::array<int, 3>>& rk,
+            int nmat, cudaStream_t s, const std::function<void(int)>& elim) {
+  int maxR = 0, maxK = 0, maxRows = 0;
+  for (const auto& m : rk) {
+    maxR = std::max(maxR, m[0]);
+    maxK = std::max(maxK, m[1]);
+    maxRows = std::max(maxRows, m[2]);
+  }
+  const int def = choose_nb(maxK, elem, nmat);
+  if (!h->opts.autotune) return def;
+  std::vector<int> cands;
+  for (int nb : {4, 8, 16})
+    if (nb <= nb_cap(maxK, elem)) cands.push_back(nb);
+  if (cands.empty()) return def;
+  const std::string key = std::string("gj_nb ") + what + " e" + std::to_string(elem) + " n" + std::to_string(nmat) +
+                          " R" + std::to_string(maxR) + " K" + std::to_string(maxK) + " rows" + std::to_string(maxRows);
+  return tuned_choice(key, cands, h->tune_path, [&](int nb) { return time_on_stream(s, [&] { elim(nb); }); });
 }
 
 void build_stage(hps_handle* h, const double* coeffs, cudaStream_t s) {
@@ -1054,11 +1073,14 @@ void build_stage(hps_handle* h, const double* coeffs, cudaStream_t s) {
       for (int i = 0; i < n; ++i) gd[i].box = h->tree.leaves[l0 + i];
       GJDesc* dgd = (GJDesc*)get(n * sizeof(GJDesc));
       CK(cudaMemcpyAsync(dgd, gd.data(), n * sizeof(GJDesc), cudaMemcpyHostToDevice, s));
-      TIMED("leaf_assemble_f64", 0, (double)n * per_leaf * 8,
-            launch_leaf_assemble<double>(coeffs, h->n_leaf, l0, n, h->dhxy, h->p, h->q, tb, work, per_leaf, s));
-      CKL();
-      run_gj<double>(dgd, n, R, m, work, perm, pinv, prow, h->d_status,
-                     std::vector<std::array<int, 3>>(n, {R, m, R}), "leaf", s);
+      const std::vector<std::array<int, 3>> rk(n, {R, m, R});
+      auto elim = [&](int nb) {
+        TIMED("leaf_assemble_f64", 0, (double)n * per_leaf * 8,
+              launch_leaf_assemble<double>(coeffs, h->n_leaf, l0, n, h->dhxy, h->p, h->q, tb, work, per_leaf, s));
+        CKL();
+        run_gj<double>(dgd, n, R, m, work, perm, pinv, prow, h->d_status, rk, "leaf", s, nb);
+      };
+      elim(pick_nb(h, "leaf", sizeof(double), rk, n, s, elim));
       ExtractDst dst{};
       const long long gl0 = h->gl_base + (long long)l0 * m * R;
       dst.TL = h->ops64 + gl0; dst.TL_off_stride = (long long)m * R; dst.TL_ld = R;
@@ -1116,9 +1138,12 @@ void build_stage(hps_handle* h, const double* coeffs, cudaStream_t s) {
         int* pm = (int*)get((size_t)std::max(1, lv.perm_elems) * sizeof(int));
         double* pi = (double*)get((size_t)nmat * 256 * sizeof(double));
         double* pr = (double*)get((size_t)nmat * 16 * lv.maxR * sizeof(double));
-        TIMED("merge_assemble_f64", 0, wbytes, launch_merge_assemble<double, double>(lv.md, nmat, lv.maxR, tstore, h->didx, w, s));
-        CKL();
-        run_gj<double>(lv.gj, nmat, lv.maxR, lv.maxK, w, pm, pi, pr, h->d_status, rk, "merge", s);
+        auto elim = [&](int nb) {
+          TIMED("merge_assemble_f64", 0, wbytes, launch_merge_assemble<double, double>(lv.md, nmat, lv.maxR, tstore, h->didx, w, s));
+          CKL();
+          run_gj<double>(lv.gj, nmat, lv.maxR, lv.maxK, w, pm, pi, pr, h->d_status, rk, "merge", s, nb);
+        };
+        elim(pick_nb(h, "merge", sizeof(double), rk, nmat, s, elim));
         TIMED("gj_extract_f64", 0, wbytes, launch_gj_extract<double, double>(lv.gj, nmat, lv.maxR, w, pm, dst, s));
         CKL();
       } else {
@@ -1126,9 +1151,12 @@ void build_stage(hps_handle* h, const double* coeffs, cudaStream_t s) {
         int* pm = (int*)get((size_t)std::max(1, lv.perm_elems) * sizeof(int));
         float* pi = (float*)get((size_t)nmat * 256 * sizeof(float));
         float* pr = (float*)get((size_t)nmat * 16 * lv.maxR * sizeof(float));
-        TIMED("merge_assemble_f32", 0, wbytes, launch_merge_assemble<float, double>(lv.md, nmat, lv.maxR, tstore, h->didx, w, s));
-        CKL();
-        run_gj<float>(lv.gj, nmat, lv.maxR, lv.maxK, w, pm, pi, pr, h->d_status, rk, "merge", s);
+        auto elim = [&](int nb) {
+          TIMED("merge_assemble_f32", 0, wbytes, launch_merge_assemble<float, double>(lv.md, nmat, lv.maxR, tstore, h->didx, w, s));
+          CKL();
+          run_gj<float>(lv.gj, nmat, lv.maxR, lv.maxK, w, pm, pi, pr, h->d_status, rk, "merge", s, nb);
+        };
+        elim(pick_nb(h, "merge", sizeof(float), rk, nmat, s, elim));
         TIMED("gj_extract_f32", 0, wbytes, launch_gj_extract<float, double>(lv.gj, nmat, lv.maxR, w, pm, dst, s));
         CKL();
       }
@@ -1240,8 +1268,27 @@ void solve_pass(hps_handle* h, const TA* ops, const double* f, const TV* g, cons
   const std::string sf = tsuf<TA>();
   auto gemm = [&](const char* step, const ItemSet& is, const TV* B0, const TV* B1, TV* C, const TV* Add,
                   double beta) {
+    int bn = 0;
+    // right-hand-side tile: tuned for products that overwrite their output (beta = 0), so
+    // that a trial run can be repeated; looked up only while the sweep is being captured
+    if (h->opts.autotune && nrhs > 16 && beta == 0.0 && is.n > 0) {
+      std::vector<int> cands{16, 32};
+      if (nrhs > 32) cands.push_back(64);
+      const std::string key = "gemm_bn " + std::string(step) + " " + sf + " nrhs" + std::to_string(nrhs) +
+                              " items" + std::to_string(is.n) + " elems" + std::to_string((long long)is.elems);
+      cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+      CK(cudaStreamIsCapturing(s, &cs));
+      std::function<float(int)> trial;
+      if (cs == cudaStreamCaptureStatusNone)
+        trial = [&](int b) {
+          return time_on_stream(s, [&] {
+            launch_gemm_items<TA, TV>(is.dev, is.n, ROWBLK, 0, ops, B0, B1, C, Add, idx, nrhs, beta, s, b);
+          });
+        };
+      bn = tuned_choice(key, cands, h->tune_path, trial);
+    }
     TIMED(("gemm_" + std::string(step) + "_" + sf).c_str(), 2.0 * is.elems * nrhs, is.elems * sizeof(TA),
-          launch_gemm_items<TA, TV>(is.dev, is.n, ROWBLK, 0, ops, B0, B1, C, Add, idx, nrhs, beta, s));
+          launch_gemm_items<TA, TV>(is.dev, is.n, ROWBLK, 0, ops, B0, B1, C, Add, idx, nrhs, beta, s, bn));
   };
   auto gemmp = [&](const char* step, const Prod& pr, const TV* B0, TV* C, const TV* Add, double beta) {
     gemm(step, pr.direct, B0, nullptr, C, Add, beta);
@@ -1394,6 +1441,8 @@ void hps_opts_default(hps_opts* o) {
   o->ir_max_iter = 0;
   o->fp64_top_levels = -1;
   o->use_graphs = 1;
+  o->autotune = 0;
+  o->autotune_cache = nullptr;
 }
 
 const char* hps_last_error(void) { return g_err.c_str(); }
@@ -1657,6 +1706,7 @@ int hps_build(const hps_tree* tree, const double* coeffs, int p, const hps_opts*
         plan = hp;
       }
     }
+    h->tune_path = o.autotune_cache ? o.autotune_cache : "";
     // device tables
     h->dD = upload(h->al, s, h->rt.D, h->owned);
     h->dD2 = upload(h->al, s, h->rt.D2, h->owned);

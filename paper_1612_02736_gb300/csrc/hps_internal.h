@@ -4,6 +4,7 @@
 
 #include <array>
 #include <cstdint>
+#include <functional>
 #include <map>
 #include <string>
 #include <vector>
@@ -195,11 +196,12 @@ struct BGemm {
 void launch_bgemm(const BGemm* d, int n, int maxM, int maxN, const double* A, const double* B, double* C,
                   cudaStream_t s);
 
-// Batched gathered products.
+// Batched gathered products.  bn: right-hand-side tile of the tiled product (16, 32 or 64;
+// 0 = fixed rule), used for nrhs > 4.
 template <typename TA, typename TV>
 void launch_gemm_items(const GemmItem* items, int nitems, int maxM, int trans, const TA* A,
                        const TV* B0, const TV* B1, TV* C, const TV* Add, const int* idx,
-                       int nrhs, double beta, cudaStream_t s);
+                       int nrhs, double beta, cudaStream_t s, int bn = 0);
 
 // Split-K partial products: rows [0, M) of one output block were computed in nsplit K
 // ranges into the partial buffer P (rows p_row + j * M + i); the reduction writes
@@ -265,6 +267,21 @@ struct DownScatter {  // adjoint of the up gather: distribute hbar_tau and dbar 
 template <typename TV>
 void launch_down_scatter(const DownScatter* g, int n, int maxrows, TV* VB, const TV* dbar,
                          double* rhobar, const int* idx, int nrhs, cudaStream_t s);
+
+// Error thrown inside the library and turned into a status code at the C boundary.
+struct CudaError {
+  int code;
+  std::string msg;
+};
+
+// Tile autotuner: tuned_choice returns the stored choice for key, or runs trial_ms for
+// every candidate (each returns the measured milliseconds of one run), keeps the fastest
+// in process memory and appends it to the cache file at path (empty: none).  With an
+// empty trial_ms it only looks up, and returns 0 for a shape not tuned yet.
+// time_on_stream runs a callable between two CUDA events on s and synchronises.
+int tuned_choice(const std::string& key, const std::vector<int>& cands, const std::string& path,
+                 const std::function<float(int)>& trial_ms);
+float time_on_stream(cudaStream_t s, const std::function<void()>& run);
 
 // Optional launch timing (enabled with hps_timing_enable): records a pair of CUDA events
 // around the launches made while the scope is alive.

@@ -401,7 +401,7 @@ inline int grid_for(long long n, int bs = 256, int cap = 8192) {
 template <typename TA, typename TV>
 void launch_gemm_items(const GemmItem* items, int nitems, int maxM, int trans, const TA* A, const TV* B0,
                        const TV* B1, TV* C, const TV* Add, const int* idx, int nrhs, double beta,
-                       cudaStream_t s) {
+                       cudaStream_t s, int bn) {
   (void)maxM;
   if (nitems <= 0) return;
   const TV b = (TV)beta;
@@ -417,12 +417,17 @@ void launch_gemm_items(const GemmItem* items, int nitems, int maxM, int trans, c
     }
     return;
   }
-  if (nrhs <= 16) {
-    dim3 grid(nitems, (nrhs + 15) / 16);
+  // right-hand-side tile: the caller's (autotuned) choice, else 16 up to 16 rhs and 64 above;
+  // every choice computes each output with the same k order (bit-identical results)
+  const int BN = (bn == 16 || bn == 32 || bn == 64) ? bn : (nrhs <= 16 ? 16 : 64);
+  dim3 grid(nitems, (nrhs + BN - 1) / BN);
+  if (BN == 16) {
     if (trans) gemm_items_kernel<TA, TV, 16, true><<<grid, 256, 0, s>>>(items, A, B0, B1, C, Add, idx, nrhs, b);
     else gemm_items_kernel<TA, TV, 16, false><<<grid, 256, 0, s>>>(items, A, B0, B1, C, Add, idx, nrhs, b);
+  } else if (BN == 32) {
+    if (trans) gemm_items_kernel<TA, TV, 32, true><<<grid, 256, 0, s>>>(items, A, B0, B1, C, Add, idx, nrhs, b);
+    else gemm_items_kernel<TA, TV, 32, false><<<grid, 256, 0, s>>>(items, A, B0, B1, C, Add, idx, nrhs, b);
   } else {
-    dim3 grid(nitems, (nrhs + 63) / 64);
     if (trans) gemm_items_kernel<TA, TV, 64, true><<<grid, 256, 0, s>>>(items, A, B0, B1, C, Add, idx, nrhs, b);
     else gemm_items_kernel<TA, TV, 64, false><<<grid, 256, 0, s>>>(items, A, B0, B1, C, Add, idx, nrhs, b);
   }
@@ -495,10 +500,10 @@ void launch_jump_residual(const int* pairs, int npairs, int q, const double* vfl
 
 template void launch_gemm_items<double, double>(const GemmItem*, int, int, int, const double*, const double*,
                                                 const double*, double*, const double*, const int*, int, double,
-                                                cudaStream_t);
+                                                cudaStream_t, int);
 template void launch_gemm_items<float, float>(const GemmItem*, int, int, int, const float*, const float*,
                                               const float*, float*, const float*, const int*, int, double,
-                                              cudaStream_t);
+                                              cudaStream_t, int);
 template void launch_split_reduce<double>(const SplitRed*, int, const double*, double*, const double*, const int*,
                                           int, double, cudaStream_t);
 template void launch_split_reduce<float>(const SplitRed*, int, const float*, float*, const float*, const int*, int,

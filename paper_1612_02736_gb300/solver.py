@@ -130,10 +130,13 @@ class Solver:
 
     coeffs: CUDA float64 tensor (6, n_leaf, p*p) with c11, c12, c22, c1, c2, c at every leaf
     Chebyshev node.  precision: 'fp64' or 'mixed' (FP32 sweeps + FP64 iterative refinement).
+    autotune: time the candidate tile configurations of each new launch shape once and keep
+    the fastest (autotune_cache: a text file that keeps the choices across processes).
     """
 
     def __init__(self, tree, coeffs, p, precision="fp64", q=None, ir_tol=None, ir_max_iter=None,
-                 fp64_top_levels=None, store_leaf_ops=True, use_graphs=True, allocator="torch"):
+                 fp64_top_levels=None, store_leaf_ops=True, use_graphs=True, autotune=False,
+                 autotune_cache=None, allocator="torch"):
         lib = N.load()
         if not (coeffs.is_cuda and coeffs.dtype == torch.float64 and coeffs.is_contiguous()):
             raise ValueError("coeffs must be a contiguous CUDA float64 tensor")
@@ -150,6 +153,9 @@ class Solver:
             opts.fp64_top_levels = fp64_top_levels
         opts.store_leaf_ops = 1 if store_leaf_ops else 0
         opts.use_graphs = 1 if use_graphs else 0
+        opts.autotune = 1 if autotune else 0
+        self._tune_path = None if autotune_cache is None else str(autotune_cache).encode()
+        opts.autotune_cache = self._tune_path
         self.tree, self.p, self.precision = tree, p, precision
         self._alloc = _allocator() if allocator == "torch" else None
         out = C.c_void_p()
