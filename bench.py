@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--nrhs", type=int, default=64)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="fixed tile rules instead of the autotuner (profiling captures of a chosen launch)")
     ap.add_argument("--nx", type=int, default=64, help="leaves per side (64 is the benchmark workload; "
                     "smaller values are for profiling captures)")
     args = ap.parse_args()
@@ -215,6 +217,8 @@ def run_gpu(args, rank, world, local):
     del s_obs
 
     stream = torch.cuda.current_stream()
+    # tile autotuner: the warm-up steps tune every launch shape once (kept in memory)
+    tune = not args.no_autotune
 
     def ev():
         e = torch.cuda.Event(enable_timing=True)
@@ -223,13 +227,13 @@ def run_gpu(args, rank, world, local):
 
     def step(coeffs, f, g, record):
         t = [ev()]
-        s64 = Solver(tree, coeffs, P, "fp64")
+        s64 = Solver(tree, coeffs, P, "fp64", autotune=tune)
         t.append(ev())
         u64 = s64.solve(f, g)
         t.append(ev())
         fb, gb, cb = s64.adjoint(u64 - u_obs, u=u64)
         t.append(ev())
-        sm = Solver(tree, coeffs, P, "mixed")
+        sm = Solver(tree, coeffs, P, "mixed", autotune=tune)
         t.append(ev())
         um = sm.solve(f, g)
         t.append(ev())
@@ -301,8 +305,8 @@ def run_gpu(args, rank, world, local):
     # ---- solve-only throughput at nrhs 1, 8, 64 on one built operator of each precision
     # (repeat solves: the FP64 sweep replays its captured CUDA graph from the second call)
     sweep = {}
-    s64 = Solver(tree, coeffs, P, "fp64")
-    smx = Solver(tree, coeffs, P, "mixed")
+    s64 = Solver(tree, coeffs, P, "fp64", autotune=tune)
+    smx = Solver(tree, coeffs, P, "mixed", autotune=tune)
     for nr in (1, 8, 64):
         fk, gk = f[:, :nr].contiguous(), g[..., :nr].contiguous()
         row = {}
@@ -350,6 +354,7 @@ def run_gpu(args, rank, world, local):
         "config": {"workload": workload(), "leaves": n_leaf, "p": P, "q": P - 1, "nrhs": nrhs,
                    "dof_per_rhs": n_leaf * P * P, "paper_N_per_rhs": NX * NX * (P - 1) ** 2 + 2 * NX * (P - 1) + 1,
                    "parallelism": "replicas" if world > 1 else "single",
+                   "tiles": "fixed rules" if args.no_autotune else "autotuned during warm-up",
                    "l2": "inputs larger than L2 (operator store of 2.7 GB streamed per solve)"},
         "phases_s": {"build_fp64": b64, "solve_fp64": s64, "adjoint_fp64": a64, "build_mixed": bm,
                      "solve_mixed": sm},
