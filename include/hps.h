@@ -94,10 +94,16 @@ typedef struct {
   const char* autotune_cache; /* with autotune: a text file of earlier choices, read once
                         * and appended to (one "key value" line per shape); NULL keeps the
                         * choices in process memory only.  The library copies the path    */
+  int shared_leaf;     /* leaf operators shared by every leaf (the constant-coefficient remark
+                        * of Sec. 7.1): -1 (default) shares them when every leaf has the same
+                        * size and the same coefficient values at its interior nodes (checked
+                        * on the device at build time, one synchronisation); 0 never; 1
+                        * requires it (INVALID_ARG when the leaves differ).  Shared, one
+                        * leaf is eliminated and stored, and store_leaf_ops is ignored     */
 } hps_opts;
 
 /* Fills *opts with the defaults above (FP64, q = p - 1, store leaf operators, graphs on,
- * no autotuning). */
+ * no autotuning, leaf operators shared when the leaves allow it). */
 void hps_opts_default(hps_opts* opts);
 
 /* Uniform tree of nx x ny equal leaves over [x0,x1] x [y0,y1] by recursive halving

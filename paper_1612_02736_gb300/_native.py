@@ -33,7 +33,8 @@ class hps_allocator(C.Structure):
 class hps_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("q", C.c_int), ("store_leaf_ops", C.c_int),
                 ("ir_tol", C.c_double), ("ir_max_iter", C.c_int), ("fp64_top_levels", C.c_int),
-                ("use_graphs", C.c_int), ("autotune", C.c_int), ("autotune_cache", C.c_char_p)]
+                ("use_graphs", C.c_int), ("autotune", C.c_int), ("autotune_cache", C.c_char_p),
+                ("shared_leaf", C.c_int)]
 
 
 P = C.c_void_p

@@ -254,6 +254,7 @@ struct hps_handle {
   std::vector<long long> toff;    // per box: T block offset in the build's T store
   long long tstore_elems = 0;     // size of the build's T store
   std::string tune_path;          // autotuner cache file ("" = process memory only)
+  bool shared = false;            // one leaf's operators serve every leaf (equal leaves)
   std::vector<long long> ttmp;    // coarsened boxes: T before coarsening (T store)
   std::vector<long long> puo, pdo, pco;  // coarsened boxes: P_up, P_down, P_up(fine, coarse)
   std::vector<int> k3, k12, k12o; // |J3|, |I_ge| seen by the parent, |J1 + J2|
@@ -441,7 +442,7 @@ void make_plan(hps_handle* h, HostPlan& hp) {
   // operator pool layout
   long long off = 0;
   const long long gsz = (long long)m * (m + nq), hsz = (long long)nq * m;
-  h->econ = h->opts.store_leaf_ops == 0;
+  h->econ = h->opts.store_leaf_ops == 0 && !h->shared;
   if (h->econ) {
     // leaf operators live in a per-chunk buffer: about 512 MiB of operators and workspace
     const long long per = (long long)(m + nq) * (m + nq) + gsz + hsz;
@@ -449,10 +450,11 @@ void make_plan(hps_handle* h, HostPlan& hp) {
     h->gl_base = 0;
     h->h_base = (long long)h->echunk * gsz;
   } else {
+    const long long nl = h->shared ? 1 : h->n_leaf;  // shared: one leaf's F, S_ci, H
     h->gl_base = off;
-    off += (long long)h->n_leaf * gsz;
+    off += nl * gsz;
     h->h_base = off;
-    off += (long long)h->n_leaf * hsz;
+    off += nl * hsz;
   }
   h->lce_base = off;
   off += (long long)h->ne * nq;
@@ -522,8 +524,8 @@ void make_plan(hps_handle* h, HostPlan& hp) {
   toff.assign(nb, -1);
   long long tsz = 0;
   for (int lf = 0; lf < h->n_leaf; ++lf) {
-    toff[t.leaves[lf]] = tsz;
-    tsz += (long long)nq * nq;
+    toff[t.leaves[lf]] = h->shared ? 0 : tsz;  // shared: every leaf reads leaf 0's T
+    if (!h->shared || lf == 0) tsz += (long long)nq * nq;
   }
   h->ttmp.assign(nb, -1);
   for (int b = 0; b < nb; ++b) {
@@ -682,7 +684,8 @@ void make_plan(hps_handle* h, HostPlan& hp) {
                         &aH = hp.aH;
   for (int lf = 0; lf < h->n_leaf; ++lf) {
     const int b = t.leaves[lf];
-    const int slot = h->econ ? lf % h->echunk : lf;  // econ: offsets inside the chunk buffer
+    // econ: offsets inside the chunk buffer; shared: every leaf applies leaf 0's operators
+    const int slot = h->shared ? 0 : (h->econ ? lf % h->echunk : lf);
     const long long gl = h->gl_base + (long long)slot * gsz;
     const long long hb = h->h_base + (long long)slot * hsz;
     add_product(lup, hb, m, nq, m, m, lf * pp, h->off_ci, 0, -1, h->vrow[b], -1, -1, false);
@@ -744,7 +747,7 @@ Prod upload_prod(hps_handle* h, cudaStream_t s, const ProdHost& ph) {
 // the same problem) copies it instead of recomputing it.
 struct PlanCache {
   struct Entry {
-    std::array<int, 5> key;
+    std::array<int, 6> key;
     std::shared_ptr<const hps_handle> layout;  // the handle's host fields after planning
     std::shared_ptr<const HostPlan> plan;
   };
@@ -754,9 +757,9 @@ struct PlanCache {
 
 namespace {
 
-std::array<int, 5> plan_key(int p, const hps_opts& o) {
+std::array<int, 6> plan_key(int p, const hps_opts& o, bool shared) {
   const int top = o.precision == HPS_FP64 ? 0 : (o.fp64_top_levels < 0 ? 1 : o.fp64_top_levels);
-  return {p, o.q, o.precision, top, o.store_leaf_ops};
+  return {p, o.q, o.precision, top, shared ? 1 : o.store_leaf_ops, shared ? 1 : 0};
 }
 
 void upload_plan(hps_handle* h, const HostPlan& hp, cudaStream_t s) {
@@ -1052,7 +1055,8 @@ void build_stage(hps_handle* h, const double* coeffs, cudaStream_t s) {
     // ---- leaves (FP64 always), in chunks
     const long long per_leaf = (long long)R * R;
     const long long budget = 3ll << 30;  // bytes of elimination workspace per chunk
-    int chunk = (int)std::max<long long>(1, std::min<long long>(h->n_leaf, budget / (per_leaf * 8)));
+    const int n_build = h->shared ? 1 : h->n_leaf;  // shared: leaf 0 stands for every leaf
+    int chunk = (int)std::max<long long>(1, std::min<long long>(n_build, budget / (per_leaf * 8)));
     chunk = std::min(chunk, 8192);
     double* work = (double*)get((size_t)per_leaf * chunk * sizeof(double));
     int* perm = (int*)get((size_t)chunk * m * sizeof(int));
@@ -1068,8 +1072,8 @@ void build_stage(hps_handle* h, const double* coeffs, cudaStream_t s) {
       gd[i].box = 0;
     }
     LeafTablesDev tb{h->dD, h->dD2, h->dLs, h->dDLs, h->dLloc, h->dDceL, h->didx + h->off_ci};
-    for (int l0 = 0; l0 < h->n_leaf; l0 += chunk) {
-      const int n = std::min(chunk, h->n_leaf - l0);
+    for (int l0 = 0; l0 < n_build; l0 += chunk) {
+      const int n = std::min(chunk, n_build - l0);
       for (int i = 0; i < n; ++i) gd[i].box = h->tree.leaves[l0 + i];
       GJDesc* dgd = (GJDesc*)get(n * sizeof(GJDesc));
       CK(cudaMemcpyAsync(dgd, gd.data(), n * sizeof(GJDesc), cudaMemcpyHostToDevice, s));
@@ -1443,6 +1447,7 @@ void hps_opts_default(hps_opts* o) {
   o->use_graphs = 1;
   o->autotune = 0;
   o->autotune_cache = nullptr;
+  o->shared_leaf = -1;
 }
 
 const char* hps_last_error(void) { return g_err.c_str(); }
@@ -1577,9 +1582,22 @@ namespace {
 
 // Options, reference tables, node sets and the size checks shared by hps_build and
 // hps_plan_check.  Returns an empty string or the reason the tree/options are rejected.
-std::string setup_host(hps_handle* h, const Tree& tree, int p, const hps_opts& o) {
+// Every leaf spans the same number of finest-grid units in x and in y (so all leaves have
+// the same size and the same reference-to-physical scaling).
+bool equal_leaf_spans(const Tree& t) {
+  if (t.leaves.empty()) return false;
+  const Box& b0 = t.boxes[t.leaves[0]];
+  for (int b : t.leaves) {
+    const Box& bx = t.boxes[b];
+    if (bx.i1 - bx.i0 != b0.i1 - b0.i0 || bx.j1 - bx.j0 != b0.j1 - b0.j0) return false;
+  }
+  return true;
+}
+
+std::string setup_host(hps_handle* h, const Tree& tree, int p, const hps_opts& o, bool shared) {
   h->tree = tree;
   h->opts = o;
+  h->shared = shared;
   h->p = p;
   h->q = o.q;
   h->pp = p * p;
@@ -1622,6 +1640,7 @@ int check_opts(int p, const hps_opts* opts, hps_opts& o) {
   if (o.store_leaf_ops != 0 && o.store_leaf_ops != 1) return fail(HPS_ERR_INVALID_ARG, "store_leaf_ops must be 0 or 1");
   if (o.store_leaf_ops == 0 && o.precision != HPS_FP64)
     return fail(HPS_ERR_INVALID_ARG, "leaf recomputation (store_leaf_ops = 0) needs precision HPS_FP64");
+  if (o.shared_leaf < -1 || o.shared_leaf > 1) return fail(HPS_ERR_INVALID_ARG, "shared_leaf must be -1, 0 or 1");
   if (o.ir_tol <= 0.0) o.ir_tol = 1e-10;
   if (o.ir_max_iter <= 0) o.ir_max_iter = 10;
   return HPS_OK;
@@ -1640,7 +1659,12 @@ int hps_plan_check(const hps_tree* tree, int p, const hps_opts* opts) {
   if (!h) return fail(HPS_ERR_OOM, "host allocation failed");
   std::string err;
   try {
-    err = setup_host(h, tree->t, p, o);
+    bool shared = false;
+    if (o.shared_leaf == 1) {
+      shared = equal_leaf_spans(tree->t);
+      if (!shared) err = "shared_leaf = 1 needs leaves of one size";
+    }
+    if (err.empty()) err = setup_host(h, tree->t, p, o, shared);
     if (err.empty()) {
       HostPlan hp;
       make_plan(h, hp);
@@ -1672,12 +1696,35 @@ int hps_build(const hps_tree* tree, const double* coeffs, int p, const hps_opts*
     h->al.custom = true;
   }
   try {
+    // shared leaf operators: equal leaf sizes (host) and equal interior coefficients
+    // (device check, one synchronisation)
+    bool shared = false;
+    if (o.shared_leaf != 0 && equal_leaf_spans(tree->t)) {
+      int* flag = (int*)h->al.get(sizeof(int), s);
+      int differ = 1;
+      try {
+        CK(cudaMemsetAsync(flag, 0, sizeof(int), s));
+        launch_leaf_uniform_check(coeffs, (int)tree->t.leaves.size(), p, flag, s);
+        CKL();
+        CK(cudaMemcpyAsync(&differ, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+      } catch (...) {
+        h->al.put(flag, s);
+        throw;
+      }
+      h->al.put(flag, s);
+      shared = differ == 0;
+    }
+    if (o.shared_leaf == 1 && !shared) {
+      delete h;
+      return fail(HPS_ERR_INVALID_ARG, "shared_leaf = 1 needs leaves of one size with equal interior coefficients");
+    }
     // host plan: from the tree's cache, or made, checked and cached
     std::shared_ptr<const HostPlan> plan;
     {
       std::lock_guard<std::mutex> lk(tree->cache_mu);
       if (!tree->cache) tree->cache = std::make_shared<PlanCache>();
-      const std::array<int, 5> key = plan_key(p, o);
+      const std::array<int, 6> key = plan_key(p, o, shared);
       for (const PlanCache::Entry& e : tree->cache->entries)
         if (e.key == key) {
           const Alloc al = h->al;
@@ -1688,7 +1735,7 @@ int hps_build(const hps_tree* tree, const double* coeffs, int p, const hps_opts*
           break;
         }
       if (!plan) {
-        std::string err = setup_host(h, tree->t, p, o);
+        std::string err = setup_host(h, tree->t, p, o, shared);
         auto hp = std::make_shared<HostPlan>();
         if (err.empty()) {
           make_plan(h, *hp);

@@ -133,6 +133,8 @@ struct LeafTablesDev {
   const double* DceL;   // 4q x 4q
   const int* ci;        // m
 };
+// *flag = 1 when the interior coefficients of some leaf differ from leaf 0's.
+void launch_leaf_uniform_check(const double* coeffs, int n_leaf, int p, int* flag, cudaStream_t s);
 template <typename T>
 void launch_leaf_assemble(const double* coeffs, long long n_leaf_total, int leaf0, int nleaf,
                           const double* hxy, int p, int q, const LeafTablesDev& tb, T* work,

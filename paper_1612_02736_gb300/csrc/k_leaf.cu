@@ -15,6 +15,8 @@
 //                                + (-c22 sy^2 D2[iy][0] + c2 sy D[iy][0]) Ls[ix][a].
 // The bottom rows are reference-element constants scaled by 2/h of the side's
 // derivative direction.
+#include <algorithm>
+
 #include "hps_internal.h"
 
 namespace hps {
@@ -106,7 +108,29 @@ __global__ void __launch_bounds__(256) leaf_assemble_kernel(
   }
 }
 
+// flag = 1 when some leaf's coefficient at an interior node differs from leaf 0's (the
+// exterior values are never used by the method).
+__global__ void leaf_uniform_kernel(const double* __restrict__ coeffs, long long n_leaf, int p,
+                                    int* __restrict__ flag) {
+  const int pp = p * p;
+  const long long total = 6 * n_leaf * pp;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long k = e / (n_leaf * pp);
+    const int n = (int)(e % pp);
+    const int ix = n % p, iy = n / p;
+    if (ix == 0 || ix == p - 1 || iy == 0 || iy == p - 1) continue;
+    if (coeffs[e] != coeffs[k * n_leaf * pp + n]) *flag = 1;
+  }
+}
+
 }  // namespace
+
+void launch_leaf_uniform_check(const double* coeffs, int n_leaf, int p, int* flag, cudaStream_t s) {
+  const long long total = 6ll * n_leaf * p * p;
+  const int grid = (int)std::min<long long>((total + 255) / 256, 152 * 16);
+  leaf_uniform_kernel<<<grid, 256, 0, s>>>(coeffs, n_leaf, p, flag);
+}
 
 template <typename T>
 void launch_leaf_assemble(const double* coeffs, long long n_leaf_total, int leaf0, int nleaf,

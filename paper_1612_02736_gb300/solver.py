@@ -132,11 +132,14 @@ class Solver:
     Chebyshev node.  precision: 'fp64' or 'mixed' (FP32 sweeps + FP64 iterative refinement).
     autotune: time the candidate tile configurations of each new launch shape once and keep
     the fastest (autotune_cache: a text file that keeps the choices across processes).
+    shared_leaf: "auto" stores one leaf's operators for all leaves when every leaf has the
+    same size and interior coefficients (constant-coefficient problems); True requires it,
+    False never shares.
     """
 
     def __init__(self, tree, coeffs, p, precision="fp64", q=None, ir_tol=None, ir_max_iter=None,
                  fp64_top_levels=None, store_leaf_ops=True, use_graphs=True, autotune=False,
-                 autotune_cache=None, allocator="torch"):
+                 autotune_cache=None, shared_leaf="auto", allocator="torch"):
         lib = N.load()
         if not (coeffs.is_cuda and coeffs.dtype == torch.float64 and coeffs.is_contiguous()):
             raise ValueError("coeffs must be a contiguous CUDA float64 tensor")
@@ -156,6 +159,7 @@ class Solver:
         opts.autotune = 1 if autotune else 0
         self._tune_path = None if autotune_cache is None else str(autotune_cache).encode()
         opts.autotune_cache = self._tune_path
+        opts.shared_leaf = {"auto": -1, False: 0, True: 1}[shared_leaf]
         self.tree, self.p, self.precision = tree, p, precision
         self._alloc = _allocator() if allocator == "torch" else None
         out = C.c_void_p()

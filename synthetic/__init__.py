@@ -152,3 +152,23 @@ def lshape_load_centre(seed_offset=300):
 def point_load(x, y, centre, width=1e-3):
     """g = exp(-|x - centre|^2 / width^2) (a Gaussian point load of the given width)."""
     return np.exp(-((x - centre[0]) ** 2 + (y - centre[1]) ** 2) / width ** 2)
+
+
+def plane_wave(x, y, kappa, theta=0.3):
+    """u = sin(kappa (x cos(theta) + y sin(theta))): solves -Laplace(u) - kappa^2 u = 0."""
+    return np.sin(kappa * (np.cos(theta) * x + np.sin(theta) * y))
+
+
+def helmholtz_scattering(x, y, kappa=40.0):
+    """The variable-coefficient Helmholtz problem of Sec. 7.2 at the given points:
+    -Laplace(u) - kappa^2 (1 - b(x)) u = g with the scattering potential b a sum of two
+    Gaussians (amplitude 1/2, exponent 200, centres (7/20, 6/10) and (6/10, 9/20)) and the
+    Gaussian load g = exp(-300 |x - (1/4, 3/4)|^2).  Returns (coefficients, g); the
+    Dirichlet data are zero (the section does not state them)."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    z = np.zeros_like(x)
+    b = 0.5 * np.exp(-200.0 * ((x - 0.35) ** 2 + (y - 0.6) ** 2)) + \
+        0.5 * np.exp(-200.0 * ((x - 0.6) ** 2 + (y - 0.45) ** 2))
+    g = np.exp(-300.0 * ((x - 0.25) ** 2 + (y - 0.75) ** 2))
+    return (z + 1.0, z, z + 1.0, z, z, -kappa ** 2 * (1.0 - b)), g

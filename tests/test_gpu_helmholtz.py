@@ -1,0 +1,90 @@
+"""Indefinite operators on the GPU (Sec. 7.2, c < 0): the variable-coefficient scattering
+problem against the oracle, an exact plane wave at the full 64 x 64 size, and the
+breakdown report for an exactly singular leaf."""
+import numpy as np
+import pytest
+
+import synthetic as syn
+from oracle import hps, tree as tr
+from tests.gpu_common import to_dev
+from tests.helpers import boundary_points, leaf_points, rel_linf
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1612_02736_gb300 import build
+    build.build()
+
+
+def _scaled_residuals(o, coeffs, p, f, g, u, ug):
+    r_ci, r_jump, r_bdry = hps.residual(o, coeffs, p, f, g, u, ug)
+    scale = np.max(np.abs(u)) * max(np.max(np.abs(c)) for c in coeffs) * (2.0 * o.n_leaves ** 0.5) ** 2
+    return np.max(np.abs(r_ci)) / scale, np.max(np.abs(r_jump)) / scale, np.max(np.abs(r_bdry))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_scattering_kappa40_matches_oracle(precision):
+    # The scattering problem of Sec. 7.2 at 16 x 16 leaves, p = 16.  Both solutions satisfy
+    # the collocation equations to rounding (backward error ~1e-16), but at kappa = 40 the
+    # discrete Helmholtz problem amplifies rounding: two backward-stable FP64 solvers (the
+    # NumPy oracle and the GPU elimination) differ by about 2e-10 relative here (3e-11 at
+    # kappa = 20), so the forward bound is 1e-9 and the residuals carry the FP64 claim.
+    from paper_1612_02736_gb300 import Solver, Tree
+    n, p = 16, 16
+    o = tr.uniform_tree(0, 0, 1, 1, n, n, p - 1)
+    X, Y = leaf_points(o, p)
+    bx, _ = boundary_points(o)
+    c, g = syn.helmholtz_scattering(X, Y, kappa=40.0)
+    coeffs = np.array(c)
+    f = np.zeros_like(bx)
+    uc, ugo = hps.solve(o, hps.build(o, coeffs, p), p, f, g)
+    s = Solver(Tree.uniform(0.0, 0.0, 1.0, 1.0, n, n), to_dev(coeffs), p, precision)
+    u, ug = s.solve(to_dev(f), to_dev(g), return_gauss=True)
+    u, ug = u.cpu().numpy(), ug.cpu().numpy()
+    assert rel_linf(u, uc[..., 0]) < (1e-9 if precision == "fp64" else 1e-8)
+    ro = _scaled_residuals(o, coeffs, p, f, g, uc, ugo)
+    rg = _scaled_residuals(o, coeffs, p, f, g, u[..., None], ug[:, None])
+    assert ro[0] < 1e-13 and ro[1] < 1e-13
+    if precision == "fp64":
+        assert rg[0] < 10 * ro[0] + 1e-16 and rg[1] < 10 * ro[1] + 1e-16
+    assert rg[2] == 0.0
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_plane_wave_full_size(precision):
+    # 64 x 64 leaves, p = 16, kappa = 40 (6.4 wavelengths across): exact solution
+    from paper_1612_02736_gb300 import Solver, Tree
+    n, p, kappa = 64, 16, 40.0
+    t = Tree.uniform(0.0, 0.0, 1.0, 1.0, n, n)
+    xy = t.nodes(p, p - 1, "cheb")
+    bnd = t.nodes(p, p - 1, "boundary")
+    X, Y = xy[:, 0].reshape(n * n, p * p), xy[:, 1].reshape(n * n, p * p)
+    z = np.zeros_like(X)
+    coeffs = np.array([z + 1, z, z + 1, z, z, z - kappa ** 2])
+    s = Solver(t, to_dev(coeffs), p, precision)
+    u = s.solve(to_dev(syn.plane_wave(bnd[:, 0], bnd[:, 1], kappa)), to_dev(z)).cpu().numpy()
+    assert np.max(np.abs(u - syn.plane_wave(X, Y, kappa))) < 1e-9
+
+
+def test_singular_leaf_is_reported_and_library_stays_usable():
+    # all coefficients zero: A_ci,ci = 0, the first pivot of every leaf breaks down
+    import torch
+    from paper_1612_02736_gb300 import Solver, Tree, _native
+    t = Tree.uniform(0.0, 0.0, 1.0, 1.0, 2, 2)
+    zero = torch.zeros((6, 4, 64), dtype=torch.float64, device="cuda")
+    with pytest.raises(_native.HPSError) as ei:
+        Solver(t, zero, 8)
+    assert ei.value.code == 3   # HPS_ERR_SINGULAR
+    assert "box" in str(ei.value)
+    ok = zero.clone()
+    ok[0] = 1.0
+    ok[2] = 1.0
+    s = Solver(t, ok, 8)
+    u = s.solve(torch.ones(s.n_bdry, dtype=torch.float64, device="cuda"),
+                torch.zeros((4, 64), dtype=torch.float64, device="cuda"))
+    assert torch.allclose(u, torch.ones_like(u), atol=1e-12)   # Laplace with u = 1 on the boundary

@@ -133,6 +133,37 @@ def test_plan_non_power_of_two_trees(lib, nx, ny):
     lib.hps_tree_destroy(t)
 
 
+@pytest.mark.parametrize("nx,ny,p,prec", [(1, 1, 8, 0), (2, 2, 16, 1), (64, 64, 16, 0), (5, 3, 10, 0),
+                                         (128, 128, 16, 1)])
+def test_plan_shared_leaf_operators_stay_in_bounds(lib, nx, ny, p, prec):
+    # one leaf's operators and T block shared by every leaf (constant coefficients)
+    from paper_1612_02736_gb300 import _native
+    t = _tree(lib, nx, ny)
+    opts = _native.hps_opts()
+    lib.hps_opts_default(C.byref(opts))
+    opts.precision = prec
+    opts.shared_leaf = 1
+    assert lib.hps_plan_check(t, p, C.byref(opts)) == 0, lib.hps_last_error()
+    lib.hps_tree_destroy(t)
+
+
+def test_plan_shared_leaf_needs_equal_leaves(lib):
+    from paper_1612_02736_gb300 import _native
+    t = _tree(lib, 2, 2)
+    pts = (C.c_double * 2)(0.1, 0.1)
+    r = C.c_void_p()
+    assert lib.hps_tree_refine(t, pts, 1, 1, C.byref(r)) == 0, lib.hps_last_error()
+    opts = _native.hps_opts()
+    lib.hps_opts_default(C.byref(opts))
+    opts.shared_leaf = 1
+    assert lib.hps_plan_check(r, 8, C.byref(opts)) == 1
+    assert "one size" in lib.hps_last_error().decode()
+    opts.shared_leaf = -1
+    assert lib.hps_plan_check(r, 8, C.byref(opts)) == 0, lib.hps_last_error()
+    lib.hps_tree_destroy(r)
+    lib.hps_tree_destroy(t)
+
+
 def test_plan_rejects_bad_options(lib):
     from paper_1612_02736_gb300 import _native
     t = _tree(lib, 2, 2)
