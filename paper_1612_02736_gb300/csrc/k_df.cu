@@ -52,6 +52,19 @@ __device__ __forceinline__ df df_mul(df a, df b) {
   return fast_two_sum(p, e);
 }
 __device__ __forceinline__ df df_fma(df acc, df a, df b) { return df_add(acc, df_mul(a, b)); }
+// Accumulating multiply-add for dot products (15 instead of 27 float operations): the
+// product's hi part joins acc.hi through TwoSum, every low-order term (the product's
+// rounding error, its cross terms and acc.lo) is summed in plain float, then the pair is
+// renormalised.  Its error is about 2^-48 (|acc| + |a b|), the bound of a sum of
+// products in FP64-like arithmetic relative to the magnitudes of the terms.
+__device__ __forceinline__ df df_fma_acc(df acc, df a, df b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  const df s = two_sum(acc.hi, p);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(acc.lo, e)));
+}
 
 constexpr int RC = 4;
 
@@ -69,10 +82,15 @@ __global__ void __launch_bounds__(256) leaf_residual_df_kernel(
   df* uys = uxs + pp * RC;     // pp * RC
   df* ugs = uys + pp * RC;     // nq * RC
   df* cf = ugs + nq * RC;      // 6 * pp: -c11, -2 c12, -c22, c1, c2, c of this leaf
+  df* sDt = cf + 6 * pp;       // D and D2 transposed: lanes that differ in ix read
+  df* sD2t = sDt + pp;         // consecutive words (no bank conflicts)
   const int tid = threadIdx.x, bs = blockDim.x;
   for (int e = tid; e < pp; e += bs) {
     sD[e] = df_from(a.D[e]);
     sD2[e] = df_from(a.D2[e]);
+    const int i = e / p, k = e - (e / p) * p;
+    sDt[k * p + i] = sD[e];
+    sD2t[k * p + i] = sD2[e];
   }
   const long long st = a.n_leaf * pp;
   for (int e = tid; e < 6 * pp; e += bs) {
@@ -105,7 +123,7 @@ __global__ void __launch_bounds__(256) leaf_residual_df_kernel(
       const float2* Lrow = a.Lce_df + (long long)k * nq;
       for (int gq = 0; gq < nq; ++gq) {
         const float2 l = __ldg(Lrow + gq);
-        v = df_fma(v, df{l.x, l.y}, ugs[gq * RC + rr]);
+        v = df_fma_acc(v, df{l.x, l.y}, ugs[gq * RC + rr]);
       }
       const int n = ce[k];
       us[n * RC + rr] = v;
@@ -117,8 +135,8 @@ __global__ void __launch_bounds__(256) leaf_residual_df_kernel(
       const int ix = n % p, iy = n / p;
       df sxv = {0.f, 0.f}, syv = {0.f, 0.f};
       for (int k = 0; k < p; ++k) {
-        sxv = df_fma(sxv, sD[ix * p + k], us[(iy * p + k) * RC + rr]);
-        syv = df_fma(syv, sD[iy * p + k], us[(k * p + ix) * RC + rr]);
+        sxv = df_fma_acc(sxv, sDt[k * p + ix], us[(iy * p + k) * RC + rr]);
+        syv = df_fma_acc(syv, sD[iy * p + k], us[(k * p + ix) * RC + rr]);
       }
       uxs[e] = df_mul(sx, sxv);
       uys[e] = df_mul(sy, syv);
@@ -132,9 +150,9 @@ __global__ void __launch_bounds__(256) leaf_residual_df_kernel(
       if (ix > 0 && ix < p - 1 && iy > 0 && iy < p - 1) {
         df uxx = {0.f, 0.f}, uyy = {0.f, 0.f}, uxy = {0.f, 0.f};
         for (int k = 0; k < p; ++k) {
-          uxx = df_fma(uxx, sD2[ix * p + k], us[(iy * p + k) * RC + rr]);
-          uyy = df_fma(uyy, sD2[iy * p + k], us[(k * p + ix) * RC + rr]);
-          uxy = df_fma(uxy, sD[iy * p + k], uxs[(k * p + ix) * RC + rr]);
+          uxx = df_fma_acc(uxx, sD2t[k * p + ix], us[(iy * p + k) * RC + rr]);
+          uyy = df_fma_acc(uyy, sD2[iy * p + k], us[(k * p + ix) * RC + rr]);
+          uxy = df_fma_acc(uxy, sD[iy * p + k], uxs[(k * p + ix) * RC + rr]);
         }
         uxx = df_mul(uxx, sxx);
         uyy = df_mul(uyy, syy);
@@ -166,7 +184,7 @@ __global__ void __launch_bounds__(256) leaf_residual_df_kernel(
           default: d = uxs[(t * p + 0) * RC + rr]; break;
         }
         const float2 l = __ldg(a.Lloc_df + k * p + t);
-        v = df_fma(v, df{l.x, l.y}, d);
+        v = df_fma_acc(v, df{l.x, l.y}, d);
       }
       vflux[((long long)lf * nq + gq) * nrhs + r0 + rr] = df_to(v);
     }
@@ -187,10 +205,15 @@ __global__ void __launch_bounds__(256) coeff_grad_df_kernel(ResidualArgs a, cons
   df* us = sD2 + pp;    // pp
   df* uxs = us + pp;    // pp
   df* acc = uxs + pp;   // 6 * pp
+  df* sDt = acc + 6 * pp;  // transposed D, D2 (conflict-free reads across ix)
+  df* sD2t = sDt + pp;
   const int tid = threadIdx.x, bs = blockDim.x;
   for (int e = tid; e < pp; e += bs) {
     sD[e] = df_from(a.D[e]);
     sD2[e] = df_from(a.D2[e]);
+    const int i = e / p, k = e - (e / p) * p;
+    sDt[k * p + i] = sD[e];
+    sD2t[k * p + i] = sD2[e];
   }
   for (int e = tid; e < 6 * pp; e += bs) acc[e] = {0.f, 0.f};
   const df sx = df_from(2.0 / a.hxy[2 * lf]), sy = df_from(2.0 / a.hxy[2 * lf + 1]);
@@ -203,7 +226,7 @@ __global__ void __launch_bounds__(256) coeff_grad_df_kernel(ResidualArgs a, cons
     for (int n = tid; n < pp; n += bs) {
       const int ix = n % p, iy = n / p;
       df v = {0.f, 0.f};
-      for (int k = 0; k < p; ++k) v = df_fma(v, sD[ix * p + k], us[iy * p + k]);
+      for (int k = 0; k < p; ++k) v = df_fma_acc(v, sDt[k * p + ix], us[iy * p + k]);
       uxs[n] = df_mul(sx, v);
     }
     __syncthreads();
@@ -212,18 +235,18 @@ __global__ void __launch_bounds__(256) coeff_grad_df_kernel(ResidualArgs a, cons
       if (!(ix > 0 && ix < p - 1 && iy > 0 && iy < p - 1)) continue;
       df uy = {0.f, 0.f}, uxx = {0.f, 0.f}, uyy = {0.f, 0.f}, uxy = {0.f, 0.f};
       for (int k = 0; k < p; ++k) {
-        uy = df_fma(uy, sD[iy * p + k], us[k * p + ix]);
-        uxx = df_fma(uxx, sD2[ix * p + k], us[iy * p + k]);
-        uyy = df_fma(uyy, sD2[iy * p + k], us[k * p + ix]);
-        uxy = df_fma(uxy, sD[iy * p + k], uxs[k * p + ix]);
+        uy = df_fma_acc(uy, sD[iy * p + k], us[k * p + ix]);
+        uxx = df_fma_acc(uxx, sD2t[k * p + ix], us[iy * p + k]);
+        uyy = df_fma_acc(uyy, sD2[iy * p + k], us[k * p + ix]);
+        uxy = df_fma_acc(uxy, sD[iy * p + k], uxs[k * p + ix]);
       }
       const df lam = df_from(gbar[lbase + (long long)n * nrhs + r]);
-      acc[0 * pp + n] = df_fma(acc[0 * pp + n], lam, df_mul(sxx, uxx));
-      acc[1 * pp + n] = df_fma(acc[1 * pp + n], lam, df_mul(two_sy, uxy));
-      acc[2 * pp + n] = df_fma(acc[2 * pp + n], lam, df_mul(syy, uyy));
-      acc[3 * pp + n] = df_fma(acc[3 * pp + n], df_neg(lam), uxs[n]);
-      acc[4 * pp + n] = df_fma(acc[4 * pp + n], df_neg(lam), df_mul(sy, uy));
-      acc[5 * pp + n] = df_fma(acc[5 * pp + n], df_neg(lam), us[n]);
+      acc[0 * pp + n] = df_fma_acc(acc[0 * pp + n], lam, df_mul(sxx, uxx));
+      acc[1 * pp + n] = df_fma_acc(acc[1 * pp + n], lam, df_mul(two_sy, uxy));
+      acc[2 * pp + n] = df_fma_acc(acc[2 * pp + n], lam, df_mul(syy, uyy));
+      acc[3 * pp + n] = df_fma_acc(acc[3 * pp + n], df_neg(lam), uxs[n]);
+      acc[4 * pp + n] = df_fma_acc(acc[4 * pp + n], df_neg(lam), df_mul(sy, uy));
+      acc[5 * pp + n] = df_fma_acc(acc[5 * pp + n], df_neg(lam), us[n]);
     }
   }
   __syncthreads();
@@ -238,7 +261,7 @@ __global__ void __launch_bounds__(256) coeff_grad_df_kernel(ResidualArgs a, cons
 void launch_coeff_grad(const ResidualArgs& a, const double* uc, const double* gbar, double* grad, int nrhs,
                        cudaStream_t s) {
   const int pp = a.p * a.p;
-  const size_t smem = (size_t)(10 * pp) * sizeof(df);
+  const size_t smem = (size_t)(12 * pp) * sizeof(df);
   static size_t configured = 0;
   if (smem > 48 * 1024 && smem > configured) {
     cudaFuncSetAttribute(coeff_grad_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -251,7 +274,7 @@ void launch_leaf_residual_df(const ResidualArgs& a, const int* leaf_edges, const
                              const double* ug, const double* g, double* uc, double* r_out, double* vflux, int nrhs,
                              cudaStream_t s) {
   const int pp = a.p * a.p;
-  const size_t smem = (size_t)(8 * pp + 3 * pp * RC + 4 * a.q * RC) * sizeof(df);
+  const size_t smem = (size_t)(10 * pp + 3 * pp * RC + 4 * a.q * RC) * sizeof(df);
   static size_t configured = 0;
   if (smem > 48 * 1024 && smem > configured) {
     cudaFuncSetAttribute(leaf_residual_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
