@@ -12,13 +12,18 @@ Equations, in this order:
        u_j - (P_up u_coarse)_j = 0;
      - a coarse node facing a refined parent: the coarse leaf's flux minus the P_down
        projection of the fine leaves' fluxes (W/S side minus E/N side) = rho_j,
-  3. every boundary Gaussian node: u_j = f_j   (Eq. basic, Algorithm 2 root step),
+  3. every boundary Gaussian node: u_j = f_j   (Eq. basic, Algorithm 2 root step); with
+     other boundary kinds (Sec. 7.6, ``oracle.boundary``): for each periodic west node j
+     and its east partner e, u_j - u_e = 0 and (D_ge,c u_c)_east leaf(e) -
+     (D_ge,c u_c)_west leaf(j) = 0 (flux continuity across the seam); on a Neumann side
+     (D_ge,c u_c)(j) = f_j,
 with u_c = [L_ce,ge u_ge on I_ce ; u_ci on I_ci] on each leaf.
 
 This module is oracle code (test infrastructure); see ``oracle/__init__.py``.
 """
 import numpy as np
 
+from . import boundary as bd
 from . import spectral as sp
 from .leaf import leaf_A
 
@@ -26,7 +31,35 @@ from .leaf import leaf_A
 SIDES_WS = {0: False, 1: True, 2: True, 3: False}
 
 
-def assemble(tree, coeffs, p):
+def _boundary_rows(tree, bc):
+    """Boundary equations in order: ("dir", j), ("neu", j) or ("seam", j, e)."""
+    we, sn = (bd.DIRICHLET, bd.DIRICHLET) if bc is None else bc
+    partner = {}
+    if we == bd.PERIODIC:
+        W, E = bd.periodic_pairs(tree)
+        partner = {int(w): int(e) for w, e in zip(W, E)}
+        east = set(int(e) for e in E)
+    else:
+        east = set()
+    neu = set()
+    if sn == bd.NEUMANN:
+        _, _, S, N = bd.classify(tree)
+        neu = set(int(g) for g in S) | set(int(g) for g in N)
+    rows = []
+    for j in tree.boundary:
+        j = int(j)
+        if j in partner:
+            rows.append(("seam", j, partner[j]))
+        elif j in east:
+            continue
+        elif j in neu:
+            rows.append(("neu", j))
+        else:
+            rows.append(("dir", j))
+    return rows
+
+
+def assemble(tree, coeffs, p, bc=None):
     """Return (K, meta): the dense system matrix and the index bookkeeping."""
     q = tree.q
     ce, ci, _ = sp.leaf_index_sets(p)
@@ -79,14 +112,27 @@ def assemble(tree, coeffs, p):
         coarse_is_ws = SIDES_WS[pc // q]
         K[row] = (flux[lc][pc] - proj) if coarse_is_ws else (proj - flux[lc][pc])
         row += 1
-    for j in tree.boundary:
-        K[row, j] = 1.0
-        row += 1
+    for r in _boundary_rows(tree, bc):
+        if r[0] == "dir":
+            K[row, r[1]] = 1.0
+            row += 1
+        elif r[0] == "neu":
+            (lb, pb), = own[r[1]]
+            K[row] = flux[lb][pb]
+            row += 1
+        else:
+            j, e = r[1], r[2]
+            K[row, j] = 1.0
+            K[row, e] = -1.0
+            (lw, pw), = own[j]
+            (le, pe), = own[e]
+            K[row + 1] = flux[le][pe] - flux[lw][pw]
+            row += 2
     assert row == n, "every Gaussian node needs exactly one interface or boundary equation"
     return K, {"E": E, "m": m, "ci": ci, "ng": ng}
 
 
-def rhs(tree, p, f, g, rho=None):
+def rhs(tree, p, f, g, rho=None, bc=None):
     """Right-hand side of the assembled system, same equation order."""
     _, ci, _ = sp.leaf_index_sets(p)
     g = np.asarray(g, dtype=np.float64)
@@ -107,14 +153,21 @@ def rhs(tree, p, f, g, rho=None):
         parts.append(np.zeros((len(tree.coarse_of), nrhs)))
     else:
         parts.append(rho[sorted(tree.coarse_of)])
-    parts.append(f)
+    brow = {int(j): k for k, j in enumerate(tree.boundary)}
+    fb = []
+    for r in _boundary_rows(tree, bc):
+        if r[0] == "seam":
+            fb += [np.zeros(nrhs), np.zeros(nrhs)]
+        else:
+            fb.append(f[brow[r[1]]])
+    parts.append(np.array(fb).reshape(-1, nrhs))
     return np.vstack(parts)
 
 
-def solve(tree, coeffs, p, f, g, rho=None):
+def solve(tree, coeffs, p, f, g, rho=None, bc=None):
     """Dense solve; returns (u_c (n_leaf, p^2, nrhs), u_g (n_gauss, nrhs))."""
-    K, meta = assemble(tree, coeffs, p)
-    z = np.linalg.solve(K, rhs(tree, p, f, g, rho))
+    K, meta = assemble(tree, coeffs, p, bc)
+    z = np.linalg.solve(K, rhs(tree, p, f, g, rho, bc))
     u_c = np.array([El @ z for El in meta["E"]])
     return u_c, z[:meta["ng"]]
 

@@ -15,6 +15,7 @@ This module is oracle code (test infrastructure); see ``oracle/__init__.py``.
 """
 import numpy as np
 
+from . import boundary as bd
 from . import spectral as sp
 from .leaf import leaf_ops, leaf_A
 
@@ -64,13 +65,16 @@ def _as2d(a, lead):
     return a.reshape(a.shape[:lead] + (-1,)) if a.ndim == lead else a
 
 
-def solve(tree, ops, p, f, g, rho=None):
+def solve(tree, ops, p, f, g, rho=None, bc=None):
     """Algorithm 2 (upward pass for particular solutions, downward pass for potentials),
     with per-box flux vectors h.  A non-zero ``rho`` enters the merge of the box whose J3
     holds the node: Eq. swiss with the continuity condition v3(alpha) - v3(beta) = rho3
     gives u3 = X (T32b u2 - T31a u1 + h3b - h3a + rho3).  Refined parents (Sec. 6.4): the
     upward flux is projected, h_new = P_down h_old, and on the way down the fine nodes of a
-    coarsened side get u_fine = P_up u_coarse before the parent's S is applied."""
+    coarsened side get u_fine = P_up u_coarse before the parent's S is applied.
+    bc = (west/east, south/north) boundary kinds (``oracle.boundary``): with periodic or
+    Neumann sides the root's boundary values come from the root DtN relation (Sec. 7.6),
+    and f holds Dirichlet values or flux data per boundary node."""
     f = _as2d(f, 1)
     g = _as2d(g, 2)
     nrhs = g.shape[-1]
@@ -93,7 +97,11 @@ def solve(tree, ops, p, f, g, rho=None):
         if b.Pup is not None:
             h[bid] = b.Pdown @ h[bid]
     u_g = np.zeros((tree.n_gauss, nrhs))
-    u_g[tree.boundary] = f
+    if bc is None or tuple(bc) == (bd.DIRICHLET, bd.DIRICHLET):
+        u_g[tree.boundary] = f
+    else:
+        root = tree.boxes[0]
+        u_g[root.ge] = bd.root_values(tree, ops[0]["T"], h[0], f, bc)
     u_c = np.zeros((tree.n_leaves, p * p, nrhs))
     for bid in range(len(tree.boxes)):
         b = tree.boxes[bid]
