@@ -58,6 +58,13 @@ typedef enum {
   HPS_NODES_GAUSS_ALL = 2       /* every Gaussian node, by global id                     */
 } hps_node_set;
 
+/* Boundary condition kinds of a rectangular domain's sides (hps_opts.bc_we, bc_sn). */
+typedef enum {
+  HPS_BC_DIRICHLET = 0, /* u given (both pairs of sides)                                  */
+  HPS_BC_PERIODIC = 1,  /* west/east only: u and its x-flux equal at facing nodes        */
+  HPS_BC_NEUMANN = 2    /* south/north only: the y-flux du/dy given                       */
+} hps_bc;
+
 typedef struct hps_tree hps_tree;     /* opaque, host memory                              */
 typedef struct hps_handle hps_handle; /* opaque, owns the device operator store          */
 
@@ -100,6 +107,13 @@ typedef struct {
                         * on the device at build time, one synchronisation); 0 never; 1
                         * requires it (INVALID_ARG when the leaves differ).  Shared, one
                         * leaf is eliminated and stored, and store_leaf_ops is ignored     */
+  int bc_we;           /* west/east sides: HPS_BC_DIRICHLET (default) or HPS_BC_PERIODIC   */
+  int bc_sn;           /* south/north sides: HPS_BC_DIRICHLET (default) or HPS_BC_NEUMANN.
+                        * Other than Dirichlet (the channel problem of Sec. 7.6): the
+                        * domain must be a rectangle (hps_tree_uniform, refined or not, with
+                        * matching west/east nodes when periodic); the root keeps its DtN
+                        * map and the solve obtains the boundary values from it; HPS_FP64
+                        * handles only; hps_adjoint and hps_solve_noalloc return STATE     */
 } hps_opts;
 
 /* Fills *opts with the defaults above (FP64, q = p - 1, store leaf operators, graphs on,
@@ -158,7 +172,9 @@ int hps_build(const hps_tree* tree, const double* coeffs_dev, int p, const hps_o
               const hps_allocator* alloc, void* stream, hps_handle** out);
 
 /* Solve stage (Algorithm 2) for nrhs right-hand sides at once.
- *   f_dev : [n_boundary][nrhs]        Dirichlet data at the boundary Gaussian nodes
+ *   f_dev : [n_boundary][nrhs]        Dirichlet data at the boundary Gaussian nodes; with
+ *                                     HPS_BC_NEUMANN, du/dy at the south and north nodes;
+ *                                     ignored at periodic west/east nodes
  *   g_dev : [n_leaf][p*p][nrhs]       body load at the leaf Chebyshev nodes (interior
  *                                     values used)
  *   u_dev : [n_leaf][p*p][nrhs]       output: the solution at every leaf Chebyshev node
@@ -169,6 +185,19 @@ int hps_build(const hps_tree* tree, const double* coeffs_dev, int p, const hps_o
  * return NO_CONVERGENCE after ir_max_iter steps. */
 int hps_solve(hps_handle* h, const double* f_dev, const double* g_dev, int nrhs, double* u_dev,
               void* stream);
+
+/* Operator application on the handle's leaves: out = alpha u + beta A u at every leaf's
+ * interior Chebyshev nodes and 0 at its exterior nodes, with A the collocation of Eq.
+ * basic (Sec. 3.2: tensor-product spectral derivatives) for the coefficient fields
+ * coeffs_dev ([6][n_leaf][p*p], as hps_build takes them; they need not be the handle's).
+ * u_dev, out_dev: [n_leaf][p*p][nrhs] device FP64 (u's exterior values are used as given,
+ * e.g. a solution from hps_solve).  This is the explicit half of an implicit time step:
+ * Crank-Nicolson (Sec. 7.6) solves (I/k - A/2) u_{n+1} = (I/k + A/2) u_n, whose right-hand
+ * side is 2/k u_n - (I/k - A/2) u_n (alpha = 2/k, beta = -1 with the solved operator's
+ * coefficients).  Computed in double-float arithmetic (about 48 significant bits),
+ * asynchronous on stream. */
+int hps_apply(hps_handle* h, const double* coeffs_dev, const double* u_dev, int nrhs, double alpha, double beta,
+              double* out_dev, void* stream);
 
 /* hps_solve with extras: rho_dev (may be NULL) is a right-hand side for the flux
  * continuity equations, [n_gauss][nrhs] by global id (entries off interior nodes are

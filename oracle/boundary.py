@@ -18,6 +18,14 @@ Flux data on a set N of the remaining nodes (the rest, D, keep Dirichlet data) g
     u_N = T'_NN^-1 (f_N - h'_N - T'_ND u_D).
 Then u_s = X_s (R_s u_x + d_s) and the downward pass of Algorithm 2 runs unchanged.
 
+When no side carries Dirichlet data the flux system T'_NN can be singular: the Gaussian-
+node unknowns admit values that the corner-averaged interpolation L_ce,ge (Sec. 3.3) maps
+to zero on every leaf (on a side, the polynomial of degree q - 1 that vanishes at the side's
+p - 2 interior Chebyshev points, with the corner averages cancelling).  No Chebyshev value,
+residual or flux sees such a direction, so T' maps it to zero and any solution of the flux
+system gives the same u_c.  The oracle takes the least-squares solution with singular
+values below 1e-9 of the largest treated as zero.
+
 This module is oracle code (test infrastructure); see ``oracle/__init__.py``.
 """
 import numpy as np
@@ -89,7 +97,7 @@ def root_values(tree, T, h, f, bc):
     if kN:
         fN = np.array([f[brow[xs[k]]] for k in kN])
         rhs = fN - hp[kN] - Tp[np.ix_(kN, kD)] @ ux[kD]
-        ux[kN] = np.linalg.solve(Tp[np.ix_(kN, kN)], rhs)
+        ux[kN] = np.linalg.lstsq(Tp[np.ix_(kN, kN)], rhs, rcond=1e-9)[0]
     for k, g in enumerate(xs):
         u[pos[g]] = ux[k]
     if we == PERIODIC:

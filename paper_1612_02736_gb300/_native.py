@@ -15,6 +15,9 @@ HPS_MIXED = 1
 HPS_NODES_CHEB_LEAF = 0
 HPS_NODES_GAUSS_BOUNDARY = 1
 HPS_NODES_GAUSS_ALL = 2
+HPS_BC_DIRICHLET = 0
+HPS_BC_PERIODIC = 1
+HPS_BC_NEUMANN = 2
 
 STATUS_NAMES = {
     0: "OK", 1: "INVALID_ARG", 2: "NOT_ELLIPTIC", 3: "SINGULAR", 4: "OOM", 5: "CUDA",
@@ -34,7 +37,7 @@ class hps_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("q", C.c_int), ("store_leaf_ops", C.c_int),
                 ("ir_tol", C.c_double), ("ir_max_iter", C.c_int), ("fp64_top_levels", C.c_int),
                 ("use_graphs", C.c_int), ("autotune", C.c_int), ("autotune_cache", C.c_char_p),
-                ("shared_leaf", C.c_int)]
+                ("shared_leaf", C.c_int), ("bc_we", C.c_int), ("bc_sn", C.c_int)]
 
 
 P = C.c_void_p
@@ -47,6 +50,7 @@ SIGNATURES = {
     "hps_tree_info": (C.c_int, [P, C.c_int] + [C.POINTER(C.c_int)] * 5),
     "hps_nodes": (C.c_int, [P, C.c_int, C.c_int, C.c_int, P, C.POINTER(C.c_int64)]),
     "hps_plan_check": (C.c_int, [P, C.c_int, C.POINTER(hps_opts)]),
+    "hps_apply": (C.c_int, [P, P, P, C.c_int, C.c_double, C.c_double, P, P]),
     "hps_build": (C.c_int, [P, P, C.c_int, C.POINTER(hps_opts), C.POINTER(hps_allocator), P, C.POINTER(P)]),
     "hps_solve": (C.c_int, [P, P, P, C.c_int, P, P]),
     "hps_solve_noalloc": (C.c_int, [P, P, P, C.c_int, P, P]),

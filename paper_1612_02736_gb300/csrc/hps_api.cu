@@ -10,6 +10,7 @@
 #include <memory>
 #include <mutex>
 #include <new>
+#include <set>
 #include <string>
 #include <type_traits>
 #include <unordered_map>
@@ -222,6 +223,30 @@ struct Workspace {
   double* LB = nullptr;
   double* UB = nullptr;
   double* ubar = nullptr;
+  // root conditions: seam data d, seam particular values w, remaining-node flux h', and
+  // the flux data of Neumann nodes, row blocks of one buffer
+  double* bcw = nullptr;
+};
+
+// Root conditions other than Dirichlet data: periodic west/east sides and flux data on the
+// south/north sides (the channel problem of Sec. 7.6).  With the root DtN relation
+// v = T u + h, periodic sides glue the root to itself like a merge of Sec. 4 (seam nodes
+// W = E; X_s, S_s, C_s X_s and the DtN map T' of the remaining nodes x), and Neumann
+// nodes N of x are solved from T'_NN u_N = f_N - h'_N - T'_ND u_D.
+struct BcPlan {
+  bool on = false, periodic = false, neumann = false;
+  int root = -1;
+  std::vector<int> ext;    // root exterior node ids: the order of its T and h
+  std::vector<int> W, E;   // facing west/east node ids, by height (periodic)
+  std::vector<int> X;      // ext without W and E (all of ext when not periodic)
+  std::vector<int> N, D;   // X split: flux nodes (Neumann) and value nodes, in X order
+  int Ks = 0, nx = 0, Kn = 0, nd = 0;
+  long long xs_off = -1, ss_off = -1, cxs_off = -1, bn_off = -1;  // operator pool
+  long long tp_off = -1;   // T' (nx x nx) in the build's T store
+  int rows = 0;            // bcw rows: d [0, Ks), w [Ks, 2Ks), h' [2Ks, 2Ks+nx), r [.., +Kn)
+  int seam_rt = -1, seam_ct = -1, neu_rt = -1, neu_ct = -1;  // assembly tables (in idx)
+  int c_d = -1, c_hx = -1, c_fD = -1, c_r = -1, c_E = -1;   // row-combine tables (in idx)
+  ItemSet p_ws, p_hx, p_uN, p_uW;                            // products (device)
 };
 
 }  // namespace
@@ -255,6 +280,7 @@ struct hps_handle {
   long long tstore_elems = 0;     // size of the build's T store
   std::string tune_path;          // autotuner cache file ("" = process memory only)
   bool shared = false;            // one leaf's operators serve every leaf (equal leaves)
+  BcPlan bc;                      // periodic / Neumann root conditions
   std::vector<long long> ttmp;    // coarsened boxes: T before coarsening (T store)
   std::vector<long long> puo, pdo, pco;  // coarsened boxes: P_up, P_down, P_up(fine, coarse)
   std::vector<int> k3, k12, k12o; // |J3|, |I_ge| seen by the parent, |J1 + J2|
@@ -398,8 +424,71 @@ struct HostPlan {
   std::vector<LevelHost> lv;
   std::vector<GemmItem> lup, ldown, llce, aF, aS, aL, aH;
   std::vector<int> lred, ftab, pairs;
+  std::vector<GemmItem> bc_ws, bc_hx, bc_uN, bc_uW;
   long long tsz = 0;
 };
+
+// Tables and product items of the root conditions (see BcPlan).
+template <typename Push>
+void make_bc_plan(hps_handle* h, HostPlan& hp, Push push) {
+  BcPlan& bc = h->bc;
+  const int Ks = bc.Ks, nx = bc.nx, Kn = bc.Kn, nd = bc.nd;
+  const int d0 = 0, w0 = Ks, x0 = 2 * Ks, r0 = 2 * Ks + nx;
+  std::unordered_map<int, int> pe, px, brow;
+  for (size_t k = 0; k < bc.ext.size(); ++k) pe[bc.ext[k]] = (int)k;
+  for (size_t k = 0; k < bc.X.size(); ++k) px[bc.X[k]] = (int)k;
+  for (size_t k = 0; k < h->ns.boundary.size(); ++k) brow[h->ns.boundary[k]] = (int)k;
+  const int hb = h->hrow_old(bc.root);
+  std::vector<int> rt, ct;
+  if (bc.periodic) {
+    // M_s = [[Z_s, R_s], [-C_s, T_xx]] from T_root: rows (E - W | x), columns (E + W | x),
+    // off-diagonal blocks negated
+    for (int k = 0; k < Ks; ++k) rt.insert(rt.end(), {pe.at(bc.E[k]), 1, pe.at(bc.W[k]), -1});
+    for (int g : bc.X) rt.insert(rt.end(), {pe.at(g), 1, -1, 0});
+    for (int k = 0; k < Ks; ++k) ct.insert(ct.end(), {pe.at(bc.E[k]), 1, pe.at(bc.W[k]), 1});
+    for (int g : bc.X) ct.insert(ct.end(), {pe.at(g), 1, -1, 0});
+    bc.seam_rt = push(rt);
+    bc.seam_ct = push(ct);
+  }
+  if (Kn > 0) {
+    // [T'_NN | T'_ND] from T' (periodic: positions in X) or T_root (positions in ext)
+    auto at = [&](int g) { return bc.periodic ? px.at(g) : pe.at(g); };
+    rt.clear();
+    ct.clear();
+    for (int g : bc.N) rt.insert(rt.end(), {at(g), 1, -1, 0});
+    for (int g : bc.N) ct.insert(ct.end(), {at(g), 1, -1, 0});
+    for (int g : bc.D) ct.insert(ct.end(), {at(g), 1, -1, 0});
+    bc.neu_rt = push(rt);
+    bc.neu_ct = push(ct);
+  }
+  // row combinations dst = a (+ sign b), in vector rows
+  std::vector<int> c;
+  if (bc.periodic) {
+    for (int k = 0; k < Ks; ++k) c.insert(c.end(), {d0 + k, hb + pe.at(bc.W[k]), hb + pe.at(bc.E[k]), -1});
+    bc.c_d = push(c);
+    c.clear();
+    for (int k = 0; k < Ks; ++k) c.insert(c.end(), {bc.E[k], bc.W[k], -1, 0});
+    bc.c_E = push(c);
+    c.clear();
+  }
+  for (int i = 0; i < nx; ++i) c.insert(c.end(), {x0 + i, hb + pe.at(bc.X[i]), -1, 0});
+  bc.c_hx = push(c);
+  c.clear();
+  for (int g : bc.D) c.insert(c.end(), {g, brow.at(g), -1, 0});
+  bc.c_fD = push(c);
+  c.clear();
+  for (int i = 0; i < Kn; ++i) c.insert(c.end(), {r0 + i, brow.at(bc.N[i]), x0 + px.at(bc.N[i]), -1});
+  bc.c_r = push(c);
+  // products
+  if (bc.periodic) {
+    add_product(hp.bc_ws, bc.xs_off, Ks, Ks, Ks, Ks, d0, -1, 0, -1, w0, -1, -1, false);          // w_s = X_s d_s
+    add_product(hp.bc_hx, bc.cxs_off, Ks, nx, Ks, Ks, d0, -1, 0, -1, x0, -1, -1, false);         // h' += C_s X_s d_s
+    add_product(hp.bc_uW, bc.ss_off, nx, Ks, nx, nx, 0, push(bc.X), 0, -1, 0, push(bc.W), w0, false);  // u_W
+  }
+  if (Kn > 0)  // u_N = X_n r_N - X_n T'_ND u_D
+    add_product(hp.bc_uN, bc.bn_off, Kn + nd, Kn, Kn + nd, Kn, r0, -1, 0, nd > 0 ? push(bc.D) : -1, 0, push(bc.N), -1,
+                false);
+}
 
 void make_plan(hps_handle* h, HostPlan& hp) {
   const Tree& t = h->tree;
@@ -466,7 +555,7 @@ void make_plan(hps_handle* h, HostPlan& hp) {
   for (int b = 0; b < nb; ++b) {
     if (t.boxes[b].leaf >= 0) continue;
     // [X; C X] (the root keeps X only: nothing above it applies C X)
-    const int R = t.boxes[b].parent < 0 ? h->k3[b] : h->k3[b] + h->k12o[b];
+    const int R = (t.boxes[b].parent < 0 && !h->bc.on) ? h->k3[b] : h->k3[b] + h->k12o[b];
     h->mo[b] = off;
     off += (long long)R * h->k3[b];
     h->so[b] = off;
@@ -478,6 +567,21 @@ void make_plan(hps_handle* h, HostPlan& hp) {
       off += (long long)h->k12[b] * h->k12o[b];
       h->pco[b] = off;
       off += (long long)ns.co[b].fine.size() * ns.co[b].coarse.size();
+    }
+  }
+  if (h->bc.on) {  // root-condition operators: X_s, S_s, C_s X_s; [X_n | -X_n T'_ND]
+    BcPlan& bc = h->bc;
+    if (bc.periodic) {
+      bc.xs_off = off;
+      off += (long long)bc.Ks * bc.Ks;
+      bc.ss_off = off;
+      off += (long long)bc.Ks * bc.nx;
+      bc.cxs_off = off;
+      off += (long long)bc.nx * bc.Ks;
+    }
+    if (bc.Kn > 0) {
+      bc.bn_off = off;
+      off += (long long)bc.Kn * (bc.Kn + bc.nd);
     }
   }
   h->ops_elems = off;
@@ -529,13 +633,18 @@ void make_plan(hps_handle* h, HostPlan& hp) {
   }
   h->ttmp.assign(nb, -1);
   for (int b = 0; b < nb; ++b) {
-    if (t.boxes[b].leaf >= 0 || t.boxes[b].parent < 0) continue;  // no DtN map is kept for the root
+    // no DtN map is kept for the root, unless periodic / Neumann root conditions need it
+    if (t.boxes[b].leaf >= 0 || (t.boxes[b].parent < 0 && !h->bc.on)) continue;
     toff[b] = tsz;
     tsz += (long long)h->k12[b] * h->k12[b];
     if (ns.co[b].active) {
       h->ttmp[b] = tsz;
       tsz += (long long)h->k12o[b] * h->k12o[b];
     }
+  }
+  if (h->bc.periodic) {  // T' of the nodes left after the periodic seam
+    h->bc.tp_off = tsz;
+    tsz += (long long)h->bc.nx * h->bc.nx;
   }
   for (int L = 0; L < H; ++L) {
     Level& lv = h->levels[L];
@@ -551,7 +660,7 @@ void make_plan(hps_handle* h, HostPlan& hp) {
       const int k3 = h->k3[b], k12 = h->k12o[b], R = k3 + k12, n1 = ns.n1[b], n2 = k12 - n1;
       // The root's solve needs X and S only (u_ge = f there): its elimination forms and
       // eliminates the top rows [Z | R] and never computes C X or T_tau.
-      const bool root = bx.parent < 0;
+      const bool root = bx.parent < 0 && !h->bc.on;
       const int rows = root ? k3 : R;
       lv.maxR = std::max(lv.maxR, R);
       lv.maxK = std::max(lv.maxK, k3);
@@ -727,6 +836,7 @@ void make_plan(hps_handle* h, HostPlan& hp) {
     pairs.push_back(o2 % 4);
   }
   h->npairs = (int)pairs.size() / 5;
+  if (h->bc.on) make_bc_plan(h, hp, push);
 }
 
 Prod upload_prod(hps_handle* h, cudaStream_t s, const ProdHost& ph) {
@@ -802,6 +912,10 @@ void upload_plan(hps_handle* h, const HostPlan& hp, cudaStream_t s) {
   h->n_leaf_reduce = (int)hp.lred.size() / 3;
   h->fbar_tab = upload(h->al, s, hp.ftab, h->owned);
   h->d_pairs = upload(h->al, s, hp.pairs, h->owned);
+  h->bc.p_ws = upload_items(h, s, hp.bc_ws);
+  h->bc.p_hx = upload_items(h, s, hp.bc_hx);
+  h->bc.p_uN = upload_items(h, s, hp.bc_uN);
+  h->bc.p_uW = upload_items(h, s, hp.bc_uW);
 }
 
 // Every device access the kernels make is described by the plan; check each descriptor
@@ -869,8 +983,70 @@ void check_tab(PlanCheck& pc, const std::vector<int>& tab, long long drows, long
   }
 }
 
+// Row-combine table of the root conditions: n entries (dst, a, b, sign).
+void check_comb(PlanCheck& pc, const std::vector<int>& idx, int off, int n, long long drows, long long arows,
+                long long brows, const char* what) {
+  if (n == 0) return;
+  if (off < 0 || (size_t)off + 4 * (size_t)n > idx.size()) {
+    pc.fail(std::string(what) + ": table out of range");
+    return;
+  }
+  for (int k = 0; k < n; ++k) {
+    const int* e = &idx[off + 4 * k];
+    if (e[0] < 0 || e[0] >= drows || e[1] < 0 || e[1] >= arows || e[2] >= brows || e[2] < -1)
+      pc.fail(std::string(what) + ": row out of range");
+  }
+}
+
+void check_bc(PlanCheck& pc, const hps_handle* h, const HostPlan& hp) {
+  const BcPlan& bc = h->bc;
+  const std::vector<int>& idx = hp.idx;
+  const long long G = h->ns.n_gauss, NB = h->n_bdry, BR = bc.rows, V = h->v_rows;
+  const long long ext = (long long)bc.ext.size();
+  if (bc.Ks + bc.Ks + bc.nx != ext && bc.periodic) pc.fail("root conditions: seam split");
+  if (!bc.periodic && bc.nx != ext) pc.fail("root conditions: node split");
+  if (bc.Kn + bc.nd != bc.nx) pc.fail("root conditions: flux split");
+  const long long hb = h->hrow_old(bc.root);
+  if (hb < 0 || hb + ext > V) pc.fail("root conditions: root flux rows");
+  if (bc.periodic) {
+    check_comb(pc, idx, bc.c_d, bc.Ks, BR, V, V, "seam data");
+    check_comb(pc, idx, bc.c_E, bc.Ks, G, G, 1, "seam copy");
+    check_items(pc, idx, hp.bc_ws, false, h->ops_elems, BR, 0, BR, 0, "seam w");
+    check_items(pc, idx, hp.bc_hx, false, h->ops_elems, BR, 0, BR, 0, "seam flux");
+    check_items(pc, idx, hp.bc_uW, false, h->ops_elems, G, 0, G, BR, "seam values");
+    if (bc.tp_off < 0 || bc.tp_off + (long long)bc.nx * bc.nx > hp.tsz) pc.fail("root conditions: T' out of range");
+  }
+  check_comb(pc, idx, bc.c_hx, bc.nx, BR, V, 1, "root flux gather");
+  check_comb(pc, idx, bc.c_fD, bc.nd, G, NB, 1, "value data");
+  check_comb(pc, idx, bc.c_r, bc.Kn, BR, NB, BR, "flux data");
+  if (bc.Kn > 0) check_items(pc, idx, hp.bc_uN, false, h->ops_elems, BR, G, G, 0, "flux values");
+  // assembly tables: (index, sign) pairs inside the source DtN map
+  auto check_asm = [&](int off, int n, long long ld, const char* what) {
+    if (off < 0 || (size_t)off + 4 * (size_t)n > idx.size()) {
+      pc.fail(std::string(what) + ": table out of range");
+      return;
+    }
+    for (int k = 0; k < n; ++k) {
+      const int* e = &idx[off + 4 * k];
+      if (e[0] < 0 || e[0] >= ld || e[2] < -1 || e[2] >= ld) pc.fail(std::string(what) + ": index out of range");
+    }
+  };
+  if (bc.periodic) {
+    check_asm(bc.seam_rt, bc.Ks + bc.nx, ext, "seam rows");
+    check_asm(bc.seam_ct, bc.Ks + bc.nx, ext, "seam columns");
+  }
+  if (bc.Kn > 0) {
+    check_asm(bc.neu_rt, bc.Kn, bc.periodic ? bc.nx : ext, "flux rows");
+    check_asm(bc.neu_ct, bc.Kn + bc.nd, bc.periodic ? bc.nx : ext, "flux columns");
+  }
+  const long long troot = h->toff[bc.root];
+  const long long text = h->tree.boxes[bc.root].leaf >= 0 ? h->nq : h->k12[bc.root];
+  if (troot < 0 || text != ext || troot + ext * ext > hp.tsz) pc.fail("root conditions: root T out of range");
+}
+
 std::string validate_plan(const hps_handle* h, const HostPlan& hp) {
   PlanCheck pc;
+  if (h->bc.on) check_bc(pc, h, hp);
   const std::vector<int>& idx = hp.idx;
   const long long ops = h->ops_elems, V = h->v_rows, D = h->d_rows, UB = h->ub_rows;
   const long long G = h->ns.n_gauss, LP = (long long)h->n_leaf * h->pp, LB = (long long)h->n_leaf * h->nq;
@@ -1028,6 +1204,73 @@ int pick_nb(const hps_handle* h, const char* what, size_t elem, const std::vecto
   return tuned_choice(key, cands, h->tune_path, [&](int nb) { return time_on_stream(s, [&] { elim(nb); }); });
 }
 
+// Root conditions (BcPlan): the periodic seam's elimination [[Z_s, R_s], [-C_s, T_xx]] ->
+// [[X_s, S_s], [C_s X_s, T']] and the flux nodes' [T'_NN | T'_ND] -> [X_n | X_n T'_ND], both
+// with the build's elimination kernels (one matrix each, FP64), from the root's T.
+void build_root_bc(hps_handle* h, double* tstore, cudaStream_t s, const std::function<void*(size_t)>& get) {
+  BcPlan& bc = h->bc;
+  const int ext = (int)bc.ext.size();
+  const double* troot = tstore + h->toff[bc.root];
+  auto eliminate = [&](const CombAsm& a, const double* src, const ExtractDst& dst, float null_tol) {
+    double* work = (double*)get((size_t)a.rows * a.R * sizeof(double));
+    TIMED("root_bc_assemble", 0, (double)a.rows * a.R * 8, launch_comb_assemble(a, src, h->didx, work, s));
+    CKL();
+    GJDesc gd;
+    gd.off = 0;
+    gd.R = a.R;
+    gd.K = a.K;
+    gd.rows = a.rows;
+    gd.perm_off = 0;
+    gd.box = bc.root;
+    gd.null_tol = null_tol;
+    if (null_tol > 0.f) {  // scale of the null-direction test: the largest entry
+      double* scal = (double*)get(sizeof(double));
+      CK(cudaMemsetAsync(scal, 0, sizeof(double), s));
+      TIMED("absmax", 0, 0, launch_absmax(work, (long long)a.rows * a.R, scal, s));
+      gd.null_scale = scal;
+    }
+    GJDesc* dgd = (GJDesc*)get(sizeof(GJDesc));
+    CK(cudaMemcpyAsync(dgd, &gd, sizeof(GJDesc), cudaMemcpyHostToDevice, s));
+    int* perm = (int*)get((size_t)a.K * sizeof(int));
+    double* pinv = (double*)get(256 * sizeof(double));
+    double* prow = (double*)get((size_t)16 * a.R * sizeof(double));
+    run_gj<double>(dgd, 1, a.R, a.K, work, perm, pinv, prow, h->d_status,
+                   std::vector<std::array<int, 3>>(1, {a.R, a.K, a.rows}), "root_bc", s);
+    TIMED("gj_extract_f64", 0, (double)a.rows * a.R * 8, launch_gj_extract<double, double>(dgd, 1, a.R, work, perm, dst, s));
+    CKL();
+  };
+  if (bc.periodic) {
+    const int Rs = bc.Ks + bc.nx;
+    CombAsm a{ext, Rs, Rs, bc.Ks, 1, bc.seam_rt, bc.seam_ct};
+    ExtractDst dst{};
+    dst.TL = h->ops64 + bc.xs_off;
+    dst.TR = h->ops64 + bc.ss_off;
+    dst.BL = h->ops64 + bc.cxs_off;
+    dst.BR = tstore + bc.tp_off;
+    dst.sTL = dst.sTR = dst.sBL = 1.0;
+    dst.ld_from_desc = 1;  // X_s, C_s X_s: ld Ks; S_s, T': ld nx
+    eliminate(a, troot, dst, 0.f);
+  }
+  if (bc.Kn > 0) {
+    const int Rn = bc.Kn + bc.nd;
+    CombAsm a{bc.periodic ? bc.nx : ext, Rn, bc.Kn, bc.Kn, 0, bc.neu_rt, bc.neu_ct};
+    ExtractDst dst{};
+    dst.TL = h->ops64 + bc.bn_off;
+    dst.TL_ld = Rn;
+    dst.TR = h->ops64 + bc.bn_off + bc.Kn;
+    dst.TR_ld = Rn;
+    dst.sTL = 1.0;
+    dst.sTR = -1.0;
+    dst.sBL = 1.0;
+    // Without Dirichlet data on any side, T'_NN can be singular along Gaussian-node
+    // directions that the corner-averaged L_ce,ge maps to zero on every leaf (no Chebyshev
+    // value sees them): pivots below 1e-9 of the matrix's largest entry are such null
+    // directions (unknown set to zero); the legitimate pivots of these systems are orders
+    // of magnitude larger (condition numbers up to about 1e6).
+    eliminate(a, bc.periodic ? tstore + bc.tp_off : troot, dst, bc.nd == 0 ? 1e-9f : 0.f);
+  }
+}
+
 void build_stage(hps_handle* h, const double* coeffs, cudaStream_t s) {
   const int m = h->m, nq = h->nq, R = m + nq;
   std::vector<void*> tmp;
@@ -1127,7 +1370,7 @@ void build_stage(hps_handle* h, const double* coeffs, cudaStream_t s) {
       std::vector<std::array<int, 3>> rk;
       for (int b : lv.boxes) {
         const int R = h->k3[b] + h->k12o[b];
-        rk.push_back({R, h->k3[b], h->tree.boxes[b].parent < 0 ? h->k3[b] : R});
+        rk.push_back({R, h->k3[b], (h->tree.boxes[b].parent < 0 && !h->bc.on) ? h->k3[b] : R});
       }
       const double wbytes = (double)lv.work_elems * (lv.fp64 ? 8 : 4);
       ExtractDst dst{};
@@ -1177,6 +1420,7 @@ void build_stage(hps_handle* h, const double* coeffs, cudaStream_t s) {
         CKL();
       }
     }
+    if (h->bc.on) build_root_bc(h, tstore, s, get);
     if (h->opts.precision == HPS_MIXED) {
       h->ops32 = (float*)h->al.get(h->ops_elems * sizeof(float), s);
       h->owned.push_back({h->ops32, (size_t)h->ops_elems * sizeof(float)});
@@ -1227,6 +1471,7 @@ void ensure_ws(hps_handle* h, int nrhs, cudaStream_t s) {
     w.ubar = (double*)get((size_t)ng * sizeof(double));
   }
   w.scal = (double*)get(4 * sizeof(double));
+  if (h->bc.on) w.bcw = (double*)get((size_t)std::max(1, h->bc.rows) * R * sizeof(double));
 }
 
 // Econ mode: rebuild the leaf operators [F | S_ci] and H of chunk c into the chunk buffer
@@ -1264,6 +1509,38 @@ ItemSet leaf_range(const hps_handle* h, const ItemSet& is, int l0, int n) {
 // One pass of Algorithm 2 with operator type TA and vector type TV.
 //   f: [n_bdry][nrhs] FP64 (scattered as TV), g: [n_leaf][pp][nrhs] TV, rho: optional
 //   FP64 [n_gauss][nrhs], outputs uc [n_leaf][pp][nrhs] TV and ug [n_gauss][nrhs] TV.
+// Root conditions in the solve (BcPlan): from the root's particular flux h (rows of V),
+// the seam values u_s = S_s u_x + X_s d_s, the flux nodes' values
+// u_N = X_n (f_N - h'_N) - X_n T'_ND u_D and the value nodes' data u_D = f_D, written into
+// the Gaussian vector ug for the downward pass.  FP64.
+void root_bc_solve(hps_handle* h, const double* ops, const double* f, double* V, double* ug, int nrhs,
+                   cudaStream_t s) {
+  const BcPlan& bc = h->bc;
+  const int* idx = h->didx;
+  double* bcw = h->ws.bcw;
+  auto prod = [&](const char* name, const ItemSet& is, const double* B0, const double* B1, double* C,
+                  const double* Add, double beta) {
+    TIMED(name, 2.0 * is.elems * nrhs, is.elems * 8.0,
+          launch_gemm_items<double, double>(is.dev, is.n, ROWBLK, 0, ops, B0, B1, C, Add, idx, nrhs, beta, s));
+  };
+  if (bc.periodic) {
+    TIMED("root_bc_rows", 0, 0, launch_row_combine(idx + bc.c_d, bc.Ks, bcw, V, V, nrhs, s));
+    prod("gemm_root_bc_f64", bc.p_ws, bcw, nullptr, bcw, nullptr, 0.0);
+  }
+  TIMED("root_bc_rows", 0, 0, launch_row_combine(idx + bc.c_hx, bc.nx, bcw, V, nullptr, nrhs, s));
+  if (bc.periodic) prod("gemm_root_bc_f64", bc.p_hx, bcw, nullptr, bcw, nullptr, 1.0);
+  TIMED("root_bc_rows", 0, 0, launch_row_combine(idx + bc.c_fD, bc.nd, ug, f, nullptr, nrhs, s));
+  if (bc.Kn > 0) {
+    TIMED("root_bc_rows", 0, 0, launch_row_combine(idx + bc.c_r, bc.Kn, bcw, f, bcw, nrhs, s));
+    prod("gemm_root_bc_f64", bc.p_uN, bcw, ug, ug, nullptr, 0.0);
+  }
+  if (bc.periodic) {
+    prod("gemm_root_bc_f64", bc.p_uW, ug, nullptr, ug, bcw, 0.0);
+    TIMED("root_bc_rows", 0, 0, launch_row_combine(idx + bc.c_E, bc.Ks, ug, ug, nullptr, nrhs, s));
+  }
+  CKL();
+}
+
 template <typename TA, typename TV>
 void solve_pass(hps_handle* h, const TA* ops, const double* f, const TV* g, const double* rho, TV* uc, TV* ug,
                 TV* V, TV* dbuf, TV* P, int nrhs, cudaStream_t s) {
@@ -1325,8 +1602,14 @@ void solve_pass(hps_handle* h, const TA* ops, const double* f, const TV* g, cons
     gemmp("merge_up", lv.up, dbuf, V, nullptr, 1.0);
     if (lv.iup.n) gemm("coarsen_up", lv.iup, V, nullptr, V, nullptr, 0.0);
   }
-  // root boundary data, then the downward pass
-  if (f) TIMED("scatter_rows", 0, 0, launch_scatter_rows<TV>(f, idx + h->off_bnd, h->n_bdry, ug, nrhs, s));
+  // root boundary data (or the values that periodic / Neumann root conditions give), then
+  // the downward pass
+  if (h->bc.on) {
+    if constexpr (std::is_same<TA, double>::value && std::is_same<TV, double>::value)
+      root_bc_solve(h, ops, f, V, ug, nrhs, s);
+  } else if (f) {
+    TIMED("scatter_rows", 0, 0, launch_scatter_rows<TV>(f, idx + h->off_bnd, h->n_bdry, ug, nrhs, s));
+  }
   for (int L = H - 1; L >= 0; --L) {
     Level& lv = h->levels[L];
     if (lv.idown.n) gemm("refine_down", lv.idown, ug, nullptr, ug, nullptr, 0.0);
@@ -1448,6 +1731,8 @@ void hps_opts_default(hps_opts* o) {
   o->autotune = 0;
   o->autotune_cache = nullptr;
   o->shared_leaf = -1;
+  o->bc_we = HPS_BC_DIRICHLET;
+  o->bc_sn = HPS_BC_DIRICHLET;
 }
 
 const char* hps_last_error(void) { return g_err.c_str(); }
@@ -1582,6 +1867,79 @@ namespace {
 
 // Options, reference tables, node sets and the size checks shared by hps_build and
 // hps_plan_check.  Returns an empty string or the reason the tree/options are rejected.
+// Root conditions by side (Sec. 7.6): the boundary node ids of the west, east, south and
+// north sides of a rectangular domain; the facing west/east nodes for a periodic seam;
+// the split of the remaining root exterior nodes into flux (Neumann) and value nodes.
+std::string classify_sides(hps_handle* h, const hps_opts& o) {
+  const Tree& t = h->tree;
+  BcPlan& bc = h->bc;
+  bc = BcPlan();
+  bc.periodic = o.bc_we == HPS_BC_PERIODIC;
+  bc.neumann = o.bc_sn == HPS_BC_NEUMANN;
+  bc.on = bc.periodic || bc.neumann;
+  if (!bc.on) return std::string();
+  for (size_t b = 0; b < t.boxes.size(); ++b)
+    if (t.boxes[b].parent < 0) bc.root = (int)b;
+  const Box& r = t.boxes[bc.root];
+  bc.ext = r.leaf >= 0 ? h->ns.ge[bc.root] : h->ns.ge_old[bc.root];
+  const int q = h->q;
+  // the leaves must tile the root's rectangle; the sides are then the edges on its lines
+  long long area = 0;
+  for (int b : t.leaves) {
+    const Box& bx = t.boxes[b];
+    area += (long long)(bx.i1 - bx.i0) * (bx.j1 - bx.j0);
+  }
+  if (area != (long long)(r.i1 - r.i0) * (r.j1 - r.j0)) return "periodic or Neumann sides need a rectangular domain";
+  std::vector<std::array<int, 3>> side[4];  // S, E, N, W: (lo, hi, edge)
+  for (int e = 0; e < t.n_edges; ++e) {
+    const std::array<int, 4>& k = t.edge_keys[e];
+    int sd = -1;
+    if (k[0] == 0 && k[1] == r.j0) sd = 0;
+    else if (k[0] == 1 && k[1] == r.i1) sd = 1;
+    else if (k[0] == 0 && k[1] == r.j1) sd = 2;
+    else if (k[0] == 1 && k[1] == r.i0) sd = 3;
+    if (sd >= 0) side[sd].push_back({k[2], k[3], e});
+  }
+  for (auto& v : side) std::sort(v.begin(), v.end());
+  auto ids = [&](const std::vector<std::array<int, 3>>& v) {
+    std::vector<int> out;
+    for (const auto& a : v)
+      for (int kk = 0; kk < q; ++kk) out.push_back(a[2] * q + kk);
+    return out;
+  };
+  std::set<int> seam, flux;
+  if (bc.periodic) {
+    if (side[1].size() != side[3].size()) return "periodic west/east sides need matching nodes";
+    for (size_t i = 0; i < side[1].size(); ++i)
+      if (side[1][i][0] != side[3][i][0] || side[1][i][1] != side[3][i][1])
+        return "periodic west/east sides need matching nodes";
+    bc.W = ids(side[3]);
+    bc.E = ids(side[1]);
+    seam.insert(bc.W.begin(), bc.W.end());
+    seam.insert(bc.E.begin(), bc.E.end());
+  }
+  if (bc.neumann) {
+    for (int sd : {0, 2})
+      for (int g : ids(side[sd])) flux.insert(g);
+  }
+  std::set<int> ext(bc.ext.begin(), bc.ext.end());
+  for (int sd = 0; sd < 4; ++sd)
+    for (int g : ids(side[sd]))
+      if (!ext.count(g)) return "root exterior does not match the domain boundary";
+  for (int g : bc.ext) {
+    if (seam.count(g)) continue;
+    bc.X.push_back(g);
+    if (flux.count(g)) bc.N.push_back(g);
+    else bc.D.push_back(g);
+  }
+  bc.Ks = (int)bc.W.size();
+  bc.nx = (int)bc.X.size();
+  bc.Kn = (int)bc.N.size();
+  bc.nd = (int)bc.D.size();
+  bc.rows = 2 * bc.Ks + bc.nx + bc.Kn;
+  return std::string();
+}
+
 // Every leaf spans the same number of finest-grid units in x and in y (so all leaves have
 // the same size and the same reference-to-physical scaling).
 bool equal_leaf_spans(const Tree& t) {
@@ -1627,7 +1985,7 @@ std::string setup_host(hps_handle* h, const Tree& tree, int p, const hps_opts& o
   }
   for (size_t b = 0; b < h->tree.boxes.size(); ++b)
     if (h->tree.boxes[b].leaf < 0 && h->ns.J3[b].empty()) return "a merge has no shared edge";
-  return std::string();
+  return classify_sides(h, o);
 }
 
 int check_opts(int p, const hps_opts* opts, hps_opts& o) {
@@ -1641,6 +1999,12 @@ int check_opts(int p, const hps_opts* opts, hps_opts& o) {
   if (o.store_leaf_ops == 0 && o.precision != HPS_FP64)
     return fail(HPS_ERR_INVALID_ARG, "leaf recomputation (store_leaf_ops = 0) needs precision HPS_FP64");
   if (o.shared_leaf < -1 || o.shared_leaf > 1) return fail(HPS_ERR_INVALID_ARG, "shared_leaf must be -1, 0 or 1");
+  if (o.bc_we != HPS_BC_DIRICHLET && o.bc_we != HPS_BC_PERIODIC)
+    return fail(HPS_ERR_INVALID_ARG, "bc_we must be HPS_BC_DIRICHLET or HPS_BC_PERIODIC");
+  if (o.bc_sn != HPS_BC_DIRICHLET && o.bc_sn != HPS_BC_NEUMANN)
+    return fail(HPS_ERR_INVALID_ARG, "bc_sn must be HPS_BC_DIRICHLET or HPS_BC_NEUMANN");
+  if ((o.bc_we != HPS_BC_DIRICHLET || o.bc_sn != HPS_BC_DIRICHLET) && o.precision != HPS_FP64)
+    return fail(HPS_ERR_INVALID_ARG, "periodic or Neumann sides need precision HPS_FP64");
   if (o.ir_tol <= 0.0) o.ir_tol = 1e-10;
   if (o.ir_max_iter <= 0) o.ir_max_iter = 10;
   return HPS_OK;
@@ -1896,6 +2260,34 @@ int hps_solve_ext(hps_handle* h, const double* f, const double* g, const double*
   }
 }
 
+int hps_apply(hps_handle* h, const double* coeffs, const double* u, int nrhs, double alpha, double beta, double* out,
+              void* stream) {
+  if (!h) return fail(HPS_ERR_INVALID_ARG, "handle is NULL");
+  if (!coeffs || !u || !out) return fail(HPS_ERR_INVALID_ARG, "coeffs, u and out must be device pointers");
+  if (nrhs < 1 || nrhs > 4096) return fail(HPS_ERR_INVALID_ARG, "nrhs must be in [1, 4096]");
+  cudaStream_t s = (cudaStream_t)stream;
+  try {
+    ResidualArgs ra;
+    ra.coeffs = coeffs;
+    ra.n_leaf = h->n_leaf;
+    ra.p = h->p;
+    ra.q = h->q;
+    ra.hxy = h->dhxy;
+    ra.D = h->dD;
+    ra.D2 = h->dD2;
+    ra.Lloc = h->dLloc;
+    ra.ci = h->didx + h->off_ci;
+    ra.Lloc_df = h->dLloc_df;
+    ra.Lce_df = h->dLce_df;
+    TIMED("leaf_apply_df", 2.0 * h->n_leaf * nrhs * 5.0 * h->p * h->p * h->p, (double)h->n_leaf * h->pp * nrhs * 16.0,
+          launch_leaf_apply_df(ra, u, alpha, beta, out, nrhs, s));
+    CKL();
+    return HPS_OK;
+  } catch (const CudaError& e) {
+    return fail(e.code, e.msg);
+  }
+}
+
 int hps_solve(hps_handle* h, const double* f, const double* g, int nrhs, double* u, void* stream) {
   return hps_solve_ext(h, f, g, nullptr, nrhs, u, nullptr, nullptr, stream);
 }
@@ -1906,6 +2298,7 @@ int hps_adjoint(hps_handle* h, const double* ubar_in, int nrhs, const double* u,
   if (!ubar_in) return fail(HPS_ERR_INVALID_ARG, "dJdu is NULL");
   if (nrhs < 1 || nrhs > 4096) return fail(HPS_ERR_INVALID_ARG, "nrhs must be in [1, 4096]");
   if (h->opts.precision != HPS_FP64) return fail(HPS_ERR_STATE, "hps_adjoint needs an HPS_FP64 handle");
+  if (h->bc.on) return fail(HPS_ERR_STATE, "hps_adjoint needs Dirichlet data on every side");
   if (cbar && !u) return fail(HPS_ERR_INVALID_ARG, "coefficient gradients need the forward solution u");
   cudaStream_t s = (cudaStream_t)stream;
   try {
@@ -2100,6 +2493,7 @@ extern "C" int hps_solve_noalloc(hps_handle* h, const double* f, const double* g
   if (!f || !g || !u) return fail(HPS_ERR_INVALID_ARG, "f, g and u must be device pointers");
   if (nrhs < 1) return fail(HPS_ERR_INVALID_ARG, "nrhs must be >= 1");
   if (h->opts.precision != HPS_FP64) return fail(HPS_ERR_STATE, "hps_solve_noalloc needs an HPS_FP64 handle");
+  if (h->bc.on) return fail(HPS_ERR_STATE, "hps_solve_noalloc needs Dirichlet data on every side");
   const size_t R = (size_t)nrhs;
   const size_t bV = align256((size_t)h->v_rows * R * sizeof(double));
   const size_t bD = align256((size_t)std::max(1, h->d_rows) * R * sizeof(double));

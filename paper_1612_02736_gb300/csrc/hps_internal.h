@@ -101,6 +101,10 @@ struct GJDesc {
                        // top block rows [X | S] are wanted (row stride stays R)
   int perm_off;        // offset of its K-entry logical->physical row map
   int box;             // box id, for error reports
+  float null_tol = 0.f;  // > 0: a pivot below null_tol x (*null_scale, the matrix's largest
+                         // entry) is a null direction of a consistent singular system: its
+                         // unknown is set to zero and its equation dropped, not reported
+  const double* null_scale = nullptr;
 };
 
 // A gathered, batched matrix product item: rows [0, M) of a row block of operator A.
@@ -189,6 +193,14 @@ template <typename T, typename TT>
 void launch_merge_assemble(const MergeDesc* d, int nmat, int maxR, const TT* tstore,
                            const int* pos, T* work, cudaStream_t s);
 
+// One root-condition matrix (rows x R, row-major) assembled from a DtN map src (ld):
+// row r takes up to two (index, sign) pairs from idx[rt + 4r ..], column c from
+// idx[ct + 4c ..]; flip negates the blocks off the K x K diagonal partition.
+struct CombAsm {
+  int ld, R, rows, K, flip, rt, ct;
+};
+void launch_comb_assemble(const CombAsm& a, const double* src, const int* idx, double* dst, cudaStream_t s);
+
 // Small batched dense products C = A B (row-major, per-matrix offsets from three bases),
 // used for the coarsened DtN maps T_new = P_down T P_up of refined parents.
 struct BGemm {
@@ -253,9 +265,16 @@ struct ResidualArgs {
 // Residual r = g - A u, leaf fluxes and u_ce = L_ce,ge u_ge, in double-float arithmetic.
 void launch_leaf_residual_df(const ResidualArgs& a, const int* leaf_edges, const int* ce, const double* ug, const double* g, double* uc,
                              double* r_out, double* vflux, int nrhs, cudaStream_t s);
+// y = alpha u + beta A u at leaf interior nodes, 0 at exterior nodes, double-float.
+void launch_leaf_apply_df(const ResidualArgs& a, const double* u, double alpha, double beta, double* out, int nrhs,
+                          cudaStream_t s);
 void launch_jump_residual(const int* pairs, int npairs, int q, const double* vflux,
                           double* rho_out, int nrhs, cudaStream_t s);
 void launch_absmax(const double* x, long long n, double* out, cudaStream_t s);
+// Row combinations dst[d] = A[a] (+ sign * B[b] if b >= 0), entries (d, a, b, sign) at tab,
+// rows of nrhs values.
+void launch_row_combine(const int* tab, int n, double* dst, const double* A, const double* B, int nrhs,
+                        cudaStream_t s);
 
 // Adjoint helpers.
 void launch_coeff_grad(const ResidualArgs& a, const double* uc, const double* gbar,

@@ -256,7 +256,95 @@ __global__ void __launch_bounds__(256) coeff_grad_df_kernel(ResidualArgs a, cons
   }
 }
 
+// y = alpha u + beta A u at interior nodes (0 on the exterior) with A the collocation
+// operator of Sec. 3.2; u's exterior values are used as given.  Double-float arithmetic.
+__global__ void __launch_bounds__(256) leaf_apply_df_kernel(ResidualArgs a, const double* __restrict__ u,
+                                                            double alpha, double beta, double* __restrict__ out,
+                                                            int nrhs) {
+  const int lf = blockIdx.x;
+  const int p = a.p, pp = p * p;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  df* sD = reinterpret_cast<df*>(smraw);
+  df* sD2 = sD + pp;
+  df* sDt = sD2 + pp;
+  df* sD2t = sDt + pp;
+  df* cf = sD2t + pp;        // 6 * pp
+  df* us = cf + 6 * pp;      // pp * RC
+  df* uxs = us + pp * RC;    // pp * RC
+  const int tid = threadIdx.x, bs = blockDim.x;
+  for (int e = tid; e < pp; e += bs) {
+    sD[e] = df_from(a.D[e]);
+    sD2[e] = df_from(a.D2[e]);
+    const int i = e / p, k = e - (e / p) * p;
+    sDt[k * p + i] = sD[e];
+    sD2t[k * p + i] = sD2[e];
+  }
+  const long long st = a.n_leaf * pp;
+  for (int e = tid; e < 6 * pp; e += bs) {
+    const int k = e / pp, n = e - (e / pp) * pp;
+    const double c = a.coeffs[k * st + (long long)lf * pp + n];
+    cf[e] = df_from(k == 0 || k == 2 ? -c : (k == 1 ? -2.0 * c : c));
+  }
+  const df sx = df_from(2.0 / a.hxy[2 * lf]), sy = df_from(2.0 / a.hxy[2 * lf + 1]);
+  const df sxx = df_mul(sx, sx), syy = df_mul(sy, sy);
+  const df dal = df_from(alpha), dbe = df_from(beta);
+  const long long lbase = (long long)lf * pp * nrhs;
+  for (int r0 = 0; r0 < nrhs; r0 += RC) {
+    const int rc = min(RC, nrhs - r0);
+    __syncthreads();
+    for (int e = tid; e < pp * RC; e += bs) {
+      const int n = e / RC, rr = e - (e / RC) * RC;
+      us[e] = df_from(rr < rc ? u[lbase + (long long)n * nrhs + r0 + rr] : 0.0);
+    }
+    __syncthreads();
+    for (int e = tid; e < pp * RC; e += bs) {
+      const int n = e / RC, rr = e - (e / RC) * RC;
+      const int ix = n % p, iy = n / p;
+      df v = {0.f, 0.f};
+      for (int k = 0; k < p; ++k) v = df_fma_acc(v, sDt[k * p + ix], us[(iy * p + k) * RC + rr]);
+      uxs[e] = df_mul(sx, v);
+    }
+    __syncthreads();
+    for (int e = tid; e < pp * RC; e += bs) {
+      const int n = e / RC, rr = e - (e / RC) * RC;
+      if (rr >= rc) continue;
+      const int ix = n % p, iy = n / p;
+      double y = 0.0;
+      if (ix > 0 && ix < p - 1 && iy > 0 && iy < p - 1) {
+        df uy = {0.f, 0.f}, uxx = {0.f, 0.f}, uyy = {0.f, 0.f}, uxy = {0.f, 0.f};
+        for (int k = 0; k < p; ++k) {
+          uy = df_fma_acc(uy, sD[iy * p + k], us[(k * p + ix) * RC + rr]);
+          uxx = df_fma_acc(uxx, sD2t[k * p + ix], us[(iy * p + k) * RC + rr]);
+          uyy = df_fma_acc(uyy, sD2[iy * p + k], us[(k * p + ix) * RC + rr]);
+          uxy = df_fma_acc(uxy, sD[iy * p + k], uxs[(k * p + ix) * RC + rr]);
+        }
+        // A u = -c11 u_xx - 2 c12 u_xy - c22 u_yy + c1 u_x + c2 u_y + c u  (Sec. 3.2)
+        df Au = df_mul(cf[n], df_mul(uxx, sxx));
+        Au = df_fma(Au, cf[pp + n], df_mul(uxy, sy));
+        Au = df_fma(Au, cf[2 * pp + n], df_mul(uyy, syy));
+        Au = df_fma(Au, cf[3 * pp + n], uxs[e]);
+        Au = df_fma(Au, cf[4 * pp + n], df_mul(sy, uy));
+        Au = df_fma(Au, cf[5 * pp + n], us[e]);
+        y = df_to(df_add(df_mul(dal, us[e]), df_mul(dbe, Au)));
+      }
+      out[lbase + (long long)n * nrhs + r0 + rr] = y;
+    }
+  }
+}
+
 }  // namespace
+
+void launch_leaf_apply_df(const ResidualArgs& a, const double* u, double alpha, double beta, double* out, int nrhs,
+                          cudaStream_t s) {
+  const int pp = a.p * a.p;
+  const size_t smem = (size_t)(10 * pp + 2 * pp * RC) * sizeof(df);
+  static size_t configured = 0;
+  if (smem > 48 * 1024 && smem > configured) {
+    cudaFuncSetAttribute(leaf_apply_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    configured = smem;
+  }
+  leaf_apply_df_kernel<<<(unsigned)a.n_leaf, 256, smem, s>>>(a, u, alpha, beta, out, nrhs);
+}
 
 void launch_coeff_grad(const ResidualArgs& a, const double* uc, const double* gbar, double* grad, int nrhs,
                        cudaStream_t s) {

@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(256) gj_panel_kernel(const GJDesc* __restrict_
   __shared__ T red_v[32];
   __shared__ int red_i[32];
   __shared__ T colscale[NBMAX];
-  __shared__ int piv_row;
+  __shared__ int piv_row, piv_null;
   T* M = work + md.off;
   const int R = md.R;
   int* pm = perm + md.perm_off + c0;
@@ -100,7 +100,8 @@ __global__ void __launch_bounds__(256) gj_panel_kernel(const GJDesc* __restrict_
       for (int w = 1; w < nwarp; ++w)
         if (red_v[w] > b || (red_v[w] == b && red_i[w] < ib)) { b = red_v[w]; ib = red_i[w]; }
       const T tiny = T(64) * Eps<T>::v * colscale[j];
-      if (!(b > tiny) && status) atomicCAS(status, 0, md.box + 1);
+      piv_null = md.null_tol > 0.f && md.null_scale && !(b > (T)(md.null_tol * *md.null_scale));
+      if (!piv_null && !(b > tiny) && status) atomicCAS(status, 0, md.box + 1);
       if (ib >= nrows) ib = j;
       piv_row = ib;
       const int t = pr[j]; pr[j] = pr[ib]; pr[ib] = t;
@@ -111,6 +112,10 @@ __global__ void __launch_bounds__(256) gj_panel_kernel(const GJDesc* __restrict_
       const T t = P[j * nb + tid]; P[j * nb + tid] = P[r * nb + tid]; P[r * nb + tid] = t;
     }
     __syncthreads();
+    if (piv_null) {  // null direction: zero pivot, so no multipliers and a zero Pinv row
+      if (tid == 0) P[j * nb + j] = T(0);
+      __syncthreads();
+    }
     const T pv = P[j * nb + j];
     const T inv = (pv != T(0)) ? T(1) / pv : T(0);
     for (int i = j + 1 + tid; i < nrows; i += bs) {

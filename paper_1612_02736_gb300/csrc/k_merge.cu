@@ -7,6 +7,8 @@
 // S = X [-T31a | T32b], C X and T_tau = blkdiag(T11a, T22b) + [T13a; T23b] S in place.
 // posA / posB give each row's position in alpha's / beta's exterior list (or -1), so an
 // entry is  sa * Ta[posA r][posA c] + sb * Tb[posB r][posB c]  with the signs above.
+#include <algorithm>
+
 #include "hps_internal.h"
 
 namespace hps {
@@ -41,6 +43,34 @@ __global__ void __launch_bounds__(256) merge_assemble_kernel(const MergeDesc* __
       v += sb * (double)Tb[(long long)br * md.lda_b + bc];
     }
     M[e] = (T)v;
+  }
+}
+
+// Root-condition matrices (periodic seam, Neumann nodes): entry (r, c) is
+// sum over (i, si) of row r and (j, sj) of column c of si sj src[i][j], with up to two
+// terms each, negated in the off-diagonal blocks (r < K) != (c < K) when flip is set.
+__global__ void __launch_bounds__(256) comb_assemble_kernel(CombAsm a, const double* __restrict__ src,
+                                                            const int* __restrict__ idx,
+                                                            double* __restrict__ dst) {
+  const long long total = (long long)a.rows * a.R;
+  const int* rt = idx + a.rt;
+  const int* ct = idx + a.ct;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(e / a.R), c = (int)(e - (e / a.R) * a.R);
+    double v = 0.0;
+    for (int u = 0; u < 2; ++u) {
+      const int i = rt[4 * r + 2 * u];
+      if (i < 0) continue;
+      const double si = (double)rt[4 * r + 2 * u + 1];
+      for (int w = 0; w < 2; ++w) {
+        const int j = ct[4 * c + 2 * w];
+        if (j < 0) continue;
+        v += si * (double)ct[4 * c + 2 * w + 1] * src[(long long)i * a.ld + j];
+      }
+    }
+    if (a.flip && ((r < a.K) != (c < a.K))) v = -v;
+    dst[e] = v;
   }
 }
 
@@ -81,6 +111,12 @@ void launch_merge_assemble(const MergeDesc* d, int nmat, int maxR, const TT* tst
   int gx = (int)((total + 255) / 256);
   if (gx > 2048) gx = 2048;
   merge_assemble_kernel<T, TT><<<dim3(gx, nmat), 256, 0, s>>>(d, tstore, pos, work);
+}
+
+void launch_comb_assemble(const CombAsm& a, const double* src, const int* idx, double* dst, cudaStream_t s) {
+  const long long total = (long long)a.rows * a.R;
+  const int grid = (int)std::min<long long>((total + 255) / 256, 4096);
+  comb_assemble_kernel<<<grid, 256, 0, s>>>(a, src, idx, dst);
 }
 
 template void launch_merge_assemble<double, double>(const MergeDesc*, int, int, const double*, const int*,

@@ -389,6 +389,19 @@ __global__ void exterior_refresh_kernel(int p, int q, const int* __restrict__ le
   }
 }
 
+__global__ void row_combine_kernel(const int* __restrict__ tab, int n, double* __restrict__ dst,
+                                   const double* __restrict__ A, const double* __restrict__ B, int nrhs) {
+  const long long total = (long long)n * nrhs;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(e / nrhs), r = (int)(e - (e / nrhs) * nrhs);
+    const int* t = tab + 4 * k;
+    double v = A[(long long)t[1] * nrhs + r];
+    if (t[2] >= 0) v += (double)t[3] * B[(long long)t[2] * nrhs + r];
+    dst[(long long)t[0] * nrhs + r] = v;
+  }
+}
+
 inline int grid_for(long long n, int bs = 256, int cap = 8192) {
   long long g = (n + bs - 1) / bs;
   if (g < 1) g = 1;
@@ -439,6 +452,12 @@ void launch_split_reduce(const SplitRed* d, int n, const TV* P, TV* C, const TV*
   if (n <= 0) return;
   dim3 grid(grid_for((long long)ROWS_HINT * nrhs, 256, 16), n);
   split_reduce_kernel<TV><<<grid, 256, 0, s>>>(d, P, C, Add, idx, nrhs, (TV)beta);
+}
+
+void launch_row_combine(const int* tab, int n, double* dst, const double* A, const double* B, int nrhs,
+                        cudaStream_t s) {
+  if (n <= 0) return;
+  row_combine_kernel<<<grid_for((long long)n * nrhs), 256, 0, s>>>(tab, n, dst, A, B, nrhs);
 }
 
 void launch_exterior_refresh(int n_leaf, int p, int q, const int* leaf_edges, const double* Lce, const int* ce,

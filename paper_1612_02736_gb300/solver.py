@@ -135,11 +135,15 @@ class Solver:
     shared_leaf: "auto" stores one leaf's operators for all leaves when every leaf has the
     same size and interior coefficients (constant-coefficient problems); True requires it,
     False never shares.
+    bc_we ("dirichlet" | "periodic") and bc_sn ("dirichlet" | "neumann"): boundary kinds of
+    the west/east and south/north sides of a rectangular domain (Sec. 7.6); f then holds
+    Dirichlet values, or du/dy on Neumann sides, and is ignored on periodic sides.
     """
 
     def __init__(self, tree, coeffs, p, precision="fp64", q=None, ir_tol=None, ir_max_iter=None,
                  fp64_top_levels=None, store_leaf_ops=True, use_graphs=True, autotune=False,
-                 autotune_cache=None, shared_leaf="auto", allocator="torch"):
+                 autotune_cache=None, shared_leaf="auto", bc_we="dirichlet", bc_sn="dirichlet",
+                 allocator="torch"):
         lib = N.load()
         if not (coeffs.is_cuda and coeffs.dtype == torch.float64 and coeffs.is_contiguous()):
             raise ValueError("coeffs must be a contiguous CUDA float64 tensor")
@@ -160,6 +164,8 @@ class Solver:
         self._tune_path = None if autotune_cache is None else str(autotune_cache).encode()
         opts.autotune_cache = self._tune_path
         opts.shared_leaf = {"auto": -1, False: 0, True: 1}[shared_leaf]
+        opts.bc_we = {"dirichlet": N.HPS_BC_DIRICHLET, "periodic": N.HPS_BC_PERIODIC}[bc_we]
+        opts.bc_sn = {"dirichlet": N.HPS_BC_DIRICHLET, "neumann": N.HPS_BC_NEUMANN}[bc_sn]
         self.tree, self.p, self.precision = tree, p, precision
         self._alloc = _allocator() if allocator == "torch" else None
         out = C.c_void_p()
@@ -198,6 +204,19 @@ class Solver:
             if ug is not None:
                 ug = ug.squeeze(-1)
         return (u, ug) if return_gauss else u
+
+    def apply(self, coeffs, u, alpha=0.0, beta=1.0):
+        """alpha u + beta A u at every leaf's interior Chebyshev nodes (0 at the exterior
+        ones), A the collocation operator for the coefficient fields coeffs (6, n_leaf,
+        p*p); u is (n_leaf, p*p[, nrhs])."""
+        squeeze = u.dim() == 2
+        uu = (u.unsqueeze(-1) if squeeze else u).contiguous()
+        if not (coeffs.is_cuda and coeffs.dtype == torch.float64 and coeffs.is_contiguous()):
+            raise ValueError("coeffs must be a contiguous CUDA float64 tensor")
+        out = torch.empty_like(uu)
+        N.check(N.load().hps_apply(self._h, _ptr(coeffs), _ptr(uu), uu.shape[-1], float(alpha), float(beta),
+                                   _ptr(out), _stream()))
+        return out.squeeze(-1) if squeeze else out
 
     def adjoint(self, dJdu, u=None, want_coeffs=True):
         """(dJ/df, dJ/dg, dJ/dcoeffs) for the gradient dJdu of the solution; dJ/dcoeffs

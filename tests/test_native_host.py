@@ -164,6 +164,48 @@ def test_plan_shared_leaf_needs_equal_leaves(lib):
     lib.hps_tree_destroy(t)
 
 
+@pytest.mark.parametrize("bc", [(1, 2), (1, 0), (0, 2)])
+@pytest.mark.parametrize("nx,ny,p", [(1, 1, 8), (2, 2, 8), (4, 2, 7), (3, 5, 9), (16, 16, 17), (64, 64, 16)])
+def test_plan_root_conditions_stay_in_bounds(lib, bc, nx, ny, p):
+    # periodic west/east and Neumann south/north sides: seam and flux tables, products
+    from paper_1612_02736_gb300 import _native
+    t = _tree(lib, nx, ny)
+    opts = _native.hps_opts()
+    lib.hps_opts_default(C.byref(opts))
+    opts.bc_we, opts.bc_sn = bc
+    assert lib.hps_plan_check(t, p, C.byref(opts)) == 0, lib.hps_last_error()
+    opts.precision = 1
+    assert lib.hps_plan_check(t, p, C.byref(opts)) == 1      # FP64 only
+    lib.hps_tree_destroy(t)
+
+
+def test_plan_root_conditions_need_a_rectangle(lib):
+    from paper_1612_02736_gb300 import _native
+    opts = _native.hps_opts()
+    lib.hps_opts_default(C.byref(opts))
+    opts.bc_sn = 2
+    mask = (C.c_uint8 * 4)(1, 0, 1, 1)        # an L of three unit squares
+    t = C.c_void_p()
+    assert lib.hps_tree_mask(0.0, 0.0, 1.0, 2, 2, mask, C.byref(t)) == 0, lib.hps_last_error()
+    assert lib.hps_plan_check(t, 8, C.byref(opts)) == 1
+    assert "rectangular" in lib.hps_last_error().decode()
+    lib.hps_tree_destroy(t)
+    # refined toward the west side only: facing west/east nodes no longer match
+    u = _tree(lib, 2, 2)
+    pts = (C.c_double * 2)(0.01, 0.5)
+    r = C.c_void_p()
+    assert lib.hps_tree_refine(u, pts, 1, 1, C.byref(r)) == 0, lib.hps_last_error()
+    opts.bc_we = 1
+    opts.bc_sn = 0
+    assert lib.hps_plan_check(r, 8, C.byref(opts)) == 1
+    assert "matching" in lib.hps_last_error().decode()
+    opts.bc_we = 0
+    opts.bc_sn = 2
+    assert lib.hps_plan_check(r, 8, C.byref(opts)) == 0, lib.hps_last_error()
+    lib.hps_tree_destroy(r)
+    lib.hps_tree_destroy(u)
+
+
 def test_plan_rejects_bad_options(lib):
     from paper_1612_02736_gb300 import _native
     t = _tree(lib, 2, 2)

@@ -92,3 +92,30 @@ def test_crank_nicolson_fourier_mode():
     G = (1 / k + lam / 2) / (1 / k - lam / 2)
     exact = np.real(G ** steps * np.exp(2j * np.pi * X)) * np.cos(np.pi * Y)
     assert np.max(np.abs(u - exact)) < 1e-9
+
+
+def test_null_directions_are_invisible_to_chebyshev_values():
+    # periodic west/east + Neumann south/north with p = 8: the dense system is singular,
+    # its null vector lives on the Gaussian unknowns only, every leaf's corner-averaged
+    # interpolation L_ce,ge maps it to zero, and solutions differing by it give the same
+    # u_c (the least-squares solution is taken)
+    from oracle import spectral as sp
+    p = 8
+    t = tr.uniform_tree(0, 0, 1, 1, 2, 2, p - 1)
+    X, Y = leaf_points(t, p)
+    coeffs = np.array(syn.VarCoeffProblem().coeffs(X, Y))
+    coeffs[5] += 1.0
+    bc = (bd.PERIODIC, bd.NEUMANN)
+    K, meta = dense.assemble(t, coeffs, p, bc)
+    _, sv, Vt = np.linalg.svd(K)
+    assert sv[-1] < 1e-11 * sv[0] < sv[-2]
+    v = Vt[-1]
+    ng = meta["ng"]
+    assert np.max(np.abs(v[ng:])) < 1e-12
+    L = sp.L_ce_ge(p, p - 1)
+    for lf in range(t.n_leaves):
+        assert np.max(np.abs(L @ v[t.boxes[t.leaves[lf]].ge])) < 1e-12
+    g = np.cos(2 * X) * Y
+    ud, _ = dense.solve(t, coeffs, p, np.zeros(len(t.boundary)), g, bc=bc)
+    uh, _ = hps.solve(t, hps.build(t, coeffs, p), p, np.zeros(len(t.boundary)), g, bc=bc)
+    assert np.max(np.abs(uh - ud)) < 1e-10 * np.max(np.abs(ud))
