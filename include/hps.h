@@ -45,7 +45,7 @@ typedef enum {
   HPS_ERR_SINGULAR = 3,      /* a leaf or merge pivot fell below tiny * scale            */
   HPS_ERR_OOM = 4,           /* the allocator returned NULL                              */
   HPS_ERR_CUDA = 5,          /* a CUDA runtime call failed (message has the CUDA text)   */
-  HPS_ERR_TIMEOUT = 6,       /* reserved for bounded device waits                        */
+  HPS_ERR_TIMEOUT = 6,       /* a bounded device wait (tensor-core product) ran out      */
   HPS_ERR_NO_CONVERGENCE = 7,/* iterative refinement hit ir_max_iter                     */
   HPS_ERR_STATE = 8          /* call not valid for this handle (e.g. precision)          */
 } hps_status;

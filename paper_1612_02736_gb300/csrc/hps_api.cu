@@ -1177,7 +1177,7 @@ void run_gj(const GJDesc* gj, int nmat, int maxR, int maxK, T* work, int* perm, 
     TIMED(("gj_prep_" + sf).c_str(), fq, 0,
           launch_gj_prep<T>(gj, nmat, maxR, work, perm, pinv, prow, prow_stride, c0, nb, s));
     TIMED(("gj_update_" + sf).c_str(), fu, bu,
-          launch_gj_update<T>(gj, nmat, maxR, maxRows, work, perm, prow, prow_stride, c0, nb, s));
+          launch_gj_update<T>(gj, nmat, maxR, maxRows, work, perm, prow, prow_stride, c0, nb, s, status));
   }
   CKL();
 }
@@ -2148,6 +2148,10 @@ int hps_build(const hps_tree* tree, const double* coeffs, int p, const hps_opts*
     int status = 0;
     CK(cudaMemcpyAsync(&status, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    if (status < 0) {
+      delete h;
+      return fail(HPS_ERR_TIMEOUT, "a tensor-core update did not complete within its wait limit");
+    }
     if (status != 0) {
       const int box = status - 1;
       delete h;
@@ -2428,6 +2432,7 @@ int hps_sync_status(hps_handle* h, void* stream) {
   if (cudaMemcpyAsync(&status, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
     return fail(HPS_ERR_CUDA, cudaGetErrorString(cudaGetLastError()));
+  if (status < 0) return fail(HPS_ERR_TIMEOUT, "a tensor-core update did not complete within its wait limit");
   if (status) return fail(HPS_ERR_SINGULAR, "pivot breakdown in box " + std::to_string(status - 1));
   return HPS_OK;
 }

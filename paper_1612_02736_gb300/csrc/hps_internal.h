@@ -154,7 +154,7 @@ void launch_gj_prep(const GJDesc* d, int nmat, int maxR, T* work, const int* per
                     T* prow, long long prow_stride, int c0, int nb, cudaStream_t s);
 template <typename T>
 void launch_gj_update(const GJDesc* d, int nmat, int maxR, int maxRows, T* work, const int* perm, T* prow,
-                      long long prow_stride, int c0, int nb, cudaStream_t s);
+                      long long prow_stride, int c0, int nb, cudaStream_t s, int* status);
 
 // Extraction of a finished elimination: with sigma the logical->physical row map,
 //   TL[i][j] = sTL * M[sigma(i)][sigma^-1(j)]   (i, j < K)

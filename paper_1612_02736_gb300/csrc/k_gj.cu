@@ -21,7 +21,11 @@
 // FP64 on GB300 runs on the FFMA pipe (no FP64 tensor path is faster on this part), so
 // the update is a register-tiled SIMT product.
 #include <cfloat>
+#include <cstdint>
 #include <cstdio>
+#include <type_traits>
+
+#include <cuda_bf16.h>
 
 #include "hps_internal.h"
 
@@ -267,6 +271,238 @@ __global__ void __launch_bounds__(256) gj_update_kernel(const GJDesc* __restrict
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// FP64 rank-nb update on the tcgen05 tensor cores with exact digit slicing.
+//
+// GB300's FP64 pipe does 2 FMA per clock per SM, its bf16 tensor cores about 1000 times
+// that.  The update M_r += W_r Prow is a product with inner dimension nb <= 16, so it is
+// computed exactly in pieces: every row of W (over its nb entries) is scaled by a power
+// of two 2^e_r (e_r the exponent of the row's largest entry) and written as 8 signed
+// base-256 digits, W_rt = 2^e_r sum_s a_s 2^(1-8s), |a_s| <= 128, each digit an integer
+// exactly representable in bf16; every column of Prow likewise with 2^f_c and digits b_t.
+// Digit products are integers below 2^14 and a diagonal d = s + t sums at most 8 x 16 of
+// them, so the FP32 accumulation of the tensor core is exact.  One tcgen05.mma per digit
+// pair with s + t <= 9 (36 per tile) accumulates diagonal d in its own TMEM columns; the
+// epilogue combines the diagonals exactly in 128-bit integers, normalises, converts once to FP64 and
+// scales by a power of two.  The neglected terms are below about 2^-64 x 16 x max|W_r| x
+// max|P_c|: on the leaf and merge eliminations that normwise bound can exceed the
+// elementwise FP64 bound 2^-53 sum_t |W_rt| |P_tc| by up to 1e5 (measured on leaf panels),
+// which 7 digits (2^-56) did not absorb and 8 digits do.  The kernel is then bound by
+// the read and write of the updated matrix (HBM), not by arithmetic.
+//
+// Tile: 128 rows x 32 columns, 128 threads (thread r owns row r for the digits and the
+// epilogue); operands in shared memory in the canonical K-major no-swizzle layout (8-row x
+// 16-byte core matrices, LBO 128 bytes along K, SBO 256 bytes between row groups).
+constexpr int TCM = 128, TCN = 32, TCS = 8, TCKEEP = 9, TCNACC = TCKEEP - 1;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor (tcgen05): start, LBO, SBO (all >> 4), version 1,
+// no swizzle.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFF) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// byte offset of (row, k) in a K-major tile with 16 k per row
+__device__ __forceinline__ int kmaj16(int row, int k) {
+  return (row >> 3) * 256 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
+}
+
+// Digits are formed with integer operations only (the FP64 pipe is the scarce unit):
+// with E the biased exponent of x and Emax the largest of its row (or column), the
+// fixed-point value X = x / 2^(Emax - 1022) * 2^63 is the 53-bit significand shifted by
+// E - Emax + 10 (rounded when shifted right), |X| < 2^63; its balanced base-256 digits
+// a_8 .. a_1 (each in [-128, 128]) satisfy x = 2^(Emax-1022) sum_s a_s 2^(1-8s).
+__device__ __forceinline__ int biased_exp(long long bits) { return (int)((bits >> 52) & 0x7FF); }
+
+__device__ __forceinline__ void write_digits(long long bits, int emax, unsigned char* base, int plane_bytes,
+                                             int off) {
+  const int E = biased_exp(bits);
+  long long X = 0;
+  if (E > 0) {
+    const long long m = (bits & 0xFFFFFFFFFFFFFll) | (1ll << 52);
+    const int sh = E - emax + 10;
+    if (sh >= 0) X = m << sh;
+    else if (sh > -60) X = (m + (1ll << (-sh - 1))) >> (-sh);
+    if (bits < 0) X = -X;
+  }
+#pragma unroll
+  for (int s = TCS - 1; s >= 0; --s) {
+    int a;
+    if (s > 0) {
+      a = (int)((X + 128) & 255) - 128;
+      X = (X - a) >> 8;
+    } else {
+      a = (int)X;
+    }
+    *reinterpret_cast<__nv_bfloat16*>(base + s * plane_bytes + off) = __float2bfloat16_rn((float)a);
+  }
+}
+
+__global__ void __launch_bounds__(128) gj_update_tc_kernel(const GJDesc* __restrict__ d, double* __restrict__ work,
+                                                          const int* __restrict__ perm,
+                                                          const double* __restrict__ prow, long long prow_stride,
+                                                          int c0, int nb_req, int* __restrict__ status) {
+  const GJDesc md = d[blockIdx.y];
+  if (c0 >= md.K) return;
+  const int nb = min(nb_req, md.K - c0);
+  const int R = md.R, rows = md.rows;
+  const int tiles = (R + TCN - 1) / TCN;
+  const int tm = blockIdx.x / tiles, tn = blockIdx.x - (blockIdx.x / tiles) * tiles;
+  const int row0 = tm * TCM, col0 = tn * TCN;
+  if (row0 >= rows) return;
+  if (col0 >= c0 && col0 + TCN <= c0 + nb) return;  // tile entirely inside the panel
+  __shared__ __align__(1024) unsigned char sA[TCS * TCM * 16 * 2];  // 8 planes x 4 KB
+  __shared__ __align__(1024) unsigned char sB[TCS * TCN * 16 * 2];  // 8 planes x 1 KB
+  __shared__ int cexp[TCN];
+  __shared__ int pphys[16];
+  __shared__ uint32_t tmem_base;
+  __shared__ __align__(8) uint64_t mbar;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  double* M = work + md.off;
+  if (tid < nb) pphys[tid] = perm[md.perm_off + c0 + tid];
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  __syncthreads();
+  // row digits (W = the final panel columns of this row)
+  const int row = row0 + tid;
+  const bool rvalid = row < rows;
+  bool isp = false;
+  int er = 0;  // biased exponent of the row's largest entry
+  {
+    long long w[16];
+#pragma unroll
+    for (int t = 0; t < 16; ++t) {
+      w[t] = (rvalid && t < nb) ? __double_as_longlong(M[(long long)row * R + c0 + t]) : 0ll;
+      er = max(er, biased_exp(w[t]));
+    }
+    for (int t = 0; t < nb; ++t) isp = isp || (pphys[t] == row);
+#pragma unroll
+    for (int t = 0; t < 16; ++t) write_digits(w[t], er, sA, TCM * 32, kmaj16(tid, t));
+  }
+  // column digits (Prow, the pivot rows); panel columns and columns past R are zero
+  if (tid < TCN) {
+    const int c = col0 + tid;
+    const bool cvalid = c < R && !(c >= c0 && c < c0 + nb);
+    const double* pb = prow + (long long)blockIdx.y * prow_stride;
+    long long pv[16];
+    int ec = 0;
+#pragma unroll
+    for (int t = 0; t < 16; ++t) {
+      pv[t] = (cvalid && t < nb) ? __double_as_longlong(pb[(long long)t * R + c]) : 0ll;
+      ec = max(ec, biased_exp(pv[t]));
+    }
+    cexp[tid] = ec;
+#pragma unroll
+    for (int t = 0; t < 16; ++t) write_digits(pv[t], ec, sB, TCN * 32, kmaj16(tid, t));
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(256));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("fence.proxy.async.shared::cta;");
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_base;
+  if (tid == 0) {
+    // kind::f16, bf16 x bf16 -> f32, both K-major, N = 32, M = 128
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TCN >> 3) << 17) |
+                           ((uint32_t)(TCM >> 4) << 24);
+    const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+    for (int dg = 2; dg <= TCKEEP; ++dg) {
+      uint32_t acc = 0;
+      for (int sa = 1; sa <= TCS; ++sa) {
+        const int sb = dg - sa;
+        if (sb < 1 || sb > TCS) continue;
+        const uint64_t ad = umma_desc(a0 + (sa - 1) * (TCM * 32), 128, 256);
+        const uint64_t bd = umma_desc(b0 + (sb - 1) * (TCN * 32), 128, 256);
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + (uint32_t)((dg - 2) * TCN)),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+        acc = 1;
+      }
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(&mbar)));
+  }
+  // bounded wait for the products; on a timeout the tile is left alone and reported
+  uint32_t done = 0;
+  for (int it = 0; it < (1 << 22) && !done; ++it) {
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(&mbar)), "r"(0));
+  }
+  // I = sum_d acc_d 2^(8(9-d)) = Ih 2^32 + Il exactly (128-bit), normalised to its top 62
+  // bits T = I >> sh and converted once: the product is T 2^(sh + e_r + f_c - 70) with
+  // e = biased exponent - 1022.  (Dropping a fixed number of low bits instead loses
+  // precision whenever cancellation makes the product small next to max|W_r| max|P_c|.)
+  double vv[TCN];
+#pragma unroll
+  for (int j = 0; j < TCN; ++j) vv[j] = 0.0;
+  if (done) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll
+    for (int jb = 0; jb < TCN; jb += 16) {
+      long long Ih[16], Il[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) Ih[j] = Il[j] = 0;
+#pragma unroll
+      for (int dg = 2; dg <= TCKEEP; ++dg) {
+        uint32_t v[16];
+        const uint32_t addr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)((dg - 2) * TCN + jb);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(addr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const long long a = (long long)__float2int_rz(__uint_as_float(v[j]));  // exact integer
+          // (multiplications: a is signed, and a left shift of a negative value is undefined)
+          if (dg <= 5) Ih[j] += a * (1ll << (8 * (5 - dg)));
+          else Il[j] += a * (1ll << (8 * (9 - dg)));
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const __int128 I = (__int128)Ih[j] * ((__int128)1 << 32) + (__int128)Il[j];
+        if (I == 0) continue;
+        const unsigned __int128 mag = I < 0 ? (unsigned __int128)(-I) : (unsigned __int128)I;
+        const unsigned long long hi = (unsigned long long)(mag >> 64), lo = (unsigned long long)mag;
+        const int bl = hi ? 128 - __clzll((long long)hi) : 64 - __clzll((long long)lo);
+        const int sh = bl > 62 ? bl - 62 : 0;
+        const long long T = (long long)(I >> sh);
+        const long long b = __double_as_longlong(__ll2double_rn(T));
+        const int E = biased_exp(b) + sh + (er - 1022) + (cexp[jb + j] - 1022) - 70;
+        vv[jb + j] = E > 0 ? __longlong_as_double((b & ~(0x7FFll << 52)) | ((long long)E << 52)) : 0.0;
+      }
+    }
+  } else if (lane == 0 && status) {
+    atomicCAS(status, 0, -1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
+  if (!done || !rvalid) return;
+  double* Mr = M + (long long)row * R;
+#pragma unroll
+  for (int j = 0; j < TCN; ++j) {
+    const int c = col0 + j;
+    if (c >= R || (c >= c0 && c < c0 + nb)) continue;
+    Mr[c] = isp ? vv[j] : Mr[c] + vv[j];
+  }
+}
+
 template <typename T, typename TO>
 __global__ void __launch_bounds__(256) gj_extract_kernel(const GJDesc* __restrict__ d,
                                                          const T* __restrict__ work,
@@ -343,11 +579,18 @@ void launch_gj_prep(const GJDesc* d, int nmat, int maxR, T* work, const int* per
 
 template <typename T>
 void launch_gj_update(const GJDesc* d, int nmat, int maxR, int maxRows, T* work, const int* perm, T* prow,
-                      long long prow_stride, int c0, int nb, cudaStream_t s) {
-  // every matrix needs ceil(rows / UBM) x ceil(R / UBN) tiles, which this grid covers
-  const int tiles = (maxR + UBN - 1) / UBN, rtiles = (maxRows + UBM - 1) / UBM;
-  dim3 grid(rtiles * tiles, nmat);
-  gj_update_kernel<T><<<grid, 256, 0, s>>>(d, work, perm, prow, prow_stride, c0, nb);
+                      long long prow_stride, int c0, int nb, cudaStream_t s, int* status) {
+  if constexpr (std::is_same<T, double>::value) {
+    // FP64: the tensor-core kernel; every matrix needs ceil(rows / 128) x ceil(R / 32) tiles
+    const int tiles = (maxR + TCN - 1) / TCN, rtiles = (maxRows + TCM - 1) / TCM;
+    dim3 grid(rtiles * tiles, nmat);
+    gj_update_tc_kernel<<<grid, 128, 0, s>>>(d, work, perm, prow, prow_stride, c0, nb, status);
+  } else {
+    // every matrix needs ceil(rows / UBM) x ceil(R / UBN) tiles, which this grid covers
+    const int tiles = (maxR + UBN - 1) / UBN, rtiles = (maxRows + UBM - 1) / UBM;
+    dim3 grid(rtiles * tiles, nmat);
+    gj_update_kernel<T><<<grid, 256, 0, s>>>(d, work, perm, prow, prow_stride, c0, nb);
+  }
 }
 
 template <typename T, typename TO>
@@ -371,8 +614,8 @@ template void launch_gj_panel<double>(const GJDesc*, int, int, double*, int*, do
 template void launch_gj_panel<float>(const GJDesc*, int, int, float*, int*, float*, int, int, int*, cudaStream_t);
 template void launch_gj_prep<double>(const GJDesc*, int, int, double*, const int*, const double*, double*, long long, int, int, cudaStream_t);
 template void launch_gj_prep<float>(const GJDesc*, int, int, float*, const int*, const float*, float*, long long, int, int, cudaStream_t);
-template void launch_gj_update<double>(const GJDesc*, int, int, int, double*, const int*, double*, long long, int, int, cudaStream_t);
-template void launch_gj_update<float>(const GJDesc*, int, int, int, float*, const int*, float*, long long, int, int, cudaStream_t);
+template void launch_gj_update<double>(const GJDesc*, int, int, int, double*, const int*, double*, long long, int, int, cudaStream_t, int*);
+template void launch_gj_update<float>(const GJDesc*, int, int, int, float*, const int*, float*, long long, int, int, cudaStream_t, int*);
 template void launch_gj_extract<double, double>(const GJDesc*, int, int, const double*, const int*, const ExtractDst&, cudaStream_t);
 template void launch_gj_extract<float, double>(const GJDesc*, int, int, const float*, const int*, const ExtractDst&, cudaStream_t);
 
