@@ -1141,23 +1141,28 @@ std::string validate_plan(const hps_handle* h, const HostPlan& hp) {
 
 long long tstore_elems(const hps_handle* h) { return h->tstore_elems; }
 
-// Panel width: 16 for batches of many matrices; 8 for a level of few large matrices, whose
-// panels run on one CTA each and whose per-panel work grows with nb; capped so the panel
-// fits in shared memory.
+// Panel width: 16 (measured fastest on every level of the 64 x 64-leaf tree with either
+// update path), capped so the panel fits in shared memory.
 int nb_cap(int K, size_t elem) {
   return std::max(1, std::min(16, (int)((200 * 1024) / ((size_t)std::max(K, 1) * (elem + 4)))));
 }
-int choose_nb(int K, size_t elem, int nmat) { return std::min(nmat < 64 ? 8 : 16, nb_cap(K, elem)); }
+int choose_nb(int K, size_t elem, int nmat) {
+  (void)nmat;
+  return nb_cap(K, elem);
+}
 
 // rk: (R, K, rows) of every matrix of the batch, for the grid and the flop counts of the
 // timing records.
 template <typename T>
 void run_gj(const GJDesc* gj, int nmat, int maxR, int maxK, T* work, int* perm, T* pinv, T* prow,
             int* status, const std::vector<std::array<int, 3>>& rk, const char* what, cudaStream_t s,
-            int nb_force = 0) {
+            int cfg = 0) {
   int maxRows = 0;
   for (const auto& m : rk) maxRows = std::max(maxRows, m[2]);
-  const int nb = nb_force > 0 ? std::min(nb_force, nb_cap(maxK, sizeof(T))) : choose_nb(maxK, sizeof(T), nmat);
+  // cfg = panel width + 100 x path (path 1: the FP64 tensor-core update); 0: fixed rules
+  // (the tensor-core update for every FP64 batch: measured fastest on every level)
+  const int nb = cfg % 100 > 0 ? std::min(cfg % 100, nb_cap(maxK, sizeof(T))) : choose_nb(maxK, sizeof(T), nmat);
+  const int tensor = sizeof(T) == 8 && (cfg > 0 ? cfg / 100 : 1);
   const std::string sf = std::string(tsuf<T>()) + ":" + what;
   TIMED(("gj_init_" + sf).c_str(), 0, 0, launch_gj_init<T>(gj, nmat, perm, s));
   CKL();
@@ -1176,15 +1181,16 @@ void run_gj(const GJDesc* gj, int nmat, int maxR, int maxK, T* work, int* perm, 
           launch_gj_panel<T>(gj, nmat, maxK, work, perm, pinv, c0, nb, status, s));
     TIMED(("gj_prep_" + sf).c_str(), fq, 0,
           launch_gj_prep<T>(gj, nmat, maxR, work, perm, pinv, prow, prow_stride, c0, nb, s));
-    TIMED(("gj_update_" + sf).c_str(), fu, bu,
-          launch_gj_update<T>(gj, nmat, maxR, maxRows, work, perm, prow, prow_stride, c0, nb, s, status));
+    TIMED((std::string(tensor ? "gj_update_tc_" : "gj_update_") + sf).c_str(), fu, bu,
+          launch_gj_update<T>(gj, nmat, maxR, maxRows, work, perm, prow, prow_stride, c0, nb, s, status, tensor));
   }
   CKL();
 }
 
-// Panel width of one batched elimination: the fixed rule, or with autotuning the fastest
-// of 4, 8 and 16 (within the shared-memory cap) measured on the batch itself; elim(nb)
-// assembles the batch's matrices and eliminates them with panel width nb.
+// Configuration of one batched elimination (panel width + 100 x update path): the fixed
+// rule, or with autotuning the fastest of panel widths 4, 8 and 16 (within the
+// shared-memory cap), each with the SIMT and, for FP64, the tensor-core update, measured on
+// the batch itself; elim(cfg) assembles the batch's matrices and eliminates them.
 int pick_nb(const hps_handle* h, const char* what, size_t elem, const std::vector<std::array<int, 3>>& rk,
             int nmat, cudaStream_t s, const std::function<void(int)>& elim) {
   int maxR = 0, maxK = 0, maxRows = 0;
@@ -1193,13 +1199,15 @@ int pick_nb(const hps_handle* h, const char* what, size_t elem, const std::vecto
     maxK = std::max(maxK, m[1]);
     maxRows = std::max(maxRows, m[2]);
   }
-  const int def = choose_nb(maxK, elem, nmat);
-  if (!h->opts.autotune) return def;
+  if (!h->opts.autotune) return 0;  // fixed rules inside run_gj
   std::vector<int> cands;
   for (int nb : {4, 8, 16})
-    if (nb <= nb_cap(maxK, elem)) cands.push_back(nb);
-  if (cands.empty()) return def;
-  const std::string key = std::string("gj_nb ") + what + " e" + std::to_string(elem) + " n" + std::to_string(nmat) +
+    if (nb <= nb_cap(maxK, elem)) {
+      cands.push_back(nb);
+      if (elem == 8) cands.push_back(100 + nb);
+    }
+  if (cands.empty()) return 0;
+  const std::string key = std::string("gj_cfg ") + what + " e" + std::to_string(elem) + " n" + std::to_string(nmat) +
                           " R" + std::to_string(maxR) + " K" + std::to_string(maxK) + " rows" + std::to_string(maxRows);
   return tuned_choice(key, cands, h->tune_path, [&](int nb) { return time_on_stream(s, [&] { elim(nb); }); });
 }

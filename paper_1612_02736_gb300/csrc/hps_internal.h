@@ -153,8 +153,10 @@ template <typename T>
 void launch_gj_prep(const GJDesc* d, int nmat, int maxR, T* work, const int* perm, const T* pinv,
                     T* prow, long long prow_stride, int c0, int nb, cudaStream_t s);
 template <typename T>
+// tensor = 1 (FP64 only): the tcgen05 kernel with exact digit slicing, else the FP64 / FP32
+// register-tiled SIMT kernel.
 void launch_gj_update(const GJDesc* d, int nmat, int maxR, int maxRows, T* work, const int* perm, T* prow,
-                      long long prow_stride, int c0, int nb, cudaStream_t s, int* status);
+                      long long prow_stride, int c0, int nb, cudaStream_t s, int* status, int tensor);
 
 // Extraction of a finished elimination: with sigma the logical->physical row map,
 //   TL[i][j] = sTL * M[sigma(i)][sigma^-1(j)]   (i, j < K)

@@ -356,8 +356,13 @@ __global__ void __launch_bounds__(128) gj_update_tc_kernel(const GJDesc* __restr
   const int row0 = tm * TCM, col0 = tn * TCN;
   if (row0 >= rows) return;
   if (col0 >= c0 && col0 + TCN <= c0 + nb) return;  // tile entirely inside the panel
-  __shared__ __align__(1024) unsigned char sA[TCS * TCM * 16 * 2];  // 8 planes x 4 KB
-  __shared__ __align__(1024) unsigned char sB[TCS * TCN * 16 * 2];  // 8 planes x 1 KB
+  // One 40 KB buffer, three uses in turn: the tile's W rows (loaded coalesced, row stride
+  // 17 doubles), then the digit planes (8 x 4 KB for W, 8 x 1 KB for Prow), then the
+  // 128 x 32 result (row stride 33 doubles: conflict-free column reads).
+  __shared__ __align__(1024) unsigned char sA[TCS * TCM * 16 * 2 + TCS * TCN * 16 * 2];
+  unsigned char* sB = sA + TCS * TCM * 16 * 2;
+  double (*sW)[17] = reinterpret_cast<double (*)[17]>(sA);
+  __shared__ unsigned char sisp[TCM];
   __shared__ int cexp[TCN];
   __shared__ int pphys[16];
   __shared__ uint32_t tmem_base;
@@ -370,35 +375,44 @@ __global__ void __launch_bounds__(128) gj_update_tc_kernel(const GJDesc* __restr
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   __syncthreads();
-  // row digits (W = the final panel columns of this row)
-  const int row = row0 + tid;
-  const bool rvalid = row < rows;
-  bool isp = false;
-  int er = 0;  // biased exponent of the row's largest entry
-  {
-    long long w[16];
-#pragma unroll
-    for (int t = 0; t < 16; ++t) {
-      w[t] = (rvalid && t < nb) ? __double_as_longlong(M[(long long)row * R + c0 + t]) : 0ll;
-      er = max(er, biased_exp(w[t]));
-    }
-    for (int t = 0; t < nb; ++t) isp = isp || (pphys[t] == row);
-#pragma unroll
-    for (int t = 0; t < 16; ++t) write_digits(w[t], er, sA, TCM * 32, kmaj16(tid, t));
-  }
-  // column digits (Prow, the pivot rows); panel columns and columns past R are zero
+  // Prow columns (the pivot rows; panel columns and columns past R are zero), loaded first
+  // so that they are in flight together with the W tile
+  long long w[16], pv[16];
   if (tid < TCN) {
     const int c = col0 + tid;
     const bool cvalid = c < R && !(c >= c0 && c < c0 + nb);
     const double* pb = prow + (long long)blockIdx.y * prow_stride;
-    long long pv[16];
-    int ec = 0;
 #pragma unroll
-    for (int t = 0; t < 16; ++t) {
-      pv[t] = (cvalid && t < nb) ? __double_as_longlong(pb[(long long)t * R + c]) : 0ll;
-      ec = max(ec, biased_exp(pv[t]));
-    }
+    for (int t = 0; t < 16; ++t) pv[t] = (cvalid && t < nb) ? __double_as_longlong(pb[(long long)t * R + c]) : 0ll;
+  }
+  // W tile (the final panel columns of 128 rows), 16 consecutive threads per row
+  for (int e = tid; e < TCM * 16; e += 128) {
+    const int r = e >> 4, t = e & 15, rr = row0 + r;
+    sW[r][t] = (rr < rows && t < nb) ? M[(long long)rr * R + c0 + t] : 0.0;
+  }
+  __syncthreads();
+  // row digits
+  const int row = row0 + tid;
+  const bool rvalid = row < rows;
+  bool isp = false;
+  int er = 0;  // biased exponent of the row's largest entry
+#pragma unroll
+  for (int t = 0; t < 16; ++t) {
+    w[t] = __double_as_longlong(sW[tid][t]);
+    er = max(er, biased_exp(w[t]));
+  }
+  for (int t = 0; t < nb; ++t) isp = isp || (pphys[t] == row);
+  sisp[tid] = isp ? 1 : 0;
+  int ec = 0;
+  if (tid < TCN) {
+#pragma unroll
+    for (int t = 0; t < 16; ++t) ec = max(ec, biased_exp(pv[t]));
     cexp[tid] = ec;
+  }
+  __syncthreads();  // every row is in registers: the buffer now takes the digit planes
+#pragma unroll
+  for (int t = 0; t < 16; ++t) write_digits(w[t], er, sA, TCM * 32, kmaj16(tid, t));
+  if (tid < TCN) {
 #pragma unroll
     for (int t = 0; t < 16; ++t) write_digits(pv[t], ec, sB, TCN * 32, kmaj16(tid, t));
   }
@@ -441,6 +455,7 @@ __global__ void __launch_bounds__(128) gj_update_tc_kernel(const GJDesc* __restr
         : "=r"(done)
         : "r"(smem_u32(&mbar)), "r"(0));
   }
+  done = __syncthreads_and(done);  // one verdict for the whole tile
   // I = sum_d acc_d 2^(8(9-d)) = Ih 2^32 + Il exactly (128-bit), normalised to its top 62
   // bits T = I >> sh and converted once: the product is T 2^(sh + e_r + f_c - 70) with
   // e = biased exponent - 1022.  (Dropping a fixed number of low bits instead loses
@@ -487,19 +502,32 @@ __global__ void __launch_bounds__(128) gj_update_tc_kernel(const GJDesc* __restr
         vv[jb + j] = E > 0 ? __longlong_as_double((b & ~(0x7FFll << 52)) | ((long long)E << 52)) : 0.0;
       }
     }
-  } else if (lane == 0 && status) {
+  } else if (tid == 0 && status) {
     atomicCAS(status, 0, -1);
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
-  if (!done || !rvalid) return;
-  double* Mr = M + (long long)row * R;
+  if (!done) return;  // uniform (one verdict per tile)
+  // stage the products, then update M with one row of 32 consecutive columns per warp
+  // instruction (coalesced)
+  double* st = reinterpret_cast<double*>(sA);
 #pragma unroll
-  for (int j = 0; j < TCN; ++j) {
-    const int c = col0 + j;
-    if (c >= R || (c >= c0 && c < c0 + nb)) continue;
-    Mr[c] = isp ? vv[j] : Mr[c] + vv[j];
+  for (int j = 0; j < TCN; ++j) st[tid * (TCN + 1) + j] = vv[j];
+  __syncthreads();
+  const int c = col0 + lane;
+  const bool cok = c < R && !(c >= c0 && c < c0 + nb);
+  // all 32 loads of this lane first (independent, in flight together), then the updates
+  double cv[TCM / 4];
+#pragma unroll
+  for (int k = 0; k < TCM / 4; ++k) {
+    const int r = warp + 4 * k, rr = row0 + r;
+    cv[k] = (cok && rr < rows && !sisp[r]) ? M[(long long)rr * R + c] : 0.0;
+  }
+#pragma unroll
+  for (int k = 0; k < TCM / 4; ++k) {
+    const int r = warp + 4 * k, rr = row0 + r;
+    if (cok && rr < rows) M[(long long)rr * R + c] = cv[k] + st[r * (TCN + 1) + lane];
   }
 }
 
@@ -579,12 +607,13 @@ void launch_gj_prep(const GJDesc* d, int nmat, int maxR, T* work, const int* per
 
 template <typename T>
 void launch_gj_update(const GJDesc* d, int nmat, int maxR, int maxRows, T* work, const int* perm, T* prow,
-                      long long prow_stride, int c0, int nb, cudaStream_t s, int* status) {
-  if constexpr (std::is_same<T, double>::value) {
+                      long long prow_stride, int c0, int nb, cudaStream_t s, int* status, int tensor) {
+  if (std::is_same<T, double>::value && tensor) {
     // FP64: the tensor-core kernel; every matrix needs ceil(rows / 128) x ceil(R / 32) tiles
     const int tiles = (maxR + TCN - 1) / TCN, rtiles = (maxRows + TCM - 1) / TCM;
     dim3 grid(rtiles * tiles, nmat);
-    gj_update_tc_kernel<<<grid, 128, 0, s>>>(d, work, perm, prow, prow_stride, c0, nb, status);
+    gj_update_tc_kernel<<<grid, 128, 0, s>>>(d, (double*)work, perm, (const double*)prow, prow_stride, c0, nb,
+                                              status);
   } else {
     // every matrix needs ceil(rows / UBM) x ceil(R / UBN) tiles, which this grid covers
     const int tiles = (maxR + UBN - 1) / UBN, rtiles = (maxRows + UBM - 1) / UBM;
@@ -614,8 +643,8 @@ template void launch_gj_panel<double>(const GJDesc*, int, int, double*, int*, do
 template void launch_gj_panel<float>(const GJDesc*, int, int, float*, int*, float*, int, int, int*, cudaStream_t);
 template void launch_gj_prep<double>(const GJDesc*, int, int, double*, const int*, const double*, double*, long long, int, int, cudaStream_t);
 template void launch_gj_prep<float>(const GJDesc*, int, int, float*, const int*, const float*, float*, long long, int, int, cudaStream_t);
-template void launch_gj_update<double>(const GJDesc*, int, int, int, double*, const int*, double*, long long, int, int, cudaStream_t, int*);
-template void launch_gj_update<float>(const GJDesc*, int, int, int, float*, const int*, float*, long long, int, int, cudaStream_t, int*);
+template void launch_gj_update<double>(const GJDesc*, int, int, int, double*, const int*, double*, long long, int, int, cudaStream_t, int*, int);
+template void launch_gj_update<float>(const GJDesc*, int, int, int, float*, const int*, float*, long long, int, int, cudaStream_t, int*, int);
 template void launch_gj_extract<double, double>(const GJDesc*, int, int, const double*, const int*, const ExtractDst&, cudaStream_t);
 template void launch_gj_extract<float, double>(const GJDesc*, int, int, const float*, const int*, const ExtractDst&, cudaStream_t);
 
