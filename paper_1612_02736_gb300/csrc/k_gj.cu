@@ -20,6 +20,7 @@
 //               replaced by Pinv Prow).
 // FP64 on GB300 runs on the FFMA pipe (no FP64 tensor path is faster on this part), so
 // the update is a register-tiled SIMT product.
+#include <algorithm>
 #include <cfloat>
 #include <cstdint>
 #include <cstdio>
@@ -290,9 +291,9 @@ __global__ void __launch_bounds__(256) gj_update_kernel(const GJDesc* __restrict
 // which 7 digits (2^-56) did not absorb and 8 digits do.  The kernel is then bound by
 // the read and write of the updated matrix (HBM), not by arithmetic.
 //
-// Tile: 128 rows x 32 columns, 128 threads (thread r owns row r for the digits and the
-// epilogue); operands in shared memory in the canonical K-major no-swizzle layout (8-row x
-// 16-byte core matrices, LBO 128 bytes along K, SBO 256 bytes between row groups).
+// Tile: 128 rows x 32 columns (MMA M = 128, N = 32, K = 16); operands in shared memory in
+// the canonical K-major no-swizzle layout (8-row x 16-byte core matrices, LBO 128 bytes
+// along K, SBO 256 bytes between row groups).
 constexpr int TCM = 128, TCN = 32, TCS = 8, TCKEEP = 9, TCNACC = TCKEEP - 1;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -343,137 +344,220 @@ __device__ __forceinline__ void write_digits(long long bits, int emax, unsigned 
   }
 }
 
-__global__ void __launch_bounds__(128) gj_update_tc_kernel(const GJDesc* __restrict__ d, double* __restrict__ work,
-                                                          const int* __restrict__ perm,
-                                                          const double* __restrict__ prow, long long prow_stride,
-                                                          int c0, int nb_req, int* __restrict__ status) {
-  const GJDesc md = d[blockIdx.y];
-  if (c0 >= md.K) return;
-  const int nb = min(nb_req, md.K - c0);
-  const int R = md.R, rows = md.rows;
-  const int tiles = (R + TCN - 1) / TCN;
-  const int tm = blockIdx.x / tiles, tn = blockIdx.x - (blockIdx.x / tiles) * tiles;
-  const int row0 = tm * TCM, col0 = tn * TCN;
-  if (row0 >= rows) return;
-  if (col0 >= c0 && col0 + TCN <= c0 + nb) return;  // tile entirely inside the panel
-  // One 40 KB buffer, three uses in turn: the tile's W rows (loaded coalesced, row stride
-  // 17 doubles), then the digit planes (8 x 4 KB for W, 8 x 1 KB for Prow), then the
-  // 128 x 32 result (row stride 33 doubles: conflict-free column reads).
-  __shared__ __align__(1024) unsigned char sA[TCS * TCM * 16 * 2 + TCS * TCN * 16 * 2];
-  unsigned char* sB = sA + TCS * TCM * 16 * 2;
-  double (*sW)[17] = reinterpret_cast<double (*)[17]>(sA);
-  __shared__ unsigned char sisp[TCM];
-  __shared__ int cexp[TCN];
-  __shared__ int pphys[16];
-  __shared__ uint32_t tmem_base;
-  __shared__ __align__(8) uint64_t mbar;
+// ---------------------------------------------------------------------------------------
+// Persistent, warp-specialised form of the tensor-core update.  One CTA per SM loops over
+// the launch's tiles (tile t = blockIdx.x + k gridDim.x), and three roles work on three
+// tiles at once:
+//   warps 0-3  (producers): load the tile's W rows and pivot-row columns, write their
+//              digit planes and scales into buffer k % 2;
+//   warp 4     (one thread): issue the 36 digit-pair products of tile k into TMEM buffer
+//              k % 2 and commit them to an mbarrier;
+//   warps 8-15 (epilogue): read TMEM (warp w reads lanes 32 (w % 4) ..., columns
+//              16 ((w - 8) / 4) ...), recombine, update the matrix through a staging
+//              buffer (coalesced).
+// Handoffs use mbarriers per buffer: full (producers -> MMA), done (MMA -> epilogue),
+// free (epilogue -> producers).  One elected thread per role waits, with an iteration
+// limit, and broadcasts the verdict over the role's named barrier; a timeout stops every
+// role (abort flag) and is reported as status -1.
+constexpr int PT_THREADS = 512;
+constexpr int PT_EPI = 256;  // epilogue threads: 2 per tile row, 16 columns each
+constexpr int PT_PLANES = TCS * TCM * 16 * 2 + TCS * TCN * 16 * 2;  // 40 KB per buffer
+constexpr long long PT_WAIT = 1ll << 26;
+
+struct PtShared {
+  unsigned char planes[2][PT_PLANES];
+  double sW[TCM][17];            // producers: the W tile, loaded coalesced
+  double stg[TCM][TCN + 1];      // epilogue: the products, stored coalesced
+  int er[2][TCM];
+  int cexp[2][TCN];
+  unsigned char isp[2][TCM];
+  unsigned long long full[2], done[2], freeb[2];
+  unsigned int tmem_base;
+  int abort_flag;
+  int ok_prod, ok_epi;
+};
+
+__device__ __forceinline__ void mb_init(unsigned long long* b, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count));
+}
+__device__ __forceinline__ void mb_arrive(unsigned long long* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+// bounded wait for the phase with the given parity; false on timeout or abort
+__device__ __forceinline__ bool mb_wait(unsigned long long* b, int parity, volatile int* abort_flag, int* status) {
+  for (long long it = 0; it < PT_WAIT; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if ((it & 255) == 255 && *abort_flag) return false;
+  }
+  *abort_flag = 1;
+  if (status) atomicCAS(status, 0, -1);
+  return false;
+}
+__device__ __forceinline__ void named_bar(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+__global__ void __launch_bounds__(PT_THREADS, 1) gj_update_tcp_kernel(
+    const GJDesc* __restrict__ d, int nmat, int rtmax, int ctmax, double* __restrict__ work,
+    const int* __restrict__ perm, const double* __restrict__ prow, long long prow_stride, int c0, int nb_req,
+    int* __restrict__ status) {
+  extern __shared__ __align__(1024) unsigned char pt_raw[];
+  PtShared& sh = *reinterpret_cast<PtShared*>(pt_raw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  double* M = work + md.off;
-  if (tid < nb) pphys[tid] = perm[md.perm_off + c0 + tid];
+  const long long tpm = (long long)rtmax * ctmax, total = (long long)nmat * tpm;
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+    for (int b = 0; b < 2; ++b) {
+      mb_init(&sh.full[b], TCM);
+      mb_init(&sh.done[b], 1);
+      mb_init(&sh.freeb[b], PT_EPI);
+    }
+    sh.abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
-  __syncthreads();
-  // Prow columns (the pivot rows; panel columns and columns past R are zero), loaded first
-  // so that they are in flight together with the W tile
-  long long w[16], pv[16];
-  if (tid < TCN) {
-    const int c = col0 + tid;
-    const bool cvalid = c < R && !(c >= c0 && c < c0 + nb);
-    const double* pb = prow + (long long)blockIdx.y * prow_stride;
-#pragma unroll
-    for (int t = 0; t < 16; ++t) pv[t] = (cvalid && t < nb) ? __double_as_longlong(pb[(long long)t * R + c]) : 0ll;
-  }
-  // W tile (the final panel columns of 128 rows), 16 consecutive threads per row
-  for (int e = tid; e < TCM * 16; e += 128) {
-    const int r = e >> 4, t = e & 15, rr = row0 + r;
-    sW[r][t] = (rr < rows && t < nb) ? M[(long long)rr * R + c0 + t] : 0.0;
-  }
-  __syncthreads();
-  // row digits
-  const int row = row0 + tid;
-  const bool rvalid = row < rows;
-  bool isp = false;
-  int er = 0;  // biased exponent of the row's largest entry
-#pragma unroll
-  for (int t = 0; t < 16; ++t) {
-    w[t] = __double_as_longlong(sW[tid][t]);
-    er = max(er, biased_exp(w[t]));
-  }
-  for (int t = 0; t < nb; ++t) isp = isp || (pphys[t] == row);
-  sisp[tid] = isp ? 1 : 0;
-  int ec = 0;
-  if (tid < TCN) {
-#pragma unroll
-    for (int t = 0; t < 16; ++t) ec = max(ec, biased_exp(pv[t]));
-    cexp[tid] = ec;
-  }
-  __syncthreads();  // every row is in registers: the buffer now takes the digit planes
-#pragma unroll
-  for (int t = 0; t < 16; ++t) write_digits(w[t], er, sA, TCM * 32, kmaj16(tid, t));
-  if (tid < TCN) {
-#pragma unroll
-    for (int t = 0; t < 16; ++t) write_digits(pv[t], ec, sB, TCN * 32, kmaj16(tid, t));
-  }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
-                 "r"(256));
+  if (warp == 4) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh.tmem_base)),
+                 "r"(512));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  asm volatile("fence.proxy.async.shared::cta;");
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
-  const uint32_t tmem = tmem_base;
-  if (tid == 0) {
-    // kind::f16, bf16 x bf16 -> f32, both K-major, N = 32, M = 128
-    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TCN >> 3) << 17) |
-                           ((uint32_t)(TCM >> 4) << 24);
-    const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
-    for (int dg = 2; dg <= TCKEEP; ++dg) {
-      uint32_t acc = 0;
-      for (int sa = 1; sa <= TCS; ++sa) {
-        const int sb = dg - sa;
-        if (sb < 1 || sb > TCS) continue;
-        const uint64_t ad = umma_desc(a0 + (sa - 1) * (TCM * 32), 128, 256);
-        const uint64_t bd = umma_desc(b0 + (sb - 1) * (TCN * 32), 128, 256);
-        asm volatile(
-            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + (uint32_t)((dg - 2) * TCN)),
-            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-        acc = 1;
+  const uint32_t tmem = sh.tmem_base;
+  volatile int* abort_flag = &sh.abort_flag;
+  // tile decoding, identical in every role
+  auto decode = [&](long long t, GJDesc& md, int& nb, int& row0, int& col0) -> bool {
+    const int m = (int)(t / tpm);
+    const int local = (int)(t - (long long)m * tpm);
+    md = d[m];
+    if (c0 >= md.K) return false;
+    nb = min(nb_req, md.K - c0);
+    row0 = (local / ctmax) * TCM;
+    col0 = (local % ctmax) * TCN;
+    if (row0 >= md.rows || col0 >= md.R) return false;
+    if (col0 >= c0 && col0 + TCN <= c0 + nb) return false;
+    return true;
+  };
+  if (warp < 4) {
+    // ---------------- producers
+    const int i = tid;  // row of the tile
+    int k = 0;
+    for (long long t = blockIdx.x; t < total; t += gridDim.x) {
+      GJDesc md;
+      int nb, row0, col0;
+      if (!decode(t, md, nb, row0, col0)) continue;
+      const int buf = k & 1;
+      if (k >= 2) {
+        if (i == 0) sh.ok_prod = mb_wait(&sh.freeb[buf], ((k >> 1) - 1) & 1, abort_flag, status) ? 1 : 0;
+        named_bar(1, TCM);
+        if (!sh.ok_prod) break;
+      }
+      const int R = md.R, rows = md.rows;
+      const double* M = work + md.off;
+      long long pv[16];
+      if (i < TCN) {
+        const int c = col0 + i;
+        const bool cvalid = c < R && !(c >= c0 && c < c0 + nb);
+        const double* pb = prow + (long long)(t / tpm) * prow_stride;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) pv[q] = (cvalid && q < nb) ? __double_as_longlong(pb[(long long)q * R + c]) : 0ll;
+      }
+      for (int e = i; e < TCM * 16; e += TCM) {
+        const int r = e >> 4, q = e & 15, rr = row0 + r;
+        sh.sW[r][q] = (rr < rows && q < nb) ? M[(long long)rr * R + c0 + q] : 0.0;
+      }
+      named_bar(1, TCM);
+      const int row = row0 + i;
+      int er = 0;
+      long long w[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        w[q] = __double_as_longlong(sh.sW[i][q]);
+        er = max(er, biased_exp(w[q]));
+      }
+      bool isp = false;
+      for (int q = 0; q < nb; ++q) isp = isp || (perm[md.perm_off + c0 + q] == row);
+      sh.er[buf][i] = er;
+      sh.isp[buf][i] = (row < rows && isp) ? 1 : 0;
+      unsigned char* A = sh.planes[buf];
+      unsigned char* B = A + TCS * TCM * 32;
+#pragma unroll
+      for (int q = 0; q < 16; ++q) write_digits(w[q], er, A, TCM * 32, kmaj16(i, q));
+      if (i < TCN) {
+        int ec = 0;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) ec = max(ec, biased_exp(pv[q]));
+        sh.cexp[buf][i] = ec;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) write_digits(pv[q], ec, B, TCN * 32, kmaj16(i, q));
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mb_arrive(&sh.full[buf]);
+      named_bar(1, TCM);  // sW is reused by the next tile
+      ++k;
+    }
+  } else if (warp == 4) {
+    // ---------------- MMA issue (one thread)
+    if (lane == 0) {
+      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TCN >> 3) << 17) |
+                             ((uint32_t)(TCM >> 4) << 24);
+      int k = 0;
+      for (long long t = blockIdx.x; t < total; t += gridDim.x) {
+        GJDesc md;
+        int nb, row0, col0;
+        if (!decode(t, md, nb, row0, col0)) continue;
+        const int buf = k & 1;
+        if (!mb_wait(&sh.full[buf], (k >> 1) & 1, abort_flag, status)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t a0 = smem_u32(sh.planes[buf]), b0 = a0 + TCS * TCM * 32;
+        const uint32_t tb = tmem + (uint32_t)(buf * 256);
+        for (int dg = 2; dg <= TCKEEP; ++dg) {
+          uint32_t acc = 0;
+          for (int sa = 1; sa <= TCS; ++sa) {
+            const int sb = dg - sa;
+            if (sb < 1 || sb > TCS) continue;
+            const uint64_t ad = umma_desc(a0 + (sa - 1) * (TCM * 32), 128, 256);
+            const uint64_t bd = umma_desc(b0 + (sb - 1) * (TCN * 32), 128, 256);
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tb + (uint32_t)((dg - 2) * TCN)),
+                "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+            acc = 1;
+          }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(&sh.done[buf])));
+        ++k;
       }
     }
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(&mbar)));
-  }
-  // bounded wait for the products; on a timeout the tile is left alone and reported
-  uint32_t done = 0;
-  for (int it = 0; it < (1 << 22) && !done; ++it) {
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(smem_u32(&mbar)), "r"(0));
-  }
-  done = __syncthreads_and(done);  // one verdict for the whole tile
-  // I = sum_d acc_d 2^(8(9-d)) = Ih 2^32 + Il exactly (128-bit), normalised to its top 62
-  // bits T = I >> sh and converted once: the product is T 2^(sh + e_r + f_c - 70) with
-  // e = biased exponent - 1022.  (Dropping a fixed number of low bits instead loses
-  // precision whenever cancellation makes the product small next to max|W_r| max|P_c|.)
-  double vv[TCN];
-#pragma unroll
-  for (int j = 0; j < TCN; ++j) vv[j] = 0.0;
-  if (done) {
-    asm volatile("tcgen05.fence::after_thread_sync;");
-#pragma unroll
-    for (int jb = 0; jb < TCN; jb += 16) {
+  } else if (warp >= 8) {
+    // ---------------- epilogue: thread (half h, row e) takes columns 16 h .. 16 h + 15
+    const int te = tid - 256, ew = warp & 3, h = (warp - 8) >> 2;
+    const int e = ew * 32 + lane;  // row of the tile = TMEM lane
+    int k = 0;
+    for (long long t = blockIdx.x; t < total; t += gridDim.x) {
+      GJDesc md;
+      int nb, row0, col0;
+      if (!decode(t, md, nb, row0, col0)) continue;
+      const int buf = k & 1;
+      if (te == 0) sh.ok_epi = mb_wait(&sh.done[buf], (k >> 1) & 1, abort_flag, status) ? 1 : 0;
+      named_bar(2, PT_EPI);
+      if (!sh.ok_epi) break;
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const int er = sh.er[buf][e];
+      const int jb = 16 * h;
       long long Ih[16], Il[16];
 #pragma unroll
       for (int j = 0; j < 16; ++j) Ih[j] = Il[j] = 0;
 #pragma unroll
       for (int dg = 2; dg <= TCKEEP; ++dg) {
         uint32_t v[16];
-        const uint32_t addr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)((dg - 2) * TCN + jb);
+        const uint32_t addr = tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)(buf * 256 + (dg - 2) * TCN + jb);
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
             : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
@@ -482,53 +566,56 @@ __global__ void __launch_bounds__(128) gj_update_tc_kernel(const GJDesc* __restr
         asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-          const long long a = (long long)__float2int_rz(__uint_as_float(v[j]));  // exact integer
-          // (multiplications: a is signed, and a left shift of a negative value is undefined)
+          const long long a = (long long)__float2int_rz(__uint_as_float(v[j]));
           if (dg <= 5) Ih[j] += a * (1ll << (8 * (5 - dg)));
           else Il[j] += a * (1ll << (8 * (9 - dg)));
         }
       }
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
+        double vv = 0.0;
         const __int128 I = (__int128)Ih[j] * ((__int128)1 << 32) + (__int128)Il[j];
-        if (I == 0) continue;
-        const unsigned __int128 mag = I < 0 ? (unsigned __int128)(-I) : (unsigned __int128)I;
-        const unsigned long long hi = (unsigned long long)(mag >> 64), lo = (unsigned long long)mag;
-        const int bl = hi ? 128 - __clzll((long long)hi) : 64 - __clzll((long long)lo);
-        const int sh = bl > 62 ? bl - 62 : 0;
-        const long long T = (long long)(I >> sh);
-        const long long b = __double_as_longlong(__ll2double_rn(T));
-        const int E = biased_exp(b) + sh + (er - 1022) + (cexp[jb + j] - 1022) - 70;
-        vv[jb + j] = E > 0 ? __longlong_as_double((b & ~(0x7FFll << 52)) | ((long long)E << 52)) : 0.0;
+        if (I != 0) {
+          const unsigned __int128 mag = I < 0 ? (unsigned __int128)(-I) : (unsigned __int128)I;
+          const unsigned long long hi = (unsigned long long)(mag >> 64), lo = (unsigned long long)mag;
+          const int bl = hi ? 128 - __clzll((long long)hi) : 64 - __clzll((long long)lo);
+          const int shf = bl > 62 ? bl - 62 : 0;
+          const long long T = (long long)(I >> shf);
+          const long long b = __double_as_longlong(__ll2double_rn(T));
+          const int E = biased_exp(b) + shf + (er - 1022) + (sh.cexp[buf][jb + j] - 1022) - 70;
+          vv = E > 0 ? __longlong_as_double((b & ~(0x7FFll << 52)) | ((long long)E << 52)) : 0.0;
+        }
+        sh.stg[e][jb + j] = vv;
       }
+      __shared__ unsigned char isp_row[TCM];
+      if (h == 0) isp_row[e] = sh.isp[buf][e];
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      mb_arrive(&sh.freeb[buf]);  // TMEM and buffer metadata read: producers may refill
+      named_bar(2, PT_EPI);
+      // coalesced update: epilogue warp q = te / 32 takes rows q, q + 8, ...; lane = column
+      const int R = md.R, rows = md.rows, wq = te >> 5;
+      double* M = work + md.off;
+      const int c = col0 + lane;
+      const bool cok = c < R && !(c >= c0 && c < c0 + nb);
+      double cv[TCM / 8];
+#pragma unroll
+      for (int q = 0; q < TCM / 8; ++q) {
+        const int r = wq + 8 * q, rr = row0 + r;
+        cv[q] = (cok && rr < rows && !isp_row[r]) ? M[(long long)rr * R + c] : 0.0;
+      }
+#pragma unroll
+      for (int q = 0; q < TCM / 8; ++q) {
+        const int r = wq + 8 * q, rr = row0 + r;
+        if (cok && rr < rows) M[(long long)rr * R + c] = cv[q] + sh.stg[r][lane];
+      }
+      named_bar(2, PT_EPI);  // stg and isp_row are reused by the next tile
+      ++k;
     }
-  } else if (tid == 0 && status) {
-    atomicCAS(status, 0, -1);
   }
+  // warps 5-7 have no role
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
-  if (!done) return;  // uniform (one verdict per tile)
-  // stage the products, then update M with one row of 32 consecutive columns per warp
-  // instruction (coalesced)
-  double* st = reinterpret_cast<double*>(sA);
-#pragma unroll
-  for (int j = 0; j < TCN; ++j) st[tid * (TCN + 1) + j] = vv[j];
-  __syncthreads();
-  const int c = col0 + lane;
-  const bool cok = c < R && !(c >= c0 && c < c0 + nb);
-  // all 32 loads of this lane first (independent, in flight together), then the updates
-  double cv[TCM / 4];
-#pragma unroll
-  for (int k = 0; k < TCM / 4; ++k) {
-    const int r = warp + 4 * k, rr = row0 + r;
-    cv[k] = (cok && rr < rows && !sisp[r]) ? M[(long long)rr * R + c] : 0.0;
-  }
-#pragma unroll
-  for (int k = 0; k < TCM / 4; ++k) {
-    const int r = warp + 4 * k, rr = row0 + r;
-    if (cok && rr < rows) M[(long long)rr * R + c] = cv[k] + st[r * (TCN + 1) + lane];
-  }
+  if (warp == 4) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
 }
 
 template <typename T, typename TO>
@@ -609,11 +696,21 @@ template <typename T>
 void launch_gj_update(const GJDesc* d, int nmat, int maxR, int maxRows, T* work, const int* perm, T* prow,
                       long long prow_stride, int c0, int nb, cudaStream_t s, int* status, int tensor) {
   if (std::is_same<T, double>::value && tensor) {
-    // FP64: the tensor-core kernel; every matrix needs ceil(rows / 128) x ceil(R / 32) tiles
-    const int tiles = (maxR + TCN - 1) / TCN, rtiles = (maxRows + TCM - 1) / TCM;
-    dim3 grid(rtiles * tiles, nmat);
-    gj_update_tc_kernel<<<grid, 128, 0, s>>>(d, (double*)work, perm, (const double*)prow, prow_stride, c0, nb,
-                                              status);
+    // FP64: the persistent tensor-core kernel, one CTA per SM over ceil(rows / 128) x
+    // ceil(R / 32) tiles of every matrix
+    static int nsm = 0;
+    if (!nsm) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+      cudaFuncSetAttribute(gj_update_tcp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PtShared));
+      if (nsm <= 0) nsm = 1;
+    }
+    const int ctmax = (maxR + TCN - 1) / TCN, rtmax = (maxRows + TCM - 1) / TCM;
+    const long long total = (long long)nmat * ctmax * rtmax;
+    const int grid = (int)std::min<long long>(nsm, total);
+    gj_update_tcp_kernel<<<grid, PT_THREADS, sizeof(PtShared), s>>>(d, nmat, rtmax, ctmax, (double*)work, perm,
+                                                                    (const double*)prow, prow_stride, c0, nb, status);
   } else {
     // every matrix needs ceil(rows / UBM) x ceil(R / UBN) tiles, which this grid covers
     const int tiles = (maxR + UBN - 1) / UBN, rtiles = (maxRows + UBM - 1) / UBM;
