@@ -294,7 +294,7 @@ __global__ void __launch_bounds__(256) gj_update_kernel(const GJDesc* __restrict
 // Tile: 128 rows x 32 columns (MMA M = 128, N = 32, K = 16); operands in shared memory in
 // the canonical K-major no-swizzle layout (8-row x 16-byte core matrices, LBO 128 bytes
 // along K, SBO 256 bytes between row groups).
-constexpr int TCM = 128, TCN = 32, TCS = 8, TCKEEP = 9, TCNACC = TCKEEP - 1;
+constexpr int TCM = 128, TCN = 32, TCS = 8, TCKEEP = 9;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
