@@ -375,6 +375,7 @@ struct PtShared {
   unsigned int tmem_base;
   int abort_flag;
   int ok_prod, ok_epi;
+  int pphys[16];
 };
 
 __device__ __forceinline__ void mb_init(unsigned long long* b, int count) {
@@ -452,11 +453,6 @@ __global__ void __launch_bounds__(PT_THREADS, 1) gj_update_tcp_kernel(
       int nb, row0, col0;
       if (!decode(t, md, nb, row0, col0)) continue;
       const int buf = k & 1;
-      if (k >= 2) {
-        if (i == 0) sh.ok_prod = mb_wait(&sh.freeb[buf], ((k >> 1) - 1) & 1, abort_flag, status) ? 1 : 0;
-        named_bar(1, TCM);
-        if (!sh.ok_prod) break;
-      }
       const int R = md.R, rows = md.rows;
       const double* M = work + md.off;
       long long pv[16];
@@ -471,7 +467,11 @@ __global__ void __launch_bounds__(PT_THREADS, 1) gj_update_tcp_kernel(
         const int r = e >> 4, q = e & 15, rr = row0 + r;
         sh.sW[r][q] = (rr < rows && q < nb) ? M[(long long)rr * R + c0 + q] : 0.0;
       }
+      if (i < 16) sh.pphys[i] = i < nb ? perm[md.perm_off + c0 + i] : -1;
+      // the loads above are in flight while waiting for buffer buf to be released
+      if (k >= 2 && i == 0) sh.ok_prod = mb_wait(&sh.freeb[buf], ((k >> 1) - 1) & 1, abort_flag, status) ? 1 : 0;
       named_bar(1, TCM);
+      if (k >= 2 && !sh.ok_prod) break;
       const int row = row0 + i;
       int er = 0;
       long long w[16];
@@ -481,7 +481,8 @@ __global__ void __launch_bounds__(PT_THREADS, 1) gj_update_tcp_kernel(
         er = max(er, biased_exp(w[q]));
       }
       bool isp = false;
-      for (int q = 0; q < nb; ++q) isp = isp || (perm[md.perm_off + c0 + q] == row);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) isp |= (sh.pphys[q] == row);
       sh.er[buf][i] = er;
       sh.isp[buf][i] = (row < rows && isp) ? 1 : 0;
       unsigned char* A = sh.planes[buf];
@@ -545,30 +546,51 @@ __global__ void __launch_bounds__(PT_THREADS, 1) gj_update_tcp_kernel(
       int nb, row0, col0;
       if (!decode(t, md, nb, row0, col0)) continue;
       const int buf = k & 1;
+      // the old values of this thread's 16 entries do not depend on the products: load
+      // them first, so that their latency overlaps the wait
+      const int R = md.R, rows = md.rows, wq = te >> 5;
+      double* M = work + md.off;
+      const int c = col0 + lane;
+      const bool cok = c < R && !(c >= c0 && c < c0 + nb);
+      double cv[TCM / 8];
+#pragma unroll
+      for (int q = 0; q < TCM / 8; ++q) {
+        const int rr = row0 + wq + 8 * q;
+        cv[q] = (cok && rr < rows) ? M[(long long)rr * R + c] : 0.0;
+      }
       if (te == 0) sh.ok_epi = mb_wait(&sh.done[buf], (k >> 1) & 1, abort_flag, status) ? 1 : 0;
       named_bar(2, PT_EPI);
       if (!sh.ok_epi) break;
       asm volatile("tcgen05.fence::after_thread_sync;");
       const int er = sh.er[buf][e];
       const int jb = 16 * h;
+      // the 8 diagonals of 8 columns at a time: 8 TMEM loads in flight, one wait
       long long Ih[16], Il[16];
 #pragma unroll
-      for (int j = 0; j < 16; ++j) Ih[j] = Il[j] = 0;
+      for (int half = 0; half < 2; ++half) {
+        uint32_t v[TCKEEP - 1][8];
 #pragma unroll
-      for (int dg = 2; dg <= TCKEEP; ++dg) {
-        uint32_t v[16];
-        const uint32_t addr = tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)(buf * 256 + (dg - 2) * TCN + jb);
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-            : "r"(addr));
+        for (int dg = 2; dg <= TCKEEP; ++dg) {
+          const uint32_t addr =
+              tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)(buf * 256 + (dg - 2) * TCN + jb + 8 * half);
+          uint32_t* vd = v[dg - 2];
+          asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                       : "=r"(vd[0]), "=r"(vd[1]), "=r"(vd[2]), "=r"(vd[3]), "=r"(vd[4]), "=r"(vd[5]), "=r"(vd[6]),
+                         "=r"(vd[7])
+                       : "r"(addr));
+        }
         asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const long long a = (long long)__float2int_rz(__uint_as_float(v[j]));
-          if (dg <= 5) Ih[j] += a * (1ll << (8 * (5 - dg)));
-          else Il[j] += a * (1ll << (8 * (9 - dg)));
+        for (int j = 0; j < 8; ++j) {
+          long long hsum = 0, lsum = 0;
+#pragma unroll
+          for (int dg = 2; dg <= TCKEEP; ++dg) {
+            const long long a = (long long)__float2int_rz(__uint_as_float(v[dg - 2][j]));
+            if (dg <= 5) hsum += a * (1ll << (8 * (5 - dg)));
+            else lsum += a * (1ll << (8 * (9 - dg)));
+          }
+          Ih[8 * half + j] = hsum;
+          Il[8 * half + j] = lsum;
         }
       }
 #pragma unroll
@@ -593,20 +615,10 @@ __global__ void __launch_bounds__(PT_THREADS, 1) gj_update_tcp_kernel(
       mb_arrive(&sh.freeb[buf]);  // TMEM and buffer metadata read: producers may refill
       named_bar(2, PT_EPI);
       // coalesced update: epilogue warp q = te / 32 takes rows q, q + 8, ...; lane = column
-      const int R = md.R, rows = md.rows, wq = te >> 5;
-      double* M = work + md.off;
-      const int c = col0 + lane;
-      const bool cok = c < R && !(c >= c0 && c < c0 + nb);
-      double cv[TCM / 8];
 #pragma unroll
       for (int q = 0; q < TCM / 8; ++q) {
         const int r = wq + 8 * q, rr = row0 + r;
-        cv[q] = (cok && rr < rows && !isp_row[r]) ? M[(long long)rr * R + c] : 0.0;
-      }
-#pragma unroll
-      for (int q = 0; q < TCM / 8; ++q) {
-        const int r = wq + 8 * q, rr = row0 + r;
-        if (cok && rr < rows) M[(long long)rr * R + c] = cv[q] + sh.stg[r][lane];
+        if (cok && rr < rows) M[(long long)rr * R + c] = (isp_row[r] ? 0.0 : cv[q]) + sh.stg[r][lane];
       }
       named_bar(2, PT_EPI);  // stg and isp_row are reused by the next tile
       ++k;
