@@ -1162,7 +1162,15 @@ void run_gj(const GJDesc* gj, int nmat, int maxR, int maxK, T* work, int* perm, 
   // cfg = panel width + 100 x path (path 1: the FP64 tensor-core update); 0: fixed rules
   // (the tensor-core update for every FP64 batch: measured fastest on every level)
   const int nb = cfg % 100 > 0 ? std::min(cfg % 100, nb_cap(maxK, sizeof(T))) : choose_nb(maxK, sizeof(T), nmat);
-  const int tensor = sizeof(T) == 8 && (cfg > 0 ? cfg / 100 : 1);
+  int tensor = sizeof(T) == 8 && (cfg > 0 ? cfg / 100 : 1);
+  // the streamed form of the tensor-core update moves matrix rows by bulk copies, which
+  // need 16-byte aligned rows: an aligned workspace and even row lengths (every matrix
+  // offset in a batch is a sum of multiples of the row lengths)
+  if (tensor) {
+    bool even = ((uintptr_t)work & 15) == 0;
+    for (const auto& m : rk) even = even && m[0] % 2 == 0;
+    if (even) tensor = 2;
+  }
   const std::string sf = std::string(tsuf<T>()) + ":" + what;
   TIMED(("gj_init_" + sf).c_str(), 0, 0, launch_gj_init<T>(gj, nmat, perm, s));
   CKL();

@@ -630,6 +630,475 @@ __global__ void __launch_bounds__(PT_THREADS, 1) gj_update_tcp_kernel(
   if (warp == 4) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
 }
 
+// ---------------------------------------------------------------------------------------
+// Streamed form of the tensor-core update, for batches whose matrices start on 16-byte
+// boundaries and have an even row length.  The work unit is a block of 128 rows and a run
+// of up to ct column tiles of one matrix: the digit planes of the block's W rows are
+// formed once per unit and serve every tile of the run.  Matrix tiles reach shared memory
+// by 16-byte asynchronous copies, three tiles ahead of the epilogue, so that no thread
+// holds a matrix load in flight; the epilogue writes the updated entries straight back.
+// Roles (24 warps):
+//   warps 0-3   producers: per unit, the W rows -> A digit planes (buffer u % 2) and row
+//               scales; per tile k, warp k % 4 forms the pivot-row column digits (B slot k % 4);
+//   warp 4      one thread issues the 36 digit-pair products of tile k into TMEM buffer k % 2;
+//   warp 5      loader: asynchronous copies of tile k's rows into C buffer k % 3;
+//   warps 8-23  epilogue (4 warps per TMEM lane quarter, 8 columns each): TMEM -> exact
+//               recombination, rounded once to FP64 with integer operations -> + old value
+//               from the C buffer -> matrix.
+// Every handoff is an mbarrier; waits are bounded and a timeout stops every role (status -1).
+constexpr int PS_THREADS = 768;
+constexpr int PS_EPI = 512;
+constexpr int PS_CP = 34;  // C buffer row pitch in doubles: 272 bytes, 16-byte aligned rows
+constexpr int PS_NC = 3;   // C buffers
+constexpr int PS_NB = 4;   // B slots (one per producer warp)
+constexpr int PS_NE = 8;   // column-scale slots (tile k uses k % 8)
+constexpr int PS_NU = 4;   // row-scale slots (unit u uses u % 4)
+
+struct PsShared {
+  unsigned char A[2][TCS * TCM * 32];
+  unsigned char B[PS_NB][TCS * TCN * 32];
+  double C[PS_NC][TCM][PS_CP];
+  int er[PS_NU][TCM];
+  int cexp[PS_NE][TCN];
+  unsigned char isp[PS_NU][TCM];
+  unsigned long long afull[2], afree[2], bfull[PS_NB], bfree[PS_NB], cfull[PS_NC], cfree[PS_NC];
+  unsigned long long tfull[2], tfree[2], mdone;
+  unsigned int tmem_base;
+  int abort_flag;
+  int ok_epi[2];
+};
+
+struct PsGeom {
+  int rtmax, ctmax, ct, ncc;
+  long long upm, total;
+};
+
+// Unit u of the launch: matrix, row block and column-tile run [j0, j1).  False when the
+// unit holds no tile to update (past the matrix, or inside the pivot columns only).
+__device__ __forceinline__ bool ps_unit(const GJDesc* __restrict__ d, long long u, const PsGeom& g, int c0,
+                                        int nb_req, GJDesc& md, int& nb, int& row0, int& j0, int& j1) {
+  const long long m = u / g.upm;
+  const int r = (int)(u - m * g.upm);
+  const int rb = r / g.ncc, cc = r - rb * g.ncc;
+  md = d[m];
+  if (c0 >= md.K) return false;
+  nb = min(nb_req, md.K - c0);
+  row0 = rb * TCM;
+  if (row0 >= md.rows) return false;
+  j0 = cc * g.ct;
+  j1 = min(j0 + g.ct, (md.R + TCN - 1) / TCN);
+  for (int j = j0; j < j1; ++j)
+    if (!(j * TCN >= c0 && j * TCN + TCN <= c0 + nb)) return true;
+  return false;
+}
+
+__device__ __forceinline__ bool ps_tile(int j, int c0, int nb) { return !(j * TCN >= c0 && j * TCN + TCN <= c0 + nb); }
+
+// the fixed-point form of x = bits against the row (or column) exponent emax, as in
+// write_digits
+__device__ __forceinline__ long long fixed_point(long long bits, int emax) {
+  const int E = biased_exp(bits);
+  long long X = 0;
+  if (E > 0) {
+    const long long m = (bits & 0xFFFFFFFFFFFFFll) | (1ll << 52);
+    const int sh = E - emax + 10;
+    if (sh >= 0) X = m << sh;
+    else if (sh > -60) X = (m + (1ll << (-sh - 1))) >> (-sh);
+    if (bits < 0) X = -X;
+  }
+  return X;
+}
+
+// bf16 bits of a small integer |a| <= 2^8, exactly: 1.5 2^23 + a is an FP32 number with
+// unit spacing, so subtracting 1.5 2^23 leaves a exactly, and a value with at most 8
+// significant bits keeps them all in the upper half of its FP32 encoding.
+__device__ __forceinline__ uint32_t bf16_of_int(int a) {
+  return __float_as_uint(__int_as_float(0x4B400000 + a) - 12582912.0f) >> 16;
+}
+
+// The 8 balanced base-256 digit planes of one K-major row of 16 values (a row of W, or a
+// column of Prow), written as two 16-byte stores per plane.
+__device__ __forceinline__ void write_digit_row(const long long* w, int emax, unsigned char* base, int plane_bytes,
+                                                int row) {
+  long long X[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) X[q] = fixed_point(w[q], emax);
+  unsigned char* p0 = base + kmaj16(row, 0);
+#pragma unroll
+  for (int s = TCS - 1; s >= 0; --s) {
+    uint32_t pk[8];
+#pragma unroll
+    for (int q = 0; q < 16; q += 2) {
+      int a[2];
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        if (s > 0) {
+          a[t] = (int)(((unsigned int)X[q + t] + 128u) & 255u) - 128;
+          X[q + t] = (X[q + t] - a[t]) >> 8;
+        } else {
+          a[t] = (int)X[q + t];
+        }
+      }
+      pk[q >> 1] = bf16_of_int(a[0]) | (bf16_of_int(a[1]) << 16);
+    }
+    *reinterpret_cast<uint4*>(p0 + s * plane_bytes) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    *reinterpret_cast<uint4*>(p0 + s * plane_bytes + 128) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+  }
+}
+
+// FP32 accumulator holding an exact integer |v| <= 2^22 -> that integer (same unit-spacing
+// argument as bf16_of_int)
+__device__ __forceinline__ int int_of_acc(uint32_t v) {
+  return __float_as_int(__uint_as_float(v) + 12582912.0f) - 0x4B400000;
+}
+
+// The product entry from its 8 diagonal sums S_2 .. S_9 (s[0] .. s[7]):
+//   W_r Prow_c = 2^(er + ec - 2114) I,  I = sum_d S_d 2^(8 (9 - d)),
+// with I assembled exactly (|I| < 2^80) and rounded once to FP64 with integer operations
+// (the FP64 pipe is the scarce unit): to nearest, ties away from zero, so the error is at
+// most half a unit in the last place.  Results below the normal range flush to zero.
+__device__ __forceinline__ double recombine(const int* s, int er, int ec) {
+  const int p01 = s[0] * 256 + s[1], p23 = s[2] * 256 + s[3], p45 = s[4] * 256 + s[5], p67 = s[6] * 256 + s[7];
+  const long long H = (long long)p01 * 65536 + p23;  // I = H 2^32 + L
+  const long long L = (long long)p45 * 65536 + p67;
+  const long long T = H + (L >> 32);  // I = T 2^32 + u, 0 <= u < 2^32
+  const unsigned int u = (unsigned int)L;
+  const bool neg = T < 0;
+  // |I| = A 2^32 + B
+  const unsigned long long A = neg ? (unsigned long long)(-T) - (u != 0u ? 1ull : 0ull) : (unsigned long long)T;
+  const unsigned int B = neg ? 0u - u : u;
+  // N: |I| shifted so that its leading bit is bit 63 (bits shifted out lie below the
+  // rounding position and cannot change a round-half-up decision); top: that bit's
+  // position in |I|
+  unsigned long long N;
+  int top;
+  if ((A >> 32) == 0) {
+    const unsigned long long V = (A << 32) | B;
+    if (V == 0) return 0.0;
+    const int z = __clzll((long long)V);
+    N = V << z;
+    top = 63 - z;
+  } else {
+    const int lz = __clzll((long long)A);  // 16 .. 31
+    N = (A << lz) | ((unsigned long long)B >> (32 - lz));
+    top = 95 - lz;
+  }
+  unsigned long long mant = (N >> 11) + ((N >> 10) & 1ull);
+  if (mant >> 53) {
+    mant >>= 1;
+    ++top;
+  }
+  const int E = top + er + ec - 1091;
+  if (E <= 0) return 0.0;
+  const unsigned long long sgn = (unsigned long long)neg << 63;
+  if (E >= 2047) return __longlong_as_double((long long)(sgn | 0x7FF0000000000000ull));
+  return __longlong_as_double((long long)(sgn | ((unsigned long long)E << 52) | (mant & 0xFFFFFFFFFFFFFull)));
+}
+
+// bounded wait that ignores the abort flag: used only to drain the role's own operations
+// before the block exits
+__device__ __forceinline__ bool mb_drain(unsigned long long* b, int parity) {
+  for (long long it = 0; it < PT_WAIT; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+// the barrier receives one arrival when this thread's earlier asynchronous copies have landed
+__device__ __forceinline__ void cp_async_arrive(unsigned long long* b) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+
+__global__ void __launch_bounds__(PS_THREADS, 1) gj_update_tcs_kernel(
+    const GJDesc* __restrict__ d, PsGeom g, double* __restrict__ work, const int* __restrict__ perm,
+    const double* __restrict__ prow, long long prow_stride, int c0, int nb_req, int* __restrict__ status) {
+  extern __shared__ __align__(1024) unsigned char ps_raw[];
+  PsShared& sh = *reinterpret_cast<PsShared*>(ps_raw);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int b = 0; b < 2; ++b) {
+      mb_init(&sh.afull[b], TCM);
+      mb_init(&sh.afree[b], 1);
+      mb_init(&sh.tfull[b], 1);
+      mb_init(&sh.tfree[b], PS_EPI);
+    }
+    for (int b = 0; b < PS_NB; ++b) {
+      mb_init(&sh.bfull[b], 32);
+      mb_init(&sh.bfree[b], 1);
+    }
+    for (int b = 0; b < PS_NC; ++b) {
+      mb_init(&sh.cfull[b], 32);
+      mb_init(&sh.cfree[b], PS_EPI);
+    }
+    mb_init(&sh.mdone, 1);
+    sh.abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 4) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh.tmem_base)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = sh.tmem_base;
+  volatile int* abort_flag = &sh.abort_flag;
+
+  if (warp < 4) {
+    // ---------------- producers (no block-wide barrier: a warp that stops leaves the others free)
+    const int i = tid;
+    long long k = 0;
+    int ua = 0;
+    bool stop = false;
+    for (long long u = blockIdx.x; u < g.total && !stop; u += gridDim.x) {
+      GJDesc md;
+      int nb, row0, j0, j1;
+      if (!ps_unit(d, u, g, c0, nb_req, md, nb, row0, j0, j1)) continue;
+      const int R = md.R, rows = md.rows;
+      const double* Mw = work + md.off;
+      // the unit's W rows; their loads are in flight during the wait for the A buffer
+      const int row = row0 + i;
+      const bool rowok = row < rows;
+      long long w[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q)
+        w[q] = (rowok && q < nb) ? __double_as_longlong(Mw[(long long)row * R + c0 + q]) : 0ll;
+      bool isp = false;
+#pragma unroll
+      for (int q = 0; q < 16; ++q) isp |= (q < nb) && (perm[md.perm_off + c0 + q] == row);
+      if (ua >= 2) {
+        int ok = 1;
+        if (lane == 0) ok = mb_wait(&sh.afree[ua & 1], ((ua >> 1) - 1) & 1, abort_flag, status) ? 1 : 0;
+        if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+      }
+      int er = 0;
+#pragma unroll
+      for (int q = 0; q < 16; ++q) er = max(er, biased_exp(w[q]));
+      sh.er[ua & (PS_NU - 1)][i] = er;
+      sh.isp[ua & (PS_NU - 1)][i] = (rowok && isp) ? 1 : 0;
+      write_digit_row(w, er, sh.A[ua & 1], TCM * 32, i);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mb_arrive(&sh.afull[ua & 1]);
+      const double* pb = prow + (long long)(u / g.upm) * prow_stride;
+      for (int j = j0; j < j1; ++j) {
+        if (!ps_tile(j, c0, nb)) continue;
+        if ((int)(k & 3) == warp) {
+          const int c = j * TCN + lane;
+          const bool cvalid = c < R && !(c >= c0 && c < c0 + nb);
+          long long pv[16];
+#pragma unroll
+          for (int q = 0; q < 16; ++q) pv[q] = (cvalid && q < nb) ? __double_as_longlong(pb[(long long)q * R + c]) : 0ll;
+          if (k >= PS_NB) {
+            int ok = 1;
+            if (lane == 0) ok = mb_wait(&sh.bfree[warp], ((k >> 2) - 1) & 1, abort_flag, status) ? 1 : 0;
+            if (!__shfl_sync(0xffffffffu, ok, 0)) {
+              stop = true;
+              break;
+            }
+          }
+          int ec = 0;
+#pragma unroll
+          for (int q = 0; q < 16; ++q) ec = max(ec, biased_exp(pv[q]));
+          sh.cexp[k & (PS_NE - 1)][lane] = ec;
+          write_digit_row(pv, ec, sh.B[warp], TCN * 32, lane);
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          mb_arrive(&sh.bfull[warp]);
+        }
+        ++k;
+      }
+      ++ua;
+    }
+  } else if (warp == 4) {
+    // ---------------- MMA issue (one thread)
+    if (lane == 0) {
+      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TCN >> 3) << 17) |
+                             ((uint32_t)(TCM >> 4) << 24);
+      long long k = 0;
+      int ua = 0;
+      bool stop = false;
+      for (long long u = blockIdx.x; u < g.total && !stop; u += gridDim.x) {
+        GJDesc md;
+        int nb, row0, j0, j1;
+        if (!ps_unit(d, u, g, c0, nb_req, md, nb, row0, j0, j1)) continue;
+        if (!mb_wait(&sh.afull[ua & 1], (ua >> 1) & 1, abort_flag, status)) break;
+        const uint32_t a0 = smem_u32(sh.A[ua & 1]);
+        for (int j = j0; j < j1; ++j) {
+          if (!ps_tile(j, c0, nb)) continue;
+          const int tb = (int)(k & 1), bs = (int)(k & 3);
+          if (!mb_wait(&sh.bfull[bs], (k >> 2) & 1, abort_flag, status) ||
+              (k >= 2 && !mb_wait(&sh.tfree[tb], ((k >> 1) - 1) & 1, abort_flag, status))) {
+            stop = true;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const uint32_t b0 = smem_u32(sh.B[bs]);
+          const uint32_t tcol = tmem + (uint32_t)(tb * 256);
+          for (int dg = 2; dg <= TCKEEP; ++dg) {
+            uint32_t acc = 0;
+            for (int sa = 1; sa <= TCS; ++sa) {
+              const int sb = dg - sa;
+              if (sb < 1 || sb > TCS) continue;
+              const uint64_t ad = umma_desc(a0 + (sa - 1) * (TCM * 32), 128, 256);
+              const uint64_t bd = umma_desc(b0 + (sb - 1) * (TCN * 32), 128, 256);
+              asm volatile(
+                  "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                  " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tcol + (uint32_t)((dg - 2) * TCN)),
+                  "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+              acc = 1;
+            }
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              smem_u32(&sh.tfull[tb])));
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              smem_u32(&sh.bfree[bs])));
+          ++k;
+        }
+        if (stop) break;
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(&sh.afree[ua & 1])));
+        ++ua;
+      }
+      // every product issued has completed before the block frees TMEM
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(&sh.mdone)));
+      mb_drain(&sh.mdone, 0);
+    }
+  } else if (warp == 5) {
+    // ---------------- loader: 16-byte asynchronous copies of the tile rows into C buffer k % 3
+    long long k = 0;
+    int cb = 0;
+    bool stop = false;
+    for (long long u = blockIdx.x; u < g.total && !stop; u += gridDim.x) {
+      GJDesc md;
+      int nb, row0, j0, j1;
+      if (!ps_unit(d, u, g, c0, nb_req, md, nb, row0, j0, j1)) continue;
+      const double* Mw = work + md.off;
+      const int R = md.R, nr = min(TCM, md.rows - row0);
+      for (int j = j0; j < j1; ++j) {
+        if (!ps_tile(j, c0, nb)) continue;
+        if (k >= PS_NC) {
+          int ok = 1;
+          if (lane == 0) ok = mb_wait(&sh.cfree[cb], (int)((k / PS_NC) - 1) & 1, abort_flag, status) ? 1 : 0;
+          if (!__shfl_sync(0xffffffffu, ok, 0)) {
+            stop = true;
+            break;
+          }
+        }
+        const int col0 = j * TCN;
+        const int cpr = min(TCN, R - col0) >> 1;  // 16-byte chunks per row (R is even)
+        const int nch = nr * cpr;
+        for (int c = lane; c < nch; c += 32) {
+          const int r = c / cpr, q = c - r * cpr;
+          cp_async16(&sh.C[cb][r][2 * q], Mw + (long long)(row0 + r) * R + col0 + 2 * q);
+        }
+        cp_async_arrive(&sh.cfull[cb]);
+        ++k;
+        cb = cb == PS_NC - 1 ? 0 : cb + 1;
+      }
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");  // the copies issued have landed
+  } else if (warp >= 8) {
+    // ---------------- epilogue: thread (row e, group cg) takes columns 8 cg .. 8 cg + 7
+    const int ew = warp & 3, cg = (warp - 8) >> 2, te = tid - 256;
+    const int e = ew * 32 + lane;  // row of the tile = TMEM lane
+    long long k = 0;
+    int ua = 0, cb = 0;
+    bool stop = false;
+    for (long long u = blockIdx.x; u < g.total && !stop; u += gridDim.x) {
+      GJDesc md;
+      int nb, row0, j0, j1;
+      if (!ps_unit(d, u, g, c0, nb_req, md, nb, row0, j0, j1)) continue;
+      const int R = md.R;
+      const bool rowok = row0 + e < md.rows;
+      double* grow = work + md.off + (long long)(rowok ? row0 + e : 0) * R;
+      for (int j = j0; j < j1; ++j) {
+        if (!ps_tile(j, c0, nb)) continue;
+        const int tb = (int)(k & 1);
+        if (te == 0)
+          sh.ok_epi[tb] = (mb_wait(&sh.tfull[tb], (int)(k >> 1) & 1, abort_flag, status) &&
+                           mb_wait(&sh.cfull[cb], (int)(k / PS_NC) & 1, abort_flag, status))
+                              ? 1
+                              : 0;
+        named_bar(2, PS_EPI);
+        if (!sh.ok_epi[tb]) {
+          stop = true;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        // row scale and pivot flag of the unit (written before its first products)
+        const int er = sh.er[ua & (PS_NU - 1)][e];
+        const bool isp = sh.isp[ua & (PS_NU - 1)][e] != 0;
+        const double* crow = &sh.C[cb][e][0];
+        const int col0 = j * TCN;
+#pragma unroll
+        for (int bt = 0; bt < 2; ++bt) {
+          const int jb = 8 * cg + 4 * bt;
+          uint32_t v[TCKEEP - 1][4];
+#pragma unroll
+          for (int dg = 2; dg <= TCKEEP; ++dg) {
+            const uint32_t addr =
+                tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)(tb * 256 + (dg - 2) * TCN + jb);
+            uint32_t* vd = v[dg - 2];
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                         : "=r"(vd[0]), "=r"(vd[1]), "=r"(vd[2]), "=r"(vd[3])
+                         : "r"(addr));
+          }
+          asm volatile("tcgen05.wait::ld.sync.aligned;");
+          int ec[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) ec[q] = sh.cexp[k & (PS_NE - 1)][jb + q];
+          const double2 o0 = *reinterpret_cast<const double2*>(crow + jb);
+          const double2 o1 = *reinterpret_cast<const double2*>(crow + jb + 2);
+          if (bt == 1) {
+            // TMEM buffer, column scales and C buffer read: hand them back
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            mb_arrive(&sh.tfree[tb]);
+            mb_arrive(&sh.cfree[cb]);
+          }
+          const double ov[4] = {o0.x, o0.y, o1.x, o1.y};
+          double nv[4];
+          bool up[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            int s[TCKEEP - 1];
+#pragma unroll
+            for (int dg = 0; dg < TCKEEP - 1; ++dg) s[dg] = int_of_acc(v[dg][q]);
+            const int col = col0 + jb + q;
+            up[q] = rowok && col < R && !(col >= c0 && col < c0 + nb);
+            nv[q] = (isp ? 0.0 : ov[q]) + recombine(s, er, ec[q]);
+          }
+#pragma unroll
+          for (int q = 0; q < 4; q += 2) {
+            double* dst = grow + col0 + jb + q;
+            if (up[q] && up[q + 1]) {
+              *reinterpret_cast<double2*>(dst) = make_double2(nv[q], nv[q + 1]);
+            } else {
+              if (up[q]) dst[0] = nv[q];
+              if (up[q + 1]) dst[1] = nv[q + 1];
+            }
+          }
+        }
+        ++k;
+        cb = cb == PS_NC - 1 ? 0 : cb + 1;
+      }
+      ++ua;
+    }
+  }
+  // warps 6 and 7 have no role
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 4) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+
 template <typename T, typename TO>
 __global__ void __launch_bounds__(256) gj_extract_kernel(const GJDesc* __restrict__ d,
                                                          const T* __restrict__ work,
@@ -707,17 +1176,32 @@ void launch_gj_prep(const GJDesc* d, int nmat, int maxR, T* work, const int* per
 template <typename T>
 void launch_gj_update(const GJDesc* d, int nmat, int maxR, int maxRows, T* work, const int* perm, T* prow,
                       long long prow_stride, int c0, int nb, cudaStream_t s, int* status, int tensor) {
-  if (std::is_same<T, double>::value && tensor) {
+  static int nsm = 0;
+  if (std::is_same<T, double>::value && tensor && !nsm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(gj_update_tcp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PtShared));
+    cudaFuncSetAttribute(gj_update_tcs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PsShared));
+    if (nsm <= 0) nsm = 1;
+  }
+  if (std::is_same<T, double>::value && tensor == 2) {
+    // FP64, streamed tensor-core kernel (16-byte aligned rows): one CTA per SM over units
+    // of 128 rows x ct column tiles, ct chosen to leave about 4 units per SM
+    PsGeom g;
+    g.rtmax = (maxRows + TCM - 1) / TCM;
+    g.ctmax = (maxR + TCN - 1) / TCN;
+    const long long tiles = (long long)nmat * g.rtmax * g.ctmax;
+    g.ct = (int)std::min<long long>(g.ctmax, std::max<long long>(1, (tiles + 4ll * nsm - 1) / (4ll * nsm)));
+    g.ncc = (g.ctmax + g.ct - 1) / g.ct;
+    g.upm = (long long)g.rtmax * g.ncc;
+    g.total = (long long)nmat * g.upm;
+    const int grid = (int)std::min<long long>(nsm, g.total);
+    gj_update_tcs_kernel<<<grid, PS_THREADS, sizeof(PsShared), s>>>(d, g, (double*)work, perm, (const double*)prow,
+                                                                    prow_stride, c0, nb, status);
+  } else if (std::is_same<T, double>::value && tensor) {
     // FP64: the persistent tensor-core kernel, one CTA per SM over ceil(rows / 128) x
     // ceil(R / 32) tiles of every matrix
-    static int nsm = 0;
-    if (!nsm) {
-      int dev = 0;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-      cudaFuncSetAttribute(gj_update_tcp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PtShared));
-      if (nsm <= 0) nsm = 1;
-    }
     const int ctmax = (maxR + TCN - 1) / TCN, rtmax = (maxRows + TCM - 1) / TCM;
     const long long total = (long long)nmat * ctmax * rtmax;
     const int grid = (int)std::min<long long>(nsm, total);
