@@ -175,6 +175,7 @@ struct Level {
   long long* off_tr = nullptr;
   long long* off_br = nullptr;
   long long work_elems = 0;
+  long long mstride = 0;  // matrix m of the batch at work + m * mstride, all of one shape (0: not so)
   int perm_elems = 0;
   // solve
   UpGather* ug = nullptr;
@@ -775,6 +776,14 @@ void make_plan(hps_handle* h, HostPlan& hp) {
       }
     }
     lv.work_elems = woff;
+    lv.mstride = 0;
+    if (!pd.gj.empty()) {
+      const GJDesc& g0 = pd.gj[0];
+      bool same = g0.off == 0 && g0.R == lv.maxR && g0.rows == lv.maxRows;
+      for (size_t i = 0; i < pd.gj.size() && same; ++i)
+        same = pd.gj[i].R == g0.R && pd.gj[i].rows == g0.rows && pd.gj[i].off == (long long)i * g0.rows * g0.R;
+      if (same) lv.mstride = (long long)g0.rows * g0.R;
+    }
     lv.perm_elems = poff;
     h->p_rows = std::max(h->p_rows, split_prod(pd.up, false));
     h->p_rows = std::max(h->p_rows, split_prod(pd.down, false));
@@ -1156,7 +1165,7 @@ int choose_nb(int K, size_t elem, int nmat) {
 template <typename T>
 void run_gj(const GJDesc* gj, int nmat, int maxR, int maxK, T* work, int* perm, T* pinv, T* prow,
             int* status, const std::vector<std::array<int, 3>>& rk, const char* what, cudaStream_t s,
-            int cfg = 0) {
+            int cfg = 0, long long mat_stride = 0) {
   int maxRows = 0;
   for (const auto& m : rk) maxRows = std::max(maxRows, m[2]);
   // cfg = panel width + 100 x path (path 1: the FP64 tensor-core update); 0: fixed rules
@@ -1190,7 +1199,8 @@ void run_gj(const GJDesc* gj, int nmat, int maxR, int maxK, T* work, int* perm, 
     TIMED(("gj_prep_" + sf).c_str(), fq, 0,
           launch_gj_prep<T>(gj, nmat, maxR, work, perm, pinv, prow, prow_stride, c0, nb, s));
     TIMED((std::string(tensor ? "gj_update_tc_" : "gj_update_") + sf).c_str(), fu, bu,
-          launch_gj_update<T>(gj, nmat, maxR, maxRows, work, perm, prow, prow_stride, c0, nb, s, status, tensor));
+          launch_gj_update<T>(gj, nmat, maxR, maxRows, work, perm, prow, prow_stride, c0, nb, s, status, tensor,
+                              mat_stride));
   }
   CKL();
 }
@@ -1251,7 +1261,7 @@ void build_root_bc(hps_handle* h, double* tstore, cudaStream_t s, const std::fun
     double* pinv = (double*)get(256 * sizeof(double));
     double* prow = (double*)get((size_t)16 * a.R * sizeof(double));
     run_gj<double>(dgd, 1, a.R, a.K, work, perm, pinv, prow, h->d_status,
-                   std::vector<std::array<int, 3>>(1, {a.R, a.K, a.rows}), "root_bc", s);
+                   std::vector<std::array<int, 3>>(1, {a.R, a.K, a.rows}), "root_bc", s, 0, (long long)a.rows * a.R);
     TIMED("gj_extract_f64", 0, (double)a.rows * a.R * 8, launch_gj_extract<double, double>(dgd, 1, a.R, work, perm, dst, s));
     CKL();
   };
@@ -1341,7 +1351,7 @@ void build_stage(hps_handle* h, const double* coeffs, cudaStream_t s) {
         TIMED("leaf_assemble_f64", 0, (double)n * per_leaf * 8,
               launch_leaf_assemble<double>(coeffs, h->n_leaf, l0, n, h->dhxy, h->p, h->q, tb, work, per_leaf, s));
         CKL();
-        run_gj<double>(dgd, n, R, m, work, perm, pinv, prow, h->d_status, rk, "leaf", s, nb);
+        run_gj<double>(dgd, n, R, m, work, perm, pinv, prow, h->d_status, rk, "leaf", s, nb, per_leaf);
       };
       elim(pick_nb(h, "leaf", sizeof(double), rk, n, s, elim));
       ExtractDst dst{};
@@ -1404,7 +1414,7 @@ void build_stage(hps_handle* h, const double* coeffs, cudaStream_t s) {
         auto elim = [&](int nb) {
           TIMED("merge_assemble_f64", 0, wbytes, launch_merge_assemble<double, double>(lv.md, nmat, lv.maxR, tstore, h->didx, w, s));
           CKL();
-          run_gj<double>(lv.gj, nmat, lv.maxR, lv.maxK, w, pm, pi, pr, h->d_status, rk, "merge", s, nb);
+          run_gj<double>(lv.gj, nmat, lv.maxR, lv.maxK, w, pm, pi, pr, h->d_status, rk, "merge", s, nb, lv.mstride);
         };
         elim(pick_nb(h, "merge", sizeof(double), rk, nmat, s, elim));
         TIMED("gj_extract_f64", 0, wbytes, launch_gj_extract<double, double>(lv.gj, nmat, lv.maxR, w, pm, dst, s));
@@ -1501,7 +1511,7 @@ void recompute_leaf_chunk(hps_handle* h, int c, cudaStream_t s) {
         launch_leaf_assemble<double>(h->coeffs_copy, h->n_leaf, l0, n, h->dhxy, h->p, h->q, tb, h->ework, per_leaf,
                                      s));
   run_gj<double>(h->egd + l0, n, R, m, h->ework, h->eperm, h->epinv, h->eprow, h->d_status,
-                 std::vector<std::array<int, 3>>(n, {R, m, R}), "leaf_econ", s);
+                 std::vector<std::array<int, 3>>(n, {R, m, R}), "leaf_econ", s, 0, per_leaf);
   ExtractDst dst{};
   dst.TL = h->eops; dst.TL_off_stride = (long long)m * R; dst.TL_ld = R;
   dst.TR = h->eops + m; dst.TR_off_stride = (long long)m * R; dst.TR_ld = R;

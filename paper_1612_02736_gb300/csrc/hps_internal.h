@@ -153,10 +153,14 @@ template <typename T>
 void launch_gj_prep(const GJDesc* d, int nmat, int maxR, T* work, const int* perm, const T* pinv,
                     T* prow, long long prow_stride, int c0, int nb, cudaStream_t s);
 template <typename T>
-// tensor = 1 (FP64 only): the tcgen05 kernel with exact digit slicing, else the FP64 / FP32
-// register-tiled SIMT kernel.
+// tensor (FP64 only): 1 the persistent tcgen05 kernel with exact digit slicing, 2 its
+// streamed form (needs 16-byte aligned rows: even R and offsets, aligned work), 0 the FP64 /
+// FP32 register-tiled SIMT kernel.  mat_stride > 0 states that every matrix has R = maxR,
+// rows = maxRows and sits at work + m * mat_stride (the streamed form then copies tiles with
+// a tensor map); 0 makes no such claim.
 void launch_gj_update(const GJDesc* d, int nmat, int maxR, int maxRows, T* work, const int* perm, T* prow,
-                      long long prow_stride, int c0, int nb, cudaStream_t s, int* status, int tensor);
+                      long long prow_stride, int c0, int nb, cudaStream_t s, int* status, int tensor,
+                      long long mat_stride = 0);
 
 // Extraction of a finished elimination: with sigma the logical->physical row map,
 //   TL[i][j] = sTL * M[sigma(i)][sigma^-1(j)]   (i, j < K)

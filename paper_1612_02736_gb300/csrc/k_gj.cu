@@ -24,9 +24,12 @@
 #include <cfloat>
 #include <cstdint>
 #include <cstdio>
+#include <cstring>
 #include <type_traits>
 
+#include <cuda.h>
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
 
 #include "hps_internal.h"
 
@@ -635,20 +638,22 @@ __global__ void __launch_bounds__(PT_THREADS, 1) gj_update_tcp_kernel(
 // boundaries and have an even row length.  The work unit is a block of 128 rows and a run
 // of up to ct column tiles of one matrix: the digit planes of the block's W rows are
 // formed once per unit and serve every tile of the run.  Matrix tiles reach shared memory
-// by 16-byte asynchronous copies, three tiles ahead of the epilogue, so that no thread
-// holds a matrix load in flight; the epilogue writes the updated entries straight back.
+// three tiles ahead of the epilogue, so that no thread holds a matrix load in flight: for
+// a batch of equal matrices at a fixed stride by two tensor-map (TMA) copies of 128 x 16
+// entries each (128-byte swizzled rows), otherwise by 16-byte asynchronous copies.  The
+// epilogue writes the updated entries straight back.
 // Roles (24 warps):
 //   warps 0-3   producers: per unit, the W rows -> A digit planes (buffer u % 2) and row
 //               scales; per tile k, warp k % 4 forms the pivot-row column digits (B slot k % 4);
 //   warp 4      one thread issues the 36 digit-pair products of tile k into TMEM buffer k % 2;
-//   warp 5      loader: asynchronous copies of tile k's rows into C buffer k % 3;
+//   warp 5      loader: tile k's rows into C buffer k % 3;
 //   warps 8-23  epilogue (4 warps per TMEM lane quarter, 8 columns each): TMEM -> exact
 //               recombination, rounded once to FP64 with integer operations -> + old value
 //               from the C buffer -> matrix.
 // Every handoff is an mbarrier; waits are bounded and a timeout stops every role (status -1).
 constexpr int PS_THREADS = 768;
 constexpr int PS_EPI = 512;
-constexpr int PS_CP = 34;  // C buffer row pitch in doubles: 272 bytes, 16-byte aligned rows
+constexpr int PS_CP = 34;  // C buffer row pitch in doubles (16-byte copies): 272 bytes, 16-byte aligned rows
 constexpr int PS_NC = 3;   // C buffers
 constexpr int PS_NB = 4;   // B slots (one per producer warp)
 constexpr int PS_NE = 8;   // column-scale slots (tile k uses k % 8)
@@ -657,6 +662,7 @@ constexpr int PS_NU = 4;   // row-scale slots (unit u uses u % 4)
 struct PsShared {
   unsigned char A[2][TCS * TCM * 32];
   unsigned char B[PS_NB][TCS * TCN * 32];
+  // C buffers, 1024-byte aligned; with tensor-map copies each holds two swizzled 128 x 16 halves
   double C[PS_NC][TCM][PS_CP];
   int er[PS_NU][TCM];
   int cexp[PS_NE][TCN];
@@ -809,6 +815,18 @@ __device__ __forceinline__ bool mb_drain(unsigned long long* b, int parity) {
   }
   return false;
 }
+__device__ __forceinline__ void mb_expect_arrive(unsigned long long* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+// box (x .. x + 15, y .. y + 127) of matrix z into shared memory (128-byte swizzled rows)
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                            unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
@@ -817,9 +835,11 @@ __device__ __forceinline__ void cp_async_arrive(unsigned long long* b) {
   asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(b)) : "memory");
 }
 
+template <bool TMA>
 __global__ void __launch_bounds__(PS_THREADS, 1) gj_update_tcs_kernel(
     const GJDesc* __restrict__ d, PsGeom g, double* __restrict__ work, const int* __restrict__ perm,
-    const double* __restrict__ prow, long long prow_stride, int c0, int nb_req, int* __restrict__ status) {
+    const double* __restrict__ prow, long long prow_stride, int c0, int nb_req, int* __restrict__ status,
+    const __grid_constant__ CUtensorMap cmap) {
   extern __shared__ __align__(1024) unsigned char ps_raw[];
   PsShared& sh = *reinterpret_cast<PsShared*>(ps_raw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -835,7 +855,7 @@ __global__ void __launch_bounds__(PS_THREADS, 1) gj_update_tcs_kernel(
       mb_init(&sh.bfree[b], 1);
     }
     for (int b = 0; b < PS_NC; ++b) {
-      mb_init(&sh.cfull[b], 32);
+      mb_init(&sh.cfull[b], TMA ? 1 : 32);
       mb_init(&sh.cfree[b], PS_EPI);
     }
     mb_init(&sh.mdone, 1);
@@ -973,7 +993,7 @@ __global__ void __launch_bounds__(PS_THREADS, 1) gj_update_tcs_kernel(
       mb_drain(&sh.mdone, 0);
     }
   } else if (warp == 5) {
-    // ---------------- loader: 16-byte asynchronous copies of the tile rows into C buffer k % 3
+    // ---------------- loader: the tile rows into C buffer k % 3
     long long k = 0;
     int cb = 0;
     bool stop = false;
@@ -982,7 +1002,7 @@ __global__ void __launch_bounds__(PS_THREADS, 1) gj_update_tcs_kernel(
       int nb, row0, j0, j1;
       if (!ps_unit(d, u, g, c0, nb_req, md, nb, row0, j0, j1)) continue;
       const double* Mw = work + md.off;
-      const int R = md.R, nr = min(TCM, md.rows - row0);
+      const int R = md.R, nr = min(TCM, md.rows - row0), m = (int)(u / g.upm);
       for (int j = j0; j < j1; ++j) {
         if (!ps_tile(j, c0, nb)) continue;
         if (k >= PS_NC) {
@@ -994,18 +1014,38 @@ __global__ void __launch_bounds__(PS_THREADS, 1) gj_update_tcs_kernel(
           }
         }
         const int col0 = j * TCN;
-        const int cpr = min(TCN, R - col0) >> 1;  // 16-byte chunks per row (R is even)
-        const int nch = nr * cpr;
-        for (int c = lane; c < nch; c += 32) {
-          const int r = c / cpr, q = c - r * cpr;
-          cp_async16(&sh.C[cb][r][2 * q], Mw + (long long)(row0 + r) * R + col0 + 2 * q);
+        if (TMA) {
+          // two 128 x 16 boxes; entries past the matrix arrive as zeros
+          if (lane == 0) {
+            const bool two = col0 + 16 < R;
+            mb_expect_arrive(&sh.cfull[cb], (two ? 2u : 1u) * (TCM * 16 * 8));
+            unsigned char* cbuf = reinterpret_cast<unsigned char*>(&sh.C[cb][0][0]);
+            tma_load_3d(cbuf, &cmap, col0, row0, m, &sh.cfull[cb]);
+            if (two) tma_load_3d(cbuf + TCM * 16 * 8, &cmap, col0 + 16, row0, m, &sh.cfull[cb]);
+          }
+        } else {
+          const int cpr = min(TCN, R - col0) >> 1;  // 16-byte chunks per row (R is even)
+          const int nch = nr * cpr;
+          for (int c = lane; c < nch; c += 32) {
+            const int r = c / cpr, q = c - r * cpr;
+            cp_async16(&sh.C[cb][r][2 * q], Mw + (long long)(row0 + r) * R + col0 + 2 * q);
+          }
+          cp_async_arrive(&sh.cfull[cb]);
         }
-        cp_async_arrive(&sh.cfull[cb]);
         ++k;
         cb = cb == PS_NC - 1 ? 0 : cb + 1;
       }
     }
-    asm volatile("cp.async.wait_all;" ::: "memory");  // the copies issued have landed
+    // the copies issued have landed before the block exits
+    if (TMA) {
+      if (lane == 0)
+        for (int b = 0; b < PS_NC; ++b) {
+          const long long n = k > b ? (k - 1 - b) / PS_NC + 1 : 0;  // copies armed on buffer b
+          if (n > 0) mb_drain(&sh.cfull[b], (int)((n - 1) & 1));
+        }
+    } else {
+      asm volatile("cp.async.wait_all;" ::: "memory");
+    }
   } else if (warp >= 8) {
     // ---------------- epilogue: thread (row e, group cg) takes columns 8 cg .. 8 cg + 7
     const int ew = warp & 3, cg = (warp - 8) >> 2, te = tid - 256;
@@ -1038,6 +1078,7 @@ __global__ void __launch_bounds__(PS_THREADS, 1) gj_update_tcs_kernel(
         const int er = sh.er[ua & (PS_NU - 1)][e];
         const bool isp = sh.isp[ua & (PS_NU - 1)][e] != 0;
         const double* crow = &sh.C[cb][e][0];
+        const unsigned char* cbyte = reinterpret_cast<const unsigned char*>(&sh.C[cb][0][0]);
         const int col0 = j * TCN;
 #pragma unroll
         for (int bt = 0; bt < 2; ++bt) {
@@ -1056,8 +1097,17 @@ __global__ void __launch_bounds__(PS_THREADS, 1) gj_update_tcs_kernel(
           int ec[4];
 #pragma unroll
           for (int q = 0; q < 4; ++q) ec[q] = sh.cexp[k & (PS_NE - 1)][jb + q];
-          const double2 o0 = *reinterpret_cast<const double2*>(crow + jb);
-          const double2 o1 = *reinterpret_cast<const double2*>(crow + jb + 2);
+          double2 o0, o1;
+          if (TMA) {
+            // half jb / 16, row e: 16-byte chunk c of the row sits at chunk c ^ (e % 8)
+            const unsigned char* rb = cbyte + (jb >> 4) * (TCM * 16 * 8) + e * 128;
+            const int ch = (jb & 15) >> 1;
+            o0 = *reinterpret_cast<const double2*>(rb + ((ch ^ (e & 7)) << 4));
+            o1 = *reinterpret_cast<const double2*>(rb + (((ch + 1) ^ (e & 7)) << 4));
+          } else {
+            o0 = *reinterpret_cast<const double2*>(crow + jb);
+            o1 = *reinterpret_cast<const double2*>(crow + jb + 2);
+          }
           if (bt == 1) {
             // TMEM buffer, column scales and C buffer read: hand them back
             asm volatile("tcgen05.fence::before_thread_sync;");
@@ -1173,16 +1223,36 @@ void launch_gj_prep(const GJDesc* d, int nmat, int maxR, T* work, const int* per
   gj_prep_kernel<T><<<grid, 256, 0, s>>>(d, work, perm, pinv, prow, prow_stride, c0, nb);
 }
 
+// cuTensorMapEncodeTiled from the driver, or null
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static bool tried = false;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    cudaGetLastError();
+  }
+  return fn;
+}
+
 template <typename T>
 void launch_gj_update(const GJDesc* d, int nmat, int maxR, int maxRows, T* work, const int* perm, T* prow,
-                      long long prow_stride, int c0, int nb, cudaStream_t s, int* status, int tensor) {
+                      long long prow_stride, int c0, int nb, cudaStream_t s, int* status, int tensor,
+                      long long mat_stride) {
   static int nsm = 0;
   if (std::is_same<T, double>::value && tensor && !nsm) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     cudaFuncSetAttribute(gj_update_tcp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PtShared));
-    cudaFuncSetAttribute(gj_update_tcs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PsShared));
+    cudaFuncSetAttribute(gj_update_tcs_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(PsShared));
+    cudaFuncSetAttribute(gj_update_tcs_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(PsShared));
     if (nsm <= 0) nsm = 1;
   }
   if (std::is_same<T, double>::value && tensor == 2) {
@@ -1197,8 +1267,29 @@ void launch_gj_update(const GJDesc* d, int nmat, int maxR, int maxRows, T* work,
     g.upm = (long long)g.rtmax * g.ncc;
     g.total = (long long)nmat * g.upm;
     const int grid = (int)std::min<long long>(nsm, g.total);
-    gj_update_tcs_kernel<<<grid, PS_THREADS, sizeof(PsShared), s>>>(d, g, (double*)work, perm, (const double*)prow,
-                                                                    prow_stride, c0, nb, status);
+    // equal matrices (R = maxR, rows = maxRows) at a fixed stride: tensor-map tile copies
+    CUtensorMap map;
+    std::memset(&map, 0, sizeof(map));
+    bool tma = false;
+    if (mat_stride > 0) {
+      if (auto enc = tensor_map_encoder()) {
+        const cuuint64_t dims[3] = {(cuuint64_t)maxR, (cuuint64_t)maxRows, (cuuint64_t)nmat};
+        const cuuint64_t strides[2] = {(cuuint64_t)maxR * 8, (cuuint64_t)mat_stride * 8};
+        const cuuint32_t box[3] = {16, (cuuint32_t)TCM, 1};
+        const cuuint32_t estr[3] = {1, 1, 1};
+        tma = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, (void*)work, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+      }
+    }
+    if (tma)
+      gj_update_tcs_kernel<true><<<grid, PS_THREADS, sizeof(PsShared), s>>>(d, g, (double*)work, perm,
+                                                                           (const double*)prow, prow_stride, c0,
+                                                                           nb, status, map);
+    else
+      gj_update_tcs_kernel<false><<<grid, PS_THREADS, sizeof(PsShared), s>>>(d, g, (double*)work, perm,
+                                                                            (const double*)prow, prow_stride, c0,
+                                                                            nb, status, map);
   } else if (std::is_same<T, double>::value && tensor) {
     // FP64: the persistent tensor-core kernel, one CTA per SM over ceil(rows / 128) x
     // ceil(R / 32) tiles of every matrix
@@ -1236,8 +1327,8 @@ template void launch_gj_panel<double>(const GJDesc*, int, int, double*, int*, do
 template void launch_gj_panel<float>(const GJDesc*, int, int, float*, int*, float*, int, int, int*, cudaStream_t);
 template void launch_gj_prep<double>(const GJDesc*, int, int, double*, const int*, const double*, double*, long long, int, int, cudaStream_t);
 template void launch_gj_prep<float>(const GJDesc*, int, int, float*, const int*, const float*, float*, long long, int, int, cudaStream_t);
-template void launch_gj_update<double>(const GJDesc*, int, int, int, double*, const int*, double*, long long, int, int, cudaStream_t, int*, int);
-template void launch_gj_update<float>(const GJDesc*, int, int, int, float*, const int*, float*, long long, int, int, cudaStream_t, int*, int);
+template void launch_gj_update<double>(const GJDesc*, int, int, int, double*, const int*, double*, long long, int, int, cudaStream_t, int*, int, long long);
+template void launch_gj_update<float>(const GJDesc*, int, int, int, float*, const int*, float*, long long, int, int, cudaStream_t, int*, int, long long);
 template void launch_gj_extract<double, double>(const GJDesc*, int, int, const double*, const int*, const ExtractDst&, cudaStream_t);
 template void launch_gj_extract<float, double>(const GJDesc*, int, int, const float*, const int*, const ExtractDst&, cudaStream_t);
 
