@@ -671,7 +671,6 @@ struct PsShared {
   unsigned long long tfull[2], tfree[2], mdone;
   unsigned int tmem_base;
   int abort_flag;
-  int ok_epi[2];
 };
 
 struct PsGeom {
@@ -773,32 +772,23 @@ __device__ __forceinline__ double recombine(const int* s, int er, int ec) {
   // |I| = A 2^32 + B
   const unsigned long long A = neg ? (unsigned long long)(-T) - (u != 0u ? 1ull : 0ull) : (unsigned long long)T;
   const unsigned int B = neg ? 0u - u : u;
-  // N: |I| shifted so that its leading bit is bit 63 (bits shifted out lie below the
-  // rounding position and cannot change a round-half-up decision); top: that bit's
-  // position in |I|
-  unsigned long long N;
-  int top;
-  if ((A >> 32) == 0) {
-    const unsigned long long V = (A << 32) | B;
-    if (V == 0) return 0.0;
-    const int z = __clzll((long long)V);
-    N = V << z;
-    top = 63 - z;
-  } else {
-    const int lz = __clzll((long long)A);  // 16 .. 31
-    N = (A << lz) | ((unsigned long long)B >> (32 - lz));
-    top = 95 - lz;
-  }
-  unsigned long long mant = (N >> 11) + ((N >> 10) & 1ull);
-  if (mant >> 53) {
-    mant >>= 1;
-    ++top;
-  }
+  // W: the leading 64 bits of |I| when A >= 2^32 (B's top bits are shifted in below), else
+  // all of |I|; N: W normalised so that the leading bit is bit 63.  Bits shifted out lie
+  // below the rounding position and cannot change a round-half-up decision.
+  const bool big = (A >> 32) != 0;
+  const unsigned long long W = big ? A : ((A << 32) | B);
+  if (W == 0) return 0.0;
+  const int z = __clzll((long long)W);  // 16 .. 31 when big
+  unsigned long long N = W << z;
+  if (big) N |= (unsigned long long)(B >> (32 - z));
+  const int top = (big ? 95 : 63) - z;  // position of the leading bit in |I|
+  const unsigned long long mant = (N >> 11) + ((N >> 10) & 1ull);  // 2^52 .. 2^53
   const int E = top + er + ec - 1091;
   if (E <= 0) return 0.0;
   const unsigned long long sgn = (unsigned long long)neg << 63;
   if (E >= 2047) return __longlong_as_double((long long)(sgn | 0x7FF0000000000000ull));
-  return __longlong_as_double((long long)(sgn | ((unsigned long long)E << 52) | (mant & 0xFFFFFFFFFFFFFull)));
+  // the leading bit of mant lands in the exponent field: a rounding carry to 2^53 raises it
+  return __longlong_as_double((long long)(sgn + ((unsigned long long)(E - 1) << 52) + mant));
 }
 
 // bounded wait that ignores the abort flag: used only to drain the role's own operations
@@ -1048,7 +1038,7 @@ __global__ void __launch_bounds__(PS_THREADS, 1) gj_update_tcs_kernel(
     }
   } else if (warp >= 8) {
     // ---------------- epilogue: thread (row e, group cg) takes columns 8 cg .. 8 cg + 7
-    const int ew = warp & 3, cg = (warp - 8) >> 2, te = tid - 256;
+    const int ew = warp & 3, cg = (warp - 8) >> 2;
     const int e = ew * 32 + lane;  // row of the tile = TMEM lane
     long long k = 0;
     int ua = 0, cb = 0;
@@ -1063,13 +1053,15 @@ __global__ void __launch_bounds__(PS_THREADS, 1) gj_update_tcs_kernel(
       for (int j = j0; j < j1; ++j) {
         if (!ps_tile(j, c0, nb)) continue;
         const int tb = (int)(k & 1);
-        if (te == 0)
-          sh.ok_epi[tb] = (mb_wait(&sh.tfull[tb], (int)(k >> 1) & 1, abort_flag, status) &&
-                           mb_wait(&sh.cfull[cb], (int)(k / PS_NC) & 1, abort_flag, status))
-                              ? 1
-                              : 0;
-        named_bar(2, PS_EPI);
-        if (!sh.ok_epi[tb]) {
+        // every warp waits for itself, so that the warps drift apart and one warp's TMEM
+        // and shared-memory latency overlaps the others' arithmetic
+        int ok = 1;
+        if (lane == 0)
+          ok = (mb_wait(&sh.tfull[tb], (int)(k >> 1) & 1, abort_flag, status) &&
+                mb_wait(&sh.cfull[cb], (int)(k / PS_NC) & 1, abort_flag, status))
+                   ? 1
+                   : 0;
+        if (!__shfl_sync(0xffffffffu, ok, 0)) {
           stop = true;
           break;
         }
