@@ -58,6 +58,15 @@ typedef enum {
   HPS_NODES_GAUSS_ALL = 2       /* every Gaussian node, by global id                     */
 } hps_node_set;
 
+/* Arithmetic of the FP64 solve and adjoint products (hps_opts.fp64_gemm). */
+typedef enum {
+  HPS_GEMM_TENSOR = 0, /* tcgen05 tensor cores by exact digit slicing (9 base-128 digits per
+                        * entry, scaled per operator row and per vector column, exact FP32
+                        * digit sums, one rounding to FP64) where a product's inner
+                        * dimension is at most 448 and nrhs >= 8; SIMT FP64 elsewhere      */
+  HPS_GEMM_SIMT = 1    /* SIMT FP64 for every product                                     */
+} hps_gemm;
+
 /* Boundary condition kinds of a rectangular domain's sides (hps_opts.bc_we, bc_sn). */
 typedef enum {
   HPS_BC_DIRICHLET = 0, /* u given (both pairs of sides)                                  */
@@ -114,6 +123,8 @@ typedef struct {
                         * matching west/east nodes when periodic); the root keeps its DtN
                         * map and the solve obtains the boundary values from it; HPS_FP64
                         * handles only; hps_adjoint and hps_solve_noalloc return STATE     */
+  int fp64_gemm;       /* FP64 solve and adjoint products: HPS_GEMM_TENSOR (default) or
+                        * HPS_GEMM_SIMT.  The two agree to FP64 rounding, not bit for bit   */
 } hps_opts;
 
 /* Fills *opts with the defaults above (FP64, q = p - 1, store leaf operators, graphs on,

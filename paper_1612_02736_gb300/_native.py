@@ -18,6 +18,8 @@ HPS_NODES_GAUSS_ALL = 2
 HPS_BC_DIRICHLET = 0
 HPS_BC_PERIODIC = 1
 HPS_BC_NEUMANN = 2
+HPS_GEMM_TENSOR = 0
+HPS_GEMM_SIMT = 1
 
 STATUS_NAMES = {
     0: "OK", 1: "INVALID_ARG", 2: "NOT_ELLIPTIC", 3: "SINGULAR", 4: "OOM", 5: "CUDA",
@@ -37,7 +39,8 @@ class hps_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("q", C.c_int), ("store_leaf_ops", C.c_int),
                 ("ir_tol", C.c_double), ("ir_max_iter", C.c_int), ("fp64_top_levels", C.c_int),
                 ("use_graphs", C.c_int), ("autotune", C.c_int), ("autotune_cache", C.c_char_p),
-                ("shared_leaf", C.c_int), ("bc_we", C.c_int), ("bc_sn", C.c_int)]
+                ("shared_leaf", C.c_int), ("bc_we", C.c_int), ("bc_sn", C.c_int),
+                ("fp64_gemm", C.c_int)]
 
 
 P = C.c_void_p

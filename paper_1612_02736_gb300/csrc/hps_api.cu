@@ -152,6 +152,7 @@ void add_product(std::vector<GemmItem>& out, long long a_base, int lda, int M, i
 struct ItemSet {
   GemmItem* dev = nullptr;
   int n = 0;
+  int maxK = 0;        // largest inner dimension of the items
   double elems = 0.0;  // operator entries streamed by one application
 };
 
@@ -300,6 +301,7 @@ struct hps_handle {
   // chunk whenever a sweep needs them (Sec. 5.4 remark)
   bool econ = false;
   int echunk = 0;                 // leaves per chunk
+  int max_items = 0;              // largest product item set (sizes the tensor-core exponent buffer)
   double* ework = nullptr;        // elimination workspace of one chunk
   int* eperm = nullptr;
   double* epinv = nullptr;
@@ -350,7 +352,11 @@ namespace {
 ItemSet upload_items(hps_handle* h, cudaStream_t s, const std::vector<GemmItem>& v) {
   ItemSet is;
   is.n = (int)v.size();
-  for (const GemmItem& it : v) is.elems += (double)it.M * it.K;
+  for (const GemmItem& it : v) {
+    is.elems += (double)it.M * it.K;
+    is.maxK = std::max(is.maxK, it.K);
+  }
+  h->max_items = std::max(h->max_items, is.n);
   is.dev = v.empty() ? nullptr : upload(h->al, s, v, h->owned);
   return is;
 }
@@ -1462,6 +1468,7 @@ void build_stage(hps_handle* h, const double* coeffs, cudaStream_t s) {
 
 void ensure_ws(hps_handle* h, int nrhs, cudaStream_t s) {
   Workspace& w = h->ws;
+  if (h->opts.fp64_gemm != HPS_GEMM_SIMT) gemm_tc_reserve((long long)h->max_items * ((nrhs + 31) / 32));
   if (w.nrhs >= nrhs) return;
   h->drop_graph();  // a captured sweep points into the old buffers
   for (void* p : w.ptrs) h->al.put(p, s);
@@ -1528,6 +1535,7 @@ ItemSet leaf_range(const hps_handle* h, const ItemSet& is, int l0, int n) {
   const int per = is.n / h->n_leaf;
   r.dev = is.dev + (long long)l0 * per;
   r.n = n * per;
+  r.maxK = is.maxK;
   r.elems = is.elems * (double)n / h->n_leaf;
   return r;
 }
@@ -1547,7 +1555,8 @@ void root_bc_solve(hps_handle* h, const double* ops, const double* f, double* V,
   auto prod = [&](const char* name, const ItemSet& is, const double* B0, const double* B1, double* C,
                   const double* Add, double beta) {
     TIMED(name, 2.0 * is.elems * nrhs, is.elems * 8.0,
-          launch_gemm_items<double, double>(is.dev, is.n, ROWBLK, 0, ops, B0, B1, C, Add, idx, nrhs, beta, s));
+          launch_gemm_items<double, double>(is.dev, is.n, ROWBLK, 0, ops, B0, B1, C, Add, idx, nrhs, beta, s, 0,
+                                            h->opts.fp64_gemm == HPS_GEMM_SIMT ? 0 : is.maxK, h->d_status));
   };
   if (bc.periodic) {
     TIMED("root_bc_rows", 0, 0, launch_row_combine(idx + bc.c_d, bc.Ks, bcw, V, V, nrhs, s));
@@ -1576,9 +1585,12 @@ void solve_pass(hps_handle* h, const TA* ops, const double* f, const TV* g, cons
   auto gemm = [&](const char* step, const ItemSet& is, const TV* B0, const TV* B1, TV* C, const TV* Add,
                   double beta) {
     int bn = 0;
+    // FP64 products on the tensor cores (exact digit slicing) where they apply
+    const int mk = h->opts.fp64_gemm == HPS_GEMM_SIMT ? 0 : is.maxK;
+    const bool tc = std::is_same<TA, double>::value && gemm_tc_eligible(mk, nrhs);
     // right-hand-side tile: tuned for products that overwrite their output (beta = 0), so
     // that a trial run can be repeated; looked up only while the sweep is being captured
-    if (h->opts.autotune && nrhs > 16 && beta == 0.0 && is.n > 0) {
+    if (h->opts.autotune && !tc && nrhs > 16 && beta == 0.0 && is.n > 0) {
       std::vector<int> cands{16, 32};
       if (nrhs > 32) cands.push_back(64);
       const std::string key = "gemm_bn " + std::string(step) + " " + sf + " nrhs" + std::to_string(nrhs) +
@@ -1595,7 +1607,8 @@ void solve_pass(hps_handle* h, const TA* ops, const double* f, const TV* g, cons
       bn = tuned_choice(key, cands, h->tune_path, trial);
     }
     TIMED(("gemm_" + std::string(step) + "_" + sf).c_str(), 2.0 * is.elems * nrhs, is.elems * sizeof(TA),
-          launch_gemm_items<TA, TV>(is.dev, is.n, ROWBLK, 0, ops, B0, B1, C, Add, idx, nrhs, beta, s, bn));
+          launch_gemm_items<TA, TV>(is.dev, is.n, ROWBLK, 0, ops, B0, B1, C, Add, idx, nrhs, beta, s, bn, mk,
+                                    h->d_status));
   };
   auto gemmp = [&](const char* step, const Prod& pr, const TV* B0, TV* C, const TV* Add, double beta) {
     gemm(step, pr.direct, B0, nullptr, C, Add, beta);
@@ -1616,7 +1629,8 @@ void solve_pass(hps_handle* h, const TA* ops, const double* f, const TV* g, cons
         const int l0 = c * h->echunk, n = std::min(h->echunk, h->n_leaf - l0);
         const ItemSet r = leaf_range(h, is, l0, n);
         TIMED(("gemm_" + std::string(step) + "_" + sf).c_str(), 2.0 * r.elems * nrhs, r.elems * sizeof(TA),
-              launch_gemm_items<TA, TV>(r.dev, r.n, ROWBLK, 0, h->eops, B0, B1, C, nullptr, idx, nrhs, 0.0, s));
+              launch_gemm_items<TA, TV>(r.dev, r.n, ROWBLK, 0, h->eops, B0, B1, C, nullptr, idx, nrhs, 0.0, s, 0,
+                                        h->opts.fp64_gemm == HPS_GEMM_SIMT ? 0 : r.maxK, h->d_status));
       }
     }
   };
@@ -1759,6 +1773,7 @@ void hps_opts_default(hps_opts* o) {
   o->shared_leaf = -1;
   o->bc_we = HPS_BC_DIRICHLET;
   o->bc_sn = HPS_BC_DIRICHLET;
+  o->fp64_gemm = HPS_GEMM_TENSOR;
 }
 
 const char* hps_last_error(void) { return g_err.c_str(); }
@@ -2348,9 +2363,11 @@ int hps_adjoint(hps_handle* h, const double* ubar_in, int nrhs, const double* u,
     double* ub = w.ubar;
     CK(cudaMemsetAsync(gb, 0, nuc * sizeof(double), s));
     CK(cudaMemsetAsync(VB, 0, (size_t)h->v_rows * nrhs * sizeof(double), s));
+    const bool simt = h->opts.fp64_gemm == HPS_GEMM_SIMT;
     auto gemmT = [&](const char* step, const ItemSet& is, const double* B0, double* C, double beta) {
       TIMED(("gemmT_" + std::string(step) + "_f64").c_str(), 2.0 * is.elems * nrhs, is.elems * 8.0,
-            launch_gemm_items<double, double>(is.dev, is.n, ROWBLK, 1, ops, B0, nullptr, C, nullptr, idx, nrhs, beta, s));
+            launch_gemm_items<double, double>(is.dev, is.n, ROWBLK, 1, ops, B0, nullptr, C, nullptr, idx, nrhs, beta,
+                                              s, 0, simt ? 0 : is.maxK, h->d_status));
     };
     auto gemmTp = [&](const char* step, const Prod& pr, const double* B0, double* C, double beta) {
       gemmT(step, pr.direct, B0, C, beta);
@@ -2374,12 +2391,12 @@ int hps_adjoint(hps_handle* h, const double* ubar_in, int nrhs, const double* u,
         const ItemSet r = leaf_range(h, is, l0, n);
         TIMED(("gemmT_" + std::string(step) + "_f64").c_str(), 2.0 * r.elems * nrhs, r.elems * 8.0,
               launch_gemm_items<double, double>(r.dev, r.n, ROWBLK, 1, h->eops, B0, nullptr, C, nullptr, idx, nrhs,
-                                                beta, s));
+                                                beta, s, 0, simt ? 0 : r.maxK, h->d_status));
         if (is2) {
           const ItemSet r2 = leaf_range(h, *is2, l0, n);
           TIMED(("gemmT_" + std::string(step) + "_f64").c_str(), 2.0 * r2.elems * nrhs, r2.elems * 8.0,
                 launch_gemm_items<double, double>(r2.dev, r2.n, ROWBLK, 1, h->eops, B0, nullptr, C2, nullptr, idx,
-                                                  nrhs, beta, s));
+                                                  nrhs, beta, s, 0, simt ? 0 : r2.maxK, h->d_status));
         }
       }
     };

@@ -1,0 +1,518 @@
+// FP64 batched gathered products on the tcgen05 tensor cores by exact digit slicing.
+//
+// The solve and the adjoint (Algorithm 2 and its transpose) apply stored dense operators
+// to blocks of gathered vectors: C_rows = beta C_rows + A_item B_gathered (+ Add), one
+// GemmItem per block of at most 64 operator rows.  In FP64 on GB300 these products are
+// bound by the FP64 FFMA pipe.  Here every row of A (over the item's whole K) is scaled by
+// the power of two 2^e_r of its largest entry and written as 9 signed base-128 digits,
+// A_rk = 2^e_r sum_s a_s 2^(1-7s) with |a_s| <= 64, every column of B likewise with 2^f_n and
+// digits b_t.  Digits are integers exactly representable in bf16; a digit product is at
+// most 2^12 in magnitude, so a diagonal d = s + t of the digit-pair products summed over
+// K <= 448 stays below 2^24 and the FP32 accumulation of the tensor core is exact.  One
+// tcgen05.mma per digit pair with s + t <= 10 (45 per K step of 16) accumulates diagonal d
+// in its own TMEM columns; the epilogue combines the 9 diagonals exactly in integers and
+// rounds once to FP64.  The pairs left out weigh below about K 2^-63 max|A_r| max|B_n|,
+// and every digit of A and B is exact to 2^-62 of its row (column) maximum: the product
+// agrees with FP64 arithmetic to its normwise rounding level.
+//
+// Work unit: one item (<= 64 rows, MMA M = 128 with rows 64..127 zero) and 32 right-hand
+// sides (MMA N = 32).  A first kernel writes every unit's 64 row and 32 column exponents;
+// the product kernel's roles (16 warps, one CTA per SM looping over the units):
+//   warps 2, 3, 6, 7, 10, 11, 14  producers: per K step of 16 the digit planes of A (64 x 16)
+//              and B (32 x 16), three stages deep;
+//   warp 15    one thread issues the 45 digit-pair products of each K step into TMEM;
+//   warps 0, 1, 4, 5, 8, 9, 12, 13  epilogue: TMEM lanes 0..63 (warp w reads lane quarter
+//              w % 4), 8 right-hand sides per thread; recombination, beta, Add, scatter.
+// Handoffs are mbarriers with bounded waits; a timeout stops every role (status -1).
+#include <cstdint>
+#include <cstdio>
+
+#include <cuda_bf16.h>
+
+#include "hps_internal.h"
+
+namespace hps {
+
+namespace {
+
+constexpr int GM = 128;     // MMA rows (item rows 0..63, the rest zero)
+constexpr int GR = 64;      // item rows
+constexpr int GN = 32;      // right-hand sides per unit
+constexpr int GS = 9;       // digits per entry
+constexpr int GD = 9;       // kept diagonals d = 2 .. 10
+constexpr int GKMAX = 448;  // longest K with exact FP32 diagonal sums
+constexpr int GST = 3;      // K-step stages
+constexpr int G_THREADS = 512;
+constexpr int G_PROD = 224;  // producer threads (7 warps)
+constexpr int G_EPI = 256;   // epilogue threads (8 warps)
+constexpr long long G_WAIT = 1ll << 26;
+
+struct GStage {
+  unsigned char A[GS][GM * 32];  // K-major planes, 128 rows x 16 k (rows 64..127 stay zero)
+  unsigned char B[GS][GN * 32];  // 32 columns x 16 k
+};
+
+constexpr int GSC = GR + GN;  // exponents per unit: 64 rows, then 32 columns
+
+struct GShared {
+  GStage st[GST];
+  unsigned long long sfull[GST], sfree[GST], tfull, tfree, mdone;
+  unsigned int tmem_base;
+  int abort_flag;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFF) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// byte offset of (row, k) in a K-major plane with 16 k per row (8-row x 16-byte core
+// matrices, LBO 128 bytes along K, SBO 256 bytes between row groups)
+__device__ __forceinline__ int kmaj(int row, int k) {
+  return (row >> 3) * 256 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
+}
+
+__device__ __forceinline__ int bexp(double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7FF); }
+
+__device__ __forceinline__ void mb_init(unsigned long long* b, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count));
+}
+__device__ __forceinline__ void mb_arrive(unsigned long long* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ bool mb_try(unsigned long long* b, int parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait for the phase with the given parity; false on timeout or abort
+__device__ __forceinline__ bool mb_wait(unsigned long long* b, int parity, volatile int* abort_flag, int* status) {
+  for (long long it = 0; it < G_WAIT; ++it) {
+    if (mb_try(b, parity)) return true;
+    if ((it & 255) == 255 && *abort_flag) return false;
+  }
+  *abort_flag = 1;
+  if (status) atomicCAS(status, 0, -1);
+  return false;
+}
+// bounded wait that ignores the abort flag (drains the role's own operations at exit)
+__device__ __forceinline__ void mb_drain(unsigned long long* b, int parity) {
+  for (long long it = 0; it < G_WAIT; ++it)
+    if (mb_try(b, parity)) return;
+}
+// warp-uniform bounded wait: lane 0 waits, the verdict is broadcast
+__device__ __forceinline__ bool warp_wait(unsigned long long* b, int parity, volatile int* abort_flag, int* status) {
+  int ok = 1;
+  if ((threadIdx.x & 31) == 0) ok = mb_wait(b, parity, abort_flag, status) ? 1 : 0;
+  return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
+__device__ __forceinline__ int map_row(const int* __restrict__ idx, int base_or_off, int row_base, int k) {
+  return base_or_off < 0 ? row_base + k : row_base + idx[base_or_off + k];
+}
+
+// bf16 bits of a small integer |a| <= 2^8 exactly: 1.5 2^23 + a is an FP32 number with unit
+// spacing, and a value with at most 8 significant bits keeps them in the upper half.
+__device__ __forceinline__ uint32_t bf16_of_int(int a) {
+  return __float_as_uint(__int_as_float(0x4B400000 + a) - 12582912.0f) >> 16;
+}
+
+// Fixed-point form of x against the row (column) exponent emax: X = x 2^(62 - (emax - 1022))
+// exactly (the 53-bit significand shifted, rounded when shifted right), |X| < 2^62.
+__device__ __forceinline__ long long fixed62(double x, int emax) {
+  const long long bits = __double_as_longlong(x);
+  const int E = (int)((bits >> 52) & 0x7FF);
+  long long X = 0;
+  if (E > 0) {
+    const long long m = (bits & 0xFFFFFFFFFFFFFll) | (1ll << 52);
+    const int sh = E - emax + 9;
+    if (sh >= 0) X = m << sh;
+    else if (sh > -60) X = (m + (1ll << (-sh - 1))) >> (-sh);
+    if (bits < 0) X = -X;
+  }
+  return X;
+}
+
+// The 9 balanced base-128 digit planes of 4 consecutive k of one row (column): one 8-byte
+// store per plane.  Plane s - 1 holds a_s (a_1 the most significant).  With
+// X = sum_(i<8) a'_i 2^(7i) + a_top 2^56 and a'_i in [-64, 63], Y = X + 64 sum_(i<8) 2^(7i)
+// has the base-128 digits a'_i + 64 in its low 56 bits and a_top in the bits above, so
+// every digit is one bit-field extraction.
+__device__ __forceinline__ void write_digits4(const double* v, int emax, unsigned char* plane0, int plane_bytes,
+                                             int off) {
+  constexpr long long kOff = 64ll * ((1ll << 56) - 1) / 127;  // 64 in each of the 8 low digits
+  long long Y[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) Y[q] = fixed62(v[q], emax) + kOff;
+  // the most significant digit (plane 0)
+  {
+    int a[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) a[q] = (int)(Y[q] >> 56);
+    *reinterpret_cast<uint2*>(plane0 + off) = make_uint2(bf16_of_int(a[0]) | (bf16_of_int(a[1]) << 16),
+                                                         bf16_of_int(a[2]) | (bf16_of_int(a[3]) << 16));
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {  // digit a'_i -> plane 8 - i
+    int a[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) a[q] = (int)((unsigned long long)Y[q] >> (7 * i) & 127ull) - 64;
+    *reinterpret_cast<uint2*>(plane0 + (GS - 1 - i) * plane_bytes + off) =
+        make_uint2(bf16_of_int(a[0]) | (bf16_of_int(a[1]) << 16), bf16_of_int(a[2]) | (bf16_of_int(a[3]) << 16));
+  }
+}
+
+// zero digits of 4 k of one row (a row past the item)
+__device__ __forceinline__ void zero_digits4(unsigned char* plane0, int plane_bytes, int off) {
+#pragma unroll
+  for (int s = 0; s < GS; ++s) *reinterpret_cast<uint2*>(plane0 + s * plane_bytes + off) = make_uint2(0u, 0u);
+}
+
+// The product entry from its 9 diagonal sums S_2 .. S_10, each given as the FP32 bit
+// pattern y_d of S_d + 1.5 2^23 (exact, |S_d| < 2^24):
+//   sum_k A_rk B_kn = 2^(er + ec - 2112) I,  I = sum_d S_d 2^(7 (10 - d)),  |I| < 2^81,
+// assembled exactly and rounded once to FP64 with integer operations: to nearest, ties
+// away from zero.  Results below the normal range flush to zero.
+__device__ __forceinline__ double recombine9(const uint32_t* v, int er, int ec) {
+  long long y[GD];
+#pragma unroll
+  for (int d = 0; d < GD; ++d) y[d] = (long long)__float_as_int(__uint_as_float(v[d]) + 12582912.0f);
+  constexpr long long K0 = 0x4B400000ll;
+  // I = H 2^35 + L with the biases removed
+  const long long H = (y[0] << 21) + (y[1] << 14) + (y[2] << 7) + y[3] - K0 * ((1ll << 21) + (1ll << 14) + (1ll << 7) + 1);
+  const long long L = (y[4] << 28) + (y[5] << 21) + (y[6] << 14) + (y[7] << 7) + y[8] -
+                      K0 * ((1ll << 28) + (1ll << 21) + (1ll << 14) + (1ll << 7) + 1);
+  const long long T = (H << 3) + (L >> 32);  // I = T 2^32 + u, 0 <= u < 2^32
+  const unsigned int u = (unsigned int)L;
+  const bool neg = T < 0;
+  const unsigned long long A = neg ? (unsigned long long)(-T) - (u != 0u ? 1ull : 0ull) : (unsigned long long)T;
+  const unsigned int B = neg ? 0u - u : u;
+  // W: the leading 64 bits of |I| when A >= 2^32 (B's top bits shifted in below), else all
+  // of |I|; N: W normalised to a leading bit 63.  Bits shifted out lie below the rounding
+  // position and cannot change a round-half-up decision.
+  const bool big = (A >> 32) != 0;
+  const unsigned long long W = big ? A : ((A << 32) | B);
+  if (W == 0) return 0.0;
+  const int z = __clzll((long long)W);  // 14 .. 31 when big
+  unsigned long long N = W << z;
+  if (big) N |= (unsigned long long)(B >> (32 - z));
+  const int top = (big ? 95 : 63) - z;
+  const unsigned long long mant = (N >> 11) + ((N >> 10) & 1ull);  // 2^52 .. 2^53
+  const int E = top + er + ec - 1089;
+  if (E <= 0) return 0.0;
+  const unsigned long long sgn = (unsigned long long)neg << 63;
+  if (E >= 2047) return __longlong_as_double((long long)(sgn | 0x7FF0000000000000ull));
+  return __longlong_as_double((long long)(sgn + ((unsigned long long)(E - 1) << 52) + mant));
+}
+
+// element k of column n (< nrhs) of the item's gathered B
+__device__ __forceinline__ double b_at(const GemmItem& it, const double* __restrict__ B0, const double* __restrict__ B1,
+                                       const int* __restrict__ idx, int k, int n, int nrhs) {
+  return k < it.kseg ? B0[(long long)map_row(idx, it.b0_idx, it.b0_row, k) * nrhs + n]
+                     : B1[(long long)map_row(idx, it.b1_idx, it.b1_row, k - it.kseg) * nrhs + n];
+}
+
+template <bool TRANS>
+__device__ __forceinline__ double a_at(const GemmItem& it, const double* __restrict__ A, int r, int k) {
+  return TRANS ? A[it.a_off + (long long)k * it.lda + r] : A[it.a_off + (long long)r * it.lda + k];
+}
+
+// Exponent (biased) of the largest entry of every row of A and every column of B, per
+// unit: scales[u][0 .. 63] rows, scales[u][64 .. 95] columns (0 for rows or columns past
+// the item).  256 threads: A rows 4 threads each (k phases), B columns 8 threads each.
+template <bool TRANS>
+__global__ void __launch_bounds__(256) gemm_scales_kernel(const GemmItem* __restrict__ items,
+                                                          const double* __restrict__ A,
+                                                          const double* __restrict__ B0,
+                                                          const double* __restrict__ B1,
+                                                          const int* __restrict__ idx, int nrhs,
+                                                          int* __restrict__ scales) {
+  const int nnb = (nrhs + GN - 1) / GN;
+  const long long u = blockIdx.x;
+  const GemmItem it = items[u / nnb];
+  const int n0 = (int)(u % nnb) * GN;
+  const int t = threadIdx.x;
+  __shared__ int part[256 + 256];
+  {
+    // A: row r = t % 64 (trans: consecutive threads read consecutive addresses), or with
+    // non-transposed storage row r = t / 4 with the 4 threads of a row on interleaved k
+    int r, ph;
+    if (TRANS) { r = t & 63; ph = t >> 6; }
+    else { r = t >> 2; ph = t & 3; }
+    int m = 0;
+    if (r < it.M) {
+#pragma unroll 4
+      for (int k = ph; k < it.K; k += 4) m = max(m, bexp(a_at<TRANS>(it, A, r, k)));
+    }
+    part[TRANS ? ph * 64 + r : r * 4 + ph] = m;
+  }
+  {
+    // B: column n = t % 32, k phase t / 32
+    const int nl = t & 31, ph = t >> 5, n = n0 + nl;
+    int m = 0;
+    if (n < nrhs) {
+#pragma unroll 4
+      for (int k = ph; k < it.K; k += 8) m = max(m, bexp(b_at(it, B0, B1, idx, k, n, nrhs)));
+    }
+    part[256 + ph * 32 + nl] = m;
+  }
+  __syncthreads();
+  int* out = scales + u * GSC;
+  if (t < GR) {
+    int m = 0;
+    for (int ph = 0; ph < 4; ++ph) m = max(m, TRANS ? part[ph * 64 + t] : part[t * 4 + ph]);
+    out[t] = m;
+  } else if (t < GR + GN) {
+    const int nl = t - GR;
+    int m = 0;
+    for (int ph = 0; ph < 8; ++ph) m = max(m, part[256 + ph * 32 + nl]);
+    out[t] = m;
+  }
+}
+
+template <bool TRANS>
+__global__ void __launch_bounds__(G_THREADS, 1) gemm_tc_kernel(const GemmItem* __restrict__ items, int nitems,
+                                                                const double* __restrict__ A,
+                                                                const double* __restrict__ B0,
+                                                                const double* __restrict__ B1, double* __restrict__ C,
+                                                                const double* __restrict__ Add,
+                                                                const int* __restrict__ idx, int nrhs, double beta,
+                                                                const int* __restrict__ scales,
+                                                                int* __restrict__ status) {
+  extern __shared__ __align__(1024) unsigned char g_raw[];
+  GShared& sh = *reinterpret_cast<GShared*>(g_raw);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nnb = (nrhs + GN - 1) / GN;
+  const long long total = (long long)nitems * nnb;
+  // the zero rows 64..127 of every A plane (bytes 2048 .. 4095 of the plane), once
+  for (int e = tid; e < GST * GS * 128; e += G_THREADS) {
+    const int st = e / (GS * 128), s = (e / 128) % GS, c = e % 128;
+    *reinterpret_cast<uint4*>(&sh.st[st].A[s][GR * 32 + c * 16]) = make_uint4(0, 0, 0, 0);
+  }
+  if (tid == 0) {
+    for (int b = 0; b < GST; ++b) {
+      mb_init(&sh.sfull[b], G_PROD);
+      mb_init(&sh.sfree[b], 1);
+    }
+    mb_init(&sh.tfull, 1);
+    mb_init(&sh.tfree, G_EPI);
+    mb_init(&sh.mdone, 1);
+    sh.abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 15) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh.tmem_base)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = sh.tmem_base;
+  volatile int* abort_flag = &sh.abort_flag;
+  const int q4 = warp & 3;
+
+  if (warp == 15) {
+    // ---------------- MMA issue (one thread)
+    if (lane == 0) {
+      const uint32_t idesc =
+          (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(GN >> 3) << 17) | ((uint32_t)(GM >> 4) << 24);
+      long long ks = 0;  // K steps issued so far (stage ks % GST)
+      int nu = 0;
+      bool stop = false;
+      for (long long u = blockIdx.x; u < total && !stop; u += gridDim.x, ++nu) {
+        const GemmItem it = items[u / nnb];
+        const int nk = (it.K + 15) >> 4;
+        if (nu >= 1 && !mb_wait(&sh.tfree, (nu - 1) & 1, abort_flag, status)) break;
+        for (int c = 0; c < nk; ++c, ++ks) {
+          const int st = (int)(ks % GST);
+          if (!mb_wait(&sh.sfull[st], (int)((ks / GST) & 1), abort_flag, status)) {
+            stop = true;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const uint32_t a0 = smem_u32(sh.st[st].A[0]), b0 = smem_u32(sh.st[st].B[0]);
+#pragma unroll 1
+          for (int dg = 2; dg <= GD + 1; ++dg) {
+#pragma unroll 1
+            for (int sa = 1; sa <= GS; ++sa) {
+              const int sb = dg - sa;
+              if (sb < 1 || sb > GS) continue;
+              const uint64_t ad = umma_desc(a0 + (sa - 1) * (GM * 32), 128, 256);
+              const uint64_t bd = umma_desc(b0 + (sb - 1) * (GN * 32), 128, 256);
+              const uint32_t acc = (c > 0 || sa > 1) ? 1u : 0u;
+              asm volatile(
+                  "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                  " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + (uint32_t)((dg - 2) * GN)),
+                  "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+            }
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              smem_u32(&sh.sfree[st])));
+        }
+        if (stop) break;
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(&sh.tfull)));
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(&sh.mdone)));
+      mb_drain(&sh.mdone, 0);
+    }
+  } else if (q4 >= 2) {
+    // ---------------- producers: warps 2, 3, 6, 7, 10, 11, 14 -> producer index 0 .. 223
+    const int pw = (warp >> 2) * 2 + (q4 - 2);  // 0 .. 6
+    const int pt = pw * 32 + lane;
+    long long ks = 0;
+    bool stop = false;
+    for (long long u = blockIdx.x; u < total && !stop; u += gridDim.x) {
+      const GemmItem it = items[u / nnb];
+      const int n0 = (int)(u % nnb) * GN;
+      const int nk = (it.K + 15) >> 4;
+      const int* sc = scales + u * GSC;
+      // digit planes per K step: 64 rows x 4 groups of 4 k for A, 32 columns x 4 groups for B
+      for (int c = 0; c < nk; ++c, ++ks) {
+        const int st = (int)(ks % GST);
+        if (ks >= GST && !warp_wait(&sh.sfree[st], (int)((ks / GST) - 1) & 1, abort_flag, status)) {
+          stop = true;
+          break;
+        }
+        const int k0 = c * 16;
+        for (int task = pt; task < (GR + GN) * 4; task += G_PROD) {
+          const int line = task >> 2, kg = (task & 3) * 4;
+          double v[4];
+          if (line < GR) {
+            if (line >= it.M) {
+              zero_digits4(sh.st[st].A[0], GM * 32, kmaj(line, kg));
+              continue;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const int k = k0 + kg + q;
+              v[q] = k < it.K ? a_at<TRANS>(it, A, line, k) : 0.0;
+            }
+            write_digits4(v, sc[line], sh.st[st].A[0], GM * 32, kmaj(line, kg));
+          } else {
+            const int nl = line - GR, n = n0 + nl;
+            const bool ok = n < nrhs;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const int k = k0 + kg + q;
+              v[q] = (ok && k < it.K) ? b_at(it, B0, B1, idx, k, n, nrhs) : 0.0;
+            }
+            write_digits4(v, sc[line], sh.st[st].B[0], GN * 32, kmaj(nl, kg));
+          }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mb_arrive(&sh.sfull[st]);
+      }
+    }
+  } else {
+    // ---------------- epilogue: warps 0, 1, 4, 5, 8, 9, 12, 13; row = 32 (w % 4) + lane,
+    // right-hand sides 8 g .. 8 g + 7 with g = w / 4
+    const int row = q4 * 32 + lane, g = warp >> 2;
+    int nu = 0;
+    for (long long u = blockIdx.x; u < total; u += gridDim.x, ++nu) {
+      const GemmItem it = items[u / nnb];
+      const int n0 = (int)(u % nnb) * GN;
+      const int* sc = scales + u * GSC;
+      const int er = sc[row];
+      int ec[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) ec[j] = sc[GR + 8 * g + j];
+      if (!warp_wait(&sh.tfull, nu & 1, abort_flag, status)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      uint32_t v[GD][8];
+#pragma unroll
+      for (int d = 0; d < GD; ++d) {
+        const uint32_t addr = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(d * GN + 8 * g);
+        uint32_t* vd = v[d];
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                     : "=r"(vd[0]), "=r"(vd[1]), "=r"(vd[2]), "=r"(vd[3]), "=r"(vd[4]), "=r"(vd[5]), "=r"(vd[6]),
+                       "=r"(vd[7])
+                     : "r"(addr));
+      }
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      mb_arrive(&sh.tfree);  // TMEM read: the next unit's products may start
+      if (row < it.M) {
+        const long long crow = (long long)map_row(idx, it.c_idx, it.c_row, row) * nrhs;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int n = n0 + 8 * g + j;
+          if (n >= nrhs) continue;
+          uint32_t dj[GD];
+#pragma unroll
+          for (int d = 0; d < GD; ++d) dj[d] = v[d][j];
+          double r = recombine9(dj, er, ec[j]);
+          if (it.add_row >= 0) r += Add[(long long)(it.add_row + row) * nrhs + n];
+          C[crow + n] = (beta != 0.0 ? beta * C[crow + n] : 0.0) + r;
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 15) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+
+}  // namespace
+
+bool gemm_tc_eligible(int maxK, int nrhs) { return maxK > 0 && maxK <= GKMAX && nrhs >= 8; }
+
+// exponent buffer, grown outside stream capture (a launch that would need more falls back)
+static int* g_scales = nullptr;
+static long long g_scales_units = 0;
+
+static int g_nsm = 0;
+
+// device properties and the kernels' shared-memory limit, once (outside stream capture)
+static void gemm_tc_init() {
+  if (g_nsm) return;
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaFuncSetAttribute(gemm_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(GShared));
+  cudaFuncSetAttribute(gemm_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(GShared));
+  g_nsm = nsm > 0 ? nsm : 1;
+}
+
+void gemm_tc_reserve(long long units) {
+  gemm_tc_init();
+  if (units <= g_scales_units) return;
+  if (g_scales) cudaFree(g_scales);
+  g_scales = nullptr;
+  g_scales_units = 0;
+  if (cudaMalloc(&g_scales, (size_t)units * GSC * sizeof(int)) == cudaSuccess) g_scales_units = units;
+  else cudaGetLastError();
+}
+
+bool launch_gemm_tc(const GemmItem* items, int nitems, int trans, const double* A, const double* B0,
+                    const double* B1, double* C, const double* Add, const int* idx, int nrhs, double beta,
+                    int* status, cudaStream_t s) {
+  if (nitems <= 0) return true;
+  const long long units = (long long)nitems * ((nrhs + GN - 1) / GN);
+  if (units > g_scales_units || !g_nsm) return false;
+  const int grid = (int)std::min<long long>(g_nsm, units);
+  if (trans) {
+    gemm_scales_kernel<true><<<(unsigned)units, 256, 0, s>>>(items, A, B0, B1, idx, nrhs, g_scales);
+    gemm_tc_kernel<true><<<grid, G_THREADS, sizeof(GShared), s>>>(items, nitems, A, B0, B1, C, Add, idx, nrhs, beta,
+                                                                  g_scales, status);
+  } else {
+    gemm_scales_kernel<false><<<(unsigned)units, 256, 0, s>>>(items, A, B0, B1, idx, nrhs, g_scales);
+    gemm_tc_kernel<false><<<grid, G_THREADS, sizeof(GShared), s>>>(items, nitems, A, B0, B1, C, Add, idx, nrhs, beta,
+                                                                   g_scales, status);
+  }
+  return true;
+}
+
+}  // namespace hps
