@@ -8,10 +8,10 @@
 // A_rk = 2^e_r sum_s a_s 2^(1-7s) with |a_s| <= 64, every column of B likewise with 2^f_n and
 // digits b_t.  Digits are integers exactly representable in bf16; a digit product is at
 // most 2^12 in magnitude, so a diagonal d = s + t of the digit-pair products summed over
-// K <= 448 stays below 2^24 and the FP32 accumulation of the tensor core is exact.  One
-// tcgen05.mma per digit pair with s + t <= 10 (45 per K step of 16) accumulates diagonal d
-// in its own TMEM columns; the epilogue combines the 9 diagonals exactly in integers and
-// rounds once to FP64.  The pairs left out weigh below about K 2^-63 max|A_r| max|B_n|,
+// K <= 448 stays below 2^24 and the FP32 accumulation of the tensor core is exact.  The
+// digit pairs with s + t <= 10 accumulate diagonal d in its own TMEM columns, 10 tcgen05.mma
+// per K step of 16 (one per A digit plane against the B planes side by side); the epilogue
+// combines the 9 diagonals exactly in integers and rounds once to FP64.  The pairs left out weigh below about K 2^-63 max|A_r| max|B_n|,
 // and every digit of A and B is exact to 2^-62 of its row (column) maximum: the product
 // agrees with FP64 arithmetic to its normwise rounding level.
 //
@@ -53,9 +53,13 @@ struct GStage {
 };
 
 constexpr int GSC = GR + GN;  // exponents per unit: 64 rows, then 32 columns
+constexpr int GTASK = (GR + GN) * 4;  // producer tasks per K step: 4 consecutive k of a row or column
+constexpr int GPF = 2;                // K steps the entry copies run ahead of the digits
+constexpr int GRAW = GPF + 1;         // raw entry slots
 
 struct GShared {
   GStage st[GST];
+  double raw[GRAW][GTASK][4];  // the entries of a K step, per producer task
   unsigned long long sfull[GST], sfree[GST], tfull, tfree, mdone;
   unsigned int tmem_base;
   int abort_flag;
@@ -109,6 +113,15 @@ __device__ __forceinline__ void mb_drain(unsigned long long* b, int parity) {
   for (long long it = 0; it < G_WAIT; ++it)
     if (mb_try(b, parity)) return;
 }
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // warp-uniform bounded wait: lane 0 waits, the verdict is broadcast
 __device__ __forceinline__ bool warp_wait(unsigned long long* b, int parity, volatile int* abort_flag, int* status) {
   int ok = 1;
@@ -325,8 +338,8 @@ __global__ void __launch_bounds__(G_THREADS, 1) gemm_tc_kernel(const GemmItem* _
   if (warp == 15) {
     // ---------------- MMA issue (one thread)
     if (lane == 0) {
-      const uint32_t idesc =
-          (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(GN >> 3) << 17) | ((uint32_t)(GM >> 4) << 24);
+      // kind::f16 with bf16 A and B, FP32 accumulators, M = 128; N is set per product
+      const uint32_t idesc0 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(GM >> 4) << 24);
       long long ks = 0;  // K steps issued so far (stage ks % GST)
       int nu = 0;
       bool stop = false;
@@ -342,18 +355,23 @@ __global__ void __launch_bounds__(G_THREADS, 1) gemm_tc_kernel(const GemmItem* _
           }
           asm volatile("tcgen05.fence::after_thread_sync;");
           const uint32_t a0 = smem_u32(sh.st[st].A[0]), b0 = smem_u32(sh.st[st].B[0]);
+          // one product per A digit plane s against the B planes t = 1 .. 10 - s side by side
+          // (contiguous in the K-major layout: N = 32 (10 - s), at most 256 per instruction),
+          // written from TMEM column 32 (s - 1): block t lands on diagonal s + t
 #pragma unroll 1
-          for (int dg = 2; dg <= GD + 1; ++dg) {
+          for (int sa = 1; sa <= GS; ++sa) {
+            const int nt = GD + 1 - sa;
 #pragma unroll 1
-            for (int sa = 1; sa <= GS; ++sa) {
-              const int sb = dg - sa;
-              if (sb < 1 || sb > GS) continue;
+            for (int t0 = 1; t0 <= nt; t0 += 8) {
+              const int cnt = min(8, nt - t0 + 1);
               const uint64_t ad = umma_desc(a0 + (sa - 1) * (GM * 32), 128, 256);
-              const uint64_t bd = umma_desc(b0 + (sb - 1) * (GN * 32), 128, 256);
+              const uint64_t bd = umma_desc(b0 + (t0 - 1) * (GN * 32), 128, 256);
+              const uint32_t idesc = idesc0 | ((uint32_t)((GN * cnt) >> 3) << 17);
               const uint32_t acc = (c > 0 || sa > 1) ? 1u : 0u;
               asm volatile(
                   "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                  " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + (uint32_t)((dg - 2) * GN)),
+                  " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                      tmem + (uint32_t)((sa - 1 + t0 - 1) * GN)),
                   "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
             }
           }
@@ -369,53 +387,91 @@ __global__ void __launch_bounds__(G_THREADS, 1) gemm_tc_kernel(const GemmItem* _
       mb_drain(&sh.mdone, 0);
     }
   } else if (q4 >= 2) {
-    // ---------------- producers: warps 2, 3, 6, 7, 10, 11, 14 -> producer index 0 .. 223
+    // ---------------- producers: warps 2, 3, 6, 7, 10, 11, 14 -> producer index 0 .. 223.
+    // Thread pt owns tasks pt and pt + 224 (4 consecutive k of one row of A or column of B)
+    // of every K step; it copies their entries GPF steps ahead (asynchronously, into its own
+    // slots) and turns them into digits when their step comes, so no thread waits on memory
+    // for the step it is working on.
     const int pw = (warp >> 2) * 2 + (q4 - 2);  // 0 .. 6
     const int pt = pw * 32 + lane;
-    long long ks = 0;
-    bool stop = false;
-    for (long long u = blockIdx.x; u < total && !stop; u += gridDim.x) {
-      const GemmItem it = items[u / nnb];
-      const int n0 = (int)(u % nnb) * GN;
-      const int nk = (it.K + 15) >> 4;
-      const int* sc = scales + u * GSC;
-      // digit planes per K step: 64 rows x 4 groups of 4 k for A, 32 columns x 4 groups for B
-      for (int c = 0; c < nk; ++c, ++ks) {
-        const int st = (int)(ks % GST);
-        if (ks >= GST && !warp_wait(&sh.sfree[st], (int)((ks / GST) - 1) & 1, abort_flag, status)) {
-          stop = true;
-          break;
-        }
-        const int k0 = c * 16;
-        for (int task = pt; task < (GR + GN) * 4; task += G_PROD) {
-          const int line = task >> 2, kg = (task & 3) * 4;
-          double v[4];
+    const int ntask = pt + G_PROD < GTASK ? 2 : 1;
+    // step iterators over (unit, K step) in this block's order: cu/cc current, pu/pc copy
+    long long cu = blockIdx.x, pu = blockIdx.x;
+    int cc = 0, pc = 0;
+    GemmItem cit, pit;
+    if (cu < total) cit = pit = items[cu / nnb];
+    auto advance = [&](long long& uu, int& c, GemmItem& it) {
+      if (++c >= ((it.K + 15) >> 4)) {
+        c = 0;
+        uu += gridDim.x;
+        if (uu < total) it = items[uu / nnb];
+      }
+    };
+    auto issue = [&](long long uu, int c, const GemmItem& it, int slot) {
+      if (uu < total) {
+        const int n0 = (int)(uu % nnb) * GN, k0 = c * 16;
+        for (int j = 0; j < ntask; ++j) {
+          const int task = pt + j * G_PROD, line = task >> 2, kg = (task & 3) * 4;
+          double* dst = sh.raw[slot][task];
           if (line < GR) {
-            if (line >= it.M) {
-              zero_digits4(sh.st[st].A[0], GM * 32, kmaj(line, kg));
-              continue;
-            }
+            if (line >= it.M) continue;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
               const int k = k0 + kg + q;
-              v[q] = k < it.K ? a_at<TRANS>(it, A, line, k) : 0.0;
+              if (k < it.K) {
+                if (TRANS) cp_async8(dst + q, A + it.a_off + (long long)k * it.lda + line);
+                else cp_async8(dst + q, A + it.a_off + (long long)line * it.lda + k);
+              } else {
+                dst[q] = 0.0;
+              }
             }
-            write_digits4(v, sc[line], sh.st[st].A[0], GM * 32, kmaj(line, kg));
           } else {
-            const int nl = line - GR, n = n0 + nl;
-            const bool ok = n < nrhs;
+            const int n = n0 + line - GR;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
               const int k = k0 + kg + q;
-              v[q] = (ok && k < it.K) ? b_at(it, B0, B1, idx, k, n, nrhs) : 0.0;
+              if (n < nrhs && k < it.K) {
+                const double* src = k < it.kseg
+                                        ? B0 + (long long)map_row(idx, it.b0_idx, it.b0_row, k) * nrhs + n
+                                        : B1 + (long long)map_row(idx, it.b1_idx, it.b1_row, k - it.kseg) * nrhs + n;
+                cp_async8(dst + q, src);
+              } else {
+                dst[q] = 0.0;
+              }
             }
-            write_digits4(v, sc[line], sh.st[st].B[0], GN * 32, kmaj(nl, kg));
           }
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mb_arrive(&sh.sfull[st]);
       }
+      cp_commit();  // one group per step, empty past the end, so that the count stays aligned
+    };
+    for (int i = 0; i < GPF; ++i) {
+      issue(pu, pc, pit, i % GRAW);
+      if (pu < total) advance(pu, pc, pit);
     }
+    long long ks = 0;
+    while (cu < total) {
+      issue(pu, pc, pit, (int)((ks + GPF) % GRAW));
+      if (pu < total) advance(pu, pc, pit);
+      cp_wait<GPF>();  // this thread's entries of step ks have landed
+      const int st = (int)(ks % GST), slot = (int)(ks % GRAW);
+      if (ks >= GST && !warp_wait(&sh.sfree[st], (int)((ks / GST) - 1) & 1, abort_flag, status)) break;
+      const int* sc = scales + cu * GSC;
+      for (int j = 0; j < ntask; ++j) {
+        const int task = pt + j * G_PROD, line = task >> 2, kg = (task & 3) * 4;
+        const double* v = sh.raw[slot][task];
+        if (line < GR) {
+          if (line >= cit.M) zero_digits4(sh.st[st].A[0], GM * 32, kmaj(line, kg));
+          else write_digits4(v, sc[line], sh.st[st].A[0], GM * 32, kmaj(line, kg));
+        } else {
+          write_digits4(v, sc[line], sh.st[st].B[0], GN * 32, kmaj(line - GR, kg));
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mb_arrive(&sh.sfull[st]);
+      advance(cu, cc, cit);
+      ++ks;
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");  // copies still in flight land before exit
   } else {
     // ---------------- epilogue: warps 0, 1, 4, 5, 8, 9, 12, 13; row = 32 (w % 4) + lane,
     // right-hand sides 8 g .. 8 g + 7 with g = w / 4

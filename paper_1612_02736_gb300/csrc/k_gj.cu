@@ -285,10 +285,10 @@ __global__ void __launch_bounds__(256) gj_update_kernel(const GJDesc* __restrict
 // base-256 digits, W_rt = 2^e_r sum_s a_s 2^(1-8s), |a_s| <= 128, each digit an integer
 // exactly representable in bf16; every column of Prow likewise with 2^f_c and digits b_t.
 // Digit products are integers below 2^14 and a diagonal d = s + t sums at most 8 x 16 of
-// them, so the FP32 accumulation of the tensor core is exact.  One tcgen05.mma per digit
-// pair with s + t <= 9 (36 per tile) accumulates diagonal d in its own TMEM columns; the
-// epilogue combines the diagonals exactly in 128-bit integers, normalises, converts once to FP64 and
-// scales by a power of two.  The neglected terms are below about 2^-64 x 16 x max|W_r| x
+// them, so the FP32 accumulation of the tensor core is exact.  The digit pairs with
+// s + t <= 9 accumulate diagonal d in its own TMEM columns, 8 tcgen05.mma per tile (one per
+// W digit plane against the Prow planes side by side); the epilogue combines the diagonals
+// exactly in integers and rounds once to FP64.  The neglected terms are below about 2^-64 x 16 x max|W_r| x
 // max|P_c|: on the leaf and merge eliminations that normwise bound can exceed the
 // elementwise FP64 bound 2^-53 sum_t |W_rt| |P_tc| by up to 1e5 (measured on leaf panels),
 // which 7 digits (2^-56) did not absorb and 8 digits do.  The kernel is then bound by
@@ -353,7 +353,7 @@ __device__ __forceinline__ void write_digits(long long bits, int emax, unsigned 
 // tiles at once:
 //   warps 0-3  (producers): load the tile's W rows and pivot-row columns, write their
 //              digit planes and scales into buffer k % 2;
-//   warp 4     (one thread): issue the 36 digit-pair products of tile k into TMEM buffer
+//   warp 4     (one thread): issue the digit-pair products of tile k into TMEM buffer
 //              k % 2 and commit them to an mbarrier;
 //   warps 8-15 (epilogue): read TMEM (warp w reads lanes 32 (w % 4) ..., columns
 //              16 ((w - 8) / 4) ...), recombine, update the matrix through a staging
@@ -508,8 +508,7 @@ __global__ void __launch_bounds__(PT_THREADS, 1) gj_update_tcp_kernel(
   } else if (warp == 4) {
     // ---------------- MMA issue (one thread)
     if (lane == 0) {
-      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TCN >> 3) << 17) |
-                             ((uint32_t)(TCM >> 4) << 24);
+      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TCM >> 4) << 24);  // N per product
       int k = 0;
       for (long long t = blockIdx.x; t < total; t += gridDim.x) {
         GJDesc md;
@@ -520,19 +519,18 @@ __global__ void __launch_bounds__(PT_THREADS, 1) gj_update_tcp_kernel(
         asm volatile("tcgen05.fence::after_thread_sync;");
         const uint32_t a0 = smem_u32(sh.planes[buf]), b0 = a0 + TCS * TCM * 32;
         const uint32_t tb = tmem + (uint32_t)(buf * 256);
-        for (int dg = 2; dg <= TCKEEP; ++dg) {
-          uint32_t acc = 0;
-          for (int sa = 1; sa <= TCS; ++sa) {
-            const int sb = dg - sa;
-            if (sb < 1 || sb > TCS) continue;
-            const uint64_t ad = umma_desc(a0 + (sa - 1) * (TCM * 32), 128, 256);
-            const uint64_t bd = umma_desc(b0 + (sb - 1) * (TCN * 32), 128, 256);
-            asm volatile(
-                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tb + (uint32_t)((dg - 2) * TCN)),
-                "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-            acc = 1;
-          }
+        // one product per A digit plane s against the B planes t = 1 .. 9 - s side by side
+        // (contiguous in the K-major layout, N = 32 (9 - s)), written from TMEM column
+        // 32 (s - 1): block t lands on diagonal s + t
+        for (int sa = 1; sa < TCKEEP; ++sa) {
+          const uint64_t ad = umma_desc(a0 + (sa - 1) * (TCM * 32), 128, 256);
+          const uint64_t bd = umma_desc(b0, 128, 256);
+          const uint32_t idn = idesc | ((uint32_t)((TCN * (TCKEEP - sa)) >> 3) << 17);
+          const uint32_t acc = sa > 1 ? 1u : 0u;
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tb + (uint32_t)((sa - 1) * TCN)),
+              "l"(ad), "l"(bd), "r"(idn), "r"(acc));
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
             smem_u32(&sh.done[buf])));
@@ -645,7 +643,7 @@ __global__ void __launch_bounds__(PT_THREADS, 1) gj_update_tcp_kernel(
 // Roles (24 warps):
 //   warps 0-3   producers: per unit, the W rows -> A digit planes (buffer u % 2) and row
 //               scales; per tile k, warp k % 4 forms the pivot-row column digits (B slot k % 4);
-//   warp 4      one thread issues the 36 digit-pair products of tile k into TMEM buffer k % 2;
+//   warp 4      one thread issues the digit-pair products of tile k into TMEM buffer k % 2;
 //   warp 5      loader: tile k's rows into C buffer k % 3;
 //   warps 8-23  epilogue (4 warps per TMEM lane quarter, 8 columns each): TMEM -> exact
 //               recombination, rounded once to FP64 with integer operations -> + old value
@@ -722,48 +720,53 @@ __device__ __forceinline__ uint32_t bf16_of_int(int a) {
 }
 
 // The 8 balanced base-256 digit planes of one K-major row of 16 values (a row of W, or a
-// column of Prow), written as two 16-byte stores per plane.
+// column of Prow), one 16-byte store per plane and half row.  The loop over planes stays
+// rolled: the kernel's roles share each SM's instruction cache.
 __device__ __forceinline__ void write_digit_row(const long long* w, int emax, unsigned char* base, int plane_bytes,
                                                 int row) {
-  long long X[16];
-#pragma unroll
-  for (int q = 0; q < 16; ++q) X[q] = fixed_point(w[q], emax);
   unsigned char* p0 = base + kmaj16(row, 0);
 #pragma unroll
-  for (int s = TCS - 1; s >= 0; --s) {
-    uint32_t pk[8];
+  for (int hq = 0; hq < 2; ++hq) {
+    long long X[8];
 #pragma unroll
-    for (int q = 0; q < 16; q += 2) {
-      int a[2];
+    for (int q = 0; q < 8; ++q) X[q] = fixed_point(w[8 * hq + q], emax);
+#pragma unroll 1
+    for (int s = TCS - 1; s >= 0; --s) {
+      uint32_t pk[4];
 #pragma unroll
-      for (int t = 0; t < 2; ++t) {
-        if (s > 0) {
-          a[t] = (int)(((unsigned int)X[q + t] + 128u) & 255u) - 128;
+      for (int q = 0; q < 8; q += 2) {
+        int a[2];
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+          // the lowest remaining digit in [-128, 127] (the last, most significant one keeps
+          // the remainder, |a| <= 128)
+          a[t] = s > 0 ? (int)(((unsigned int)X[q + t] + 128u) & 255u) - 128 : (int)X[q + t];
           X[q + t] = (X[q + t] - a[t]) >> 8;
-        } else {
-          a[t] = (int)X[q + t];
         }
+        pk[q >> 1] = bf16_of_int(a[0]) | (bf16_of_int(a[1]) << 16);
       }
-      pk[q >> 1] = bf16_of_int(a[0]) | (bf16_of_int(a[1]) << 16);
+      *reinterpret_cast<uint4*>(p0 + s * plane_bytes + 128 * hq) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
     }
-    *reinterpret_cast<uint4*>(p0 + s * plane_bytes) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-    *reinterpret_cast<uint4*>(p0 + s * plane_bytes + 128) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
   }
 }
 
-// FP32 accumulator holding an exact integer |v| <= 2^22 -> that integer (same unit-spacing
-// argument as bf16_of_int)
-__device__ __forceinline__ int int_of_acc(uint32_t v) {
-  return __float_as_int(__uint_as_float(v) + 12582912.0f) - 0x4B400000;
+// FP32 accumulator holding an exact integer |v| <= 2^22 -> that integer plus 0x4B400000
+// (same unit-spacing argument as bf16_of_int; the bias is removed in recombine)
+__device__ __forceinline__ int biased_int_of_acc(uint32_t v) {
+  return __float_as_int(__uint_as_float(v) + 12582912.0f);
 }
 
-// The product entry from its 8 diagonal sums S_2 .. S_9 (s[0] .. s[7]):
+// The product entry from its 8 diagonal sums S_2 .. S_9 (s[0] .. s[7], each biased by
+// 0x4B400000 as biased_int_of_acc leaves it):
 //   W_r Prow_c = 2^(er + ec - 2114) I,  I = sum_d S_d 2^(8 (9 - d)),
 // with I assembled exactly (|I| < 2^80) and rounded once to FP64 with integer operations
 // (the FP64 pipe is the scarce unit): to nearest, ties away from zero, so the error is at
 // most half a unit in the last place.  Results below the normal range flush to zero.
 __device__ __forceinline__ double recombine(const int* s, int er, int ec) {
-  const int p01 = s[0] * 256 + s[1], p23 = s[2] * 256 + s[3], p45 = s[4] * 256 + s[5], p67 = s[6] * 256 + s[7];
+  // pairs S_d 2^8 + S_(d+1) (|.| < 2^31), the biases removed modulo 2^32
+  constexpr unsigned int kBias = 257u * 0x4B400000u;
+  auto pair = [](int hi, int lo) { return (int)((unsigned int)hi * 256u + (unsigned int)lo - kBias); };
+  const int p01 = pair(s[0], s[1]), p23 = pair(s[2], s[3]), p45 = pair(s[4], s[5]), p67 = pair(s[6], s[7]);
   const long long H = (long long)p01 * 65536 + p23;  // I = H 2^32 + L
   const long long L = (long long)p45 * 65536 + p67;
   const long long T = H + (L >> 32);  // I = T 2^32 + u, 0 <= u < 2^32
@@ -930,8 +933,7 @@ __global__ void __launch_bounds__(PS_THREADS, 1) gj_update_tcs_kernel(
   } else if (warp == 4) {
     // ---------------- MMA issue (one thread)
     if (lane == 0) {
-      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TCN >> 3) << 17) |
-                             ((uint32_t)(TCM >> 4) << 24);
+      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TCM >> 4) << 24);  // N per product
       long long k = 0;
       int ua = 0;
       bool stop = false;
@@ -952,19 +954,19 @@ __global__ void __launch_bounds__(PS_THREADS, 1) gj_update_tcs_kernel(
           asm volatile("tcgen05.fence::after_thread_sync;");
           const uint32_t b0 = smem_u32(sh.B[bs]);
           const uint32_t tcol = tmem + (uint32_t)(tb * 256);
-          for (int dg = 2; dg <= TCKEEP; ++dg) {
-            uint32_t acc = 0;
-            for (int sa = 1; sa <= TCS; ++sa) {
-              const int sb = dg - sa;
-              if (sb < 1 || sb > TCS) continue;
-              const uint64_t ad = umma_desc(a0 + (sa - 1) * (TCM * 32), 128, 256);
-              const uint64_t bd = umma_desc(b0 + (sb - 1) * (TCN * 32), 128, 256);
-              asm volatile(
-                  "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                  " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tcol + (uint32_t)((dg - 2) * TCN)),
-                  "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-              acc = 1;
-            }
+          // one product per A digit plane s against the B planes t = 1 .. 9 - s side by side
+          // (contiguous in the K-major layout, N = 32 (9 - s)), written from TMEM column
+          // 32 (s - 1): block t lands on diagonal s + t
+#pragma unroll 1
+          for (int sa = 1; sa < TCKEEP; ++sa) {
+            const uint64_t ad = umma_desc(a0 + (sa - 1) * (TCM * 32), 128, 256);
+            const uint64_t bd = umma_desc(b0, 128, 256);
+            const uint32_t idn = idesc | ((uint32_t)((TCN * (TCKEEP - sa)) >> 3) << 17);
+            const uint32_t acc = sa > 1 ? 1u : 0u;
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tcol + (uint32_t)((sa - 1) * TCN)),
+                "l"(ad), "l"(bd), "r"(idn), "r"(acc));
           }
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
               smem_u32(&sh.tfull[tb])));
@@ -1072,7 +1074,7 @@ __global__ void __launch_bounds__(PS_THREADS, 1) gj_update_tcs_kernel(
         const double* crow = &sh.C[cb][e][0];
         const unsigned char* cbyte = reinterpret_cast<const unsigned char*>(&sh.C[cb][0][0]);
         const int col0 = j * TCN;
-#pragma unroll
+#pragma unroll 1
         for (int bt = 0; bt < 2; ++bt) {
           const int jb = 8 * cg + 4 * bt;
           uint32_t v[TCKEEP - 1][4];
@@ -1113,7 +1115,7 @@ __global__ void __launch_bounds__(PS_THREADS, 1) gj_update_tcs_kernel(
           for (int q = 0; q < 4; ++q) {
             int s[TCKEEP - 1];
 #pragma unroll
-            for (int dg = 0; dg < TCKEEP - 1; ++dg) s[dg] = int_of_acc(v[dg][q]);
+            for (int dg = 0; dg < TCKEEP - 1; ++dg) s[dg] = biased_int_of_acc(v[dg][q]);
             const int col = col0 + jb + q;
             up[q] = rowok && col < R && !(col >= c0 && col < c0 + nb);
             nv[q] = (isp ? 0.0 : ov[q]) + recombine(s, er, ec[q]);
