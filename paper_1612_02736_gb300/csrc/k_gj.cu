@@ -63,8 +63,11 @@ __global__ void __launch_bounds__(256) gj_panel_kernel(const GJDesc* __restrict_
   const int nrows = md.K - c0;
   const int tid = threadIdx.x, bs = blockDim.x;
   extern __shared__ __align__(16) unsigned char smraw[];
-  T* P = reinterpret_cast<T*>(smraw);                    // nrows x nb
-  int* pr = reinterpret_cast<int*>(P + (size_t)nrows * nb);  // nrows
+  // the panel, nrows x nb with row pitch nb + 1 (odd): a warp walking down a column hits
+  // distinct banks
+  const int ldp = nb + 1;
+  T* P = reinterpret_cast<T*>(smraw);
+  int* pr = reinterpret_cast<int*>(P + (size_t)nrows * ldp);  // nrows
   __shared__ T red_v[32];
   __shared__ int red_i[32];
   __shared__ T colscale[NBMAX];
@@ -76,14 +79,14 @@ __global__ void __launch_bounds__(256) gj_panel_kernel(const GJDesc* __restrict_
   __syncthreads();
   for (int e = tid; e < nrows * nb; e += bs) {
     const int i = e / nb, j = e - (e / nb) * nb;
-    P[e] = M[(long long)pr[i] * R + c0 + j];
+    P[i * ldp + j] = M[(long long)pr[i] * R + c0 + j];
   }
   __syncthreads();
   // column scales for the breakdown test: one warp per column, lanes stride the rows
   const int lane = tid & 31, warp = tid >> 5, nwarp = bs >> 5;
   for (int j = warp; j < nb; j += nwarp) {
     T mx = T(0);
-    for (int i = lane; i < nrows; i += 32) mx = fmax(mx, tabs(P[i * nb + j]));
+    for (int i = lane; i < nrows; i += 32) mx = fmax(mx, tabs(P[i * ldp + j]));
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if (lane == 0) colscale[j] = mx;
   }
@@ -92,7 +95,7 @@ __global__ void __launch_bounds__(256) gj_panel_kernel(const GJDesc* __restrict_
     T best = T(-1);
     int bi = nrows;
     for (int i = j + tid; i < nrows; i += bs) {
-      const T v = tabs(P[i * nb + j]);
+      const T v = tabs(P[i * ldp + j]);
       if (v > best) { best = v; bi = i; }
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -117,19 +120,19 @@ __global__ void __launch_bounds__(256) gj_panel_kernel(const GJDesc* __restrict_
     __syncthreads();
     const int r = piv_row;
     if (r != j && tid < nb) {
-      const T t = P[j * nb + tid]; P[j * nb + tid] = P[r * nb + tid]; P[r * nb + tid] = t;
+      const T t = P[j * ldp + tid]; P[j * ldp + tid] = P[r * ldp + tid]; P[r * ldp + tid] = t;
     }
     __syncthreads();
     if (piv_null) {  // null direction: zero pivot, so no multipliers and a zero Pinv row
-      if (tid == 0) P[j * nb + j] = T(0);
+      if (tid == 0) P[j * ldp + j] = T(0);
       __syncthreads();
     }
-    const T pv = P[j * nb + j];
+    const T pv = P[j * ldp + j];
     const T inv = (pv != T(0)) ? T(1) / pv : T(0);
     for (int i = j + 1 + tid; i < nrows; i += bs) {
-      const T l = P[i * nb + j] * inv;
-      P[i * nb + j] = l;
-      for (int c = j + 1; c < nb; ++c) P[i * nb + c] -= l * P[j * nb + c];
+      const T l = P[i * ldp + j] * inv;
+      P[i * ldp + j] = l;
+      for (int c = j + 1; c < nb; ++c) P[i * ldp + c] -= l * P[j * ldp + c];
     }
     __syncthreads();
   }
@@ -138,13 +141,13 @@ __global__ void __launch_bounds__(256) gj_panel_kernel(const GJDesc* __restrict_
     T y[NBMAX];
     for (int k = 0; k < nb; ++k) {
       T s = (k == tid) ? T(1) : T(0);
-      for (int l = 0; l < k; ++l) s -= P[k * nb + l] * y[l];
+      for (int l = 0; l < k; ++l) s -= P[k * ldp + l] * y[l];
       y[k] = s;
     }
     for (int k = nb - 1; k >= 0; --k) {
       T s = y[k];
-      for (int l = k + 1; l < nb; ++l) s -= P[k * nb + l] * y[l];
-      const T pv = P[k * nb + k];
+      for (int l = k + 1; l < nb; ++l) s -= P[k * ldp + l] * y[l];
+      const T pv = P[k * ldp + k];
       y[k] = (pv != T(0)) ? s / pv : T(0);
     }
     T* Pi = pinv + (long long)blockIdx.x * NBMAX * NBMAX;
@@ -1201,7 +1204,7 @@ void launch_gj_panel(const GJDesc* d, int nmat, int maxK, T* work, int* perm, T*
                      int nb, int* status, cudaStream_t s) {
   const int nrows = maxK - c0;
   if (nrows <= 0) return;
-  const size_t smem = (size_t)nrows * nb * sizeof(T) + (size_t)nrows * sizeof(int) + 16;
+  const size_t smem = (size_t)nrows * (nb + 1) * sizeof(T) + (size_t)nrows * sizeof(int) + 16;
   static size_t configured = 0;
   if (smem > 48 * 1024 && smem > configured) {
     cudaFuncSetAttribute(gj_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
