@@ -52,11 +52,29 @@ __global__ void gj_init_kernel(const GJDesc* __restrict__ d, int* __restrict__ p
   for (int i = threadIdx.x; i < md.K; i += blockDim.x) perm[md.perm_off + i] = i;
 }
 
+// Magnitude order of floating-point values as integers: the bit pattern of |v| read as an
+// unsigned integer is monotone in |v| (finite values), so pivot searches run on the integer
+// pipe instead of the scarce FP64 one.
+template <typename T> struct KeyOf;
+template <> struct KeyOf<double> {
+  using type = unsigned long long;
+  static __device__ __forceinline__ type key(double v) {
+    return (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
+  }
+  static __device__ __forceinline__ double val(type k) { return __longlong_as_double((long long)k); }
+};
+template <> struct KeyOf<float> {
+  using type = unsigned int;
+  static __device__ __forceinline__ type key(float v) { return __float_as_uint(v) & 0x7FFFFFFFu; }
+  static __device__ __forceinline__ float val(type k) { return __uint_as_float(k); }
+};
+
 template <typename T>
 __global__ void __launch_bounds__(256) gj_panel_kernel(const GJDesc* __restrict__ d,
                                                        T* __restrict__ work, int* __restrict__ perm,
                                                        T* __restrict__ pinv, int c0, int nb_req,
                                                        int* __restrict__ status) {
+  using Key = typename KeyOf<T>::type;
   const GJDesc md = d[blockIdx.x];
   if (c0 >= md.K) return;
   const int nb = min(nb_req, md.K - c0);
@@ -68,9 +86,10 @@ __global__ void __launch_bounds__(256) gj_panel_kernel(const GJDesc* __restrict_
   const int ldp = nb + 1;
   T* P = reinterpret_cast<T*>(smraw);
   int* pr = reinterpret_cast<int*>(P + (size_t)nrows * ldp);  // nrows
-  __shared__ T red_v[32];
+  __shared__ Key red_v[32];
   __shared__ int red_i[32];
   __shared__ T colscale[NBMAX];
+  __shared__ T piv_inv;
   __shared__ int piv_row, piv_null;
   T* M = work + md.off;
   const int R = md.R;
@@ -85,31 +104,36 @@ __global__ void __launch_bounds__(256) gj_panel_kernel(const GJDesc* __restrict_
   // column scales for the breakdown test: one warp per column, lanes stride the rows
   const int lane = tid & 31, warp = tid >> 5, nwarp = bs >> 5;
   for (int j = warp; j < nb; j += nwarp) {
-    T mx = T(0);
-    for (int i = lane; i < nrows; i += 32) mx = fmax(mx, tabs(P[i * ldp + j]));
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (lane == 0) colscale[j] = mx;
+    Key mx = 0;
+    for (int i = lane; i < nrows; i += 32) mx = max(mx, KeyOf<T>::key(P[i * ldp + j]));
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, (Key)__shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) colscale[j] = KeyOf<T>::val(mx);
   }
   __syncthreads();
   for (int j = 0; j < nb; ++j) {
-    T best = T(-1);
+    // pivot: the largest |P_ij|, i >= j, the first row among equals
+    Key best = 0;
     int bi = nrows;
     for (int i = j + tid; i < nrows; i += bs) {
-      const T v = tabs(P[i * ldp + j]);
-      if (v > best) { best = v; bi = i; }
+      const Key v = KeyOf<T>::key(P[i * ldp + j]);
+      if (bi == nrows || v > best) { best = v; bi = i; }
     }
     for (int o = 16; o > 0; o >>= 1) {
-      const T ov = __shfl_down_sync(0xffffffffu, best, o);
+      const Key ov = __shfl_down_sync(0xffffffffu, best, o);
       const int oi = __shfl_down_sync(0xffffffffu, bi, o);
-      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+      if (oi < nrows && (bi == nrows || ov > best || (ov == best && oi < bi))) { best = ov; bi = oi; }
     }
     if (lane == 0) { red_v[warp] = best; red_i[warp] = bi; }
     __syncthreads();
     if (tid == 0) {
-      T b = red_v[0];
+      Key kb = red_v[0];
       int ib = red_i[0];
       for (int w = 1; w < nwarp; ++w)
-        if (red_v[w] > b || (red_v[w] == b && red_i[w] < ib)) { b = red_v[w]; ib = red_i[w]; }
+        if (red_i[w] < nrows && (ib == nrows || red_v[w] > kb || (red_v[w] == kb && red_i[w] < ib))) {
+          kb = red_v[w];
+          ib = red_i[w];
+        }
+      const T b = ib < nrows ? KeyOf<T>::val(kb) : T(-1);
       const T tiny = T(64) * Eps<T>::v * colscale[j];
       piv_null = md.null_tol > 0.f && md.null_scale && !(b > (T)(md.null_tol * *md.null_scale));
       if (!piv_null && !(b > tiny) && status) atomicCAS(status, 0, md.box + 1);
@@ -123,12 +147,15 @@ __global__ void __launch_bounds__(256) gj_panel_kernel(const GJDesc* __restrict_
       const T t = P[j * ldp + tid]; P[j * ldp + tid] = P[r * ldp + tid]; P[r * ldp + tid] = t;
     }
     __syncthreads();
-    if (piv_null) {  // null direction: zero pivot, so no multipliers and a zero Pinv row
-      if (tid == 0) P[j * ldp + j] = T(0);
-      __syncthreads();
+    // one reciprocal for the block (null direction: zero pivot, so no multipliers and a
+    // zero Pinv row)
+    if (tid == 0) {
+      if (piv_null) P[j * ldp + j] = T(0);
+      const T pv = P[j * ldp + j];
+      piv_inv = (pv != T(0)) ? T(1) / pv : T(0);
     }
-    const T pv = P[j * ldp + j];
-    const T inv = (pv != T(0)) ? T(1) / pv : T(0);
+    __syncthreads();
+    const T inv = piv_inv;
     for (int i = j + 1 + tid; i < nrows; i += bs) {
       const T l = P[i * ldp + j] * inv;
       P[i * ldp + j] = l;
