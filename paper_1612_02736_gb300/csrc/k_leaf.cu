@@ -40,6 +40,8 @@ __global__ void __launch_bounds__(256) leaf_assemble_kernel(
   double* sLl = sLs + p * q;                       // q * p
   double* sDL = sLl + q * p;                       // p * q
   int* sci = reinterpret_cast<int*>(sDL + p * q);  // m
+  int* sjx = sci + m;                              // m: x index of interior node sci[j]
+  int* sjy = sjx + m;                              // m: y index
   const int tid = threadIdx.x, bs = blockDim.x;
   for (int e = tid; e < 6 * pp; e += bs) {
     const int k = e / pp, n = e - (e / pp) * pp;
@@ -47,51 +49,59 @@ __global__ void __launch_bounds__(256) leaf_assemble_kernel(
   }
   for (int e = tid; e < pp; e += bs) { sD[e] = tb.D[e]; sD2[e] = tb.D2[e]; }
   for (int e = tid; e < p * q; e += bs) { sLs[e] = tb.Ls[e]; sLl[e] = tb.Lloc[e]; sDL[e] = tb.DLs[e]; }
-  for (int e = tid; e < m; e += bs) sci[e] = tb.ci[e];
+  for (int e = tid; e < m; e += bs) {
+    const int n = tb.ci[e];
+    sci[e] = n;
+    sjx[e] = n % p;
+    sjy[e] = n / p;
+  }
   __syncthreads();
   const double sx = 2.0 / hxy[2 * lf], sy = 2.0 / hxy[2 * lf + 1];
   T* M = work + (long long)blockIdx.x * mat_stride;
-  const long long total = (long long)R * R;
-  for (long long e = tid; e < total; e += bs) {
-    const int row = (int)(e / R);
-    const int col = (int)(e - (long long)row * R);
-    double v = 0.0;
+  // one warp per row (the row's coefficients and factors once), lanes along the row
+  const int lane = tid & 31, nwarp = bs >> 5;
+  for (int row = tid >> 5; row < R; row += nwarp) {
+    T* Mr = M + (long long)row * R;
     if (row < m) {
-      const int ni = sci[row];
-      const int ix = ni % p, iy = ni / p;
+      const int ni = sci[row], ix = sjx[row], iy = sjy[row];
       const double c11 = cf[ni], c12 = cf[pp + ni], c22 = cf[2 * pp + ni];
       const double c1 = cf[3 * pp + ni], c2 = cf[4 * pp + ni], c0 = cf[5 * pp + ni];
-      // A[ni][(jx, jy)] for the operator of Sec. 3.2
-      auto Aent = [&](int jx, int jy) -> double {
-        double a = -2.0 * c12 * sx * sy * sD[ix * p + jx] * sD[iy * p + jy];
-        if (iy == jy) a += -c11 * sx * sx * sD2[ix * p + jx] + c1 * sx * sD[ix * p + jx];
-        if (ix == jx) a += -c22 * sy * sy * sD2[iy * p + jy] + c2 * sy * sD[iy * p + jy];
+      // A[ni][(jx, jy)] for the operator of Sec. 3.2:
+      //   al Dx[ix][jx] Dy[iy][jy] + [iy = jy] (bx D2[ix][jx] + gx D[ix][jx])
+      //   + [ix = jx] (by D2[iy][jy] + gy D[iy][jy]) + [ix = jx, iy = jy] c0
+      const double al = -2.0 * c12 * sx * sy;
+      const double bx = -c11 * sx * sx, gx = c1 * sx, by = -c22 * sy * sy, gy = c2 * sy;
+      const double* Dix = sD + ix * p;
+      const double* Diy = sD + iy * p;
+      const double* D2ix = sD2 + ix * p;
+      const double* D2iy = sD2 + iy * p;
+      for (int col = lane; col < m; col += 32) {
+        const int jx = sjx[col], jy = sjy[col];
+        double a = al * Dix[jx] * Diy[jy];
+        if (iy == jy) a += bx * D2ix[jx] + gx * Dix[jx];
+        if (ix == jx) a += by * D2iy[jy] + gy * Diy[jy];
         if (ix == jx && iy == jy) a += c0;
-        return a;
-      };
-      if (col < m) {
-        const int nj = sci[col];
-        v = Aent(nj % p, nj / p);
-      } else {
-        const int g = col - m, s = g / q, a = g - (g / q) * q;
+        Mr[col] = (T)a;
+      }
+      for (int g = lane; g < nq; g += 32) {
+        const int s = g / q, a = g - s * q;
+        double v;
         if (s == 0 || s == 2) {  // horizontal side jy = 0 or p-1: node (ix, jy) on the row's column
           const int jy = (s == 0) ? 0 : p - 1;
-          const double dy = sD[iy * p + jy];
-          v = -2.0 * c12 * sx * sy * dy * sDL[ix * q + a] +
-              (-c22 * sy * sy * sD2[iy * p + jy] + c2 * sy * dy) * sLs[ix * q + a];
+          const double dy = Diy[jy];
+          v = al * dy * sDL[ix * q + a] + (by * D2iy[jy] + gy * dy) * sLs[ix * q + a];
         } else {  // vertical side jx = p-1 or 0: node (jx, iy) on the row's line
           const int jx = (s == 1) ? p - 1 : 0;
-          const double dx = sD[ix * p + jx];
-          v = -2.0 * c12 * sx * sy * dx * sDL[iy * q + a] +
-              (-c11 * sx * sx * sD2[ix * p + jx] + c1 * sx * dx) * sLs[iy * q + a];
+          const double dx = Dix[jx];
+          v = al * dx * sDL[iy * q + a] + (bx * D2ix[jx] + gx * dx) * sLs[iy * q + a];
         }
+        Mr[m + g] = (T)v;
       }
     } else {
       const int g = row - m, s = g / q, a = g - (g / q) * q;
       const double sc = (s == 0 || s == 2) ? sy : sx;
-      if (col < m) {
-        const int nj = sci[col];
-        const int nx = nj % p, ny = nj / p;
+      for (int col = lane; col < m; col += 32) {
+        const int nx = sjx[col], ny = sjy[col];
         double r;
         switch (s) {
           case 0: r = sLl[a * p + nx] * sD[0 * p + ny]; break;
@@ -99,12 +109,10 @@ __global__ void __launch_bounds__(256) leaf_assemble_kernel(
           case 2: r = sLl[a * p + nx] * sD[(p - 1) * p + ny]; break;
           default: r = sLl[a * p + ny] * sD[0 * p + nx]; break;
         }
-        v = sc * r;
-      } else {
-        v = sc * tb.DceL[(long long)g * nq + (col - m)];
+        Mr[col] = (T)(sc * r);
       }
+      for (int c = lane; c < nq; c += 32) Mr[m + c] = (T)(sc * tb.DceL[(long long)g * nq + c]);
     }
-    M[e] = (T)v;
   }
 }
 
@@ -137,7 +145,7 @@ void launch_leaf_assemble(const double* coeffs, long long n_leaf_total, int leaf
                           const double* hxy, int p, int q, const LeafTablesDev& tb, T* work,
                           long long mat_stride, cudaStream_t s) {
   const int pp = p * p, m = (p - 2) * (p - 2);
-  const size_t smem = (size_t)(6 * pp + 2 * pp + 3 * p * q) * sizeof(double) + (size_t)m * sizeof(int) + 16;
+  const size_t smem = (size_t)(6 * pp + 2 * pp + 3 * p * q) * sizeof(double) + (size_t)3 * m * sizeof(int) + 16;
   static size_t configured = 0;
   if (smem > 48 * 1024 && smem > configured) {
     cudaFuncSetAttribute(leaf_assemble_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
