@@ -17,12 +17,13 @@
 //
 // Work unit: one item (<= 64 rows, MMA M = 128 with rows 64..127 zero) and 32 right-hand
 // sides (MMA N = 32).  A first kernel writes every unit's 64 row and 32 column exponents;
-// the product kernel's roles (16 warps, one CTA per SM looping over the units):
-//   warps 2, 3, 6, 7, 10, 11, 14  producers: per K step of 16 the digit planes of A (64 x 16)
-//              and B (32 x 16), three stages deep;
-//   warp 15    one thread issues the 45 digit-pair products of each K step into TMEM;
-//   warps 0, 1, 4, 5, 8, 9, 12, 13  epilogue: TMEM lanes 0..63 (warp w reads lane quarter
-//              w % 4), 8 right-hand sides per thread; recombination, beta, Add, scatter.
+// the product kernel's roles (17 warps, one CTA per SM looping over the units):
+//   warps 0, 1, 4, 5   epilogue: TMEM lanes 0..63 (warp w reads lane quarter w % 4), 16
+//              right-hand sides per thread, four at a time; recombination, beta, Add, scatter;
+//   the other warps but 16  producers (12 warps, spread over the four SM sub-partitions):
+//              per K step of 16 the digit planes of A (64 x 16) and B (32 x 16), one task of
+//              4 consecutive k per thread, three stages deep;
+//   warp 16    one thread issues the digit-pair products of each K step into TMEM.
 // Handoffs are mbarriers with bounded waits; a timeout stops every role (status -1).
 #include <cstdint>
 #include <cstdio>
@@ -42,9 +43,10 @@ constexpr int GS = 9;       // digits per entry
 constexpr int GD = 9;       // kept diagonals d = 2 .. 10
 constexpr int GKMAX = 448;  // longest K with exact FP32 diagonal sums
 constexpr int GST = 3;      // K-step stages
-constexpr int G_THREADS = 512;
-constexpr int G_PROD = 224;  // producer threads (7 warps)
-constexpr int G_EPI = 256;   // epilogue threads (8 warps)
+constexpr int G_THREADS = 544;  // 17 warps (5 on one SM sub-partition: at most 96 registers)
+constexpr int G_PROD = 384;    // producer threads (12 warps, one task each)
+constexpr int G_EPI = 128;     // epilogue threads (4 warps)
+constexpr int G_MMA_WARP = 16;
 constexpr long long G_WAIT = 1ll << 26;
 
 struct GStage {
@@ -322,7 +324,7 @@ __global__ void __launch_bounds__(G_THREADS, 1) gemm_tc_kernel(const GemmItem* _
     sh.abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
-  if (warp == 15) {
+  if (warp == G_MMA_WARP) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh.tmem_base)),
                  "r"(512));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -335,7 +337,7 @@ __global__ void __launch_bounds__(G_THREADS, 1) gemm_tc_kernel(const GemmItem* _
   volatile int* abort_flag = &sh.abort_flag;
   const int q4 = warp & 3;
 
-  if (warp == 15) {
+  if (warp == G_MMA_WARP) {
     // ---------------- MMA issue (one thread)
     if (lane == 0) {
       // kind::f16 with bf16 A and B, FP32 accumulators, M = 128; N is set per product
@@ -386,15 +388,15 @@ __global__ void __launch_bounds__(G_THREADS, 1) gemm_tc_kernel(const GemmItem* _
           smem_u32(&sh.mdone)));
       mb_drain(&sh.mdone, 0);
     }
-  } else if (q4 >= 2) {
-    // ---------------- producers: warps 2, 3, 6, 7, 10, 11, 14 -> producer index 0 .. 223.
-    // Thread pt owns tasks pt and pt + 224 (4 consecutive k of one row of A or column of B)
-    // of every K step; it copies their entries GPF steps ahead (asynchronously, into its own
-    // slots) and turns them into digits when their step comes, so no thread waits on memory
-    // for the step it is working on.
-    const int pw = (warp >> 2) * 2 + (q4 - 2);  // 0 .. 6
+  } else if (!(warp < 8 && q4 < 2)) {
+    // ---------------- producers: warps 2, 3, 6, 7, 8 .. 15 -> producer index 0 .. 11.
+    // Thread pt owns task pt (4 consecutive k of one row of A or column of B) of every K
+    // step; it copies the entries GPF steps ahead (asynchronously, into its own slot) and
+    // turns them into digits when their step comes, so no thread waits on memory for the
+    // step it is working on.
+    const int pw = warp < 8 ? (warp >> 2) * 2 + (q4 - 2) : warp - 4;
     const int pt = pw * 32 + lane;
-    const int ntask = pt + G_PROD < GTASK ? 2 : 1;
+    const int ntask = pt + G_PROD < GTASK ? 2 : 1;  // 1 while G_PROD = GTASK
     // step iterators over (unit, K step) in this block's order: cu/cc current, pu/pc copy
     long long cu = blockIdx.x, pu = blockIdx.x;
     int cc = 0, pc = 0;
@@ -473,8 +475,8 @@ __global__ void __launch_bounds__(G_THREADS, 1) gemm_tc_kernel(const GemmItem* _
     }
     asm volatile("cp.async.wait_all;" ::: "memory");  // copies still in flight land before exit
   } else {
-    // ---------------- epilogue: warps 0, 1, 4, 5, 8, 9, 12, 13; row = 32 (w % 4) + lane,
-    // right-hand sides 8 g .. 8 g + 7 with g = w / 4
+    // ---------------- epilogue: warps 0, 1, 4, 5; row = 32 (w % 4) + lane, right-hand
+    // sides 16 g .. 16 g + 15 with g = w / 4, four at a time
     const int row = q4 * 32 + lane, g = warp >> 2;
     int nu = 0;
     for (long long u = blockIdx.x; u < total; u += gridDim.x, ++nu) {
@@ -482,43 +484,48 @@ __global__ void __launch_bounds__(G_THREADS, 1) gemm_tc_kernel(const GemmItem* _
       const int n0 = (int)(u % nnb) * GN;
       const int* sc = scales + u * GSC;
       const int er = sc[row];
-      int ec[8];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) ec[j] = sc[GR + 8 * g + j];
       if (!warp_wait(&sh.tfull, nu & 1, abort_flag, status)) break;
       asm volatile("tcgen05.fence::after_thread_sync;");
-      uint32_t v[GD][8];
+      const long long crow = row < it.M ? (long long)map_row(idx, it.c_idx, it.c_row, row) * nrhs : 0;
+#pragma unroll 1
+      for (int hh = 0; hh < 4; ++hh) {
+        const int jb = 16 * g + 4 * hh;
+        int ec[4];
 #pragma unroll
-      for (int d = 0; d < GD; ++d) {
-        const uint32_t addr = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(d * GN + 8 * g);
-        uint32_t* vd = v[d];
-        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                     : "=r"(vd[0]), "=r"(vd[1]), "=r"(vd[2]), "=r"(vd[3]), "=r"(vd[4]), "=r"(vd[5]), "=r"(vd[6]),
-                       "=r"(vd[7])
-                     : "r"(addr));
-      }
-      asm volatile("tcgen05.wait::ld.sync.aligned;");
-      asm volatile("tcgen05.fence::before_thread_sync;");
-      mb_arrive(&sh.tfree);  // TMEM read: the next unit's products may start
-      if (row < it.M) {
-        const long long crow = (long long)map_row(idx, it.c_idx, it.c_row, row) * nrhs;
+        for (int j = 0; j < 4; ++j) ec[j] = sc[GR + jb + j];
+        uint32_t v[GD][4];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int n = n0 + 8 * g + j;
-          if (n >= nrhs) continue;
-          uint32_t dj[GD];
+        for (int d = 0; d < GD; ++d) {
+          const uint32_t addr = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(d * GN + jb);
+          uint32_t* vd = v[d];
+          asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                       : "=r"(vd[0]), "=r"(vd[1]), "=r"(vd[2]), "=r"(vd[3])
+                       : "r"(addr));
+        }
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+        if (hh == 3) {
+          asm volatile("tcgen05.fence::before_thread_sync;");
+          mb_arrive(&sh.tfree);  // TMEM read: the next unit's products may start
+        }
+        if (row < it.M) {
 #pragma unroll
-          for (int d = 0; d < GD; ++d) dj[d] = v[d][j];
-          double r = recombine9(dj, er, ec[j]);
-          if (it.add_row >= 0) r += Add[(long long)(it.add_row + row) * nrhs + n];
-          C[crow + n] = (beta != 0.0 ? beta * C[crow + n] : 0.0) + r;
+          for (int j = 0; j < 4; ++j) {
+            const int n = n0 + jb + j;
+            if (n >= nrhs) continue;
+            uint32_t dj[GD];
+#pragma unroll
+            for (int d = 0; d < GD; ++d) dj[d] = v[d][j];
+            double r = recombine9(dj, er, ec[j]);
+            if (it.add_row >= 0) r += Add[(long long)(it.add_row + row) * nrhs + n];
+            C[crow + n] = (beta != 0.0 ? beta * C[crow + n] : 0.0) + r;
+          }
         }
       }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  if (warp == 15) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+  if (warp == G_MMA_WARP) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
 }
 
 }  // namespace
