@@ -1196,25 +1196,24 @@ __global__ void __launch_bounds__(256) gj_extract_kernel(const GJDesc* __restric
   const long long bro = dst.BR_off ? dst.BR_off[b] : (long long)b * dst.BR_off_stride;
   const int ldTL = dst.ld_from_desc ? K : dst.TL_ld, ldBL = dst.ld_from_desc ? K : dst.BL_ld;
   const int ldTR = dst.ld_from_desc ? R - K : dst.TR_ld, ldBR = dst.ld_from_desc ? R - K : dst.BR_ld;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int lr = (int)(e / R);
-    const int lc = (int)(e - (long long)lr * R);
+  (void)total;
+  // one warp per logical row, lanes along it (reads of a row stay within one physical row;
+  // writes are contiguous)
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int lr = blockIdx.x * nw + (threadIdx.x >> 5); lr < md.rows; lr += gridDim.x * nw) {
     const int sr = lr < K ? sig[lr] : lr;
-    const int sc = lc < K ? isig[lc] : lc;
-    const T v = M[(long long)sr * R + sc];
+    const T* Mr = M + (long long)sr * R;
     if (lr < K) {
-      if (lc < K) {
-        if (TL) TL[tlo + (long long)lr * ldTL + lc] = (TO)(dst.sTL * (double)v);
-      } else if (TR) {
-        TR[tro + (long long)lr * ldTR + (lc - K)] = (TO)(dst.sTR * (double)v);
-      }
+      if (TL)
+        for (int lc = lane; lc < K; lc += 32) TL[tlo + (long long)lr * ldTL + lc] = (TO)(dst.sTL * (double)Mr[isig[lc]]);
+      if (TR)
+        for (int lc = K + lane; lc < R; lc += 32) TR[tro + (long long)lr * ldTR + (lc - K)] = (TO)(dst.sTR * (double)Mr[lc]);
     } else {
-      if (lc < K) {
-        if (BL) BL[blo + (long long)(lr - K) * ldBL + lc] = (TO)(dst.sBL * (double)v);
-      } else if (BR) {
-        BR[bro + (long long)(lr - K) * ldBR + (lc - K)] = (TO)v;
-      }
+      if (BL)
+        for (int lc = lane; lc < K; lc += 32)
+          BL[blo + (long long)(lr - K) * ldBL + lc] = (TO)(dst.sBL * (double)Mr[isig[lc]]);
+      if (BR)
+        for (int lc = K + lane; lc < R; lc += 32) BR[bro + (long long)(lr - K) * ldBR + (lc - K)] = (TO)Mr[lc];
     }
   }
 }
@@ -1333,8 +1332,7 @@ void launch_gj_update(const GJDesc* d, int nmat, int maxR, int maxRows, T* work,
 template <typename T, typename TO>
 void launch_gj_extract(const GJDesc* d, int nmat, int maxR, const T* work, const int* perm,
                        const ExtractDst& dst, cudaStream_t s) {
-  const long long total = (long long)maxR * maxR;
-  int gx = (int)((total + 255) / 256);
+  int gx = (maxR + 7) / 8;  // one warp per row, 8 per block
   if (gx > 1024) gx = 1024;
   const size_t smem = (size_t)2 * maxR * sizeof(int);
   static size_t configured = 0;
