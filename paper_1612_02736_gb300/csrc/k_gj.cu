@@ -70,7 +70,7 @@ template <> struct KeyOf<float> {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(256) gj_panel_kernel(const GJDesc* __restrict__ d,
+__global__ void __launch_bounds__(1024) gj_panel_kernel(const GJDesc* __restrict__ d,
                                                        T* __restrict__ work, int* __restrict__ perm,
                                                        T* __restrict__ pinv, int c0, int nb_req,
                                                        int* __restrict__ status) {
@@ -200,24 +200,26 @@ __global__ void __launch_bounds__(256) gj_prep_kernel(const GJDesc* __restrict__
   if (tid < nb) pphys[tid] = perm[md.perm_off + c0 + tid];
   __syncthreads();
   T* M = work + md.off;
-  const int r = blockIdx.x * blockDim.x + tid;
-  if (r < md.rows) {
-    int tp = -1;
+  // thread (row r, output column j): 16 rows per block, 16 threads per row; a row's 16
+  // threads are in one warp, read the row's panel entries first, then write
+  const int r = blockIdx.x * 16 + (tid >> 4), j = tid & 15;
+  const bool act = r < md.rows && j < nb;
+  T* Mr = M + (long long)(act ? r : 0) * R + c0;
+  int tp = -1;
+  T w = T(0);
+  if (act) {
     for (int t = 0; t < nb; ++t)
       if (pphys[t] == r) tp = t;
-    T* Mr = M + (long long)r * R + c0;
-    if (tp >= 0) {
-      for (int j = 0; j < nb; ++j) Mr[j] = Pi[tp * NBMAX + j];
+    if (tp < 0) {
+      T acc = T(0);
+      for (int t = 0; t < nb; ++t) acc += Mr[t] * Pi[t * NBMAX + j];
+      w = -acc;
     } else {
-      T mrow[NBMAX];
-      for (int t = 0; t < nb; ++t) mrow[t] = Mr[t];
-      for (int j = 0; j < nb; ++j) {
-        T s = T(0);
-        for (int t = 0; t < nb; ++t) s += mrow[t] * Pi[t * NBMAX + j];
-        Mr[j] = -s;
-      }
+      w = Pi[tp * NBMAX + j];
     }
   }
+  __syncwarp();
+  if (act) Mr[j] = w;
   // copy the pivot rows (columns outside the panel) to the side buffer
   T* pb = prow + (long long)blockIdx.y * prow_stride;
   const long long total = (long long)nb * R;
@@ -1236,13 +1238,16 @@ void launch_gj_panel(const GJDesc* d, int nmat, int maxK, T* work, int* perm, T*
     cudaFuncSetAttribute(gj_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     configured = smem;
   }
-  gj_panel_kernel<T><<<nmat, 256, smem, s>>>(d, work, perm, pinv, c0, nb, status);
+  // many matrices: 256 threads each, several CTAs per SM; few (the large merges near the
+  // root): a thread per panel row, up to 1024, so that each pivot step is short
+  const int threads = nmat >= 2 * 152 ? 256 : std::max(256, std::min(1024, (nrows + 31) / 32 * 32));
+  gj_panel_kernel<T><<<nmat, threads, smem, s>>>(d, work, perm, pinv, c0, nb, status);
 }
 
 template <typename T>
 void launch_gj_prep(const GJDesc* d, int nmat, int maxR, T* work, const int* perm, const T* pinv,
                     T* prow, long long prow_stride, int c0, int nb, cudaStream_t s) {
-  dim3 grid((maxR + 255) / 256, nmat);
+  dim3 grid((maxR + 15) / 16, nmat);  // 16 rows per block
   gj_prep_kernel<T><<<grid, 256, 0, s>>>(d, work, perm, pinv, prow, prow_stride, c0, nb);
 }
 
