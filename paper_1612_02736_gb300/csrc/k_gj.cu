@@ -18,8 +18,10 @@
 //               and copies the pivot rows to a side buffer;
 //   gj_update : rank-nb update of every other column, M_r += W_r Prow (pivot rows are
 //               replaced by Pinv Prow).
-// FP64 on GB300 runs on the FFMA pipe (no FP64 tensor path is faster on this part), so
-// the update is a register-tiled SIMT product.
+// FP64 FFMA and DMMA run at about 1.2 TFLOP/s on GB300, so the FP64 update runs on the
+// bf16 tensor cores by exact digit slicing (gj_update_tcs_kernel, gj_update_tcp_kernel
+// below); the register-tiled SIMT kernel serves FP32 batches and remains a tuning
+// candidate.
 #include <algorithm>
 #include <cfloat>
 #include <cstdint>

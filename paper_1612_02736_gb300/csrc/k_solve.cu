@@ -4,9 +4,11 @@
 // Every operator application of Algorithm 2 -- h = H g on leaves, [w; h] = [X; C X] d and
 // u_gi = S u_ge + w on merges, u_c = [F | S_ci] [g_ci; u_ge] on leaves -- is a batched
 // product of a stored dense operator with a block of gathered vectors (one column per
-// right-hand side).  The stored operators are streamed exactly once per solve (Sec. 5.4),
-// so the sweep is bound by HBM bandwidth (FP32 operators) or by the FP64 FFMA pipe (FP64
-// operators on GB300).  Vectors are [row][rhs] with the right-hand side fastest.
+// right-hand side).  The stored operators are streamed exactly once per solve (Sec. 5.4).
+// FP64 products with inner dimension up to 448 and at least 8 right-hand sides go to the
+// tensor-core kernel (k_gemm_tc.cu); the SIMT kernels here take the rest (FP32 sweeps,
+// few right-hand sides, long inner dimensions).  Vectors are [row][rhs] with the
+// right-hand side fastest.
 #include <cfloat>
 #include <type_traits>
 
