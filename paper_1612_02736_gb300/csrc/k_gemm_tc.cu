@@ -124,7 +124,7 @@ __device__ __forceinline__ void cp_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// warp-uniform bounded wait: lane 0 waits, the verdict is broadcast
+// warp-uniform bounded wait: lane 0 waits, the result is broadcast
 __device__ __forceinline__ bool warp_wait(unsigned long long* b, int parity, volatile int* abort_flag, int* status) {
   int ok = 1;
   if ((threadIdx.x & 31) == 0) ok = mb_wait(b, parity, abort_flag, status) ? 1 : 0;

@@ -394,7 +394,7 @@ __device__ __forceinline__ void write_digits(long long bits, int emax, unsigned 
 //              buffer (coalesced).
 // Handoffs use mbarriers per buffer: full (producers -> MMA), done (MMA -> epilogue),
 // free (epilogue -> producers).  One elected thread per role waits, with an iteration
-// limit, and broadcasts the verdict over the role's named barrier; a timeout stops every
+// limit, and broadcasts the result over the role's named barrier; a timeout stops every
 // role (abort flag) and is reported as status -1.
 constexpr int PT_THREADS = 512;
 constexpr int PT_EPI = 256;  // epilogue threads: 2 per tile row, 16 columns each
