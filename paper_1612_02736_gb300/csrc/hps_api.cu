@@ -2046,6 +2046,8 @@ int check_opts(int p, const hps_opts* opts, hps_opts& o) {
     return fail(HPS_ERR_INVALID_ARG, "bc_sn must be HPS_BC_DIRICHLET or HPS_BC_NEUMANN");
   if ((o.bc_we != HPS_BC_DIRICHLET || o.bc_sn != HPS_BC_DIRICHLET) && o.precision != HPS_FP64)
     return fail(HPS_ERR_INVALID_ARG, "periodic or Neumann sides need precision HPS_FP64");
+  if (o.fp64_gemm != HPS_GEMM_TENSOR && o.fp64_gemm != HPS_GEMM_SIMT)
+    return fail(HPS_ERR_INVALID_ARG, "fp64_gemm must be HPS_GEMM_TENSOR or HPS_GEMM_SIMT");
   if (o.ir_tol <= 0.0) o.ir_tol = 1e-10;
   if (o.ir_max_iter <= 0) o.ir_max_iter = 10;
   return HPS_OK;

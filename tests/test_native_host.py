@@ -216,6 +216,12 @@ def test_plan_rejects_bad_options(lib):
     opts.precision = 0
     opts.q = 40
     assert lib.hps_plan_check(t, 8, C.byref(opts)) == 1
+    lib.hps_opts_default(C.byref(opts))
+    assert opts.fp64_gemm == _native.HPS_GEMM_TENSOR
+    opts.fp64_gemm = _native.HPS_GEMM_SIMT
+    assert lib.hps_plan_check(t, 8, C.byref(opts)) == 0
+    opts.fp64_gemm = 5
+    assert lib.hps_plan_check(t, 8, C.byref(opts)) == 1
     lib.hps_tree_destroy(t)
 
 
