@@ -452,9 +452,7 @@ __global__ void __launch_bounds__(G_THREADS, 1) gemm_tc_kernel(const GemmItem* _
     }
     long long ks = 0;
     while (cu < total) {
-      issue(pu, pc, pit, (int)((ks + GPF) % GRAW));
-      if (pu < total) advance(pu, pc, pit);
-      cp_wait<GPF>();  // this thread's entries of step ks have landed
+      cp_wait<GPF - 1>();  // this thread's entries of step ks have landed
       const int st = (int)(ks % GST), slot = (int)(ks % GRAW);
       if (ks >= GST && !warp_wait(&sh.sfree[st], (int)((ks / GST) - 1) & 1, abort_flag, status)) break;
       const int* sc = scales + cu * GSC;
@@ -470,6 +468,10 @@ __global__ void __launch_bounds__(G_THREADS, 1) gemm_tc_kernel(const GemmItem* _
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       mb_arrive(&sh.sfull[st]);
+      // the copies of step ks + GPF (their index lookups may wait on memory) after this
+      // step's digits are out, off the products' critical path
+      issue(pu, pc, pit, (int)((ks + GPF) % GRAW));
+      if (pu < total) advance(pu, pc, pit);
       advance(cu, cc, cit);
       ++ks;
     }
