@@ -154,6 +154,13 @@ struct ItemSet {
   int n = 0;
   int maxK = 0;        // largest inner dimension of the items
   double elems = 0.0;  // operator entries streamed by one application
+  // tensor-core products: each item's first K step in the operator digit cache (prefix sums
+  // of ceil(K / 16)) and the cache itself, formed on first use outside stream capture
+  long long* dstep = nullptr;
+  long long dsteps = 0;
+  mutable GemmDigits dg;
+  mutable bool dg_tried = false;
+  mutable int uses = 0;  // tensor-core applications so far (the cache is formed on the second)
 };
 
 // A product step of one level: items writing final outputs, and split-K items writing
@@ -302,6 +309,7 @@ struct hps_handle {
   bool econ = false;
   int echunk = 0;                 // leaves per chunk
   int max_items = 0;              // largest product item set (sizes the tensor-core exponent buffer)
+  bool noalloc_call = false;      // inside hps_solve_noalloc: no allocation, no digit caches
   double* ework = nullptr;        // elimination workspace of one chunk
   int* eperm = nullptr;
   double* epinv = nullptr;
@@ -352,11 +360,16 @@ namespace {
 ItemSet upload_items(hps_handle* h, cudaStream_t s, const std::vector<GemmItem>& v) {
   ItemSet is;
   is.n = (int)v.size();
+  std::vector<long long> steps;
+  steps.reserve(v.size());
   for (const GemmItem& it : v) {
     is.elems += (double)it.M * it.K;
     is.maxK = std::max(is.maxK, it.K);
+    steps.push_back(is.dsteps);
+    is.dsteps += (it.K + 15) / 16;
   }
   h->max_items = std::max(h->max_items, is.n);
+  if (!v.empty()) is.dstep = upload(h->al, s, steps, h->owned);
   is.dev = v.empty() ? nullptr : upload(h->al, s, v, h->owned);
   return is;
 }
@@ -1529,13 +1542,49 @@ void recompute_leaf_chunk(hps_handle* h, int c, cudaStream_t s) {
   CKL();
 }
 
+// The operator digit cache of an FP64 item set for the tensor-core products (the operators
+// are fixed after the build; `ops` is the FP64 operator store the items index, trans how the
+// product reads them).  It is formed outside stream capture on the set's second application
+// (a handle solved once does not pay for it) or when `now` is set (before a sweep is
+// captured, so that the replayed graph reads it).  nullptr when the products do not run on
+// the tensor cores, before the cache exists, inside hps_solve_noalloc, or if the allocation
+// failed; the products then form the operator digits themselves (same results).
+const GemmDigits* item_digits(hps_handle* h, const ItemSet& is, int trans, const double* ops, int nrhs,
+                              cudaStream_t s, bool now = false) {
+  if (h->opts.fp64_gemm == HPS_GEMM_SIMT || is.n == 0 || is.dsteps == 0 || !gemm_tc_eligible(is.maxK, nrhs))
+    return nullptr;
+  if (!now) ++is.uses;
+  if (!is.dg.dig && !is.dg_tried && !h->noalloc_call && (now || is.uses >= 2)) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(s, &cs));
+    if (cs == cudaStreamCaptureStatusNone) {
+      is.dg_tried = true;
+      try {
+        const size_t db = (size_t)gemm_tc_digit_bytes(is.dsteps), eb = (size_t)is.n * 64 * sizeof(int);
+        unsigned char* dig = (unsigned char*)h->al.get(db, s);
+        h->owned.push_back({dig, db});
+        int* er = (int*)h->al.get(eb, s);
+        h->owned.push_back({er, eb});
+        TIMED("gemm_digits", 0, (double)db, launch_gemm_tc_digitize(is.dev, is.n, trans, ops, is.dstep, dig, er, s));
+        CKL();
+        is.dg.dig = dig;
+        is.dg.step = is.dstep;
+        is.dg.er = er;
+      } catch (const CudaError&) {
+        cudaGetLastError();
+      }
+    }
+  }
+  return is.dg.dig ? &is.dg : nullptr;
+}
+
 // Items [l0, l0 + n) leaves of a leaf item set (every leaf has the same number of items).
 ItemSet leaf_range(const hps_handle* h, const ItemSet& is, int l0, int n) {
   ItemSet r;
   const int per = is.n / h->n_leaf;
   r.dev = is.dev + (long long)l0 * per;
   r.n = n * per;
-  r.maxK = is.maxK;
+  r.maxK = is.maxK;  // no digit cache: these operators are rebuilt chunk by chunk
   r.elems = is.elems * (double)n / h->n_leaf;
   return r;
 }
@@ -1554,9 +1603,10 @@ void root_bc_solve(hps_handle* h, const double* ops, const double* f, double* V,
   double* bcw = h->ws.bcw;
   auto prod = [&](const char* name, const ItemSet& is, const double* B0, const double* B1, double* C,
                   const double* Add, double beta) {
+    const GemmDigits* dg = item_digits(h, is, 0, ops, nrhs, s);
     TIMED(name, 2.0 * is.elems * nrhs, is.elems * 8.0,
           launch_gemm_items<double, double>(is.dev, is.n, ROWBLK, 0, ops, B0, B1, C, Add, idx, nrhs, beta, s, 0,
-                                            h->opts.fp64_gemm == HPS_GEMM_SIMT ? 0 : is.maxK, h->d_status));
+                                            h->opts.fp64_gemm == HPS_GEMM_SIMT ? 0 : is.maxK, h->d_status, dg));
   };
   if (bc.periodic) {
     TIMED("root_bc_rows", 0, 0, launch_row_combine(idx + bc.c_d, bc.Ks, bcw, V, V, nrhs, s));
@@ -1606,9 +1656,13 @@ void solve_pass(hps_handle* h, const TA* ops, const double* f, const TV* g, cons
         };
       bn = tuned_choice(key, cands, h->tune_path, trial);
     }
+    const GemmDigits* dg = nullptr;
+    if constexpr (std::is_same<TA, double>::value) {
+      if (tc) dg = item_digits(h, is, 0, ops, nrhs, s);
+    }
     TIMED(("gemm_" + std::string(step) + "_" + sf).c_str(), 2.0 * is.elems * nrhs, is.elems * sizeof(TA),
           launch_gemm_items<TA, TV>(is.dev, is.n, ROWBLK, 0, ops, B0, B1, C, Add, idx, nrhs, beta, s, bn, mk,
-                                    h->d_status));
+                                    h->d_status, dg));
   };
   auto gemmp = [&](const char* step, const Prod& pr, const TV* B0, TV* C, const TV* Add, double beta) {
     gemm(step, pr.direct, B0, nullptr, C, Add, beta);
@@ -1660,6 +1714,26 @@ void solve_pass(hps_handle* h, const TA* ops, const double* f, const TV* g, cons
   CKL();
 }
 
+// Operator digit caches of every FP64 product set of the sweep, formed before a capture.
+void prepare_sweep_digits(hps_handle* h, int nrhs, cudaStream_t s) {
+  const double* ops = h->ops64;
+  auto one = [&](const ItemSet& is) { item_digits(h, is, 0, ops, nrhs, s, true); };
+  if (!h->econ) {
+    one(h->leafup);
+    one(h->leafdown);
+  }
+  one(h->lce);
+  for (const Level& lv : h->levels) {
+    if (!lv.fp64) continue;
+    one(lv.up.direct);
+    one(lv.up.split);
+    one(lv.down.direct);
+    one(lv.down.split);
+    one(lv.iup);
+    one(lv.idown);
+  }
+}
+
 double read_scalar(const double* d, cudaStream_t s) {
   double v = 0.0;
   CK(cudaMemcpyAsync(&v, d, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -1678,6 +1752,7 @@ void capture_solve(hps_handle* h, int nrhs, cudaStream_t s) {
   h->graph.f_in = (double*)h->al.get((size_t)h->n_bdry * nrhs * sizeof(double), s);
   h->graph.g_in = (double*)h->al.get((size_t)nuc * sizeof(double), s);
   h->graph.u_out = (double*)h->al.get((size_t)nuc * sizeof(double), s);
+  prepare_sweep_digits(h, nrhs, s);
   CK(cudaStreamSynchronize(s));
   if (!h->graph.cs) CK(cudaStreamCreateWithFlags(&h->graph.cs, cudaStreamNonBlocking));
   cudaStream_t cs = h->graph.cs;
@@ -2367,9 +2442,10 @@ int hps_adjoint(hps_handle* h, const double* ubar_in, int nrhs, const double* u,
     CK(cudaMemsetAsync(VB, 0, (size_t)h->v_rows * nrhs * sizeof(double), s));
     const bool simt = h->opts.fp64_gemm == HPS_GEMM_SIMT;
     auto gemmT = [&](const char* step, const ItemSet& is, const double* B0, double* C, double beta) {
+      const GemmDigits* dg = item_digits(h, is, 1, ops, nrhs, s);
       TIMED(("gemmT_" + std::string(step) + "_f64").c_str(), 2.0 * is.elems * nrhs, is.elems * 8.0,
             launch_gemm_items<double, double>(is.dev, is.n, ROWBLK, 1, ops, B0, nullptr, C, nullptr, idx, nrhs, beta,
-                                              s, 0, simt ? 0 : is.maxK, h->d_status));
+                                              s, 0, simt ? 0 : is.maxK, h->d_status, dg));
     };
     auto gemmTp = [&](const char* step, const Prod& pr, const double* B0, double* C, double beta) {
       gemmT(step, pr.direct, B0, C, beta);
@@ -2568,8 +2644,11 @@ extern "C" int hps_solve_noalloc(hps_handle* h, const double* f, const double* g
     // the Gaussian-node vector is assembled by scatters, so it must start at zero; the
     // other buffers are fully written before they are read
     CK(cudaMemsetAsync(ug, 0, (size_t)h->ns.n_gauss * R * sizeof(double), s));
+    h->noalloc_call = true;
     solve_pass<double, double>(h, h->ops64, f, g, nullptr, u, ug, V, d, Pp, nrhs, s);
+    h->noalloc_call = false;
   } catch (const CudaError& e) {
+    h->noalloc_call = false;
     return fail(e.code, e.msg);
   }
   return HPS_OK;

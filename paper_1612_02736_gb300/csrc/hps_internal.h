@@ -218,24 +218,39 @@ void launch_bgemm(const BGemm* d, int n, int maxM, int maxN, const double* A, co
 
 // Batched gathered products.  bn: right-hand-side tile of the tiled product (16, 32 or 64;
 // 0 = fixed rule), used for nrhs > 4.
+// The operator digit planes of an item set, formed once (launch_gemm_tc_digitize): item i's
+// K steps at dig + step[i] * gemm_tc_digit_bytes(1), its 64 row exponents at er + 64 i.
+struct GemmDigits {
+  const unsigned char* dig = nullptr;
+  const long long* step = nullptr;
+  const int* er = nullptr;
+};
+
 // maxK > 0 states the largest inner dimension of the items: FP64 products with maxK <= 448
 // and nrhs >= 8 then run on the tensor cores (launch_gemm_tc) when its exponent buffer is
-// large enough, else on the SIMT kernels; status receives -1 if a tensor-core wait times out.
+// large enough, else on the SIMT kernels; status receives -1 if a tensor-core wait times out;
+// dg (optional) holds the items' operator digits.
 template <typename TA, typename TV>
 void launch_gemm_items(const GemmItem* items, int nitems, int maxM, int trans, const TA* A,
                        const TV* B0, const TV* B1, TV* C, const TV* Add, const int* idx,
                        int nrhs, double beta, cudaStream_t s, int bn = 0, int maxK = 0,
-                       int* status = nullptr);
+                       int* status = nullptr, const GemmDigits* dg = nullptr);
 
 // FP64 gathered products on the tcgen05 tensor cores by exact digit slicing (k_gemm_tc.cu):
 // items of at most 64 rows and K <= 448.  gemm_tc_reserve grows the per-unit exponent
 // buffer (call outside stream capture: units = items x ceil(nrhs / 32)); launch_gemm_tc
-// returns false, launching nothing, when the buffer is too small.
+// returns false, launching nothing, when the buffer is too small.  With dg the operator's
+// digits are read from it instead of being formed (same results).
 bool gemm_tc_eligible(int maxK, int nrhs);
 void gemm_tc_reserve(long long units);
 bool launch_gemm_tc(const GemmItem* items, int nitems, int trans, const double* A, const double* B0,
                     const double* B1, double* C, const double* Add, const int* idx, int nrhs, double beta,
-                    int* status, cudaStream_t s);
+                    int* status, cudaStream_t s, const GemmDigits* dg);
+// bytes of the digit planes of `steps` K steps; fill adig / aer for the items (astep: each
+// item's first step, prefix sums of ceil(K / 16))
+long long gemm_tc_digit_bytes(long long steps);
+void launch_gemm_tc_digitize(const GemmItem* items, int nitems, int trans, const double* A, const long long* astep,
+                             unsigned char* adig, int* aer, cudaStream_t s);
 
 // Split-K partial products: rows [0, M) of one output block were computed in nsplit K
 // ranges into the partial buffer P (rows p_row + j * M + i); the reduction writes

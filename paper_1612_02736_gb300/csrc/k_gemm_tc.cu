@@ -49,8 +49,14 @@ constexpr int G_EPI = 128;     // epilogue threads (4 warps)
 constexpr int G_MMA_WARP = 16;
 constexpr long long G_WAIT = 1ll << 26;
 
+// Stage of one K step.  The A planes hold the item's 64 rows (2048 bytes each); a product
+// (M = 128) reads 128 rows from a plane's start, so its rows 64..127 are the next plane's
+// (or the B planes') bytes: bf16 digits, accumulated into TMEM lanes 64..127, which no
+// epilogue reads.  Rows are independent in the product, so lanes 0..63 stay exact.
+constexpr int GAPL = GR * 32;          // bytes per A plane
+constexpr int GASTEP = GS * GAPL;      // bytes of a K step's A planes (cached operators)
 struct GStage {
-  unsigned char A[GS][GM * 32];  // K-major planes, 128 rows x 16 k (rows 64..127 stay zero)
+  unsigned char A[GS][GAPL];     // K-major planes, 64 rows x 16 k
   unsigned char B[GS][GN * 32];  // 32 columns x 16 k
 };
 
@@ -114,6 +120,15 @@ __device__ __forceinline__ bool mb_wait(unsigned long long* b, int parity, volat
 __device__ __forceinline__ void mb_drain(unsigned long long* b, int parity) {
   for (long long it = 0; it < G_WAIT; ++it)
     if (mb_try(b, parity)) return;
+}
+__device__ __forceinline__ void mb_expect_arrive(unsigned long long* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
 }
 __device__ __forceinline__ void cp_async8(void* dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
@@ -250,7 +265,7 @@ __global__ void __launch_bounds__(256) gemm_scales_kernel(const GemmItem* __rest
                                                           const double* __restrict__ B0,
                                                           const double* __restrict__ B1,
                                                           const int* __restrict__ idx, int nrhs,
-                                                          int* __restrict__ scales) {
+                                                          int* __restrict__ scales, int rows) {
   const int nnb = (nrhs + GN - 1) / GN;
   const long long u = blockIdx.x;
   const GemmItem it = items[u / nnb];
@@ -264,7 +279,7 @@ __global__ void __launch_bounds__(256) gemm_scales_kernel(const GemmItem* __rest
     if (TRANS) { r = t & 63; ph = t >> 6; }
     else { r = t >> 2; ph = t & 3; }
     int m = 0;
-    if (r < it.M) {
+    if (rows && r < it.M) {
 #pragma unroll 4
       for (int k = ph; k < it.K; k += 4) m = max(m, bexp(a_at<TRANS>(it, A, r, k)));
     }
@@ -294,6 +309,57 @@ __global__ void __launch_bounds__(256) gemm_scales_kernel(const GemmItem* __rest
   }
 }
 
+// The operator's digit planes of every K step of one item (one block per item), in the
+// stage layout, at adig + astep[item] * GASTEP, and its 64 row exponents at aer[item * 64].
+// Operators do not change between solves, so their digits are formed once.
+template <bool TRANS>
+__global__ void __launch_bounds__(256) gemm_digits_kernel(const GemmItem* __restrict__ items,
+                                                          const double* __restrict__ A,
+                                                          const long long* __restrict__ astep,
+                                                          unsigned char* __restrict__ adig, int* __restrict__ aer) {
+  const long long item = blockIdx.x;
+  const GemmItem it = items[item];
+  const int t = threadIdx.x;
+  __shared__ int part[256];
+  __shared__ int er[GR];
+  {
+    int r, ph;
+    if (TRANS) { r = t & 63; ph = t >> 6; }
+    else { r = t >> 2; ph = t & 3; }
+    int m = 0;
+    if (r < it.M) {
+#pragma unroll 4
+      for (int k = ph; k < it.K; k += 4) m = max(m, bexp(a_at<TRANS>(it, A, r, k)));
+    }
+    part[TRANS ? ph * 64 + r : r * 4 + ph] = m;
+  }
+  __syncthreads();
+  if (t < GR) {
+    int m = 0;
+    for (int ph = 0; ph < 4; ++ph) m = max(m, TRANS ? part[ph * 64 + t] : part[t * 4 + ph]);
+    er[t] = m;
+    aer[item * GR + t] = m;
+  }
+  __syncthreads();
+  unsigned char* dst = adig + astep[item] * GASTEP;
+  const int nk = (it.K + 15) >> 4;
+  const int row = t >> 2, kg = (t & 3) * 4;  // 64 rows x 4 groups of 4 k
+  for (int c = 0; c < nk; ++c) {
+    unsigned char* pl = dst + (long long)c * GASTEP;
+    if (row >= it.M) {
+      zero_digits4(pl, GAPL, kmaj(row, kg));
+    } else {
+      double v[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int k = c * 16 + kg + q;
+        v[q] = k < it.K ? a_at<TRANS>(it, A, row, k) : 0.0;
+      }
+      write_digits4(v, er[row], pl, GAPL, kmaj(row, kg));
+    }
+  }
+}
+
 template <bool TRANS>
 __global__ void __launch_bounds__(G_THREADS, 1) gemm_tc_kernel(const GemmItem* __restrict__ items, int nitems,
                                                                 const double* __restrict__ A,
@@ -302,20 +368,21 @@ __global__ void __launch_bounds__(G_THREADS, 1) gemm_tc_kernel(const GemmItem* _
                                                                 const double* __restrict__ Add,
                                                                 const int* __restrict__ idx, int nrhs, double beta,
                                                                 const int* __restrict__ scales,
+                                                                const unsigned char* __restrict__ adig,
+                                                                const long long* __restrict__ astep,
+                                                                const int* __restrict__ aer,
                                                                 int* __restrict__ status) {
   extern __shared__ __align__(1024) unsigned char g_raw[];
   GShared& sh = *reinterpret_cast<GShared*>(g_raw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nnb = (nrhs + GN - 1) / GN;
   const long long total = (long long)nitems * nnb;
-  // the zero rows 64..127 of every A plane (bytes 2048 .. 4095 of the plane), once
-  for (int e = tid; e < GST * GS * 128; e += G_THREADS) {
-    const int st = e / (GS * 128), s = (e / 128) % GS, c = e % 128;
-    *reinterpret_cast<uint4*>(&sh.st[st].A[s][GR * 32 + c * 16]) = make_uint4(0, 0, 0, 0);
-  }
+  // cached operator digits (adig): the producers form only the vectors' digits (threads
+  // 256 .. 383) and one thread copies each K step's A planes
+  const bool cached = adig != nullptr;
   if (tid == 0) {
     for (int b = 0; b < GST; ++b) {
-      mb_init(&sh.sfull[b], G_PROD);
+      mb_init(&sh.sfull[b], cached ? GN * 4 + 1 : G_PROD);
       mb_init(&sh.sfree[b], 1);
     }
     mb_init(&sh.tfull, 1);
@@ -366,7 +433,7 @@ __global__ void __launch_bounds__(G_THREADS, 1) gemm_tc_kernel(const GemmItem* _
 #pragma unroll 1
             for (int t0 = 1; t0 <= nt; t0 += 8) {
               const int cnt = min(8, nt - t0 + 1);
-              const uint64_t ad = umma_desc(a0 + (sa - 1) * (GM * 32), 128, 256);
+              const uint64_t ad = umma_desc(a0 + (sa - 1) * GAPL, 128, 256);
               const uint64_t bd = umma_desc(b0 + (t0 - 1) * (GN * 32), 128, 256);
               const uint32_t idesc = idesc0 | ((uint32_t)((GN * cnt) >> 3) << 17);
               const uint32_t acc = (c > 0 || sa > 1) ? 1u : 0u;
@@ -397,6 +464,33 @@ __global__ void __launch_bounds__(G_THREADS, 1) gemm_tc_kernel(const GemmItem* _
     const int pw = warp < 8 ? (warp >> 2) * 2 + (q4 - 2) : warp - 4;
     const int pt = pw * 32 + lane;
     const int ntask = pt + G_PROD < GTASK ? 2 : 1;  // 1 while G_PROD = GTASK
+    if (cached && pt < GR * 4) {
+      // the operator's digit planes come from the cache: thread 0 copies each K step's
+      // planes (one bulk copy) and arms the stage's barrier with their bytes
+      if (pt == 0) {
+        long long ks = 0;
+        bool stop = false;
+        for (long long u = blockIdx.x; u < total && !stop; u += gridDim.x) {
+          const long long item = u / nnb;
+          const int nk = (items[item].K + 15) >> 4;
+          const unsigned char* src = adig + astep[item] * GASTEP;
+          for (int c = 0; c < nk; ++c, ++ks) {
+            const int st = (int)(ks % GST);
+            if (ks >= GST && !mb_wait(&sh.sfree[st], (int)((ks / GST) - 1) & 1, abort_flag, status)) {
+              stop = true;
+              break;
+            }
+            mb_expect_arrive(&sh.sfull[st], GASTEP);
+            bulk_load(sh.st[st].A[0], src + (long long)c * GASTEP, GASTEP, &sh.sfull[st]);
+          }
+        }
+        // the copies issued have landed before the block exits
+        for (int b = 0; b < GST; ++b) {
+          const long long n = ks > b ? (ks - 1 - b) / GST + 1 : 0;  // copies armed on stage b
+          if (n > 0) mb_drain(&sh.sfull[b], (int)((n - 1) & 1));
+        }
+      }
+    } else {
     // step iterators over (unit, K step) in this block's order: cu/cc current, pu/pc copy
     long long cu = blockIdx.x, pu = blockIdx.x;
     int cc = 0, pc = 0;
@@ -460,8 +554,8 @@ __global__ void __launch_bounds__(G_THREADS, 1) gemm_tc_kernel(const GemmItem* _
         const int task = pt + j * G_PROD, line = task >> 2, kg = (task & 3) * 4;
         const double* v = sh.raw[slot][task];
         if (line < GR) {
-          if (line >= cit.M) zero_digits4(sh.st[st].A[0], GM * 32, kmaj(line, kg));
-          else write_digits4(v, sc[line], sh.st[st].A[0], GM * 32, kmaj(line, kg));
+          if (line >= cit.M) zero_digits4(sh.st[st].A[0], GAPL, kmaj(line, kg));
+          else write_digits4(v, sc[line], sh.st[st].A[0], GAPL, kmaj(line, kg));
         } else {
           write_digits4(v, sc[line], sh.st[st].B[0], GN * 32, kmaj(line - GR, kg));
         }
@@ -476,6 +570,7 @@ __global__ void __launch_bounds__(G_THREADS, 1) gemm_tc_kernel(const GemmItem* _
       ++ks;
     }
     asm volatile("cp.async.wait_all;" ::: "memory");  // copies still in flight land before exit
+    }
   } else {
     // ---------------- epilogue: warps 0, 1, 4, 5; row = 32 (w % 4) + lane, right-hand
     // sides 16 g .. 16 g + 15 with g = w / 4, four at a time
@@ -485,7 +580,7 @@ __global__ void __launch_bounds__(G_THREADS, 1) gemm_tc_kernel(const GemmItem* _
       const GemmItem it = items[u / nnb];
       const int n0 = (int)(u % nnb) * GN;
       const int* sc = scales + u * GSC;
-      const int er = sc[row];
+      const int er = cached ? aer[(u / nnb) * GR + row] : sc[row];
       if (!warp_wait(&sh.tfull, nu & 1, abort_flag, status)) break;
       asm volatile("tcgen05.fence::after_thread_sync;");
       const long long crow = row < it.M ? (long long)map_row(idx, it.c_idx, it.c_row, row) * nrhs : 0;
@@ -563,21 +658,34 @@ void gemm_tc_reserve(long long units) {
 
 bool launch_gemm_tc(const GemmItem* items, int nitems, int trans, const double* A, const double* B0,
                     const double* B1, double* C, const double* Add, const int* idx, int nrhs, double beta,
-                    int* status, cudaStream_t s) {
+                    int* status, cudaStream_t s, const GemmDigits* dg) {
   if (nitems <= 0) return true;
   const long long units = (long long)nitems * ((nrhs + GN - 1) / GN);
   if (units > g_scales_units || !g_nsm) return false;
   const int grid = (int)std::min<long long>(g_nsm, units);
+  const unsigned char* adig = dg ? dg->dig : nullptr;
+  const long long* astep = dg ? dg->step : nullptr;
+  const int* aer = dg ? dg->er : nullptr;
+  const int rows = adig ? 0 : 1;
   if (trans) {
-    gemm_scales_kernel<true><<<(unsigned)units, 256, 0, s>>>(items, A, B0, B1, idx, nrhs, g_scales);
+    gemm_scales_kernel<true><<<(unsigned)units, 256, 0, s>>>(items, A, B0, B1, idx, nrhs, g_scales, rows);
     gemm_tc_kernel<true><<<grid, G_THREADS, sizeof(GShared), s>>>(items, nitems, A, B0, B1, C, Add, idx, nrhs, beta,
-                                                                  g_scales, status);
+                                                                  g_scales, adig, astep, aer, status);
   } else {
-    gemm_scales_kernel<false><<<(unsigned)units, 256, 0, s>>>(items, A, B0, B1, idx, nrhs, g_scales);
+    gemm_scales_kernel<false><<<(unsigned)units, 256, 0, s>>>(items, A, B0, B1, idx, nrhs, g_scales, rows);
     gemm_tc_kernel<false><<<grid, G_THREADS, sizeof(GShared), s>>>(items, nitems, A, B0, B1, C, Add, idx, nrhs, beta,
-                                                                   g_scales, status);
+                                                                   g_scales, adig, astep, aer, status);
   }
   return true;
+}
+
+long long gemm_tc_digit_bytes(long long steps) { return steps * GASTEP; }
+
+void launch_gemm_tc_digitize(const GemmItem* items, int nitems, int trans, const double* A, const long long* astep,
+                             unsigned char* adig, int* aer, cudaStream_t s) {
+  if (nitems <= 0) return;
+  if (trans) gemm_digits_kernel<true><<<(unsigned)nitems, 256, 0, s>>>(items, A, astep, adig, aer);
+  else gemm_digits_kernel<false><<<(unsigned)nitems, 256, 0, s>>>(items, A, astep, adig, aer);
 }
 
 }  // namespace hps

@@ -417,12 +417,12 @@ inline int grid_for(long long n, int bs = 256, int cap = 8192) {
 template <typename TA, typename TV>
 void launch_gemm_items(const GemmItem* items, int nitems, int maxM, int trans, const TA* A, const TV* B0,
                        const TV* B1, TV* C, const TV* Add, const int* idx, int nrhs, double beta,
-                       cudaStream_t s, int bn, int maxK, int* status) {
+                       cudaStream_t s, int bn, int maxK, int* status, const GemmDigits* dg) {
   (void)maxM;
   if (nitems <= 0) return;
   if constexpr (std::is_same<TA, double>::value && std::is_same<TV, double>::value) {
     if (gemm_tc_eligible(maxK, nrhs) &&
-        launch_gemm_tc(items, nitems, trans, A, B0, B1, C, Add, idx, nrhs, beta, status, s))
+        launch_gemm_tc(items, nitems, trans, A, B0, B1, C, Add, idx, nrhs, beta, status, s, dg))
       return;
   }
   const TV b = (TV)beta;
@@ -527,10 +527,10 @@ void launch_jump_residual(const int* pairs, int npairs, int q, const double* vfl
 
 template void launch_gemm_items<double, double>(const GemmItem*, int, int, int, const double*, const double*,
                                                 const double*, double*, const double*, const int*, int, double,
-                                                cudaStream_t, int, int, int*);
+                                                cudaStream_t, int, int, int*, const GemmDigits*);
 template void launch_gemm_items<float, float>(const GemmItem*, int, int, int, const float*, const float*,
                                               const float*, float*, const float*, const int*, int, double,
-                                              cudaStream_t, int, int, int*);
+                                              cudaStream_t, int, int, int*, const GemmDigits*);
 template void launch_split_reduce<double>(const SplitRed*, int, const double*, double*, const double*, const int*,
                                           int, double, cudaStream_t);
 template void launch_split_reduce<float>(const SplitRed*, int, const float*, float*, const float*, const int*, int,
