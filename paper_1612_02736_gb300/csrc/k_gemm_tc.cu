@@ -11,18 +11,23 @@
 // K <= 448 stays below 2^24 and the FP32 accumulation of the tensor core is exact.  The
 // digit pairs with s + t <= 10 accumulate diagonal d in its own TMEM columns, 10 tcgen05.mma
 // per K step of 16 (one per A digit plane against the B planes side by side); the epilogue
-// combines the 9 diagonals exactly in integers and rounds once to FP64.  The pairs left out weigh below about K 2^-63 max|A_r| max|B_n|,
-// and every digit of A and B is exact to 2^-62 of its row (column) maximum: the product
-// agrees with FP64 arithmetic to its normwise rounding level.
+// combines the 9 diagonals exactly in integers and rounds once to FP64.  The pairs left out
+// weigh below about K 2^-63 max|A_r| max|B_n|, and every digit of A and B is exact to 2^-62
+// of its row (column) maximum: the product agrees with FP64 arithmetic to its normwise
+// rounding level.
 //
-// Work unit: one item (<= 64 rows, MMA M = 128 with rows 64..127 zero) and 32 right-hand
-// sides (MMA N = 32).  A first kernel writes every unit's 64 row and 32 column exponents;
-// the product kernel's roles (17 warps, one CTA per SM looping over the units):
+// Work unit: one item (<= 64 rows; MMA M = 128, rows 64..127 are padding that no epilogue
+// reads) and 32 right-hand sides (MMA N = 32).  A first kernel writes every unit's 32 column
+// exponents (and its 64 row exponents unless the operator's digits are cached: the
+// operators are fixed after the build, so a product set can keep their digit planes, formed
+// once by gemm_digits_kernel).  The product kernel's roles (17 warps, one CTA per SM
+// looping over the units):
 //   warps 0, 1, 4, 5   epilogue: TMEM lanes 0..63 (warp w reads lane quarter w % 4), 16
 //              right-hand sides per thread, four at a time; recombination, beta, Add, scatter;
 //   the other warps but 16  producers (12 warps, spread over the four SM sub-partitions):
-//              per K step of 16 the digit planes of A (64 x 16) and B (32 x 16), one task of
-//              4 consecutive k per thread, three stages deep;
+//              per K step of 16 the digit planes of A (64 x 16, or one bulk copy of the
+//              cached planes) and B (32 x 16), one task of 4 consecutive k per thread, three
+//              stages deep;
 //   warp 16    one thread issues the digit-pair products of each K step into TMEM.
 // Handoffs are mbarriers with bounded waits; a timeout stops every role (status -1).
 #include <cstdint>
@@ -36,7 +41,7 @@ namespace hps {
 
 namespace {
 
-constexpr int GM = 128;     // MMA rows (item rows 0..63, the rest zero)
+constexpr int GM = 128;     // MMA rows (item rows 0..63, the rest padding)
 constexpr int GR = 64;      // item rows
 constexpr int GN = 32;      // right-hand sides per unit
 constexpr int GS = 9;       // digits per entry
