@@ -61,3 +61,22 @@ def test_tensor_products_econ_and_graphs_off():
         s = Solver(gpu_tree(case), to_dev(case["coeffs"]), 16, fp64_gemm="tensor", **kw)
         u = s.solve(to_dev(case["f"]), to_dev(case["g"]))
         assert rel_linf(u.cpu().numpy(), uc) < 1e-10
+
+
+def test_cached_operator_digits_reproduce_the_first_solve():
+    # The first solve forms the operators' digits inside the products; the second (captured
+    # into a graph) and later solves read the cached digit planes.  Same digits, same
+    # arithmetic: results bit for bit equal.  The adjoint likewise on its second call.
+    import torch
+    from paper_1612_02736_gb300 import Solver
+    case = make_case(8, 8, 16, nrhs=16)
+    s = Solver(gpu_tree(case), to_dev(case["coeffs"]), 16)
+    f, g = to_dev(case["f"]), to_dev(case["g"])
+    u1 = s.solve(f, g)
+    u2 = s.solve(f, g)
+    u3 = s.solve(f, g)
+    assert torch.equal(u1, u2) and torch.equal(u1, u3)
+    ubar = to_dev(np.random.default_rng(3).standard_normal(case["g"].shape))
+    a1 = s.adjoint(ubar, want_coeffs=False)
+    a2 = s.adjoint(ubar, want_coeffs=False)
+    assert torch.equal(a1[0], a2[0]) and torch.equal(a1[1], a2[1])
