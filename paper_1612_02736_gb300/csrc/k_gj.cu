@@ -754,32 +754,40 @@ __device__ __forceinline__ uint32_t bf16_of_int(int a) {
 }
 
 // The 8 balanced base-256 digit planes of one K-major row of 16 values (a row of W, or a
-// column of Prow), one 16-byte store per plane and half row.  The loop over planes stays
-// rolled: the kernel's roles share each SM's instruction cache.
+// column of Prow), one 16-byte store per plane and half row.  With X = sum_(i<7) a_i 2^(8i)
+// + a_top 2^56 and a_i in [-128, 127], Y = X + 128 sum_(i<7) 2^(8i) (modulo 2^64) holds
+// a_i + 128 in its byte i, so each low digit is one bit-field extraction; a_top is
+// floor(Y / 2^56) read as a signed value, or unsigned when X >= 0 carried Y past 2^63.
+// The loop over planes stays rolled: the kernel's roles share each SM's instruction cache.
 __device__ __forceinline__ void write_digit_row(const long long* w, int emax, unsigned char* base, int plane_bytes,
                                                 int row) {
+  constexpr unsigned long long kOff = 128ull * ((1ull << 56) - 1) / 255;  // 128 in bytes 0 .. 6
   unsigned char* p0 = base + kmaj16(row, 0);
 #pragma unroll
   for (int hq = 0; hq < 2; ++hq) {
-    long long X[8];
+    unsigned long long Y[8];
+    int top[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) X[q] = fixed_point(w[8 * hq + q], emax);
+    for (int q = 0; q < 8; ++q) {
+      const long long X = fixed_point(w[8 * hq + q], emax);
+      Y[q] = (unsigned long long)X + kOff;
+      top[q] = X >= 0 ? (int)(Y[q] >> 56) : (int)((long long)Y[q] >> 56);
+    }
+    {
+      uint32_t pk[4];
+#pragma unroll
+      for (int q = 0; q < 8; q += 2) pk[q >> 1] = bf16_of_int(top[q]) | (bf16_of_int(top[q + 1]) << 16);
+      *reinterpret_cast<uint4*>(p0 + 128 * hq) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    }
 #pragma unroll 1
-    for (int s = TCS - 1; s >= 0; --s) {
+    for (int i = 0; i < TCS - 1; ++i) {  // digit i -> plane 7 - i
       uint32_t pk[4];
 #pragma unroll
       for (int q = 0; q < 8; q += 2) {
-        int a[2];
-#pragma unroll
-        for (int t = 0; t < 2; ++t) {
-          // the lowest remaining digit in [-128, 127] (the last, most significant one keeps
-          // the remainder, |a| <= 128)
-          a[t] = s > 0 ? (int)(((unsigned int)X[q + t] + 128u) & 255u) - 128 : (int)X[q + t];
-          X[q + t] = (X[q + t] - a[t]) >> 8;
-        }
-        pk[q >> 1] = bf16_of_int(a[0]) | (bf16_of_int(a[1]) << 16);
+        const int a0 = (int)((Y[q] >> (8 * i)) & 255ull) - 128, a1 = (int)((Y[q + 1] >> (8 * i)) & 255ull) - 128;
+        pk[q >> 1] = bf16_of_int(a0) | (bf16_of_int(a1) << 16);
       }
-      *reinterpret_cast<uint4*>(p0 + s * plane_bytes + 128 * hq) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+      *reinterpret_cast<uint4*>(p0 + (TCS - 1 - i) * plane_bytes + 128 * hq) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
     }
   }
 }
