@@ -23,8 +23,9 @@
  *  - Every call returns an hps_status.  Nothing aborts, traps or exits the process; the
  *    text of the last error of the calling thread is returned by hps_last_error().
  *  - Calls taking a stream are stream-ordered.  hps_solve and hps_adjoint return once
- *    their work is enqueued (the iterative-refinement path of HPS_MIXED synchronises
- *    the stream once per refinement step to test convergence).  Errors found by device
+ *    their work is enqueued (the iterative refinement of HPS_MIXED synchronises the
+ *    stream to test convergence: once per call once calibrated, once per refinement
+ *    step before, see hps_solve).  Errors found by device
  *    code (singular pivots) are reported by hps_build (which synchronises) and by
  *    hps_sync_status.
  */
@@ -93,7 +94,8 @@ typedef struct {
                         * rebuild F, S, H chunk by chunk whenever a solve or adjoint needs
                         * them (the storage-efficient variant of the Sec. 5.4 remark;
                         * HPS_FP64 only)                                                    */
-  double ir_tol;       /* HPS_MIXED: stop when max|du| <= ir_tol * max|u|; 0 means 1e-10   */
+  double ir_tol;       /* HPS_MIXED: target of the estimated remaining error relative to
+                        * max|u| (see hps_solve); 0 means 1e-9, ten times below 1e-8    */
   int ir_max_iter;     /* HPS_MIXED: refinement steps allowed; 0 means 10                  */
   int fp64_top_levels; /* HPS_MIXED: number of top merge levels kept in FP64; -1 means 1   */
   int use_graphs;      /* HPS_FP64 solves without a flux-jump input: 1 (default) replays
@@ -190,10 +192,17 @@ int hps_build(const hps_tree* tree, const double* coeffs_dev, int p, const hps_o
  *                                     values used)
  *   u_dev : [n_leaf][p*p][nrhs]       output: the solution at every leaf Chebyshev node
  * FP64 handles run the sweeps in FP64.  HPS_MIXED handles run them in FP32 and refine
- * against the FP64 residual of the collocation system (leaf equations and flux jumps)
- * until max|du| <= ir_tol max|u|, or until the observed contraction of two successive
- * corrections (ratio r < 1/2) predicts the remaining error r max|du| below that; they
- * return NO_CONVERGENCE after ir_max_iter steps. */
+ * against the residual of the collocation system (leaf equations and flux jumps, in
+ * double-float arithmetic) with FP64 accumulation.  Until a handle is calibrated the
+ * refinement is adaptive, synchronising after every correction du: it stops when
+ * max|du| <= ir_tol max|u|, or when the observed contraction of two successive corrections
+ * (ratio r < 1/2) predicts the remaining error r max|du| below that.  Those ratios
+ * calibrate a contraction bound rho (twice the largest ratio) and the number n of
+ * corrections that bring the initial solve below tolerance; later calls without flux-jump
+ * data run the initial solve and n corrections without a test in between (one CUDA graph
+ * from the second such call with the same nrhs when use_graphs is set), synchronise once
+ * and accept when rho max|du_n| <= ir_tol max|u|, else refine on adaptively.  NaN or
+ * ir_max_iter steps without convergence give NO_CONVERGENCE. */
 int hps_solve(hps_handle* h, const double* f_dev, const double* g_dev, int nrhs, double* u_dev,
               void* stream);
 
@@ -225,7 +234,8 @@ int hps_solve_ext(hps_handle* h, const double* f_dev, const double* g_dev, const
  * comes from hps_build, which does allocate.  The per-call work buffers -- the box
  * flux/particular-solution pool, the merge difference vectors, the Gaussian-node
  * solution and the split-K partial sums, (box rows + merge rows + n_gauss + partial rows)
- * * nrhs doubles -- live in one fixed
+ * * nrhs doubles, and from 8 right-hand sides on the exponents of the tensor-core products
+ * (96 ints per 64-row operator block and 32 right-hand sides) -- live in one fixed
  * array of HPS_NOALLOC_SCRATCH_BYTES in device memory that the library image carries and
  * every GPU that loads it keeps until the process exits; a call that would need more is
  * rejected with INVALID_ARG and a message giving the size.  All calls share that array:

@@ -20,6 +20,7 @@ tree       uniform box trees, leaf Gauss-node numbering and the merge index sets
 hps        Algorithm 1 (build), Algorithm 2 (solve, optionally with a flux-jump right
            hand side), the FP64 residual of the global collocation system, and the
            transposed (adjoint) sweeps with the coefficient gradients.
+points     node coordinates (leaf Chebyshev nodes, boundary Gaussian nodes) for inputs.
 dense      brute force: the global collocation system assembled densely and solved with
            numpy.linalg.solve (for tiny meshes).
 

@@ -228,6 +228,9 @@ struct Workspace {
   double* vflux = nullptr;
   double* rho64 = nullptr;
   double* scal = nullptr;
+  // exponent buffer of the tensor-core FP64 products (units of one launch at most)
+  int* tc_scales = nullptr;
+  long long tc_units = 0;
   // adjoint
   double* LB = nullptr;
   double* UB = nullptr;
@@ -310,6 +313,8 @@ struct hps_handle {
   int echunk = 0;                 // leaves per chunk
   int max_items = 0;              // largest product item set (sizes the tensor-core exponent buffer)
   bool noalloc_call = false;      // inside hps_solve_noalloc: no allocation, no digit caches
+  int* tc_scales = nullptr;       // tensor-core exponent buffer of the current call (workspace
+  long long tc_units = 0;         // or the no-allocation scratch) and its capacity in units
   double* ework = nullptr;        // elimination workspace of one chunk
   int* eperm = nullptr;
   double* epinv = nullptr;
@@ -321,9 +326,18 @@ struct hps_handle {
   int* fbar_tab = nullptr;
   // workspace
   Workspace ws;
-  // captured FP64 sweep (per nrhs) and its staging buffers
+  // iterative refinement (HPS_MIXED): contraction bound calibrated on the adaptive solves
+  // (rho: twice the largest observed ratio of successive corrections, 0 until known) and the
+  // number of corrections a solve then runs without testing between them
+  struct {
+    double rho = 0.0;
+    int nfix = 0;
+  } ir;
+  // captured sweep (FP64) or fixed-schedule refined solve (HPS_MIXED) per nrhs, and its
+  // staging buffers
   struct {
     int nrhs = 0;
+    int nfix = 0;        // refinement steps in the captured mixed solve
     cudaGraphExec_t exec = nullptr;
     cudaStream_t cs = nullptr;
     double *f_in = nullptr, *g_in = nullptr, *u_out = nullptr;
@@ -1481,8 +1495,11 @@ void build_stage(hps_handle* h, const double* coeffs, cudaStream_t s) {
 
 void ensure_ws(hps_handle* h, int nrhs, cudaStream_t s) {
   Workspace& w = h->ws;
-  if (h->opts.fp64_gemm != HPS_GEMM_SIMT) gemm_tc_reserve((long long)h->max_items * ((nrhs + 31) / 32));
-  if (w.nrhs >= nrhs) return;
+  if (w.nrhs >= nrhs) {
+    h->tc_scales = w.tc_scales;
+    h->tc_units = w.tc_units;
+    return;
+  }
   h->drop_graph();  // a captured sweep points into the old buffers
   for (void* p : w.ptrs) h->al.put(p, s);
   w = Workspace();
@@ -1517,6 +1534,13 @@ void ensure_ws(hps_handle* h, int nrhs, cudaStream_t s) {
     w.ubar = (double*)get((size_t)ng * sizeof(double));
   }
   w.scal = (double*)get(4 * sizeof(double));
+  if (h->opts.fp64_gemm != HPS_GEMM_SIMT && nrhs >= 8) {
+    gemm_tc_prepare();
+    w.tc_units = (long long)h->max_items * ((nrhs + 31) / 32);
+    w.tc_scales = (int*)get((size_t)gemm_tc_scale_bytes(w.tc_units));
+  }
+  h->tc_scales = w.tc_scales;
+  h->tc_units = w.tc_units;
   if (h->bc.on) w.bcw = (double*)get((size_t)std::max(1, h->bc.rows) * R * sizeof(double));
 }
 
@@ -1589,6 +1613,18 @@ ItemSet leaf_range(const hps_handle* h, const ItemSet& is, int l0, int n) {
   return r;
 }
 
+// Launch options of a product of item set `is` for the handle's current call.
+GemmCtx gemm_ctx(const hps_handle* h, int maxK, const GemmDigits* dg = nullptr, int bn = 0) {
+  GemmCtx cx;
+  cx.bn = bn;
+  cx.maxK = h->opts.fp64_gemm == HPS_GEMM_SIMT ? 0 : maxK;
+  cx.status = h->d_status;
+  cx.dg = dg;
+  cx.tc_scales = h->tc_scales;
+  cx.tc_units = h->tc_units;
+  return cx;
+}
+
 // One pass of Algorithm 2 with operator type TA and vector type TV.
 //   f: [n_bdry][nrhs] FP64 (scattered as TV), g: [n_leaf][pp][nrhs] TV, rho: optional
 //   FP64 [n_gauss][nrhs], outputs uc [n_leaf][pp][nrhs] TV and ug [n_gauss][nrhs] TV.
@@ -1605,8 +1641,8 @@ void root_bc_solve(hps_handle* h, const double* ops, const double* f, double* V,
                   const double* Add, double beta) {
     const GemmDigits* dg = item_digits(h, is, 0, ops, nrhs, s);
     TIMED(name, 2.0 * is.elems * nrhs, is.elems * 8.0,
-          launch_gemm_items<double, double>(is.dev, is.n, ROWBLK, 0, ops, B0, B1, C, Add, idx, nrhs, beta, s, 0,
-                                            h->opts.fp64_gemm == HPS_GEMM_SIMT ? 0 : is.maxK, h->d_status, dg));
+          launch_gemm_items<double, double>(is.dev, is.n, ROWBLK, 0, ops, B0, B1, C, Add, idx, nrhs, beta, s,
+                                            gemm_ctx(h, is.maxK, dg)));
   };
   if (bc.periodic) {
     TIMED("root_bc_rows", 0, 0, launch_row_combine(idx + bc.c_d, bc.Ks, bcw, V, V, nrhs, s));
@@ -1651,7 +1687,8 @@ void solve_pass(hps_handle* h, const TA* ops, const double* f, const TV* g, cons
       if (cs == cudaStreamCaptureStatusNone)
         trial = [&](int b) {
           return time_on_stream(s, [&] {
-            launch_gemm_items<TA, TV>(is.dev, is.n, ROWBLK, 0, ops, B0, B1, C, Add, idx, nrhs, beta, s, b);
+            launch_gemm_items<TA, TV>(is.dev, is.n, ROWBLK, 0, ops, B0, B1, C, Add, idx, nrhs, beta, s,
+                                      gemm_ctx(h, 0, nullptr, b));
           });
         };
       bn = tuned_choice(key, cands, h->tune_path, trial);
@@ -1661,8 +1698,8 @@ void solve_pass(hps_handle* h, const TA* ops, const double* f, const TV* g, cons
       if (tc) dg = item_digits(h, is, 0, ops, nrhs, s);
     }
     TIMED(("gemm_" + std::string(step) + "_" + sf).c_str(), 2.0 * is.elems * nrhs, is.elems * sizeof(TA),
-          launch_gemm_items<TA, TV>(is.dev, is.n, ROWBLK, 0, ops, B0, B1, C, Add, idx, nrhs, beta, s, bn, mk,
-                                    h->d_status, dg));
+          launch_gemm_items<TA, TV>(is.dev, is.n, ROWBLK, 0, ops, B0, B1, C, Add, idx, nrhs, beta, s,
+                                    gemm_ctx(h, mk, dg, bn)));
   };
   auto gemmp = [&](const char* step, const Prod& pr, const TV* B0, TV* C, const TV* Add, double beta) {
     gemm(step, pr.direct, B0, nullptr, C, Add, beta);
@@ -1683,8 +1720,8 @@ void solve_pass(hps_handle* h, const TA* ops, const double* f, const TV* g, cons
         const int l0 = c * h->echunk, n = std::min(h->echunk, h->n_leaf - l0);
         const ItemSet r = leaf_range(h, is, l0, n);
         TIMED(("gemm_" + std::string(step) + "_" + sf).c_str(), 2.0 * r.elems * nrhs, r.elems * sizeof(TA),
-              launch_gemm_items<TA, TV>(r.dev, r.n, ROWBLK, 0, h->eops, B0, B1, C, nullptr, idx, nrhs, 0.0, s, 0,
-                                        h->opts.fp64_gemm == HPS_GEMM_SIMT ? 0 : r.maxK, h->d_status));
+              launch_gemm_items<TA, TV>(r.dev, r.n, ROWBLK, 0, h->eops, B0, B1, C, nullptr, idx, nrhs, 0.0, s,
+                                        gemm_ctx(h, r.maxK)));
       }
     }
   };
@@ -1734,25 +1771,103 @@ void prepare_sweep_digits(hps_handle* h, int nrhs, cudaStream_t s) {
   }
 }
 
-double read_scalar(const double* d, cudaStream_t s) {
-  double v = 0.0;
-  CK(cudaMemcpyAsync(&v, d, sizeof(double), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  return v;
+ResidualArgs residual_args(const hps_handle* h, const double* coeffs) {
+  ResidualArgs ra;
+  ra.coeffs = coeffs;
+  ra.n_leaf = h->n_leaf;
+  ra.p = h->p;
+  ra.q = h->q;
+  ra.hxy = h->dhxy;
+  ra.D = h->dD;
+  ra.D2 = h->dD2;
+  ra.Lloc = h->dLloc;
+  ra.ci = h->didx + h->off_ci;
+  ra.Lloc_df = h->dLloc_df;
+  ra.Lce_df = h->dLce_df;
+  return ra;
 }
 
-// Capture the whole FP64 sweep for this nrhs into a CUDA graph that reads its inputs from
-// (and writes u to) staging buffers owned by the handle.  Capture runs on a private
-// stream; a capture failure disables graphs for this handle (direct launches remain).
-void capture_solve(hps_handle* h, int nrhs, cudaStream_t s) {
+// Mixed precision (HPS_MIXED): FP32 sweeps refined against the residual of the collocation
+// system computed in double-float arithmetic, corrections accumulated in FP64.
+//
+// The low-precision solve of the original system: u (FP64) and the Gaussian-node vector
+// ug64, with the exact boundary data.
+void mixed_initial(hps_handle* h, const double* f, const double* g, const double* rho, double* u, int nrhs,
+                   cudaStream_t s) {
+  Workspace& w = h->ws;
+  const long long nuc = (long long)h->n_leaf * h->pp * nrhs;
+  const long long ng = (long long)h->ns.n_gauss * nrhs;
+  TIMED("convert", 0, nuc * 12.0, launch_convert<double, float>(g, w.g32, nuc, 1.0, s));
+  CK(cudaMemsetAsync(w.ug32, 0, ng * sizeof(float), s));
+  solve_pass<float, float>(h, h->ops32, f, w.g32, rho, w.uc32, w.ug32, w.V32, w.d32, w.P32, nrhs, s);
+  TIMED("convert", 0, nuc * 12.0, launch_convert<float, double>(w.uc32, u, nuc, 1.0, s));
+  TIMED("convert", 0, ng * 12.0, launch_convert<float, double>(w.ug32, w.ug64, ng, 1.0, s));
+  TIMED("scatter_rows", 0, 0, launch_scatter_rows<double>(f, h->didx + h->off_bnd, h->n_bdry, w.ug64, nrhs, s));
+  CKL();
+}
+
+// One refinement step: the residual of the collocation system (leaf equations and flux
+// jumps), an FP32 correction solve with the jumps as flux-continuity data, the FP64
+// update.  With measure, max|du| goes to scal[0] and max|u| to scal[1].
+void mixed_step(hps_handle* h, const double* g, const double* rho, double* u, int nrhs, bool measure,
+                cudaStream_t s) {
+  Workspace& w = h->ws;
+  const long long nuc = (long long)h->n_leaf * h->pp * nrhs;
+  const long long ng = (long long)h->ns.n_gauss * nrhs;
+  const ResidualArgs ra = residual_args(h, h->coeffs_copy);
+  // derivative passes (5 p^3), exterior refresh (ne 4q) and fluxes (4q p) per leaf and rhs
+  const double res_flops = 2.0 * ((double)h->n_leaf * nrhs) *
+                           (5.0 * h->p * h->p * h->p + (double)h->ne * h->nq + (double)h->nq * h->p + 12.0 * h->m);
+  TIMED("leaf_residual_df", res_flops, nuc * 32.0,
+        launch_leaf_residual_df(ra, h->d_leaf_edges, h->didx + h->off_ce, w.ug64, g, u, w.r64, w.vflux, nrhs, s));
+  CK(cudaMemsetAsync(w.rho64, 0, ng * sizeof(double), s));
+  TIMED("jump_residual", 0, 0, launch_jump_residual(h->d_pairs, h->npairs, h->q, w.vflux, w.rho64, nrhs, s));
+  if (rho) TIMED("axpy", 0, 0, launch_axpy_to_f64<double>(rho, w.rho64, ng, s));
+  CKL();
+  TIMED("convert", 0, nuc * 12.0, launch_convert<double, float>(w.r64, w.g32, nuc, 1.0, s));
+  CK(cudaMemsetAsync(w.ug32, 0, ng * sizeof(float), s));
+  solve_pass<float, float>(h, h->ops32, nullptr, w.g32, w.rho64, w.uc32, w.ug32, w.V32, w.d32, w.P32, nrhs, s);
+  TIMED("axpy", 0, nuc * 20.0, launch_axpy_to_f64<float>(w.uc32, u, nuc, s));
+  TIMED("axpy", 0, ng * 20.0, launch_axpy_to_f64<float>(w.ug32, w.ug64, ng, s));
+  if (measure) {
+    CK(cudaMemsetAsync(w.scal, 0, 2 * sizeof(double), s));
+    TIMED("absmax", 0, nuc * 4.0, launch_absmax_f32(w.uc32, nuc, w.scal, s));
+    TIMED("absmax", 0, nuc * 8.0, launch_absmax(u, nuc, w.scal + 1, s));
+  }
+  CKL();
+}
+
+// u_ce = L_ce,ge u_ge in FP64 on every leaf (the exterior values the last correction left
+// in FP32).
+void mixed_finish(hps_handle* h, double* u, int nrhs, cudaStream_t s) {
+  TIMED("exterior_refresh", 2.0 * h->n_leaf * nrhs * h->ne * h->nq, 0,
+        launch_exterior_refresh(h->n_leaf, h->p, h->q, h->d_leaf_edges, h->ops64 + h->lce_base, h->didx + h->off_ce,
+                                h->ws.ug64, u, nrhs, s));
+  CKL();
+}
+
+// The fixed-schedule refined solve: the initial solve, nfix corrections (the last one
+// measured) and the exterior refresh.
+void mixed_fixed(hps_handle* h, const double* f, const double* g, double* u, int nrhs, int nfix, cudaStream_t s) {
+  mixed_initial(h, f, g, nullptr, u, nrhs, s);
+  for (int k = 0; k < nfix; ++k) mixed_step(h, g, nullptr, u, nrhs, k == nfix - 1, s);
+  mixed_finish(h, u, nrhs, s);
+}
+
+// Capture the solve for this nrhs into a CUDA graph that reads its inputs from (and writes
+// u to) staging buffers owned by the handle: the FP64 sweep, or for HPS_MIXED the
+// fixed-schedule refined solve with nfix corrections.  Capture runs on a private stream; a
+// capture failure disables graphs for this handle (direct launches remain).
+void capture_solve(hps_handle* h, int nrhs, int nfix, cudaStream_t s) {
   h->drop_graph();
   Workspace& w = h->ws;
+  const bool mixed = h->opts.precision == HPS_MIXED;
   const long long nuc = (long long)h->n_leaf * h->pp * nrhs;
   const long long ng = (long long)h->ns.n_gauss * nrhs;
   h->graph.f_in = (double*)h->al.get((size_t)h->n_bdry * nrhs * sizeof(double), s);
   h->graph.g_in = (double*)h->al.get((size_t)nuc * sizeof(double), s);
   h->graph.u_out = (double*)h->al.get((size_t)nuc * sizeof(double), s);
-  prepare_sweep_digits(h, nrhs, s);
+  if (!mixed) prepare_sweep_digits(h, nrhs, s);
   CK(cudaStreamSynchronize(s));
   if (!h->graph.cs) CK(cudaStreamCreateWithFlags(&h->graph.cs, cudaStreamNonBlocking));
   cudaStream_t cs = h->graph.cs;
@@ -1761,9 +1876,13 @@ void capture_solve(hps_handle* h, int nrhs, cudaStream_t s) {
   cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
     try {
-      cudaMemsetAsync(w.ug64, 0, ng * sizeof(double), cs);
-      solve_pass<double, double>(h, h->ops64, h->graph.f_in, h->graph.g_in, nullptr, h->graph.u_out, w.ug64, w.V64,
-                                 w.d64, w.P64, nrhs, cs);
+      if (mixed) {
+        mixed_fixed(h, h->graph.f_in, h->graph.g_in, h->graph.u_out, nrhs, nfix, cs);
+      } else {
+        cudaMemsetAsync(w.ug64, 0, ng * sizeof(double), cs);
+        solve_pass<double, double>(h, h->ops64, h->graph.f_in, h->graph.g_in, nullptr, h->graph.u_out, w.ug64, w.V64,
+                                   w.d64, w.P64, nrhs, cs);
+      }
     } catch (const CudaError&) {
     }
     e = cudaStreamEndCapture(cs, &graph);
@@ -1784,8 +1903,9 @@ void capture_solve(hps_handle* h, int nrhs, cudaStream_t s) {
     for (const Level& lv : h->levels)
       el += lv.up.direct.elems + lv.up.split.elems + lv.down.direct.elems + lv.down.split.elems + lv.iup.elems +
             lv.idown.elems;
-    h->graph.flops = 2.0 * el * nrhs;
-    h->graph.bytes = 8.0 * el;
+    const int sweeps = mixed ? 1 + nfix : 1;
+    h->graph.flops = 2.0 * el * nrhs * sweeps;
+    h->graph.bytes = (mixed ? 4.0 : 8.0) * el * sweeps;
     e = cudaGraphInstantiate(&h->graph.exec, graph, 0);
   }
   if (graph) cudaGraphDestroy(graph);
@@ -1796,38 +1916,106 @@ void capture_solve(hps_handle* h, int nrhs, cudaStream_t s) {
     return;
   }
   h->graph.nrhs = nrhs;
+  h->graph.nfix = nfix;
 }
 
-int solve_impl(hps_handle* h, const double* f, const double* g, const double* rho, int nrhs, double* u,
-               double* ug_out, int* iters, cudaStream_t s) {
+// Run the captured graph for this call if there is one (capturing it on the second call
+// with the same nrhs); false if the caller has to launch directly.
+bool graph_solve(hps_handle* h, const double* f, const double* g, double* u, int nrhs, int nfix, cudaStream_t s) {
+  if (!h->opts.use_graphs || h->graph.broken) return false;
+  if ((h->graph.nrhs != nrhs || h->graph.nfix != nfix) && h->graph.last_nrhs == nrhs) capture_solve(h, nrhs, nfix, s);
+  h->graph.last_nrhs = nrhs;
+  if (!h->graph.exec || h->graph.nrhs != nrhs || h->graph.nfix != nfix) return false;
+  const long long nuc = (long long)h->n_leaf * h->pp * nrhs;
+  CK(cudaMemcpyAsync(h->graph.f_in, f, (size_t)h->n_bdry * nrhs * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(h->graph.g_in, g, nuc * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  {
+    TimingScope ts_(h->opts.precision == HPS_MIXED ? "graph_solve_mixed" : "graph_solve_f64", s, h->graph.flops,
+                    h->graph.bytes, std::max(1, h->graph.kernels));
+    CK(cudaGraphLaunch(h->graph.exec, s));
+  }
+  CK(cudaMemcpyAsync(u, h->graph.u_out, nuc * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  return true;
+}
+
+int solve_fp64(hps_handle* h, const double* f, const double* g, const double* rho, int nrhs, double* u,
+               double* ug_out, cudaStream_t s) {
   ensure_ws(h, nrhs, s);
   Workspace& w = h->ws;
-  const long long nuc = (long long)h->n_leaf * h->pp * nrhs;
   const long long ng = (long long)h->ns.n_gauss * nrhs;
-  if (iters) *iters = 0;
-  if (h->opts.precision == HPS_FP64) {
-    const long long nf = (long long)h->n_bdry * nrhs;
-    if (h->opts.use_graphs && !rho && !h->graph.broken) {
-      if (h->graph.nrhs != nrhs && h->graph.last_nrhs == nrhs) capture_solve(h, nrhs, s);
-      h->graph.last_nrhs = nrhs;
-      if (h->graph.exec && h->graph.nrhs == nrhs) {
-        CK(cudaMemcpyAsync(h->graph.f_in, f, nf * sizeof(double), cudaMemcpyDeviceToDevice, s));
-        CK(cudaMemcpyAsync(h->graph.g_in, g, nuc * sizeof(double), cudaMemcpyDeviceToDevice, s));
-        {
-          TimingScope ts_("graph_solve_f64", s, h->graph.flops, h->graph.bytes, std::max(1, h->graph.kernels));
-          CK(cudaGraphLaunch(h->graph.exec, s));
-        }
-        CK(cudaMemcpyAsync(u, h->graph.u_out, nuc * sizeof(double), cudaMemcpyDeviceToDevice, s));
-        if (ug_out) CK(cudaMemcpyAsync(ug_out, w.ug64, ng * sizeof(double), cudaMemcpyDeviceToDevice, s));
-        return HPS_OK;
-      }
-    }
+  if (rho || !graph_solve(h, f, g, u, nrhs, 0, s)) {
     CK(cudaMemsetAsync(w.ug64, 0, ng * sizeof(double), s));
     solve_pass<double, double>(h, h->ops64, f, g, rho, u, w.ug64, w.V64, w.d64, w.P64, nrhs, s);
-    if (ug_out) CK(cudaMemcpyAsync(ug_out, w.ug64, ng * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    return HPS_OK;
   }
-  return HPS_ERR_STATE;
+  if (ug_out) CK(cudaMemcpyAsync(ug_out, w.ug64, ng * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  return HPS_OK;
+}
+
+// HPS_MIXED solve.  Until the handle has a calibrated contraction bound, the refinement is
+// adaptive: after every correction the host reads max|du| and max|u| and stops when the
+// correction is below tolerance, or when the observed contraction r = |du_k| / |du_(k-1)|
+// (< 1/2) predicts the error left after it, r |du_k|, below tolerance.  The ratios seen
+// calibrate the bound rho and the number nfix of corrections that brings the initial
+// solve's error below tolerance with a tenfold margin.  Later solves without flux-jump
+// data run the initial solve and nfix corrections without testing in between (one CUDA
+// graph), then test once: rho |du_nfix| <= tol max|u|.  A solve that fails the test goes
+// on adaptively from where it is and recalibrates.
+int solve_mixed(hps_handle* h, const double* f, const double* g, const double* rho, int nrhs, double* u,
+                double* ug_out, int* iters, cudaStream_t s) {
+  ensure_ws(h, nrhs, s);
+  Workspace& w = h->ws;
+  const long long ng = (long long)h->ns.n_gauss * nrhs;
+  const double tol = h->opts.ir_tol;
+  auto read2 = [&](double* sc) {
+    CK(cudaMemcpyAsync(sc, w.scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  };
+  int it = 0;
+  bool conv = false, finished = false;
+  double prev = -1.0, first = -1.0, ratio = 0.0;
+  double sc[2] = {0.0, 0.0};
+  const int nfix = h->ir.nfix;
+  if (!rho && nfix > 0 && h->ir.rho > 0.0) {
+    if (!graph_solve(h, f, g, u, nrhs, nfix, s)) mixed_fixed(h, f, g, u, nrhs, nfix, s);
+    read2(sc);
+    it = nfix;
+    finished = true;
+    if (!(sc[0] == sc[0]) || !(sc[1] == sc[1])) return fail(HPS_ERR_NO_CONVERGENCE, "refinement produced NaN");
+    conv = h->ir.rho * sc[0] <= tol * sc[1];
+    prev = sc[0];
+  } else {
+    mixed_initial(h, f, g, rho, u, nrhs, s);
+  }
+  for (; !conv && it < h->opts.ir_max_iter; ++it) {
+    mixed_step(h, g, rho, u, nrhs, true, s);
+    finished = false;
+    read2(sc);
+    if (!(sc[0] == sc[0]) || !(sc[1] == sc[1])) break;
+    const double tolu = tol * sc[1];
+    if (first < 0.0) first = sc[0] / std::max(sc[1], 1e-300);
+    if (prev > 0.0) ratio = std::max(ratio, sc[0] / prev);
+    const bool small = sc[0] <= tolu;
+    const bool predicted = prev > 0.0 && sc[0] < 0.5 * prev && (sc[0] / prev) * sc[0] <= tolu;
+    prev = sc[0];
+    if (small || predicted) {
+      conv = true;
+      ++it;
+      // calibrate from the ratios of this solve (needs two corrections of the original system)
+      if (!rho && ratio > 0.0 && ratio < 0.5 && first > 0.0) {
+        h->ir.rho = std::max(h->ir.rho, 2.0 * ratio);
+        int n = 1;
+        double e = first;
+        while (n < h->opts.ir_max_iter && (e *= h->ir.rho) * 10.0 > tol) ++n;
+        h->ir.nfix = std::max(h->ir.nfix, n);
+      }
+      break;
+    }
+  }
+  if (!finished) mixed_finish(h, u, nrhs, s);
+  if (ug_out) CK(cudaMemcpyAsync(ug_out, w.ug64, ng * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  if (iters) *iters = it;
+  if (!conv) return fail(HPS_ERR_NO_CONVERGENCE, "iterative refinement did not converge in " + std::to_string(it) + " steps");
+  return HPS_OK;
 }
 
 }  // namespace
@@ -2123,7 +2311,7 @@ int check_opts(int p, const hps_opts* opts, hps_opts& o) {
     return fail(HPS_ERR_INVALID_ARG, "periodic or Neumann sides need precision HPS_FP64");
   if (o.fp64_gemm != HPS_GEMM_TENSOR && o.fp64_gemm != HPS_GEMM_SIMT)
     return fail(HPS_ERR_INVALID_ARG, "fp64_gemm must be HPS_GEMM_TENSOR or HPS_GEMM_SIMT");
-  if (o.ir_tol <= 0.0) o.ir_tol = 1e-10;
+  if (o.ir_tol <= 0.0) o.ir_tol = 1e-9;
   if (o.ir_max_iter <= 0) o.ir_max_iter = 10;
   return HPS_OK;
 }
@@ -2297,88 +2485,14 @@ int hps_solve_ext(hps_handle* h, const double* f, const double* g, const double*
   cudaStream_t s = (cudaStream_t)stream;
   try {
     if (iters) *iters = 0;
-    if (h->opts.precision == HPS_FP64) return solve_impl(h, f, g, rho, nrhs, u, ug_out, iters, s);
-    ensure_ws(h, nrhs, s);
-    Workspace& w = h->ws;
-    const long long nuc = (long long)h->n_leaf * h->pp * nrhs;
-    const long long ng = (long long)h->ns.n_gauss * nrhs;
-    const double* coeffs = h->coeffs_copy;
-    // 1. low-precision solve of the original system
-    TIMED("convert", 0, nuc * 12.0, launch_convert<double, float>(g, w.g32, nuc, 1.0, s));
-    CK(cudaMemsetAsync(w.ug32, 0, ng * sizeof(float), s));
-    solve_pass<float, float>(h, h->ops32, f, w.g32, rho, w.uc32, w.ug32, w.V32, w.d32, w.P32, nrhs, s);
-    TIMED("convert", 0, nuc * 12.0, launch_convert<float, double>(w.uc32, u, nuc, 1.0, s));
-    TIMED("convert", 0, ng * 12.0, launch_convert<float, double>(w.ug32, w.ug64, ng, 1.0, s));
-    TIMED("scatter_rows", 0, 0, launch_scatter_rows<double>(f, h->didx + h->off_bnd, h->n_bdry, w.ug64, nrhs, s));  // exact boundary data
-    CKL();
-    ResidualArgs ra;
-    ra.coeffs = coeffs;
-    ra.n_leaf = h->n_leaf;
-    ra.p = h->p;
-    ra.q = h->q;
-    ra.hxy = h->dhxy;
-    ra.D = h->dD;
-    ra.D2 = h->dD2;
-    ra.Lloc = h->dLloc;
-    ra.ci = h->didx + h->off_ci;
-    ra.Lloc_df = h->dLloc_df;
-    ra.Lce_df = h->dLce_df;
-    // derivative passes (5 p^3), exterior refresh (ne 4q) and fluxes (4q p) per leaf and rhs
-    const double res_flops = 2.0 * ((double)h->n_leaf * nrhs) *
-                             (5.0 * h->p * h->p * h->p + (double)h->ne * h->nq + (double)h->nq * h->p + 12.0 * h->m);
-    int it = 0;
-    bool conv = false;
-    double prev = -1.0;
-    for (; it < h->opts.ir_max_iter; ++it) {
-      // 2. FP64 residual: leaf equations and flux jumps (refreshes u_ce = L u_ge)
-      TIMED("leaf_residual_df", res_flops, nuc * 32.0,
-            launch_leaf_residual_df(ra, h->d_leaf_edges, h->didx + h->off_ce, w.ug64, g, u, w.r64, w.vflux,
-                                      nrhs, s));
-      CK(cudaMemsetAsync(w.rho64, 0, ng * sizeof(double), s));
-      TIMED("jump_residual", 0, 0, launch_jump_residual(h->d_pairs, h->npairs, h->q, w.vflux, w.rho64, nrhs, s));
-      if (rho) TIMED("axpy", 0, 0, launch_axpy_to_f64<double>(rho, w.rho64, ng, s));
-      CKL();
-      // 3. correction solve in FP32 with the jump residual as flux-continuity data
-      TIMED("convert", 0, nuc * 12.0, launch_convert<double, float>(w.r64, w.g32, nuc, 1.0, s));
-      CK(cudaMemsetAsync(w.ug32, 0, ng * sizeof(float), s));
-      solve_pass<float, float>(h, h->ops32, nullptr, w.g32, w.rho64, w.uc32, w.ug32, w.V32, w.d32, w.P32, nrhs, s);
-      // 4. update and convergence test
-      TIMED("axpy", 0, nuc * 20.0, launch_axpy_to_f64<float>(w.uc32, u, nuc, s));
-      TIMED("axpy", 0, ng * 20.0, launch_axpy_to_f64<float>(w.ug32, w.ug64, ng, s));
-      CK(cudaMemsetAsync(w.scal, 0, 4 * sizeof(double), s));
-      TIMED("convert", 0, nuc * 12.0, launch_convert<float, double>(w.uc32, w.r64, nuc, 1.0, s));
-      TIMED("absmax", 0, nuc * 8.0, launch_absmax(w.r64, nuc, w.scal, s));
-      TIMED("absmax", 0, nuc * 8.0, launch_absmax(u, nuc, w.scal + 1, s));
-      CKL();
-      double sc[2];
-      CK(cudaMemcpyAsync(sc, w.scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
-      CK(cudaStreamSynchronize(s));
-      if (!(sc[0] == sc[0]) || !(sc[1] == sc[1])) break;
-      // Converged when this correction is below tolerance, or when the observed contraction
-      // rho = |du_k| / |du_(k-1)| (< 1/2) predicts the error left after it, rho |du_k|, is.
-      const double tolu = h->opts.ir_tol * sc[1];
-      const bool small = sc[0] <= tolu;
-      const bool predicted = prev > 0.0 && sc[0] < 0.5 * prev && (sc[0] / prev) * sc[0] <= tolu;
-      prev = sc[0];
-      if (small || predicted) {
-        conv = true;
-        ++it;
-        break;
-      }
-    }
-    // final exterior refresh u_ce = L_ce,ge u_ge in FP64
-    TIMED("exterior_refresh", 2.0 * h->n_leaf * nrhs * h->ne * h->nq, 0,
-          launch_exterior_refresh(h->n_leaf, h->p, h->q, h->d_leaf_edges, h->ops64 + h->lce_base, h->didx + h->off_ce, w.ug64, u,
-                                  nrhs, s));
-    CKL();
-    if (ug_out) CK(cudaMemcpyAsync(ug_out, w.ug64, ng * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    if (iters) *iters = it;
-    if (!conv) return fail(HPS_ERR_NO_CONVERGENCE, "iterative refinement did not converge in " + std::to_string(it) + " steps");
-    return HPS_OK;
+    if (h->opts.precision == HPS_FP64) return solve_fp64(h, f, g, rho, nrhs, u, ug_out, s);
+    return solve_mixed(h, f, g, rho, nrhs, u, ug_out, iters, s);
   } catch (const CudaError& e) {
     return fail(e.code, e.msg);
   } catch (const std::bad_alloc&) {
     return fail(HPS_ERR_OOM, "host allocation failed");
+  } catch (const std::exception& e) {
+    return fail(HPS_ERR_INVALID_ARG, e.what());
   }
 }
 
@@ -2389,18 +2503,7 @@ int hps_apply(hps_handle* h, const double* coeffs, const double* u, int nrhs, do
   if (nrhs < 1 || nrhs > 4096) return fail(HPS_ERR_INVALID_ARG, "nrhs must be in [1, 4096]");
   cudaStream_t s = (cudaStream_t)stream;
   try {
-    ResidualArgs ra;
-    ra.coeffs = coeffs;
-    ra.n_leaf = h->n_leaf;
-    ra.p = h->p;
-    ra.q = h->q;
-    ra.hxy = h->dhxy;
-    ra.D = h->dD;
-    ra.D2 = h->dD2;
-    ra.Lloc = h->dLloc;
-    ra.ci = h->didx + h->off_ci;
-    ra.Lloc_df = h->dLloc_df;
-    ra.Lce_df = h->dLce_df;
+    const ResidualArgs ra = residual_args(h, coeffs);
     TIMED("leaf_apply_df", 2.0 * h->n_leaf * nrhs * 5.0 * h->p * h->p * h->p, (double)h->n_leaf * h->pp * nrhs * 16.0,
           launch_leaf_apply_df(ra, u, alpha, beta, out, nrhs, s));
     CKL();
@@ -2440,12 +2543,11 @@ int hps_adjoint(hps_handle* h, const double* ubar_in, int nrhs, const double* u,
     double* ub = w.ubar;
     CK(cudaMemsetAsync(gb, 0, nuc * sizeof(double), s));
     CK(cudaMemsetAsync(VB, 0, (size_t)h->v_rows * nrhs * sizeof(double), s));
-    const bool simt = h->opts.fp64_gemm == HPS_GEMM_SIMT;
     auto gemmT = [&](const char* step, const ItemSet& is, const double* B0, double* C, double beta) {
       const GemmDigits* dg = item_digits(h, is, 1, ops, nrhs, s);
       TIMED(("gemmT_" + std::string(step) + "_f64").c_str(), 2.0 * is.elems * nrhs, is.elems * 8.0,
             launch_gemm_items<double, double>(is.dev, is.n, ROWBLK, 1, ops, B0, nullptr, C, nullptr, idx, nrhs, beta,
-                                              s, 0, simt ? 0 : is.maxK, h->d_status, dg));
+                                              s, gemm_ctx(h, is.maxK, dg)));
     };
     auto gemmTp = [&](const char* step, const Prod& pr, const double* B0, double* C, double beta) {
       gemmT(step, pr.direct, B0, C, beta);
@@ -2469,12 +2571,12 @@ int hps_adjoint(hps_handle* h, const double* ubar_in, int nrhs, const double* u,
         const ItemSet r = leaf_range(h, is, l0, n);
         TIMED(("gemmT_" + std::string(step) + "_f64").c_str(), 2.0 * r.elems * nrhs, r.elems * 8.0,
               launch_gemm_items<double, double>(r.dev, r.n, ROWBLK, 1, h->eops, B0, nullptr, C, nullptr, idx, nrhs,
-                                                beta, s, 0, simt ? 0 : r.maxK, h->d_status));
+                                                beta, s, gemm_ctx(h, r.maxK)));
         if (is2) {
           const ItemSet r2 = leaf_range(h, *is2, l0, n);
           TIMED(("gemmT_" + std::string(step) + "_f64").c_str(), 2.0 * r2.elems * nrhs, r2.elems * 8.0,
                 launch_gemm_items<double, double>(r2.dev, r2.n, ROWBLK, 1, h->eops, B0, nullptr, C2, nullptr, idx,
-                                                  nrhs, beta, s, 0, simt ? 0 : r2.maxK, h->d_status));
+                                                  nrhs, beta, s, gemm_ctx(h, r2.maxK)));
         }
       }
     };
@@ -2507,18 +2609,7 @@ int hps_adjoint(hps_handle* h, const double* ubar_in, int nrhs, const double* u,
     CKL();
     // 6. coefficient gradients
     if (cbar) {
-      ResidualArgs ra;
-      ra.coeffs = nullptr;
-      ra.n_leaf = h->n_leaf;
-      ra.p = h->p;
-      ra.q = h->q;
-      ra.hxy = h->dhxy;
-      ra.D = h->dD;
-      ra.D2 = h->dD2;
-      ra.Lloc = h->dLloc;
-      ra.Lloc_df = h->dLloc_df;
-      ra.Lce_df = h->dLce_df;
-      ra.ci = h->didx + h->off_ci;
+      const ResidualArgs ra = residual_args(h, nullptr);
       TIMED("coeff_grad_df", 2.0 * h->n_leaf * nrhs * (5.0 * h->p * h->p * h->p + 12.0 * h->m), nuc * 16.0,
             launch_coeff_grad(ra, u, gb, cbar, nrhs, s));
       CKL();
@@ -2625,7 +2716,11 @@ extern "C" int hps_solve_noalloc(hps_handle* h, const double* f, const double* g
   const size_t bD = align256((size_t)std::max(1, h->d_rows) * R * sizeof(double));
   const size_t bG = align256((size_t)h->ns.n_gauss * R * sizeof(double));
   const size_t bP = align256((size_t)std::max(1, h->p_rows) * R * sizeof(double));
-  const size_t need = bV + bD + bG + bP;
+  // exponents of the tensor-core products (only when they can run: nrhs >= 8)
+  const long long tc_units =
+      (h->opts.fp64_gemm != HPS_GEMM_SIMT && nrhs >= 8) ? (long long)h->max_items * ((nrhs + 31) / 32) : 0;
+  const size_t bS = align256((size_t)gemm_tc_scale_bytes(tc_units));
+  const size_t need = bV + bD + bG + bP + bS;
   if (need > (size_t)HPS_NOALLOC_SCRATCH_BYTES)
     return fail(HPS_ERR_INVALID_ARG, "hps_solve_noalloc needs " + std::to_string(need) +
                                          " bytes of scratch for this tree and nrhs, more than the fixed " +
@@ -2640,16 +2735,36 @@ extern "C" int hps_solve_noalloc(hps_handle* h, const double* f, const double* g
   double* d = (double*)(b + bV);
   double* ug = (double*)(b + bV + bD);
   double* Pp = (double*)(b + bV + bD + bG);
+  int* sc = tc_units ? (int*)(b + bV + bD + bG + bP) : nullptr;
+  // the handle's per-call state points at the scratch array for the duration of the call
+  struct CallScope {
+    hps_handle* h;
+    int* sc0;
+    long long u0;
+    CallScope(hps_handle* hh, int* sc, long long units) : h(hh), sc0(hh->tc_scales), u0(hh->tc_units) {
+      h->noalloc_call = true;
+      h->tc_scales = sc;
+      h->tc_units = units;
+    }
+    ~CallScope() {
+      h->noalloc_call = false;
+      h->tc_scales = sc0;
+      h->tc_units = u0;
+    }
+  };
   try {
+    if (tc_units) gemm_tc_prepare();
+    CallScope scope(h, sc, tc_units);
     // the Gaussian-node vector is assembled by scatters, so it must start at zero; the
     // other buffers are fully written before they are read
     CK(cudaMemsetAsync(ug, 0, (size_t)h->ns.n_gauss * R * sizeof(double), s));
-    h->noalloc_call = true;
     solve_pass<double, double>(h, h->ops64, f, g, nullptr, u, ug, V, d, Pp, nrhs, s);
-    h->noalloc_call = false;
   } catch (const CudaError& e) {
-    h->noalloc_call = false;
     return fail(e.code, e.msg);
+  } catch (const std::bad_alloc&) {
+    return fail(HPS_ERR_OOM, "host allocation failed");
+  } catch (const std::exception& e) {
+    return fail(HPS_ERR_INVALID_ARG, e.what());
   }
   return HPS_OK;
 }

@@ -216,8 +216,6 @@ struct BGemm {
 void launch_bgemm(const BGemm* d, int n, int maxM, int maxN, const double* A, const double* B, double* C,
                   cudaStream_t s);
 
-// Batched gathered products.  bn: right-hand-side tile of the tiled product (16, 32 or 64;
-// 0 = fixed rule), used for nrhs > 4.
 // The operator digit planes of an item set, formed once (launch_gemm_tc_digitize): item i's
 // K steps at dig + step[i] * gemm_tc_digit_bytes(1), its 64 row exponents at er + 64 i.
 struct GemmDigits {
@@ -226,26 +224,41 @@ struct GemmDigits {
   const int* er = nullptr;
 };
 
-// maxK > 0 states the largest inner dimension of the items: FP64 products with maxK <= 448
-// and nrhs >= 8 then run on the tensor cores (launch_gemm_tc) when its exponent buffer is
-// large enough, else on the SIMT kernels; status receives -1 if a tensor-core wait times out;
-// dg (optional) holds the items' operator digits.
+// Options of one batched product launch.
+//   bn        right-hand-side tile of the SIMT tiled product (16, 32 or 64; 0 = fixed rule)
+//   maxK      > 0 states the largest inner dimension of the items: FP64 products with
+//             maxK <= 448 and nrhs >= 8 then run on the tensor cores (launch_gemm_tc) when
+//             the exponent buffer below is large enough, else on the SIMT kernels
+//   status    receives -1 if a tensor-core wait times out
+//   dg        optional operator digits of the items
+//   tc_scales the tensor-core product's per-unit exponent buffer (gemm_tc_scale_bytes(units)
+//             bytes, owned by the caller) and its capacity in units
+struct GemmCtx {
+  int bn = 0;
+  int maxK = 0;
+  int* status = nullptr;
+  const GemmDigits* dg = nullptr;
+  int* tc_scales = nullptr;
+  long long tc_units = 0;
+};
+
 template <typename TA, typename TV>
 void launch_gemm_items(const GemmItem* items, int nitems, int maxM, int trans, const TA* A,
                        const TV* B0, const TV* B1, TV* C, const TV* Add, const int* idx,
-                       int nrhs, double beta, cudaStream_t s, int bn = 0, int maxK = 0,
-                       int* status = nullptr, const GemmDigits* dg = nullptr);
+                       int nrhs, double beta, cudaStream_t s, const GemmCtx& cx);
 
 // FP64 gathered products on the tcgen05 tensor cores by exact digit slicing (k_gemm_tc.cu):
-// items of at most 64 rows and K <= 448.  gemm_tc_reserve grows the per-unit exponent
-// buffer (call outside stream capture: units = items x ceil(nrhs / 32)); launch_gemm_tc
-// returns false, launching nothing, when the buffer is too small.  With dg the operator's
-// digits are read from it instead of being formed (same results).
+// items of at most 64 rows and K <= 448.  A launch needs units = items x ceil(nrhs / 32)
+// entries of the exponent buffer cx.tc_scales; launch_gemm_tc returns false, launching
+// nothing, when it is missing or too small.  With cx.dg the operator's digits are read from
+// it instead of being formed (same results).  gemm_tc_prepare does the per-device set-up
+// (call it outside stream capture; launches do it themselves otherwise).
 bool gemm_tc_eligible(int maxK, int nrhs);
-void gemm_tc_reserve(long long units);
+long long gemm_tc_scale_bytes(long long units);
+void gemm_tc_prepare();
 bool launch_gemm_tc(const GemmItem* items, int nitems, int trans, const double* A, const double* B0,
                     const double* B1, double* C, const double* Add, const int* idx, int nrhs, double beta,
-                    int* status, cudaStream_t s, const GemmDigits* dg);
+                    cudaStream_t s, const GemmCtx& cx);
 // bytes of the digit planes of `steps` K steps; fill adig / aer for the items (astep: each
 // item's first step, prefix sums of ceil(K / 16))
 long long gemm_tc_digit_bytes(long long steps);
@@ -306,6 +319,7 @@ void launch_leaf_apply_df(const ResidualArgs& a, const double* u, double alpha, 
 void launch_jump_residual(const int* pairs, int npairs, int q, const double* vflux,
                           double* rho_out, int nrhs, cudaStream_t s);
 void launch_absmax(const double* x, long long n, double* out, cudaStream_t s);
+void launch_absmax_f32(const float* x, long long n, double* out, cudaStream_t s);  // max |x| as a double
 // Row combinations dst[d] = A[a] (+ sign * B[b] if b >= 0), entries (d, a, b, sign) at tab,
 // rows of nrhs values.
 void launch_row_combine(const int* tab, int n, double* dst, const double* A, const double* B, int nrhs,

@@ -30,8 +30,10 @@
 //              stages deep;
 //   warp 16    one thread issues the digit-pair products of each K step into TMEM.
 // Handoffs are mbarriers with bounded waits; a timeout stops every role (status -1).
+#include <algorithm>
 #include <cstdint>
 #include <cstdio>
+#include <mutex>
 
 #include <cuda_bf16.h>
 
@@ -634,52 +636,59 @@ __global__ void __launch_bounds__(G_THREADS, 1) gemm_tc_kernel(const GemmItem* _
 
 bool gemm_tc_eligible(int maxK, int nrhs) { return maxK > 0 && maxK <= GKMAX && nrhs >= 8; }
 
-// exponent buffer, grown outside stream capture (a launch that would need more falls back)
-static int* g_scales = nullptr;
-static long long g_scales_units = 0;
+long long gemm_tc_scale_bytes(long long units) { return units * GSC * (long long)sizeof(int); }
 
-static int g_nsm = 0;
+// Per-device set-up, once per device (outside stream capture): the SM count and the
+// kernels' dynamic shared-memory limit, which is a property of the device's context.
+namespace {
+constexpr int kTcMaxDev = 64;
+std::mutex g_tc_mu;
+int g_tc_nsm[kTcMaxDev] = {0};
+}  // namespace
 
-// device properties and the kernels' shared-memory limit, once (outside stream capture)
-static void gemm_tc_init() {
-  if (g_nsm) return;
-  int dev = 0, nsm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaFuncSetAttribute(gemm_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(GShared));
-  cudaFuncSetAttribute(gemm_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(GShared));
-  g_nsm = nsm > 0 ? nsm : 1;
+static int gemm_tc_nsm() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kTcMaxDev) {
+    cudaGetLastError();
+    return 0;
+  }
+  std::lock_guard<std::mutex> lk(g_tc_mu);
+  if (!g_tc_nsm[dev]) {
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(gemm_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(GShared));
+    cudaFuncSetAttribute(gemm_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(GShared));
+    if (cudaGetLastError() != cudaSuccess) return 0;
+    g_tc_nsm[dev] = nsm > 0 ? nsm : 1;
+  }
+  return g_tc_nsm[dev];
 }
 
-void gemm_tc_reserve(long long units) {
-  gemm_tc_init();
-  if (units <= g_scales_units) return;
-  if (g_scales) cudaFree(g_scales);
-  g_scales = nullptr;
-  g_scales_units = 0;
-  if (cudaMalloc(&g_scales, (size_t)units * GSC * sizeof(int)) == cudaSuccess) g_scales_units = units;
-  else cudaGetLastError();
-}
+void gemm_tc_prepare() { (void)gemm_tc_nsm(); }
 
 bool launch_gemm_tc(const GemmItem* items, int nitems, int trans, const double* A, const double* B0,
                     const double* B1, double* C, const double* Add, const int* idx, int nrhs, double beta,
-                    int* status, cudaStream_t s, const GemmDigits* dg) {
+                    cudaStream_t s, const GemmCtx& cx) {
   if (nitems <= 0) return true;
   const long long units = (long long)nitems * ((nrhs + GN - 1) / GN);
-  if (units > g_scales_units || !g_nsm) return false;
-  const int grid = (int)std::min<long long>(g_nsm, units);
+  if (!cx.tc_scales || units > cx.tc_units) return false;
+  const int nsm = gemm_tc_nsm();
+  if (!nsm) return false;
+  const int grid = (int)std::min<long long>(nsm, units);
+  const GemmDigits* dg = cx.dg;
   const unsigned char* adig = dg ? dg->dig : nullptr;
   const long long* astep = dg ? dg->step : nullptr;
   const int* aer = dg ? dg->er : nullptr;
   const int rows = adig ? 0 : 1;
+  int* scales = cx.tc_scales;
   if (trans) {
-    gemm_scales_kernel<true><<<(unsigned)units, 256, 0, s>>>(items, A, B0, B1, idx, nrhs, g_scales, rows);
+    gemm_scales_kernel<true><<<(unsigned)units, 256, 0, s>>>(items, A, B0, B1, idx, nrhs, scales, rows);
     gemm_tc_kernel<true><<<grid, G_THREADS, sizeof(GShared), s>>>(items, nitems, A, B0, B1, C, Add, idx, nrhs, beta,
-                                                                  g_scales, adig, astep, aer, status);
+                                                                  scales, adig, astep, aer, cx.status);
   } else {
-    gemm_scales_kernel<false><<<(unsigned)units, 256, 0, s>>>(items, A, B0, B1, idx, nrhs, g_scales, rows);
+    gemm_scales_kernel<false><<<(unsigned)units, 256, 0, s>>>(items, A, B0, B1, idx, nrhs, scales, rows);
     gemm_tc_kernel<false><<<grid, G_THREADS, sizeof(GShared), s>>>(items, nitems, A, B0, B1, C, Add, idx, nrhs, beta,
-                                                                   g_scales, adig, astep, aer, status);
+                                                                   scales, adig, astep, aer, cx.status);
   }
   return true;
 }

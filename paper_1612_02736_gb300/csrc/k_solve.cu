@@ -25,69 +25,155 @@ __device__ __forceinline__ int map_row(const int* __restrict__ idx, int base_or_
   return base_or_off < 0 ? row_base + k : row_base + idx[base_or_off + k];
 }
 
-constexpr int KC = 256;  // K chunk staged in shared memory (GEMV path)
+constexpr int KC = 256;  // K chunk staged in shared memory (transposed GEMV path)
 constexpr int ROWS_HINT = 64;  // rows of one split-K output block
 
-// nrhs <= NR (1, 2 or 4).  Non-transposed: one warp per output row, lanes split K.
+// Warp-wide sums of V values per lane ("transposing" reduction: every shuffle step halves
+// the values a lane carries while V > 1).  On return lane l holds, in v[0 .. n), n =
+// max(1, V / 32), the sums of values j = base * n + t with base = l for V >= 32 and
+// base = l >> (5 - log2 V) otherwise (the lanes sharing a base hold equal sums).  V is a
+// power of two.  V - 1 + max(0, 5 - log2 V) shuffles instead of 5 V.
+template <int V, typename T>
+__device__ __forceinline__ void warp_transpose_sum(T (&v)[V], int lane) {
+  int n = V;
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    if (n > 1) {
+      const bool up = (lane & o) != 0;
+      const int hn = n / 2;
+#pragma unroll
+      for (int j = 0; j < V / 2; ++j) {
+        if (j < hn) {
+          const T send = up ? v[j] : v[j + hn];
+          const T keep = up ? v[j + hn] : v[j];
+          v[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+      }
+      n = hn;
+    } else {
+      v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+    }
+  }
+}
+
+template <typename T> struct Vec16;
+template <> struct Vec16<double> { using type = double2; static constexpr int n = 2; };
+template <> struct Vec16<float> { using type = float4; static constexpr int n = 4; };
+
+template <typename T>
+__device__ __forceinline__ T vget(const typename Vec16<T>::type& a, int j);
+template <>
+__device__ __forceinline__ double vget<double>(const double2& a, int j) { return j == 0 ? a.x : a.y; }
+template <>
+__device__ __forceinline__ float vget<float>(const float4& a, int j) {
+  return j == 0 ? a.x : (j == 1 ? a.y : (j == 2 ? a.z : a.w));
+}
+
+// Streaming products for few right-hand sides (nrhs <= NR), non-transposed: the bytes of
+// the stored operator dominate, so the kernel is built to stream them.  One CTA of 256
+// threads per item (<= 64 rows).  The item's gathered vector block is staged in shared
+// memory in chunks of KC entries ([k][NR], zero past nrhs); warp w owns rows w, w + 8, ...
+// (at most 8) and accumulates all of them at once.  Those rows start 8 lda apart, so they
+// share one offset modulo the 16-byte vector width: after a scalar head of fewer than VW
+// entries the warp reads every row with 16-byte streaming loads (each operator entry is
+// read once per solve), 8 rows in flight per lane, and each staged vector entry once for
+// all 8 rows.  Lane sums are combined by a transposing warp reduction.
 template <typename TA, typename TV, int NR>
 __global__ void __launch_bounds__(256) gemv_items_kernel(const GemmItem* __restrict__ items,
                                                          const TA* __restrict__ A, const TV* __restrict__ B0,
                                                          const TV* __restrict__ B1, TV* __restrict__ C,
                                                          const TV* __restrict__ Add, const int* __restrict__ idx,
                                                          int nrhs, TV beta) {
-  using Acc = TV;
+  using VecT = typename Vec16<TA>::type;
+  constexpr int VW = Vec16<TA>::n;
+  constexpr int KC = 16384 / (NR * (int)sizeof(TV));  // 16 KB of staged vector entries
+  constexpr int RW = 8;                                // rows per warp
+  __shared__ __align__(16) TV xs[KC * NR];
   const GemmItem it = items[blockIdx.x];
-  __shared__ Acc Bs[KC][NR];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const TA* Ab = A + it.a_off;
-  Acc acc[8][NR];
+  const int nrow = it.M > warp ? (it.M - warp + 7) / 8 : 0;  // rows warp + 8 i < M
+  const TA* Aw = A + it.a_off + (long long)warp * it.lda;
+  const long long rs = 8ll * it.lda;                           // row step within the warp
+  TV acc[RW * NR];
 #pragma unroll
-  for (int i = 0; i < 8; ++i)
-#pragma unroll
-    for (int r = 0; r < NR; ++r) acc[i][r] = Acc(0);
+  for (int j = 0; j < RW * NR; ++j) acc[j] = TV(0);
   for (int k0 = 0; k0 < it.K; k0 += KC) {
     const int kc = min(KC, it.K - k0);
     for (int e = tid; e < kc * NR; e += 256) {
-      const int kk = e / NR, r = e - (e / NR) * NR;
+      const int kk = e / NR, r = e % NR;
       const int k = k0 + kk;
-      Acc v = Acc(0);
+      TV v = TV(0);
       if (r < nrhs) {
         if (k < it.kseg) v = B0[(long long)map_row(idx, it.b0_idx, it.b0_row, k) * nrhs + r];
         else v = B1[(long long)map_row(idx, it.b1_idx, it.b1_row, k - it.kseg) * nrhs + r];
       }
-      Bs[kk][r] = v;
+      xs[e] = v;
     }
     __syncthreads();
+    if (nrow > 0) {
+      // head: entries before the first 16-byte boundary of this warp's rows
+      const long long o0 = it.a_off + (long long)warp * it.lda + k0;
+      const int h = min(kc, (int)((VW - (int)(o0 % VW)) % VW));
+      const int nv = (kc - h) / VW;
+      const int t0 = h + nv * VW;  // first tail entry
+      const TA* Ak = Aw + k0;
+      // scalar entries: the head (lane l < h takes entry l) and the tail (lane l takes entry
+      // t0 + l while it is below kc)
+#pragma unroll 1
+      for (int pass = 0; pass < 2; ++pass) {
+        const int kk = pass == 0 ? (lane < h ? lane : -1) : (t0 + lane < kc ? t0 + lane : -1);
+        if (kk < 0) continue;
+        TV xv[NR];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int row = warp + 8 * i;
-      if (row >= it.M) break;
-      const TA* Ar = Ab + (long long)row * it.lda + k0;
-      for (int kk = lane; kk < kc; kk += 32) {
-        const Acc a = (Acc)Ar[kk];
+        for (int r = 0; r < NR; ++r) xv[r] = xs[kk * NR + r];
 #pragma unroll
-        for (int r = 0; r < NR; ++r) acc[i][r] += a * Bs[kk][r];
+        for (int i = 0; i < RW; ++i)
+          if (i < nrow) {
+            const TV a = (TV)Ak[i * rs + kk];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) acc[i * NR + r] += a * xv[r];
+          }
+      }
+      // body: 16-byte vectors
+      for (int v = lane; v < nv; v += 32) {
+        const int kk = h + v * VW;
+        VecT a[RW];
+#pragma unroll
+        for (int i = 0; i < RW; ++i)
+          if (i < nrow) a[i] = __ldcs(reinterpret_cast<const VecT*>(Ak + i * rs + kk));
+#pragma unroll
+        for (int j = 0; j < VW; ++j) {
+          TV xv[NR];
+#pragma unroll
+          for (int r = 0; r < NR; ++r) xv[r] = xs[(kk + j) * NR + r];
+#pragma unroll
+          for (int i = 0; i < RW; ++i)
+            if (i < nrow) {
+              const TV aij = (TV)vget<TA>(a[i], j);
+#pragma unroll
+              for (int r = 0; r < NR; ++r) acc[i * NR + r] += aij * xv[r];
+            }
+        }
       }
     }
     __syncthreads();
   }
+  if (nrow == 0) return;
+  constexpr int V = RW * NR;
+  warp_transpose_sum<V>(acc, lane);
+  constexpr int NV = V >= 32 ? V / 32 : 1;
+  constexpr int SH = V >= 32 ? 0 : (V == 16 ? 1 : (V == 8 ? 2 : (V == 4 ? 3 : (V == 2 ? 4 : 5))));
+  if ((lane & ((1 << SH) - 1)) != 0) return;
+  const int base = lane >> SH;
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
+  for (int t = 0; t < NV; ++t) {
+    const int j = base * NV + t;
+    const int i = j / NR, r = j % NR;
     const int row = warp + 8 * i;
-    if (row >= it.M) break;
-#pragma unroll
-    for (int r = 0; r < NR; ++r) {
-      Acc v = acc[i][r];
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);  // all lanes hold the sum
-      acc[i][r] = v;
-    }
-    if (lane < NR && lane < nrhs) {
-      Acc v = Acc(0);
-#pragma unroll
-      for (int r = 0; r < NR; ++r)
-        if (r == lane) v = acc[i][r];
-      const long long cr = (long long)map_row(idx, it.c_idx, it.c_row, row) * nrhs + lane;
-      if (it.add_row >= 0) v += Add[(long long)(it.add_row + row) * nrhs + lane];
+    if (row < it.M && r < nrhs) {
+      TV v = acc[t];
+      const long long cr = (long long)map_row(idx, it.c_idx, it.c_row, row) * nrhs + r;
+      if (it.add_row >= 0) v += Add[(long long)(it.add_row + row) * nrhs + r];
       C[cr] = (beta != TV(0) ? beta * C[cr] : TV(0)) + v;
     }
   }
@@ -305,10 +391,11 @@ __global__ void axpy_kernel(const TI* __restrict__ x, double* __restrict__ y, lo
     y[e] += (double)x[e];
 }
 
-__global__ void absmax_kernel(const double* __restrict__ x, long long n, unsigned long long* __restrict__ out) {
+template <typename T>
+__global__ void absmax_kernel(const T* __restrict__ x, long long n, unsigned long long* __restrict__ out) {
   double m = 0.0;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
-    m = fmax(m, fabs(x[e]));
+    m = fmax(m, fabs((double)x[e]));
   for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
   __shared__ double red[32];
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
@@ -417,25 +504,29 @@ inline int grid_for(long long n, int bs = 256, int cap = 8192) {
 template <typename TA, typename TV>
 void launch_gemm_items(const GemmItem* items, int nitems, int maxM, int trans, const TA* A, const TV* B0,
                        const TV* B1, TV* C, const TV* Add, const int* idx, int nrhs, double beta,
-                       cudaStream_t s, int bn, int maxK, int* status, const GemmDigits* dg) {
+                       cudaStream_t s, const GemmCtx& cx) {
   (void)maxM;
   if (nitems <= 0) return;
   if constexpr (std::is_same<TA, double>::value && std::is_same<TV, double>::value) {
-    if (gemm_tc_eligible(maxK, nrhs) &&
-        launch_gemm_tc(items, nitems, trans, A, B0, B1, C, Add, idx, nrhs, beta, status, s, dg))
+    if (gemm_tc_eligible(cx.maxK, nrhs) && launch_gemm_tc(items, nitems, trans, A, B0, B1, C, Add, idx, nrhs, beta, s, cx))
       return;
   }
+  const int bn = cx.bn;
   const TV b = (TV)beta;
-  if (nrhs <= 4) {
-    if (trans) {
-      if (nrhs == 1) gemvT_items_kernel<TA, TV, 1><<<nitems, 256, 0, s>>>(items, A, B0, B1, C, Add, idx, nrhs, b);
-      else if (nrhs == 2) gemvT_items_kernel<TA, TV, 2><<<nitems, 256, 0, s>>>(items, A, B0, B1, C, Add, idx, nrhs, b);
-      else gemvT_items_kernel<TA, TV, 4><<<nitems, 256, 0, s>>>(items, A, B0, B1, C, Add, idx, nrhs, b);
-    } else {
-      if (nrhs == 1) gemv_items_kernel<TA, TV, 1><<<nitems, 256, 0, s>>>(items, A, B0, B1, C, Add, idx, nrhs, b);
-      else if (nrhs == 2) gemv_items_kernel<TA, TV, 2><<<nitems, 256, 0, s>>>(items, A, B0, B1, C, Add, idx, nrhs, b);
-      else gemv_items_kernel<TA, TV, 4><<<nitems, 256, 0, s>>>(items, A, B0, B1, C, Add, idx, nrhs, b);
-    }
+  if (trans && nrhs <= 4) {
+    if (nrhs == 1) gemvT_items_kernel<TA, TV, 1><<<nitems, 256, 0, s>>>(items, A, B0, B1, C, Add, idx, nrhs, b);
+    else if (nrhs == 2) gemvT_items_kernel<TA, TV, 2><<<nitems, 256, 0, s>>>(items, A, B0, B1, C, Add, idx, nrhs, b);
+    else gemvT_items_kernel<TA, TV, 4><<<nitems, 256, 0, s>>>(items, A, B0, B1, C, Add, idx, nrhs, b);
+    return;
+  }
+  // streaming products: up to 4 right-hand sides in FP64 (bound by the FP64 pipe beyond),
+  // up to 8 in FP32
+  if (!trans && nrhs <= (sizeof(TV) == 8 ? 4 : 8)) {
+    if (nrhs == 1) gemv_items_kernel<TA, TV, 1><<<nitems, 256, 0, s>>>(items, A, B0, B1, C, Add, idx, nrhs, b);
+    else if (nrhs == 2) gemv_items_kernel<TA, TV, 2><<<nitems, 256, 0, s>>>(items, A, B0, B1, C, Add, idx, nrhs, b);
+    else if (nrhs <= 4) gemv_items_kernel<TA, TV, 4><<<nitems, 256, 0, s>>>(items, A, B0, B1, C, Add, idx, nrhs, b);
+    else if constexpr (sizeof(TV) == 4)
+      gemv_items_kernel<TA, TV, 8><<<nitems, 256, 0, s>>>(items, A, B0, B1, C, Add, idx, nrhs, b);
     return;
   }
   // right-hand-side tile: the caller's (autotuned) choice, else 16 up to 16 rhs and 64 above;
@@ -509,7 +600,10 @@ void launch_axpy_to_f64(const TI* x, double* y, long long n, cudaStream_t s) {
 }
 
 void launch_absmax(const double* x, long long n, double* out, cudaStream_t s) {
-  absmax_kernel<<<grid_for(n, 256, 1024), 256, 0, s>>>(x, n, reinterpret_cast<unsigned long long*>(out));
+  absmax_kernel<double><<<grid_for(n, 256, 1024), 256, 0, s>>>(x, n, reinterpret_cast<unsigned long long*>(out));
+}
+void launch_absmax_f32(const float* x, long long n, double* out, cudaStream_t s) {
+  absmax_kernel<float><<<grid_for(n, 256, 1024), 256, 0, s>>>(x, n, reinterpret_cast<unsigned long long*>(out));
 }
 
 template <typename TV>
@@ -527,10 +621,10 @@ void launch_jump_residual(const int* pairs, int npairs, int q, const double* vfl
 
 template void launch_gemm_items<double, double>(const GemmItem*, int, int, int, const double*, const double*,
                                                 const double*, double*, const double*, const int*, int, double,
-                                                cudaStream_t, int, int, int*, const GemmDigits*);
+                                                cudaStream_t, const GemmCtx&);
 template void launch_gemm_items<float, float>(const GemmItem*, int, int, int, const float*, const float*,
                                               const float*, float*, const float*, const int*, int, double,
-                                              cudaStream_t, int, int, int*, const GemmDigits*);
+                                              cudaStream_t, const GemmCtx&);
 template void launch_split_reduce<double>(const SplitRed*, int, const double*, double*, const double*, const int*,
                                           int, double, cudaStream_t);
 template void launch_split_reduce<float>(const SplitRed*, int, const float*, float*, const float*, const int*, int,

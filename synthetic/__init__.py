@@ -101,13 +101,20 @@ class VarCoeffProblem:
         return u_star(x, y)
 
 
-def heat_initial(x, y, member=0, n_gauss=20):
-    """Sum of 20 Gaussians a_i exp(-alpha_i |x - x_i|^2), a_i ~ U(0.5, 1),
-    alpha_i ~ U(50, 300), centres ~ U[0.1, 0.9]^2; ``member`` offsets the seed."""
+def heat_initial_params(member=0, n_gauss=20):
+    """(a, alpha, centres) of ensemble member ``member``: a_i ~ U(0.5, 1),
+    alpha_i ~ U(50, 300), centres ~ U[0.1, 0.9]^2 (seed offset 1000 + member)."""
     gen = rng(1000 + member)
     a = gen.uniform(0.5, 1.0, n_gauss)
     al = gen.uniform(50.0, 300.0, n_gauss)
     c = gen.uniform(0.1, 0.9, (n_gauss, 2))
+    return a, al, c
+
+
+def heat_initial(x, y, member=0, n_gauss=20):
+    """Sum of 20 Gaussians a_i exp(-alpha_i |x - x_i|^2) with the parameters of
+    ``heat_initial_params``."""
+    a, al, c = heat_initial_params(member, n_gauss)
     out = np.zeros(np.broadcast(np.asarray(x), np.asarray(y)).shape)
     for i in range(n_gauss):
         out = out + a[i] * np.exp(-al[i] * ((x - c[i, 0]) ** 2 + (y - c[i, 1]) ** 2))

@@ -3,23 +3,7 @@
 comes from the oracle or from ``synthetic``."""
 import numpy as np
 
-from oracle import spectral as sp
-
-
-def leaf_points(tree, p):
-    """(X, Y), each (n_leaf, p^2): leaf Chebyshev node coordinates, node iy * p + ix."""
-    X, Y = [], []
-    for lf in range(tree.n_leaves):
-        x0, y0, x1, y1 = tree.leaf_rect(lf)
-        x, y = sp.leaf_cheb_points(x0, y0, x1 - x0, y1 - y0, p)
-        X.append(x)
-        Y.append(y)
-    return np.array(X), np.array(Y)
-
-
-def boundary_points(tree):
-    gp = tree.gauss_points()
-    return gp[tree.boundary, 0], gp[tree.boundary, 1]
+from oracle.points import boundary_points, leaf_points  # noqa: F401  (re-exported)
 
 
 def poly_data(X, Y, coeffs, a, b):
