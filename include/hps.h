@@ -42,7 +42,7 @@ extern "C" {
 typedef enum {
   HPS_OK = 0,
   HPS_ERR_INVALID_ARG = 1,   /* bad pointer, size, tree or option                      */
-  HPS_ERR_NOT_ELLIPTIC = 2,  /* reserved: c11 c22 - c12^2 <= 0 detected by the caller    */
+  HPS_ERR_NOT_ELLIPTIC = 2,  /* c11 <= 0 or c11 c22 - c12^2 <= 0 at an interior node     */
   HPS_ERR_SINGULAR = 3,      /* a leaf or merge pivot fell below tiny * scale            */
   HPS_ERR_OOM = 4,           /* the allocator returned NULL                              */
   HPS_ERR_CUDA = 5,          /* a CUDA runtime call failed (message has the CUDA text)   */
@@ -94,10 +94,11 @@ typedef struct {
                         * rebuild F, S, H chunk by chunk whenever a solve or adjoint needs
                         * them (the storage-efficient variant of the Sec. 5.4 remark;
                         * HPS_FP64 only)                                                    */
-  double ir_tol;       /* HPS_MIXED: target of the estimated remaining error relative to
-                        * max|u| (see hps_solve); 0 means 1e-9, ten times below 1e-8    */
+  double ir_tol;       /* HPS_MIXED: bound on the estimated remaining error relative to
+                        * max|u| (see hps_solve); 0 means 1e-8                          */
   int ir_max_iter;     /* HPS_MIXED: refinement steps allowed; 0 means 10                  */
-  int fp64_top_levels; /* HPS_MIXED: number of top merge levels kept in FP64; -1 means 1   */
+  int fp64_top_levels; /* HPS_MIXED: number of top merge levels eliminated in FP64 (their
+                        * operators are stored in FP32 like the rest); -1 means 5         */
   int use_graphs;      /* HPS_FP64 solves without a flux-jump input: 1 (default) replays
                         * one captured CUDA graph of the whole sweep per nrhs (the inputs
                         * are copied into and the result out of staging buffers the
@@ -127,6 +128,11 @@ typedef struct {
                         * handles only; hps_adjoint and hps_solve_noalloc return STATE     */
   int fp64_gemm;       /* FP64 solve and adjoint products: HPS_GEMM_TENSOR (default) or
                         * HPS_GEMM_SIMT.  The two agree to FP64 rounding, not bit for bit   */
+  int fp32_gemm;       /* FP32 sweep products of HPS_MIXED solves with more than 8 right-hand
+                        * sides: HPS_GEMM_TENSOR (default: tcgen05 tensor cores, every entry
+                        * split into three bf16 pieces, the six piece pairs of weight >= 2^-16
+                        * summed in FP32) or HPS_GEMM_SIMT (FP32 FFMA).  Both are FP32-accurate
+                        * products; the refined solution meets the same tolerance            */
 } hps_opts;
 
 /* Fills *opts with the defaults above (FP64, q = p - 1, store leaf operators, graphs on,
@@ -179,8 +185,11 @@ int hps_plan_check(const hps_tree* tree, int p, const hps_opts* opts);
  * step forms A on each leaf, factors A_ci,ci and writes F, S, H, T (Sec. 3, Eqs.
  * alpine1-alpine4); each merge forms X, S, T from the children (Sec. 4).  p in [4, 32].
  * The library does not keep coeffs_dev.  opts and alloc may be NULL (defaults).  The
+ * coefficients are checked first at every interior node: INVALID_ARG if one is not finite,
+ * NOT_ELLIPTIC if c11 <= 0 or c11 c22 - c12^2 <= 0 (the leaf index is in the message).  The
  * call synchronises the stream before it returns and reports SINGULAR with the box id
- * in the message if a pivot broke down.  *out receives the handle. */
+ * in the message if a pivot broke down; an allocation failure gives OOM with everything
+ * allocated so far released.  *out receives the handle. */
 int hps_build(const hps_tree* tree, const double* coeffs_dev, int p, const hps_opts* opts,
               const hps_allocator* alloc, void* stream, hps_handle** out);
 
@@ -196,9 +205,9 @@ int hps_build(const hps_tree* tree, const double* coeffs_dev, int p, const hps_o
  * double-float arithmetic) with FP64 accumulation.  Until a handle is calibrated the
  * refinement is adaptive, synchronising after every correction du: it stops when
  * max|du| <= ir_tol max|u|, or when the observed contraction of two successive corrections
- * (ratio r < 1/2) predicts the remaining error r max|du| below that.  Those ratios
+ * (ratio r < 1/2) predicts the remaining error 2 r max|du| below that.  Those ratios
  * calibrate a contraction bound rho (twice the largest ratio) and the number n of
- * corrections that bring the initial solve below tolerance; later calls without flux-jump
+ * corrections that bring the initial solve's error below ir_tol; later calls without flux-jump
  * data run the initial solve and n corrections without a test in between (one CUDA graph
  * from the second such call with the same nrhs when use_graphs is set), synchronise once
  * and accept when rho max|du_n| <= ir_tol max|u|, else refine on adaptively.  NaN or

@@ -40,7 +40,7 @@ class hps_opts(C.Structure):
                 ("ir_tol", C.c_double), ("ir_max_iter", C.c_int), ("fp64_top_levels", C.c_int),
                 ("use_graphs", C.c_int), ("autotune", C.c_int), ("autotune_cache", C.c_char_p),
                 ("shared_leaf", C.c_int), ("bc_we", C.c_int), ("bc_sn", C.c_int),
-                ("fp64_gemm", C.c_int)]
+                ("fp64_gemm", C.c_int), ("fp32_gemm", C.c_int)]
 
 
 P = C.c_void_p

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 OBJDIR = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libhps_gb300.so")
 
-SOURCES = ["hps_api.cu", "k_gj.cu", "k_gemm_tc.cu", "k_leaf.cu", "k_merge.cu", "k_solve.cu", "k_df.cu", "autotune.cpp",
+SOURCES = ["hps_api.cu", "k_gj.cu", "k_gemm_tc.cu", "k_gemm_tc32.cu", "k_leaf.cu", "k_merge.cu", "k_solve.cu", "k_df.cu", "autotune.cpp",
            "tables.cpp", "timing.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-lineinfo", "-I" + os.path.join(ROOT, "include")]

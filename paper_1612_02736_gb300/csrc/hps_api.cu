@@ -4,6 +4,7 @@
 // step of the build, the solve, the residual and the adjoint runs in the kernels.
 #include <algorithm>
 #include <array>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -112,6 +113,13 @@ T* upload(Alloc& al, cudaStream_t s, const std::vector<T>& v, std::vector<DBuf>&
 }
 
 constexpr int ROWBLK = 64;
+
+// HPS_MIXED: merge levels at the top of the tree eliminated in FP64 by default.  The FP32
+// eliminations below them bound the contraction of the refinement: on the 64 x 64-leaf,
+// p = 16 variable-coefficient workload one correction leaves a relative error of 1.1e-8
+// with 1 FP64 level, 5.8e-9 with 3, 2.0e-9 with 5, 6.7e-11 with all of them, while the
+// build time grows from 68 to 86 ms (FP64 build: 88 ms).
+constexpr int kFp64TopLevels = 5;
 
 #define TIMED(name, fl, by, ...)                                  \
   do {                                                            \
@@ -273,7 +281,7 @@ struct hps_handle {
   int p = 0, q = 0, m = 0, nq = 0, ne = 0, pp = 0, n_leaf = 0, n_bdry = 0;
   // tables
   double *dD = nullptr, *dD2 = nullptr, *dLs = nullptr, *dDLs = nullptr, *dLloc = nullptr, *dDceL = nullptr;
-  float2 *dLloc_df = nullptr, *dLce_df = nullptr;
+  float2 *dLloc_df = nullptr, *dLce_df = nullptr, *dD_df = nullptr, *dD2_df = nullptr;
   double* dhxy = nullptr;
   int* didx = nullptr;
   int* d_leaf_edges = nullptr;
@@ -653,7 +661,7 @@ void make_plan(hps_handle* h, HostPlan& hp) {
   h->levels.assign(H, Level());
   for (int b = 0; b < nb; ++b)
     if (t.boxes[b].leaf < 0) h->levels[t.boxes[b].height - 1].boxes.push_back(b);
-  int top64 = h->opts.fp64_top_levels < 0 ? 1 : h->opts.fp64_top_levels;
+  int top64 = h->opts.fp64_top_levels < 0 ? kFp64TopLevels : h->opts.fp64_top_levels;
   hp.lv.assign(H, LevelHost());
   // T store offsets per box (children T blocks live there until the build ends): the
   // leaves first, in leaf order (the leaf extraction writes them with a fixed stride),
@@ -910,7 +918,7 @@ struct PlanCache {
 namespace {
 
 std::array<int, 6> plan_key(int p, const hps_opts& o, bool shared) {
-  const int top = o.precision == HPS_FP64 ? 0 : (o.fp64_top_levels < 0 ? 1 : o.fp64_top_levels);
+  const int top = o.precision == HPS_FP64 ? 0 : (o.fp64_top_levels < 0 ? kFp64TopLevels : o.fp64_top_levels);
   return {p, o.q, o.precision, top, shared ? 1 : o.store_leaf_ops, shared ? 1 : 0};
 }
 
@@ -1503,45 +1511,59 @@ void ensure_ws(hps_handle* h, int nrhs, cudaStream_t s) {
   h->drop_graph();  // a captured sweep points into the old buffers
   for (void* p : w.ptrs) h->al.put(p, s);
   w = Workspace();
-  w.nrhs = nrhs;
+  h->tc_scales = nullptr;
+  h->tc_units = 0;
+  // the new buffers are made in a local workspace and installed only when all of them
+  // exist: a failed allocation releases the others and leaves the handle without a
+  // workspace (the next call makes one again)
+  Workspace nw;
+  nw.nrhs = nrhs;
   auto get = [&](size_t bytes) {
-    void* p = h->al.get(bytes, s);
-    w.ptrs.push_back(p);
+    void* p = nullptr;
+    try {
+      p = h->al.get(bytes, s);
+    } catch (...) {
+      for (void* q : nw.ptrs) h->al.put(q, s);
+      throw;
+    }
+    nw.ptrs.push_back(p);
     return p;
   };
   const long long R = nrhs;
   const long long nuc = (long long)h->n_leaf * h->pp * R;
   const long long ng = (long long)h->ns.n_gauss * R;
   const bool mixed = h->opts.precision == HPS_MIXED;
-  w.V64 = (double*)get((size_t)h->v_rows * R * sizeof(double));
-  w.P64 = (double*)get((size_t)std::max(1, h->p_rows) * R * sizeof(double));
-  w.d64 = (double*)get((size_t)std::max(1, h->d_rows) * R * sizeof(double));
-  w.ug64 = (double*)get((size_t)ng * sizeof(double));
+  nw.V64 = (double*)get((size_t)h->v_rows * R * sizeof(double));
+  nw.P64 = (double*)get((size_t)std::max(1, h->p_rows) * R * sizeof(double));
+  nw.d64 = (double*)get((size_t)std::max(1, h->d_rows) * R * sizeof(double));
+  nw.ug64 = (double*)get((size_t)ng * sizeof(double));
   if (mixed) {
-    w.V32 = (float*)get((size_t)h->v_rows * R * sizeof(float));
-    w.P32 = (float*)get((size_t)std::max(1, h->p_rows) * R * sizeof(float));
-    w.d32 = (float*)get((size_t)std::max(1, h->d_rows) * R * sizeof(float));
-    w.ug32 = (float*)get((size_t)ng * sizeof(float));
-    w.g32 = (float*)get((size_t)nuc * sizeof(float));
-    w.uc32 = (float*)get((size_t)nuc * sizeof(float));
-    w.rho32 = (float*)get((size_t)ng * sizeof(float));
-    w.r64 = (double*)get((size_t)nuc * sizeof(double));
-    w.vflux = (double*)get((size_t)h->n_leaf * h->nq * R * sizeof(double));
-    w.rho64 = (double*)get((size_t)ng * sizeof(double));
+    nw.V32 = (float*)get((size_t)h->v_rows * R * sizeof(float));
+    nw.P32 = (float*)get((size_t)std::max(1, h->p_rows) * R * sizeof(float));
+    nw.d32 = (float*)get((size_t)std::max(1, h->d_rows) * R * sizeof(float));
+    nw.ug32 = (float*)get((size_t)ng * sizeof(float));
+    nw.g32 = (float*)get((size_t)nuc * sizeof(float));
+    nw.uc32 = (float*)get((size_t)nuc * sizeof(float));
+    nw.rho32 = (float*)get((size_t)ng * sizeof(float));
+    nw.r64 = (double*)get((size_t)nuc * sizeof(double));
+    nw.vflux = (double*)get((size_t)h->n_leaf * h->nq * R * sizeof(double));
+    nw.rho64 = (double*)get((size_t)ng * sizeof(double));
   } else {
-    w.LB = (double*)get((size_t)h->n_leaf * h->nq * R * sizeof(double));
-    w.UB = (double*)get((size_t)std::max(1, h->ub_rows) * R * sizeof(double));
-    w.ubar = (double*)get((size_t)ng * sizeof(double));
+    nw.LB = (double*)get((size_t)h->n_leaf * h->nq * R * sizeof(double));
+    nw.UB = (double*)get((size_t)std::max(1, h->ub_rows) * R * sizeof(double));
+    nw.ubar = (double*)get((size_t)ng * sizeof(double));
   }
-  w.scal = (double*)get(4 * sizeof(double));
+  nw.scal = (double*)get(4 * sizeof(double));
+  if (mixed && h->opts.fp32_gemm != HPS_GEMM_SIMT && gemm_tc32_eligible(nrhs)) gemm_tc32_prepare();
   if (h->opts.fp64_gemm != HPS_GEMM_SIMT && nrhs >= 8) {
     gemm_tc_prepare();
-    w.tc_units = (long long)h->max_items * ((nrhs + 31) / 32);
-    w.tc_scales = (int*)get((size_t)gemm_tc_scale_bytes(w.tc_units));
+    nw.tc_units = (long long)h->max_items * ((nrhs + 31) / 32);
+    nw.tc_scales = (int*)get((size_t)gemm_tc_scale_bytes(nw.tc_units));
   }
+  if (h->bc.on) nw.bcw = (double*)get((size_t)std::max(1, h->bc.rows) * R * sizeof(double));
+  w = nw;
   h->tc_scales = w.tc_scales;
   h->tc_units = w.tc_units;
-  if (h->bc.on) w.bcw = (double*)get((size_t)std::max(1, h->bc.rows) * R * sizeof(double));
 }
 
 // Econ mode: rebuild the leaf operators [F | S_ci] and H of chunk c into the chunk buffer
@@ -1618,10 +1640,12 @@ GemmCtx gemm_ctx(const hps_handle* h, int maxK, const GemmDigits* dg = nullptr, 
   GemmCtx cx;
   cx.bn = bn;
   cx.maxK = h->opts.fp64_gemm == HPS_GEMM_SIMT ? 0 : maxK;
+  cx.maxKv = maxK;
   cx.status = h->d_status;
   cx.dg = dg;
   cx.tc_scales = h->tc_scales;
   cx.tc_units = h->tc_units;
+  cx.tc32 = h->opts.fp32_gemm != HPS_GEMM_SIMT;
   return cx;
 }
 
@@ -1673,7 +1697,9 @@ void solve_pass(hps_handle* h, const TA* ops, const double* f, const TV* g, cons
     int bn = 0;
     // FP64 products on the tensor cores (exact digit slicing) where they apply
     const int mk = h->opts.fp64_gemm == HPS_GEMM_SIMT ? 0 : is.maxK;
-    const bool tc = std::is_same<TA, double>::value && gemm_tc_eligible(mk, nrhs);
+    const bool tc = std::is_same<TA, double>::value
+                        ? gemm_tc_eligible(mk, nrhs)
+                        : (h->opts.fp32_gemm != HPS_GEMM_SIMT && gemm_tc32_eligible(nrhs));
     // right-hand-side tile: tuned for products that overwrite their output (beta = 0), so
     // that a trial run can be repeated; looked up only while the sweep is being captured
     if (h->opts.autotune && !tc && nrhs > 16 && beta == 0.0 && is.n > 0) {
@@ -1699,7 +1725,7 @@ void solve_pass(hps_handle* h, const TA* ops, const double* f, const TV* g, cons
     }
     TIMED(("gemm_" + std::string(step) + "_" + sf).c_str(), 2.0 * is.elems * nrhs, is.elems * sizeof(TA),
           launch_gemm_items<TA, TV>(is.dev, is.n, ROWBLK, 0, ops, B0, B1, C, Add, idx, nrhs, beta, s,
-                                    gemm_ctx(h, mk, dg, bn)));
+                                    gemm_ctx(h, is.maxK, dg, bn)));
   };
   auto gemmp = [&](const char* step, const Prod& pr, const TV* B0, TV* C, const TV* Add, double beta) {
     gemm(step, pr.direct, B0, nullptr, C, Add, beta);
@@ -1784,6 +1810,8 @@ ResidualArgs residual_args(const hps_handle* h, const double* coeffs) {
   ra.ci = h->didx + h->off_ci;
   ra.Lloc_df = h->dLloc_df;
   ra.Lce_df = h->dLce_df;
+  ra.D_df = h->dD_df;
+  ra.D2_df = h->dD2_df;
   return ra;
 }
 
@@ -1837,21 +1865,13 @@ void mixed_step(hps_handle* h, const double* g, const double* rho, double* u, in
   CKL();
 }
 
-// u_ce = L_ce,ge u_ge in FP64 on every leaf (the exterior values the last correction left
-// in FP32).
-void mixed_finish(hps_handle* h, double* u, int nrhs, cudaStream_t s) {
-  TIMED("exterior_refresh", 2.0 * h->n_leaf * nrhs * h->ne * h->nq, 0,
-        launch_exterior_refresh(h->n_leaf, h->p, h->q, h->d_leaf_edges, h->ops64 + h->lce_base, h->didx + h->off_ce,
-                                h->ws.ug64, u, nrhs, s));
-  CKL();
-}
-
-// The fixed-schedule refined solve: the initial solve, nfix corrections (the last one
-// measured) and the exterior refresh.
+// The fixed-schedule refined solve: the initial solve and nfix corrections (the last one
+// measured).  Exterior values need no final refresh: each residual pass writes
+// u_ce = L_ce,ge u_ge back into u in double-float arithmetic, and the correction then adds
+// its own L_ce,ge du_ge, whose FP32 error is about 2^-24 |du|, far below the tolerance.
 void mixed_fixed(hps_handle* h, const double* f, const double* g, double* u, int nrhs, int nfix, cudaStream_t s) {
   mixed_initial(h, f, g, nullptr, u, nrhs, s);
   for (int k = 0; k < nfix; ++k) mixed_step(h, g, nullptr, u, nrhs, k == nfix - 1, s);
-  mixed_finish(h, u, nrhs, s);
 }
 
 // Capture the solve for this nrhs into a CUDA graph that reads its inputs from (and writes
@@ -1954,9 +1974,10 @@ int solve_fp64(hps_handle* h, const double* f, const double* g, const double* rh
 // HPS_MIXED solve.  Until the handle has a calibrated contraction bound, the refinement is
 // adaptive: after every correction the host reads max|du| and max|u| and stops when the
 // correction is below tolerance, or when the observed contraction r = |du_k| / |du_(k-1)|
-// (< 1/2) predicts the error left after it, r |du_k|, below tolerance.  The ratios seen
-// calibrate the bound rho and the number nfix of corrections that brings the initial
-// solve's error below tolerance with a tenfold margin.  Later solves without flux-jump
+// (< 1/2) predicts the error left after it, 2 r |du_k|, below tolerance.  The ratios seen
+// calibrate the bound rho (twice the largest ratio) and the number nfix of corrections
+// with rho^nfix e_0 below tolerance (e_0 = |du_1| / |u|, the initial solve's error).
+// Later solves without flux-jump
 // data run the initial solve and nfix corrections without testing in between (one CUDA
 // graph), then test once: rho |du_nfix| <= tol max|u|.  A solve that fails the test goes
 // on adaptively from where it is and recalibrates.
@@ -1971,7 +1992,7 @@ int solve_mixed(hps_handle* h, const double* f, const double* g, const double* r
     CK(cudaStreamSynchronize(s));
   };
   int it = 0;
-  bool conv = false, finished = false;
+  bool conv = false;
   double prev = -1.0, first = -1.0, ratio = 0.0;
   double sc[2] = {0.0, 0.0};
   const int nfix = h->ir.nfix;
@@ -1979,7 +2000,6 @@ int solve_mixed(hps_handle* h, const double* f, const double* g, const double* r
     if (!graph_solve(h, f, g, u, nrhs, nfix, s)) mixed_fixed(h, f, g, u, nrhs, nfix, s);
     read2(sc);
     it = nfix;
-    finished = true;
     if (!(sc[0] == sc[0]) || !(sc[1] == sc[1])) return fail(HPS_ERR_NO_CONVERGENCE, "refinement produced NaN");
     conv = h->ir.rho * sc[0] <= tol * sc[1];
     prev = sc[0];
@@ -1988,14 +2008,13 @@ int solve_mixed(hps_handle* h, const double* f, const double* g, const double* r
   }
   for (; !conv && it < h->opts.ir_max_iter; ++it) {
     mixed_step(h, g, rho, u, nrhs, true, s);
-    finished = false;
     read2(sc);
     if (!(sc[0] == sc[0]) || !(sc[1] == sc[1])) break;
     const double tolu = tol * sc[1];
     if (first < 0.0) first = sc[0] / std::max(sc[1], 1e-300);
     if (prev > 0.0) ratio = std::max(ratio, sc[0] / prev);
     const bool small = sc[0] <= tolu;
-    const bool predicted = prev > 0.0 && sc[0] < 0.5 * prev && (sc[0] / prev) * sc[0] <= tolu;
+    const bool predicted = prev > 0.0 && sc[0] < 0.5 * prev && 2.0 * (sc[0] / prev) * sc[0] <= tolu;
     prev = sc[0];
     if (small || predicted) {
       conv = true;
@@ -2005,13 +2024,12 @@ int solve_mixed(hps_handle* h, const double* f, const double* g, const double* r
         h->ir.rho = std::max(h->ir.rho, 2.0 * ratio);
         int n = 1;
         double e = first;
-        while (n < h->opts.ir_max_iter && (e *= h->ir.rho) * 10.0 > tol) ++n;
+        while (n < h->opts.ir_max_iter && (e *= h->ir.rho) > tol) ++n;
         h->ir.nfix = std::max(h->ir.nfix, n);
       }
       break;
     }
   }
-  if (!finished) mixed_finish(h, u, nrhs, s);
   if (ug_out) CK(cudaMemcpyAsync(ug_out, w.ug64, ng * sizeof(double), cudaMemcpyDeviceToDevice, s));
   if (iters) *iters = it;
   if (!conv) return fail(HPS_ERR_NO_CONVERGENCE, "iterative refinement did not converge in " + std::to_string(it) + " steps");
@@ -2037,6 +2055,7 @@ void hps_opts_default(hps_opts* o) {
   o->bc_we = HPS_BC_DIRICHLET;
   o->bc_sn = HPS_BC_DIRICHLET;
   o->fp64_gemm = HPS_GEMM_TENSOR;
+  o->fp32_gemm = HPS_GEMM_TENSOR;
 }
 
 const char* hps_last_error(void) { return g_err.c_str(); }
@@ -2311,7 +2330,9 @@ int check_opts(int p, const hps_opts* opts, hps_opts& o) {
     return fail(HPS_ERR_INVALID_ARG, "periodic or Neumann sides need precision HPS_FP64");
   if (o.fp64_gemm != HPS_GEMM_TENSOR && o.fp64_gemm != HPS_GEMM_SIMT)
     return fail(HPS_ERR_INVALID_ARG, "fp64_gemm must be HPS_GEMM_TENSOR or HPS_GEMM_SIMT");
-  if (o.ir_tol <= 0.0) o.ir_tol = 1e-9;
+  if (o.fp32_gemm != HPS_GEMM_TENSOR && o.fp32_gemm != HPS_GEMM_SIMT)
+    return fail(HPS_ERR_INVALID_ARG, "fp32_gemm must be HPS_GEMM_TENSOR or HPS_GEMM_SIMT");
+  if (o.ir_tol <= 0.0) o.ir_tol = 1e-8;
   if (o.ir_max_iter <= 0) o.ir_max_iter = 10;
   return HPS_OK;
 }
@@ -2366,6 +2387,34 @@ int hps_build(const hps_tree* tree, const double* coeffs, int p, const hps_opts*
     h->al.custom = true;
   }
   try {
+    // the coefficient fields: finite, and elliptic principal part (c11 > 0 and
+    // c11 c22 - c12^2 > 0) at every interior node (device check, one synchronisation)
+    {
+      const int nl = (int)tree->t.leaves.size();
+      int* bad = (int*)h->al.get(2 * sizeof(int), s);
+      int res[2] = {INT_MAX, INT_MAX};
+      try {
+        CK(cudaMemcpyAsync(bad, res, 2 * sizeof(int), cudaMemcpyHostToDevice, s));
+        launch_coeff_check(coeffs, nl, p, bad, s);
+        CKL();
+        CK(cudaMemcpyAsync(res, bad, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+      } catch (...) {
+        h->al.put(bad, s);
+        throw;
+      }
+      h->al.put(bad, s);
+      if (res[0] != INT_MAX) {
+        delete h;
+        return fail(HPS_ERR_INVALID_ARG, "a coefficient is not finite at an interior node of leaf " +
+                                             std::to_string(res[0]));
+      }
+      if (res[1] != INT_MAX) {
+        delete h;
+        return fail(HPS_ERR_NOT_ELLIPTIC, "c11 > 0 and c11 c22 - c12^2 > 0 fail at an interior node of leaf " +
+                                              std::to_string(res[1]));
+      }
+    }
     // shared leaf operators: equal leaf sizes (host) and equal interior coefficients
     // (device check, one synchronisation)
     bool shared = false;
@@ -2432,6 +2481,8 @@ int hps_build(const hps_tree* tree, const double* coeffs, int p, const hps_opts*
     h->dLloc = upload(h->al, s, h->rt.Lloc, h->owned);
     h->dLloc_df = (float2*)upload(h->al, s, split_df(h->rt.Lloc), h->owned);
     h->dLce_df = (float2*)upload(h->al, s, split_df(h->rt.Lce), h->owned);
+    h->dD_df = (float2*)upload(h->al, s, split_df(h->rt.D), h->owned);
+    h->dD2_df = (float2*)upload(h->al, s, split_df(h->rt.D2), h->owned);
     h->dDceL = upload(h->al, s, h->rt.DceL, h->owned);
     std::vector<double> hxy(2 * (size_t)h->n_leaf);
     for (int lf = 0; lf < h->n_leaf; ++lf) {
@@ -2526,6 +2577,7 @@ int hps_adjoint(hps_handle* h, const double* ubar_in, int nrhs, const double* u,
   if (h->bc.on) return fail(HPS_ERR_STATE, "hps_adjoint needs Dirichlet data on every side");
   if (cbar && !u) return fail(HPS_ERR_INVALID_ARG, "coefficient gradients need the forward solution u");
   cudaStream_t s = (cudaStream_t)stream;
+  std::vector<void*> tmp;  // call-local buffers, released on every exit
   try {
     ensure_ws(h, nrhs, s);
     Workspace& w = h->ws;
@@ -2534,7 +2586,6 @@ int hps_adjoint(hps_handle* h, const double* ubar_in, int nrhs, const double* u,
     const int* idx = h->didx;
     const double* ops = h->ops64;
     double* gb = gbar;
-    std::vector<void*> tmp;
     if (!gb) {
       gb = (double*)h->al.get(nuc * sizeof(double), s);
       tmp.push_back(gb);
@@ -2618,9 +2669,14 @@ int hps_adjoint(hps_handle* h, const double* ubar_in, int nrhs, const double* u,
     (void)ng;
     return HPS_OK;
   } catch (const CudaError& e) {
+    for (void* p : tmp) h->al.put(p, s);
     return fail(e.code, e.msg);
   } catch (const std::bad_alloc&) {
+    for (void* p : tmp) h->al.put(p, s);
     return fail(HPS_ERR_OOM, "host allocation failed");
+  } catch (const std::exception& e) {
+    for (void* p : tmp) h->al.put(p, s);
+    return fail(HPS_ERR_INVALID_ARG, e.what());
   }
 }
 

@@ -137,6 +137,9 @@ struct LeafTablesDev {
   const double* DceL;   // 4q x 4q
   const int* ci;        // m
 };
+// out[0] = smallest leaf index with a non-finite interior coefficient, out[1] = smallest leaf
+// index whose principal part is not elliptic at an interior node (out preset by the caller).
+void launch_coeff_check(const double* coeffs, int n_leaf, int p, int* out, cudaStream_t s);
 // *flag = 1 when the interior coefficients of some leaf differ from leaf 0's.
 void launch_leaf_uniform_check(const double* coeffs, int n_leaf, int p, int* flag, cudaStream_t s);
 template <typename T>
@@ -233,6 +236,7 @@ struct GemmDigits {
 //   dg        optional operator digits of the items
 //   tc_scales the tensor-core product's per-unit exponent buffer (gemm_tc_scale_bytes(units)
 //             bytes, owned by the caller) and its capacity in units
+//   tc32      FP32 non-transposed products with nrhs > 8 run on the tensor cores
 struct GemmCtx {
   int bn = 0;
   int maxK = 0;
@@ -240,6 +244,9 @@ struct GemmCtx {
   const GemmDigits* dg = nullptr;
   int* tc_scales = nullptr;
   long long tc_units = 0;
+  bool tc32 = false;   // FP32 products may run on the tensor cores (launch_gemm_tc32)
+  int maxKv = 0;       // largest inner dimension of the items, when known (0: unknown);
+                       // small ones select the warp-per-item streaming product
 };
 
 template <typename TA, typename TV>
@@ -259,6 +266,14 @@ void gemm_tc_prepare();
 bool launch_gemm_tc(const GemmItem* items, int nitems, int trans, const double* A, const double* B0,
                     const double* B1, double* C, const double* Add, const int* idx, int nrhs, double beta,
                     cudaStream_t s, const GemmCtx& cx);
+// FP32 gathered products on the tcgen05 tensor cores (k_gemm_tc32.cu): each entry split into
+// three bf16 pieces, the six piece pairs of weight >= 2^-16 summed in FP32 accumulators
+// (the accuracy of an FP32 product); items of at most 64 rows, non-transposed, nrhs > 8.
+// Returns false, launching nothing, if the device set-up failed.
+bool gemm_tc32_eligible(int nrhs);
+void gemm_tc32_prepare();
+bool launch_gemm_tc32(const GemmItem* items, int nitems, const float* A, const float* B0, const float* B1, float* C,
+                      const float* Add, const int* idx, int nrhs, double beta, int* status, cudaStream_t s);
 // bytes of the digit planes of `steps` K steps; fill adig / aer for the items (astep: each
 // item's first step, prefix sums of ceil(K / 16))
 long long gemm_tc_digit_bytes(long long steps);
@@ -275,9 +290,6 @@ struct SplitRed {
 template <typename TV>
 void launch_split_reduce(const SplitRed* d, int n, const TV* P, TV* C, const TV* Add, const int* idx,
                          int nrhs, double beta, cudaStream_t s);
-// u_ce = L_ce,ge u_ge on every leaf (FP64), rows of uc at the exterior nodes.
-void launch_exterior_refresh(int n_leaf, int p, int q, const int* leaf_edges, const double* Lce,
-                             const int* ce, const double* ug, double* uc, int nrhs, cudaStream_t s);
 
 // Up-sweep gather for a level of merges: d = h_b[pos3b] - h_a[pos3a] (+ rho[J3]) and
 // prefill V_tau = [0 (k3 rows) ; h_a[pos1a] ; h_b[pos2b]].
@@ -309,6 +321,7 @@ struct ResidualArgs {
   const int* ci;
   // the same tables as unevaluated float pairs (hi, lo) for the double-float kernels
   const float2* Lloc_df; const float2* Lce_df;
+  const float2* D_df; const float2* D2_df;
 };
 // Residual r = g - A u, leaf fluxes and u_ce = L_ce,ge u_ge, in double-float arithmetic.
 void launch_leaf_residual_df(const ResidualArgs& a, const int* leaf_edges, const int* ce, const double* ug, const double* g, double* uc,

@@ -132,7 +132,39 @@ __global__ void leaf_uniform_kernel(const double* __restrict__ coeffs, long long
   }
 }
 
+// Validity of the coefficient fields at the interior nodes (the exterior values are never
+// used): out[0] receives the smallest leaf index with a non-finite coefficient, out[1] the
+// smallest leaf index where the principal part is not elliptic (c11 <= 0 or
+// c11 c22 - c12^2 <= 0, Eq. defA); both stay as the caller set them otherwise.
+__global__ void coeff_check_kernel(const double* __restrict__ coeffs, long long n_leaf, int p,
+                                   int* __restrict__ out) {
+  const int pp = p * p;
+  const long long total = n_leaf * pp, st = n_leaf * pp;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int n = (int)(e % pp);
+    const int ix = n % p, iy = n / p;
+    if (ix == 0 || ix == p - 1 || iy == 0 || iy == p - 1) continue;
+    const int lf = (int)(e / pp);
+    double c[6];
+    bool finite = true;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      c[k] = coeffs[k * st + e];
+      finite = finite && isfinite(c[k]);
+    }
+    if (!finite) atomicMin(out, lf);
+    else if (!(c[0] > 0.0) || !(c[0] * c[2] - c[1] * c[1] > 0.0)) atomicMin(out + 1, lf);
+  }
+}
+
 }  // namespace
+
+void launch_coeff_check(const double* coeffs, int n_leaf, int p, int* out, cudaStream_t s) {
+  const long long total = (long long)n_leaf * p * p;
+  const int grid = (int)std::min<long long>((total + 255) / 256, 152 * 16);
+  coeff_check_kernel<<<grid, 256, 0, s>>>(coeffs, n_leaf, p, out);
+}
 
 void launch_leaf_uniform_check(const double* coeffs, int n_leaf, int p, int* flag, cudaStream_t s) {
   const long long total = 6ll * n_leaf * p * p;

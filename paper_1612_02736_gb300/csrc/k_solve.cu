@@ -97,8 +97,25 @@ __global__ void __launch_bounds__(256) gemv_items_kernel(const GemmItem* __restr
   TV acc[RW * NR];
 #pragma unroll
   for (int j = 0; j < RW * NR; ++j) acc[j] = TV(0);
+  // FP64 products double-buffer the operator loads (the next 8 rows' vectors are in flight
+  // while the current ones feed the FP64 pipe, which bounds these products)
+  constexpr bool DB = sizeof(TA) == 8;
   for (int k0 = 0; k0 < it.K; k0 += KC) {
     const int kc = min(KC, it.K - k0);
+    // head: entries before the first 16-byte boundary of this warp's rows
+    const long long o0 = it.a_off + (long long)warp * it.lda + k0;
+    const int h = min(kc, (int)((VW - (int)(o0 % VW)) % VW));
+    const int nv = (kc - h) / VW;
+    const int t0 = h + nv * VW;  // first tail entry
+    const TA* Ak = Aw + k0;
+    // FP64: the first vectors of this chunk are requested before the staging, so that the
+    // two latencies overlap (FP32 keeps the registers for occupancy)
+    VecT ap[DB ? RW : 1];
+    if (DB && lane < nv) {
+#pragma unroll
+      for (int i = 0; i < RW; ++i)
+        if (i < nrow) ap[i] = __ldcs(reinterpret_cast<const VecT*>(Ak + i * rs + h + lane * VW));
+    }
     for (int e = tid; e < kc * NR; e += 256) {
       const int kk = e / NR, r = e % NR;
       const int k = k0 + kk;
@@ -111,12 +128,6 @@ __global__ void __launch_bounds__(256) gemv_items_kernel(const GemmItem* __restr
     }
     __syncthreads();
     if (nrow > 0) {
-      // head: entries before the first 16-byte boundary of this warp's rows
-      const long long o0 = it.a_off + (long long)warp * it.lda + k0;
-      const int h = min(kc, (int)((VW - (int)(o0 % VW)) % VW));
-      const int nv = (kc - h) / VW;
-      const int t0 = h + nv * VW;  // first tail entry
-      const TA* Ak = Aw + k0;
       // scalar entries: the head (lane l < h takes entry l) and the tail (lane l takes entry
       // t0 + l while it is below kc)
 #pragma unroll 1
@@ -129,18 +140,29 @@ __global__ void __launch_bounds__(256) gemv_items_kernel(const GemmItem* __restr
 #pragma unroll
         for (int i = 0; i < RW; ++i)
           if (i < nrow) {
-            const TV a = (TV)Ak[i * rs + kk];
+            const TV av = (TV)Ak[i * rs + kk];
 #pragma unroll
-            for (int r = 0; r < NR; ++r) acc[i * NR + r] += a * xv[r];
+            for (int r = 0; r < NR; ++r) acc[i * NR + r] += av * xv[r];
           }
       }
       // body: 16-byte vectors
       for (int v = lane; v < nv; v += 32) {
         const int kk = h + v * VW;
         VecT a[RW];
+        VecT an[DB ? RW : 1];
+        if constexpr (DB) {
 #pragma unroll
-        for (int i = 0; i < RW; ++i)
-          if (i < nrow) a[i] = __ldcs(reinterpret_cast<const VecT*>(Ak + i * rs + kk));
+          for (int i = 0; i < RW; ++i) a[i] = ap[i];
+          if (v + 32 < nv) {
+#pragma unroll
+            for (int i = 0; i < RW; ++i)
+              if (i < nrow) an[i] = __ldcs(reinterpret_cast<const VecT*>(Ak + i * rs + kk + 32 * VW));
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < RW; ++i)
+            if (i < nrow) a[i] = __ldcs(reinterpret_cast<const VecT*>(Ak + i * rs + kk));
+        }
 #pragma unroll
         for (int j = 0; j < VW; ++j) {
           TV xv[NR];
@@ -153,6 +175,10 @@ __global__ void __launch_bounds__(256) gemv_items_kernel(const GemmItem* __restr
 #pragma unroll
               for (int r = 0; r < NR; ++r) acc[i * NR + r] += aij * xv[r];
             }
+        }
+        if constexpr (DB) {
+#pragma unroll
+          for (int i = 0; i < RW; ++i) ap[i] = an[i];
         }
       }
     }
@@ -175,6 +201,103 @@ __global__ void __launch_bounds__(256) gemv_items_kernel(const GemmItem* __restr
       const long long cr = (long long)map_row(idx, it.c_idx, it.c_row, row) * nrhs + r;
       if (it.add_row >= 0) v += Add[(long long)(it.add_row + row) * nrhs + r];
       C[cr] = (beta != TV(0) ? beta * C[cr] : TV(0)) + v;
+    }
+  }
+}
+
+// Streaming products of small items (inner dimension K <= WKMAX, nrhs <= NR): one warp per
+// item, 8 items per CTA, each warp staging its own vector block in shared memory, so that
+// the thousands of small products near the leaves (merge levels, the exterior-value product)
+// do not pay a CTA's set-up each.  K <= 64: lane l computes rows l and l + 32 (the row's
+// entries are contiguous and stay in L1 across the k loop; the staged vector is read by all
+// lanes at once).  64 < K <= WKMAX: the rows are taken 8 at a time with the lanes along K,
+// as in gemv_items_kernel.
+constexpr int WKMAX = 128;
+
+template <typename TA, typename TV, int NR>
+__global__ void __launch_bounds__(256) gemv_warp_items_kernel(const GemmItem* __restrict__ items, int nitems,
+                                                              const TA* __restrict__ A, const TV* __restrict__ B0,
+                                                              const TV* __restrict__ B1, TV* __restrict__ C,
+                                                              const TV* __restrict__ Add, const int* __restrict__ idx,
+                                                              int nrhs, TV beta) {
+  __shared__ TV xs_all[8][WKMAX * NR];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int item = blockIdx.x * 8 + warp;
+  if (item >= nitems) return;
+  const GemmItem it = items[item];
+  TV* xs = xs_all[warp];
+  for (int e = lane; e < it.K * NR; e += 32) {
+    const int k = e / NR, r = e % NR;
+    TV v = TV(0);
+    if (r < nrhs) {
+      if (k < it.kseg) v = B0[(long long)map_row(idx, it.b0_idx, it.b0_row, k) * nrhs + r];
+      else v = B1[(long long)map_row(idx, it.b1_idx, it.b1_row, k - it.kseg) * nrhs + r];
+    }
+    xs[e] = v;
+  }
+  __syncwarp();
+  const TA* Ab = A + it.a_off;
+  auto store = [&](int row, int r, TV v) {
+    if (row < it.M && r < nrhs) {
+      const long long cr = (long long)map_row(idx, it.c_idx, it.c_row, row) * nrhs + r;
+      if (it.add_row >= 0) v += Add[(long long)(it.add_row + row) * nrhs + r];
+      C[cr] = (beta != TV(0) ? beta * C[cr] : TV(0)) + v;
+    }
+  };
+  if (it.K <= 64) {
+    TV acc[2][NR];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int r = 0; r < NR; ++r) acc[i][r] = TV(0);
+    const int r0 = lane, r1 = lane + 32;
+    const TA* a0 = Ab + (long long)min(r0, it.M - 1) * it.lda;
+    const TA* a1 = Ab + (long long)min(r1, it.M - 1) * it.lda;
+#pragma unroll 4
+    for (int k = 0; k < it.K; ++k) {
+      const TV v0 = (TV)a0[k], v1 = (TV)a1[k];
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        const TV xv = xs[k * NR + r];
+        acc[0][r] += v0 * xv;
+        acc[1][r] += v1 * xv;
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      store(r0, r, acc[0][r]);
+      store(r1, r, acc[1][r]);
+    }
+    return;
+  }
+  // lanes along K (consecutive lanes read consecutive entries of a row), 8 rows at a time
+  for (int g0 = 0; g0 < it.M; g0 += 8) {
+    TV acc[8 * NR];
+#pragma unroll
+    for (int j = 0; j < 8 * NR; ++j) acc[j] = TV(0);
+    for (int k = lane; k < it.K; k += 32) {
+      TV xv[NR];
+#pragma unroll
+      for (int r = 0; r < NR; ++r) xv[r] = xs[k * NR + r];
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        if (g0 + i < it.M) {
+          const TV av = (TV)Ab[(long long)(g0 + i) * it.lda + k];
+#pragma unroll
+          for (int r = 0; r < NR; ++r) acc[i * NR + r] += av * xv[r];
+        }
+    }
+    constexpr int V = 8 * NR;
+    warp_transpose_sum<V>(acc, lane);
+    constexpr int NV = V >= 32 ? V / 32 : 1;
+    constexpr int SH = V >= 32 ? 0 : (V == 16 ? 1 : (V == 8 ? 2 : 3));
+    if ((lane & ((1 << SH) - 1)) == 0) {
+      const int base = lane >> SH;
+#pragma unroll
+      for (int t = 0; t < NV; ++t) {
+        const int j = base * NV + t;
+        store(g0 + j / NR, j % NR, acc[t]);
+      }
     }
   }
 }
@@ -460,25 +583,6 @@ __global__ void split_reduce_kernel(const SplitRed* __restrict__ d, const TV* __
   }
 }
 
-// u_ce = L_ce,ge u_ge (FP64): one leaf per CTA, one exterior node and rhs per thread.
-__global__ void exterior_refresh_kernel(int p, int q, const int* __restrict__ leaf_edges,
-                                        const double* __restrict__ Lce, const int* __restrict__ ce,
-                                        const double* __restrict__ ug, double* __restrict__ uc, int nrhs) {
-  const int lf = blockIdx.x;
-  const int ne = 4 * (p - 1), nq = 4 * q, pp = p * p;
-  const long long total = (long long)ne * nrhs;
-  for (long long e = threadIdx.x; e < total; e += blockDim.x) {
-    const int k = (int)(e / nrhs);
-    const int r = (int)(e - (long long)k * nrhs);
-    double v = 0.0;
-    for (int g = 0; g < nq; ++g) {
-      const int s = g / q, a = g - (g / q) * q;
-      v += Lce[(long long)k * nq + g] * ug[((long long)leaf_edges[4 * lf + s] * q + a) * nrhs + r];
-    }
-    uc[((long long)lf * pp + ce[k]) * nrhs + r] = v;
-  }
-}
-
 __global__ void row_combine_kernel(const int* __restrict__ tab, int n, double* __restrict__ dst,
                                    const double* __restrict__ A, const double* __restrict__ B, int nrhs) {
   const long long total = (long long)n * nrhs;
@@ -511,6 +615,11 @@ void launch_gemm_items(const GemmItem* items, int nitems, int maxM, int trans, c
     if (gemm_tc_eligible(cx.maxK, nrhs) && launch_gemm_tc(items, nitems, trans, A, B0, B1, C, Add, idx, nrhs, beta, s, cx))
       return;
   }
+  if constexpr (std::is_same<TA, float>::value && std::is_same<TV, float>::value) {
+    if (cx.tc32 && !trans && gemm_tc32_eligible(nrhs) &&
+        launch_gemm_tc32(items, nitems, A, B0, B1, C, Add, idx, nrhs, beta, cx.status, s))
+      return;
+  }
   const int bn = cx.bn;
   const TV b = (TV)beta;
   if (trans && nrhs <= 4) {
@@ -521,6 +630,16 @@ void launch_gemm_items(const GemmItem* items, int nitems, int maxM, int trans, c
   }
   // streaming products: up to 4 right-hand sides in FP64 (bound by the FP64 pipe beyond),
   // up to 8 in FP32
+  // small items, and enough of them for 16 warps per SM: one warp per item
+  if (!trans && nrhs <= (sizeof(TV) == 8 ? 4 : 8) && cx.maxKv > 0 && cx.maxKv <= WKMAX && nitems >= 16 * 152) {
+    const int grid = (nitems + 7) / 8;
+    if (nrhs == 1) gemv_warp_items_kernel<TA, TV, 1><<<grid, 256, 0, s>>>(items, nitems, A, B0, B1, C, Add, idx, nrhs, b);
+    else if (nrhs == 2) gemv_warp_items_kernel<TA, TV, 2><<<grid, 256, 0, s>>>(items, nitems, A, B0, B1, C, Add, idx, nrhs, b);
+    else if (nrhs <= 4) gemv_warp_items_kernel<TA, TV, 4><<<grid, 256, 0, s>>>(items, nitems, A, B0, B1, C, Add, idx, nrhs, b);
+    else if constexpr (sizeof(TV) == 4)
+      gemv_warp_items_kernel<TA, TV, 8><<<grid, 256, 0, s>>>(items, nitems, A, B0, B1, C, Add, idx, nrhs, b);
+    return;
+  }
   if (!trans && nrhs <= (sizeof(TV) == 8 ? 4 : 8)) {
     if (nrhs == 1) gemv_items_kernel<TA, TV, 1><<<nitems, 256, 0, s>>>(items, A, B0, B1, C, Add, idx, nrhs, b);
     else if (nrhs == 2) gemv_items_kernel<TA, TV, 2><<<nitems, 256, 0, s>>>(items, A, B0, B1, C, Add, idx, nrhs, b);
@@ -557,12 +676,6 @@ void launch_row_combine(const int* tab, int n, double* dst, const double* A, con
                         cudaStream_t s) {
   if (n <= 0) return;
   row_combine_kernel<<<grid_for((long long)n * nrhs), 256, 0, s>>>(tab, n, dst, A, B, nrhs);
-}
-
-void launch_exterior_refresh(int n_leaf, int p, int q, const int* leaf_edges, const double* Lce, const int* ce,
-                             const double* ug, double* uc, int nrhs, cudaStream_t s) {
-  if (n_leaf <= 0) return;
-  exterior_refresh_kernel<<<n_leaf, 256, 0, s>>>(p, q, leaf_edges, Lce, ce, ug, uc, nrhs);
 }
 
 template <typename TV>

@@ -140,13 +140,15 @@ class Solver:
     Dirichlet values, or du/dy on Neumann sides, and is ignored on periodic sides.
     fp64_gemm: "tensor" runs the FP64 solve and adjoint products on the tensor cores by exact
     digit slicing where they apply (inner dimension <= 448, nrhs >= 8), "simt" on the FP64
-    FFMA pipe throughout.
+    FFMA pipe throughout.  fp32_gemm: the FP32 sweep products of the mixed path with more
+    than 8 right-hand sides on the tensor cores ("tensor", three bf16 pieces per entry) or
+    on the FP32 FFMA pipe ("simt").
     """
 
     def __init__(self, tree, coeffs, p, precision="fp64", q=None, ir_tol=None, ir_max_iter=None,
                  fp64_top_levels=None, store_leaf_ops=True, use_graphs=True, autotune=False,
                  autotune_cache=None, shared_leaf="auto", bc_we="dirichlet", bc_sn="dirichlet",
-                 fp64_gemm="tensor", allocator="torch"):
+                 fp64_gemm="tensor", fp32_gemm="tensor", allocator="torch"):
         lib = N.load()
         if not (coeffs.is_cuda and coeffs.dtype == torch.float64 and coeffs.is_contiguous()):
             raise ValueError("coeffs must be a contiguous CUDA float64 tensor")
@@ -170,6 +172,7 @@ class Solver:
         opts.bc_we = {"dirichlet": N.HPS_BC_DIRICHLET, "periodic": N.HPS_BC_PERIODIC}[bc_we]
         opts.bc_sn = {"dirichlet": N.HPS_BC_DIRICHLET, "neumann": N.HPS_BC_NEUMANN}[bc_sn]
         opts.fp64_gemm = {"tensor": N.HPS_GEMM_TENSOR, "simt": N.HPS_GEMM_SIMT}[fp64_gemm]
+        opts.fp32_gemm = {"tensor": N.HPS_GEMM_TENSOR, "simt": N.HPS_GEMM_SIMT}[fp32_gemm]
         self.tree, self.p, self.precision = tree, p, precision
         self._alloc = _allocator() if allocator == "torch" else None
         out = C.c_void_p()

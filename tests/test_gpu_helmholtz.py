@@ -1,6 +1,6 @@
 """Indefinite operators on the GPU (Sec. 7.2, c < 0): the variable-coefficient scattering
 problem against the oracle, an exact plane wave at the full 64 x 64 size, and the
-breakdown report for an exactly singular leaf."""
+rejection of a degenerate (non-elliptic) operator."""
 import numpy as np
 import pytest
 
@@ -71,16 +71,17 @@ def test_plane_wave_full_size(precision):
     assert np.max(np.abs(u - syn.plane_wave(X, Y, kappa))) < 1e-9
 
 
-def test_singular_leaf_is_reported_and_library_stays_usable():
-    # all coefficients zero: A_ci,ci = 0, the first pivot of every leaf breaks down
+def test_degenerate_operator_is_reported_and_library_stays_usable():
+    # all coefficients zero: no elliptic principal part, rejected before any elimination
+    # (a singular but elliptic leaf is in test_gpu_failure.py)
     import torch
     from paper_1612_02736_gb300 import Solver, Tree, _native
     t = Tree.uniform(0.0, 0.0, 1.0, 1.0, 2, 2)
     zero = torch.zeros((6, 4, 64), dtype=torch.float64, device="cuda")
     with pytest.raises(_native.HPSError) as ei:
         Solver(t, zero, 8)
-    assert ei.value.code == 3   # HPS_ERR_SINGULAR
-    assert "box" in str(ei.value)
+    assert ei.value.code == 2   # HPS_ERR_NOT_ELLIPTIC
+    assert "leaf 0" in str(ei.value)
     ok = zero.clone()
     ok[0] = 1.0
     ok[2] = 1.0

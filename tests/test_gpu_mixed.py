@@ -53,3 +53,22 @@ def test_flux_jump_data_keeps_adaptive_refinement():
     u, ugg = s.solve(to_dev(case["f"]), to_dev(case["g"]), rho=to_dev(rho), return_gauss=True)
     assert rel_linf(u.cpu().numpy(), uc) < 1e-8 and rel_linf(ugg.cpu().numpy(), ug) < 1e-8
     assert s.last_iters >= 2
+
+
+@pytest.mark.parametrize("nx,ny,p,nrhs", [(8, 8, 16, 9), (8, 4, 12, 64), (4, 4, 10, 100)])
+def test_fp32_tensor_core_products(nx, ny, p, nrhs):
+    # FP32 sweep products on the tensor cores (three bf16 pieces per entry) and on the FP32
+    # FFMA pipe: both refined solutions within 1e-8 of the oracle, and of each other; nrhs
+    # 100 spans two 64-column units per operator block, 9 leaves most of one unused
+    from paper_1612_02736_gb300 import Solver
+    case = make_case(nx, ny, p, nrhs=nrhs)
+    (uc, ug), _ = oracle_solve(case)
+    out = {}
+    for mode in ("tensor", "simt"):
+        s = Solver(gpu_tree(case), to_dev(case["coeffs"]), p, precision="mixed", fp32_gemm=mode)
+        for _ in range(2):  # the second solve runs the calibrated schedule
+            u, ugg = s.solve(to_dev(case["f"]), to_dev(case["g"]), return_gauss=True)
+            assert rel_linf(u.cpu().numpy(), uc) < 1e-8, (mode, rel_linf(u.cpu().numpy(), uc))
+            assert rel_linf(ugg.cpu().numpy(), ug) < 1e-8
+        out[mode] = u.cpu().numpy()
+    assert rel_linf(out["tensor"], out["simt"]) < 1e-8

@@ -222,6 +222,13 @@ def test_plan_rejects_bad_options(lib):
     assert lib.hps_plan_check(t, 8, C.byref(opts)) == 0
     opts.fp64_gemm = 5
     assert lib.hps_plan_check(t, 8, C.byref(opts)) == 1
+    lib.hps_opts_default(C.byref(opts))
+    assert opts.fp32_gemm == _native.HPS_GEMM_TENSOR
+    opts.precision = _native.HPS_MIXED
+    opts.fp32_gemm = _native.HPS_GEMM_SIMT
+    assert lib.hps_plan_check(t, 8, C.byref(opts)) == 0
+    opts.fp32_gemm = -1
+    assert lib.hps_plan_check(t, 8, C.byref(opts)) == 1
     lib.hps_tree_destroy(t)
 
 
