@@ -169,6 +169,10 @@ struct ItemSet {
   mutable GemmDigits dg;
   mutable bool dg_tried = false;
   mutable int uses = 0;  // tensor-core applications so far (the cache is formed on the second)
+  // the same for the FP32 operators of a mixed-precision handle: their bf16 pieces
+  mutable GemmDigits dg32;
+  mutable bool dg32_tried = false;
+  mutable int uses32 = 0;
 };
 
 // A product step of one level: items writing final outputs, and split-K items writing
@@ -1624,6 +1628,35 @@ const GemmDigits* item_digits(hps_handle* h, const ItemSet& is, int trans, const
   return is.dg.dig ? &is.dg : nullptr;
 }
 
+// The bf16 operator pieces of an FP32 item set for the tensor-core products (the FP32 copy of
+// the operators is fixed after the build), formed like item_digits: on the set's second
+// tensor-core application outside stream capture, or when `now` is set; nullptr otherwise
+// (the products then split the operator themselves, same results).
+const GemmDigits* item_pieces32(hps_handle* h, const ItemSet& is, int nrhs, cudaStream_t s, bool now = false) {
+  if (h->opts.fp32_gemm == HPS_GEMM_SIMT || is.n == 0 || is.dsteps == 0 || !gemm_tc32_eligible(nrhs) || !h->ops32)
+    return nullptr;
+  if (!now) ++is.uses32;
+  if (!is.dg32.dig && !is.dg32_tried && (now || is.uses32 >= 2)) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(s, &cs));
+    if (cs == cudaStreamCaptureStatusNone) {
+      is.dg32_tried = true;
+      try {
+        const size_t db = (size_t)gemm_tc32_piece_bytes(is.dsteps);
+        unsigned char* dig = (unsigned char*)h->al.get(db, s);
+        h->owned.push_back({dig, db});
+        TIMED("gemm_pieces_f32", 0, (double)db, launch_gemm_tc32_pieces(is.dev, is.n, h->ops32, is.dstep, dig, s));
+        CKL();
+        is.dg32.dig = dig;
+        is.dg32.step = is.dstep;
+      } catch (const CudaError&) {
+        cudaGetLastError();
+      }
+    }
+  }
+  return is.dg32.dig ? &is.dg32 : nullptr;
+}
+
 // Items [l0, l0 + n) leaves of a leaf item set (every leaf has the same number of items).
 ItemSet leaf_range(const hps_handle* h, const ItemSet& is, int l0, int n) {
   ItemSet r;
@@ -1722,6 +1755,8 @@ void solve_pass(hps_handle* h, const TA* ops, const double* f, const TV* g, cons
     const GemmDigits* dg = nullptr;
     if constexpr (std::is_same<TA, double>::value) {
       if (tc) dg = item_digits(h, is, 0, ops, nrhs, s);
+    } else {
+      if (tc) dg = item_pieces32(h, is, nrhs, s);
     }
     TIMED(("gemm_" + std::string(step) + "_" + sf).c_str(), 2.0 * is.elems * nrhs, is.elems * sizeof(TA),
           launch_gemm_items<TA, TV>(is.dev, is.n, ROWBLK, 0, ops, B0, B1, C, Add, idx, nrhs, beta, s,
@@ -1874,6 +1909,22 @@ void mixed_fixed(hps_handle* h, const double* f, const double* g, double* u, int
   for (int k = 0; k < nfix; ++k) mixed_step(h, g, nullptr, u, nrhs, k == nfix - 1, s);
 }
 
+// Operator pieces of every FP32 product set of the mixed sweep, formed before a capture.
+void prepare_sweep_pieces32(hps_handle* h, int nrhs, cudaStream_t s) {
+  auto one = [&](const ItemSet& is) { item_pieces32(h, is, nrhs, s, true); };
+  one(h->leafup);
+  one(h->leafdown);
+  one(h->lce);
+  for (const Level& lv : h->levels) {
+    one(lv.up.direct);
+    one(lv.up.split);
+    one(lv.down.direct);
+    one(lv.down.split);
+    one(lv.iup);
+    one(lv.idown);
+  }
+}
+
 // Capture the solve for this nrhs into a CUDA graph that reads its inputs from (and writes
 // u to) staging buffers owned by the handle: the FP64 sweep, or for HPS_MIXED the
 // fixed-schedule refined solve with nfix corrections.  Capture runs on a private stream; a
@@ -1888,6 +1939,7 @@ void capture_solve(hps_handle* h, int nrhs, int nfix, cudaStream_t s) {
   h->graph.g_in = (double*)h->al.get((size_t)nuc * sizeof(double), s);
   h->graph.u_out = (double*)h->al.get((size_t)nuc * sizeof(double), s);
   if (!mixed) prepare_sweep_digits(h, nrhs, s);
+  else prepare_sweep_pieces32(h, nrhs, s);
   CK(cudaStreamSynchronize(s));
   if (!h->graph.cs) CK(cudaStreamCreateWithFlags(&h->graph.cs, cudaStreamNonBlocking));
   cudaStream_t cs = h->graph.cs;

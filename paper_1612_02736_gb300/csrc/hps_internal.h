@@ -270,10 +270,18 @@ bool launch_gemm_tc(const GemmItem* items, int nitems, int trans, const double* 
 // three bf16 pieces, the six piece pairs of weight >= 2^-16 summed in FP32 accumulators
 // (the accuracy of an FP32 product); items of at most 64 rows, non-transposed, nrhs > 8.
 // Returns false, launching nothing, if the device set-up failed.
+// With dg, the operator's bf16 pieces are read from it (launch_gemm_tc32_pieces, same
+// results).
 bool gemm_tc32_eligible(int nrhs);
 void gemm_tc32_prepare();
 bool launch_gemm_tc32(const GemmItem* items, int nitems, const float* A, const float* B0, const float* B1, float* C,
-                      const float* Add, const int* idx, int nrhs, double beta, int* status, cudaStream_t s);
+                      const float* Add, const int* idx, int nrhs, double beta, int* status, cudaStream_t s,
+                      const GemmDigits* dg);
+// bytes of the bf16 operator pieces of `steps` K steps; fill adig for the items (astep: each
+// item's first step)
+long long gemm_tc32_piece_bytes(long long steps);
+void launch_gemm_tc32_pieces(const GemmItem* items, int nitems, const float* A, const long long* astep,
+                             unsigned char* adig, cudaStream_t s);
 // bytes of the digit planes of `steps` K steps; fill adig / aer for the items (astep: each
 // item's first step, prefix sums of ceil(K / 16))
 long long gemm_tc_digit_bytes(long long steps);

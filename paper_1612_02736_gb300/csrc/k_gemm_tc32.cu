@@ -21,6 +21,9 @@
 //                      K step (16-byte cp.async where aligned, GPF steps ahead, the gathered
 //                      rows' indices read a step earlier) and splits them into the three bf16
 //                      planes when the step comes; no exchange leaves the warp.
+//   warp 13            with cached operator planes (formed once per product set by
+//                      gemm_tc32_pieces_kernel), one thread copies each K step's planes with
+//                      one bulk copy and the producers only split the vectors.
 // Stages (GST) and the two TMEM accumulators are handed on with mbarriers; every wait is
 // bounded and a timeout stops every role (status -1).
 #include <algorithm>
@@ -45,13 +48,15 @@ constexpr int T_PL = 3;             // bf16 pieces per entry
 constexpr int T_GST = 4;            // K-step stages
 constexpr int T_GPF = 4;            // K steps the entry copies run ahead
 constexpr int T_GRAW = T_GPF + 1;   // raw entry slots
-constexpr int T_THREADS = 416;      // 13 warps
+constexpr int T_THREADS = 448;      // 14 warps
+constexpr int T_LOAD_WARP = 13;     // bulk copies of cached operator planes
 constexpr int T_PROD = 256;         // producer threads (8 warps)
 constexpr int T_EPI = 128;          // epilogue threads (4 warps)
 constexpr int T_MMA_WARP = 2;
 constexpr int T_APL = T_GR * 32;            // bytes per A plane (64 rows x 16 k x 2 B)
 constexpr int T_BPL = T_GN * 32;            // bytes per B plane (64 columns x 16 k x 2 B)
 constexpr int T_TBUF = 256;                 // TMEM columns between the two accumulators
+constexpr int T_ASTEP = T_PL * T_APL;       // bytes of one K step's operator planes
 
 // One K step.  A product (M = 128) reads 128 rows from an A plane's start: rows 64..127
 // are the next plane's bytes (for the last plane, the first B plane's), bf16 values that
@@ -124,15 +129,20 @@ __global__ void __launch_bounds__(T_THREADS, 1) gemm_tc32_kernel(const GemmItem*
                                                                  const float* __restrict__ B1, float* __restrict__ C,
                                                                  const float* __restrict__ Add,
                                                                  const int* __restrict__ idx, int nrhs, float beta,
+                                                                 const unsigned char* __restrict__ adig,
+                                                                 const long long* __restrict__ astep,
                                                                  int* __restrict__ status) {
   extern __shared__ __align__(1024) unsigned char t_raw[];
   TShared& sh = *reinterpret_cast<TShared*>(t_raw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nnb = (nrhs + T_GN - 1) / T_GN;
   const long long total = (long long)nitems * nnb;
+  // cached operator planes (adig): one thread of the loader warp copies each K step's planes
+  // with one bulk copy, and the producers only split the vectors
+  const bool cached = adig != nullptr;
   if (tid == 0) {
     for (int b = 0; b < T_GST; ++b) {
-      mb_init(&sh.sfull[b], T_PROD);
+      mb_init(&sh.sfull[b], cached ? T_PROD + 1 : T_PROD);
       mb_init(&sh.sfree[b], 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -204,6 +214,32 @@ __global__ void __launch_bounds__(T_THREADS, 1) gemm_tc32_kernel(const GemmItem*
           smem_u32(&sh.mdone)));
       mb_drain(&sh.mdone, 0);
     }
+  } else if (warp == T_LOAD_WARP) {
+    // ---------------- cached operator planes: lane 0 copies each K step's planes into its
+    // stage once the stage is free, arming the stage's barrier with their bytes
+    if (cached && lane == 0) {
+      long long ks = 0;
+      bool stop = false;
+      for (long long u = blockIdx.x; u < total && !stop; u += gridDim.x) {
+        const long long item = u / nnb;
+        const int nk = (items[item].K + 15) >> 4;
+        const unsigned char* src = adig + astep[item] * T_ASTEP;
+        for (int c = 0; c < nk; ++c, ++ks) {
+          const int st = (int)(ks % T_GST);
+          if (ks >= T_GST && !mb_wait(&sh.sfree[st], (int)((ks / T_GST) - 1) & 1, abort_flag, status)) {
+            stop = true;
+            break;
+          }
+          mb_expect_arrive(&sh.sfull[st], T_ASTEP);
+          bulk_load(sh.st[st].A[0], src + (long long)c * T_ASTEP, T_ASTEP, &sh.sfull[st]);
+        }
+      }
+      // the copies issued have landed before the block exits
+      for (int b = 0; b < T_GST; ++b) {
+        const long long n = ks > b ? (ks - 1 - b) / T_GST + 1 : 0;  // copies armed on stage b
+        if (n > 0) mb_drain(&sh.sfull[b], (int)((n - 1) & 1));
+      }
+    }
   } else if (!epi) {
     // ---------------- producers: warps 3, 6 .. 12 -> producer warp pw = 0 .. 7.  Warp pw owns
     // operator rows 8 pw .. 8 pw + 7 and vector columns 8 pw .. 8 pw + 7 of every K step: it
@@ -251,7 +287,7 @@ __global__ void __launch_bounds__(T_THREADS, 1) gemm_tc32_kernel(const GemmItem*
         TRaw& rw = sh.raw[slot];
         const GemmItem& it = x.it;
         const int n0 = (int)(x.u % nnb) * T_GN, k0 = x.c * 16;
-        if (arow < it.M) {
+        if (!cached && arow < it.M) {
           float* dst = &rw.A[arow][akq];
           const float* src = A + it.a_off + (long long)arow * it.lda + k0 + akq;
           if (k0 + akq + 3 < it.K && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
@@ -302,8 +338,10 @@ __global__ void __launch_bounds__(T_THREADS, 1) gemm_tc32_kernel(const GemmItem*
       const int st = (int)(ks % T_GST), slot = (int)(ks % T_GRAW);
       if (ks >= T_GST && !warp_wait(&sh.sfree[st], (int)((ks / T_GST) - 1) & 1, abort_flag, status)) break;
       const TRaw& rw = sh.raw[slot];
-      if (arow >= cv.it.M) zero_pieces4(sh.st[st].A[0], T_APL, kmaj(arow, akq));
-      else write_pieces4(&rw.A[arow][akq], sh.st[st].A[0], T_APL, kmaj(arow, akq));
+      if (!cached) {
+        if (arow >= cv.it.M) zero_pieces4(sh.st[st].A[0], T_APL, kmaj(arow, akq));
+        else write_pieces4(&rw.A[arow][akq], sh.st[st].A[0], T_APL, kmaj(arow, akq));
+      }
       {
         float v[4];
 #pragma unroll
@@ -363,17 +401,33 @@ __global__ void __launch_bounds__(T_THREADS, 1) gemm_tc32_kernel(const GemmItem*
       asm volatile("tcgen05.fence::before_thread_sync;");
       mb_arrive(&sh.tfree[tb]);  // accumulator read: the unit after next may write it
       __syncwarp();
+      // the 32 rows' output addresses (one row index per lane, broadcast), the old values and
+      // addends all requested before any store, so that the row loop does not wait on them
+      // one by one
       const int n = n0 + 32 * g + lane;
-#pragma unroll 4
-      for (int rr = 0; rr < 32; ++rr) {
-        const int row = q4 * 32 + rr;
-        if (row >= it.M) break;
-        if (n < nrhs) {
-          const long long cr = (long long)map_row32(idx, it.c_idx, it.c_row, row) * nrhs + n;
-          float o = tile[rr][lane];
-          if (it.add_row >= 0) o += Add[(long long)(it.add_row + row) * nrhs + n];
-          C[cr] = (beta != 0.f ? beta * C[cr] : 0.f) + o;
+      const int myrow = q4 * 32 + lane;
+      const int mymap = myrow < it.M ? map_row32(idx, it.c_idx, it.c_row, myrow) : 0;
+      const int nrow = min(32, it.M - q4 * 32);
+      const bool col_ok = n < nrhs;
+      float o[32];
+#pragma unroll
+      for (int rr = 0; rr < 32; ++rr) o[rr] = tile[rr][lane];
+      if (it.add_row >= 0) {
+#pragma unroll
+        for (int rr = 0; rr < 32; ++rr)
+          if (rr < nrow && col_ok) o[rr] += Add[(long long)(it.add_row + q4 * 32 + rr) * nrhs + n];
+      }
+      if (beta != 0.f) {
+#pragma unroll
+        for (int rr = 0; rr < 32; ++rr) {
+          const int rmap = __shfl_sync(0xffffffffu, mymap, rr);
+          if (rr < nrow && col_ok) o[rr] += beta * C[(long long)rmap * nrhs + n];
         }
+      }
+#pragma unroll
+      for (int rr = 0; rr < 32; ++rr) {
+        const int rmap = __shfl_sync(0xffffffffu, mymap, rr);
+        if (rr < nrow && col_ok) C[(long long)rmap * nrhs + n] = o[rr];
       }
       __syncwarp();  // the tile is rewritten for the next unit
     }
@@ -383,9 +437,44 @@ __global__ void __launch_bounds__(T_THREADS, 1) gemm_tc32_kernel(const GemmItem*
   if (warp == T_MMA_WARP) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
 }
 
+// The operator's bf16 pieces of every K step of one item (one block per item), in the stage
+// layout, at adig + astep[item] * T_ASTEP; rows past the item are zero.  The operators do not
+// change after the build, so a product set keeps these planes across solves.
+__global__ void __launch_bounds__(256) gemm_tc32_pieces_kernel(const GemmItem* __restrict__ items,
+                                                               const float* __restrict__ A,
+                                                               const long long* __restrict__ astep,
+                                                               unsigned char* __restrict__ adig) {
+  const GemmItem it = items[blockIdx.x];
+  const int t = threadIdx.x, row = t >> 2, kg = (t & 3) * 4;
+  unsigned char* dst = adig + astep[blockIdx.x] * T_ASTEP;
+  const int nk = (it.K + 15) >> 4;
+  for (int c = 0; c < nk; ++c) {
+    unsigned char* pl = dst + (long long)c * T_ASTEP;
+    if (row >= it.M) {
+      zero_pieces4(pl, T_APL, kmaj(row, kg));
+      continue;
+    }
+    float v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int k = c * 16 + kg + q;
+      v[q] = k < it.K ? A[it.a_off + (long long)row * it.lda + k] : 0.f;
+    }
+    write_pieces4(v, pl, T_APL, kmaj(row, kg));
+  }
+}
+
 }  // namespace
 
 bool gemm_tc32_eligible(int nrhs) { return nrhs > 8; }
+
+long long gemm_tc32_piece_bytes(long long steps) { return steps * T_ASTEP; }
+
+void launch_gemm_tc32_pieces(const GemmItem* items, int nitems, const float* A, const long long* astep,
+                             unsigned char* adig, cudaStream_t s) {
+  if (nitems <= 0) return;
+  gemm_tc32_pieces_kernel<<<(unsigned)nitems, 256, 0, s>>>(items, A, astep, adig);
+}
 
 namespace {
 constexpr int kTc32MaxDev = 64;
@@ -414,14 +503,15 @@ int tc32_nsm() {
 void gemm_tc32_prepare() { (void)tc32_nsm(); }
 
 bool launch_gemm_tc32(const GemmItem* items, int nitems, const float* A, const float* B0, const float* B1, float* C,
-                      const float* Add, const int* idx, int nrhs, double beta, int* status, cudaStream_t s) {
+                      const float* Add, const int* idx, int nrhs, double beta, int* status, cudaStream_t s,
+                      const GemmDigits* dg) {
   if (nitems <= 0) return true;
   const int nsm = tc32_nsm();
   if (!nsm) return false;
   const long long units = (long long)nitems * ((nrhs + T_GN - 1) / T_GN);
   const int grid = (int)std::min<long long>(nsm, units);
   gemm_tc32_kernel<<<grid, T_THREADS, sizeof(TShared), s>>>(items, nitems, A, B0, B1, C, Add, idx, nrhs, (float)beta,
-                                                            status);
+                                                            dg ? dg->dig : nullptr, dg ? dg->step : nullptr, status);
   return true;
 }
 

@@ -325,8 +325,10 @@ __global__ void __launch_bounds__(256) gj_update_kernel(const GJDesc* __restrict
 // exactly in integers and rounds once to FP64.  The neglected terms are below about 2^-64 x 16 x max|W_r| x
 // max|P_c|: on the leaf and merge eliminations that normwise bound can exceed the
 // elementwise FP64 bound 2^-53 sum_t |W_rt| |P_tc| by up to 1e5 (measured on leaf panels),
-// which 7 digits (2^-56) did not absorb and 8 digits do.  The kernel is then bound by
-// the read and write of the updated matrix (HBM), not by arithmetic.
+// which 7 digits (2^-56) did not absorb and 8 digits do.  The tensor work is small (the
+// tensor pipe is about 8 % busy); the kernel is bound by the epilogue's exact integer
+// recombination of the diagonals (ALU and issue about 67 % busy), ahead of the read and write
+// of the updated matrix (HBM about 30 % busy).
 //
 // Tile: 128 rows x 32 columns (MMA M = 128, N = 32, K = 16); operands in shared memory in
 // the canonical K-major no-swizzle layout (8-row x 16-byte core matrices, LBO 128 bytes

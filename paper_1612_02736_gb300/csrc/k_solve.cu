@@ -617,7 +617,7 @@ void launch_gemm_items(const GemmItem* items, int nitems, int maxM, int trans, c
   }
   if constexpr (std::is_same<TA, float>::value && std::is_same<TV, float>::value) {
     if (cx.tc32 && !trans && gemm_tc32_eligible(nrhs) &&
-        launch_gemm_tc32(items, nitems, A, B0, B1, C, Add, idx, nrhs, beta, cx.status, s))
+        launch_gemm_tc32(items, nitems, A, B0, B1, C, Add, idx, nrhs, beta, cx.status, s, cx.dg))
       return;
   }
   const int bn = cx.bn;

@@ -68,6 +68,19 @@ __device__ __forceinline__ bool warp_wait(unsigned long long* b, int parity, vol
   return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 
+// Arrive on the barrier and raise its expected transaction count by `bytes`.
+__device__ __forceinline__ void mb_expect_arrive(unsigned long long* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+// Bulk copy (16-byte aligned addresses, size a multiple of 16) from global to shared memory
+// that completes `bytes` transactions on the barrier.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
 __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
