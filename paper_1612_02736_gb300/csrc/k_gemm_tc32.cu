@@ -2,35 +2,36 @@
 // precision solve, Algorithm 2 with FP32 operators).
 //
 // Every FP32 entry x of the operator block and of the gathered vectors is split into three
-// bf16 values, x1 = bf16(x), x2 = bf16(x - x1), x3 = bf16(x - x1 - x2) (each difference is
-// exact in FP32), so that x1 + x2 + x3 carries the 24 significant bits of x.  A product
-// a b is the sum of the pairs a_s b_t; the pairs with s + t <= 4 are kept, the others weigh
-// below 2^-24 |a| |b|.  Per K step of 16 the three products A_s [B_1 .. B_(4-s)] (one
-// tcgen05.mma each, N = 64 (4 - s), the B planes side by side) write block t of their
-// result to TMEM block s + t - 2, and the epilogue adds the three blocks: FP32
-// accumulation of exact bf16 x bf16 products, the accuracy of an FP32 product.
+// bf16 values x1 = rna(x), x2 = rna(x - x1), x3 = x - x1 - x2 (rna: rounded to 8 significant
+// bits, ties away from zero; each difference is exact in FP32 and x3 has at most 8
+// significant bits), so that x1 + x2 + x3 = x.  A product a b is the sum of the pairs
+// a_s b_t; the pairs with s + t <= 4 are kept, the others together weigh below 2^-23 |a| |b|.  Per
+// K slice of 16 the three products A_s [B_1 .. B_(4-s)] (one tcgen05.mma each, N = 64 (4 - s),
+// the B planes side by side) write block t of their result to TMEM block s + t - 2, and the
+// epilogue adds the three blocks: FP32 accumulation of exact bf16 x bf16 products, the
+// accuracy of an FP32 product.
 //
 // Work unit: one item (<= 64 rows; MMA M = 128, rows 64..127 are padding that no epilogue
-// reads) and 64 right-hand sides.  One CTA per SM loops over the units.  Roles (13 warps):
+// reads) and 64 right-hand sides.  One CTA per SM loops over the units; a stage carries 64
+// k (four K slices).  Roles (14 warps):
 //   warps 0, 1, 4, 5   epilogue: TMEM lanes 0..63 (warp w reads lane quarter w % 4), 32
 //                      right-hand sides each; adds the blocks, passes the 32 x 32 result
 //                      through shared memory and stores whole rows (coalesced), with beta
 //                      and Add;
-//   warp 2             one thread issues the products of each K step;
-//   warps 3, 6 .. 12   producers: warp w copies 8 operator rows and 8 vector columns of every
-//                      K step (16-byte cp.async where aligned, GPF steps ahead, the gathered
-//                      rows' indices read a step earlier) and splits them into the three bf16
-//                      planes when the step comes; no exchange leaves the warp.
-//   warp 13            with cached operator planes (formed once per product set by
-//                      gemm_tc32_pieces_kernel), one thread copies each K step's planes with
+//   warp 2             one thread issues the products of each stage;
+//   warps 3, 6 .. 10,  producers (two per SM sub-partition): producer warp w copies 8 operator
+//   12, 13             rows and 8 vector columns of every stage (16-byte cp.async where
+//                      aligned, GPF stages ahead, the gathered rows' indices read a stage
+//                      earlier) and splits them into the bf16 planes when the stage comes; no
+//                      exchange leaves the warp;
+//   warp 11            with cached operator planes (formed once per product set by
+//                      gemm_tc32_pieces_kernel), one thread copies each stage's planes with
 //                      one bulk copy and the producers only split the vectors.
 // Stages (GST) and the two TMEM accumulators are handed on with mbarriers; every wait is
 // bounded and a timeout stops every role (status -1).
 #include <algorithm>
 #include <cstdint>
 #include <mutex>
-
-#include <cuda_bf16.h>
 
 #include "hps_internal.h"
 #include "tc_common.cuh"
@@ -45,68 +46,77 @@ constexpr int T_GM = 128;           // MMA rows (item rows 0..63, the rest paddi
 constexpr int T_GR = 64;            // item rows
 constexpr int T_GN = 64;            // right-hand sides per unit
 constexpr int T_PL = 3;             // bf16 pieces per entry
-constexpr int T_GST = 4;            // K-step stages
-constexpr int T_GPF = 4;            // K steps the entry copies run ahead
+constexpr int T_KS = 64;            // k per stage
+constexpr int T_NSUB = T_KS / 16;   // K slices (MMA K steps) per stage
+constexpr int T_GST = 2;            // stages
+constexpr int T_GPF = 2;            // stages the entry copies run ahead
 constexpr int T_GRAW = T_GPF + 1;   // raw entry slots
 constexpr int T_THREADS = 448;      // 14 warps
-constexpr int T_LOAD_WARP = 13;     // bulk copies of cached operator planes
+constexpr int T_LOAD_WARP = 11;     // bulk copies of cached operator planes
 constexpr int T_PROD = 256;         // producer threads (8 warps)
 constexpr int T_EPI = 128;          // epilogue threads (4 warps)
 constexpr int T_MMA_WARP = 2;
-constexpr int T_APL = T_GR * 32;            // bytes per A plane (64 rows x 16 k x 2 B)
-constexpr int T_BPL = T_GN * 32;            // bytes per B plane (64 columns x 16 k x 2 B)
+constexpr int T_SPL = 2048;                 // bytes of one piece of one K slice (64 rows x 16 k x 2 B)
+constexpr int T_ASTEP = T_PL * T_SPL;       // bytes of one K slice's operator pieces
 constexpr int T_TBUF = 256;                 // TMEM columns between the two accumulators
-constexpr int T_ASTEP = T_PL * T_APL;       // bytes of one K step's operator planes
 
-// One K step.  A product (M = 128) reads 128 rows from an A plane's start: rows 64..127
-// are the next plane's bytes (for the last plane, the first B plane's), bf16 values that
-// land in TMEM lanes 64..127, which no epilogue reads.
+// One stage: per K slice j, the three pieces' planes side by side (K-major, 8 x 16-byte core
+// matrices, kmaj layout).  The B pieces of a slice are adjacent, so that one product with
+// N = 64 t reads the first t of them as one operand.  A product (M = 128) reads 128 rows from
+// an A plane's start: rows 64..127 are the following bytes (the next plane, or for the last
+// plane of the last slice the first B plane), bf16 values that land in TMEM lanes 64..127,
+// which no epilogue reads.
 struct TStage {
-  unsigned char A[T_PL][T_APL];
-  unsigned char B[T_PL][T_BPL];
+  unsigned char A[T_NSUB][T_PL][T_SPL];
+  unsigned char B[T_NSUB][T_PL][T_SPL];
 };
 
-// Entries of one K step as copied: the operator block row-major (64 rows x 16 k) and the
-// vector block k-major (16 k x 64 right-hand sides), so that each producer thread moves one
-// 16-byte piece of each.
+// Entries of one stage as copied: the operator block row-major (64 rows x 64 k, the 16-byte
+// chunks of row r at chunk index c ^ 4 (r & 1)) and the vector block k-major (64 k x 64
+// right-hand sides, the 16-byte chunks of row k at c ^ 2 ((k >> 2) & 3)), so that the
+// producers' reads in the split hit distinct banks.
 struct TRaw {
-  float A[T_GR][16];
-  float B[16][T_GN];
+  float A[T_GR][T_KS];
+  float B[T_KS][T_GN];
 };
 
 struct TShared {
   TStage st[T_GST];
   TRaw raw[T_GRAW];
   float ct[4][32][33];  // epilogue: each warp's 32 x 32 result tile, for coalesced stores
+  int2 meta[8][T_GRAW];  // per producer warp and raw slot: item rows, K slices (0: none)
   unsigned long long sfull[T_GST], sfree[T_GST], tfull[2], tfree[2], mdone;
   unsigned int tmem_base;
   int abort_flag;
 };
 
-// The three bf16 pieces of 4 consecutive k of one row (column), one 8-byte store per plane.
+__device__ __forceinline__ int swz_a(int row, int chunk) { return chunk ^ ((row & 1) << 2); }
+__device__ __forceinline__ int swz_b(int k, int chunk) { return chunk ^ (((k >> 2) & 3) << 1); }
+
+// x rounded to 8 significant bits, ties away from zero, as an FP32 bit pattern whose low 16
+// bits are garbage (the caller masks or takes the high half).
+__device__ __forceinline__ uint32_t rna8(float x) { return __float_as_uint(x) + 0x8000u; }
+
+// The three bf16 pieces of 4 consecutive k of one row (column), one 8-byte store per plane;
+// the planes of a slice are `plane_bytes` apart.
 __device__ __forceinline__ void write_pieces4(const float* v, unsigned char* plane0, int plane_bytes, int off) {
-  uint32_t w[T_PL][2];
+  uint32_t p[T_PL][4];
 #pragma unroll
-  for (int q = 0; q < 4; q += 2) {
-    uint32_t lo[T_PL], hi[T_PL];
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      float x = v[q + e];
-#pragma unroll
-      for (int s = 0; s < T_PL; ++s) {
-        const __nv_bfloat16 b = __float2bfloat16_rn(x);
-        x = x - __bfloat162float(b);  // exact: b is x rounded to 8 significant bits
-        const uint32_t bits = (uint32_t)__bfloat16_as_ushort(b);
-        if (e == 0) lo[s] = bits;
-        else hi[s] = bits;
-      }
-    }
-#pragma unroll
-    for (int s = 0; s < T_PL; ++s) w[s][q / 2] = lo[s] | (hi[s] << 16);
+  for (int e = 0; e < 4; ++e) {
+    const float x = v[e];
+    const uint32_t h1 = rna8(x);
+    const float r1 = x - __uint_as_float(h1 & 0xffff0000u);   // exact
+    const uint32_t h2 = rna8(r1);
+    const float r2 = r1 - __uint_as_float(h2 & 0xffff0000u);  // exact, 8 significant bits
+    p[0][e] = h1;
+    p[1][e] = h2;
+    p[2][e] = __float_as_uint(r2);
   }
 #pragma unroll
-  for (int s = 0; s < T_PL; ++s)
-    *reinterpret_cast<uint2*>(plane0 + s * plane_bytes + off) = make_uint2(w[s][0], w[s][1]);
+  for (int s = 0; s < T_PL; ++s) {
+    const uint32_t lo = __byte_perm(p[s][0], p[s][1], 0x7632), hi = __byte_perm(p[s][2], p[s][3], 0x7632);
+    *reinterpret_cast<uint2*>(plane0 + s * plane_bytes + off) = make_uint2(lo, hi);
+  }
 }
 
 __device__ __forceinline__ void zero_pieces4(unsigned char* plane0, int plane_bytes, int off) {
@@ -114,14 +124,31 @@ __device__ __forceinline__ void zero_pieces4(unsigned char* plane0, int plane_by
   for (int s = 0; s < T_PL; ++s) *reinterpret_cast<uint2*>(plane0 + s * plane_bytes + off) = make_uint2(0u, 0u);
 }
 
-__device__ __forceinline__ int map_row32(const int* __restrict__ idx, int base_or_off, int row_base, int k) {
-  return base_or_off < 0 ? row_base + k : row_base + idx[base_or_off + k];
-}
-
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
 
+// Position of a CTA in its sequence of units (item ii, column block nb), advanced by the
+// grid size without division.
+struct UnitCur {
+  int ii, nb;
+};
+struct UnitStep {
+  int nnb, dq, dr;  // column blocks per item; grid = dq nnb + dr
+  __device__ UnitCur first() const { return {(int)blockIdx.x / nnb, (int)blockIdx.x % nnb}; }
+  __device__ void next(UnitCur& u) const {
+    u.ii += dq;
+    u.nb += dr;
+    if (u.nb >= nnb) {
+      u.nb -= nnb;
+      ++u.ii;
+    }
+  }
+};
+
+// Stages of a unit's item: ceil(K / 64); K slices of stage c: min(4, ceil((K - 64 c) / 16)).
+__device__ __forceinline__ int item_stages(int K) { return (K + T_KS - 1) / T_KS; }
+__device__ __forceinline__ int stage_slices(int K, int c) { return min(T_NSUB, (K - c * T_KS + 15) >> 4); }
 
 __global__ void __launch_bounds__(T_THREADS, 1) gemm_tc32_kernel(const GemmItem* __restrict__ items, int nitems,
                                                                  const float* __restrict__ A,
@@ -135,9 +162,11 @@ __global__ void __launch_bounds__(T_THREADS, 1) gemm_tc32_kernel(const GemmItem*
   extern __shared__ __align__(1024) unsigned char t_raw[];
   TShared& sh = *reinterpret_cast<TShared*>(t_raw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int nnb = (nrhs + T_GN - 1) / T_GN;
-  const long long total = (long long)nitems * nnb;
-  // cached operator planes (adig): one thread of the loader warp copies each K step's planes
+  UnitStep us;
+  us.nnb = (nrhs + T_GN - 1) / T_GN;
+  us.dq = (int)gridDim.x / us.nnb;
+  us.dr = (int)gridDim.x % us.nnb;
+  // cached operator planes (adig): one thread of the loader warp copies each stage's planes
   // with one bulk copy, and the producers only split the vectors
   const bool cached = adig != nullptr;
   if (tid == 0) {
@@ -172,42 +201,51 @@ __global__ void __launch_bounds__(T_THREADS, 1) gemm_tc32_kernel(const GemmItem*
     if (lane == 0) {
       // kind::f16 with bf16 A and B, FP32 accumulators, M = 128; N set per product
       const uint32_t idesc0 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(T_GM >> 4) << 24);
-      long long ks = 0;
-      int nu = 0;
+      int ks = 0, nu = 0;
       bool stop = false;
-      for (long long u = blockIdx.x; u < total && !stop; u += gridDim.x, ++nu) {
-        const GemmItem it = items[u / nnb];
-        const int nk = (it.K + 15) >> 4;
+      UnitCur u = us.first();
+      int K = u.ii < nitems ? items[u.ii].K : 0;
+      for (; u.ii < nitems && !stop; ++nu) {
+        UnitCur un = u;
+        us.next(un);
+        const int Kn = un.ii < nitems ? items[un.ii].K : 0;  // read a unit ahead of its use
         const int tb = nu & 1;
         if (nu >= 2 && !mb_wait(&sh.tfree[tb], ((nu >> 1) - 1) & 1, abort_flag, status)) break;
         asm volatile("tcgen05.fence::after_thread_sync;");
+        const int nk = item_stages(K);
         for (int c = 0; c < nk; ++c, ++ks) {
-          const int st = (int)(ks % T_GST);
-          if (!mb_wait(&sh.sfull[st], (int)((ks / T_GST) & 1), abort_flag, status)) {
+          const int st = ks % T_GST;
+          if (!mb_wait(&sh.sfull[st], (ks / T_GST) & 1, abort_flag, status)) {
             stop = true;
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;");
-          const uint32_t a0 = smem_u32(sh.st[st].A[0]), b0 = smem_u32(sh.st[st].B[0]);
+          const int nsub = stage_slices(K, c);
 #pragma unroll 1
-          for (int sa = 1; sa <= T_PL; ++sa) {
-            const int nt = T_PL + 1 - sa;  // B pieces 1 .. 4 - sa
-            const uint64_t ad = umma_desc(a0 + (sa - 1) * T_APL, 128, 256);
-            const uint64_t bd = umma_desc(b0, 128, 256);
-            const uint32_t idesc = idesc0 | ((uint32_t)((T_GN * nt) >> 3) << 17);
-            const uint32_t acc = (c > 0 || sa > 1) ? 1u : 0u;
-            asm volatile(
-                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-                    tmem + (uint32_t)(tb * T_TBUF + (sa - 1) * T_GN)),
-                "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+          for (int j = 0; j < nsub; ++j) {
+            const uint64_t bd = umma_desc(smem_u32(sh.st[st].B[j][0]), 128, 256);
+#pragma unroll
+            for (int sa = 1; sa <= T_PL; ++sa) {
+              const int nt = T_PL + 1 - sa;  // B pieces 1 .. 4 - sa
+              const uint64_t ad = umma_desc(smem_u32(sh.st[st].A[j][sa - 1]), 128, 256);
+              const uint32_t idesc = idesc0 | ((uint32_t)((T_GN * nt) >> 3) << 17);
+              const uint32_t acc = (c > 0 || j > 0 || sa > 1) ? 1u : 0u;
+              asm volatile(
+                  "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                  " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                      tmem + (uint32_t)(tb * T_TBUF + (sa - 1) * T_GN)),
+                  "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+            }
           }
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
               smem_u32(&sh.sfree[st])));
         }
         if (stop) break;
+        // (an item with K = 0 issues no product: the epilogue does not read its accumulator)
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
             smem_u32(&sh.tfull[tb])));
+        u = un;
+        K = Kn;
       }
       // every product issued has completed before the TMEM is released
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -215,150 +253,208 @@ __global__ void __launch_bounds__(T_THREADS, 1) gemm_tc32_kernel(const GemmItem*
       mb_drain(&sh.mdone, 0);
     }
   } else if (warp == T_LOAD_WARP) {
-    // ---------------- cached operator planes: lane 0 copies each K step's planes into its
-    // stage once the stage is free, arming the stage's barrier with their bytes
+    // ---------------- cached operator planes: lane 0 copies each stage's planes into the
+    // stage once it is free, arming the stage's barrier with their bytes
     if (cached && lane == 0) {
-      long long ks = 0;
+      int ks = 0;
       bool stop = false;
-      for (long long u = blockIdx.x; u < total && !stop; u += gridDim.x) {
-        const long long item = u / nnb;
-        const int nk = (items[item].K + 15) >> 4;
-        const unsigned char* src = adig + astep[item] * T_ASTEP;
+      UnitCur u = us.first();
+      int K = 0;
+      long long a0 = 0;
+      if (u.ii < nitems) {
+        K = items[u.ii].K;
+        a0 = astep[u.ii];
+      }
+      for (; u.ii < nitems && !stop;) {
+        UnitCur un = u;
+        us.next(un);
+        int Kn = 0;
+        long long an = 0;
+        if (un.ii < nitems) {  // read a unit ahead of their use
+          Kn = items[un.ii].K;
+          an = astep[un.ii];
+        }
+        const unsigned char* src = adig + a0 * T_ASTEP;
+        const int nk = item_stages(K);
         for (int c = 0; c < nk; ++c, ++ks) {
-          const int st = (int)(ks % T_GST);
-          if (ks >= T_GST && !mb_wait(&sh.sfree[st], (int)((ks / T_GST) - 1) & 1, abort_flag, status)) {
+          const int st = ks % T_GST;
+          if (ks >= T_GST && !mb_wait(&sh.sfree[st], ((ks / T_GST) - 1) & 1, abort_flag, status)) {
             stop = true;
             break;
           }
-          mb_expect_arrive(&sh.sfull[st], T_ASTEP);
-          bulk_load(sh.st[st].A[0], src + (long long)c * T_ASTEP, T_ASTEP, &sh.sfull[st]);
+          const uint32_t bytes = (uint32_t)stage_slices(K, c) * T_ASTEP;
+          mb_expect_arrive(&sh.sfull[st], bytes);
+          bulk_load(sh.st[st].A[0][0], src + (long long)c * T_NSUB * T_ASTEP, bytes, &sh.sfull[st]);
         }
+        u = un;
+        K = Kn;
+        a0 = an;
       }
       // the copies issued have landed before the block exits
       for (int b = 0; b < T_GST; ++b) {
-        const long long n = ks > b ? (ks - 1 - b) / T_GST + 1 : 0;  // copies armed on stage b
-        if (n > 0) mb_drain(&sh.sfull[b], (int)((n - 1) & 1));
+        const int n = ks > b ? (ks - 1 - b) / T_GST + 1 : 0;  // copies armed on stage b
+        if (n > 0) mb_drain(&sh.sfull[b], (n - 1) & 1);
       }
     }
   } else if (!epi) {
-    // ---------------- producers: warps 3, 6 .. 12 -> producer warp pw = 0 .. 7.  Warp pw owns
-    // operator rows 8 pw .. 8 pw + 7 and vector columns 8 pw .. 8 pw + 7 of every K step: it
-    // copies them GPF steps ahead (lane l: 4 consecutive k of row 8 pw + l / 4; 4 consecutive
-    // right-hand sides 8 pw + 4 (l % 2) .. + 3 at k = l / 2) and, when the step comes, splits
-    // them into the bf16 planes (lane l: 4 k of row 8 pw + l / 4 and of column 8 pw + l / 4),
-    // so every exchange stays inside the warp.  The item of a step and the gathered vector row
-    // of the lane's k are read one step before the step's copies are issued (the next unit's
-    // item one unit ahead), so that no copy waits for an index load.
-    const int pw = warp == 3 ? 0 : warp - 5;
-    const int arow = 8 * pw + (lane >> 2), akq = (lane & 3) * 4;  // operator row: copy and split
-    const int bk = lane >> 1, bnq = 8 * pw + (lane & 1) * 4;        // vector copy
-    const int bcol = 8 * pw + (lane >> 2), bkg = (lane & 3) * 4;    // vector split
+    // ---------------- producers: warps 3, 6 .. 10, 12, 13 -> producer warp pw = 0 .. 7.  Warp
+    // pw owns operator rows 8 pw .. 8 pw + 7 and vector columns 8 pw .. 8 pw + 7 of every
+    // stage.  Lane l copies, GPF stages ahead, 4 consecutive k (16 j + 4 (l % 4), j = 0..3) of
+    // operator row 8 pw + l / 4, and 4 consecutive right-hand sides 8 pw + 4 (l % 2) .. + 3 at
+    // stage k = l / 2 + 16 j; when the stage comes it splits its own operator entries and the
+    // vector entries of column 8 pw + l / 4 at k = 16 j + 4 (l % 4) .. + 3 into the bf16 planes,
+    // so every exchange stays inside the warp.  The gathered vector rows' indices of a stage
+    // are read one stage before its copies are issued, the next unit's item one unit ahead,
+    // so that no copy waits for an index load.
+    const int pw = warp == 3 ? 0 : (warp <= 10 ? warp - 5 : warp - 6);
+    const int arow = 8 * pw + (lane >> 2), aq = lane & 3;       // operator row, k quad
+    const int bkl = lane >> 1, bch = 2 * pw + (lane & 1);        // vector copy: k, 16-byte chunk
+    const int bcol = 8 * pw + (lane >> 2);                       // vector split: column
     const bool bvec = (nrhs & 3) == 0 && ((reinterpret_cast<uintptr_t>(B0) | reinterpret_cast<uintptr_t>(B1)) & 15) == 0;
     struct Cur {
-      long long u;
-      int c;
-      GemmItem it, itn;  // the unit's item and the next unit's
+      UnitCur u, un;   // this unit and the next
+      int c;           // stage within the unit
+      GemmItem it, itn;
+    };
+    auto load_item = [&](const UnitCur& x, GemmItem& it) {
+      if (x.ii < nitems) it = items[x.ii];
+      else it.K = 0;
+    };
+    // to the next unit with K > 0 (or past the end)
+    auto next_unit = [&](Cur& x) {
+      do {
+        x.u = x.un;
+        x.it = x.itn;
+        us.next(x.un);
+        load_item(x.un, x.itn);
+      } while (x.u.ii < nitems && x.it.K == 0);
+      x.c = 0;
     };
     auto start_cur = [&](Cur& x) {
-      x.u = blockIdx.x;
-      x.c = 0;
-      if (x.u < total) x.it = items[x.u / nnb];
-      if (x.u + gridDim.x < total) x.itn = items[(x.u + gridDim.x) / nnb];
+      x.un = us.first();
+      load_item(x.un, x.itn);
+      next_unit(x);
     };
-    auto step_cur = [&](Cur& x) {
-      if (x.u >= total) return;
-      if (++x.c >= ((x.it.K + 15) >> 4)) {
-        x.c = 0;
-        x.u += gridDim.x;
-        x.it = x.itn;
-        if (x.u + gridDim.x < total) x.itn = items[(x.u + gridDim.x) / nnb];
+    auto advance = [&](Cur& x) {
+      if (x.u.ii >= nitems) return;
+      if (++x.c >= item_stages(x.it.K)) next_unit(x);
+    };
+    // raw index entries of the gathered vector rows of this lane's 4 k at the cursor's stage
+    auto load_rows = [&](const Cur& x, int (&r)[T_NSUB]) {
+#pragma unroll
+      for (int j = 0; j < T_NSUB; ++j) {
+        r[j] = 0;
+        if (x.u.ii >= nitems) continue;
+        const int k = x.c * T_KS + 16 * j + bkl;
+        if (k >= x.it.K) continue;
+        if (k < x.it.kseg) {
+          if (x.it.b0_idx >= 0) r[j] = idx[x.it.b0_idx + k];
+        } else if (x.it.b1_idx >= 0) {
+          r[j] = idx[x.it.b1_idx + k - x.it.kseg];
+        }
       }
     };
-    // gathered vector row of this lane's k at the cursor's step: 2 row + (1 for B1), or -1
-    auto brow_of = [&](const Cur& x) -> long long {
-      if (x.u >= total) return -1;
-      const int k = x.c * 16 + bk;
-      if (k >= x.it.K) return -1;
-      return k < x.it.kseg ? 2ll * map_row32(idx, x.it.b0_idx, x.it.b0_row, k)
-                           : 2ll * map_row32(idx, x.it.b1_idx, x.it.b1_row, k - x.it.kseg) + 1;
-    };
-    auto issue = [&](const Cur& x, long long brow, int slot) {
-      if (x.u < total) {
+    auto issue = [&](const Cur& x, const int (&r)[T_NSUB], int slot) {
+      const bool valid = x.u.ii < nitems;
+      const int nsub = valid ? stage_slices(x.it.K, x.c) : 0;
+      if (lane == 0) sh.meta[pw][slot] = make_int2(valid ? x.it.M : 0, nsub);
+      if (valid) {
         TRaw& rw = sh.raw[slot];
         const GemmItem& it = x.it;
-        const int n0 = (int)(x.u % nnb) * T_GN, k0 = x.c * 16;
+        const int k0 = x.c * T_KS;
         if (!cached && arow < it.M) {
-          float* dst = &rw.A[arow][akq];
-          const float* src = A + it.a_off + (long long)arow * it.lda + k0 + akq;
-          if (k0 + akq + 3 < it.K && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
-            cp_async16(dst, src);
-          } else {
+          const float* srow = A + it.a_off + (long long)arow * it.lda;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              if (k0 + akq + q < it.K) cp_async4(dst + q, src + q);
-              else dst[q] = 0.f;
+          for (int j = 0; j < T_NSUB; ++j) {
+            if (j >= nsub) break;
+            const int k = k0 + 16 * j + 4 * aq;
+            float* dst = &rw.A[arow][4 * swz_a(arow, 4 * j + aq)];
+            const float* src = srow + k;
+            if (k + 3 < it.K && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+              cp_async16(dst, src);
+            } else {
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                if (k + q < it.K) cp_async4(dst + q, src + q);
+                else dst[q] = 0.f;
+              }
             }
           }
         }
-        float* dst = &rw.B[bk][bnq];
-        const int n = n0 + bnq;
-        if (brow >= 0) {
-          const float* src = ((brow & 1) ? B1 : B0) + (brow >> 1) * nrhs + n;
-          if (bvec && n + 3 < nrhs) {
-            cp_async16(dst, src);
+        const int n = x.u.nb * T_GN + 4 * bch;
+#pragma unroll
+        for (int j = 0; j < T_NSUB; ++j) {
+          if (j >= nsub) break;
+          const int kl = 16 * j + bkl, k = k0 + kl;
+          float* dst = &rw.B[kl][4 * swz_b(kl, bch)];
+          if (k < it.K) {
+            const bool s1 = k >= it.kseg;
+            const int kk = s1 ? k - it.kseg : k;
+            const int row = (s1 ? it.b1_row : it.b0_row) + ((s1 ? it.b1_idx : it.b0_idx) >= 0 ? r[j] : kk);
+            const float* src = (s1 ? B1 : B0) + (long long)row * nrhs + n;
+            if (bvec && n + 3 < nrhs) {
+              cp_async16(dst, src);
+            } else {
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                if (n + q < nrhs) cp_async4(dst + q, src + q);
+                else dst[q] = 0.f;
+              }
+            }
           } else {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              if (n + q < nrhs) cp_async4(dst + q, src + q);
-              else dst[q] = 0.f;
-            }
+            for (int q = 0; q < 4; ++q) dst[q] = 0.f;
           }
-        } else {
-#pragma unroll
-          for (int q = 0; q < 4; ++q) dst[q] = 0.f;
         }
       }
-      cp_commit();  // one group per step, empty past the end, so that the counts stay aligned
+      cp_commit();  // one group per stage, empty past the end, so that the counts stay aligned
     };
-    Cur cv, is, la;  // conversion (step ks), issue (ks + GPF), look-ahead (ks + GPF + 1)
-    start_cur(cv);
-    start_cur(is);
-    long long brow = brow_of(is);
+    Cur x;  // the stage whose copies are issued next
+    int r[T_NSUB];
+    start_cur(x);
+    load_rows(x, r);
     for (int i = 0; i < T_GPF; ++i) {
-      issue(is, brow, i % T_GRAW);
-      step_cur(is);
-      brow = brow_of(is);
+      issue(x, r, i);
+      advance(x);
+      load_rows(x, r);
     }
-    la = is;
-    step_cur(la);
-    long long ks = 0;
-    while (cv.u < total) {
-      cp_wait<T_GPF - 1>();  // this lane's copies of step ks have landed
+    for (int ks = 0;; ++ks) {
+      cp_wait<T_GPF - 1>();  // this lane's copies of stage ks have landed
       __syncwarp();          // ... and every lane's of this warp
-      const int st = (int)(ks % T_GST), slot = (int)(ks % T_GRAW);
-      if (ks >= T_GST && !warp_wait(&sh.sfree[st], (int)((ks / T_GST) - 1) & 1, abort_flag, status)) break;
+      const int st = ks % T_GST, slot = ks % T_GRAW;
+      const int2 mt = sh.meta[pw][slot];
+      if (mt.y == 0) break;
+      if (ks >= T_GST && !warp_wait(&sh.sfree[st], ((ks / T_GST) - 1) & 1, abort_flag, status)) break;
       const TRaw& rw = sh.raw[slot];
-      if (!cached) {
-        if (arow >= cv.it.M) zero_pieces4(sh.st[st].A[0], T_APL, kmaj(arow, akq));
-        else write_pieces4(&rw.A[arow][akq], sh.st[st].A[0], T_APL, kmaj(arow, akq));
-      }
-      {
+      TStage& sg = sh.st[st];
+#pragma unroll
+      for (int j = 0; j < T_NSUB; ++j) {
+        if (j >= mt.y) break;
+        if (!cached) {
+          const int off = kmaj(arow, 4 * aq);
+          if (arow >= mt.x) {
+            zero_pieces4(sg.A[j][0], T_SPL, off);
+          } else {
+            const float4 a4 = *reinterpret_cast<const float4*>(&rw.A[arow][4 * swz_a(arow, 4 * j + aq)]);
+            const float v[4] = {a4.x, a4.y, a4.z, a4.w};
+            write_pieces4(v, sg.A[j][0], T_SPL, off);
+          }
+        }
         float v[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) v[q] = rw.B[bkg + q][bcol];
-        write_pieces4(v, sh.st[st].B[0], T_BPL, kmaj(bcol, bkg));
+        for (int q = 0; q < 4; ++q) {
+          const int kl = 16 * j + 4 * aq + q;
+          v[q] = rw.B[kl][4 * swz_b(kl, bcol >> 2) + (bcol & 3)];
+        }
+        write_pieces4(v, sg.B[j][0], T_SPL, kmaj(bcol, 4 * aq));
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       mb_arrive(&sh.sfull[st]);
-      // step ks + GPF reuses the slot of step ks - 1, which this warp finished reading
-      // before the warp barrier above
-      const long long brow_la = brow_of(la);  // read a step ahead of its use
-      issue(is, brow, (int)((ks + T_GPF) % T_GRAW));
-      is = la;
-      brow = brow_la;
-      step_cur(la);
-      step_cur(cv);
-      ++ks;
+      // stage ks + GPF reuses the slot of stage ks - 1, which this warp finished reading before
+      // the warp barrier above
+      issue(x, r, (ks + T_GPF) % T_GRAW);
+      advance(x);
+      load_rows(x, r);  // first used by the next stage's issue
     }
     asm volatile("cp.async.wait_all;" ::: "memory");  // copies still in flight land before exit
   } else {
@@ -370,9 +466,9 @@ __global__ void __launch_bounds__(T_THREADS, 1) gemm_tc32_kernel(const GemmItem*
     const int g = warp >> 2, ew = (warp & 1) + 2 * g;  // tile of this warp
     float (*tile)[33] = sh.ct[ew];
     int nu = 0;
-    for (long long u = blockIdx.x; u < total; u += gridDim.x, ++nu) {
-      const GemmItem it = items[u / nnb];
-      const int n0 = (int)(u % nnb) * T_GN;
+    for (UnitCur u = us.first(); u.ii < nitems; us.next(u), ++nu) {
+      const GemmItem it = items[u.ii];
+      const int n0 = u.nb * T_GN;
       const int tb = nu & 1;
       if (!warp_wait(&sh.tfull[tb], (nu >> 1) & 1, abort_flag, status)) break;
       asm volatile("tcgen05.fence::after_thread_sync;");
@@ -382,18 +478,20 @@ __global__ void __launch_bounds__(T_THREADS, 1) gemm_tc32_kernel(const GemmItem*
         float r[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j) r[j] = 0.f;
+        if (it.K > 0) {  // (no product wrote the accumulator of an item with K = 0)
 #pragma unroll
-        for (int d = 0; d < T_PL; ++d) {
-          uint32_t v[16];
-          const uint32_t addr = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(tb * T_TBUF + d * T_GN + jb);
-          asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-              : "r"(addr));
-          asm volatile("tcgen05.wait::ld.sync.aligned;");
+          for (int d = 0; d < T_PL; ++d) {
+            uint32_t v[16];
+            const uint32_t addr = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(tb * T_TBUF + d * T_GN + jb);
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                : "r"(addr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
-          for (int j = 0; j < 16; ++j) r[j] += __uint_as_float(v[j]);
+            for (int j = 0; j < 16; ++j) r[j] += __uint_as_float(v[j]);
+          }
         }
 #pragma unroll
         for (int j = 0; j < 16; ++j) tile[lane][16 * hh + j] = r[j];
@@ -406,7 +504,7 @@ __global__ void __launch_bounds__(T_THREADS, 1) gemm_tc32_kernel(const GemmItem*
       // one by one
       const int n = n0 + 32 * g + lane;
       const int myrow = q4 * 32 + lane;
-      const int mymap = myrow < it.M ? map_row32(idx, it.c_idx, it.c_row, myrow) : 0;
+      const int mymap = myrow < it.M ? (it.c_idx < 0 ? it.c_row + myrow : it.c_row + idx[it.c_idx + myrow]) : 0;
       const int nrow = min(32, it.M - q4 * 32);
       const bool col_ok = n < nrhs;
       float o[32];
@@ -437,7 +535,7 @@ __global__ void __launch_bounds__(T_THREADS, 1) gemm_tc32_kernel(const GemmItem*
   if (warp == T_MMA_WARP) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
 }
 
-// The operator's bf16 pieces of every K step of one item (one block per item), in the stage
+// The operator's bf16 pieces of every K slice of one item (one block per item), in the stage
 // layout, at adig + astep[item] * T_ASTEP; rows past the item are zero.  The operators do not
 // change after the build, so a product set keeps these planes across solves.
 __global__ void __launch_bounds__(256) gemm_tc32_pieces_kernel(const GemmItem* __restrict__ items,
@@ -451,7 +549,7 @@ __global__ void __launch_bounds__(256) gemm_tc32_pieces_kernel(const GemmItem* _
   for (int c = 0; c < nk; ++c) {
     unsigned char* pl = dst + (long long)c * T_ASTEP;
     if (row >= it.M) {
-      zero_pieces4(pl, T_APL, kmaj(row, kg));
+      zero_pieces4(pl, T_SPL, kmaj(row, kg));
       continue;
     }
     float v[4];
@@ -460,7 +558,7 @@ __global__ void __launch_bounds__(256) gemm_tc32_pieces_kernel(const GemmItem* _
       const int k = c * 16 + kg + q;
       v[q] = k < it.K ? A[it.a_off + (long long)row * it.lda + k] : 0.f;
     }
-    write_pieces4(v, pl, T_APL, kmaj(row, kg));
+    write_pieces4(v, pl, T_SPL, kmaj(row, kg));
   }
 }
 
