@@ -2088,6 +2088,36 @@ int solve_mixed(hps_handle* h, const double* f, const double* g, const double* r
   return HPS_OK;
 }
 
+// Contraction of the refinement, measured once at the end of a mixed build on a model
+// problem of the same operator (unit load, zero boundary data, one right-hand side), so that
+// the first solve already runs the calibrated schedule.  The schedule stays checked after
+// every solve, so a problem that contracts more slowly than the model falls back to adaptive
+// refinement.  Best effort: a failure here leaves the handle uncalibrated and reports nothing.
+void calibrate_mixed(hps_handle* h, cudaStream_t s) {
+  const std::string saved = g_err;
+  const long long nf = h->n_bdry, ng = (long long)h->n_leaf * h->pp;
+  std::vector<void*> bufs;
+  try {
+    double* f = (double*)h->al.get((size_t)std::max(nf, 1ll) * sizeof(double), s);
+    bufs.push_back(f);
+    double* g = (double*)h->al.get((size_t)ng * sizeof(double), s);
+    bufs.push_back(g);
+    double* u = (double*)h->al.get((size_t)ng * sizeof(double), s);
+    bufs.push_back(u);
+    if (nf > 0) CK(cudaMemsetAsync(f, 0, (size_t)nf * sizeof(double), s));
+    launch_fill(g, ng, 1.0, s);
+    CKL();
+    int it = 0;
+    solve_mixed(h, f, g, nullptr, 1, u, nullptr, &it, s);
+    CK(cudaStreamSynchronize(s));
+  } catch (const CudaError&) {
+    cudaGetLastError();
+  } catch (const std::exception&) {
+  }
+  for (void* b : bufs) h->al.put(b, s);
+  g_err = saved;
+}
+
 }  // namespace
 
 extern "C" {
@@ -2566,6 +2596,7 @@ int hps_build(const hps_tree* tree, const double* coeffs, int p, const hps_opts*
       delete h;
       return fail(HPS_ERR_SINGULAR, "pivot breakdown in the elimination of box " + std::to_string(box));
     }
+    if (o.precision == HPS_MIXED) calibrate_mixed(h, s);
   } catch (const CudaError& e) {
     delete h;
     return fail(e.code, e.msg);

@@ -340,6 +340,7 @@ void launch_leaf_apply_df(const ResidualArgs& a, const double* u, double alpha, 
 void launch_jump_residual(const int* pairs, int npairs, int q, const double* vflux,
                           double* rho_out, int nrhs, cudaStream_t s);
 void launch_absmax(const double* x, long long n, double* out, cudaStream_t s);
+void launch_fill(double* x, long long n, double v, cudaStream_t s);  // x[0..n) = v
 void launch_absmax_f32(const float* x, long long n, double* out, cudaStream_t s);  // max |x| as a double
 // Row combinations dst[d] = A[a] (+ sign * B[b] if b >= 0), entries (d, a, b, sign) at tab,
 // rows of nrhs values.

@@ -712,6 +712,15 @@ void launch_axpy_to_f64(const TI* x, double* y, long long n, cudaStream_t s) {
   axpy_kernel<TI><<<grid_for(n), 256, 0, s>>>(x, y, n);
 }
 
+__global__ void fill_kernel(double* __restrict__ x, long long n, double v) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    x[i] = v;
+}
+void launch_fill(double* x, long long n, double v, cudaStream_t s) {
+  if (n <= 0) return;
+  fill_kernel<<<grid_for(n, 256, 1024), 256, 0, s>>>(x, n, v);
+}
+
 void launch_absmax(const double* x, long long n, double* out, cudaStream_t s) {
   absmax_kernel<double><<<grid_for(n, 256, 1024), 256, 0, s>>>(x, n, reinterpret_cast<unsigned long long*>(out));
 }

@@ -70,6 +70,56 @@ def test_autograd_function_finite_differences():
     assert abs(fd - an) < 1e-5 * abs(an)
 
 
+def test_config5_64x64_p16_recompute_ten_directions():
+    # the adjoint workload as specified: J = 0.5 ||u - u_obs||^2 over all collocation nodes
+    # for the variable-coefficient operator at 64 x 64 leaves, p = 16, u_obs the solution at
+    # the perturbed c; gradients through HPSFunction with leaf operators recomputed in the
+    # backward pass, checked by central differences along 10 seeded smooth directions of c
+    # (unit max-norm) and one of g.  At the specified step h = 1e-6 the difference quotient
+    # carries the rounding of the two solves divided by h (a few 1e-4 of the derivative on
+    # some directions); at h = 1e-3 that noise is a thousand times smaller and the O(h^2)
+    # truncation about 1e-6, so there the adjoint must agree to 2e-5.
+    import torch
+    from paper_1612_02736_gb300 import HPSFunction
+    case = make_case(64, 64, 16)
+    p = case["p"]
+    prob = syn.VarCoeffProblem()
+    c_obs = np.array(prob.coeffs(case["X"], case["Y"], perturbed=True))
+    t = gpu_tree(case)
+    f = to_dev(case["f"][:, 0])
+    g = to_dev(case["g"][..., 0])
+    u_obs = HPSFunction.apply(to_dev(c_obs), f, g, t, p).detach()
+
+    def J(c, gg, store):
+        u = HPSFunction.apply(c, f, gg, t, p, store)
+        return 0.5 * torch.sum((u - u_obs) ** 2)
+
+    c = to_dev(case["coeffs"]).requires_grad_(True)
+    gg = g.clone().requires_grad_(True)
+    J(c, gg, False).backward()
+    dirs = []
+    for v1 in syn.smooth_directions(case["X"], case["Y"], n=10, seed_offset=1100, fields=1):
+        v = np.zeros_like(case["coeffs"])
+        v[5] = v1[0] / np.abs(v1[0]).max()
+        dirs.append((to_dev(v), None))
+    vg = syn.smooth_directions(case["X"], case["Y"], n=1, seed_offset=1300, fields=1)[0][0]
+    dirs.append((None, to_dev(vg / np.abs(vg).max())))
+    errs = {1e-6: [], 1e-3: []}
+    for vc, vgd in dirs:
+        an = torch.sum(c.grad * vc).item() if vc is not None else torch.sum(gg.grad * vgd).item()
+        for h in errs:
+            with torch.no_grad():
+                if vc is not None:
+                    jp, jm = J(c.detach() + h * vc, g, True), J(c.detach() - h * vc, g, True)
+                else:
+                    jp, jm = J(c.detach(), g + h * vgd, True), J(c.detach(), g - h * vgd, True)
+            errs[h].append(abs((jp - jm).item() / (2 * h) - an) / abs(an))
+    for h, e in errs.items():
+        print("config-5 central differences, h = %g: relative errors %s" % (h, ["%.1e" % x for x in e]))
+    assert max(errs[1e-6]) < 2e-3, errs[1e-6]
+    assert max(errs[1e-3]) < 2e-5, errs[1e-3]
+
+
 def test_mixed_handle_rejects_adjoint():
     from paper_1612_02736_gb300 import HPSError, Solver
     case = make_case(2, 2, 8)
