@@ -190,9 +190,9 @@ int hps_plan_check(const hps_tree* tree, int p, const hps_opts* opts);
  * call synchronises the stream before it returns and reports SINGULAR with the box id
  * in the message if a pivot broke down; an allocation failure gives OOM with everything
  * allocated so far released.  An HPS_MIXED build ends with one
- * refined solve of a model problem (unit load, zero boundary data, one right-hand side)
- * that calibrates the refinement (see hps_solve); a failure there leaves the handle
- * uncalibrated and is not reported.  *out receives the handle. */
+ * refined solve of a model problem (no load, boundary data 1 + x + 2 y, one right-hand side)
+ * that measures the contraction bound rho of the refinement (see hps_solve); a failure
+ * there leaves the handle without it and is not reported.  *out receives the handle. */
 int hps_build(const hps_tree* tree, const double* coeffs_dev, int p, const hps_opts* opts,
               const hps_allocator* alloc, void* stream, hps_handle** out);
 
@@ -205,12 +205,14 @@ int hps_build(const hps_tree* tree, const double* coeffs_dev, int p, const hps_o
  *   u_dev : [n_leaf][p*p][nrhs]       output: the solution at every leaf Chebyshev node
  * FP64 handles run the sweeps in FP64.  HPS_MIXED handles run them in FP32 and refine
  * against the residual of the collocation system (leaf equations and flux jumps, in
- * double-float arithmetic) with FP64 accumulation.  Until a handle is calibrated (by its
- * build; else by its first solve) the refinement is adaptive, synchronising after every correction du: it stops when
- * max|du| <= ir_tol max|u|, or when the observed contraction of two successive corrections
- * (ratio r < 1/2) predicts the remaining error 2 r max|du| below that.  Those ratios
- * calibrate a contraction bound rho (twice the largest ratio) and the number n of
- * corrections that bring the initial solve's error below ir_tol; later calls without flux-jump
+ * double-float arithmetic) with FP64 accumulation.  Until a handle is calibrated the
+ * refinement is adaptive, synchronising after every correction du: it stops when
+ * max|du| <= ir_tol max|u|, when a contraction bound rho is known (measured by the build)
+ * and rho max|du| <= ir_tol max|u|, or when the observed contraction of two successive
+ * corrections (ratio r < 1/2) predicts the remaining error 2 r max|du| below ir_tol max|u|.
+ * Those ratios raise rho to twice the largest ratio; with rho and the first correction
+ * the solve calibrates the number n of corrections that bring the initial solve's error
+ * below ir_tol; later calls without flux-jump
  * data run the initial solve and n corrections without a test in between (one CUDA graph
  * from the second such call with the same nrhs when use_graphs is set), synchronise once
  * and accept when rho max|du_n| <= ir_tol max|u|, else refine on adaptively.  NaN or

@@ -104,6 +104,21 @@ std::vector<float> split_df(const std::vector<double>& v) {
   return o;
 }
 
+// For each row of a rows x (4 q) matrix (row-major): the indices of its q-column blocks
+// that hold a nonzero, -1 padded to 4 per row.
+std::vector<int> nonzero_blocks(const std::vector<double>& m, int rows, int cols, int q) {
+  std::vector<int> out((size_t)rows * 4, -1);
+  for (int r = 0; r < rows; ++r) {
+    int n = 0;
+    for (int b = 0; b < cols / q; ++b) {
+      bool nz = false;
+      for (int j = b * q; j < b * q + q; ++j) nz = nz || m[(size_t)r * cols + j] != 0.0;
+      if (nz) out[(size_t)r * 4 + n++] = b;
+    }
+  }
+  return out;
+}
+
 template <typename T>
 T* upload(Alloc& al, cudaStream_t s, const std::vector<T>& v, std::vector<DBuf>& owned) {
   void* p = al.get(v.size() * sizeof(T), s);
@@ -286,6 +301,7 @@ struct hps_handle {
   // tables
   double *dD = nullptr, *dD2 = nullptr, *dLs = nullptr, *dDLs = nullptr, *dLloc = nullptr, *dDceL = nullptr;
   float2 *dLloc_df = nullptr, *dLce_df = nullptr, *dD_df = nullptr, *dD2_df = nullptr;
+  int* dLce_blk = nullptr;
   double* dhxy = nullptr;
   int* didx = nullptr;
   int* d_leaf_edges = nullptr;
@@ -1847,6 +1863,7 @@ ResidualArgs residual_args(const hps_handle* h, const double* coeffs) {
   ra.Lce_df = h->dLce_df;
   ra.D_df = h->dD_df;
   ra.D2_df = h->dD2_df;
+  ra.Lce_blk = h->dLce_blk;
   return ra;
 }
 
@@ -2067,13 +2084,17 @@ int solve_mixed(hps_handle* h, const double* f, const double* g, const double* r
     if (prev > 0.0) ratio = std::max(ratio, sc[0] / prev);
     const bool small = sc[0] <= tolu;
     const bool predicted = prev > 0.0 && sc[0] < 0.5 * prev && 2.0 * (sc[0] / prev) * sc[0] <= tolu;
+    // a contraction bound already measured on this operator (by the build) predicts the
+    // remaining error from a single correction
+    const bool bounded = !rho && h->ir.rho > 0.0 && h->ir.rho * sc[0] <= tolu;
     prev = sc[0];
-    if (small || predicted) {
+    if (small || predicted || bounded) {
       conv = true;
       ++it;
-      // calibrate from the ratios of this solve (needs two corrections of the original system)
-      if (!rho && ratio > 0.0 && ratio < 0.5 && first > 0.0) {
-        h->ir.rho = std::max(h->ir.rho, 2.0 * ratio);
+      // calibrate from the ratios of this solve (needs two corrections of the original
+      // system), and the number of corrections from this solve's first one
+      if (!rho && ratio > 0.0 && ratio < 0.5) h->ir.rho = std::max(h->ir.rho, 2.0 * ratio);
+      if (!rho && h->ir.rho > 0.0 && h->ir.rho < 1.0 && first > 0.0) {
         int n = 1;
         double e = first;
         while (n < h->opts.ir_max_iter && (e *= h->ir.rho) > tol) ++n;
@@ -2088,28 +2109,37 @@ int solve_mixed(hps_handle* h, const double* f, const double* g, const double* r
   return HPS_OK;
 }
 
-// Contraction of the refinement, measured once at the end of a mixed build on a model
-// problem of the same operator (unit load, zero boundary data, one right-hand side), so that
-// the first solve already runs the calibrated schedule.  The schedule stays checked after
-// every solve, so a problem that contracts more slowly than the model falls back to adaptive
-// refinement.  Best effort: a failure here leaves the handle uncalibrated and reports nothing.
-void calibrate_mixed(hps_handle* h, cudaStream_t s) {
+// Contraction bound of the refinement, measured once at the end of a mixed build on a model
+// problem of the same operator (no load, the linear boundary data 1 + x + 2 y: a smooth
+// solution, with data compatible at the corners).  The bound is a property of the operator
+// and of the FP32 sweeps; the number of corrections also depends on the size of the first
+// correction, which differs between problems, so it is left to the first solve, which then
+// accepts as soon as the bound predicts convergence.  Best effort: a failure here leaves the
+// handle uncalibrated and reports nothing.
+void calibrate_mixed(hps_handle* h, const hps_tree* tree, cudaStream_t s) {
   const std::string saved = g_err;
   const long long nf = h->n_bdry, ng = (long long)h->n_leaf * h->pp;
   std::vector<void*> bufs;
   try {
-    double* f = (double*)h->al.get((size_t)std::max(nf, 1ll) * sizeof(double), s);
+    std::vector<double> fh((size_t)std::max(nf, 1ll), 0.0);
+    int64_t cnt = 0;
+    if (nf > 0 && hps_nodes(tree, h->p, h->q, HPS_NODES_GAUSS_BOUNDARY, nullptr, &cnt) == HPS_OK && cnt == nf) {
+      std::vector<double> xy((size_t)2 * nf);
+      if (hps_nodes(tree, h->p, h->q, HPS_NODES_GAUSS_BOUNDARY, xy.data(), &cnt) == HPS_OK)
+        for (long long i = 0; i < nf; ++i) fh[i] = 1.0 + xy[2 * i] + 2.0 * xy[2 * i + 1];
+    }
+    double* f = (double*)h->al.get(fh.size() * sizeof(double), s);
     bufs.push_back(f);
     double* g = (double*)h->al.get((size_t)ng * sizeof(double), s);
     bufs.push_back(g);
     double* u = (double*)h->al.get((size_t)ng * sizeof(double), s);
     bufs.push_back(u);
-    if (nf > 0) CK(cudaMemsetAsync(f, 0, (size_t)nf * sizeof(double), s));
-    launch_fill(g, ng, 1.0, s);
-    CKL();
+    CK(cudaMemcpyAsync(f, fh.data(), fh.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(g, 0, (size_t)ng * sizeof(double), s));
     int it = 0;
     solve_mixed(h, f, g, nullptr, 1, u, nullptr, &it, s);
     CK(cudaStreamSynchronize(s));
+    h->ir.nfix = 0;
   } catch (const CudaError&) {
     cudaGetLastError();
   } catch (const std::exception&) {
@@ -2563,6 +2593,7 @@ int hps_build(const hps_tree* tree, const double* coeffs, int p, const hps_opts*
     h->dLloc = upload(h->al, s, h->rt.Lloc, h->owned);
     h->dLloc_df = (float2*)upload(h->al, s, split_df(h->rt.Lloc), h->owned);
     h->dLce_df = (float2*)upload(h->al, s, split_df(h->rt.Lce), h->owned);
+    h->dLce_blk = upload(h->al, s, nonzero_blocks(h->rt.Lce, h->rt.ne, 4 * h->q, h->q), h->owned);
     h->dD_df = (float2*)upload(h->al, s, split_df(h->rt.D), h->owned);
     h->dD2_df = (float2*)upload(h->al, s, split_df(h->rt.D2), h->owned);
     h->dDceL = upload(h->al, s, h->rt.DceL, h->owned);
@@ -2596,7 +2627,7 @@ int hps_build(const hps_tree* tree, const double* coeffs, int p, const hps_opts*
       delete h;
       return fail(HPS_ERR_SINGULAR, "pivot breakdown in the elimination of box " + std::to_string(box));
     }
-    if (o.precision == HPS_MIXED) calibrate_mixed(h, s);
+    if (o.precision == HPS_MIXED) calibrate_mixed(h, tree, s);
   } catch (const CudaError& e) {
     delete h;
     return fail(e.code, e.msg);

@@ -330,6 +330,9 @@ struct ResidualArgs {
   // the same tables as unevaluated float pairs (hi, lo) for the double-float kernels
   const float2* Lloc_df; const float2* Lce_df;
   const float2* D_df; const float2* D2_df;
+  // per exterior node k (row of L_ce,ge): the indices of the edge blocks (q columns each)
+  // holding the row's nonzeros, -1 padded ([ne][4]); the other blocks are exactly zero
+  const int* Lce_blk;
 };
 // Residual r = g - A u, leaf fluxes and u_ce = L_ce,ge u_ge, in double-float arithmetic.
 void launch_leaf_residual_df(const ResidualArgs& a, const int* leaf_edges, const int* ce, const double* ug, const double* g, double* uc,
