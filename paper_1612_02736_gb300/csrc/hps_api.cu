@@ -104,19 +104,34 @@ std::vector<float> split_df(const std::vector<double>& v) {
   return o;
 }
 
-// For each row of a rows x (4 q) matrix (row-major): the indices of its q-column blocks
-// that hold a nonzero, -1 padded to 4 per row.
-std::vector<int> nonzero_blocks(const std::vector<double>& m, int rows, int cols, int q) {
-  std::vector<int> out((size_t)rows * 4, -1);
+// Compact row storage of a rows x (4 q) matrix (row-major) whose rows are nonzero on a few
+// of their four q-column blocks: blk (4 per row, -1 padded) the indices of the blocks
+// holding a nonzero, off (rows + 1) the start of each row's stored blocks in vals, vals the
+// blocks' entries as double-float pairs.
+struct BlockRows {
+  std::vector<int> blk, off;
+  std::vector<float> vals;
+};
+BlockRows block_rows(const std::vector<double>& m, int rows, int q) {
+  const int cols = 4 * q;
+  BlockRows br;
+  br.blk.assign((size_t)rows * 4, -1);
+  br.off.assign((size_t)rows + 1, 0);
+  std::vector<double> kept;
   for (int r = 0; r < rows; ++r) {
     int n = 0;
-    for (int b = 0; b < cols / q; ++b) {
+    for (int b = 0; b < 4; ++b) {
       bool nz = false;
       for (int j = b * q; j < b * q + q; ++j) nz = nz || m[(size_t)r * cols + j] != 0.0;
-      if (nz) out[(size_t)r * 4 + n++] = b;
+      if (!nz) continue;
+      br.blk[(size_t)r * 4 + n++] = b;
+      for (int j = b * q; j < b * q + q; ++j) kept.push_back(m[(size_t)r * cols + j]);
     }
+    br.off[r + 1] = (int)kept.size();
   }
-  return out;
+  br.vals = split_df(kept);
+  if (br.vals.empty()) br.vals.assign(2, 0.f);
+  return br;
 }
 
 template <typename T>
@@ -300,8 +315,9 @@ struct hps_handle {
   int p = 0, q = 0, m = 0, nq = 0, ne = 0, pp = 0, n_leaf = 0, n_bdry = 0;
   // tables
   double *dD = nullptr, *dD2 = nullptr, *dLs = nullptr, *dDLs = nullptr, *dLloc = nullptr, *dDceL = nullptr;
-  float2 *dLloc_df = nullptr, *dLce_df = nullptr, *dD_df = nullptr, *dD2_df = nullptr;
-  int* dLce_blk = nullptr;
+  float2 *dLloc_df = nullptr, *dLce_c = nullptr, *dD_df = nullptr, *dD2_df = nullptr;
+  int *dLce_blk = nullptr, *dLce_off = nullptr;
+  int n_lce = 0;
   double* dhxy = nullptr;
   int* didx = nullptr;
   int* d_leaf_edges = nullptr;
@@ -1860,7 +1876,9 @@ ResidualArgs residual_args(const hps_handle* h, const double* coeffs) {
   ra.Lloc = h->dLloc;
   ra.ci = h->didx + h->off_ci;
   ra.Lloc_df = h->dLloc_df;
-  ra.Lce_df = h->dLce_df;
+  ra.Lce_c = h->dLce_c;
+  ra.Lce_off = h->dLce_off;
+  ra.n_lce = h->n_lce;
   ra.D_df = h->dD_df;
   ra.D2_df = h->dD2_df;
   ra.Lce_blk = h->dLce_blk;
@@ -2592,8 +2610,13 @@ int hps_build(const hps_tree* tree, const double* coeffs, int p, const hps_opts*
     h->dDLs = upload(h->al, s, h->rt.DLs, h->owned);
     h->dLloc = upload(h->al, s, h->rt.Lloc, h->owned);
     h->dLloc_df = (float2*)upload(h->al, s, split_df(h->rt.Lloc), h->owned);
-    h->dLce_df = (float2*)upload(h->al, s, split_df(h->rt.Lce), h->owned);
-    h->dLce_blk = upload(h->al, s, nonzero_blocks(h->rt.Lce, h->rt.ne, 4 * h->q, h->q), h->owned);
+    {
+      const BlockRows lb = block_rows(h->rt.Lce, h->rt.ne, h->q);
+      h->dLce_c = (float2*)upload(h->al, s, lb.vals, h->owned);
+      h->dLce_blk = upload(h->al, s, lb.blk, h->owned);
+      h->dLce_off = upload(h->al, s, lb.off, h->owned);
+      h->n_lce = lb.off.back();
+    }
     h->dD_df = (float2*)upload(h->al, s, split_df(h->rt.D), h->owned);
     h->dD2_df = (float2*)upload(h->al, s, split_df(h->rt.D2), h->owned);
     h->dDceL = upload(h->al, s, h->rt.DceL, h->owned);

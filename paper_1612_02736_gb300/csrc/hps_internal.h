@@ -328,11 +328,15 @@ struct ResidualArgs {
   const double* D; const double* D2; const double* Lloc;
   const int* ci;
   // the same tables as unevaluated float pairs (hi, lo) for the double-float kernels
-  const float2* Lloc_df; const float2* Lce_df;
+  const float2* Lloc_df;
   const float2* D_df; const float2* D2_df;
-  // per exterior node k (row of L_ce,ge): the indices of the edge blocks (q columns each)
-  // holding the row's nonzeros, -1 padded ([ne][4]); the other blocks are exactly zero
+  // L_ce,ge by rows of exterior nodes k, only the edge blocks (q columns each) that hold the
+  // row's nonzeros (the others are exactly zero): Lce_blk [ne][4] their indices (-1 padded),
+  // Lce_off [ne + 1] the start of row k's stored blocks in Lce_c (double-float pairs)
+  const float2* Lce_c;
   const int* Lce_blk;
+  const int* Lce_off;
+  int n_lce;  // entries of Lce_c
 };
 // Residual r = g - A u, leaf fluxes and u_ce = L_ce,ge u_ge, in double-float arithmetic.
 void launch_leaf_residual_df(const ResidualArgs& a, const int* leaf_edges, const int* ce, const double* ug, const double* g, double* uc,

@@ -26,6 +26,49 @@ __device__ __forceinline__ df df_from(double x) {
 }
 __device__ __forceinline__ double df_to(df a) { return (double)a.hi + (double)a.lo; }
 
+// The same splitting and joining with integer operations (GB300's FP64 pipe, which also
+// runs the FP64 <-> FP32 conversions, does 2 operations per clock per SM; the integer pipe
+// 64): hi is the significand rounded to 24 bits (half up), lo the exact remainder scaled by
+// a power of two, for exponents where both are normal floats; zero, tiny, huge and
+// non-finite values take the FP64 form above.
+__device__ __forceinline__ df df_from_i(double x) {
+  const long long b = __double_as_longlong(x);
+  const int E = (int)((b >> 52) & 0x7FF);
+  if (E < 949 || E > 1150) return df_from(x);
+  const unsigned long long m = ((unsigned long long)b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const unsigned long long mh = (m + (1ull << 28)) >> 29;           // 2^23 .. 2^24
+  const int rem = (int)((long long)m - (long long)(mh << 29));      // |rem| <= 2^28
+  const unsigned sgn = (unsigned)((unsigned long long)b >> 32) & 0x80000000u;
+  const unsigned hb = sgn | (((unsigned)(E - 896) << 23) + (unsigned)mh - (1u << 23));
+  const float lo = __int2float_rn(rem) * __int_as_float((E - 948) << 23);
+  return {__uint_as_float(hb), __uint_as_float(__float_as_uint(lo) ^ sgn)};
+}
+__device__ __forceinline__ double df_to_i(float hi, float lo) {
+  const unsigned hb = __float_as_uint(hi), lb = __float_as_uint(lo);
+  const int eh = (int)((hb >> 23) & 0xFF), el = (int)((lb >> 23) & 0xFF);
+  if (eh < 40 || eh > 250) return (double)hi + (double)lo;
+  long long t = (long long)((hb & 0x7FFFFF) | 0x800000) << 29;     // hi = t 2^(eh - 179)
+  if (el > 0) {                                                      // lo in the same units
+    const long long ml = (long long)((lb & 0x7FFFFF) | 0x800000);
+    const int sh = el - eh + 29;
+    long long v = 0;
+    if (sh >= 0) v = ml << min(sh, 30);
+    else if (sh > -40) v = (ml + (1ll << (-sh - 1))) >> (-sh);
+    t += ((lb ^ hb) >> 31) ? -v : v;
+  }
+  int e = eh + 896;                                                  // biased exponent for t in [2^52, 2^53)
+  if (t >= (1ll << 53)) {
+    t = (t + 1) >> 1;
+    ++e;
+  } else if (t < (1ll << 52)) {
+    t <<= 1;
+    --e;
+  }
+  const unsigned long long bits =
+      ((unsigned long long)(hb >> 31) << 63) | ((unsigned long long)e << 52) | ((unsigned long long)t & 0xFFFFFFFFFFFFFull);
+  return __longlong_as_double((long long)bits);
+}
+
 // Knuth's TwoSum: s + e == a + b exactly.
 __device__ __forceinline__ df two_sum(float a, float b) {
   const float s = __fadd_rn(a, b);
@@ -109,13 +152,18 @@ struct dfc {
   f2 h, l, nh;
 };
 __device__ __forceinline__ dfc dfc_of(float hi, float lo) { return {f2_pack(hi, hi), f2_pack(lo, lo), f2_pack(-hi, -hi)}; }
-// from a table entry {hi, hi, lo, lo}
-__device__ __forceinline__ dfc dfc_of4(float4 v) {
-  const f2 h = f2_pack(v.x, v.y);
-  return {h, f2_pack(v.z, v.w), f2_mul(h, f2_pack(-1.f, -1.f))};
+// Shared-memory entries of a pair or of a broadcast constant are 16 bytes {h, l} read as two
+// 64-bit halves in one 128-bit load, straight into the packed registers.
+using q2 = ulonglong2;
+__device__ __forceinline__ df2 df2_ld(const q2* p) {
+  const q2 v = *p;
+  return {v.x, v.y};
 }
-__device__ __forceinline__ df2 df2_of4(float4 v) { return {f2_pack(v.x, v.y), f2_pack(v.z, v.w)}; }
-__device__ __forceinline__ float4 df2_to4(df2 v) { return make_float4(f2_lo(v.h), f2_hi(v.h), f2_lo(v.l), f2_hi(v.l)); }
+__device__ __forceinline__ void df2_st(q2* p, df2 v) { *p = make_ulonglong2(v.h, v.l); }
+__device__ __forceinline__ dfc dfc_ld(const q2* p) {
+  const q2 v = *p;
+  return {v.x, v.y, f2_mul(v.x, f2_pack(-1.f, -1.f))};
+}
 
 // acc += a b, the compensated dot product of Ogita, Rump and Oishi (Dot2): the product's
 // rounding error (TwoProduct by FMA) and the cross terms of the low parts, and the rounding
@@ -150,14 +198,8 @@ __device__ __forceinline__ df2 df2_mul(const dfc& a, const df2& b) {
   const f2 s = f2_sub(e, np);  // p + e
   return {s, f2_sub(e, f2_add(s, np))};
 }
-// the pair's values of a row of FP64 data (two consecutive right-hand sides, the second
-// zero when absent)
-__device__ __forceinline__ df2 df2_from(double x0, double x1) {
-  const df a = df_from(x0), b = df_from(x1);
-  return {f2_pack(a.hi, b.hi), f2_pack(a.lo, b.lo)};
-}
-__device__ __forceinline__ double df2_to0(df2 v) { return (double)f2_lo(v.h) + (double)f2_lo(v.l); }
-__device__ __forceinline__ double df2_to1(df2 v) { return (double)f2_hi(v.h) + (double)f2_hi(v.l); }
+__device__ __forceinline__ double df2_to0(df2 v) { return df_to_i(f2_lo(v.h), f2_lo(v.l)); }
+__device__ __forceinline__ double df2_to1(df2 v) { return df_to_i(f2_hi(v.h), f2_hi(v.l)); }
 
 constexpr int RC = 4;  // right-hand sides per pass of the operator-application kernel
 
@@ -167,35 +209,47 @@ constexpr int RC = 4;  // right-hand sides per pass of the operator-application 
 // products.  Per pass: u_ce = L_ce,ge u_ge (Eq. alpine2p5, written back to u; only the edge
 // blocks of L_ce,ge that hold a row's nonzeros are summed), the first derivatives at every
 // node, then r = g - A u at the interior nodes and the leaf fluxes v = D_ge,c u (Sec. 3.4).
+// The kernel is bound by the shared-memory / L1 data pipe, so rows of u, g and r move with
+// four lanes per 32-byte row segment (one sector), r is collected in shared memory and
+// stored coalesced, and with stage_l the small tables L_ce,ge and L_loc are read from
+// shared copies.
 template <int NP>
-__global__ void __launch_bounds__(256) leaf_residual_df_kernel(
+__global__ void __launch_bounds__(256, 3) leaf_residual_df_kernel(
     ResidualArgs a, const int* __restrict__ leaf_edges, const int* __restrict__ ce,
     const double* __restrict__ ug, const double* __restrict__ g, double* __restrict__ uc, double* __restrict__ r_out,
-    double* __restrict__ vflux, int nrhs) {
+    double* __restrict__ vflux, int nrhs, int stage_l) {
   constexpr int NRC = 2 * NP;
   const int lf = blockIdx.x;
   const int p = a.p, q = a.q, pp = p * p, nq = 4 * q, ne = 4 * (p - 1);
   extern __shared__ __align__(16) unsigned char smraw[];
-  float4* sD = reinterpret_cast<float4*>(smraw);  // {hi, hi, lo, lo} of D[i][k] at i p + k
-  float4* sD2 = sD + pp;
-  float4* sDt = sD2 + pp;                          // transposed (D[i][k] at k p + i): lanes
-  float4* sD2t = sDt + pp;                         // that differ in ix read consecutive entries
-  // pair-major (pair pr of node n at pr pp + n): lanes that differ in ix read consecutive
-  // 16-byte entries
-  float4* us = sD2t + pp;                          // NP x pp pairs {h0, h1, l0, l1}
-  float4* uxs = us + pp * NP;
-  float4* uys = uxs + pp * NP;
-  float4* ugs = uys + pp * NP;                     // NP x nq
-  df* cf = reinterpret_cast<df*>(ugs + nq * NP);   // 6 pp: -c11, -2 c12, -c22, c1, c2, c of this leaf
+  // {hi, hi, lo, lo} of D[i][k] and D2[i][k] at k p + i: lanes that differ in i read
+  // consecutive entries, lanes with equal i one entry (broadcast)
+  q2* sDt = reinterpret_cast<q2*>(smraw);
+  q2* sD2t = sDt + pp;
+  // pair-major, node (ix, iy) of pair pr at pr PS + iy (p + 1) + ix (rows padded by one entry,
+  // so that the two rows a warp spans fall on different banks), pairs {h0, h1, l0, l1}
+  const int PS = pp + p;
+  q2* us = sD2t + pp;
+  q2* uxs = us + PS * NP;
+  q2* uys = uxs + PS * NP;
+  q2* gs = uys + PS * NP;
+  q2* ugs = gs + PS * NP;                                  // NP x nq
+  double* rs = reinterpret_cast<double*>(ugs + nq * NP);   // pp x NRC: r of the pass
+  df* cf = reinterpret_cast<df*>(rs + pp * NRC);           // 6 pp: -c11, -2 c12, -c22, c1, c2, c
+  float2* sL = reinterpret_cast<float2*>(cf + 6 * pp);     // staged L_ce,ge blocks, then L_loc
+  const int nlc = stage_l ? a.n_lce : 0;
+  const float2* Lc = stage_l ? sL : a.Lce_c;
+  const float2* Ll = stage_l ? sL + ((nlc + 1) & ~1) : a.Lloc_df;
   const int tid = threadIdx.x, bs = blockDim.x;
   for (int e = tid; e < pp; e += bs) {
     const float2 d1 = __ldg(a.D_df + e), d2 = __ldg(a.D2_df + e);
     const int i = e / p, k = e - (e / p) * p;
-    const float4 v1 = make_float4(d1.x, d1.x, d1.y, d1.y), v2 = make_float4(d2.x, d2.x, d2.y, d2.y);
-    sD[e] = v1;
-    sD2[e] = v2;
-    sDt[k * p + i] = v1;
-    sD2t[k * p + i] = v2;
+    sDt[k * p + i] = make_ulonglong2(f2_pack(d1.x, d1.x), f2_pack(d1.y, d1.y));
+    sD2t[k * p + i] = make_ulonglong2(f2_pack(d2.x, d2.x), f2_pack(d2.y, d2.y));
+  }
+  if (stage_l) {
+    for (int e = tid; e < nlc; e += bs) sL[e] = __ldg(a.Lce_c + e);
+    for (int e = tid; e < q * p; e += bs) sL[((nlc + 1) & ~1) + e] = __ldg(a.Lloc_df + e);
   }
   const long long st = a.n_leaf * pp;
   for (int e = tid; e < 6 * pp; e += bs) {
@@ -209,48 +263,52 @@ __global__ void __launch_bounds__(256) leaf_residual_df_kernel(
   const dfc sx = dfc_of(sx1.hi, sx1.lo), sy = dfc_of(sy1.hi, sy1.lo);
   const dfc sxx = dfc_of(sxx1.hi, sxx1.lo), syy = dfc_of(syy1.hi, syy1.lo);
   const long long lbase = (long long)lf * pp * nrhs;
-  // the pair of FP64 values of row `row` at right-hand sides r, r + 1 (0 past nrhs)
-  auto pair_of = [&](const double* base, long long row, int r) {
-    const double x0 = r < nrhs ? base[row * nrhs + r] : 0.0;
-    const double x1 = r + 1 < nrhs ? base[row * nrhs + r + 1] : 0.0;
-    return df2_from(x0, x1);
-  };
-  auto store_pair = [&](double* base, long long row, int r, const df2& v) {
-    if (r < nrhs) base[row * nrhs + r] = df2_to0(v);
-    if (r + 1 < nrhs) base[row * nrhs + r + 1] = df2_to1(v);
+  // component rr of a pair-major entry: hi at rr & 1, lo at 2 + (rr & 1)
+  auto put = [](q2* arr, int idx, int rr, double x) {
+    float* f = reinterpret_cast<float*>(arr + idx);
+    const df v = df_from_i(x);
+    f[rr & 1] = v.hi;
+    f[2 + (rr & 1)] = v.lo;
   };
   for (int r0 = 0; r0 < nrhs; r0 += NRC) {
     __syncthreads();
-    for (int e = tid; e < nq * NP; e += bs) {
-      const int gq = e / NP, pr = e - (e / NP) * NP;
-      const int s = gq / q, k = gq - (gq / q) * q;
-      const int node = leaf_edges[4 * lf + s] * q + k;
-      ugs[pr * nq + gq] = df2_to4(pair_of(ug, node, r0 + 2 * pr));
+    // rows of u and g at this pass's right-hand sides, NRC consecutive lanes per row
+    for (int e = tid; e < pp * NRC; e += bs) {
+      const int n = e / NRC, rr = e - (e / NRC) * NRC;
+      const bool ok = r0 + rr < nrhs;
+      const long long at = lbase + (long long)n * nrhs + r0 + rr;
+      const int pn = (rr >> 1) * PS + n + n / p;
+      put(us, pn, rr, ok ? uc[at] : 0.0);
+      put(gs, pn, rr, ok ? g[at] : 0.0);
     }
-    for (int e = tid; e < pp * NP; e += bs) {
-      const int n = e / NP, pr = e - (e / NP) * NP;
-      us[pr * pp + n] = df2_to4(pair_of(uc + lbase, n, r0 + 2 * pr));
+    for (int e = tid; e < nq * NRC; e += bs) {
+      const int gq = e / NRC, rr = e - (e / NRC) * NRC;
+      const int s = gq / q, k = gq - (gq / q) * q;
+      const long long node = (long long)leaf_edges[4 * lf + s] * q + k;
+      put(ugs, (rr >> 1) * nq + gq, rr, r0 + rr < nrhs ? ug[node * nrhs + r0 + rr] : 0.0);
     }
     __syncthreads();
     // exterior values u_ce = L_ce,ge u_ge, written back in FP64
     for (int e = tid; e < ne * NP; e += bs) {
       const int k = e / NP, pr = e - (e / NP) * NP;
       df2 v = {0ull, 0ull};
-      const float2* Lrow = a.Lce_df + (long long)k * nq;
       const int4 blk = __ldg(reinterpret_cast<const int4*>(a.Lce_blk) + k);
-      const int bl[4] = {blk.x, blk.y, blk.z, blk.w};
+      const float2* Lrow = Lc + __ldg(a.Lce_off + k);
 #pragma unroll 1
       for (int b = 0; b < 4; ++b) {
-        if (bl[b] < 0) break;
-        for (int gq = bl[b] * q; gq < bl[b] * q + q; ++gq) {
-          const float2 l = __ldg(Lrow + gq);
-          dot2_acc(v, dfc_of(l.x, l.y), df2_of4(ugs[pr * nq + gq]));
+        const int cb = b == 0 ? blk.x : b == 1 ? blk.y : b == 2 ? blk.z : blk.w;
+        if (cb < 0) break;
+        for (int j = 0; j < q; ++j) {
+          const float2 l = Lrow[b * q + j];
+          dot2_acc(v, dfc_of(l.x, l.y), df2_ld(ugs + pr * nq + cb * q + j));
         }
       }
       v = df2_norm(v);
       const int n = ce[k];
-      us[pr * pp + n] = df2_to4(v);
-      store_pair(uc + lbase, n, r0 + 2 * pr, v);
+      df2_st(us + pr * PS + n + n / p, v);
+      const int r = r0 + 2 * pr;
+      if (r < nrhs) uc[lbase + (long long)n * nrhs + r] = df2_to0(v);
+      if (r + 1 < nrhs) uc[lbase + (long long)n * nrhs + r + 1] = df2_to1(v);
     }
     __syncthreads();
     // first derivatives at every node, all pairs per thread
@@ -260,19 +318,19 @@ __global__ void __launch_bounds__(256) leaf_residual_df_kernel(
 #pragma unroll
       for (int pr = 0; pr < NP; ++pr) vx[pr] = vy[pr] = df2{0ull, 0ull};
       for (int k = 0; k < p; ++k) {
-        const dfc dx = dfc_of4(sDt[k * p + ix]), dy = dfc_of4(sD[iy * p + k]);
-        const float4* ur = us + iy * p + k;
-        const float4* uc2 = us + k * p + ix;
+        const dfc dx = dfc_ld(sDt + k * p + ix), dy = dfc_ld(sDt + k * p + iy);
+        const q2* ur = us + iy * (p + 1) + k;
+        const q2* uc2 = us + k * (p + 1) + ix;
 #pragma unroll
         for (int pr = 0; pr < NP; ++pr) {
-          dot2_acc(vx[pr], dx, df2_of4(ur[pr * pp]));
-          dot2_acc(vy[pr], dy, df2_of4(uc2[pr * pp]));
+          dot2_acc(vx[pr], dx, df2_ld(ur + pr * PS));
+          dot2_acc(vy[pr], dy, df2_ld(uc2 + pr * PS));
         }
       }
 #pragma unroll
       for (int pr = 0; pr < NP; ++pr) {
-        uxs[pr * pp + n] = df2_to4(df2_mul(sx, df2_norm(vx[pr])));
-        uys[pr * pp + n] = df2_to4(df2_mul(sy, df2_norm(vy[pr])));
+        df2_st(uxs + pr * PS + iy * (p + 1) + ix, df2_mul(sx, df2_norm(vx[pr])));
+        df2_st(uys + pr * PS + iy * (p + 1) + ix, df2_mul(sy, df2_norm(vy[pr])));
       }
     }
     __syncthreads();
@@ -281,22 +339,23 @@ __global__ void __launch_bounds__(256) leaf_residual_df_kernel(
       const int ix = n % p, iy = n / p;
       const bool inner = ix > 0 && ix < p - 1 && iy > 0 && iy < p - 1;
       if (!inner) {
-        for (int rr = 0; rr < NRC && r0 + rr < nrhs; ++rr) r_out[lbase + (long long)n * nrhs + r0 + rr] = 0.0;
+#pragma unroll
+        for (int rr = 0; rr < NRC; ++rr) rs[n * NRC + rr] = 0.0;
         continue;
       }
       df2 xx[NP], yy[NP], xy[NP];
 #pragma unroll
       for (int pr = 0; pr < NP; ++pr) xx[pr] = yy[pr] = xy[pr] = df2{0ull, 0ull};
       for (int k = 0; k < p; ++k) {
-        const dfc d2x = dfc_of4(sD2t[k * p + ix]), d2y = dfc_of4(sD2[iy * p + k]), d1y = dfc_of4(sD[iy * p + k]);
-        const float4* ur = us + iy * p + k;
-        const float4* uc2 = us + k * p + ix;
-        const float4* xc = uxs + k * p + ix;
+        const dfc d2x = dfc_ld(sD2t + k * p + ix), d2y = dfc_ld(sD2t + k * p + iy), d1y = dfc_ld(sDt + k * p + iy);
+        const q2* ur = us + iy * (p + 1) + k;
+        const q2* uc2 = us + k * (p + 1) + ix;
+        const q2* xc = uxs + k * (p + 1) + ix;
 #pragma unroll
         for (int pr = 0; pr < NP; ++pr) {
-          dot2_acc(xx[pr], d2x, df2_of4(ur[pr * pp]));
-          dot2_acc(yy[pr], d2y, df2_of4(uc2[pr * pp]));
-          dot2_acc(xy[pr], d1y, df2_of4(xc[pr * pp]));
+          dot2_acc(xx[pr], d2x, df2_ld(ur + pr * PS));
+          dot2_acc(yy[pr], d2y, df2_ld(uc2 + pr * PS));
+          dot2_acc(xy[pr], d1y, df2_ld(xc + pr * PS));
         }
       }
       dfc c6[6];
@@ -309,16 +368,19 @@ __global__ void __launch_bounds__(256) leaf_residual_df_kernel(
         dot2_acc(Au, c6[0], df2_mul(sxx, df2_norm(xx[pr])));
         dot2_acc(Au, c6[1], df2_mul(sy, df2_norm(xy[pr])));
         dot2_acc(Au, c6[2], df2_mul(syy, df2_norm(yy[pr])));
-        dot2_acc(Au, c6[3], df2_of4(uxs[pr * pp + n]));
-        dot2_acc(Au, c6[4], df2_of4(uys[pr * pp + n]));
-        dot2_acc(Au, c6[5], df2_of4(us[pr * pp + n]));
+        const int pn = pr * PS + iy * (p + 1) + ix;
+        dot2_acc(Au, c6[3], df2_ld(uxs + pn));
+        dot2_acc(Au, c6[4], df2_ld(uys + pn));
+        dot2_acc(Au, c6[5], df2_ld(us + pn));
         Au = df2_norm(Au);
-        const df2 gg = pair_of(g + lbase, n, r0 + 2 * pr);
+        const df2 gg = df2_ld(gs + pn);
         // g - A u: TwoSum of the high parts plus the low parts
         const f2 sh = f2_sub(gg.h, Au.h);
         const f2 bb = f2_sub(sh, gg.h);
         const f2 t = f2_sub(f2_sub(gg.h, f2_sub(sh, bb)), f2_add(Au.h, bb));
-        store_pair(r_out + lbase, n, r0 + 2 * pr, df2_norm({sh, f2_add(t, f2_sub(gg.l, Au.l))}));
+        const df2 res = df2_norm({sh, f2_add(t, f2_sub(gg.l, Au.l))});
+        rs[n * NRC + 2 * pr] = df2_to0(res);
+        rs[n * NRC + 2 * pr + 1] = df2_to1(res);
       }
     }
     // leaf fluxes v = D_ge,c u (Sec. 3.4), taken from the last threads first (the interior
@@ -328,17 +390,25 @@ __global__ void __launch_bounds__(256) leaf_residual_df_kernel(
       const int s = gq / q, k = gq - (gq / q) * q;
       df2 v = {0ull, 0ull};
       for (int t = 0; t < p; ++t) {
-        float4 d;
+        const q2* d;
         switch (s) {
-          case 0: d = uys[pr * pp + 0 * p + t]; break;
-          case 1: d = uxs[pr * pp + t * p + (p - 1)]; break;
-          case 2: d = uys[pr * pp + (p - 1) * p + t]; break;
-          default: d = uxs[pr * pp + t * p + 0]; break;
+          case 0: d = uys + pr * PS + t; break;
+          case 1: d = uxs + pr * PS + t * (p + 1) + (p - 1); break;
+          case 2: d = uys + pr * PS + (p - 1) * (p + 1) + t; break;
+          default: d = uxs + pr * PS + t * (p + 1); break;
         }
-        const float2 l = __ldg(a.Lloc_df + k * p + t);
-        dot2_acc(v, dfc_of(l.x, l.y), df2_of4(d));
+        const float2 l = Ll[k * p + t];
+        dot2_acc(v, dfc_of(l.x, l.y), df2_ld(d));
       }
-      store_pair(vflux, (long long)lf * nq + gq, r0 + 2 * pr, df2_norm(v));
+      v = df2_norm(v);
+      const long long row = ((long long)lf * nq + gq) * nrhs + r0 + 2 * pr;
+      if (r0 + 2 * pr < nrhs) vflux[row] = df2_to0(v);
+      if (r0 + 2 * pr + 1 < nrhs) vflux[row + 1] = df2_to1(v);
+    }
+    __syncthreads();
+    for (int e = tid; e < pp * NRC; e += bs) {
+      const int n = e / NRC, rr = e - (e / NRC) * NRC;
+      if (r0 + rr < nrhs) r_out[lbase + (long long)n * nrhs + r0 + rr] = rs[e];
     }
   }
 }
@@ -510,11 +580,23 @@ void launch_coeff_grad(const ResidualArgs& a, const double* uc, const double* gb
   coeff_grad_df_kernel<<<(unsigned)a.n_leaf, 256, smem, s>>>(a, uc, gbar, grad, nrhs);
 }
 
+// Shared memory of the residual kernel: tables, pass buffers and coefficients, plus the
+// staged L tables when stage_l.
+static size_t residual_smem(const ResidualArgs& a, int np, int nlc, bool stage_l) {
+  const size_t pp = (size_t)a.p * a.p, nq = 4 * (size_t)a.q;
+  size_t b = (2 * pp + 4 * (pp + a.p) * np + nq * np) * sizeof(ulonglong2) + pp * 2 * np * sizeof(double) +
+             6 * pp * sizeof(df);
+  if (stage_l) b += (((size_t)nlc + 1) & ~(size_t)1) * sizeof(float2) + (size_t)a.q * a.p * sizeof(float2);
+  return b;
+}
+
 template <int NP>
 static void residual_launch(const ResidualArgs& a, const int* leaf_edges, const int* ce, const double* ug,
-                            const double* g, double* uc, double* r_out, double* vflux, int nrhs, cudaStream_t s) {
-  const int pp = a.p * a.p;
-  const size_t smem = (size_t)(4 * pp + 3 * pp * NP + 4 * a.q * NP) * sizeof(float4) + (size_t)6 * pp * sizeof(df);
+                            const double* g, double* uc, double* r_out, double* vflux, int nrhs, int nlc,
+                            cudaStream_t s) {
+  const size_t limit = 227 * 1024;
+  const bool stage_l = residual_smem(a, NP, nlc, true) <= limit;
+  const size_t smem = residual_smem(a, NP, nlc, stage_l);
   if (smem > 48 * 1024) {
     // the limit is a property of the device's context: raised once per device (the first
     // launch is never inside a stream capture: a handle's first solve runs directly)
@@ -528,14 +610,19 @@ static void residual_launch(const ResidualArgs& a, const int* leaf_edges, const 
       configured[dev] = smem;
     }
   }
-  leaf_residual_df_kernel<NP><<<(unsigned)a.n_leaf, 256, smem, s>>>(a, leaf_edges, ce, ug, g, uc, r_out, vflux, nrhs);
+  leaf_residual_df_kernel<NP><<<(unsigned)a.n_leaf, 256, smem, s>>>(a, leaf_edges, ce, ug, g, uc, r_out, vflux, nrhs,
+                                                                    stage_l ? 1 : 0);
 }
 
 void launch_leaf_residual_df(const ResidualArgs& a, const int* leaf_edges, const int* ce,
                              const double* ug, const double* g, double* uc, double* r_out, double* vflux, int nrhs,
                              cudaStream_t s) {
-  if (nrhs <= 2) residual_launch<1>(a, leaf_edges, ce, ug, g, uc, r_out, vflux, nrhs, s);
-  else residual_launch<2>(a, leaf_edges, ce, ug, g, uc, r_out, vflux, nrhs, s);
+  const int n_lce = a.n_lce;
+  // two pairs per pass unless the buffers then exceed the shared memory of a CTA
+  if (nrhs <= 2 || residual_smem(a, 2, n_lce, false) > 227 * 1024)
+    residual_launch<1>(a, leaf_edges, ce, ug, g, uc, r_out, vflux, nrhs, n_lce, s);
+  else
+    residual_launch<2>(a, leaf_edges, ce, ug, g, uc, r_out, vflux, nrhs, n_lce, s);
 }
 
 }  // namespace hps
