@@ -249,7 +249,8 @@ def solve_roofline(s, nrhs, ms, iters, hbm_gbs):
                         if nrhs <= 4 else "tensor-core FP64 digit products (9 digit planes per entry)")
     else:
         out["fp32_pipe_frac"] = out["tflops"] / FP32_PEAK_TFLOPS
-        out["bound"] = "hbm" if nrhs <= 16 else "fp32 pipe (SIMT products)"
+        out["bound"] = ("hbm" if nrhs <= 8 else
+                        "bf16 tensor-core piece products (3 pieces per FP32 entry) and the double-float residual")
     return out
 
 
