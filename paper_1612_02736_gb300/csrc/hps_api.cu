@@ -2134,17 +2134,29 @@ int solve_mixed(hps_handle* h, const double* f, const double* g, const double* r
 // correction, which differs between problems, so it is left to the first solve, which then
 // accepts as soon as the bound predicts convergence.  Best effort: a failure here leaves the
 // handle uncalibrated and reports nothing.
-void calibrate_mixed(hps_handle* h, const hps_tree* tree, cudaStream_t s) {
+void calibrate_mixed(hps_handle* h, cudaStream_t s) {
   const std::string saved = g_err;
   const long long nf = h->n_bdry, ng = (long long)h->n_leaf * h->pp;
   std::vector<void*> bufs;
   try {
+    // boundary data at the boundary Gaussian nodes (ascending id), from the leaves' edges
     std::vector<double> fh((size_t)std::max(nf, 1ll), 0.0);
-    int64_t cnt = 0;
-    if (nf > 0 && hps_nodes(tree, h->p, h->q, HPS_NODES_GAUSS_BOUNDARY, nullptr, &cnt) == HPS_OK && cnt == nf) {
-      std::vector<double> xy((size_t)2 * nf);
-      if (hps_nodes(tree, h->p, h->q, HPS_NODES_GAUSS_BOUNDARY, xy.data(), &cnt) == HPS_OK)
-        for (long long i = 0; i < nf; ++i) fh[i] = 1.0 + xy[2 * i] + 2.0 * xy[2 * i + 1];
+    {
+      const Tree& t = h->tree;
+      const int q = h->q;
+      std::vector<double> fall((size_t)t.n_edges * q, 0.0);
+      for (size_t lf = 0; lf < t.leaves.size(); ++lf) {
+        const Box& b = t.boxes[t.leaves[lf]];
+        for (int sd = 0; sd < 4; ++sd)
+          for (int k = 0; k < q; ++k) {
+            const double gx = b.x0 + 0.5 * (b.x1 - b.x0) * (h->rt.xg[k] + 1.0);
+            const double gy = b.y0 + 0.5 * (b.y1 - b.y0) * (h->rt.xg[k] + 1.0);
+            const double x = sd == 0 || sd == 2 ? gx : (sd == 1 ? b.x1 : b.x0);
+            const double y = sd == 1 || sd == 3 ? gy : (sd == 0 ? b.y0 : b.y1);
+            fall[(size_t)t.leaf_edges[4 * lf + sd] * q + k] = 1.0 + x + 2.0 * y;
+          }
+      }
+      for (long long i = 0; i < nf; ++i) fh[i] = fall[h->ns.boundary[i]];
     }
     double* f = (double*)h->al.get(fh.size() * sizeof(double), s);
     bufs.push_back(f);
@@ -2650,7 +2662,7 @@ int hps_build(const hps_tree* tree, const double* coeffs, int p, const hps_opts*
       delete h;
       return fail(HPS_ERR_SINGULAR, "pivot breakdown in the elimination of box " + std::to_string(box));
     }
-    if (o.precision == HPS_MIXED) calibrate_mixed(h, tree, s);
+    if (o.precision == HPS_MIXED) calibrate_mixed(h, s);
   } catch (const CudaError& e) {
     delete h;
     return fail(e.code, e.msg);
