@@ -71,6 +71,130 @@ template <> struct KeyOf<float> {
   static __device__ __forceinline__ float val(type k) { return __uint_as_float(k); }
 };
 
+// x rounded to FP32 with integer operations (significand rounded half up to 24 bits) for
+// exponents inside FP32's normal range; others take the FP64-pipe conversion.
+__device__ __forceinline__ float float_of(double x) {
+  const long long b = __double_as_longlong(x);
+  const int E = (int)((b >> 52) & 0x7FF);
+  if (E < 897 || E > 1150) return __double2float_rn(x);
+  const unsigned long long m = ((unsigned long long)b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const unsigned mh = (unsigned)((m + (1ull << 28)) >> 29);
+  const unsigned sgn = (unsigned)((unsigned long long)b >> 32) & 0x80000000u;
+  return __uint_as_float(sgn | (((unsigned)(E - 896) << 23) + mh - (1u << 23)));
+}
+
+// Panel of an FP64 elimination with the pivots chosen in FP32.  Partial pivoting only needs
+// the magnitudes of the updated panel entries to pick its rows, so the LU of the panel that
+// chooses them runs on the FP32 pipe (64 times GB300's FP64 pipe); the outputs the
+// elimination uses exactly, the pivot block's inverse Pinv and the breakdown test, come from
+// the chosen rows' FP64 values: the block (rows in pivot order) is factored without further
+// pivoting in FP64 and inverted.  A pivot chosen in FP32 is within a relative 1e-6 or so of
+// the FP64 choice's magnitude, so the growth of the elimination is that of partial pivoting.
+// (Matrices with a null-direction tolerance keep the FP64 panel: FP32 cannot resolve it.)
+__device__ __forceinline__ void gj_panel_f32_select(const GJDesc& md, double* __restrict__ M, int* __restrict__ pm,
+                                                    double* __restrict__ pinv_out, int c0, int nb, int nrows,
+                                                    int* __restrict__ status, unsigned char* smraw) {
+  const int tid = threadIdx.x, bs = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = bs >> 5;
+  const int R = md.R, ldp = nb + 1;
+  float* P = reinterpret_cast<float*>(smraw);
+  int* pr = reinterpret_cast<int*>(P + (size_t)nrows * ldp);
+  __shared__ unsigned int red_v[32];
+  __shared__ int red_i[32];
+  __shared__ double colscale[NBMAX];
+  __shared__ double B[NBMAX][NBMAX + 1];
+  __shared__ int piv_row;
+  for (int i = tid; i < nrows; i += bs) pr[i] = pm[i];
+  __syncthreads();
+  for (int e = tid; e < nrows * nb; e += bs) {
+    const int i = e / nb, j = e - (e / nb) * nb;
+    P[i * ldp + j] = float_of(M[(long long)pr[i] * R + c0 + j]);
+  }
+  __syncthreads();
+  // column scales for the breakdown test (the largest |P_ij| of the column)
+  for (int j = warp; j < nb; j += nwarp) {
+    unsigned int mx = 0;
+    for (int i = lane; i < nrows; i += 32) mx = max(mx, __float_as_uint(P[i * ldp + j]) & 0x7FFFFFFFu);
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) colscale[j] = (double)__uint_as_float(mx);
+  }
+  for (int j = 0; j < nb; ++j) {
+    // pivot: the largest |P_ij|, i >= j, the first row among equals
+    unsigned int best = 0;
+    int bi = nrows;
+    for (int i = j + tid; i < nrows; i += bs) {
+      const unsigned int v = __float_as_uint(P[i * ldp + j]) & 0x7FFFFFFFu;
+      if (bi == nrows || v > best) { best = v; bi = i; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned int ov = __shfl_down_sync(0xffffffffu, best, o);
+      const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+      if (oi < nrows && (bi == nrows || ov > best || (ov == best && oi < bi))) { best = ov; bi = oi; }
+    }
+    if (lane == 0) { red_v[warp] = best; red_i[warp] = bi; }
+    __syncthreads();
+    if (warp == 0) {
+      best = lane < nwarp ? red_v[lane] : 0u;
+      bi = lane < nwarp ? red_i[lane] : nrows;
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned int ov = __shfl_down_sync(0xffffffffu, best, o);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+        if (oi < nrows && (bi == nrows || ov > best || (ov == best && oi < bi))) { best = ov; bi = oi; }
+      }
+      if (lane == 0) {
+        const int ib = bi < nrows ? bi : j;
+        piv_row = ib;
+        const int t = pr[j]; pr[j] = pr[ib]; pr[ib] = t;
+      }
+    }
+    __syncthreads();
+    const int r = piv_row;
+    if (r != j && tid < nb) {
+      const float t = P[j * ldp + tid]; P[j * ldp + tid] = P[r * ldp + tid]; P[r * ldp + tid] = t;
+    }
+    __syncthreads();
+    const float pv = P[j * ldp + j];
+    const float inv = pv != 0.f ? 1.f / pv : 0.f;
+    for (int i = j + 1 + tid; i < nrows; i += bs) {
+      const float l = P[i * ldp + j] * inv;
+      P[i * ldp + j] = l;
+      for (int c = j + 1; c < nb; ++c) P[i * ldp + c] = fmaf(-l, P[j * ldp + c], P[i * ldp + c]);
+    }
+    __syncthreads();
+  }
+  // the pivot block in FP64 (rows in pivot order), inverted in place by Gauss-Jordan
+  // elimination without further pivoting, one thread per entry; its pivots are those of the
+  // block's LU, tested against 64 eps of their column's scale
+  __shared__ double dinv;
+  for (int e = tid; e < nb * nb; e += bs) {
+    const int t = e / nb, c = e - (e / nb) * nb;
+    B[t][c] = M[(long long)pr[t] * R + c0 + c];
+  }
+  __syncthreads();
+  const int bi_ = tid / nb, bc_ = tid - (tid / nb) * nb;
+  for (int k = 0; k < nb; ++k) {
+    if (tid == 0) {
+      const double pvk = B[k][k];
+      if (!(fabs(pvk) > 64.0 * DBL_EPSILON * colscale[k]) && status) atomicCAS(status, 0, md.box + 1);
+      dinv = pvk != 0.0 ? 1.0 / pvk : 0.0;
+    }
+    __syncthreads();
+    double v = 0.0;
+    if (tid < nb * nb) {
+      const double di = dinv;
+      if (bi_ == k) v = bc_ == k ? di : B[k][bc_] * di;
+      else v = bc_ == k ? -B[bi_][k] * di : B[bi_][bc_] - B[bi_][k] * (B[k][bc_] * di);
+    }
+    __syncthreads();
+    if (tid < nb * nb) B[bi_][bc_] = v;
+    __syncthreads();
+  }
+  for (int e = tid; e < nb * nb; e += bs) {
+    const int k = e / nb, t = e - (e / nb) * nb;
+    pinv_out[k * NBMAX + t] = B[k][t];
+  }
+  for (int i = tid; i < nrows; i += bs) pm[i] = pr[i];
+}
+
 template <typename T>
 __global__ void __launch_bounds__(1024) gj_panel_kernel(const GJDesc* __restrict__ d,
                                                        T* __restrict__ work, int* __restrict__ perm,
@@ -83,6 +207,13 @@ __global__ void __launch_bounds__(1024) gj_panel_kernel(const GJDesc* __restrict
   const int nrows = md.K - c0;
   const int tid = threadIdx.x, bs = blockDim.x;
   extern __shared__ __align__(16) unsigned char smraw[];
+  if constexpr (std::is_same<T, double>::value) {
+    if (!(md.null_tol > 0.f && md.null_scale)) {
+      gj_panel_f32_select(md, work + md.off, perm + md.perm_off + c0, pinv + (long long)blockIdx.x * NBMAX * NBMAX,
+                          c0, nb, nrows, status, smraw);
+      return;
+    }
+  }
   // the panel, nrows x nb with row pitch nb + 1 (odd): a warp walking down a column hits
   // distinct banks
   const int ldp = nb + 1;
