@@ -1383,10 +1383,23 @@ void build_stage(hps_handle* h, const double* coeffs, cudaStream_t s) {
     return p;
   };
   try {
-    h->ops64 = (double*)h->al.get(h->ops_elems * sizeof(double), s);
-    h->owned.push_back({h->ops64, (size_t)h->ops_elems * sizeof(double)});
-    CK(cudaMemcpyAsync(h->ops64 + h->lce_base, h->rt.Lce.data(), h->rt.Lce.size() * sizeof(double),
-                       cudaMemcpyHostToDevice, s));
+    // the operator store: FP64, or for HPS_MIXED FP32 only (its sweeps read nothing else),
+    // written by the extractions directly
+    const bool mixed = h->opts.precision == HPS_MIXED;
+    const size_t es = mixed ? sizeof(float) : sizeof(double);
+    if (mixed) {
+      h->ops32 = (float*)h->al.get(h->ops_elems * sizeof(float), s);
+      h->owned.push_back({h->ops32, (size_t)h->ops_elems * sizeof(float)});
+      const std::vector<float> lce32(h->rt.Lce.begin(), h->rt.Lce.end());
+      CK(cudaMemcpyAsync(h->ops32 + h->lce_base, lce32.data(), lce32.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+      CK(cudaStreamSynchronize(s));  // lce32 is a host temporary
+    } else {
+      h->ops64 = (double*)h->al.get(h->ops_elems * sizeof(double), s);
+      h->owned.push_back({h->ops64, (size_t)h->ops_elems * sizeof(double)});
+      CK(cudaMemcpyAsync(h->ops64 + h->lce_base, h->rt.Lce.data(), h->rt.Lce.size() * sizeof(double),
+                         cudaMemcpyHostToDevice, s));
+    }
+    unsigned char* opsb = mixed ? (unsigned char*)h->ops32 : (unsigned char*)h->ops64;
     for (size_t b = 0; b < h->tree.boxes.size(); ++b) {
       const Coarsen& co = h->ns.co[b];
       if (!co.active) continue;
@@ -1433,13 +1446,16 @@ void build_stage(hps_handle* h, const double* coeffs, cudaStream_t s) {
       elim(pick_nb(h, "leaf", sizeof(double), rk, n, s, elim));
       ExtractDst dst{};
       const long long gl0 = h->gl_base + (long long)l0 * m * R;
-      dst.TL = h->ops64 + gl0; dst.TL_off_stride = (long long)m * R; dst.TL_ld = R;
-      dst.TR = h->ops64 + gl0 + m; dst.TR_off_stride = (long long)m * R; dst.TR_ld = R;
-      dst.BL = h->ops64 + h->h_base + (long long)l0 * nq * m; dst.BL_off_stride = (long long)nq * m; dst.BL_ld = m;
+      dst.TL = opsb + gl0 * es; dst.TL_off_stride = (long long)m * R; dst.TL_ld = R;
+      dst.TR = opsb + (gl0 + m) * es; dst.TR_off_stride = (long long)m * R; dst.TR_ld = R;
+      dst.BL = opsb + (h->h_base + (long long)l0 * nq * m) * es; dst.BL_off_stride = (long long)nq * m; dst.BL_ld = m;
       if (h->econ) dst.TL = dst.TR = dst.BL = nullptr;  // only T is kept; F, S, H are recomputed
       dst.BR = tstore + toff[h->tree.leaves[l0]]; dst.BR_off_stride = (long long)nq * nq; dst.BR_ld = nq;
       dst.sTL = 1.0; dst.sTR = -1.0; dst.sBL = -1.0;
-      TIMED("gj_extract_f64", 0, (double)n * per_leaf * 8, launch_gj_extract<double, double>(dgd, n, R, work, perm, dst, s));
+      if (mixed)
+        TIMED("gj_extract_f64", 0, (double)n * per_leaf * 8, launch_gj_extract<double, float>(dgd, n, R, work, perm, dst, s));
+      else
+        TIMED("gj_extract_f64", 0, (double)n * per_leaf * 8, launch_gj_extract<double, double>(dgd, n, R, work, perm, dst, s));
       CKL();
     }
     if (h->econ) {  // buffers for recomputing one chunk of leaves during the sweeps
@@ -1477,9 +1493,9 @@ void build_stage(hps_handle* h, const double* coeffs, cudaStream_t s) {
       }
       const double wbytes = (double)lv.work_elems * (lv.fp64 ? 8 : 4);
       ExtractDst dst{};
-      dst.TL = h->ops64; dst.TL_ld = 0; dst.TL_off = lv.off_tl;
-      dst.TR = h->ops64; dst.TR_off = lv.off_tr;
-      dst.BL = h->ops64; dst.BL_off = lv.off_bl;
+      dst.TL = opsb; dst.TL_ld = 0; dst.TL_off = lv.off_tl;
+      dst.TR = opsb; dst.TR_off = lv.off_tr;
+      dst.BL = opsb; dst.BL_off = lv.off_bl;
       dst.BR = tstore; dst.BR_off = lv.off_br;
       dst.sTL = 1.0; dst.sTR = 1.0; dst.sBL = 1.0;
       dst.ld_from_desc = 1;  // X, C X: ld k3; S, T_tau: ld k12
@@ -1494,7 +1510,10 @@ void build_stage(hps_handle* h, const double* coeffs, cudaStream_t s) {
           run_gj<double>(lv.gj, nmat, lv.maxR, lv.maxK, w, pm, pi, pr, h->d_status, rk, "merge", s, nb, lv.mstride);
         };
         elim(pick_nb(h, "merge", sizeof(double), rk, nmat, s, elim));
-        TIMED("gj_extract_f64", 0, wbytes, launch_gj_extract<double, double>(lv.gj, nmat, lv.maxR, w, pm, dst, s));
+        if (mixed)
+          TIMED("gj_extract_f64", 0, wbytes, launch_gj_extract<double, float>(lv.gj, nmat, lv.maxR, w, pm, dst, s));
+        else
+          TIMED("gj_extract_f64", 0, wbytes, launch_gj_extract<double, double>(lv.gj, nmat, lv.maxR, w, pm, dst, s));
         CKL();
       } else {
         float* w = (float*)get((size_t)lv.work_elems * sizeof(float));
@@ -1507,7 +1526,7 @@ void build_stage(hps_handle* h, const double* coeffs, cudaStream_t s) {
           run_gj<float>(lv.gj, nmat, lv.maxR, lv.maxK, w, pm, pi, pr, h->d_status, rk, "merge", s, nb);
         };
         elim(pick_nb(h, "merge", sizeof(float), rk, nmat, s, elim));
-        TIMED("gj_extract_f32", 0, wbytes, launch_gj_extract<float, double>(lv.gj, nmat, lv.maxR, w, pm, dst, s));
+        TIMED("gj_extract_f32", 0, wbytes, launch_gj_extract<float, float>(lv.gj, nmat, lv.maxR, w, pm, dst, s));
         CKL();
       }
       if (lv.ntp > 0) {  // refined parents: T_new = P_down T P_up (Sec. 6.3)
@@ -1524,12 +1543,7 @@ void build_stage(hps_handle* h, const double* coeffs, cudaStream_t s) {
       }
     }
     if (h->bc.on) build_root_bc(h, tstore, s, get);
-    if (h->opts.precision == HPS_MIXED) {
-      h->ops32 = (float*)h->al.get(h->ops_elems * sizeof(float), s);
-      h->owned.push_back({h->ops32, (size_t)h->ops_elems * sizeof(float)});
-      TIMED("convert_ops", 0, (double)h->ops_elems * 12, launch_convert<double, float>(h->ops64, h->ops32, h->ops_elems, 1.0, s));
-      CKL();
-    }
+
   } catch (...) {
     for (void* p : tmp) h->al.put(p, s);
     throw;

@@ -172,10 +172,10 @@ void launch_gj_update(const GJDesc* d, int nmat, int maxR, int maxRows, T* work,
 //   BR[r][c] =       M[K + r][K + c]
 // Destinations are per matrix: base + b * stride with the given leading dimensions.
 struct ExtractDst {
-  void* TL; long long TL_off_stride; int TL_ld;   // element type given by the launcher
+  void* TL; long long TL_off_stride; int TL_ld;   // TL, TR, BL: element type given by the launcher
   void* TR; long long TR_off_stride; int TR_ld;
   void* BL; long long BL_off_stride; int BL_ld;
-  void* BR; long long BR_off_stride; int BR_ld;
+  void* BR; long long BR_off_stride; int BR_ld;   // FP64
   double sTL, sTR, sBL;
   const long long* TL_off;   // optional per-matrix offsets (override b * stride) or null
   const long long* TR_off;

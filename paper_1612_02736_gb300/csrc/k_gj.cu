@@ -1334,7 +1334,8 @@ __global__ void __launch_bounds__(256) gj_extract_kernel(const GJDesc* __restric
   __syncthreads();
   const T* M = work + md.off;
   const long long total = (long long)md.rows * R;
-  TO* TL = (TO*)dst.TL; TO* TR = (TO*)dst.TR; TO* BL = (TO*)dst.BL; TO* BR = (TO*)dst.BR;
+  TO* TL = (TO*)dst.TL; TO* TR = (TO*)dst.TR; TO* BL = (TO*)dst.BL;
+  double* BR = (double*)dst.BR;  // the T store of the parents' merges stays FP64
   const long long tlo = dst.TL_off ? dst.TL_off[b] : (long long)b * dst.TL_off_stride;
   const long long tro = dst.TR_off ? dst.TR_off[b] : (long long)b * dst.TR_off_stride;
   const long long blo = dst.BL_off ? dst.BL_off[b] : (long long)b * dst.BL_off_stride;
@@ -1358,7 +1359,7 @@ __global__ void __launch_bounds__(256) gj_extract_kernel(const GJDesc* __restric
         for (int lc = lane; lc < K; lc += 32)
           BL[blo + (long long)(lr - K) * ldBL + lc] = (TO)(dst.sBL * (double)Mr[isig[lc]]);
       if (BR)
-        for (int lc = K + lane; lc < R; lc += 32) BR[bro + (long long)(lr - K) * ldBR + (lc - K)] = (TO)Mr[lc];
+        for (int lc = K + lane; lc < R; lc += 32) BR[bro + (long long)(lr - K) * ldBR + (lc - K)] = (double)Mr[lc];
     }
   }
 }
@@ -1501,5 +1502,7 @@ template void launch_gj_update<double>(const GJDesc*, int, int, int, double*, co
 template void launch_gj_update<float>(const GJDesc*, int, int, int, float*, const int*, float*, long long, int, int, cudaStream_t, int*, int, long long);
 template void launch_gj_extract<double, double>(const GJDesc*, int, int, const double*, const int*, const ExtractDst&, cudaStream_t);
 template void launch_gj_extract<float, double>(const GJDesc*, int, int, const float*, const int*, const ExtractDst&, cudaStream_t);
+template void launch_gj_extract<double, float>(const GJDesc*, int, int, const double*, const int*, const ExtractDst&, cudaStream_t);
+template void launch_gj_extract<float, float>(const GJDesc*, int, int, const float*, const int*, const ExtractDst&, cudaStream_t);
 
 }  // namespace hps
