@@ -266,7 +266,6 @@ struct Workspace {
   float* uc32 = nullptr;
   float* rho32 = nullptr;
   // refinement
-  double* r64 = nullptr;
   double* vflux = nullptr;
   double* rho64 = nullptr;
   double* scal = nullptr;
@@ -1595,7 +1594,6 @@ void ensure_ws(hps_handle* h, int nrhs, cudaStream_t s) {
     nw.g32 = (float*)get((size_t)nuc * sizeof(float));
     nw.uc32 = (float*)get((size_t)nuc * sizeof(float));
     nw.rho32 = (float*)get((size_t)ng * sizeof(float));
-    nw.r64 = (double*)get((size_t)nuc * sizeof(double));
     nw.vflux = (double*)get((size_t)h->n_leaf * h->nq * R * sizeof(double));
     nw.rho64 = (double*)get((size_t)ng * sizeof(double));
   } else {
@@ -1931,21 +1929,20 @@ void mixed_step(hps_handle* h, const double* g, const double* rho, double* u, in
   const double res_flops = 2.0 * ((double)h->n_leaf * nrhs) *
                            (5.0 * h->p * h->p * h->p + (double)h->ne * h->nq + (double)h->nq * h->p + 12.0 * h->m);
   TIMED("leaf_residual_df", res_flops, nuc * 32.0,
-        launch_leaf_residual_df(ra, h->d_leaf_edges, h->didx + h->off_ce, w.ug64, g, u, w.r64, w.vflux, nrhs, s));
+        launch_leaf_residual_df(ra, h->d_leaf_edges, h->didx + h->off_ce, w.ug64, g, u, w.g32, w.vflux, nrhs, s));
   CK(cudaMemsetAsync(w.rho64, 0, ng * sizeof(double), s));
   TIMED("jump_residual", 0, 0, launch_jump_residual(h->d_pairs, h->npairs, h->q, w.vflux, w.rho64, nrhs, s));
   if (rho) TIMED("axpy", 0, 0, launch_axpy_to_f64<double>(rho, w.rho64, ng, s));
   CKL();
-  TIMED("convert", 0, nuc * 12.0, launch_convert<double, float>(w.r64, w.g32, nuc, 1.0, s));
   CK(cudaMemsetAsync(w.ug32, 0, ng * sizeof(float), s));
   solve_pass<float, float>(h, h->ops32, nullptr, w.g32, w.rho64, w.uc32, w.ug32, w.V32, w.d32, w.P32, nrhs, s);
-  TIMED("axpy", 0, nuc * 20.0, launch_axpy_to_f64<float>(w.uc32, u, nuc, s));
-  TIMED("axpy", 0, ng * 20.0, launch_axpy_to_f64<float>(w.ug32, w.ug64, ng, s));
-  if (measure) {
+  if (measure) {  // the update and the norms of the correction and of u in one pass
     CK(cudaMemsetAsync(w.scal, 0, 2 * sizeof(double), s));
-    TIMED("absmax", 0, nuc * 4.0, launch_absmax_f32(w.uc32, nuc, w.scal, s));
-    TIMED("absmax", 0, nuc * 8.0, launch_absmax(u, nuc, w.scal + 1, s));
+    TIMED("axpy", 0, nuc * 20.0, launch_axpy_measure(w.uc32, u, nuc, w.scal, s));
+  } else {
+    TIMED("axpy", 0, nuc * 20.0, launch_axpy_to_f64<float>(w.uc32, u, nuc, s));
   }
+  TIMED("axpy", 0, ng * 20.0, launch_axpy_to_f64<float>(w.ug32, w.ug64, ng, s));
   CKL();
 }
 

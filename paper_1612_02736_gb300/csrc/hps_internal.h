@@ -320,6 +320,9 @@ template <typename TI, typename TO>
 void launch_convert(const TI* src, TO* dst, long long n, double scale, cudaStream_t s);
 template <typename TI>
 void launch_axpy_to_f64(const TI* x, double* y, long long n, cudaStream_t s);
+// y += x (x FP32), and max |x| into out[0], max |y| (after the update) into out[1] (atomic
+// maxima on the bit patterns of non-negative doubles; out preset to 0 by the caller).
+void launch_axpy_measure(const float* x, double* y, long long n, double* out, cudaStream_t s);
 
 // FP64 residual of the collocation system and leaf fluxes (mixed-precision refinement).
 struct ResidualArgs {
@@ -340,7 +343,7 @@ struct ResidualArgs {
 };
 // Residual r = g - A u, leaf fluxes and u_ce = L_ce,ge u_ge, in double-float arithmetic.
 void launch_leaf_residual_df(const ResidualArgs& a, const int* leaf_edges, const int* ce, const double* ug, const double* g, double* uc,
-                             double* r_out, double* vflux, int nrhs, cudaStream_t s);
+                             float* r_out, double* vflux, int nrhs, cudaStream_t s);  // r in FP32
 // y = alpha u + beta A u at leaf interior nodes, 0 at exterior nodes, double-float.
 void launch_leaf_apply_df(const ResidualArgs& a, const double* u, double alpha, double beta, double* out, int nrhs,
                           cudaStream_t s);

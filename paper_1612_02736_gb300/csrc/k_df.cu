@@ -216,7 +216,7 @@ constexpr int RC = 4;  // right-hand sides per pass of the operator-application 
 template <int NP>
 __global__ void __launch_bounds__(256, 3) leaf_residual_df_kernel(
     ResidualArgs a, const int* __restrict__ leaf_edges, const int* __restrict__ ce,
-    const double* __restrict__ ug, const double* __restrict__ g, double* __restrict__ uc, double* __restrict__ r_out,
+    const double* __restrict__ ug, const double* __restrict__ g, double* __restrict__ uc, float* __restrict__ r_out,
     double* __restrict__ vflux, int nrhs, int stage_l) {
   constexpr int NRC = 2 * NP;
   const int lf = blockIdx.x;
@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(256, 3) leaf_residual_df_kernel(
   q2* uys = uxs + PS * NP;
   q2* gs = uys + PS * NP;
   q2* ugs = gs + PS * NP;                                  // NP x nq
-  double* rs = reinterpret_cast<double*>(ugs + nq * NP);   // pp x NRC: r of the pass
+  float* rs = reinterpret_cast<float*>(ugs + nq * NP);     // pp x NRC: r of the pass (FP32)
   df* cf = reinterpret_cast<df*>(rs + pp * NRC);           // 6 pp: -c11, -2 c12, -c22, c1, c2, c
   float2* sL = reinterpret_cast<float2*>(cf + 6 * pp);     // staged L_ce,ge blocks, then L_loc
   const int nlc = stage_l ? a.n_lce : 0;
@@ -340,7 +340,7 @@ __global__ void __launch_bounds__(256, 3) leaf_residual_df_kernel(
       const bool inner = ix > 0 && ix < p - 1 && iy > 0 && iy < p - 1;
       if (!inner) {
 #pragma unroll
-        for (int rr = 0; rr < NRC; ++rr) rs[n * NRC + rr] = 0.0;
+        for (int rr = 0; rr < NRC; ++rr) rs[n * NRC + rr] = 0.f;
         continue;
       }
       df2 xx[NP], yy[NP], xy[NP];
@@ -379,8 +379,10 @@ __global__ void __launch_bounds__(256, 3) leaf_residual_df_kernel(
         const f2 bb = f2_sub(sh, gg.h);
         const f2 t = f2_sub(f2_sub(gg.h, f2_sub(sh, bb)), f2_add(Au.h, bb));
         const df2 res = df2_norm({sh, f2_add(t, f2_sub(gg.l, Au.l))});
-        rs[n * NRC + 2 * pr] = df2_to0(res);
-        rs[n * NRC + 2 * pr + 1] = df2_to1(res);
+        // r rounded to FP32 (the high part of the renormalised pair): the correction solve's
+        // right-hand side
+        rs[n * NRC + 2 * pr] = f2_lo(res.h);
+        rs[n * NRC + 2 * pr + 1] = f2_hi(res.h);
       }
     }
     // leaf fluxes v = D_ge,c u (Sec. 3.4), taken from the last threads first (the interior
@@ -584,7 +586,7 @@ void launch_coeff_grad(const ResidualArgs& a, const double* uc, const double* gb
 // staged L tables when stage_l.
 static size_t residual_smem(const ResidualArgs& a, int np, int nlc, bool stage_l) {
   const size_t pp = (size_t)a.p * a.p, nq = 4 * (size_t)a.q;
-  size_t b = (2 * pp + 4 * (pp + a.p) * np + nq * np) * sizeof(ulonglong2) + pp * 2 * np * sizeof(double) +
+  size_t b = (2 * pp + 4 * (pp + a.p) * np + nq * np) * sizeof(ulonglong2) + pp * 2 * np * sizeof(float) +
              6 * pp * sizeof(df);
   if (stage_l) b += (((size_t)nlc + 1) & ~(size_t)1) * sizeof(float2) + (size_t)a.q * a.p * sizeof(float2);
   return b;
@@ -592,7 +594,7 @@ static size_t residual_smem(const ResidualArgs& a, int np, int nlc, bool stage_l
 
 template <int NP>
 static void residual_launch(const ResidualArgs& a, const int* leaf_edges, const int* ce, const double* ug,
-                            const double* g, double* uc, double* r_out, double* vflux, int nrhs, int nlc,
+                            const double* g, double* uc, float* r_out, double* vflux, int nrhs, int nlc,
                             cudaStream_t s) {
   const size_t limit = 227 * 1024;
   const bool stage_l = residual_smem(a, NP, nlc, true) <= limit;
@@ -615,7 +617,7 @@ static void residual_launch(const ResidualArgs& a, const int* leaf_edges, const 
 }
 
 void launch_leaf_residual_df(const ResidualArgs& a, const int* leaf_edges, const int* ce,
-                             const double* ug, const double* g, double* uc, double* r_out, double* vflux, int nrhs,
+                             const double* ug, const double* g, double* uc, float* r_out, double* vflux, int nrhs,
                              cudaStream_t s) {
   const int n_lce = a.n_lce;
   // two pairs per pass unless the buffers then exceed the shared memory of a CTA

@@ -514,6 +514,39 @@ __global__ void axpy_kernel(const TI* __restrict__ x, double* __restrict__ y, lo
     y[e] += (double)x[e];
 }
 
+// y += x with the maxima of |x| and of the updated |y| (one pass instead of three)
+__global__ void axpy_measure_kernel(const float* __restrict__ x, double* __restrict__ y, long long n,
+                                    unsigned long long* __restrict__ out) {
+  double mx = 0.0, my = 0.0;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const float xv = x[e];
+    const double yv = y[e] + (double)xv;
+    y[e] = yv;
+    mx = fmax(mx, fabs((double)xv));
+    my = fmax(my, fabs(yv));
+    if (xv != xv) mx = DBL_MAX;  // NaN propagates as "huge"
+    if (yv != yv) my = DBL_MAX;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    my = fmax(my, __shfl_down_sync(0xffffffffu, my, o));
+  }
+  __shared__ double red[2][32];
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = mx;
+    red[1][threadIdx.x >> 5] = my;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+      mx = fmax(mx, red[0][w]);
+      my = fmax(my, red[1][w]);
+    }
+    atomicMax(out, (unsigned long long)__double_as_longlong(mx));
+    atomicMax(out + 1, (unsigned long long)__double_as_longlong(my));
+  }
+}
+
 template <typename T>
 __global__ void absmax_kernel(const T* __restrict__ x, long long n, unsigned long long* __restrict__ out) {
   double m = 0.0;
@@ -721,6 +754,10 @@ void launch_fill(double* x, long long n, double v, cudaStream_t s) {
   fill_kernel<<<grid_for(n, 256, 1024), 256, 0, s>>>(x, n, v);
 }
 
+void launch_axpy_measure(const float* x, double* y, long long n, double* out, cudaStream_t s) {
+  if (n <= 0) return;
+  axpy_measure_kernel<<<grid_for(n, 256, 1216), 256, 0, s>>>(x, y, n, reinterpret_cast<unsigned long long*>(out));
+}
 void launch_absmax(const double* x, long long n, double* out, cudaStream_t s) {
   absmax_kernel<double><<<grid_for(n, 256, 1024), 256, 0, s>>>(x, n, reinterpret_cast<unsigned long long*>(out));
 }
