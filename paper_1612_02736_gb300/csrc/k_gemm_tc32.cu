@@ -366,7 +366,7 @@ __global__ void __launch_bounds__(T_THREADS, 1) gemm_tc32_kernel(const GemmItem*
           const float* srow = A + it.a_off + (long long)arow * it.lda;
 #pragma unroll
           for (int j = 0; j < T_NSUB; ++j) {
-            if (j >= nsub) break;
+            if (j >= nsub) continue;
             const int k = k0 + 16 * j + 4 * aq;
             float* dst = &rw.A[arow][4 * swz_a(arow, 4 * j + aq)];
             const float* src = srow + k;
@@ -384,7 +384,7 @@ __global__ void __launch_bounds__(T_THREADS, 1) gemm_tc32_kernel(const GemmItem*
         const int n = x.u.nb * T_GN + 4 * bch;
 #pragma unroll
         for (int j = 0; j < T_NSUB; ++j) {
-          if (j >= nsub) break;
+          if (j >= nsub) continue;
           const int kl = 16 * j + bkl, k = k0 + kl;
           float* dst = &rw.B[kl][4 * swz_b(kl, bch)];
           if (k < it.K) {
@@ -427,27 +427,39 @@ __global__ void __launch_bounds__(T_THREADS, 1) gemm_tc32_kernel(const GemmItem*
       if (ks >= T_GST && !warp_wait(&sh.sfree[st], ((ks / T_GST) - 1) & 1, abort_flag, status)) break;
       const TRaw& rw = sh.raw[slot];
       TStage& sg = sh.st[st];
+      // every slice's entries are read first (slices past the stage's last read stale but
+      // in-bounds entries and store nothing), so that the slices' splits are independent
+      // chains the compiler interleaves
+      if (!cached) {
+        const int off = kmaj(arow, 4 * aq);
+        float va[T_NSUB][4];
 #pragma unroll
-      for (int j = 0; j < T_NSUB; ++j) {
-        if (j >= mt.y) break;
-        if (!cached) {
-          const int off = kmaj(arow, 4 * aq);
-          if (arow >= mt.x) {
-            zero_pieces4(sg.A[j][0], T_SPL, off);
-          } else {
-            const float4 a4 = *reinterpret_cast<const float4*>(&rw.A[arow][4 * swz_a(arow, 4 * j + aq)]);
-            const float v[4] = {a4.x, a4.y, a4.z, a4.w};
-            write_pieces4(v, sg.A[j][0], T_SPL, off);
+        for (int j = 0; j < T_NSUB; ++j) {
+          const float4 a4 = *reinterpret_cast<const float4*>(&rw.A[arow][4 * swz_a(arow, 4 * j + aq)]);
+          va[j][0] = a4.x;
+          va[j][1] = a4.y;
+          va[j][2] = a4.z;
+          va[j][3] = a4.w;
+        }
+#pragma unroll
+        for (int j = 0; j < T_NSUB; ++j) {
+          if (j < mt.y) {
+            if (arow >= mt.x) zero_pieces4(sg.A[j][0], T_SPL, off);
+            else write_pieces4(va[j], sg.A[j][0], T_SPL, off);
           }
         }
-        float v[4];
+      }
+      float vb[T_NSUB][4];
+#pragma unroll
+      for (int j = 0; j < T_NSUB; ++j)
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const int kl = 16 * j + 4 * aq + q;
-          v[q] = rw.B[kl][4 * swz_b(kl, bcol >> 2) + (bcol & 3)];
+          vb[j][q] = rw.B[kl][4 * swz_b(kl, bcol >> 2) + (bcol & 3)];
         }
-        write_pieces4(v, sg.B[j][0], T_SPL, kmaj(bcol, 4 * aq));
-      }
+#pragma unroll
+      for (int j = 0; j < T_NSUB; ++j)
+        if (j < mt.y) write_pieces4(vb[j], sg.B[j][0], T_SPL, kmaj(bcol, 4 * aq));
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       mb_arrive(&sh.sfull[st]);
       // stage ks + GPF reuses the slot of stage ks - 1, which this warp finished reading before

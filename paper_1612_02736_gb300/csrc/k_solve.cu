@@ -438,23 +438,37 @@ __global__ void up_gather_kernel(const UpGather* __restrict__ g, const TV* __res
   const int* p1a = j3 + u.k3;
   const int* p2b = p1a + u.n1;
   const int rows = u.k3 + u.k3 + u.n1 + u.n2;
-  const long long total = (long long)rows * nrhs;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int row = (int)(e / nrhs);
-    const int r = (int)(e - (long long)row * nrhs);
+  // row `row`, right-hand sides r = r0, r0 + step, ... below nrhs
+  auto body = [&](int row, int r0, int step) {
     if (row < u.k3) {
-      TV v = V[(long long)(u.vb_row + p3b[row]) * nrhs + r] - V[(long long)(u.va_row + p3a[row]) * nrhs + r];
-      if (rho) v += (TV)rho[(long long)j3[row] * nrhs + r];
-      dbuf[(long long)(u.d_row + row) * nrhs + r] = v;
+      const TV* vb = V + (long long)(u.vb_row + p3b[row]) * nrhs;
+      const TV* va = V + (long long)(u.va_row + p3a[row]) * nrhs;
+      const double* rr = rho ? rho + (long long)j3[row] * nrhs : nullptr;
+      TV* dst = dbuf + (long long)(u.d_row + row) * nrhs;
+      for (int r = r0; r < nrhs; r += step) {
+        TV v = vb[r] - va[r];
+        if (rr) v += (TV)rr[r];
+        dst[r] = v;
+      }
     } else if (row < 2 * u.k3) {
-      Vout[(long long)(u.vt_row + row - u.k3) * nrhs + r] = TV(0);
-    } else if (row < 2 * u.k3 + u.n1) {
-      const int i = row - 2 * u.k3;
-      Vout[(long long)(u.vt_row + u.k3 + i) * nrhs + r] = V[(long long)(u.va_row + p1a[i]) * nrhs + r];
+      TV* dst = Vout + (long long)(u.vt_row + row - u.k3) * nrhs;
+      for (int r = r0; r < nrhs; r += step) dst[r] = TV(0);
     } else {
-      const int i = row - 2 * u.k3 - u.n1;
-      Vout[(long long)(u.vt_row + u.k3 + u.n1 + i) * nrhs + r] = V[(long long)(u.vb_row + p2b[i]) * nrhs + r];
+      const bool a = row < 2 * u.k3 + u.n1;
+      const int i = a ? row - 2 * u.k3 : row - 2 * u.k3 - u.n1;
+      const TV* src = V + (long long)(a ? u.va_row + p1a[i] : u.vb_row + p2b[i]) * nrhs;
+      TV* dst = Vout + (long long)(u.vt_row + u.k3 + (a ? 0 : u.n1) + i) * nrhs;
+      for (int r = r0; r < nrhs; r += step) dst[r] = src[r];
+    }
+  };
+  if (nrhs >= 32) {  // a warp per row, lanes along the right-hand sides
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int row = blockIdx.x * nw + (threadIdx.x >> 5); row < rows; row += gridDim.x * nw) body(row, lane, 32);
+  } else {
+    const int total = rows * nrhs;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+      const int row = e / nrhs;
+      body(row, e - row * nrhs, nrhs);
     }
   }
 }
@@ -603,16 +617,25 @@ template <typename TV>
 __global__ void split_reduce_kernel(const SplitRed* __restrict__ d, const TV* __restrict__ P, TV* __restrict__ C,
                                     const TV* __restrict__ Add, const int* __restrict__ idx, int nrhs, TV beta) {
   const SplitRed sr = d[blockIdx.y];
-  const long long total = (long long)sr.M * nrhs;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(e / nrhs);
-    const int r = (int)(e - (long long)i * nrhs);
-    TV v = TV(0);
-    for (int j = 0; j < sr.nsplit; ++j) v += P[(long long)(sr.p_row + j * sr.M + i) * nrhs + r];
-    if (sr.add_row >= 0) v += Add[(long long)(sr.add_row + i) * nrhs + r];
-    const long long cr = (long long)map_row(idx, sr.c_idx, sr.c_row, i) * nrhs + r;
-    C[cr] = (beta != TV(0) ? beta * C[cr] : TV(0)) + v;
+  // row i, right-hand sides r = r0, r0 + step, ... below nrhs
+  auto body = [&](int i, int r0, int step) {
+    const long long crow = (long long)map_row(idx, sr.c_idx, sr.c_row, i) * nrhs;
+    for (int r = r0; r < nrhs; r += step) {
+      TV v = TV(0);
+      for (int j = 0; j < sr.nsplit; ++j) v += P[(long long)(sr.p_row + j * sr.M + i) * nrhs + r];
+      if (sr.add_row >= 0) v += Add[(long long)(sr.add_row + i) * nrhs + r];
+      C[crow + r] = (beta != TV(0) ? beta * C[crow + r] : TV(0)) + v;
+    }
+  };
+  if (nrhs >= 32) {  // a warp per row, lanes along the right-hand sides
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int i = blockIdx.x * nw + (threadIdx.x >> 5); i < sr.M; i += gridDim.x * nw) body(i, lane, 32);
+  } else {
+    const int total = sr.M * nrhs;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+      const int i = e / nrhs;
+      body(i, e - i * nrhs, nrhs);
+    }
   }
 }
 
