@@ -352,6 +352,11 @@ void launch_jump_residual(const int* pairs, int npairs, int q, const double* vfl
 void launch_absmax(const double* x, long long n, double* out, cudaStream_t s);
 void launch_fill(double* x, long long n, double v, cudaStream_t s);  // x[0..n) = v
 void launch_absmax_f32(const float* x, long long n, double* out, cudaStream_t s);  // max |x| as a double
+// Raises a kernel's dynamic shared-memory limit on the current device to at least `bytes`
+// (set once per kernel, device and size; thread-safe).
+void ensure_smem(const void* kernel, size_t bytes);
+// SM count of the current device.
+int device_sms();
 // Row combinations dst[d] = A[a] (+ sign * B[b] if b >= 0), entries (d, a, b, sign) at tab,
 // rows of nrhs values.
 void launch_row_combine(const int* tab, int n, double* dst, const double* A, const double* B, int nrhs,

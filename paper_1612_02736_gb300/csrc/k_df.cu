@@ -562,11 +562,7 @@ void launch_leaf_apply_df(const ResidualArgs& a, const double* u, double alpha, 
                           cudaStream_t s) {
   const int pp = a.p * a.p;
   const size_t smem = (size_t)(10 * pp + 2 * pp * RC) * sizeof(df);
-  static size_t configured = 0;
-  if (smem > 48 * 1024 && smem > configured) {
-    cudaFuncSetAttribute(leaf_apply_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    configured = smem;
-  }
+  ensure_smem((const void*)leaf_apply_df_kernel, smem);
   leaf_apply_df_kernel<<<(unsigned)a.n_leaf, 256, smem, s>>>(a, u, alpha, beta, out, nrhs);
 }
 
@@ -574,11 +570,7 @@ void launch_coeff_grad(const ResidualArgs& a, const double* uc, const double* gb
                        cudaStream_t s) {
   const int pp = a.p * a.p;
   const size_t smem = (size_t)(12 * pp) * sizeof(df);
-  static size_t configured = 0;
-  if (smem > 48 * 1024 && smem > configured) {
-    cudaFuncSetAttribute(coeff_grad_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    configured = smem;
-  }
+  ensure_smem((const void*)coeff_grad_df_kernel, smem);
   coeff_grad_df_kernel<<<(unsigned)a.n_leaf, 256, smem, s>>>(a, uc, gbar, grad, nrhs);
 }
 
@@ -599,19 +591,7 @@ static void residual_launch(const ResidualArgs& a, const int* leaf_edges, const 
   const size_t limit = 227 * 1024;
   const bool stage_l = residual_smem(a, NP, nlc, true) <= limit;
   const size_t smem = residual_smem(a, NP, nlc, stage_l);
-  if (smem > 48 * 1024) {
-    // the limit is a property of the device's context: raised once per device (the first
-    // launch is never inside a stream capture: a handle's first solve runs directly)
-    static std::mutex mu;
-    static size_t configured[64] = {0};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    std::lock_guard<std::mutex> lk(mu);
-    if (dev >= 0 && dev < 64 && smem > configured[dev]) {
-      cudaFuncSetAttribute(leaf_residual_df_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      configured[dev] = smem;
-    }
-  }
+  ensure_smem((const void*)leaf_residual_df_kernel<NP>, smem);
   leaf_residual_df_kernel<NP><<<(unsigned)a.n_leaf, 256, smem, s>>>(a, leaf_edges, ce, ug, g, uc, r_out, vflux, nrhs,
                                                                     stage_l ? 1 : 0);
 }

@@ -1377,11 +1377,7 @@ void launch_gj_panel(const GJDesc* d, int nmat, int maxK, T* work, int* perm, T*
   const int nrows = maxK - c0;
   if (nrows <= 0) return;
   const size_t smem = (size_t)nrows * (nb + 1) * sizeof(T) + (size_t)nrows * sizeof(int) + 16;
-  static size_t configured = 0;
-  if (smem > 48 * 1024 && smem > configured) {
-    cudaFuncSetAttribute(gj_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    configured = smem;
-  }
+  ensure_smem((const void*)gj_panel_kernel<T>, smem);
   // many matrices: 256 threads each, several CTAs per SM; few (the large merges near the
   // root): a thread per panel row, up to 1024, so that each pivot step is short
   const int threads = nmat >= 2 * 152 ? 256 : std::max(256, std::min(1024, (nrows + 31) / 32 * 32));
@@ -1415,17 +1411,12 @@ template <typename T>
 void launch_gj_update(const GJDesc* d, int nmat, int maxR, int maxRows, T* work, const int* perm, T* prow,
                       long long prow_stride, int c0, int nb, cudaStream_t s, int* status, int tensor,
                       long long mat_stride) {
-  static int nsm = 0;
-  if (std::is_same<T, double>::value && tensor && !nsm) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(gj_update_tcp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PtShared));
-    cudaFuncSetAttribute(gj_update_tcs_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sizeof(PsShared));
-    cudaFuncSetAttribute(gj_update_tcs_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sizeof(PsShared));
-    if (nsm <= 0) nsm = 1;
+  int nsm = 1;
+  if (std::is_same<T, double>::value && tensor) {  // per device: SM count and shared-memory limits
+    nsm = device_sms();
+    ensure_smem((const void*)gj_update_tcp_kernel, sizeof(PtShared));
+    ensure_smem((const void*)gj_update_tcs_kernel<true>, sizeof(PsShared));
+    ensure_smem((const void*)gj_update_tcs_kernel<false>, sizeof(PsShared));
   }
   if (std::is_same<T, double>::value && tensor == 2) {
     // FP64, streamed tensor-core kernel (16-byte aligned rows): one CTA per SM over units
@@ -1484,11 +1475,7 @@ void launch_gj_extract(const GJDesc* d, int nmat, int maxR, const T* work, const
   int gx = (maxR + 7) / 8;  // one warp per row, 8 per block
   if (gx > 1024) gx = 1024;
   const size_t smem = (size_t)2 * maxR * sizeof(int);
-  static size_t configured = 0;
-  if (smem > 48 * 1024 && smem > configured) {
-    cudaFuncSetAttribute(gj_extract_kernel<T, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    configured = smem;
-  }
+  ensure_smem((const void*)gj_extract_kernel<T, TO>, smem);
   gj_extract_kernel<T, TO><<<dim3(gx, nmat), 256, smem, s>>>(d, work, perm, dst);
 }
 

@@ -178,11 +178,7 @@ void launch_leaf_assemble(const double* coeffs, long long n_leaf_total, int leaf
                           long long mat_stride, cudaStream_t s) {
   const int pp = p * p, m = (p - 2) * (p - 2);
   const size_t smem = (size_t)(6 * pp + 2 * pp + 3 * p * q) * sizeof(double) + (size_t)3 * m * sizeof(int) + 16;
-  static size_t configured = 0;
-  if (smem > 48 * 1024 && smem > configured) {
-    cudaFuncSetAttribute(leaf_assemble_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    configured = smem;
-  }
+  ensure_smem((const void*)leaf_assemble_kernel<T>, smem);
   leaf_assemble_kernel<T><<<nleaf, 256, smem, s>>>(coeffs, n_leaf_total, leaf0, hxy, p, q, tb, work,
                                                   mat_stride);
 }

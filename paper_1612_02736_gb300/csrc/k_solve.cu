@@ -10,6 +10,9 @@
 // few right-hand sides, long inner dimensions).  Vectors are [row][rhs] with the
 // right-hand side fastest.
 #include <cfloat>
+#include <map>
+#include <mutex>
+#include <utility>
 #include <type_traits>
 
 #include "hps_internal.h"
@@ -772,6 +775,27 @@ __global__ void fill_kernel(double* __restrict__ x, long long n, double v) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     x[i] = v;
 }
+void ensure_smem(const void* kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, size_t> done;
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& cur = done[{kernel, dev}];
+  if (bytes > cur) {
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cur = bytes;
+  }
+}
+
+int device_sms() {
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  return nsm > 0 ? nsm : 1;
+}
+
 void launch_fill(double* x, long long n, double v, cudaStream_t s) {
   if (n <= 0) return;
   fill_kernel<<<grid_for(n, 256, 1024), 256, 0, s>>>(x, n, v);
