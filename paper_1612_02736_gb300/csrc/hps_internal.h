@@ -353,7 +353,7 @@ void launch_absmax(const double* x, long long n, double* out, cudaStream_t s);
 void launch_fill(double* x, long long n, double v, cudaStream_t s);  // x[0..n) = v
 void launch_absmax_f32(const float* x, long long n, double* out, cudaStream_t s);  // max |x| as a double
 // Raises a kernel's dynamic shared-memory limit on the current device to at least `bytes`
-// (set once per kernel, device and size; thread-safe).
+// (set once per kernel, device and size, whatever the size; thread-safe).
 void ensure_smem(const void* kernel, size_t bytes);
 // SM count of the current device.
 int device_sms();
