@@ -48,9 +48,6 @@ constexpr int T_GN = 64;            // right-hand sides per unit
 constexpr int T_PL = 3;             // bf16 pieces per entry
 constexpr int T_KS = 64;            // k per stage
 constexpr int T_NSUB = T_KS / 16;   // K slices (MMA K steps) per stage
-constexpr int T_GST = 2;            // stages
-constexpr int T_GPF = 2;            // stages the entry copies run ahead
-constexpr int T_GRAW = T_GPF + 1;   // raw entry slots
 constexpr int T_THREADS = 448;      // 14 warps
 constexpr int T_LOAD_WARP = 11;     // bulk copies of cached operator planes
 constexpr int T_PROD = 256;         // producer threads (8 warps)
@@ -71,24 +68,42 @@ struct TStage {
   unsigned char B[T_NSUB][T_PL][T_SPL];
 };
 
+// Pipeline depth.  With cached operator pieces a stage's planes arrive by one bulk copy
+// issued when the stage is freed, so the copy's HBM latency is hidden only by the stages
+// ahead of it: three stages, and raw slots for the vectors alone, the vector copies three
+// stages ahead.  Without the cache the raw slots also hold the operator entries and two
+// stages fit.
+template <bool CACHED>
+struct TCfg {
+  static constexpr int GST = CACHED ? 3 : 2;         // stages
+  static constexpr int GPF = CACHED ? 3 : 2;         // stages the entry copies run ahead
+  static constexpr int GRAW = GPF + 1;               // raw entry slots
+  static constexpr int AROWS = CACHED ? 1 : T_GR;    // raw operator rows (none used when cached)
+};
+
 // Entries of one stage as copied: the operator block row-major (64 rows x 64 k, the 16-byte
 // chunks of row r at chunk index c ^ 4 (r & 1)) and the vector block k-major (64 k x 64
 // right-hand sides, the 16-byte chunks of row k at c ^ 2 ((k >> 2) & 3)), so that the
 // producers' reads in the split hit distinct banks.
-struct TRaw {
-  float A[T_GR][T_KS];
+template <bool CACHED>
+struct TRawT {
+  float A[TCfg<CACHED>::AROWS][T_KS];
   float B[T_KS][T_GN];
 };
 
-struct TShared {
-  TStage st[T_GST];
-  TRaw raw[T_GRAW];
+template <bool CACHED>
+struct TSharedT {
+  TStage st[TCfg<CACHED>::GST];
+  TRawT<CACHED> raw[TCfg<CACHED>::GRAW];
   float ct[4][32][33];  // epilogue: each warp's 32 x 32 result tile, for coalesced stores
-  int2 meta[8][T_GRAW];  // per producer warp and raw slot: item rows, K slices (0: none)
-  unsigned long long sfull[T_GST], sfree[T_GST], tfull[2], tfree[2], mdone;
+  int2 meta[8][TCfg<CACHED>::GRAW];  // per producer warp and raw slot: item rows, K slices (0: none)
+  unsigned long long sfull[TCfg<CACHED>::GST], sfree[TCfg<CACHED>::GST], tfull[2], tfree[2], mdone;
   unsigned int tmem_base;
   int abort_flag;
 };
+
+static_assert(sizeof(TSharedT<true>) <= 232448 && sizeof(TSharedT<false>) <= 232448,
+              "a CTA's shared memory exceeds the 227 KB opt-in limit");
 
 __device__ __forceinline__ int swz_a(int row, int chunk) { return chunk ^ ((row & 1) << 2); }
 __device__ __forceinline__ int swz_b(int k, int chunk) { return chunk ^ (((k >> 2) & 3) << 1); }
@@ -150,6 +165,7 @@ struct UnitStep {
 __device__ __forceinline__ int item_stages(int K) { return (K + T_KS - 1) / T_KS; }
 __device__ __forceinline__ int stage_slices(int K, int c) { return min(T_NSUB, (K - c * T_KS + 15) >> 4); }
 
+template <bool CACHED>
 __global__ void __launch_bounds__(T_THREADS, 1) gemm_tc32_kernel(const GemmItem* __restrict__ items, int nitems,
                                                                  const float* __restrict__ A,
                                                                  const float* __restrict__ B0,
@@ -160,7 +176,9 @@ __global__ void __launch_bounds__(T_THREADS, 1) gemm_tc32_kernel(const GemmItem*
                                                                  const long long* __restrict__ astep,
                                                                  int* __restrict__ status) {
   extern __shared__ __align__(1024) unsigned char t_raw[];
-  TShared& sh = *reinterpret_cast<TShared*>(t_raw);
+  constexpr int T_GST = TCfg<CACHED>::GST, T_GPF = TCfg<CACHED>::GPF, T_GRAW = TCfg<CACHED>::GRAW;
+  using TRaw = TRawT<CACHED>;
+  TSharedT<CACHED>& sh = *reinterpret_cast<TSharedT<CACHED>*>(t_raw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   UnitStep us;
   us.nnb = (nrhs + T_GN - 1) / T_GN;
@@ -168,7 +186,7 @@ __global__ void __launch_bounds__(T_THREADS, 1) gemm_tc32_kernel(const GemmItem*
   us.dr = (int)gridDim.x % us.nnb;
   // cached operator planes (adig): one thread of the loader warp copies each stage's planes
   // with one bulk copy, and the producers only split the vectors
-  const bool cached = adig != nullptr;
+  constexpr bool cached = CACHED;
   if (tid == 0) {
     for (int b = 0; b < T_GST; ++b) {
       mb_init(&sh.sfull[b], cached ? T_PROD + 1 : T_PROD);
@@ -362,7 +380,8 @@ __global__ void __launch_bounds__(T_THREADS, 1) gemm_tc32_kernel(const GemmItem*
         TRaw& rw = sh.raw[slot];
         const GemmItem& it = x.it;
         const int k0 = x.c * T_KS;
-        if (!cached && arow < it.M) {
+        if constexpr (!CACHED) {
+        if (arow < it.M) {
           const float* srow = A + it.a_off + (long long)arow * it.lda;
 #pragma unroll
           for (int j = 0; j < T_NSUB; ++j) {
@@ -380,6 +399,7 @@ __global__ void __launch_bounds__(T_THREADS, 1) gemm_tc32_kernel(const GemmItem*
               }
             }
           }
+        }
         }
         const int n = x.u.nb * T_GN + 4 * bch;
 #pragma unroll
@@ -430,7 +450,7 @@ __global__ void __launch_bounds__(T_THREADS, 1) gemm_tc32_kernel(const GemmItem*
       // every slice's entries are read first (slices past the stage's last read stale but
       // in-bounds entries and store nothing), so that the slices' splits are independent
       // chains the compiler interleaves
-      if (!cached) {
+      if constexpr (!CACHED) {
         const int off = kmaj(arow, 4 * aq);
         float va[T_NSUB][4];
 #pragma unroll
@@ -602,7 +622,10 @@ int tc32_nsm() {
   if (!g_tc32_nsm[dev]) {
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(gemm_tc32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TShared));
+    cudaFuncSetAttribute(gemm_tc32_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(TSharedT<true>));
+    cudaFuncSetAttribute(gemm_tc32_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(TSharedT<false>));
     if (cudaGetLastError() != cudaSuccess) return 0;
     g_tc32_nsm[dev] = nsm > 0 ? nsm : 1;
   }
@@ -620,8 +643,12 @@ bool launch_gemm_tc32(const GemmItem* items, int nitems, const float* A, const f
   if (!nsm) return false;
   const long long units = (long long)nitems * ((nrhs + T_GN - 1) / T_GN);
   const int grid = (int)std::min<long long>(nsm, units);
-  gemm_tc32_kernel<<<grid, T_THREADS, sizeof(TShared), s>>>(items, nitems, A, B0, B1, C, Add, idx, nrhs, (float)beta,
-                                                            dg ? dg->dig : nullptr, dg ? dg->step : nullptr, status);
+  if (dg && dg->dig)
+    gemm_tc32_kernel<true><<<grid, T_THREADS, sizeof(TSharedT<true>), s>>>(items, nitems, A, B0, B1, C, Add, idx, nrhs,
+                                                                           (float)beta, dg->dig, dg->step, status);
+  else
+    gemm_tc32_kernel<false><<<grid, T_THREADS, sizeof(TSharedT<false>), s>>>(items, nitems, A, B0, B1, C, Add, idx,
+                                                                             nrhs, (float)beta, nullptr, nullptr, status);
   return true;
 }
 
