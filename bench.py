@@ -347,16 +347,40 @@ def run_gpu(args, rank, world, local):
                 (g.shape, g.shape, (f.shape[0], nrhs), g.shape, coeffs.shape)]
         h2d = ch.numel() * 8 + fh.numel() * 8 + gh.numel() * 8
         d2h = sum(o.numel() * 8 for o in outs)
+        # a copy stream overlaps each step's transfers with the neighbouring steps' work:
+        # step k + 1's inputs are copied in while step k runs, and step k's results are
+        # copied out while step k + 1 runs; the first upload and the last download are not
+        # overlapped with anything
+        cs = torch.cuda.Stream(device=dev)
+
+        def upload():
+            with torch.cuda.stream(cs):
+                xs = [x.to(dev, non_blocking=True) for x in (ch, fh, gh)]
+                e = torch.cuda.Event()
+                e.record(cs)
+            return xs, e
+
         barrier(world)
         torch.cuda.synchronize()
         e0 = ev()
-        for _ in range(args.steps):
-            cd = ch.to(dev, non_blocking=True)
-            fd = fh.to(dev, non_blocking=True)
-            gd = gh.to(dev, non_blocking=True)
+        cs.wait_event(e0)
+        nxt = upload()
+        for k in range(args.steps):
+            (cd, fd, gd), ein = nxt
+            stream.wait_event(ein)
+            for x in (cd, fd, gd):
+                x.record_stream(stream)
+            if k + 1 < args.steps:
+                nxt = upload()
             res = step(cd, fd, gd, None)
-            for o, r in zip(outs, res):
-                o.copy_(r, non_blocking=True)
+            eout = torch.cuda.Event()
+            eout.record(stream)
+            with torch.cuda.stream(cs):
+                cs.wait_event(eout)
+                for o, r in zip(outs, res):
+                    r.record_stream(cs)
+                    o.copy_(r, non_blocking=True)
+        stream.wait_stream(cs)
         e1 = ev()
         torch.cuda.synchronize()
         barrier(world)
