@@ -292,6 +292,14 @@ int hps_timing_count(int* n);
 int hps_timing_get(int i, char* name, int name_len, int64_t* launches, double* ms, double* flops,
                    double* bytes);
 
+/* Self-test of the bounded waits that every tensor-core kernel uses: one CTA waits on an
+ * mbarrier that nothing arrives at, polling at most `polls` times (1 <= polls <= 2^26),
+ * while a second warp waits on the CTA's abort flag; the first wait gives up, raises the
+ * flag and sets the status word, the second sees the flag and returns.  Returns TIMEOUT
+ * when both behaved so (the call synchronises the stream), INVALID_ARG for a bad polls,
+ * CUDA for a launch error.  The device stays usable afterwards. */
+int hps_selftest_wait_timeout(int polls, void* stream);
+
 /* Message of the last failed call on this thread ("" if none).  Valid until the next
  * call on the same thread. */
 const char* hps_last_error(void);

@@ -63,6 +63,7 @@ SIGNATURES = {
     "hps_sync_status": (C.c_int, [P, P]),
     "hps_destroy": (C.c_int, [P]),
     "hps_last_error": (C.c_char_p, []),
+    "hps_selftest_wait_timeout": (C.c_int, [C.c_int, P]),
     "hps_timing_enable": (C.c_int, [C.c_int]),
     "hps_timing_reset": (C.c_int, []),
     "hps_timing_count": (C.c_int, [C.POINTER(C.c_int)]),

@@ -2211,6 +2211,28 @@ void hps_opts_default(hps_opts* o) {
   o->fp32_gemm = HPS_GEMM_TENSOR;
 }
 
+int hps_selftest_wait_timeout(int polls, void* stream) {
+  if (polls < 1 || polls > (1 << 26)) return fail(HPS_ERR_INVALID_ARG, "polls must be in [1, 2^26]");
+  cudaStream_t s = (cudaStream_t)stream;
+  int* d = nullptr;
+  if (cudaMallocAsync(&d, 2 * sizeof(int), s) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(HPS_ERR_OOM, "device allocation failed");
+  }
+  int h[2] = {0, 0};
+  cudaMemsetAsync(d, 0, 2 * sizeof(int), s);
+  const int rc = wait_selftest(polls, d, s);
+  cudaMemcpyAsync(h, d, 2 * sizeof(int), cudaMemcpyDeviceToHost, s);
+  const cudaError_t e = cudaStreamSynchronize(s);
+  cudaFreeAsync(d, s);
+  if (rc != 0 || e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(HPS_ERR_CUDA, "self-test launch failed");
+  }
+  if (h[0] == -1 && h[1] == 1) return fail(HPS_ERR_TIMEOUT, "the wait ran out and the abort flag stopped the other role");
+  return fail(HPS_ERR_STATE, "self-test: status " + std::to_string(h[0]) + ", flag seen " + std::to_string(h[1]));
+}
+
 const char* hps_last_error(void) { return g_err.c_str(); }
 
 int hps_tree_uniform(double x0, double y0, double x1, double y1, int nx, int ny, hps_tree** out) {

@@ -272,6 +272,8 @@ bool launch_gemm_tc(const GemmItem* items, int nitems, int trans, const double* 
 // Returns false, launching nothing, if the device set-up failed.
 // With dg, the operator's bf16 pieces are read from it (launch_gemm_tc32_pieces, same
 // results).
+// Bounded-wait self-test kernel (out_dev: 2 ints, zeroed by the caller); 0 or -1 (launch error).
+int wait_selftest(int polls, int* out_dev, cudaStream_t s);
 bool gemm_tc32_eligible(int nrhs);
 void gemm_tc32_prepare();
 bool launch_gemm_tc32(const GemmItem* items, int nitems, const float* A, const float* B0, const float* B1, float* C,

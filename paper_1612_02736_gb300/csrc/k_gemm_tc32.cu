@@ -596,6 +596,36 @@ __global__ void __launch_bounds__(256) gemm_tc32_pieces_kernel(const GemmItem* _
 
 }  // namespace
 
+namespace {
+// Self-test of the bounded waits: warp 0 waits on a barrier nothing arrives at (polls at
+// most `polls` times), warp 1 waits on a second such barrier with the full limit but gives
+// up as soon as the abort flag is raised; out[0] = the status word, out[1] = 1 if warp 1
+// returned through the flag.
+__global__ void wait_selftest_kernel(long long polls, int* out) {
+  __shared__ unsigned long long bar[2];
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    mb_init(&bar[0], 1);
+    mb_init(&bar[1], 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp == 0 && lane == 0) mb_wait_n(&bar[0], 0, polls, &abort_flag, out);
+  if (warp == 1 && lane == 0) {
+    const bool ok = mb_wait(&bar[1], 0, &abort_flag, nullptr);
+    out[1] = (!ok && abort_flag) ? 1 : 0;
+  }
+  __syncthreads();
+}
+}  // namespace
+
+int wait_selftest(int polls, int* out_dev, cudaStream_t s) {
+  wait_selftest_kernel<<<1, 64, 0, s>>>((long long)polls, out_dev);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 bool gemm_tc32_eligible(int nrhs) { return nrhs > 8; }
 
 long long gemm_tc32_piece_bytes(long long steps) { return steps * T_ASTEP; }

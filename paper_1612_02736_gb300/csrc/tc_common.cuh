@@ -56,6 +56,17 @@ __device__ __forceinline__ bool mb_wait(unsigned long long* b, int parity, volat
   if (status) atomicCAS(status, 0, -1);
   return false;
 }
+// The same wait with a caller-given poll limit.
+__device__ __forceinline__ bool mb_wait_n(unsigned long long* b, int parity, long long limit, volatile int* abort_flag,
+                                          int* status) {
+  for (long long it = 0; it < limit; ++it) {
+    if (mb_try(b, parity)) return true;
+    if ((it & 255) == 255 && *abort_flag) return false;
+  }
+  *abort_flag = 1;
+  if (status) atomicCAS(status, 0, -1);
+  return false;
+}
 // Bounded wait that ignores the abort flag (a role draining its own operations at exit).
 __device__ __forceinline__ void mb_drain(unsigned long long* b, int parity) {
   for (long long it = 0; it < kWaitLimit; ++it)

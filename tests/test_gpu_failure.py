@@ -1,7 +1,8 @@
 """Failure paths of the build and solve, made on the host or by the inputs (no GPU fault):
-non-elliptic or non-finite coefficient fields, a singular leaf, and an allocator that fails
-on its k-th request.  Each returns its status code, releases what it allocated, and leaves
-the library usable for the next call."""
+non-elliptic or non-finite coefficient fields, a singular leaf, an allocator that fails on
+its k-th request, and a bounded device wait that runs out (a barrier nothing arrives at).
+Each returns its status code, releases what it allocated, and leaves the library usable for
+the next call."""
 import ctypes as C
 
 import numpy as np
@@ -13,7 +14,7 @@ from tests.helpers import rel_linf
 
 pytestmark = pytest.mark.gpu
 
-HPS_ERR_INVALID_ARG, HPS_ERR_NOT_ELLIPTIC, HPS_ERR_SINGULAR, HPS_ERR_OOM = 1, 2, 3, 4
+HPS_ERR_INVALID_ARG, HPS_ERR_NOT_ELLIPTIC, HPS_ERR_SINGULAR, HPS_ERR_OOM, HPS_ERR_TIMEOUT = 1, 2, 3, 4, 6
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -159,3 +160,17 @@ def test_allocation_failures_release_everything():
     assert lib.hps_destroy(h) == 0
     assert not al.live
     lib.hps_tree_destroy(tree)
+
+
+def test_bounded_wait_runs_out():
+    # the bounded wait of the tensor-core kernels on a barrier that nothing arrives at: it
+    # gives up after its poll limit, raises the abort flag that stops the other role, and
+    # the call reports TIMEOUT; the device is usable afterwards
+    import torch
+    from paper_1612_02736_gb300 import _native as N
+    lib = N.load()
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for polls in (1, 1000, 100000):
+        rc = lib.hps_selftest_wait_timeout(polls, stream)
+        assert rc == HPS_ERR_TIMEOUT, (polls, rc, lib.hps_last_error())
+    _still_usable()

@@ -288,3 +288,9 @@ def test_refined_and_mask_trees_match_oracle(lib, kind):
     opts.precision = 1
     assert lib.hps_plan_check(r, p, C.byref(opts)) == 1   # mixed needs matching interfaces
     lib.hps_tree_destroy(r)
+
+
+def test_wait_selftest_rejects_bad_polls(lib):
+    # argument checks happen before any device call
+    assert lib.hps_selftest_wait_timeout(0, None) == 1
+    assert lib.hps_selftest_wait_timeout((1 << 26) + 1, None) == 1
