@@ -39,7 +39,8 @@ __global__ void __launch_bounds__(256) leaf_assemble_kernel(
   double* sLs = sD2 + pp;                          // p * q
   double* sLl = sLs + p * q;                       // q * p
   double* sDL = sLl + q * p;                       // p * q
-  int* sci = reinterpret_cast<int*>(sDL + p * q);  // m
+  double* wrow = sDL + p * q;                      // per warp: 4 p row factors (see below)
+  int* sci = reinterpret_cast<int*>(wrow + (blockDim.x >> 5) * 4 * p);  // m
   int* sjx = sci + m;                              // m: x index of interior node sci[j]
   int* sjy = sjx + m;                              // m: y index
   const int tid = threadIdx.x, bs = blockDim.x;
@@ -69,33 +70,45 @@ __global__ void __launch_bounds__(256) leaf_assemble_kernel(
       // A[ni][(jx, jy)] for the operator of Sec. 3.2:
       //   al Dx[ix][jx] Dy[iy][jy] + [iy = jy] (bx D2[ix][jx] + gx D[ix][jx])
       //   + [ix = jx] (by D2[iy][jy] + gy D[iy][jy]) + [ix = jx, iy = jy] c0
+      // The row's factors are formed once by the warp (ax = al Dx[ix][.], dy = Dy[iy][.],
+      // lx = the iy = jy line term, ly = the ix = jx line term), so that an entry is one FMA
+      // with its line term picked by selects: FP64 instructions under lane-divergent branches
+      // would cost the whole warp's FP64 pipe time.
       const double al = -2.0 * c12 * sx * sy;
       const double bx = -c11 * sx * sx, gx = c1 * sx, by = -c22 * sy * sy, gy = c2 * sy;
       const double* Dix = sD + ix * p;
       const double* Diy = sD + iy * p;
       const double* D2ix = sD2 + ix * p;
       const double* D2iy = sD2 + iy * p;
+      double* ax = wrow + (tid >> 5) * 4 * p;
+      double* dy = ax + p;
+      double* lx = dy + p;
+      double* ly = lx + p;
+      __syncwarp();
+      for (int j = lane; j < p; j += 32) {
+        ax[j] = al * Dix[j];
+        dy[j] = Diy[j];
+        lx[j] = bx * D2ix[j] + gx * Dix[j];
+        ly[j] = by * D2iy[j] + gy * Diy[j];
+      }
+      __syncwarp();
+      const double diag = lx[ix] + ly[iy] + c0;
       for (int col = lane; col < m; col += 32) {
         const int jx = sjx[col], jy = sjy[col];
-        double a = al * Dix[jx] * Diy[jy];
-        if (iy == jy) a += bx * D2ix[jx] + gx * Dix[jx];
-        if (ix == jx) a += by * D2iy[jy] + gy * Diy[jy];
-        if (ix == jx && iy == jy) a += c0;
-        Mr[col] = (T)a;
+        const double line = (iy == jy) ? ((ix == jx) ? diag : lx[jx]) : ((ix == jx) ? ly[jy] : 0.0);
+        Mr[col] = (T)fma(ax[jx], dy[jy], line);
       }
+      // exterior columns: side s, Gaussian node a; per side the two factors of the row
+      //   horizontal sides (jy = 0, p-1): al Dy[iy][jy] DL[ix][a] + ly[jy] Ls[ix][a]
+      //   vertical sides (jx = p-1, 0):   al Dx[ix][jx] DL[iy][a] + lx[jx] Ls[iy][a]
       for (int g = lane; g < nq; g += 32) {
-        const int s = g / q, a = g - s * q;
-        double v;
-        if (s == 0 || s == 2) {  // horizontal side jy = 0 or p-1: node (ix, jy) on the row's column
-          const int jy = (s == 0) ? 0 : p - 1;
-          const double dy = Diy[jy];
-          v = al * dy * sDL[ix * q + a] + (by * D2iy[jy] + gy * dy) * sLs[ix * q + a];
-        } else {  // vertical side jx = p-1 or 0: node (jx, iy) on the row's line
-          const int jx = (s == 1) ? p - 1 : 0;
-          const double dx = Dix[jx];
-          v = al * dx * sDL[iy * q + a] + (bx * D2ix[jx] + gx * dx) * sLs[iy * q + a];
-        }
-        Mr[m + g] = (T)v;
+        const int sd = g / q, a = g - sd * q;
+        const bool hz = sd == 0 || sd == 2;
+        const int jl = (sd == 0 || sd == 3) ? 0 : p - 1;
+        const double f1 = hz ? al * dy[jl] : ax[jl];
+        const double f2 = hz ? ly[jl] : lx[jl];
+        const int li = (hz ? ix : iy) * q + a;
+        Mr[m + g] = (T)fma(f1, sDL[li], f2 * sLs[li]);
       }
     } else {
       const int g = row - m, s = g / q, a = g - (g / q) * q;
@@ -177,7 +190,7 @@ void launch_leaf_assemble(const double* coeffs, long long n_leaf_total, int leaf
                           const double* hxy, int p, int q, const LeafTablesDev& tb, T* work,
                           long long mat_stride, cudaStream_t s) {
   const int pp = p * p, m = (p - 2) * (p - 2);
-  const size_t smem = (size_t)(6 * pp + 2 * pp + 3 * p * q) * sizeof(double) + (size_t)3 * m * sizeof(int) + 16;
+  const size_t smem = (size_t)(6 * pp + 2 * pp + 3 * p * q + 8 * 4 * p) * sizeof(double) + (size_t)3 * m * sizeof(int) + 16;
   ensure_smem((const void*)leaf_assemble_kernel<T>, smem);
   leaf_assemble_kernel<T><<<nleaf, 256, smem, s>>>(coeffs, n_leaf_total, leaf0, hxy, p, q, tb, work,
                                                   mat_stride);
