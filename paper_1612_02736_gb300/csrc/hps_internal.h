@@ -176,7 +176,7 @@ struct ExtractDst {
   void* TR; long long TR_off_stride; int TR_ld;
   void* BL; long long BL_off_stride; int BL_ld;
   void* BR; long long BR_off_stride; int BR_ld;   // FP64
-  double sTL, sTR, sBL;
+  double sTL, sTR, sBL;  // +1 or -1
   const long long* TL_off;   // optional per-matrix offsets (override b * stride) or null
   const long long* TR_off;
   const long long* BL_off;

@@ -1343,6 +1343,16 @@ __global__ void __launch_bounds__(256) gj_extract_kernel(const GJDesc* __restric
   const int ldTL = dst.ld_from_desc ? K : dst.TL_ld, ldBL = dst.ld_from_desc ? K : dst.BL_ld;
   const int ldTR = dst.ld_from_desc ? R - K : dst.TR_ld, ldBR = dst.ld_from_desc ? R - K : dst.BR_ld;
   (void)total;
+  // the blocks' scale factors are +1 or -1: applied as a sign flip on the integer pipe, and
+  // FP32 outputs rounded with integer operations (GB300's FP64 pipe would otherwise carry a
+  // multiply or a conversion per entry)
+  const bool nTL = dst.sTL < 0.0, nTR = dst.sTR < 0.0, nBL = dst.sBL < 0.0;
+  auto out = [](T x, bool neg) -> TO {
+    double v = (double)x;
+    if (neg) v = __longlong_as_double(__double_as_longlong(v) ^ (long long)0x8000000000000000ull);
+    if constexpr (std::is_same<TO, float>::value) return std::is_same<T, float>::value ? (float)v : float_of(v);
+    else return v;
+  };
   // one warp per logical row, lanes along it (reads of a row stay within one physical row;
   // writes are contiguous)
   const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -1351,13 +1361,13 @@ __global__ void __launch_bounds__(256) gj_extract_kernel(const GJDesc* __restric
     const T* Mr = M + (long long)sr * R;
     if (lr < K) {
       if (TL)
-        for (int lc = lane; lc < K; lc += 32) TL[tlo + (long long)lr * ldTL + lc] = (TO)(dst.sTL * (double)Mr[isig[lc]]);
+        for (int lc = lane; lc < K; lc += 32) TL[tlo + (long long)lr * ldTL + lc] = out(Mr[isig[lc]], nTL);
       if (TR)
-        for (int lc = K + lane; lc < R; lc += 32) TR[tro + (long long)lr * ldTR + (lc - K)] = (TO)(dst.sTR * (double)Mr[lc]);
+        for (int lc = K + lane; lc < R; lc += 32) TR[tro + (long long)lr * ldTR + (lc - K)] = out(Mr[lc], nTR);
     } else {
       if (BL)
         for (int lc = lane; lc < K; lc += 32)
-          BL[blo + (long long)(lr - K) * ldBL + lc] = (TO)(dst.sBL * (double)Mr[isig[lc]]);
+          BL[blo + (long long)(lr - K) * ldBL + lc] = out(Mr[isig[lc]], nBL);
       if (BR)
         for (int lc = K + lane; lc < R; lc += 32) BR[bro + (long long)(lr - K) * ldBR + (lc - K)] = (double)Mr[lc];
     }

@@ -27,22 +27,29 @@ __global__ void __launch_bounds__(256) merge_assemble_kernel(const MergeDesc* __
   const TT* Ta = tstore + md.ta_off;
   const TT* Tb = tstore + md.tb_off;
   T* M = work + md.m_off;
-  const long long total = (long long)md.rows * R;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int r = (int)(e / R);
-    const int c = (int)(e - (long long)r * R);
-    const int ar = pA[r], ac = pA[c], br = pB[r], bc = pB[c];
-    double v = 0.0;
-    if (ar >= 0 && ac >= 0) {
-      const double sa = ((r < k3) == (c < k3)) ? 1.0 : -1.0;
-      v += sa * (double)Ta[(long long)ar * md.lda_a + ac];
+  // one warp per row, lanes along it.  The children's blocks enter with signs +1 or -1
+  // (flipped on the integer pipe); only the pivot block Z = T33a - T33b adds two values,
+  // and its entries fill whole warps, so no FP64 instruction sits under a divergent branch
+  auto neg = [](double x) { return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ull); };
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int r = blockIdx.x * nw + (threadIdx.x >> 5); r < md.rows; r += gridDim.x * nw) {
+    const int ar = pA[r], br = pB[r];
+    const bool rtop = r < k3;
+    const TT* Tar = Ta + (long long)(ar >= 0 ? ar : 0) * md.lda_a;
+    const TT* Tbr = Tb + (long long)(br >= 0 ? br : 0) * md.lda_b;
+    T* Mr = M + (long long)r * R;
+    for (int c = lane; c < R; c += 32) {
+      const int ac = pA[c], bc = pB[c];
+      const bool ctop = c < k3;
+      const bool ha = ar >= 0 && ac >= 0, hb = br >= 0 && bc >= 0;
+      double va = ha ? (double)Tar[ac] : 0.0, vb = hb ? (double)Tbr[bc] : 0.0;
+      if (rtop != ctop) va = neg(va);  // sa = -1 off the diagonal blocks
+      if (ctop) vb = neg(vb);          // sb = -1 in the first k3 columns
+      double v;
+      if (ha && hb) v = va + vb;
+      else v = ha ? va : vb;
+      Mr[c] = (T)v;
     }
-    if (br >= 0 && bc >= 0) {
-      const double sb = (c < k3) ? -1.0 : 1.0;
-      v += sb * (double)Tb[(long long)br * md.lda_b + bc];
-    }
-    M[e] = (T)v;
   }
 }
 
@@ -107,8 +114,7 @@ void launch_bgemm(const BGemm* d, int n, int maxM, int maxN, const double* A, co
 template <typename T, typename TT>
 void launch_merge_assemble(const MergeDesc* d, int nmat, int maxR, const TT* tstore, const int* pos,
                            T* work, cudaStream_t s) {
-  const long long total = (long long)maxR * maxR;
-  int gx = (int)((total + 255) / 256);
+  int gx = (maxR + 7) / 8;  // one warp per row, 8 per block
   if (gx > 2048) gx = 2048;
   merge_assemble_kernel<T, TT><<<dim3(gx, nmat), 256, 0, s>>>(d, tstore, pos, work);
 }
