@@ -25,7 +25,9 @@
  *  - Calls taking a stream are stream-ordered.  hps_solve and hps_adjoint return once
  *    their work is enqueued (the iterative refinement of HPS_MIXED synchronises the
  *    stream to test convergence: once per call once calibrated, once per refinement
- *    step before, see hps_solve).  Errors found by device
+ *    step before, see hps_solve).  Calls on one handle share its workspace and graphs:
+ *    their work must not overlap on the GPU (one stream, or streams synchronised between
+ *    the calls).  Errors found by device
  *    code (singular pivots) are reported by hps_build (which synchronises) and by
  *    hps_sync_status.
  */
