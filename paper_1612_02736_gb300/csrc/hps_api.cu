@@ -227,6 +227,13 @@ struct Level {
   long long work_elems = 0;
   long long mstride = 0;  // matrix m of the batch at work + m * mstride, all of one shape (0: not so)
   int perm_elems = 0;
+  // blocked elimination (FP64 levels, see block_plan): Gauss-Jordan on the top k3 rows only
+  // (gj_top), then the bottom rows by one product with the eliminated top rows (schur, its
+  // K chunks at item ranges schur_chunk[c] .. schur_chunk[c + 1])
+  GJDesc* gj_top = nullptr;
+  ItemSet schur;
+  std::vector<int> schur_chunk;
+  int schur_R = 0;
   // solve
   UpGather* ug = nullptr;
   int ug_maxrows = 0;
@@ -484,8 +491,21 @@ int split_prod(ProdHost& ph, bool trans) {
   return prow;
 }
 
+// Blocked elimination of a level's merges (Algorithm 1's Schur complements, one product).
+// Every pivot of a merge matrix M = [[Z, R], [-C, T]] comes from its top k3 rows (the
+// interface equations), so the Gauss-Jordan elimination maps each bottom row x = [x_L | x_R]
+// to [0 | x_R] - x_L Top, Top[k] the final pivot row of column k (physical row perm[k]):
+// the bottom block ends as [0 | T] + (-C) Top, in-place layout unchanged.  Eliminating the
+// top rows alone and then forming the bottom rows by one FP64 tensor-core product (exact
+// digit slicing, K chunks of at most 448) streams the k12 x R bottom block once instead of
+// once per 16-pivot panel.  Taken for levels whose merges all keep their full matrix
+// (rows = R), share one row length, and have at least two panels.
+void block_plan(struct LevelHost& pd);
+
 struct LevelHost {
-  std::vector<GJDesc> gj;
+  std::vector<GJDesc> gj, gj_top;
+  std::vector<GemmItem> schur;
+  std::vector<int> schur_chunk;
   std::vector<MergeDesc> md;
   std::vector<long long> tl, bl, tr, br;
   std::vector<UpGather> ug;
@@ -860,6 +880,7 @@ void make_plan(hps_handle* h, HostPlan& hp) {
         same = pd.gj[i].R == g0.R && pd.gj[i].rows == g0.rows && pd.gj[i].off == (long long)i * g0.rows * g0.R;
       if (same) lv.mstride = (long long)g0.rows * g0.R;
     }
+    if (lv.fp64) block_plan(pd);
     lv.perm_elems = poff;
     h->p_rows = std::max(h->p_rows, split_prod(pd.up, false));
     h->p_rows = std::max(h->p_rows, split_prod(pd.down, false));
@@ -924,6 +945,49 @@ void make_plan(hps_handle* h, HostPlan& hp) {
   if (h->bc.on) make_bc_plan(h, hp, push);
 }
 
+void block_plan(LevelHost& pd) {
+  pd.gj_top.clear();
+  pd.schur.clear();
+  pd.schur_chunk.clear();
+  if (pd.gj.empty()) return;
+  const int R0 = pd.gj[0].R;
+  int kmax = 0;
+  for (const GJDesc& g : pd.gj) {
+    if (g.R != R0 || g.rows != g.R || g.K < 32 || g.K >= g.R || g.off % g.R != 0 || g.null_tol > 0.f) return;
+    kmax = std::max(kmax, g.K);
+  }
+  const int nck = (kmax + 447) / 448;
+  const int kc = ((kmax + nck - 1) / nck + 15) / 16 * 16;
+  for (int c = 0; c * kc < kmax; ++c) {
+    pd.schur_chunk.push_back((int)pd.schur.size());
+    for (const GJDesc& g : pd.gj) {
+      const int ks = c * kc;
+      if (ks >= g.K) continue;
+      const int K = std::min(kc, g.K - ks), k12 = g.R - g.K;
+      const int base = (int)(g.off / g.R);  // first row of the matrix, rows of length R
+      for (int r0 = 0; r0 < k12; r0 += ROWBLK) {
+        GemmItem it{};
+        it.a_off = g.off + (long long)(g.K + r0) * g.R + ks;  // -C, rows r0.., columns ks..
+        it.lda = g.R;
+        it.M = std::min(ROWBLK, k12 - r0);
+        it.K = K;
+        it.kseg = K;
+        it.b0_row = base;                // Top rows: base + perm[ks + k]
+        it.b0_idx = g.perm_off + ks;
+        it.b1_row = 0;
+        it.b1_idx = -1;
+        it.c_row = base + g.K + r0;      // the bottom rows, all R columns
+        it.c_idx = -1;
+        it.add_row = -1;
+        pd.schur.push_back(it);
+      }
+    }
+  }
+  pd.schur_chunk.push_back((int)pd.schur.size());
+  pd.gj_top = pd.gj;
+  for (GJDesc& g : pd.gj_top) g.rows = g.K;
+}
+
 Prod upload_prod(hps_handle* h, cudaStream_t s, const ProdHost& ph) {
   Prod pr;
   pr.direct = upload_items(h, s, ph.direct);
@@ -963,6 +1027,14 @@ void upload_plan(hps_handle* h, const HostPlan& hp, cudaStream_t s) {
     Level& lv = h->levels[L];
     const LevelHost& pd = hp.lv[L];
     lv.gj = upload(h->al, s, pd.gj, h->owned);
+    lv.gj_top = pd.gj_top.empty() ? nullptr : upload(h->al, s, pd.gj_top, h->owned);
+    {
+      const int mi = h->max_items;  // the build's own products do not size the solve's buffers
+      lv.schur = upload_items(h, s, pd.schur);
+      h->max_items = mi;
+    }
+    lv.schur_chunk = pd.schur_chunk;
+    lv.schur_R = pd.gj.empty() ? 0 : pd.gj[0].R;
     lv.md = upload(h->al, s, pd.md, h->owned);
     lv.off_tl = upload(h->al, s, pd.tl, h->owned);
     lv.off_bl = upload(h->al, s, pd.bl, h->owned);
@@ -1219,6 +1291,22 @@ std::string validate_plan(const hps_handle* h, const HostPlan& hp) {
           pd.tr[i] + (long long)k3 * k12 > ops ||
           (md.rows > k3 && (pd.br[i] < 0 || pd.br[i] + (long long)k12 * k12 > hp.tsz)))
         pc.fail("merge extraction out of range");
+    }
+    if (!pd.schur.empty()) {  // blocked elimination
+      const int R = pd.gj[0].R;
+      const long long wrows = lv.work_elems / R;
+      if (pd.gj_top.size() != pd.gj.size() || pd.schur_chunk.size() < 2 || pd.schur_chunk.front() != 0 ||
+          pd.schur_chunk.back() != (int)pd.schur.size())
+        pc.fail("blocked elimination: descriptors");
+      for (size_t i = 0; i < pd.gj.size(); ++i)
+        if (pd.gj_top[i].rows != pd.gj[i].K || pd.gj[i].R != R || pd.gj[i].off % R != 0)
+          pc.fail("blocked elimination: matrices");
+      for (const GemmItem& it : pd.schur)
+        if (it.M < 1 || it.M > ROWBLK || it.K < 1 || it.K > 448 || it.lda != R || it.kseg != it.K || it.a_off < 0 ||
+            it.a_off + (long long)(it.M - 1) * it.lda + it.K > lv.work_elems || it.b0_idx < 0 ||
+            it.b0_idx + it.K > lv.perm_elems || it.b0_row < 0 || it.b0_row + (long long)R > wrows || it.c_idx != -1 ||
+            it.c_row < 0 || (long long)it.c_row + it.M > wrows || it.add_row != -1)
+          pc.fail("blocked elimination: product item out of range");
     }
   }
   return pc.err;
@@ -1503,10 +1591,55 @@ void build_stage(hps_handle* h, const double* coeffs, cudaStream_t s) {
         int* pm = (int*)get((size_t)std::max(1, lv.perm_elems) * sizeof(int));
         double* pi = (double*)get((size_t)nmat * 256 * sizeof(double));
         double* pr = (double*)get((size_t)nmat * 16 * lv.maxR * sizeof(double));
+        // blocked elimination: the top rows' digit planes of -C and the product's exponent
+        // buffer, sized once for the level
+        const ItemSet& sc = lv.schur;
+        unsigned char* sdig = nullptr;
+        int *ser = nullptr, *sscale = nullptr;
+        long long sunits = 0;
+        std::vector<std::array<int, 3>> rk_top;
+        if (sc.n > 0) {
+          for (size_t c = 0; c + 1 < lv.schur_chunk.size(); ++c)
+            sunits = std::max<long long>(sunits, (long long)(lv.schur_chunk[c + 1] - lv.schur_chunk[c]) *
+                                                     ((lv.schur_R + 31) / 32));
+          sdig = (unsigned char*)get((size_t)gemm_tc_digit_bytes(sc.dsteps));
+          ser = (int*)get((size_t)sc.n * 64 * sizeof(int));
+          sscale = (int*)get((size_t)gemm_tc_scale_bytes(sunits));
+          for (auto m : rk) rk_top.push_back({m[0], m[1], m[1]});
+        }
         auto elim = [&](int nb) {
           TIMED("merge_assemble_f64", 0, wbytes, launch_merge_assemble<double, double>(lv.md, nmat, lv.maxR, tstore, h->didx, w, s));
           CKL();
-          run_gj<double>(lv.gj, nmat, lv.maxR, lv.maxK, w, pm, pi, pr, h->d_status, rk, "merge", s, nb, lv.mstride);
+          if (sc.n == 0) {
+            run_gj<double>(lv.gj, nmat, lv.maxR, lv.maxK, w, pm, pi, pr, h->d_status, rk, "merge", s, nb, lv.mstride);
+            return;
+          }
+          // Gauss-Jordan on the top rows, then bottom = [0 | T] + (-C) Top
+          run_gj<double>(lv.gj_top, nmat, lv.maxR, lv.maxK, w, pm, pi, pr, h->d_status, rk_top, "merge", s, nb,
+                         lv.mstride);
+          const long long k12max = lv.maxR - 1;
+          TIMED("gj_schur_digits_f64", 0, 0,
+                launch_gemm_tc_digitize(sc.dev, sc.n, 0, w, sc.dstep, sdig, ser, s, true));
+          TIMED("gj_schur_zero_f64", 0, 0, launch_gj_zero_bl(lv.gj, nmat, k12max * lv.maxK, w, s));
+          for (size_t c = 0; c + 1 < lv.schur_chunk.size(); ++c) {
+            const int b = lv.schur_chunk[c], e = lv.schur_chunk[c + 1];
+            GemmDigits dg;
+            dg.dig = sdig;
+            dg.step = sc.dstep + b;
+            dg.er = ser + (long long)b * 64;
+            GemmCtx cx;
+            cx.maxK = 448;
+            cx.maxKv = 448;
+            cx.status = h->d_status;
+            cx.dg = &dg;
+            cx.tc_scales = sscale;
+            cx.tc_units = sunits;
+            bool ok = false;
+            TIMED("gj_schur_f64", 2.0 * sc.elems * lv.schur_R / std::max<size_t>(1, lv.schur_chunk.size() - 1), 0,
+                  ok = launch_gemm_tc(sc.dev + b, e - b, 0, w, w, nullptr, w, nullptr, pm, lv.schur_R, 1.0, s, cx));
+            if (!ok) throw CudaError{HPS_ERR_CUDA, "blocked elimination: the tensor-core product could not be launched"};
+          }
+          CKL();
         };
         elim(pick_nb(h, "merge", sizeof(double), rk, nmat, s, elim));
         if (mixed)

@@ -149,6 +149,8 @@ void launch_leaf_assemble(const double* coeffs, long long n_leaf_total, int leaf
 
 template <typename T>
 void launch_gj_init(const GJDesc* d, int nmat, int* perm, cudaStream_t s);
+// Zeroes rows K .. R - 1, columns 0 .. K - 1 of each FP64 matrix (at most max_entries each).
+void launch_gj_zero_bl(const GJDesc* d, int nmat, long long max_entries, double* work, cudaStream_t s);
 template <typename T>
 void launch_gj_panel(const GJDesc* d, int nmat, int maxK, T* work, int* perm, T* pinv, int c0,
                      int nb, int* status, cudaStream_t s);
@@ -288,7 +290,7 @@ void launch_gemm_tc32_pieces(const GemmItem* items, int nitems, const float* A, 
 // item's first step, prefix sums of ceil(K / 16))
 long long gemm_tc_digit_bytes(long long steps);
 void launch_gemm_tc_digitize(const GemmItem* items, int nitems, int trans, const double* A, const long long* astep,
-                             unsigned char* adig, int* aer, cudaStream_t s);
+                             unsigned char* adig, int* aer, cudaStream_t s, bool negate = false);
 
 // Split-K partial products: rows [0, M) of one output block were computed in nsplit K
 // ranges into the partial buffer P (rows p_row + j * M + i); the reduction writes

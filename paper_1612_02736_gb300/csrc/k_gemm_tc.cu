@@ -49,7 +49,7 @@ constexpr int GN = 32;      // right-hand sides per unit
 constexpr int GS = 9;       // digits per entry
 constexpr int GD = 9;       // kept diagonals d = 2 .. 10
 constexpr int GKMAX = 448;  // longest K with exact FP32 diagonal sums
-constexpr int GST = 3;      // K-step stages
+constexpr int GST = 4;      // K-step stages
 constexpr int G_THREADS = 544;  // 17 warps (5 on one SM sub-partition: at most 96 registers)
 constexpr int G_PROD = 384;    // producer threads (12 warps, one task each)
 constexpr int G_EPI = 128;     // epilogue threads (4 warps)
@@ -72,13 +72,17 @@ constexpr int GTASK = (GR + GN) * 4;  // producer tasks per K step: 4 consecutiv
 constexpr int GPF = 2;                // K steps the entry copies run ahead of the digits
 constexpr int GRAW = GPF + 1;         // raw entry slots
 
+constexpr int GSTG = GR * 33;  // epilogue staging: one unit's diagonal sums, row pitch 33 words
+
 struct GShared {
   GStage st[GST];
   double raw[GRAW][GTASK][4];  // the entries of a K step, per producer task
+  uint32_t stg[GD][GSTG];      // the epilogue's copy of the unit's TMEM accumulators
   unsigned long long sfull[GST], sfree[GST], tfull, tfree, mdone;
   unsigned int tmem_base;
   int abort_flag;
 };
+static_assert(sizeof(GShared) + 1024 <= 232448, "shared memory of the product kernel");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -317,13 +321,15 @@ __global__ void __launch_bounds__(256) gemm_scales_kernel(const GemmItem* __rest
 }
 
 // The operator's digit planes of every K step of one item (one block per item), in the
-// stage layout, at adig + astep[item] * GASTEP, and its 64 row exponents at aer[item * 64].
-// Operators do not change between solves, so their digits are formed once.
+// stage layout, at adig + astep[item] * GASTEP, and its 64 row exponents at aer[item * 64],
+// of sgn A (sgn = +-1, exact).  Operators do not change between solves, so their digits are
+// formed once.
 template <bool TRANS>
 __global__ void __launch_bounds__(256) gemm_digits_kernel(const GemmItem* __restrict__ items,
                                                           const double* __restrict__ A,
                                                           const long long* __restrict__ astep,
-                                                          unsigned char* __restrict__ adig, int* __restrict__ aer) {
+                                                          unsigned char* __restrict__ adig, int* __restrict__ aer,
+                                                          double sgn) {
   const long long item = blockIdx.x;
   const GemmItem it = items[item];
   const int t = threadIdx.x;
@@ -360,7 +366,7 @@ __global__ void __launch_bounds__(256) gemm_digits_kernel(const GemmItem* __rest
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int k = c * 16 + kg + q;
-        v[q] = k < it.K ? a_at<TRANS>(it, A, row, k) : 0.0;
+        v[q] = k < it.K ? sgn * a_at<TRANS>(it, A, row, k) : 0.0;
       }
       write_digits4(v, er[row], pl, GAPL, kmaj(row, kg));
     }
@@ -580,7 +586,10 @@ __global__ void __launch_bounds__(G_THREADS, 1) gemm_tc_kernel(const GemmItem* _
     }
   } else {
     // ---------------- epilogue: warps 0, 1, 4, 5; row = 32 (w % 4) + lane, right-hand
-    // sides 16 g .. 16 g + 15 with g = w / 4, four at a time
+    // sides 16 g .. 16 g + 15 with g = w / 4.  The unit's 9 diagonal sums are first copied
+    // from TMEM to this thread's shared-memory row (pitch 33 words: the lanes' rows fall in
+    // distinct banks), which frees TMEM for the next unit's products at once; the exact
+    // recombination then runs from shared memory while those products are issued.
     const int row = q4 * 32 + lane, g = warp >> 2;
     int nu = 0;
     for (long long u = blockIdx.x; u < total; u += gridDim.x, ++nu) {
@@ -590,39 +599,45 @@ __global__ void __launch_bounds__(G_THREADS, 1) gemm_tc_kernel(const GemmItem* _
       const int er = cached ? aer[(u / nnb) * GR + row] : sc[row];
       if (!warp_wait(&sh.tfull, nu & 1, abort_flag, status)) break;
       asm volatile("tcgen05.fence::after_thread_sync;");
-      const long long crow = row < it.M ? (long long)map_row(idx, it.c_idx, it.c_row, row) * nrhs : 0;
+#pragma unroll 1
+      for (int d = 0; d < GD; ++d) {
+        const uint32_t addr = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(d * GN + 16 * g);
+        uint32_t v[16];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(addr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+        uint32_t* dst = sh.stg[d] + row * 33 + 16 * g;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) dst[j] = v[j];
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      mb_arrive(&sh.tfree);  // TMEM read: the next unit's products may start
+      if (row >= it.M) continue;
+      const long long crow = (long long)map_row(idx, it.c_idx, it.c_row, row) * nrhs;
 #pragma unroll 1
       for (int hh = 0; hh < 4; ++hh) {
         const int jb = 16 * g + 4 * hh;
         int ec[4];
+        double cv[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) ec[j] = sc[GR + jb + j];
-        uint32_t v[GD][4];
-#pragma unroll
-        for (int d = 0; d < GD; ++d) {
-          const uint32_t addr = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(d * GN + jb);
-          uint32_t* vd = v[d];
-          asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
-                       : "=r"(vd[0]), "=r"(vd[1]), "=r"(vd[2]), "=r"(vd[3])
-                       : "r"(addr));
+        for (int j = 0; j < 4; ++j) {  // the group's loads first: their latency overlaps the recombination
+          const int n = n0 + jb + j;
+          ec[j] = sc[GR + jb + j];
+          cv[j] = (beta != 0.0 && n < nrhs) ? C[crow + n] : 0.0;
         }
-        asm volatile("tcgen05.wait::ld.sync.aligned;");
-        if (hh == 3) {
-          asm volatile("tcgen05.fence::before_thread_sync;");
-          mb_arrive(&sh.tfree);  // TMEM read: the next unit's products may start
-        }
-        if (row < it.M) {
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const int n = n0 + jb + j;
-            if (n >= nrhs) continue;
-            uint32_t dj[GD];
+        for (int j = 0; j < 4; ++j) {
+          const int n = n0 + jb + j;
+          if (n >= nrhs) continue;
+          uint32_t dj[GD];
 #pragma unroll
-            for (int d = 0; d < GD; ++d) dj[d] = v[d][j];
-            double r = recombine9(dj, er, ec[j]);
-            if (it.add_row >= 0) r += Add[(long long)(it.add_row + row) * nrhs + n];
-            C[crow + n] = (beta != 0.0 ? beta * C[crow + n] : 0.0) + r;
-          }
+          for (int d = 0; d < GD; ++d) dj[d] = sh.stg[d][row * 33 + jb + j];
+          double r = recombine9(dj, er, ec[j]);
+          if (it.add_row >= 0) r += Add[(long long)(it.add_row + row) * nrhs + n];
+          C[crow + n] = (beta != 0.0 ? beta * cv[j] : 0.0) + r;
         }
       }
     }
@@ -696,10 +711,11 @@ bool launch_gemm_tc(const GemmItem* items, int nitems, int trans, const double* 
 long long gemm_tc_digit_bytes(long long steps) { return steps * GASTEP; }
 
 void launch_gemm_tc_digitize(const GemmItem* items, int nitems, int trans, const double* A, const long long* astep,
-                             unsigned char* adig, int* aer, cudaStream_t s) {
+                             unsigned char* adig, int* aer, cudaStream_t s, bool negate) {
   if (nitems <= 0) return;
-  if (trans) gemm_digits_kernel<true><<<(unsigned)nitems, 256, 0, s>>>(items, A, astep, adig, aer);
-  else gemm_digits_kernel<false><<<(unsigned)nitems, 256, 0, s>>>(items, A, astep, adig, aer);
+  const double sgn = negate ? -1.0 : 1.0;
+  if (trans) gemm_digits_kernel<true><<<(unsigned)nitems, 256, 0, s>>>(items, A, astep, adig, aer, sgn);
+  else gemm_digits_kernel<false><<<(unsigned)nitems, 256, 0, s>>>(items, A, astep, adig, aer, sgn);
 }
 
 }  // namespace hps

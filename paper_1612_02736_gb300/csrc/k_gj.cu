@@ -54,6 +54,19 @@ __global__ void gj_init_kernel(const GJDesc* __restrict__ d, int* __restrict__ p
   for (int i = threadIdx.x; i < md.K; i += blockDim.x) perm[md.perm_off + i] = i;
 }
 
+// Zeroes the bottom-left block (rows K .. R - 1, columns 0 .. K - 1) of every matrix: the
+// blocked elimination then adds (-C) Top into it (matrix blockIdx.y).
+__global__ void gj_zero_bl_kernel(const GJDesc* __restrict__ d, double* __restrict__ work) {
+  const GJDesc md = d[blockIdx.y];
+  const int K = md.K, R = md.R;
+  const long long n = (long long)(R - K) * K;
+  double* M = work + md.off + (long long)K * R;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e / K;
+    M[i * R + (e - i * K)] = 0.0;
+  }
+}
+
 // Magnitude order of floating-point values as integers: the bit pattern of |v| read as an
 // unsigned integer is monotone in |v| (finite values), so pivot searches run on the integer
 // pipe instead of the scarce FP64 one.
@@ -1379,6 +1392,12 @@ __global__ void __launch_bounds__(256) gj_extract_kernel(const GJDesc* __restric
 template <typename T>
 void launch_gj_init(const GJDesc* d, int nmat, int* perm, cudaStream_t s) {
   gj_init_kernel<T><<<nmat, 256, 0, s>>>(d, perm);
+}
+
+void launch_gj_zero_bl(const GJDesc* d, int nmat, long long max_entries, double* work, cudaStream_t s) {
+  if (nmat <= 0 || max_entries <= 0) return;
+  const long long bx = std::min<long long>((max_entries + 255) / 256, 64);
+  gj_zero_bl_kernel<<<dim3((unsigned)bx, (unsigned)nmat), 256, 0, s>>>(d, work);
 }
 
 template <typename T>
