@@ -482,7 +482,8 @@ def run_gpu(args, rank, world, local):
         "mixed": {"rel_linf_vs_fp64": rel_err, "ir_steps": int(np.median(iters)) if iters else None},
         "gpu_launches": launches, "gpu_launches_per_step": launches / args.steps,
         "roofline": roof,
-        "kernels": sorted([{"name": r["name"], "launches": r["launches"], "ms": round(r["ms"] / args.steps, 4)}
+        "kernels": sorted([{"name": r["name"], "launches": round(r["launches"] / args.steps, 2),
+                            "ms": round(r["ms"] / args.steps, 4)}
                            for r in table], key=lambda r: -r["ms"])[:12],
         "clocks": clk.summary(),
     }
