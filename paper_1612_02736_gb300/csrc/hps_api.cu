@@ -234,6 +234,11 @@ struct Level {
   ItemSet schur;
   std::vector<int> schur_chunk;
   int schur_R = 0;
+  BGroup* sgrp = nullptr;        // the product's vector groups (one per box and K chunk)
+  int n_sgrp = 0;
+  long long* sbblk = nullptr;    // per item: its group's first vector digit block
+  int* sbexo = nullptr;          // per item: its group's first column exponent
+  long long sb_blocks = 0;       // vector digit blocks of the level
   // solve
   UpGather* ug = nullptr;
   int ug_maxrows = 0;
@@ -506,6 +511,9 @@ struct LevelHost {
   std::vector<GJDesc> gj, gj_top;
   std::vector<GemmItem> schur;
   std::vector<int> schur_chunk;
+  std::vector<BGroup> sgrp;
+  std::vector<long long> sbblk;
+  std::vector<int> sbexo;
   std::vector<MergeDesc> md;
   std::vector<long long> tl, bl, tr, br;
   std::vector<UpGather> ug;
@@ -949,6 +957,9 @@ void block_plan(LevelHost& pd) {
   pd.gj_top.clear();
   pd.schur.clear();
   pd.schur_chunk.clear();
+  pd.sgrp.clear();
+  pd.sbblk.clear();
+  pd.sbexo.clear();
   if (pd.gj.empty()) return;
   const int R0 = pd.gj[0].R;
   int kmax = 0;
@@ -965,6 +976,16 @@ void block_plan(LevelHost& pd) {
       if (ks >= g.K) continue;
       const int K = std::min(kc, g.K - ks), k12 = g.R - g.K;
       const int base = (int)(g.off / g.R);  // first row of the matrix, rows of length R
+      // the items of this box and chunk gather the same top rows: one vector digit group
+      const int ncb = (g.R + 31) / 32;
+      BGroup bg;
+      bg.b0_row = base;
+      bg.b0_idx = g.perm_off + ks;
+      bg.K = K;
+      bg.ex0 = (int)pd.sgrp.size() * ncb * 32;
+      bg.blk0 = pd.sgrp.empty() ? 0
+                                : pd.sgrp.back().blk0 + (long long)ncb * ((pd.sgrp.back().K + 15) / 16);
+      pd.sgrp.push_back(bg);
       for (int r0 = 0; r0 < k12; r0 += ROWBLK) {
         GemmItem it{};
         it.a_off = g.off + (long long)(g.K + r0) * g.R + ks;  // -C, rows r0.., columns ks..
@@ -980,6 +1001,8 @@ void block_plan(LevelHost& pd) {
         it.c_idx = -1;
         it.add_row = -1;
         pd.schur.push_back(it);
+        pd.sbblk.push_back(bg.blk0);
+        pd.sbexo.push_back(bg.ex0);
       }
     }
   }
@@ -1035,6 +1058,13 @@ void upload_plan(hps_handle* h, const HostPlan& hp, cudaStream_t s) {
     }
     lv.schur_chunk = pd.schur_chunk;
     lv.schur_R = pd.gj.empty() ? 0 : pd.gj[0].R;
+    lv.n_sgrp = (int)pd.sgrp.size();
+    lv.sgrp = pd.sgrp.empty() ? nullptr : upload(h->al, s, pd.sgrp, h->owned);
+    lv.sbblk = pd.sbblk.empty() ? nullptr : upload(h->al, s, pd.sbblk, h->owned);
+    lv.sbexo = pd.sbexo.empty() ? nullptr : upload(h->al, s, pd.sbexo, h->owned);
+    lv.sb_blocks = 0;
+    if (!pd.sgrp.empty())
+      lv.sb_blocks = pd.sgrp.back().blk0 + (long long)((lv.schur_R + 31) / 32) * ((pd.sgrp.back().K + 15) / 16);
     lv.md = upload(h->al, s, pd.md, h->owned);
     lv.off_tl = upload(h->al, s, pd.tl, h->owned);
     lv.off_bl = upload(h->al, s, pd.bl, h->owned);
@@ -1307,6 +1337,20 @@ std::string validate_plan(const hps_handle* h, const HostPlan& hp) {
             it.b0_idx + it.K > lv.perm_elems || it.b0_row < 0 || it.b0_row + (long long)R > wrows || it.c_idx != -1 ||
             it.c_row < 0 || (long long)it.c_row + it.M > wrows || it.add_row != -1)
           pc.fail("blocked elimination: product item out of range");
+      const int ncb = (R + 31) / 32;
+      long long blocks = 0;
+      for (const BGroup& g : pd.sgrp) {
+        if (g.K < 1 || g.K > 448 || g.b0_idx < 0 || g.b0_idx + g.K > lv.perm_elems || g.b0_row < 0 ||
+            g.b0_row + (long long)R > wrows || g.blk0 != blocks)
+          pc.fail("blocked elimination: vector group out of range");
+        blocks += (long long)ncb * ((g.K + 15) / 16);
+      }
+      if (pd.sbblk.size() != pd.schur.size() || pd.sbexo.size() != pd.schur.size())
+        pc.fail("blocked elimination: vector group tables");
+      for (size_t i = 0; i < pd.schur.size() && i < pd.sbblk.size() && i < pd.sbexo.size(); ++i)
+        if (pd.sbblk[i] < 0 || pd.sbblk[i] + (long long)ncb * ((pd.schur[i].K + 15) / 16) > blocks || pd.sbexo[i] < 0 ||
+            (long long)pd.sbexo[i] + ncb * 32 > (long long)pd.sgrp.size() * ncb * 32)
+          pc.fail("blocked elimination: item's vector group out of range");
     }
   }
   return pc.err;
@@ -1591,20 +1635,18 @@ void build_stage(hps_handle* h, const double* coeffs, cudaStream_t s) {
         int* pm = (int*)get((size_t)std::max(1, lv.perm_elems) * sizeof(int));
         double* pi = (double*)get((size_t)nmat * 256 * sizeof(double));
         double* pr = (double*)get((size_t)nmat * 16 * lv.maxR * sizeof(double));
-        // blocked elimination: the top rows' digit planes of -C and the product's exponent
-        // buffer, sized once for the level
+        // blocked elimination: the digit planes of -C (rows) and of the eliminated top rows
+        // (columns) with their exponents, sized once for the level; the product forms no
+        // digits and needs no exponent pass
         const ItemSet& sc = lv.schur;
-        unsigned char* sdig = nullptr;
-        int *ser = nullptr, *sscale = nullptr;
-        long long sunits = 0;
+        unsigned char *sdig = nullptr, *sbdig = nullptr;
+        int *ser = nullptr, *sbex = nullptr;
         std::vector<std::array<int, 3>> rk_top;
         if (sc.n > 0) {
-          for (size_t c = 0; c + 1 < lv.schur_chunk.size(); ++c)
-            sunits = std::max<long long>(sunits, (long long)(lv.schur_chunk[c + 1] - lv.schur_chunk[c]) *
-                                                     ((lv.schur_R + 31) / 32));
           sdig = (unsigned char*)get((size_t)gemm_tc_digit_bytes(sc.dsteps));
           ser = (int*)get((size_t)sc.n * 64 * sizeof(int));
-          sscale = (int*)get((size_t)gemm_tc_scale_bytes(sunits));
+          sbdig = (unsigned char*)get((size_t)gemm_tc_bdigit_bytes(lv.sb_blocks));
+          sbex = (int*)get((size_t)lv.n_sgrp * ((lv.schur_R + 31) / 32) * 32 * sizeof(int));
           for (auto m : rk) rk_top.push_back({m[0], m[1], m[1]});
         }
         auto elim = [&](int nb) {
@@ -1620,6 +1662,9 @@ void build_stage(hps_handle* h, const double* coeffs, cudaStream_t s) {
           const long long k12max = lv.maxR - 1;
           TIMED("gj_schur_digits_f64", 0, 0,
                 launch_gemm_tc_digitize(sc.dev, sc.n, 0, w, sc.dstep, sdig, ser, s, true));
+          TIMED("gj_schur_digits_f64", 0, 0,
+                launch_gemm_tc_bdigitize(lv.sgrp, lv.n_sgrp, (lv.schur_R + 31) / 32, w, pm, lv.schur_R, sbdig, sbex,
+                                         s));
           TIMED("gj_schur_zero_f64", 0, 0, launch_gj_zero_bl(lv.gj, nmat, k12max * lv.maxK, w, s));
           for (size_t c = 0; c + 1 < lv.schur_chunk.size(); ++c) {
             const int b = lv.schur_chunk[c], e = lv.schur_chunk[c + 1];
@@ -1627,13 +1672,15 @@ void build_stage(hps_handle* h, const double* coeffs, cudaStream_t s) {
             dg.dig = sdig;
             dg.step = sc.dstep + b;
             dg.er = ser + (long long)b * 64;
+            dg.bdig = sbdig;
+            dg.bblk = lv.sbblk + b;
+            dg.bexo = lv.sbexo + b;
+            dg.bex = sbex;
             GemmCtx cx;
             cx.maxK = 448;
             cx.maxKv = 448;
             cx.status = h->d_status;
             cx.dg = &dg;
-            cx.tc_scales = sscale;
-            cx.tc_units = sunits;
             bool ok = false;
             TIMED("gj_schur_f64", 2.0 * sc.elems * lv.schur_R / std::max<size_t>(1, lv.schur_chunk.size() - 1), 0,
                   ok = launch_gemm_tc(sc.dev + b, e - b, 0, w, w, nullptr, w, nullptr, pm, lv.schur_R, 1.0, s, cx));

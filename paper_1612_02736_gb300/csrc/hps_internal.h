@@ -223,10 +223,26 @@ void launch_bgemm(const BGemm* d, int n, int maxM, int maxN, const double* A, co
 
 // The operator digit planes of an item set, formed once (launch_gemm_tc_digitize): item i's
 // K steps at dig + step[i] * gemm_tc_digit_bytes(1), its 64 row exponents at er + 64 i.
+// Optionally (FP64 products, with the operator digits) the vectors' digit planes too,
+// formed once for groups of items that gather the same vector rows over the same K
+// (launch_gemm_tc_bdigitize): for item i, column block nb (32 columns) and K step c at
+// bdig + (bblk[i] + nb ceil(K / 16) + c) * gemm_tc_bdigit_bytes(1), the column exponents
+// of column n at bex[bexo[i] + n]; the product kernel then forms no digits at all.
 struct GemmDigits {
   const unsigned char* dig = nullptr;
   const long long* step = nullptr;
   const int* er = nullptr;
+  const unsigned char* bdig = nullptr;
+  const long long* bblk = nullptr;
+  const int* bexo = nullptr;
+  const int* bex = nullptr;
+};
+// A group of items sharing their gathered vectors: rows b0_row + idx[b0_idx + k],
+// k < K (first segment only), its digit blocks from blk0 and exponents from ex0.
+struct BGroup {
+  int b0_row, b0_idx, K;
+  int ex0;
+  long long blk0;
 };
 
 // Options of one batched product launch.
@@ -289,6 +305,11 @@ void launch_gemm_tc32_pieces(const GemmItem* items, int nitems, const float* A, 
 // bytes of the digit planes of `steps` K steps; fill adig / aer for the items (astep: each
 // item's first step, prefix sums of ceil(K / 16))
 long long gemm_tc_digit_bytes(long long steps);
+long long gemm_tc_bdigit_bytes(long long blocks);
+// The vectors' digit planes and column exponents of ngroups groups (ncb column blocks of 32
+// each, nrhs columns of B0 with rows b0_row + idx[b0_idx + k]).
+void launch_gemm_tc_bdigitize(const BGroup* groups, int ngroups, int ncb, const double* B0, const int* idx, int nrhs,
+                              unsigned char* bdig, int* bex, cudaStream_t s);
 void launch_gemm_tc_digitize(const GemmItem* items, int nitems, int trans, const double* A, const long long* astep,
                              unsigned char* adig, int* aer, cudaStream_t s, bool negate = false);
 

@@ -67,6 +67,7 @@ struct GStage {
   unsigned char B[GS][GN * 32];  // 32 columns x 16 k
 };
 
+constexpr int GBSTEP = GS * GN * 32;  // bytes of a K step's B planes (cached vectors)
 constexpr int GSC = GR + GN;  // exponents per unit: 64 rows, then 32 columns
 constexpr int GTASK = (GR + GN) * 4;  // producer tasks per K step: 4 consecutive k of a row or column
 constexpr int GPF = 2;                // K steps the entry copies run ahead of the digits
@@ -373,6 +374,47 @@ __global__ void __launch_bounds__(256) gemm_digits_kernel(const GemmItem* __rest
   }
 }
 
+// The vectors' digit planes of one group (blockIdx.y) and column block (blockIdx.x): the 32
+// columns' exponents over the group's K rows, then every K step's planes in the stage
+// layout, exactly as the product kernel's producers would form them.
+__global__ void __launch_bounds__(256) gemm_bdigits_kernel(const BGroup* __restrict__ groups,
+                                                           const double* __restrict__ B0,
+                                                           const int* __restrict__ idx, int nrhs,
+                                                           unsigned char* __restrict__ bdig, int* __restrict__ bex) {
+  const BGroup g = groups[blockIdx.y];
+  const int nb = blockIdx.x, t = threadIdx.x;
+  __shared__ int part[256];
+  __shared__ int ec[GN];
+  {
+    const int nl = t & 31, ph = t >> 5, n = nb * GN + nl;
+    int m = 0;
+    if (n < nrhs) {
+#pragma unroll 4
+      for (int k = ph; k < g.K; k += 8) m = max(m, bexp(B0[(long long)(g.b0_row + idx[g.b0_idx + k]) * nrhs + n]));
+    }
+    part[ph * 32 + nl] = m;
+  }
+  __syncthreads();
+  if (t < GN) {
+    int m = 0;
+    for (int ph = 0; ph < 8; ++ph) m = max(m, part[ph * 32 + t]);
+    ec[t] = m;
+    bex[g.ex0 + nb * GN + t] = m;
+  }
+  __syncthreads();
+  const int nk = (g.K + 15) >> 4;
+  const int task = t & 127, col = task >> 2, kg = (task & 3) * 4, n = nb * GN + col;
+  for (int c = t >> 7; c < nk; c += 2) {
+    double v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int k = c * 16 + kg + q;
+      v[q] = (n < nrhs && k < g.K) ? B0[(long long)(g.b0_row + idx[g.b0_idx + k]) * nrhs + n] : 0.0;
+    }
+    write_digits4(v, ec[col], bdig + (g.blk0 + (long long)nb * nk + c) * GBSTEP, GN * 32, kmaj(col, kg));
+  }
+}
+
 template <bool TRANS>
 __global__ void __launch_bounds__(G_THREADS, 1) gemm_tc_kernel(const GemmItem* __restrict__ items, int nitems,
                                                                 const double* __restrict__ A,
@@ -384,6 +426,10 @@ __global__ void __launch_bounds__(G_THREADS, 1) gemm_tc_kernel(const GemmItem* _
                                                                 const unsigned char* __restrict__ adig,
                                                                 const long long* __restrict__ astep,
                                                                 const int* __restrict__ aer,
+                                                                const unsigned char* __restrict__ bdig,
+                                                                const long long* __restrict__ bblk,
+                                                                const int* __restrict__ bexo,
+                                                                const int* __restrict__ bex,
                                                                 int* __restrict__ status) {
   extern __shared__ __align__(1024) unsigned char g_raw[];
   GShared& sh = *reinterpret_cast<GShared*>(g_raw);
@@ -393,9 +439,10 @@ __global__ void __launch_bounds__(G_THREADS, 1) gemm_tc_kernel(const GemmItem* _
   // cached operator digits (adig): the producers form only the vectors' digits (threads
   // 256 .. 383) and one thread copies each K step's A planes
   const bool cached = adig != nullptr;
+  const bool bcached = cached && bdig != nullptr;  // both operands' digits cached: copies only
   if (tid == 0) {
     for (int b = 0; b < GST; ++b) {
-      mb_init(&sh.sfull[b], cached ? GN * 4 + 1 : G_PROD);
+      mb_init(&sh.sfull[b], bcached ? 1 : (cached ? GN * 4 + 1 : G_PROD));
       mb_init(&sh.sfree[b], 1);
     }
     mb_init(&sh.tfull, 1);
@@ -477,9 +524,10 @@ __global__ void __launch_bounds__(G_THREADS, 1) gemm_tc_kernel(const GemmItem* _
     const int pw = warp < 8 ? (warp >> 2) * 2 + (q4 - 2) : warp - 4;
     const int pt = pw * 32 + lane;
     const int ntask = pt + G_PROD < GTASK ? 2 : 1;  // 1 while G_PROD = GTASK
-    if (cached && pt < GR * 4) {
-      // the operator's digit planes come from the cache: thread 0 copies each K step's
-      // planes (one bulk copy) and arms the stage's barrier with their bytes
+    if (cached && (bcached || pt < GR * 4)) {
+      // the operator's digit planes (and with bcached the vectors') come from the caches:
+      // thread 0 copies each K step's planes (bulk copies) and arms the stage's barrier
+      // with their bytes
       if (pt == 0) {
         long long ks = 0;
         bool stop = false;
@@ -487,14 +535,16 @@ __global__ void __launch_bounds__(G_THREADS, 1) gemm_tc_kernel(const GemmItem* _
           const long long item = u / nnb;
           const int nk = (items[item].K + 15) >> 4;
           const unsigned char* src = adig + astep[item] * GASTEP;
+          const unsigned char* bsrc = bcached ? bdig + (bblk[item] + (u % nnb) * nk) * GBSTEP : nullptr;
           for (int c = 0; c < nk; ++c, ++ks) {
             const int st = (int)(ks % GST);
             if (ks >= GST && !mb_wait(&sh.sfree[st], (int)((ks / GST) - 1) & 1, abort_flag, status)) {
               stop = true;
               break;
             }
-            mb_expect_arrive(&sh.sfull[st], GASTEP);
+            mb_expect_arrive(&sh.sfull[st], bcached ? GASTEP + GBSTEP : GASTEP);
             bulk_load(sh.st[st].A[0], src + (long long)c * GASTEP, GASTEP, &sh.sfull[st]);
+            if (bcached) bulk_load(sh.st[st].B[0], bsrc + (long long)c * GBSTEP, GBSTEP, &sh.sfull[st]);
           }
         }
         // the copies issued have landed before the block exits
@@ -595,7 +645,7 @@ __global__ void __launch_bounds__(G_THREADS, 1) gemm_tc_kernel(const GemmItem* _
     for (long long u = blockIdx.x; u < total; u += gridDim.x, ++nu) {
       const GemmItem it = items[u / nnb];
       const int n0 = (int)(u % nnb) * GN;
-      const int* sc = scales + u * GSC;
+      const int* sc = scales ? scales + u * GSC : nullptr;  // none when both operands are cached
       const int er = cached ? aer[(u / nnb) * GR + row] : sc[row];
       if (!warp_wait(&sh.tfull, nu & 1, abort_flag, status)) break;
       asm volatile("tcgen05.fence::after_thread_sync;");
@@ -625,7 +675,7 @@ __global__ void __launch_bounds__(G_THREADS, 1) gemm_tc_kernel(const GemmItem* _
 #pragma unroll
         for (int j = 0; j < 4; ++j) {  // the group's loads first: their latency overlaps the recombination
           const int n = n0 + jb + j;
-          ec[j] = sc[GR + jb + j];
+          ec[j] = bcached ? bex[bexo[u / nnb] + n] : sc[GR + jb + j];
           cv[j] = (beta != 0.0 && n < nrhs) ? C[crow + n] : 0.0;
         }
 #pragma unroll
@@ -686,29 +736,45 @@ bool launch_gemm_tc(const GemmItem* items, int nitems, int trans, const double* 
                     cudaStream_t s, const GemmCtx& cx) {
   if (nitems <= 0) return true;
   const long long units = (long long)nitems * ((nrhs + GN - 1) / GN);
-  if (!cx.tc_scales || units > cx.tc_units) return false;
-  const int nsm = gemm_tc_nsm();
-  if (!nsm) return false;
-  const int grid = (int)std::min<long long>(nsm, units);
   const GemmDigits* dg = cx.dg;
   const unsigned char* adig = dg ? dg->dig : nullptr;
   const long long* astep = dg ? dg->step : nullptr;
   const int* aer = dg ? dg->er : nullptr;
+  // both operands' digits cached (and not transposed): no exponent pass, no scales buffer
+  const bool bc = adig && dg->bdig && dg->bblk && dg->bexo && dg->bex && !trans;
+  if (!bc && (!cx.tc_scales || units > cx.tc_units)) return false;
+  const int nsm = gemm_tc_nsm();
+  if (!nsm) return false;
+  const int grid = (int)std::min<long long>(nsm, units);
   const int rows = adig ? 0 : 1;
-  int* scales = cx.tc_scales;
+  int* scales = bc ? nullptr : cx.tc_scales;
+  const unsigned char* bdig = bc ? dg->bdig : nullptr;
+  const long long* bblk = bc ? dg->bblk : nullptr;
+  const int* bexo = bc ? dg->bexo : nullptr;
+  const int* bex = bc ? dg->bex : nullptr;
   if (trans) {
     gemm_scales_kernel<true><<<(unsigned)units, 256, 0, s>>>(items, A, B0, B1, idx, nrhs, scales, rows);
     gemm_tc_kernel<true><<<grid, G_THREADS, sizeof(GShared), s>>>(items, nitems, A, B0, B1, C, Add, idx, nrhs, beta,
-                                                                  scales, adig, astep, aer, cx.status);
+                                                                  scales, adig, astep, aer, nullptr, nullptr,
+                                                                  nullptr, nullptr, cx.status);
   } else {
-    gemm_scales_kernel<false><<<(unsigned)units, 256, 0, s>>>(items, A, B0, B1, idx, nrhs, scales, rows);
+    if (!bc) gemm_scales_kernel<false><<<(unsigned)units, 256, 0, s>>>(items, A, B0, B1, idx, nrhs, scales, rows);
     gemm_tc_kernel<false><<<grid, G_THREADS, sizeof(GShared), s>>>(items, nitems, A, B0, B1, C, Add, idx, nrhs, beta,
-                                                                   scales, adig, astep, aer, cx.status);
+                                                                   scales, adig, astep, aer, bdig, bblk, bexo, bex,
+                                                                   cx.status);
   }
   return true;
 }
 
 long long gemm_tc_digit_bytes(long long steps) { return steps * GASTEP; }
+
+long long gemm_tc_bdigit_bytes(long long blocks) { return blocks * GBSTEP; }
+
+void launch_gemm_tc_bdigitize(const BGroup* groups, int ngroups, int ncb, const double* B0, const int* idx, int nrhs,
+                              unsigned char* bdig, int* bex, cudaStream_t s) {
+  if (ngroups <= 0 || ncb <= 0) return;
+  gemm_bdigits_kernel<<<dim3((unsigned)ncb, (unsigned)ngroups), 256, 0, s>>>(groups, B0, idx, nrhs, bdig, bex);
+}
 
 void launch_gemm_tc_digitize(const GemmItem* items, int nitems, int trans, const double* A, const long long* astep,
                              unsigned char* adig, int* aer, cudaStream_t s, bool negate) {
