@@ -115,7 +115,6 @@ __device__ __forceinline__ void gj_panel_f32_select(const GJDesc& md, double* __
   __shared__ int red_i[32];
   __shared__ double colscale[NBMAX];
   __shared__ double B[NBMAX][NBMAX + 1];
-  __shared__ int piv_row;
   for (int i = tid; i < nrows; i += bs) pr[i] = pm[i];
   __syncthreads();
   for (int e = tid; e < nrows * nb; e += bs) {
@@ -130,21 +129,23 @@ __device__ __forceinline__ void gj_panel_f32_select(const GJDesc& md, double* __
     for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if (lane == 0) colscale[j] = (double)__uint_as_float(mx);
   }
+  // pivot of column j: the largest |P_ij|, i >= j, the first row among equals.  Each thread
+  // scans the rows it eliminates (i = j + tid, j + tid + bs, ...), so the scan of column
+  // j + 1 rides on the elimination of column j; two block barriers per column.
+  unsigned int best = 0;
+  int bi = nrows;
+  for (int i = tid; i < nrows; i += bs) {
+    const unsigned int v = __float_as_uint(P[i * ldp]) & 0x7FFFFFFFu;
+    if (bi == nrows || v > best) { best = v; bi = i; }
+  }
   for (int j = 0; j < nb; ++j) {
-    // pivot: the largest |P_ij|, i >= j, the first row among equals
-    unsigned int best = 0;
-    int bi = nrows;
-    for (int i = j + tid; i < nrows; i += bs) {
-      const unsigned int v = __float_as_uint(P[i * ldp + j]) & 0x7FFFFFFFu;
-      if (bi == nrows || v > best) { best = v; bi = i; }
-    }
     for (int o = 16; o > 0; o >>= 1) {
       const unsigned int ov = __shfl_down_sync(0xffffffffu, best, o);
       const int oi = __shfl_down_sync(0xffffffffu, bi, o);
       if (oi < nrows && (bi == nrows || ov > best || (ov == best && oi < bi))) { best = ov; bi = oi; }
     }
     if (lane == 0) { red_v[warp] = best; red_i[warp] = bi; }
-    __syncthreads();
+    __syncthreads();  // every thread's eliminations of column j - 1 and its scan are in
     if (warp == 0) {
       best = lane < nwarp ? red_v[lane] : 0u;
       bi = lane < nwarp ? red_i[lane] : nrows;
@@ -153,27 +154,31 @@ __device__ __forceinline__ void gj_panel_f32_select(const GJDesc& md, double* __
         const int oi = __shfl_down_sync(0xffffffffu, bi, o);
         if (oi < nrows && (bi == nrows || ov > best || (ov == best && oi < bi))) { best = ov; bi = oi; }
       }
+      const int r = __shfl_sync(0xffffffffu, bi < nrows ? bi : j, 0);
       if (lane == 0) {
-        const int ib = bi < nrows ? bi : j;
-        piv_row = ib;
-        const int t = pr[j]; pr[j] = pr[ib]; pr[ib] = t;
+        const int t = pr[j]; pr[j] = pr[r]; pr[r] = t;
+      }
+      if (r != j && lane < nb) {
+        const float t = P[j * ldp + lane]; P[j * ldp + lane] = P[r * ldp + lane]; P[r * ldp + lane] = t;
       }
     }
-    __syncthreads();
-    const int r = piv_row;
-    if (r != j && tid < nb) {
-      const float t = P[j * ldp + tid]; P[j * ldp + tid] = P[r * ldp + tid]; P[r * ldp + tid] = t;
-    }
-    __syncthreads();
+    __syncthreads();  // the pivot row is in place
     const float pv = P[j * ldp + j];
     const float inv = pv != 0.f ? 1.f / pv : 0.f;
+    best = 0;
+    bi = nrows;
+    const bool next = j + 1 < nb;
     for (int i = j + 1 + tid; i < nrows; i += bs) {
       const float l = P[i * ldp + j] * inv;
       P[i * ldp + j] = l;
       for (int c = j + 1; c < nb; ++c) P[i * ldp + c] = fmaf(-l, P[j * ldp + c], P[i * ldp + c]);
+      if (next) {
+        const unsigned int v = __float_as_uint(P[i * ldp + j + 1]) & 0x7FFFFFFFu;
+        if (bi == nrows || v > best) { best = v; bi = i; }
+      }
     }
-    __syncthreads();
   }
+  __syncthreads();
   // the pivot block in FP64 (rows in pivot order), inverted in place by Gauss-Jordan
   // elimination without further pivoting, one thread per entry; its pivots are those of the
   // block's LU, tested against 64 eps of their column's scale
