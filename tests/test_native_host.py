@@ -111,10 +111,13 @@ def test_python_package_fails_loudly_without_library(tmp_path, monkeypatch):
 
 @pytest.mark.parametrize("nx,ny,p,prec,store", [(1, 1, 8, 0, 1), (2, 1, 6, 0, 1), (2, 2, 16, 1, 1), (4, 4, 12, 1, 1),
                                                 (8, 4, 16, 0, 1), (64, 64, 16, 0, 1), (16, 16, 20, 1, 1),
-                                                (8, 8, 16, 0, 0), (64, 64, 16, 0, 0), (3, 5, 9, 0, 0)])
+                                                (8, 8, 16, 0, 0), (64, 64, 16, 0, 0), (3, 5, 9, 0, 0),
+                                                (128, 128, 16, 0, 1), (32, 32, 30, 1, 1), (64, 64, 24, 0, 1)])
 def test_plan_descriptors_stay_in_bounds(lib, nx, ny, p, prec, store):
     # Every kernel descriptor of the build, solve and adjoint plans is checked against the
-    # size of the buffer it addresses, on the host, before any launch.
+    # size of the buffer it addresses, on the host, before any launch; the larger trees
+    # include the blocked merge eliminations' product items and vector-digit groups (K up
+    # to 960 in chunks of at most 448).
     from paper_1612_02736_gb300 import _native
     t = _tree(lib, nx, ny)
     opts = _native.hps_opts()
