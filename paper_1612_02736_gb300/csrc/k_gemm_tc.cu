@@ -20,14 +20,19 @@
 // reads) and 32 right-hand sides (MMA N = 32).  A first kernel writes every unit's 32 column
 // exponents (and its 64 row exponents unless the operator's digits are cached: the
 // operators are fixed after the build, so a product set can keep their digit planes, formed
-// once by gemm_digits_kernel).  The product kernel's roles (17 warps, one CTA per SM
-// looping over the units):
+// once by gemm_digits_kernel; a set of items that gathers the same vector rows, such as
+// the Schur products of the blocked merge elimination, can likewise keep the vectors'
+// digit planes, formed once by gemm_bdigits_kernel, and then needs no exponent pass and
+// forms no digits at all).  The product kernel's roles (17 warps, one CTA per SM looping
+// over the units):
 //   warps 0, 1, 4, 5   epilogue: TMEM lanes 0..63 (warp w reads lane quarter w % 4), 16
-//              right-hand sides per thread, four at a time; recombination, beta, Add, scatter;
+//              right-hand sides per thread, copied from TMEM to padded shared-memory rows
+//              (which frees TMEM for the next unit) and recombined from there, four at a
+//              time; beta, Add, scatter;
 //   the other warps but 16  producers (12 warps, spread over the four SM sub-partitions):
 //              per K step of 16 the digit planes of A (64 x 16, or one bulk copy of the
-//              cached planes) and B (32 x 16), one task of 4 consecutive k per thread, three
-//              stages deep;
+//              cached planes) and B (32 x 16, or one bulk copy of cached planes), one task
+//              of 4 consecutive k per thread, four stages deep;
 //   warp 16    one thread issues the digit-pair products of each K step into TMEM.
 // Handoffs are mbarriers with bounded waits; a timeout stops every role (status -1).
 #include <algorithm>
